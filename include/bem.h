@@ -1,0 +1,180 @@
+/*
+ * bem.h — C ABI of the GB300 FMM-accelerated boundary-element library (libbem.so).
+ *
+ * The library computes the collocation boundary-element operators of the bubble-dynamics
+ * method of Gumerov, Pityuk, Abramova and Akhatov (arXiv:1905.01341):
+ *   - single layer  L[q](r_i)   ~ sum_j L_ij q_j,    double layer M[phi](r_i) ~ sum_j M_ij phi_j
+ *     (Section 3.1, Eq. (d1)), kernels G = 1/(4 pi |r - r'|) and dG/dn' = n'.(r - r')/(4 pi |r - r'|^3)
+ *     with the normal pointing out of the bubble (Eq. (2.13));
+ *   - off-diagonal entries by the one-point vertex quadrature L_ij = s_j G(r_i, r_j),
+ *     M_ij = s_j dG/dn_j(r_i, r_j), i != j, with s_j = (1/3) sum A_k and n_j the normalised
+ *     area-weighted triangle normal (Section 3.2, Eq. (ns1));
+ *   - singular diagonals from the integral identities M_ii = -1/2 - sum_{j!=i} M_ij (Eq. (s3))
+ *     and L_ii = n_i . [sum_{j!=i} (M_ij r_j - L_ij n_j) + (1/2 + M_ii) r_i] (Eq. (s5));
+ *   - the combined product (f L + g M) X (Eq. (3.27)) by the fast multipole method
+ *     (Section 3.7: octree to uniform depth, multipole/local expansions truncated at degree
+ *     p_fmm - 1) or by the direct O(N^2) sum (Section 3.9, "GPU" brute force);
+ *   - the Dirichlet solve L q = b, b = -phi/2 + M phi (Eqs. (3.1)-(3.2)) by unpreconditioned
+ *     GMRES started from a caller-given guess (Section 3.8).
+ *
+ * Conventions (all entry points):
+ *   - Every function returns a bem_status (0 = BEM_OK). No C++ exception crosses the ABI.
+ *     On failure bem_last_error(ctx) returns a NUL-terminated message owned by the context,
+ *     valid until the next call on that context.
+ *   - Array arguments are plain pointers. Each may point to host memory or to device
+ *     memory of the context's device; the library detects which. Device arrays are read and
+ *     written in order on the context's stream; host arrays are copied through internal
+ *     device buffers and the call returns after the host output is written.
+ *   - The caller owns every array it passes; the library never keeps a caller pointer
+ *     beyond the call. The context owns all internal buffers.
+ *   - Vertex arrays are indexed in the caller's vertex order. Coordinates are SoA:
+ *     xyz[0..N) = x, xyz[N..2N) = y, xyz[2N..3N) = z (double). Triangles are SoA int32:
+ *     tri[0..T) = first corner, tri[T..2T) = second, tri[2T..3T) = third; corners are
+ *     counter-clockwise seen from the liquid (outward normal, Section 3.4).
+ *   - The API is FP64. The precision mode changes internal arithmetic only.
+ *   - A context is not thread-safe: calls on one context must not overlap.
+ */
+#ifndef BEM_H_
+#define BEM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BEM_OK = 0,
+    BEM_ERR_ARG = 1,       /* invalid argument (null pointer, size, parameter range)          */
+    BEM_ERR_MESH = 2,      /* invalid mesh (index out of range, isolated vertex, zero normal) */
+    BEM_ERR_NOT_BUILT = 3, /* apply/solve before bem_mesh_upload + fmm_build                  */
+    BEM_ERR_NOCONV = 4,    /* GMRES hit maxit; q holds the last iterate, relres is set        */
+    BEM_ERR_TIMEOUT = 5,   /* a bounded device wait ran out                                   */
+    BEM_ERR_CUDA = 6,      /* CUDA runtime error                                              */
+    BEM_ERR_NAN = 7,       /* non-finite value in a result                                    */
+    BEM_ERR_NOMEM = 8      /* device allocation failed                                        */
+} bem_status;
+
+typedef enum {
+    BEM_PREC_FP64 = 0,  /* every kernel in FP64                                                */
+    BEM_PREC_MIXED = 1  /* near field and expansions in FP32 with compensated sums; geometry,
+                           diagonal assembly, GMRES and all API vectors stay FP64            */
+} bem_precision;
+
+typedef enum {
+    BEM_MVP_FMM = 0,    /* fast multipole method (Section 3.7)                                */
+    BEM_MVP_DIRECT = 1  /* direct all-pairs sum (Section 3.9 brute force; small N)            */
+} bem_mvp_kind;
+
+/* Parameters of a context. Fill with bem_params_default() and override fields. */
+typedef struct {
+    int32_t p_fmm;          /* truncation number: degrees 0..p_fmm-1, p_fmm^2 coefficients
+                               per expansion (Section 3.7). Range 2..20. Default 14.           */
+    int32_t leaf_target;    /* target mean points per non-empty leaf box (the clustering
+                               parameter s of Section 3.6). Default 64.                        */
+    int32_t fixed_level;    /* > 0: force the octree depth l_max to this value (2..10).        */
+    int32_t precision;      /* bem_precision. Default BEM_PREC_MIXED.                          */
+    int32_t mvp;            /* bem_mvp_kind. Default BEM_MVP_FMM.                              */
+    int32_t diag_precision; /* precision of the 4-RHS product that feeds Eqs. (s3)/(s5);
+                               -1 = same as `precision`. Default -1.                           */
+    int32_t gmres_maxit;    /* maximum GMRES iterations. Default 100.                          */
+    int32_t gmres_restart;  /* restart length; 0 = no restart (= maxit). Default 0.            */
+    double gmres_tol;       /* stop when |b - L q| / |b| <= tol (Section 3.8). Default 1e-6.  */
+} bem_params;
+
+/* Run-time counters of a context (cumulative since bem_create or bem_reset_stats). */
+typedef struct {
+    int64_t n_apply;        /* operator products (each multi-RHS product counts once)          */
+    int64_t n_apply_rhs;    /* right-hand sides processed by those products                    */
+    int64_t p2p_pairs;      /* near-field (or direct) source-receiver pairs per RHS, last build */
+    int64_t m2l_pairs;      /* M2L translations per RHS, all levels, last build               */
+    int32_t levels;         /* octree depth l_max of the last build                            */
+    int32_t leaves;         /* non-empty leaf boxes of the last build                          */
+    int32_t last_iters;     /* GMRES iterations of the last solve                              */
+    int32_t last_mvps;      /* operator products of the last solve (iterations + 2)            */
+    double last_relres;     /* true relative residual of the last solve                        */
+    double last_build_ms;   /* device time of the last fmm_build                               */
+    int64_t n_launches;     /* kernels launched by the library in this process (all contexts)   */
+} bem_stats;
+
+/* Phases reported by bem_profile_read, in this order. */
+#define BEM_NUM_PHASES 13
+/* geometry, tree, operators, strengths, p2m, m2m, m2l, l2l, l2p, p2p, direct, diag, gmres */
+
+/* Fill *p with the defaults listed above. */
+int bem_params_default(bem_params *p);
+
+/* Create a context on the current CUDA device. `stream` is a cudaStream_t (NULL = the
+ * legacy default stream); every kernel of the context runs on it. */
+int bem_create(void **ctx_out, const bem_params *p, void *stream);
+
+/* Destroy a context and free its device memory. Accepts NULL. */
+void bem_destroy(void *ctx);
+
+/* Change the stream of an existing context. */
+int bem_set_stream(void *ctx, void *stream);
+
+/* Message of the last failed call on ctx (or of the last failed bem_create when ctx is NULL). */
+const char *bem_last_error(const void *ctx);
+
+/* Section 2.1/3.1: upload the surface mesh. N vertices (collocation points) with SoA
+ * coordinates xyz[3N]; T triangles tri[3T] (SoA, 0-based vertex indices); M bubbles with
+ * vert_off[M+1] and tri_off[M+1] (bubble m owns vertices vert_off[m]..vert_off[m+1]-1 and
+ * triangles tri_off[m]..tri_off[m+1]-1). Copies the data into the context and invalidates
+ * any previous build. Returns BEM_ERR_ARG for bad sizes or offsets. */
+int bem_mesh_upload(void *ctx, int64_t N, const double *xyz, int64_t T, const int32_t *tri,
+                    int64_t M, const int64_t *vert_off, const int64_t *tri_off);
+
+/* Replace the vertex coordinates of the uploaded mesh (same N, same triangles), as a
+ * time step does (Eq. (3.14)); invalidates the build. */
+int bem_mesh_update_xyz(void *ctx, const double *xyz);
+
+/* Section 3.2 and 3.7: vertex weights and normals (Eq. (ns1)), the octree (bounding cube,
+ * Morton keys, radix sort, level boxes, neighbour and M2L lists), the FMM translation
+ * operators, and the singular diagonals (Eqs. (s3), (s5)) from one 4-RHS product.
+ * Returns BEM_ERR_MESH for an isolated vertex or a zero area-weighted normal. */
+int fmm_build(void *ctx);
+
+/* Eq. (3.27): out = f L xL + g M xM (diagonals included). xL may be NULL when f == 0 and
+ * xM may be NULL when g == 0. All vectors have length N. */
+int bem_apply(void *ctx, double f, const double *xL, double g, const double *xM, double *out);
+
+/* Eq. (d1): out = L q (single layer, with L_ii). */
+int bem_apply_sl(void *ctx, const double *q, double *out);
+
+/* Eq. (d1): out = M phi (double layer, with M_ii; no -phi/2 term). */
+int bem_apply_dl(void *ctx, const double *phi, double *out);
+
+/* Eq. (3.1): b = -phi/2 + M phi. */
+int bem_rhs(void *ctx, const double *phi, double *b);
+
+/* Eqs. (3.1)-(3.2), Section 3.8: given phi on S solve L q = b by GMRES with initial guess
+ * q_inout (in), returning q in q_inout. iters and relres (true relative residual
+ * |b - L q| / |b|) may be NULL. Returns BEM_ERR_NOCONV when maxit is reached. */
+int bem_solve(void *ctx, const double *phi, double *q_inout, int32_t *iters, double *relres);
+
+/* Copies of the geometry of the last build, in the caller's vertex order: s[N], n[3N]
+ * (SoA), Ldiag[N], Mdiag[N]. Any pointer may be NULL. */
+int bem_get_geometry(void *ctx, double *s, double *n, double *ldiag, double *mdiag);
+
+/* Counters; see bem_stats. */
+int bem_get_stats(void *ctx, bem_stats *out);
+int bem_reset_stats(void *ctx);
+
+/* Per-phase device timing. While enabled, each phase's kernels are bracketed by CUDA events
+ * recorded on the context's stream (a few microseconds of overhead per phase). */
+int bem_profile_enable(void *ctx, int on);
+
+/* Synchronises the context's stream and returns, per phase (BEM_NUM_PHASES entries), the
+ * device milliseconds and the number of timed intervals recorded since the last read; then
+ * clears the records. Either array may be NULL. */
+int bem_profile_read(void *ctx, double *ms, int64_t *intervals);
+
+/* Name of phase i (0 <= i < BEM_NUM_PHASES), or NULL. */
+const char *bem_phase_name(int i);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BEM_H_ */

@@ -1,0 +1,311 @@
+"""Python binding of libbem.so (include/bem.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and forwards plain
+pointers and sizes; all arithmetic runs in the CUDA library. Arrays may be torch tensors
+(CUDA or CPU) or numpy arrays; they must be contiguous and of the documented dtype. The
+library must have been built (``paper_1905_01341_gb300.build.build()``); importing this
+module without it raises, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libbem.so")
+
+BEM_OK = 0
+BEM_ERR_ARG = 1
+BEM_ERR_MESH = 2
+BEM_ERR_NOT_BUILT = 3
+BEM_ERR_NOCONV = 4
+BEM_ERR_TIMEOUT = 5
+BEM_ERR_CUDA = 6
+BEM_ERR_NAN = 7
+BEM_ERR_NOMEM = 8
+
+BEM_PREC_FP64 = 0
+BEM_PREC_MIXED = 1
+BEM_MVP_FMM = 0
+BEM_MVP_DIRECT = 1
+
+EXPORTED = [
+    "bem_params_default", "bem_create", "bem_destroy", "bem_set_stream", "bem_last_error",
+    "bem_mesh_upload", "bem_mesh_update_xyz", "fmm_build", "bem_apply", "bem_apply_sl",
+    "bem_apply_dl", "bem_rhs", "bem_solve", "bem_get_geometry", "bem_get_stats",
+    "bem_reset_stats", "bem_profile_enable", "bem_profile_read", "bem_phase_name",
+]
+
+BEM_NUM_PHASES = 13
+
+
+class bem_params(ctypes.Structure):
+    _fields_ = [
+        ("p_fmm", ctypes.c_int32),
+        ("leaf_target", ctypes.c_int32),
+        ("fixed_level", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("mvp", ctypes.c_int32),
+        ("diag_precision", ctypes.c_int32),
+        ("gmres_maxit", ctypes.c_int32),
+        ("gmres_restart", ctypes.c_int32),
+        ("gmres_tol", ctypes.c_double),
+    ]
+
+
+class bem_stats(ctypes.Structure):
+    _fields_ = [
+        ("n_apply", ctypes.c_int64),
+        ("n_apply_rhs", ctypes.c_int64),
+        ("p2p_pairs", ctypes.c_int64),
+        ("m2l_pairs", ctypes.c_int64),
+        ("levels", ctypes.c_int32),
+        ("leaves", ctypes.c_int32),
+        ("last_iters", ctypes.c_int32),
+        ("last_mvps", ctypes.c_int32),
+        ("last_relres", ctypes.c_double),
+        ("last_build_ms", ctypes.c_double),
+        ("n_launches", ctypes.c_int64),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class BemError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("bem status %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libbem.so. Raises when it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libbem.so is not built (%s); run paper_1905_01341_gb300.build.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+        sig = {
+            "bem_params_default": ([ctypes.POINTER(bem_params)], ctypes.c_int),
+            "bem_create": ([ctypes.POINTER(vp), ctypes.POINTER(bem_params), vp], ctypes.c_int),
+            "bem_destroy": ([vp], None),
+            "bem_set_stream": ([vp, vp], ctypes.c_int),
+            "bem_last_error": ([vp], ctypes.c_char_p),
+            "bem_mesh_upload": ([vp, i64, vp, i64, vp, i64, vp, vp], ctypes.c_int),
+            "bem_mesh_update_xyz": ([vp, vp], ctypes.c_int),
+            "fmm_build": ([vp], ctypes.c_int),
+            "bem_apply": ([vp, dbl, vp, dbl, vp, vp], ctypes.c_int),
+            "bem_apply_sl": ([vp, vp, vp], ctypes.c_int),
+            "bem_apply_dl": ([vp, vp, vp], ctypes.c_int),
+            "bem_rhs": ([vp, vp, vp], ctypes.c_int),
+            "bem_solve": ([vp, vp, vp, ctypes.POINTER(i32), ctypes.POINTER(dbl)], ctypes.c_int),
+            "bem_get_geometry": ([vp, vp, vp, vp, vp], ctypes.c_int),
+            "bem_get_stats": ([vp, ctypes.POINTER(bem_stats)], ctypes.c_int),
+            "bem_reset_stats": ([vp], ctypes.c_int),
+            "bem_profile_enable": ([vp, ctypes.c_int], ctypes.c_int),
+            "bem_profile_read": ([vp, ctypes.POINTER(dbl), ctypes.POINTER(i64)], ctypes.c_int),
+            "bem_phase_name": ([ctypes.c_int], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _ptr(x, dtype=None):
+    """Raw pointer of a contiguous torch tensor or numpy array (None stays None)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        if dtype is not None and x.dtype != np.dtype(dtype):
+            raise TypeError("expected dtype %s, got %s" % (dtype, x.dtype))
+        return ctypes.c_void_p(x.ctypes.data)
+    import torch  # torch tensors: device memory comes from torch
+
+    if isinstance(x, torch.Tensor):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        want = {np.float64: torch.float64, np.int32: torch.int32, np.int64: torch.int64}.get(dtype)
+        if want is not None and x.dtype != want:
+            raise TypeError("expected dtype %s, got %s" % (want, x.dtype))
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    raise TypeError("unsupported array type %r" % type(x))
+
+
+def _check(ctx, rc: int):
+    if rc != BEM_OK:
+        msg = lib().bem_last_error(ctx)
+        raise BemError(rc, msg.decode() if msg else "")
+
+
+# ------------------------------------------------------------------ one wrapper per entry point
+
+
+def bem_params_default(**overrides) -> bem_params:
+    p = bem_params()
+    lib().bem_params_default(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def bem_create(params: bem_params | None = None, stream=None):
+    """Create a context on the current device. `stream`: a torch.cuda.Stream, an int
+    handle, or None (torch's current stream)."""
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream()
+    handle = stream if isinstance(stream, int) else stream.cuda_stream
+    ctx = ctypes.c_void_p()
+    rc = lib().bem_create(ctypes.byref(ctx), ctypes.byref(params) if params is not None else None,
+                          ctypes.c_void_p(handle))
+    _check(None, rc)
+    return ctx
+
+
+def bem_destroy(ctx) -> None:
+    lib().bem_destroy(ctx)
+
+
+def bem_set_stream(ctx, stream) -> None:
+    handle = stream if isinstance(stream, int) else stream.cuda_stream
+    _check(ctx, lib().bem_set_stream(ctx, ctypes.c_void_p(handle)))
+
+
+def bem_last_error(ctx) -> str:
+    m = lib().bem_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def bem_mesh_upload(ctx, N, xyz, T, tri, M, vert_off, tri_off) -> None:
+    _check(ctx, lib().bem_mesh_upload(ctx, int(N), _ptr(xyz, np.float64), int(T), _ptr(tri, np.int32), int(M),
+                                      _ptr(vert_off, np.int64), _ptr(tri_off, np.int64)))
+
+
+def bem_mesh_update_xyz(ctx, xyz) -> None:
+    _check(ctx, lib().bem_mesh_update_xyz(ctx, _ptr(xyz, np.float64)))
+
+
+def fmm_build(ctx) -> None:
+    _check(ctx, lib().fmm_build(ctx))
+
+
+def bem_apply(ctx, f, xL, g, xM, out) -> None:
+    _check(ctx, lib().bem_apply(ctx, float(f), _ptr(xL, np.float64), float(g), _ptr(xM, np.float64),
+                                _ptr(out, np.float64)))
+
+
+def bem_apply_sl(ctx, q, out) -> None:
+    _check(ctx, lib().bem_apply_sl(ctx, _ptr(q, np.float64), _ptr(out, np.float64)))
+
+
+def bem_apply_dl(ctx, phi, out) -> None:
+    _check(ctx, lib().bem_apply_dl(ctx, _ptr(phi, np.float64), _ptr(out, np.float64)))
+
+
+def bem_rhs(ctx, phi, b) -> None:
+    _check(ctx, lib().bem_rhs(ctx, _ptr(phi, np.float64), _ptr(b, np.float64)))
+
+
+def bem_solve(ctx, phi, q_inout, raise_on_noconv: bool = True):
+    """Returns (iterations, true relative residual); q_inout holds the solution."""
+    it = ctypes.c_int32(0)
+    rr = ctypes.c_double(0.0)
+    rc = lib().bem_solve(ctx, _ptr(phi, np.float64), _ptr(q_inout, np.float64), ctypes.byref(it), ctypes.byref(rr))
+    if rc == BEM_ERR_NOCONV and not raise_on_noconv:
+        return int(it.value), float(rr.value)
+    _check(ctx, rc)
+    return int(it.value), float(rr.value)
+
+
+def bem_get_geometry(ctx, s=None, n=None, ldiag=None, mdiag=None) -> None:
+    _check(ctx, lib().bem_get_geometry(ctx, _ptr(s, np.float64), _ptr(n, np.float64), _ptr(ldiag, np.float64),
+                                       _ptr(mdiag, np.float64)))
+
+
+def bem_get_stats(ctx) -> dict:
+    st = bem_stats()
+    _check(ctx, lib().bem_get_stats(ctx, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def bem_reset_stats(ctx) -> None:
+    _check(ctx, lib().bem_reset_stats(ctx))
+
+
+def bem_profile_enable(ctx, on: bool = True) -> None:
+    _check(ctx, lib().bem_profile_enable(ctx, 1 if on else 0))
+
+
+def bem_profile_read(ctx) -> dict:
+    """{phase name: (device ms, timed intervals)} since the last read."""
+    ms = (ctypes.c_double * BEM_NUM_PHASES)()
+    cnt = (ctypes.c_int64 * BEM_NUM_PHASES)()
+    _check(ctx, lib().bem_profile_read(ctx, ms, cnt))
+    return {bem_phase_name(i): (float(ms[i]), int(cnt[i])) for i in range(BEM_NUM_PHASES)}
+
+
+def bem_phase_name(i: int) -> str:
+    n = lib().bem_phase_name(int(i))
+    return n.decode() if n else ""
+
+
+# ------------------------------------------------------------------ convenience
+
+
+class BemContext:
+    """Owns one context; methods take torch tensors or numpy arrays (SoA layouts of bem.h)."""
+
+    def __init__(self, stream=None, **params):
+        self.params = bem_params_default(**params)
+        self.ctx = bem_create(self.params, stream)
+        self.N = 0
+
+    def close(self):
+        if self.ctx is not None:
+            bem_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def upload(self, xyz_soa, tri_soa, vert_off, tri_off):
+        N = int(xyz_soa.shape[-1])
+        T = int(tri_soa.shape[-1])
+        M = int(vert_off.shape[0]) - 1
+        bem_mesh_upload(self.ctx, N, xyz_soa, T, tri_soa, M, vert_off, tri_off)
+        self.N = N
+
+    def upload_mesh(self, mesh):
+        """Upload a synth.Mesh-like object (numpy arrays) from host memory."""
+        self.upload(mesh.xyz_soa(), mesh.tri_soa(), np.ascontiguousarray(mesh.vert_off, np.int64),
+                    np.ascontiguousarray(mesh.tri_off, np.int64))
+
+    def build(self):
+        fmm_build(self.ctx)
+
+    def apply(self, f, xL, g, xM, out):
+        bem_apply(self.ctx, f, xL, g, xM, out)
+        return out
+
+    def solve(self, phi, q, raise_on_noconv=True):
+        return bem_solve(self.ctx, phi, q, raise_on_noconv)
+
+    def stats(self) -> dict:
+        return bem_get_stats(self.ctx)

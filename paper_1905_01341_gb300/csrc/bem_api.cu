@@ -1,0 +1,489 @@
+// C ABI of libbem.so (declared in include/bem.h): context management, mesh upload, build,
+// operator products, right-hand side and the GMRES solve. Host or device pointers are
+// accepted for every array; host arrays are staged through context-owned device buffers.
+#include "internal.h"
+
+#include <cmath>
+#include <cstring>
+#include <exception>
+
+namespace bem {
+
+long long g_launch_count = 0;
+
+Context::~Context() {
+    for (auto *p : up_chunks) delete p;
+}
+
+namespace {
+
+thread_local std::string g_create_error;
+
+__global__ void k_add_diag(int64_t N, double f, const double *__restrict__ xL, double g,
+                           const double *__restrict__ xM, const double *__restrict__ ld,
+                           const double *__restrict__ md, double *__restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double v = out[i];
+    if (f != 0.0) v += f * ld[i] * xL[i];
+    if (g != 0.0) v += g * md[i] * xM[i];
+    out[i] = v;
+}
+
+// Eq. (s3): M_ii = -1/2 - (M_off 1)_i.  Eq. (s5): L_ii = n_i . [v_i + (1/2 + M_ii) r_i] with
+// v_i = sum_{j != i} (M_ij r_j - L_ij n_j) componentwise.
+__global__ void k_diag_identities(int64_t N, const double *__restrict__ d0, const double *__restrict__ vx,
+                                  const double *__restrict__ vy, const double *__restrict__ vz,
+                                  const double *__restrict__ xyz, const double *__restrict__ nrm,
+                                  double *__restrict__ ld, double *__restrict__ md) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double m = -0.5 - d0[i];
+    double a = 0.5 + m;
+    md[i] = m;
+    ld[i] = nrm[i] * (vx[i] + a * xyz[i]) + nrm[N + i] * (vy[i] + a * xyz[N + i]) +
+            nrm[2 * N + i] * (vz[i] + a * xyz[2 * N + i]);
+}
+
+__global__ void k_fill(int64_t N, double v, double *a) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < N) a[i] = v;
+}
+
+__global__ void k_split(int64_t N, const double *__restrict__ x, float *__restrict__ hi, float *__restrict__ lo) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float h = (float)x[i];
+    hi[i] = h;
+    lo[i] = (float)(x[i] - (double)h);
+}
+
+__global__ void k_rhs_combine(int64_t N, const double *__restrict__ phi, double *__restrict__ b) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < N) b[i] += -0.5 * phi[i];
+}
+
+__global__ void k_check_finite(int64_t N, const double *__restrict__ a, int *__restrict__ bad) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < N && !isfinite(a[i])) atomicOr(bad, 1);
+}
+
+Context *as_ctx(void *p) {
+    if (!p) fail(BEM_ERR_ARG, "null context");
+    return static_cast<Context *>(p);
+}
+
+bool is_device_ptr(const Context &c, const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a{};
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+        if (a.type == cudaMemoryTypeDevice && a.device != c.device)
+            fail(BEM_ERR_ARG, "device pointer belongs to another device");
+        return true;
+    }
+    return false;
+}
+
+// Device view of an input vector of length n (copies host arrays into stage buffer k).
+const double *dev_in(Context &c, const double *p, int64_t n, int k) {
+    if (!p) return nullptr;
+    if (is_device_ptr(c, p)) return p;
+    c.stage_in[k].resize(n);
+    BEM_CUDA(cudaMemcpyAsync(c.stage_in[k].p, p, n * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    return c.stage_in[k].p;
+}
+
+struct OutView {
+    Context &c;
+    double *user;
+    double *dev;
+    int64_t n;
+    bool host;
+    OutView(Context &cc, double *p, int64_t nn) : c(cc), user(p), n(nn) {
+        if (!p) fail(BEM_ERR_ARG, "null output");
+        host = !is_device_ptr(c, p);
+        if (host) {
+            c.stage_out.resize(n);
+            dev = c.stage_out.p;
+        } else {
+            dev = p;
+        }
+    }
+    void finish() {
+        if (host) {
+            BEM_CUDA(cudaMemcpyAsync(user, dev, n * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+            BEM_CUDA(cudaStreamSynchronize(c.stream));
+        }
+    }
+};
+
+void require_built(Context &c) {
+    if (!c.mesh_ok) fail(BEM_ERR_NOT_BUILT, "no mesh uploaded");
+    if (!c.built) fail(BEM_ERR_NOT_BUILT, "fmm_build has not been called since the last mesh change");
+}
+
+template <class F>
+int guarded(void *ctx, F &&fn) {
+    Context *c = nullptr;
+    try {
+        c = as_ctx(ctx);
+        c->err.clear();
+        BEM_CUDA(cudaSetDevice(c->device));
+        fn(*c);
+        return BEM_OK;
+    } catch (const Error &e) {
+        if (c) c->err = e.msg;
+        else g_create_error = e.msg;
+        return e.code;
+    } catch (const std::exception &e) {
+        if (c) c->err = e.what();
+        return BEM_ERR_CUDA;
+    }
+}
+
+void check_params(const bem_params &p) {
+    if (p.p_fmm < 2 || p.p_fmm > kMaxPfmm) fail(BEM_ERR_ARG, "p_fmm must be in 2..20");
+    if (p.leaf_target < 1) fail(BEM_ERR_ARG, "leaf_target must be >= 1");
+    if (p.fixed_level < 0 || p.fixed_level > kDeepLevel || p.fixed_level == 1)
+        fail(BEM_ERR_ARG, "fixed_level must be 0 or in 2..10");
+    if (p.precision != BEM_PREC_FP64 && p.precision != BEM_PREC_MIXED) fail(BEM_ERR_ARG, "bad precision");
+    if (p.diag_precision != -1 && p.diag_precision != BEM_PREC_FP64 && p.diag_precision != BEM_PREC_MIXED)
+        fail(BEM_ERR_ARG, "bad diag_precision");
+    if (p.mvp != BEM_MVP_FMM && p.mvp != BEM_MVP_DIRECT) fail(BEM_ERR_ARG, "bad mvp kind");
+    if (p.gmres_maxit < 1 || p.gmres_restart < 0 || p.gmres_restart > 127) fail(BEM_ERR_ARG, "bad GMRES limits");
+    if (!(p.gmres_tol > 0.0)) fail(BEM_ERR_ARG, "gmres_tol must be > 0");
+}
+
+}  // namespace
+
+// out = f (L_off + diag(Ldiag)) xL + g (M_off + diag(Mdiag)) xM, all device pointers.
+void apply_full(Context &c, double f, const double *xL, double g, const double *xM, double *out) {
+    double fa[1] = {f}, ga[1] = {g};
+    const double *xl[1] = {xL};
+    const double *xm[1] = {xM};
+    double *o[1] = {out};
+    offdiag_apply(c, 1, fa, xl, ga, xm, o, c.prm.precision);
+    k_add_diag<<<div_up(c.N, 256), 256, 0, c.stream>>>(c.N, f, xL, g, xM, c.ldiag.p, c.mdiag.p, out);
+    BEM_LAUNCH_CHECK();
+}
+
+}  // namespace bem
+
+using namespace bem;
+
+extern "C" {
+
+int bem_params_default(bem_params *p) {
+    if (!p) return BEM_ERR_ARG;
+    std::memset(p, 0, sizeof(*p));
+    p->p_fmm = 14;
+    p->leaf_target = 64;
+    p->fixed_level = 0;
+    p->precision = BEM_PREC_MIXED;
+    p->mvp = BEM_MVP_FMM;
+    p->diag_precision = -1;
+    p->gmres_maxit = 100;
+    p->gmres_restart = 0;
+    p->gmres_tol = 1e-6;
+    return BEM_OK;
+}
+
+int bem_create(void **ctx_out, const bem_params *p, void *stream) {
+    if (!ctx_out) return BEM_ERR_ARG;
+    *ctx_out = nullptr;
+    Context *c = nullptr;
+    try {
+        bem_params prm;
+        if (p) prm = *p;
+        else bem_params_default(&prm);
+        check_params(prm);
+        c = new Context();
+        c->prm = prm;
+        c->stream = static_cast<cudaStream_t>(stream);
+        BEM_CUDA(cudaGetDevice(&c->device));
+        *ctx_out = c;
+        return BEM_OK;
+    } catch (const Error &e) {
+        g_create_error = e.msg;
+        delete c;
+        return e.code;
+    }
+}
+
+void bem_destroy(void *ctx) {
+    if (!ctx) return;
+    Context *c = static_cast<Context *>(ctx);
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    delete c;
+}
+
+int bem_set_stream(void *ctx, void *stream) {
+    return guarded(ctx, [&](Context &c) { c.stream = static_cast<cudaStream_t>(stream); });
+}
+
+const char *bem_last_error(const void *ctx) {
+    if (!ctx) return g_create_error.c_str();
+    return static_cast<const Context *>(ctx)->err.c_str();
+}
+
+int bem_mesh_upload(void *ctx, int64_t N, const double *xyz, int64_t T, const int32_t *tri, int64_t M,
+                    const int64_t *vert_off, const int64_t *tri_off) {
+    return guarded(ctx, [&](Context &c) {
+        if (N < 2 || T < 1 || M < 1 || !xyz || !tri || !vert_off || !tri_off) fail(BEM_ERR_ARG, "bad mesh sizes or null arrays");
+        if (N > (int64_t)INT32_MAX / 2 || T > (int64_t)INT32_MAX / 3) fail(BEM_ERR_ARG, "mesh too large for 32-bit indices");
+        c.built = false;
+        c.mesh_ok = false;
+        c.N = N;
+        c.T = T;
+        c.M = M;
+        c.xyz.resize(3 * N);
+        c.tri.resize(3 * T);
+        auto kind = [&](const void *p) { return is_device_ptr(c, p) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; };
+        BEM_CUDA(cudaMemcpyAsync(c.xyz.p, xyz, 3 * N * sizeof(double), kind(xyz), c.stream));
+        BEM_CUDA(cudaMemcpyAsync(c.tri.p, tri, 3 * T * sizeof(int32_t), kind(tri), c.stream));
+        c.vert_off.resize(M + 1);
+        c.tri_off.resize(M + 1);
+        auto kind_h = [&](const void *p) { return is_device_ptr(c, p) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost; };
+        BEM_CUDA(cudaMemcpyAsync(c.vert_off.data(), vert_off, (M + 1) * sizeof(int64_t), kind_h(vert_off), c.stream));
+        BEM_CUDA(cudaMemcpyAsync(c.tri_off.data(), tri_off, (M + 1) * sizeof(int64_t), kind_h(tri_off), c.stream));
+        BEM_CUDA(cudaStreamSynchronize(c.stream));
+        if (c.vert_off[0] != 0 || c.vert_off[M] != N || c.tri_off[0] != 0 || c.tri_off[M] != T)
+            fail(BEM_ERR_ARG, "offsets must start at 0 and end at N / T");
+        for (int64_t m = 0; m < M; ++m)
+            if (c.vert_off[m + 1] < c.vert_off[m] || c.tri_off[m + 1] < c.tri_off[m])
+                fail(BEM_ERR_ARG, "offsets must be non-decreasing");
+        build_vertex_triangle_csr(c);
+        c.mesh_ok = true;
+    });
+}
+
+int bem_mesh_update_xyz(void *ctx, const double *xyz) {
+    return guarded(ctx, [&](Context &c) {
+        if (!c.mesh_ok) fail(BEM_ERR_NOT_BUILT, "no mesh uploaded");
+        if (!xyz) fail(BEM_ERR_ARG, "null xyz");
+        c.built = false;
+        auto k = is_device_ptr(c, xyz) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        BEM_CUDA(cudaMemcpyAsync(c.xyz.p, xyz, 3 * c.N * sizeof(double), k, c.stream));
+    });
+}
+
+int fmm_build(void *ctx) {
+    return guarded(ctx, [&](Context &c) {
+        if (!c.mesh_ok) fail(BEM_ERR_NOT_BUILT, "no mesh uploaded");
+        cudaEvent_t e0, e1;
+        BEM_CUDA(cudaEventCreate(&e0));
+        BEM_CUDA(cudaEventCreate(&e1));
+        BEM_CUDA(cudaEventRecord(e0, c.stream));
+        c.built = false;
+        {
+            PhaseScope ps(c, PH_GEOMETRY);
+            compute_vertex_geometry(c);
+        }
+        const int64_t N = c.N;
+        if (c.prm.mvp == BEM_MVP_FMM) {
+            build_operators(c);
+            {
+                PhaseScope ps(c, PH_TREE);
+                build_tree(c);
+            }
+            c.m2l_chunks_h.clear();
+            c.stats.p2p_pairs = c.tree.p2p_pairs;
+            c.stats.m2l_pairs = c.tree.n_m2l;
+            c.stats.levels = c.tree.L;
+            c.stats.leaves = c.tree.nb[c.tree.L];
+        } else {
+            c.dir_hi.resize(3 * N);
+            c.dir_lo.resize(3 * N);
+            k_split<<<div_up(3 * N, 256), 256, 0, c.stream>>>(3 * N, c.xyz.p, c.dir_hi.p, c.dir_lo.p);
+            BEM_LAUNCH_CHECK();
+            c.stats.p2p_pairs = N * (N - 1);
+            c.stats.m2l_pairs = 0;
+            c.stats.levels = 0;
+            c.stats.leaves = 0;
+        }
+        // diagonals from one 4-RHS off-diagonal product (Eqs. (s3), (s5))
+        c.ones.resize(N);
+        k_fill<<<div_up(N, 256), 256, 0, c.stream>>>(N, 1.0, c.ones.p);
+        BEM_LAUNCH_CHECK();
+        DevBuf<double> tmp;
+        tmp.resize(4 * N);
+        double fa[4] = {0.0, -1.0, -1.0, -1.0}, ga[4] = {1.0, 1.0, 1.0, 1.0};
+        const double *xl[4] = {nullptr, c.nrm.p, c.nrm.p + N, c.nrm.p + 2 * N};
+        const double *xm[4] = {c.ones.p, c.xyz.p, c.xyz.p + N, c.xyz.p + 2 * N};
+        double *o[4] = {tmp.p, tmp.p + N, tmp.p + 2 * N, tmp.p + 3 * N};
+        int dprec = c.prm.diag_precision < 0 ? c.prm.precision : c.prm.diag_precision;
+        offdiag_apply(c, 4, fa, xl, ga, xm, o, dprec);
+        c.ldiag.resize(N);
+        c.mdiag.resize(N);
+        PhaseScope ps(c, PH_DIAG);
+        k_diag_identities<<<div_up(N, 256), 256, 0, c.stream>>>(N, o[0], o[1], o[2], o[3], c.xyz.p, c.nrm.p, c.ldiag.p,
+                                                                c.mdiag.p);
+        BEM_LAUNCH_CHECK();
+        DevBuf<int> bad;
+        bad.resize(1);
+        BEM_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), c.stream));
+        k_check_finite<<<div_up(N, 256), 256, 0, c.stream>>>(N, c.ldiag.p, bad.p);
+        k_check_finite<<<div_up(N, 256), 256, 0, c.stream>>>(N, c.mdiag.p, bad.p);
+        BEM_LAUNCH_CHECK();
+        BEM_CUDA(cudaEventRecord(e1, c.stream));
+        int hb = 0;
+        BEM_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+        BEM_CUDA(cudaStreamSynchronize(c.stream));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        c.stats.last_build_ms = ms;
+        if (hb) fail(BEM_ERR_NAN, "non-finite singular diagonal");
+        c.built = true;
+    });
+}
+
+int bem_apply(void *ctx, double f, const double *xL, double g, const double *xM, double *out) {
+    return guarded(ctx, [&](Context &c) {
+        require_built(c);
+        if ((f != 0.0 && !xL) || (g != 0.0 && !xM)) fail(BEM_ERR_ARG, "null input with a non-zero coefficient");
+        const double *dl = f != 0.0 ? dev_in(c, xL, c.N, 0) : nullptr;
+        const double *dm = g != 0.0 ? dev_in(c, xM, c.N, 1) : nullptr;
+        OutView ov(c, out, c.N);
+        apply_full(c, f, dl, g, dm, ov.dev);
+        ov.finish();
+    });
+}
+
+int bem_apply_sl(void *ctx, const double *q, double *out) { return bem_apply(ctx, 1.0, q, 0.0, nullptr, out); }
+
+int bem_apply_dl(void *ctx, const double *phi, double *out) { return bem_apply(ctx, 0.0, nullptr, 1.0, phi, out); }
+
+int bem_rhs(void *ctx, const double *phi, double *b) {
+    return guarded(ctx, [&](Context &c) {
+        require_built(c);
+        if (!phi) fail(BEM_ERR_ARG, "null phi");
+        const double *dp = dev_in(c, phi, c.N, 0);
+        OutView ov(c, b, c.N);
+        apply_full(c, 0.0, nullptr, 1.0, dp, ov.dev);
+        k_rhs_combine<<<div_up(c.N, 256), 256, 0, c.stream>>>(c.N, dp, ov.dev);
+        BEM_LAUNCH_CHECK();
+        ov.finish();
+    });
+}
+
+int bem_solve(void *ctx, const double *phi, double *q_inout, int32_t *iters, double *relres) {
+    int it = 0;
+    double rr = 0.0;
+    int rc = guarded(ctx, [&](Context &c) {
+        require_built(c);
+        if (!phi || !q_inout) fail(BEM_ERR_ARG, "null phi or q");
+        const double *dp = dev_in(c, phi, c.N, 0);
+        const bool host_q = !is_device_ptr(c, q_inout);
+        double *dq = q_inout;
+        if (host_q) {
+            c.stage_in[1].resize(c.N);
+            dq = c.stage_in[1].p;
+            BEM_CUDA(cudaMemcpyAsync(dq, q_inout, c.N * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+        }
+        c.bv.resize(c.N);
+        apply_full(c, 0.0, nullptr, 1.0, dp, c.bv.p);
+        k_rhs_combine<<<div_up(c.N, 256), 256, 0, c.stream>>>(c.N, dp, c.bv.p);
+        BEM_LAUNCH_CHECK();
+        struct CopyBack {
+            Context &c;
+            bool host;
+            double *user, *dev;
+            ~CopyBack() {
+                if (host) {
+                    cudaMemcpyAsync(user, dev, c.N * sizeof(double), cudaMemcpyDeviceToHost, c.stream);
+                    cudaStreamSynchronize(c.stream);
+                }
+            }
+        } cb{c, host_q, q_inout, dq};
+        gmres_solve(c, c.bv.p, dq, &it, &rr);
+    });
+    if (iters) *iters = it;
+    if (relres) *relres = rr;
+    if (rc == BEM_ERR_NOCONV && ctx) {
+        Context *c = static_cast<Context *>(ctx);
+        if (iters) *iters = c->stats.last_iters;
+        if (relres) *relres = c->stats.last_relres;
+    }
+    return rc;
+}
+
+int bem_get_geometry(void *ctx, double *s, double *n, double *ldiag, double *mdiag) {
+    return guarded(ctx, [&](Context &c) {
+        require_built(c);
+        struct Item {
+            double *dst;
+            const double *src;
+            int64_t n;
+        } items[4] = {{s, c.s.p, c.N}, {n, c.nrm.p, 3 * c.N}, {ldiag, c.ldiag.p, c.N}, {mdiag, c.mdiag.p, c.N}};
+        for (auto &it : items) {
+            if (!it.dst) continue;
+            auto k = is_device_ptr(c, it.dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+            BEM_CUDA(cudaMemcpyAsync(it.dst, it.src, it.n * sizeof(double), k, c.stream));
+        }
+        BEM_CUDA(cudaStreamSynchronize(c.stream));
+    });
+}
+
+int bem_get_stats(void *ctx, bem_stats *out) {
+    return guarded(ctx, [&](Context &c) {
+        if (!out) fail(BEM_ERR_ARG, "null stats");
+        c.stats.n_launches = g_launch_count;
+        *out = c.stats;
+    });
+}
+
+int bem_profile_enable(void *ctx, int on) {
+    return guarded(ctx, [&](Context &c) {
+        BEM_CUDA(cudaStreamSynchronize(c.stream));
+        for (auto &r : c.prof.recs) {
+            c.prof.pool.push_back(r.a);
+            c.prof.pool.push_back(r.b);
+        }
+        c.prof.recs.clear();
+        c.prof.on = on != 0;
+    });
+}
+
+int bem_profile_read(void *ctx, double *ms, int64_t *intervals) {
+    return guarded(ctx, [&](Context &c) {
+        BEM_CUDA(cudaStreamSynchronize(c.stream));
+        double acc[PH_COUNT] = {0};
+        int64_t cnt[PH_COUNT] = {0};
+        for (auto &r : c.prof.recs) {
+            float t = 0.f;
+            BEM_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+            acc[r.phase] += t;
+            cnt[r.phase] += 1;
+            c.prof.pool.push_back(r.a);
+            c.prof.pool.push_back(r.b);
+        }
+        c.prof.recs.clear();
+        for (int i = 0; i < PH_COUNT; ++i) {
+            if (ms) ms[i] = acc[i];
+            if (intervals) intervals[i] = cnt[i];
+        }
+    });
+}
+
+const char *bem_phase_name(int i) {
+    static const char *names[PH_COUNT] = {"geometry", "tree", "operators", "strengths", "p2m", "m2m", "m2l",
+                                          "l2l", "l2p", "p2p", "direct", "diag", "gmres"};
+    return (i >= 0 && i < PH_COUNT) ? names[i] : nullptr;
+}
+
+int bem_reset_stats(void *ctx) {
+    return guarded(ctx, [&](Context &c) {
+        c.stats.n_apply = 0;
+        c.stats.n_apply_rhs = 0;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,710 @@
+// Far field of the fast multipole method (Section 3.7): multipole and local expansions in
+// solid harmonics of degree n = 0..p-1 (p^2 real coefficients), P2M for monopoles and
+// dipoles, M2M, M2L, L2L and L2P, and the orchestration of one multi-RHS product of
+// Eq. (3.27) with the near field of p2p.cu.
+//
+// Conventions (derived here, checked against direct sums in the tests):
+//   R_n^m(r) = r^n P_n^m(cos t) e^{i m f} / (n+m)!,  I_n^m(r) = (n-m)! P_n^m(cos t) e^{i m f} / r^{n+1},
+//   P_n^m with the Condon-Shortley phase, R_n^{-m} = (-1)^m conj(R_n^m), same for I. Then
+//   1/|x - y| = sum_{n,m} conj(R_n^m(y)) I_n^m(x) (|y| < |x|),
+//   R_n^m(a + b) = sum_{k,l} R_k^l(a) R_{n-k}^{m-l}(b),
+//   d.grad R_n^m = d_z R_{n-1}^m - (d_x + i d_y)/2 R_{n-1}^{m-1} + (d_x - i d_y)/2 R_{n-1}^{m+1}.
+// Expansions are normalised by the box size h of their level, so the translation matrices
+// do not depend on the level: a box's field is (1/h) sum M_n^m I_n^m((x-c)/h) and its local
+// expansion (1/h) sum L_n^m R_n^m((x-c)/h). Coefficients with m >= 0 are stored as reals:
+// index n^2 for m = 0, n^2 + 2m - 1 (real part) and n^2 + 2m (imaginary part) for m > 0.
+#include "internal.h"
+
+#include <cmath>
+
+namespace bem {
+namespace {
+
+constexpr double kInv4Pi = 0.0795774715459476678844418816862571810;  // 1/(4 pi)
+
+struct cplx {
+    double re, im;
+};
+__device__ __forceinline__ int tri_idx(int n, int m) { return n * (n + 1) / 2 + m; }
+
+// Harmonic of order m (any sign) from a table of m >= 0 values.
+__device__ __forceinline__ cplx harm_get(const double *re, const double *im, int nmax, int n, int m) {
+    if (n < 0 || n >= nmax) return {0.0, 0.0};
+    int am = m < 0 ? -m : m;
+    if (am > n) return {0.0, 0.0};
+    double a = re[tri_idx(n, am)], b = im[tri_idx(n, am)];
+    if (m >= 0) return {a, b};
+    double sg = (am & 1) ? -1.0 : 1.0;
+    return {sg * a, -sg * b};
+}
+
+__device__ void regular_table(double x, double y, double z, int nmax, double *re, double *im) {
+    double r2 = x * x + y * y + z * z;
+    double mr = 1.0, mi = 0.0;  // R_m^m
+    for (int m = 0; m < nmax; ++m) {
+        if (m > 0) {
+            // R_m^m = -(x + i y)/(2m) R_{m-1}^{m-1}
+            double f = -0.5 / m;
+            double nr = f * (x * mr - y * mi), ni = f * (x * mi + y * mr);
+            mr = nr;
+            mi = ni;
+        }
+        re[tri_idx(m, m)] = mr;
+        im[tri_idx(m, m)] = mi;
+        if (m + 1 < nmax) {
+            re[tri_idx(m + 1, m)] = z * mr;
+            im[tri_idx(m + 1, m)] = z * mi;
+        }
+        for (int n = m + 2; n < nmax; ++n) {
+            double d = 1.0 / ((double)(n + m) * (double)(n - m));
+            re[tri_idx(n, m)] = ((2 * n - 1) * z * re[tri_idx(n - 1, m)] - r2 * re[tri_idx(n - 2, m)]) * d;
+            im[tri_idx(n, m)] = ((2 * n - 1) * z * im[tri_idx(n - 1, m)] - r2 * im[tri_idx(n - 2, m)]) * d;
+        }
+    }
+}
+
+__device__ void irregular_table(double x, double y, double z, int nmax, double *re, double *im) {
+    double r2 = x * x + y * y + z * z;
+    double ir2 = 1.0 / r2;
+    double mr = 1.0 / sqrt(r2), mi = 0.0;  // I_m^m
+    for (int m = 0; m < nmax; ++m) {
+        if (m > 0) {
+            // I_m^m = -(2m-1)(x + i y)/r^2 I_{m-1}^{m-1}
+            double f = -(2.0 * m - 1.0) * ir2;
+            double nr = f * (x * mr - y * mi), ni = f * (x * mi + y * mr);
+            mr = nr;
+            mi = ni;
+        }
+        re[tri_idx(m, m)] = mr;
+        im[tri_idx(m, m)] = mi;
+        if (m + 1 < nmax) {
+            re[tri_idx(m + 1, m)] = (2 * m + 1) * z * ir2 * mr;
+            im[tri_idx(m + 1, m)] = (2 * m + 1) * z * ir2 * mi;
+        }
+        for (int n = m + 2; n < nmax; ++n) {
+            double a = (2.0 * n - 1.0) * z * ir2, b = (double)(n + m - 1) * (double)(n - m - 1) * ir2;
+            re[tri_idx(n, m)] = a * re[tri_idx(n - 1, m)] - b * re[tri_idx(n - 2, m)];
+            im[tri_idx(n, m)] = a * im[tri_idx(n - 1, m)] - b * im[tri_idx(n - 2, m)];
+        }
+    }
+}
+
+__device__ __forceinline__ void decode(int ri, int &n, int &m, int &part) {
+    n = (int)sqrtf((float)ri);
+    while (n * n > ri) --n;
+    while ((n + 1) * (n + 1) <= ri) ++n;
+    int r = ri - n * n;
+    if (r == 0) {
+        m = 0;
+        part = 0;
+    } else if (r & 1) {
+        m = (r + 1) / 2;
+        part = 0;
+    } else {
+        m = r / 2;
+        part = 1;
+    }
+}
+
+constexpr int kOpM2L = 0, kOpM2M = 1, kOpL2L = 2;
+
+__device__ cplx op_kernel(int kind, const double *hre, const double *him, int nmax, int n, int m, int k, int l) {
+    if (kind == kOpM2L) {
+        cplx v = harm_get(hre, him, nmax, n + k, l - m);
+        double sg = ((n + m) & 1) ? -1.0 : 1.0;
+        return {sg * v.re, sg * v.im};
+    } else if (kind == kOpM2M) {
+        if (k > n) return {0.0, 0.0};
+        cplx v = harm_get(hre, him, nmax, n - k, m - l);
+        double s = ldexp(1.0, -k);
+        return {s * v.re, -s * v.im};
+    } else {
+        if (k < n) return {0.0, 0.0};
+        cplx v = harm_get(hre, him, nmax, k - n, l - m);
+        double s = ldexp(1.0, -n - 1);
+        return {s * v.re, s * v.im};
+    }
+}
+
+// One block per matrix. M2L: offset class -> D = target centre - source centre in units of
+// the box (the class enumerates source - target offsets lexicographically). M2M/L2L: child
+// octant o -> t = child centre - parent centre in units of the parent box.
+__global__ void k_build_ops(int kind, int p, double *__restrict__ out64, float *__restrict__ out32) {
+    extern __shared__ double sh[];
+    const int P = p * p;
+    const int nmax = (kind == kOpM2L) ? 2 * p : p;
+    const int ntri = nmax * (nmax + 1) / 2;
+    double *hre = sh, *him = sh + ntri;
+    if (threadIdx.x == 0) {
+        double v[3];
+        if (kind == kOpM2L) {
+            int c = 0, want = blockIdx.x;
+            for (int x = -3; x <= 3; ++x)
+                for (int y = -3; y <= 3; ++y)
+                    for (int z = -3; z <= 3; ++z) {
+                        bool near = (x >= -1 && x <= 1 && y >= -1 && y <= 1 && z >= -1 && z <= 1);
+                        if (near) continue;
+                        if (c == want) {
+                            v[0] = -x;
+                            v[1] = -y;
+                            v[2] = -z;
+                        }
+                        ++c;
+                    }
+            irregular_table(v[0], v[1], v[2], nmax, hre, him);
+        } else {
+            int o = blockIdx.x;
+            v[0] = (((o >> 2) & 1) - 0.5) * 0.5;
+            v[1] = (((o >> 1) & 1) - 0.5) * 0.5;
+            v[2] = ((o & 1) - 0.5) * 0.5;
+            regular_table(v[0], v[1], v[2], nmax, hre, him);
+        }
+    }
+    __syncthreads();
+    size_t mbase = (size_t)blockIdx.x * P * P;
+    for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
+        int ro = e / P, ri = e % P;
+        int n, m, po, k, l, pi;
+        decode(ro, n, m, po);
+        decode(ri, k, l, pi);
+        double val;
+        if (l == 0) {
+            cplx c = op_kernel(kind, hre, him, nmax, n, m, k, 0);
+            val = (pi != 0) ? 0.0 : (po == 0 ? c.re : c.im);
+        } else {
+            cplx kp = op_kernel(kind, hre, him, nmax, n, m, k, l);
+            cplx km = op_kernel(kind, hre, him, nmax, n, m, k, -l);
+            double sg = (l & 1) ? -1.0 : 1.0;
+            cplx A = {kp.re + sg * km.re, kp.im + sg * km.im};
+            cplx B = {kp.re - sg * km.re, kp.im - sg * km.im};
+            if (po == 0) val = (pi == 0) ? A.re : -B.im;
+            else val = (pi == 0) ? A.im : B.re;
+        }
+        out64[mbase + e] = val;
+        out32[mbase + e] = (float)val;
+    }
+}
+
+// ------------------------------------------------------------------------------ strengths
+template <int R>
+struct RhsArgs {
+    double f[R], g[R];
+    const double *xL[R];
+    const double *xM[R];
+    double *out[R];
+};
+
+// Monopole q = f s X_L / (4 pi) and dipole moment w n with w = g s X_M / (4 pi) / h_leaf
+// (leaf-box units), gathered into Morton order.
+template <class T, int R>
+__global__ void k_strengths(int64_t N, const int32_t *__restrict__ perm, const double *__restrict__ s,
+                            RhsArgs<R> a, double inv_h, T *__restrict__ q, T *__restrict__ w) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    int j = perm[k];
+    double sk = s[k] * kInv4Pi;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        double qq = a.f[r] != 0.0 ? a.f[r] * sk * a.xL[r][j] : 0.0;
+        double ww = a.g[r] != 0.0 ? a.g[r] * sk * a.xM[r][j] * inv_h : 0.0;
+        q[r * N + k] = (T)qq;
+        w[r * N + k] = (T)ww;
+    }
+}
+
+// ------------------------------------------------------------------------------ P2M
+constexpr int P2M_THREADS = 128;
+constexpr int P2M_PC = 8;  // points per chunk
+
+template <class T, int R>
+__global__ void __launch_bounds__(P2M_THREADS) k_p2m(int p, int nleaf, const int32_t *__restrict__ bstart,
+                                                     const int32_t *__restrict__ bcount, int64_t N,
+                                                     const T *__restrict__ loc, const T *__restrict__ nrm,
+                                                     const T *__restrict__ q, const T *__restrict__ w,
+                                                     T *__restrict__ mp) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int P = p * p;
+    const int ntri = p * (p + 1) / 2;
+    T *Rre = reinterpret_cast<T *>(smraw);
+    T *Rim = Rre + P2M_PC * ntri;
+    T *pn = Rim + P2M_PC * ntri;      // [PC][3]
+    T *pq = pn + P2M_PC * 3;          // [PC][R]
+    T *pw = pq + P2M_PC * R;          // [PC][R]
+    int b = blockIdx.x;
+    int s0 = bstart[b], cnt = bcount[b];
+    constexpr int MAXO = 4;  // outputs per thread: P <= 4 * 128
+    T acc[MAXO][R];
+#pragma unroll
+    for (int o = 0; o < MAXO; ++o)
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[o][r] = (T)0;
+    for (int c0 = 0; c0 < cnt; c0 += P2M_PC) {
+        int pc = min(P2M_PC, cnt - c0);
+        __syncthreads();
+        if (threadIdx.x < pc * 3) {
+            int jj = threadIdx.x / 3, d = threadIdx.x % 3;
+            pn[jj * 3 + d] = nrm[d * N + s0 + c0 + jj];
+        } else if (threadIdx.x >= 32 && threadIdx.x < 32 + pc * R) {
+            int t = threadIdx.x - 32, jj = t / R, r = t % R;
+            pq[jj * R + r] = q[r * N + s0 + c0 + jj];
+            pw[jj * R + r] = w[r * N + s0 + c0 + jj];
+        }
+        for (int task = threadIdx.x; task < pc * p; task += P2M_THREADS) {
+            int jj = task / p, m = task % p;
+            int64_t i = s0 + c0 + jj;
+            T x = loc[i], y = loc[N + i], z = loc[2 * N + i];
+            T r2 = x * x + y * y + z * z;
+            T mr = 1, mi = 0;
+            for (int k = 1; k <= m; ++k) {
+                T f = (T)(-0.5) / (T)k;
+                T nr = f * (x * mr - y * mi), ni = f * (x * mi + y * mr);
+                mr = nr;
+                mi = ni;
+            }
+            T *re = Rre + jj * ntri, *im = Rim + jj * ntri;
+            re[tri_idx(m, m)] = mr;
+            im[tri_idx(m, m)] = mi;
+            T p2r = mr, p2i = mi, p1r = z * mr, p1i = z * mi;
+            if (m + 1 < p) {
+                re[tri_idx(m + 1, m)] = p1r;
+                im[tri_idx(m + 1, m)] = p1i;
+            }
+            for (int n = m + 2; n < p; ++n) {
+                T d = (T)1 / ((T)(n + m) * (T)(n - m));
+                T cr = ((T)(2 * n - 1) * z * p1r - r2 * p2r) * d;
+                T ci = ((T)(2 * n - 1) * z * p1i - r2 * p2i) * d;
+                re[tri_idx(n, m)] = cr;
+                im[tri_idx(n, m)] = ci;
+                p2r = p1r;
+                p2i = p1i;
+                p1r = cr;
+                p1i = ci;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int o = 0; o < MAXO; ++o) {
+            int ro = threadIdx.x + o * P2M_THREADS;
+            if (ro >= P) break;
+            int n, m, part;
+            decode(ro, n, m, part);
+            for (int jj = 0; jj < pc; ++jj) {
+                const T *re = Rre + jj * ntri, *im = Rim + jj * ntri;
+                T cr = re[tri_idx(n, m)], ci = -im[tri_idx(n, m)];  // conj(R_n^m)
+                // conj(n . grad R_n^m) for the unit normal of the point
+                T dr = 0, di = 0;
+                if (n >= 1) {
+                    T nx = pn[jj * 3], ny = pn[jj * 3 + 1], nz = pn[jj * 3 + 2];
+                    T ar = 0, ai = 0;  // R_{n-1}^m
+                    if (m <= n - 1) {
+                        ar = re[tri_idx(n - 1, m)];
+                        ai = im[tri_idx(n - 1, m)];
+                    }
+                    T br, bi;  // R_{n-1}^{m-1}
+                    if (m >= 1) {
+                        br = re[tri_idx(n - 1, m - 1)];
+                        bi = im[tri_idx(n - 1, m - 1)];
+                    } else if (n - 1 >= 1) {  // R^{-1} = -conj(R^1)
+                        br = -re[tri_idx(n - 1, 1)];
+                        bi = im[tri_idx(n - 1, 1)];
+                    } else {
+                        br = 0;
+                        bi = 0;
+                    }
+                    T er = 0, ei = 0;  // R_{n-1}^{m+1}
+                    if (m + 1 <= n - 1) {
+                        er = re[tri_idx(n - 1, m + 1)];
+                        ei = im[tri_idx(n - 1, m + 1)];
+                    }
+                    // nz*A - (nx + i ny)/2 * B + (nx - i ny)/2 * E
+                    T gr = nz * ar - (T)0.5 * (nx * br - ny * bi) + (T)0.5 * (nx * er + ny * ei);
+                    T gi = nz * ai - (T)0.5 * (nx * bi + ny * br) + (T)0.5 * (nx * ei - ny * er);
+                    dr = gr;
+                    di = -gi;
+                }
+                T vm = part ? ci : cr;
+                T vd = part ? di : dr;
+#pragma unroll
+                for (int r = 0; r < R; ++r) acc[o][r] += pq[jj * R + r] * vm + pw[jj * R + r] * vd;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < MAXO; ++o) {
+        int ro = threadIdx.x + o * P2M_THREADS;
+        if (ro >= P) break;
+#pragma unroll
+        for (int r = 0; r < R; ++r) mp[((size_t)b * R + r) * P + ro] = acc[o][r];
+    }
+}
+
+// ------------------------------------------------------------------------------ translations
+// Class-grouped product: for every pair (src, tgt) of a chunk, Y[tgt] += T_cls X[src], as a
+// tiled GEMM (64 output rows x 64 columns per block; a column is one pair and one RHS).
+constexpr int XT_ROWS = 64, XT_COLS = 64, XT_K = 16, XT_THREADS = 256;
+
+template <class T, int R>
+__global__ void __launch_bounds__(XT_THREADS) k_xlat(const T *__restrict__ mats, int P, const XChunk *__restrict__ chunks,
+                                                     const int32_t *__restrict__ srcs, const int32_t *__restrict__ tgts,
+                                                     const T *X, T *Y) {  // X and Y may be one array (M2M, L2L)
+    __shared__ T As[XT_K][XT_ROWS + 4];
+    __shared__ T Bs[XT_K][XT_COLS + 4];
+    __shared__ int s_src[XT_COLS], s_tgt[XT_COLS];
+    const XChunk ch = chunks[blockIdx.x];
+    const int row0 = blockIdx.y * XT_ROWS;
+    const T *A = mats + (size_t)ch.cls * P * P;
+    const int ncol = ch.count * R;
+    int tid = threadIdx.x;
+    if (tid < XT_COLS) {
+        int pr = tid / R;
+        if (pr < ch.count) {
+            s_src[tid] = srcs[ch.start + pr];
+            s_tgt[tid] = tgts[ch.start + pr];
+        } else {
+            s_src[tid] = -1;
+            s_tgt[tid] = -1;
+        }
+    }
+    __syncthreads();
+    const int tx = tid % 16, ty = tid / 16;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
+    for (int k0 = 0; k0 < P; k0 += XT_K) {
+#pragma unroll
+        for (int it = 0; it < (XT_ROWS * XT_K) / XT_THREADS; ++it) {
+            int e = tid + it * XT_THREADS;
+            int row = e / XT_K, kk = e % XT_K;
+            int gr = row0 + row, gk = k0 + kk;
+            As[kk][row] = (gr < P && gk < P) ? A[(size_t)gr * P + gk] : (T)0;
+        }
+#pragma unroll
+        for (int it = 0; it < (XT_COLS * XT_K) / XT_THREADS; ++it) {
+            int e = tid + it * XT_THREADS;
+            int col = e / XT_K, kk = e % XT_K;
+            int gk = k0 + kk;
+            T v = (T)0;
+            if (col < ncol && gk < P) {
+                int r = col % R;
+                v = X[((size_t)s_src[col] * R + r) * P + gk];
+            }
+            Bs[kk][col] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < XT_K; ++kk) {
+            T a[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bv[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        int col = tx * 4 + j;
+        if (col >= ncol) continue;
+        int r = col % R;
+        T *yb = Y + ((size_t)s_tgt[col] * R + r) * P;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int gr = row0 + ty * 4 + i;
+            if (gr < P) atomicAdd(yb + gr, acc[i][j]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------ L2P
+constexpr int L2P_THREADS = 128;
+
+// TwoSum-compensated accumulation in T; for double the compensation is harmless.
+template <class T>
+struct CompSum {
+    T s = 0, c = 0;
+    __device__ __forceinline__ void add(T v) {
+        T t = s + v;
+        T bp = t - s;
+        c += (s - (t - bp)) + (v - bp);
+        s = t;
+    }
+    __device__ __forceinline__ T get() const { return s + c; }
+};
+
+template <class T, int R>
+__global__ void __launch_bounds__(L2P_THREADS) k_l2p(int p, const int32_t *__restrict__ bstart, const int32_t *__restrict__ bcount,
+                                                     int64_t N, const T *__restrict__ loc, const T *__restrict__ lc,
+                                                     T *__restrict__ far) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *Ls = reinterpret_cast<T *>(smraw);
+    const int P = p * p;
+    int b = blockIdx.x;
+    for (int e = threadIdx.x; e < R * P; e += L2P_THREADS) Ls[e] = lc[(size_t)b * R * P + e];
+    __syncthreads();
+    int s0 = bstart[b], cnt = bcount[b];
+    for (int c0 = threadIdx.x; c0 < cnt; c0 += L2P_THREADS) {
+        int64_t i = s0 + c0;
+        T x = loc[i], y = loc[N + i], z = loc[2 * N + i];
+        T r2 = x * x + y * y + z * z;
+        CompSum<T> acc[R];
+        T mr = 1, mi = 0;
+        for (int m = 0; m < p; ++m) {
+            if (m > 0) {
+                T f = (T)(-0.5) / (T)m;
+                T nr = f * (x * mr - y * mi), ni = f * (x * mi + y * mr);
+                mr = nr;
+                mi = ni;
+            }
+            T p2r = 0, p2i = 0, p1r = mr, p1i = mi;
+            for (int n = m; n < p; ++n) {
+                T cr, ci;
+                if (n == m) {
+                    cr = mr;
+                    ci = mi;
+                } else if (n == m + 1) {
+                    cr = z * mr;
+                    ci = z * mi;
+                    p2r = mr;
+                    p2i = mi;
+                    p1r = cr;
+                    p1i = ci;
+                } else {
+                    T d = (T)1 / ((T)(n + m) * (T)(n - m));
+                    cr = ((T)(2 * n - 1) * z * p1r - r2 * p2r) * d;
+                    ci = ((T)(2 * n - 1) * z * p1i - r2 * p2i) * d;
+                    p2r = p1r;
+                    p2i = p1i;
+                    p1r = cr;
+                    p1i = ci;
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const T *Lr = Ls + r * P;
+                    T v;
+                    if (m == 0) v = Lr[n * n] * cr;
+                    else v = (T)2 * (Lr[n * n + 2 * m - 1] * cr - Lr[n * n + 2 * m] * ci);
+                    acc[r].add(v);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) far[r * N + i] = acc[r].get();
+    }
+}
+
+template <class T>
+__global__ void k_zero(size_t n, T *a) {
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i < n) a[i] = (T)0;
+}
+
+__global__ void k_scatter_out(int64_t N, int R, const int32_t *__restrict__ perm, const double *__restrict__ src,
+                              RhsArgs<kMaxRhs> a) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    int j = perm[k];
+    for (int r = 0; r < R; ++r) a.out[r][j] = src[r * N + k];
+}
+
+// Chunks of at most `per` pairs within each class.
+void make_chunks(const std::vector<int64_t> &class_off, int64_t base, int per, std::vector<XChunk> &out) {
+    for (size_t c = 0; c + 1 < class_off.size(); ++c)
+        for (int64_t s = class_off[c]; s < class_off[c + 1]; s += per) {
+            XChunk ch;
+            ch.cls = (int32_t)c;
+            ch.start = base + s;
+            ch.count = (int32_t)std::min<int64_t>(per, class_off[c + 1] - s);
+            out.push_back(ch);
+        }
+}
+
+template <class T, int R>
+void run_fmm(Context &c, const RhsArgs<R> &a) {
+    Tree &t = c.tree;
+    cudaStream_t st = c.stream;
+    const int64_t N = c.N;
+    const int L = t.L, p = c.ops.p, P = c.ops.P;
+    const double inv_h = (double)(1 << L) / t.size;
+    const int tb = 256;
+    constexpr bool F64 = sizeof(T) == 8;
+    T *q, *w, *mp, *lc, *far;
+    const T *loc, *nrm;
+    const T *m2l, *m2m, *l2l;
+    size_t exp_sz = (size_t)t.nbox * R * P;
+    if (F64) {
+        c.q64.resize((size_t)R * N);
+        c.w64.resize((size_t)R * N);
+        c.mp64.resize(exp_sz);
+        c.lc64.resize(exp_sz);
+        c.far64.resize((size_t)R * N);
+        q = (T *)c.q64.p; w = (T *)c.w64.p; mp = (T *)c.mp64.p; lc = (T *)c.lc64.p; far = (T *)c.far64.p;
+        loc = (const T *)t.loc64.p; nrm = (const T *)t.nrm64.p;
+        m2l = (const T *)c.ops.m2l64.p; m2m = (const T *)c.ops.m2m64.p; l2l = (const T *)c.ops.l2l64.p;
+    } else {
+        c.q32.resize((size_t)R * N);
+        c.w32.resize((size_t)R * N);
+        c.mp32.resize(exp_sz);
+        c.lc32.resize(exp_sz);
+        c.far32.resize((size_t)R * N);
+        q = (T *)c.q32.p; w = (T *)c.w32.p; mp = (T *)c.mp32.p; lc = (T *)c.lc32.p; far = (T *)c.far32.p;
+        loc = (const T *)t.loc32.p; nrm = (const T *)t.nrm32.p;
+        m2l = (const T *)c.ops.m2l32.p; m2m = (const T *)c.ops.m2m32.p; l2l = (const T *)c.ops.l2l32.p;
+    }
+    {
+        PhaseScope ps(c, PH_STRENGTHS);
+        k_strengths<T, R><<<div_up(N, tb), tb, 0, st>>>(N, t.perm.p, t.s_sorted.p, a, inv_h, q, w);
+        BEM_LAUNCH_CHECK();
+    }
+
+    // chunk tables for this R (built once per build)
+    const int per = XT_COLS / R;
+    auto &mch = c.m2l_chunks_h;
+    if (mch.empty() || mch.front().cls != -R) {
+        std::vector<XChunk> all;
+        XChunk tag{-R, 0, 0};
+        all.push_back(tag);  // header: which R the table is for
+        make_chunks(t.m2l_class_off, 0, per, all);
+        for (int l = 3; l <= L; ++l) make_chunks(t.up_class_off[l], t.up_off[l], per, all);
+        mch = all;
+        c.m2l_chunks.resize(all.size());
+        BEM_CUDA(cudaMemcpyAsync(c.m2l_chunks.p, all.data(), all.size() * sizeof(XChunk), cudaMemcpyHostToDevice, st));
+    }
+    // locate the per-phase ranges in the chunk table
+    int64_t nm2l_chunks = 0;
+    for (size_t cc = 0; cc + 1 < t.m2l_class_off.size(); ++cc)
+        nm2l_chunks += (t.m2l_class_off[cc + 1] - t.m2l_class_off[cc] + per - 1) / per;
+    std::vector<int64_t> up_first(L + 2, 0), up_n(L + 2, 0);
+    int64_t cur = 1 + nm2l_chunks;
+    for (int l = 3; l <= L; ++l) {
+        int64_t k = 0;
+        for (int cc = 0; cc < 8; ++cc) k += (t.up_class_off[l][cc + 1] - t.up_class_off[l][cc] + per - 1) / per;
+        up_first[l] = cur;
+        up_n[l] = k;
+        cur += k;
+    }
+    const int rowblocks = div_up(P, XT_ROWS);
+
+    // P2M at the leaves
+    const int nleaf = t.nb[L];
+    {
+        PhaseScope ps(c, PH_P2M);
+        size_t sm = ((size_t)2 * P2M_PC * (p * (p + 1) / 2) + P2M_PC * 3 + 2 * P2M_PC * R) * sizeof(T);
+        k_p2m<T, R><<<nleaf, P2M_THREADS, sm, st>>>(p, nleaf, t.bstart.p + t.base[L], t.bcount.p + t.base[L], N, loc, nrm,
+                                                   q, w, mp + (size_t)t.base[L] * R * P);
+        BEM_LAUNCH_CHECK();
+    }
+    // zero the multipoles above the leaves and all locals
+    {
+        size_t nup = (size_t)t.base[L] * R * P;
+        if (nup) k_zero<T><<<div_up(nup, tb), tb, 0, st>>>(nup, mp);
+        k_zero<T><<<div_up(exp_sz, tb), tb, 0, st>>>(exp_sz, lc);
+        BEM_LAUNCH_CHECK();
+    }
+    // M2M upward, levels L -> 2
+    for (int l = L; l >= 3; --l) {
+        PhaseScope ps(c, PH_M2M);
+        if (!up_n[l]) continue;
+        dim3 grid((unsigned)up_n[l], rowblocks);
+        k_xlat<T, R><<<grid, XT_THREADS, 0, st>>>(m2m, P, c.m2l_chunks.p + up_first[l], t.up_child.p, t.up_parent.p, mp, mp);
+        BEM_LAUNCH_CHECK();
+    }
+    // M2L, all levels at once
+    if (nm2l_chunks) {
+        PhaseScope ps(c, PH_M2L);
+        dim3 grid((unsigned)nm2l_chunks, rowblocks);
+        k_xlat<T, R><<<grid, XT_THREADS, 0, st>>>(m2l, P, c.m2l_chunks.p + 1, t.m2l_src.p, t.m2l_tgt.p, mp, lc);
+        BEM_LAUNCH_CHECK();
+    }
+    // L2L downward, levels 3 -> L
+    for (int l = 3; l <= L; ++l) {
+        if (!up_n[l]) continue;
+        PhaseScope ps(c, PH_L2L);
+        dim3 grid((unsigned)up_n[l], rowblocks);
+        k_xlat<T, R><<<grid, XT_THREADS, 0, st>>>(l2l, P, c.m2l_chunks.p + up_first[l], t.up_parent.p, t.up_child.p, lc, lc);
+        BEM_LAUNCH_CHECK();
+    }
+    // L2P
+    {
+        PhaseScope ps(c, PH_L2P);
+        size_t sm = (size_t)R * P * sizeof(T);
+        k_l2p<T, R><<<nleaf, L2P_THREADS, sm, st>>>(p, t.bstart.p + t.base[L], t.bcount.p + t.base[L], N, loc,
+                                                    lc + (size_t)t.base[L] * R * P, far);
+        BEM_LAUNCH_CHECK();
+    }
+    // P2P (adds far, scales by 1/h), then back to the caller's order
+    c.near_out.resize((size_t)R * N);
+    {
+        PhaseScope ps(c, PH_P2P);
+        launch_p2p_list<T, R>(c, q, w, far, c.near_out.p);
+    }
+    RhsArgs<kMaxRhs> o{};
+    for (int r = 0; r < R; ++r) o.out[r] = a.out[r];
+    k_scatter_out<<<div_up(N, tb), tb, 0, st>>>(N, R, t.perm.p, c.near_out.p, o);
+    BEM_LAUNCH_CHECK();
+}
+
+}  // namespace
+
+void build_operators(Context &c) {
+    int p = c.prm.p_fmm;
+    if (c.ops_ready && c.ops_p == p) return;
+    Operators &o = c.ops;
+    o.p = p;
+    o.P = p * p;
+    size_t PP = (size_t)o.P * o.P;
+    o.m2l64.resize(kNumM2LClasses * PP);
+    o.m2l32.resize(kNumM2LClasses * PP);
+    o.m2m64.resize(8 * PP);
+    o.m2m32.resize(8 * PP);
+    o.l2l64.resize(8 * PP);
+    o.l2l32.resize(8 * PP);
+    size_t sm_m2l = (size_t)2 * (2 * p) * (2 * p + 1) / 2 * sizeof(double);
+    size_t sm_up = (size_t)2 * p * (p + 1) / 2 * sizeof(double);
+    PhaseScope ps(c, PH_OPERATORS);
+    k_build_ops<<<kNumM2LClasses, 256, sm_m2l, c.stream>>>(kOpM2L, p, o.m2l64.p, o.m2l32.p);
+    BEM_LAUNCH_CHECK();
+    k_build_ops<<<8, 256, sm_up, c.stream>>>(kOpM2M, p, o.m2m64.p, o.m2m32.p);
+    BEM_LAUNCH_CHECK();
+    k_build_ops<<<8, 256, sm_up, c.stream>>>(kOpL2L, p, o.l2l64.p, o.l2l32.p);
+    BEM_LAUNCH_CHECK();
+    c.ops_ready = true;
+    c.ops_p = p;
+}
+
+template <int R>
+static void offdiag_R(Context &c, const double *f, const double *const *xL, const double *g,
+                      const double *const *xM, double *const *out, int prec) {
+    RhsArgs<R> a{};
+    for (int r = 0; r < R; ++r) {
+        a.f[r] = f[r];
+        a.g[r] = g[r];
+        a.xL[r] = xL[r];
+        a.xM[r] = xM[r];
+        a.out[r] = out[r];
+    }
+    if (prec == BEM_PREC_FP64) run_fmm<double, R>(c, a);
+    else run_fmm<float, R>(c, a);
+}
+
+void offdiag_apply(Context &c, int R, const double *f, const double *const *xL, const double *g,
+                   const double *const *xM, double *const *out, int prec) {
+    c.stats.n_apply += 1;
+    c.stats.n_apply_rhs += R;
+    if (c.prm.mvp == BEM_MVP_DIRECT) {
+        if (R == 1) launch_direct<1>(c, prec, f, xL, g, xM, out);
+        else if (R == 4) launch_direct<4>(c, prec, f, xL, g, xM, out);
+        else fail(BEM_ERR_ARG, "unsupported RHS count");
+        return;
+    }
+    if (R == 1) offdiag_R<1>(c, f, xL, g, xM, out, prec);
+    else if (R == 4) offdiag_R<4>(c, f, xL, g, xM, out, prec);
+    else fail(BEM_ERR_ARG, "unsupported RHS count");
+}
+
+}  // namespace bem

@@ -1,0 +1,304 @@
+// Internal declarations shared by the CUDA translation units of libbem.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "bem.h"
+
+namespace bem {
+
+// ------------------------------------------------------------------------------ errors
+struct Error {
+    int code;
+    std::string msg;
+};
+
+[[noreturn]] inline void fail(int code, const std::string &msg) { throw Error{code, msg}; }
+
+#define BEM_CUDA(expr)                                                                     \
+    do {                                                                                   \
+        cudaError_t e_ = (expr);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            ::bem::fail(e_ == cudaErrorMemoryAllocation ? BEM_ERR_NOMEM : BEM_ERR_CUDA,    \
+                        std::string(#expr) + " -> " + cudaGetErrorString(e_) + " at " +    \
+                            __FILE__ + ":" + std::to_string(__LINE__));                    \
+    } while (0)
+
+// Every kernel launch of the library is followed by this check, which also counts it.
+extern long long g_launch_count;
+#define BEM_LAUNCH_CHECK()                 \
+    do {                                   \
+        ++::bem::g_launch_count;           \
+        BEM_CUDA(cudaGetLastError());      \
+    } while (0)
+
+// ------------------------------------------------------------------------------ device buffers
+// Grow-only device allocation; never shrinks, so repeated builds of the same size reuse it.
+template <class T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0, cap = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+    void resize(size_t m) {
+        if (m > cap) {
+            if (p) cudaFree(p);
+            p = nullptr;
+            cap = 0;
+            size_t bytes = (m ? m : 1) * sizeof(T);
+            BEM_CUDA(cudaMalloc(&p, bytes));
+            cap = m;
+        }
+        n = m;
+    }
+    T *get() const { return p; }
+};
+
+// Pinned host scratch for small device->host reads.
+template <class T>
+struct HostPinned {
+    T *p = nullptr;
+    size_t cap = 0;
+    HostPinned(const HostPinned &) = delete;
+    HostPinned &operator=(const HostPinned &) = delete;
+    HostPinned() = default;
+    ~HostPinned() {
+        if (p) cudaFreeHost(p);
+    }
+    T *get(size_t m) {
+        if (m > cap) {
+            if (p) cudaFreeHost(p);
+            p = nullptr;
+            BEM_CUDA(cudaMallocHost(&p, (m ? m : 1) * sizeof(T)));
+            cap = m;
+        }
+        return p;
+    }
+};
+
+inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+constexpr int kMaxRhs = 4;
+constexpr int kDeepLevel = 10;       // Morton keys are computed at this depth (30 bits)
+constexpr int kMaxPfmm = 20;
+constexpr int kNumM2LClasses = 316;  // offsets in [-3,3]^3 minus the 27 near ones
+
+// ------------------------------------------------------------------------------ octree
+struct Tree {
+    int L = 0;                 // leaf level l_max
+    double origin[3] = {0, 0, 0};
+    double size = 1.0;         // bounding cube edge
+    int64_t N = 0;
+    DevBuf<int32_t> perm;      // sorted position -> caller vertex index
+    DevBuf<uint32_t> key;      // deep Morton keys of sorted points
+    // boxes of all levels 0..L, concatenated level by level
+    std::vector<int> nb;       // boxes per level
+    std::vector<int> base;     // first global box index of each level
+    int nbox = 0;
+    DevBuf<uint32_t> bkey;     // Morton key of a box at its own level
+    DevBuf<int32_t> bstart;    // first sorted point of the box
+    DevBuf<int32_t> bcount;    // points in the box
+    DevBuf<int32_t> parent;    // global index of the parent box (-1 at level 0)
+    DevBuf<int32_t> leaf_of;   // leaf box (level-local index) of every sorted point
+    // near field: for every leaf, up to 27 neighbour leaves (self included)
+    DevBuf<int32_t> nbr;       // [nleaf][27] level-local leaf indices
+    DevBuf<int32_t> nbr_cnt;   // [nleaf]
+    DevBuf<int8_t> nbr_d;      // [nleaf][27][4] offset (dx,dy,dz) in leaf boxes
+    // M2L: pairs of all levels sorted by offset class
+    int64_t n_m2l = 0;
+    DevBuf<int32_t> m2l_src, m2l_tgt;  // global box indices
+    std::vector<int64_t> m2l_class_off;  // [kNumM2LClasses+1] host copy
+    // M2M / L2L: per level l (1..L), child->parent pairs sorted by child octant
+    std::vector<int64_t> up_off;       // per level: offset into up_child/up_parent
+    std::vector<std::vector<int64_t>> up_class_off;  // per level: [9]
+    DevBuf<int32_t> up_child, up_parent;
+    // leaf-local coordinates of sorted points in units of the leaf box (range [-1/2, 1/2))
+    DevBuf<double> loc64;      // [3][N]
+    DevBuf<float> loc32;       // [3][N]
+    DevBuf<double> nrm64;      // [3][N] sorted normals
+    DevBuf<float> nrm32;
+    DevBuf<double> s_sorted;   // [N]
+    int64_t p2p_pairs = 0;
+};
+
+// ------------------------------------------------------------------------------ FMM operators
+struct Operators {
+    int p = 0, P = 0;
+    DevBuf<double> m2l64, m2m64, l2l64;  // [316][P][P], [8][P][P], [8][P][P]
+    DevBuf<float> m2l32, m2m32, l2l32;
+};
+
+// Work chunk of the class-grouped translation product.
+struct XChunk {
+    int32_t cls;     // matrix index
+    int32_t count;   // pairs in the chunk
+    int64_t start;   // first pair
+};
+
+// ------------------------------------------------------------------------------ profiling
+// Phases timed with CUDA events on the context's stream when profiling is enabled.
+enum Phase {
+    PH_GEOMETRY = 0,
+    PH_TREE,
+    PH_OPERATORS,
+    PH_STRENGTHS,
+    PH_P2M,
+    PH_M2M,
+    PH_M2L,
+    PH_L2L,
+    PH_L2P,
+    PH_P2P,
+    PH_DIRECT,
+    PH_DIAG,
+    PH_GMRES,
+    PH_COUNT
+};
+
+struct Profiler {
+    bool on = false;
+    struct Rec {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    std::vector<cudaEvent_t> pool;
+    std::vector<Rec> recs;
+    cudaEvent_t take() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e;
+        BEM_CUDA(cudaEventCreate(&e));
+        return e;
+    }
+    ~Profiler() {
+        for (auto &r : recs) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+struct Context;
+// Records the device time of everything launched on the context stream during its lifetime.
+struct PhaseScope {
+    Context *c;
+    int phase;
+    cudaEvent_t a = nullptr;
+    PhaseScope(Context &cc, int ph);
+    ~PhaseScope();
+};
+
+// ------------------------------------------------------------------------------ context
+struct Context {
+    bem_params prm{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::string err;
+
+    int64_t N = 0, T = 0, M = 0;
+    DevBuf<double> xyz;      // [3][N]
+    DevBuf<int32_t> tri;     // [3][T]
+    std::vector<int64_t> vert_off, tri_off;
+    DevBuf<int32_t> v2t_off, v2t;  // vertex -> triangle CSR (sorted triangle ids)
+    bool mesh_ok = false;
+
+    // geometry (caller order)
+    DevBuf<double> s, nrm;         // [N], [3][N]
+    DevBuf<double> ldiag, mdiag;   // [N]
+    bool built = false;
+
+    Tree tree;
+    Operators ops;
+    bool ops_ready = false;
+    int ops_p = -1;
+
+    // FMM work arrays
+    DevBuf<double> q64, w64;       // strengths [R][N] sorted order
+    DevBuf<float> q32, w32;
+    DevBuf<double> mp64, lc64;     // expansions [nbox][R][P]
+    DevBuf<float> mp32, lc32;
+    DevBuf<double> far64;          // far-field potential [R][N] (sorted)
+    DevBuf<float> far32;
+    DevBuf<double> near_out;       // combined potential [R][N] (sorted)
+    DevBuf<XChunk> m2l_chunks;
+    std::vector<XChunk> m2l_chunks_h;
+    std::vector<DevBuf<XChunk> *> up_chunks;  // per level
+    std::vector<std::vector<XChunk>> up_chunks_h;
+    DevBuf<double> ones;
+
+    // direct-sum work arrays
+    DevBuf<float> dir_hi, dir_lo;  // [3][N] split coordinates
+    double dir_centre[3] = {0, 0, 0};
+
+    // staging for host pointers
+    DevBuf<double> stage_in[4];
+    DevBuf<double> stage_out;
+
+    // GMRES
+    DevBuf<double> V, wv, rv, bv, hcol, hmat, givens, gvec, yvec, partial, scal;
+    HostPinned<double> hscal;
+
+    bem_stats stats{};
+    Profiler prof;
+    ~Context();
+};
+
+// ------------------------------------------------------------------------------ cross-TU entry points
+// geometry.cu
+void build_vertex_triangle_csr(Context &c);
+void compute_vertex_geometry(Context &c);
+
+// tree.cu
+void build_tree(Context &c);
+void radix_sort_u32(uint32_t *keys, int32_t *vals, int64_t n, int bits, uint32_t *keys_tmp,
+                    int32_t *vals_tmp, cudaStream_t st);
+void exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *total_dev,
+                        cudaStream_t st);
+
+// fmm.cu
+void build_operators(Context &c);
+// out[r][i] (caller order) = sum over the R right-hand sides of the off-diagonal product:
+// f[r] (L_off xL[r]) + g[r] (M_off xM[r]); prec = bem_precision.
+void offdiag_apply(Context &c, int R, const double *f, const double *const *xL,
+                   const double *g, const double *const *xM, double *const *out, int prec);
+
+// p2p.cu
+template <class T, int R>
+void launch_p2p_list(Context &c, const T *q, const T *w, const T *far, double *out_sorted);
+template <int R>
+void launch_direct(Context &c, int prec, const double *f, const double *const *xL,
+                   const double *g, const double *const *xM, double *const *out);
+
+// gmres.cu
+void gmres_solve(Context &c, const double *b, double *x, int *iters, double *relres);
+
+inline PhaseScope::PhaseScope(Context &cc, int ph) : c(&cc), phase(ph) {
+    if (c->prof.on) {
+        a = c->prof.take();
+        BEM_CUDA(cudaEventRecord(a, c->stream));
+    }
+}
+inline PhaseScope::~PhaseScope() {
+    if (a) {
+        cudaEvent_t b = c->prof.take();
+        cudaEventRecord(b, c->stream);
+        c->prof.recs.push_back({phase, a, b});
+    }
+}
+
+// bem_api.cu
+void apply_full(Context &c, double f, const double *xL, double g, const double *xM, double *out);
+
+}  // namespace bem

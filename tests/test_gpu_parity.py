@@ -1,0 +1,200 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
+
+Tolerances (relative L2 over all outputs): the FP64 direct path agrees with the oracle to
+rounding (1e-11); the FP64 FMM path at p_fmm >= 14 within 1e-6 and the mixed-precision path
+(FP32 near field and expansions) within 1e-5, the bounds set for the two paths.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _bem():
+    from paper_1905_01341_gb300 import bem
+
+    return bem
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def dev(x, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(x))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def make_ctx(mesh, **params):
+    bem = _bem()
+    ctx = bem.BemContext(**params)
+    ctx.upload(dev(mesh.xyz_soa()), dev(mesh.tri_soa()), dev(mesh.vert_off), dev(mesh.tri_off))
+    ctx.build()
+    return ctx
+
+
+def small_cluster(nb=3, level=3, seed=7):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    radii = np.exp(0.3 * rng.standard_normal(nb))
+    box = max(4.0 * nb ** (1 / 3), 4.0 * radii.max())
+    centres = synth._place_centres(radii, box, 0.5, rng)
+    return synth.cluster(level, radii, centres)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1905_01341_gb300 import build
+
+    build.build()
+
+
+def test_geometry_matches_oracle():
+    bem = _bem()
+    for mesh in (synth.workload_single_sphere()[0], small_cluster(3)):
+        ctx = make_ctx(mesh, mvp=bem.BEM_MVP_DIRECT, precision=bem.BEM_PREC_FP64)
+        s = np.zeros(mesh.n)
+        n = np.zeros(3 * mesh.n)
+        ld = np.zeros(mesh.n)
+        md = np.zeros(mesh.n)
+        bem.bem_get_geometry(ctx.ctx, s, n, ld, md)
+        ref = oracle.BemOperator(mesh.xyz, mesh.tri)
+        assert np.allclose(s, ref.s, rtol=1e-13, atol=0)
+        assert np.allclose(n.reshape(3, -1).T, ref.n, rtol=0, atol=1e-13)
+        assert rel(md, ref.mdiag) < 1e-11
+        assert rel(ld, ref.ldiag) < 1e-11
+        ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-6)])
+def test_direct_apply_matches_oracle(prec, tol):
+    bem = _bem()
+    mesh = small_cluster(3)  # 1926 vertices: 15 full tiles of 128 and a ragged one
+    ctx = make_ctx(mesh, mvp=bem.BEM_MVP_DIRECT, precision=prec, diag_precision=0)
+    ref = oracle.BemOperator(mesh.xyz, mesh.tri)
+    rng = np.random.Generator(np.random.PCG64(3))
+    xL, xM = rng.standard_normal(mesh.n), rng.standard_normal(mesh.n)
+    for f, g in ((1.0, 0.0), (0.0, 1.0), (0.7, -1.3)):
+        out = torch.zeros(mesh.n, dtype=torch.float64, device="cuda")
+        ctx.apply(f, dev(xL), g, dev(xM), out)
+        exp = ref.apply(f, xL, g, xM)
+        assert rel(out.cpu().numpy(), exp) < tol, (f, g)
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec,p,tol", [(0, 17, 1e-6), (1, 14, 1e-5)])
+def test_fmm_apply_matches_oracle(prec, p, tol):
+    bem = _bem()
+    mesh = small_cluster(20, 3, seed=11)  # 12840 vertices
+    ctx = make_ctx(mesh, mvp=bem.BEM_MVP_FMM, precision=prec, p_fmm=p, leaf_target=32)
+    st = ctx.stats()
+    assert st["levels"] >= 3 and st["m2l_pairs"] > 0
+    ref = oracle.BemOperator(mesh.xyz, mesh.tri)
+    rng = np.random.Generator(np.random.PCG64(5))
+    xL, xM = rng.standard_normal(mesh.n), rng.standard_normal(mesh.n)
+    for f, g in ((1.0, 0.0), (0.0, 1.0), (0.7, -1.3)):
+        out = torch.zeros(mesh.n, dtype=torch.float64, device="cuda")
+        ctx.apply(f, dev(xL), g, dev(xM), out)
+        exp = ref.apply(f, xL, g, xM)
+        assert rel(out.cpu().numpy(), exp) < tol, (f, g, rel(out.cpu().numpy(), exp))
+    ctx.close()
+
+
+def test_config1_solve_matches_oracle_and_closed_form():
+    bem = _bem()
+    mesh, phi = synth.workload_single_sphere()
+    ref = oracle.BemOperator(mesh.xyz, mesh.tri)
+    qref, it_ref, _, _ = oracle.solve(ref, phi, tol=1e-10)
+    ctx = make_ctx(mesh, mvp=bem.BEM_MVP_DIRECT, precision=bem.BEM_PREC_FP64, gmres_tol=1e-10)
+    q = torch.zeros(mesh.n, dtype=torch.float64, device="cuda")
+    it, rr = ctx.solve(dev(phi), q)
+    qn = q.cpu().numpy()
+    assert rr <= 1e-10
+    assert abs(it - it_ref) <= 1
+    assert rel(qn, qref) < 1e-9
+    qex = -1.0 - 0.3 * (phi - 1.0) / 0.1
+    assert rel(qn, qex) < 0.01
+    st = ctx.stats()
+    assert st["last_mvps"] == it + 2
+    ctx.close()
+
+
+def test_host_pointers_match_device_pointers():
+    bem = _bem()
+    mesh, phi = synth.workload_single_sphere()
+    ctx = bem.BemContext(mvp=bem.BEM_MVP_DIRECT, precision=bem.BEM_PREC_FP64, gmres_tol=1e-10)
+    ctx.upload_mesh(mesh)  # host arrays
+    ctx.build()
+    out_h = np.zeros(mesh.n)
+    ctx.apply(0.0, None, 1.0, phi, out_h)
+    out_d = torch.zeros(mesh.n, dtype=torch.float64, device="cuda")
+    ctx.apply(0.0, None, 1.0, dev(phi), out_d)
+    assert np.array_equal(out_h, out_d.cpu().numpy())
+    qh = np.zeros(mesh.n)
+    ctx.solve(phi, qh)
+    qd = torch.zeros(mesh.n, dtype=torch.float64, device="cuda")
+    ctx.solve(dev(phi), qd)
+    assert np.array_equal(qh, qd.cpu().numpy())
+    ctx.close()
+
+
+def test_error_codes():
+    bem = _bem()
+    mesh = synth.sphere_bubble(2)
+    ctx = bem.BemContext()
+    out = np.zeros(mesh.n)
+    with pytest.raises(bem.BemError) as e:
+        ctx.apply(1.0, np.ones(mesh.n), 0.0, None, out)
+    assert e.value.code == bem.BEM_ERR_NOT_BUILT
+    bad = mesh.vert_off.copy()
+    bad[-1] += 1
+    with pytest.raises(bem.BemError) as e:
+        ctx.upload(mesh.xyz_soa(), mesh.tri_soa(), bad, mesh.tri_off)
+    assert e.value.code == bem.BEM_ERR_ARG
+    tri = mesh.tri_soa().copy()
+    tri[0, 0] = mesh.n + 5
+    with pytest.raises(bem.BemError) as e:
+        ctx.upload(mesh.xyz_soa(), tri, mesh.vert_off, mesh.tri_off)
+    assert e.value.code == bem.BEM_ERR_MESH
+    with pytest.raises(bem.BemError) as e:
+        bem.BemContext(p_fmm=40)
+    assert e.value.code == bem.BEM_ERR_ARG
+    ctx.close()
+
+
+@pytest.fixture(scope="module")
+def l6_reference():
+    mesh, phi = synth.workload_single_bubble_l6()
+    ref = oracle.BemOperator(mesh.xyz, mesh.tri)
+    rng = np.random.Generator(np.random.PCG64(8))
+    x = rng.standard_normal(mesh.n)
+    return mesh, phi, ref, x, ref.apply(1.0, x, 0.0, None), ref.apply(0.0, None, 1.0, phi)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_single_bubble_l6_p_sweep(l6_reference, prec):
+    """40962-vertex perturbed sphere: FMM error against the direct oracle falls with p;
+    FP64 reaches 1e-6 by p = 16, mixed precision 1e-5 by p = 14."""
+    bem = _bem()
+    mesh, phi, ref, x, eL, eM = l6_reference
+    errs = {}
+    for p in (8, 10, 12, 14, 16):
+        ctx = make_ctx(mesh, mvp=bem.BEM_MVP_FMM, precision=prec, p_fmm=p)
+        o1 = torch.zeros(mesh.n, dtype=torch.float64, device="cuda")
+        o2 = torch.zeros(mesh.n, dtype=torch.float64, device="cuda")
+        ctx.apply(1.0, dev(x), 0.0, None, o1)
+        ctx.apply(0.0, None, 1.0, dev(phi), o2)
+        errs[p] = max(rel(o1.cpu().numpy(), eL), rel(o2.cpu().numpy(), eM))
+        ctx.close()
+    print("p sweep prec=%d:" % prec, {k: "%.2e" % v for k, v in errs.items()})
+    assert errs[8] > errs[12] > errs[16]
+    if prec == 0:
+        assert errs[16] < 1e-6
+    assert errs[14] < 1e-5
