@@ -1,9 +1,12 @@
 """Benchmark of the FMM-BEM hot path on the 5000-bubble cluster (3.21M unknowns).
 
-One step = one pass of the hot path on one synthetic cluster: mesh upload, vertex geometry,
-octree, singular diagonals (one 4-RHS product), right-hand side, and the GMRES solve for
-q = dphi/dn to relative residual 1e-6 (started from zero). The default precision is the
-mixed path (FP32 near field and expansions, FP64 geometry/diagonal assembly/GMRES).
+One step = one time step of the bubble-dynamics method (bem_step): shape filter, vertex
+geometry, octree, singular diagonals (one 4-RHS product), right-hand side, GMRES solve for
+q = dphi/dn to relative residual 1e-6 warm-started from the previous q, tangential velocity,
+curvature, volumes and gas pressure, and the 6th-order Adams-Bashforth update. The warm-up
+steps are the 4th-order Runge-Kutta start (the first solve starts from zero). The default
+precision is the mixed path (FP32 near field and expansions; FP64 geometry, diagonal
+assembly, GMRES and time integration).
 
 Prints one JSON line (rank 0). `--impl reference` times the CPU FP64 oracle on this host's
 cores instead, on a bounded sample of the same workload.
@@ -33,7 +36,7 @@ def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--bubbles", type=int, default=5000)
     ap.add_argument("--level", type=int, default=3)
@@ -41,7 +44,11 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--leaf", type=int, default=64)
     ap.add_argument("--tol", type=float, default=1e-6)
-    ap.add_argument("--fp64-compare", type=int, default=1, help="also time one FP64 step (0 = skip)")
+    ap.add_argument("--maxit", type=int, default=400)
+    ap.add_argument("--restart", type=int, default=100)
+    ap.add_argument("--pa", type=float, default=0.5, help="acoustic amplitude Pa/p0")
+    ap.add_argument("--pf", type=int, default=6, help="shape-filter bandwidth")
+    ap.add_argument("--fp64-compare", type=int, default=1, help="also time FP64 right-hand sides (0 = skip)")
     ap.add_argument("--mvp-reps", type=int, default=5)
     ap.add_argument("--cpu-sample", type=int, default=1, help="run the CPU oracle baseline (rank 0)")
     return ap.parse_args()
@@ -215,29 +222,27 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     mesh, phi = workload(args)
     prec = bem.BEM_PREC_MIXED if args.precision == "mixed" else bem.BEM_PREC_FP64
+    N = mesh.n
 
-    xyz_h = mesh.xyz_soa()
-    tri_h = mesh.tri_soa()
-    voff_h = np.ascontiguousarray(mesh.vert_off, np.int64)
-    toff_h = np.ascontiguousarray(mesh.tri_off, np.int64)
-    phi_h = np.ascontiguousarray(phi)
-    xyz = torch.from_numpy(xyz_h).to(dev)
-    tri = torch.from_numpy(tri_h).to(dev)
-    voff = torch.from_numpy(voff_h).to(dev)
-    toff = torch.from_numpy(toff_h).to(dev)
-    phid = torch.from_numpy(phi_h).to(dev)
-    q = torch.zeros(mesh.n, dtype=torch.float64, device=dev)
+    xyz = torch.from_numpy(mesh.xyz_soa()).to(dev)
+    tri = torch.from_numpy(mesh.tri_soa()).to(dev)
+    voff = torch.from_numpy(np.ascontiguousarray(mesh.vert_off, np.int64)).to(dev)
+    toff = torch.from_numpy(np.ascontiguousarray(mesh.tri_off, np.int64)).to(dev)
+    phid = torch.from_numpy(np.ascontiguousarray(phi)).to(dev)
 
-    ctx = bem.BemContext(stream=stream, p_fmm=args.p, precision=prec, leaf_target=args.leaf, gmres_tol=args.tol)
+    def make_ctx(precision):
+        c = bem.BemContext(stream=stream, p_fmm=args.p, precision=precision, leaf_target=args.leaf,
+                           gmres_tol=args.tol, gmres_maxit=args.maxit, gmres_restart=args.restart)
+        return c
 
-    def step():
-        ctx.upload(xyz, tri, voff, toff)
-        ctx.build()
-        q.zero_()
-        return ctx.solve(phid, q)
+    ctx = make_ctx(prec)
+    ctx.upload(xyz, tri, voff, toff)
+    sp = bem.bem_step_params_default(pa=args.pa, pf=args.pf)
+    bem.bem_step_init(ctx.ctx, phid, sp)
 
+    warm = []
     for _ in range(args.warmup):
-        step()
+        warm.append(bem.bem_step(ctx.ctx))
     torch.cuda.synchronize()
     st0 = ctx.stats()
     bem.bem_profile_enable(ctx.ctx, True)
@@ -248,10 +253,9 @@ def run_ours(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    iters = []
+    infos = []
     for _ in range(args.steps):
-        it, rr = step()
-        iters.append((it, rr))
+        infos.append(bem.bem_step(ctx.ctx))
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
@@ -262,8 +266,10 @@ def run_ours(args):
     st1 = ctx.stats()
     ms = max_over_ranks(world, ms)
 
-    # one operator product (single layer), timed on its own
-    out = torch.empty(mesh.n, dtype=torch.float64, device=dev)
+    # one single-layer product on the current geometry, timed on its own
+    q = torch.zeros(N, dtype=torch.float64, device=dev)
+    bem.bem_step_get_state(ctx.ctx, None, None, q)
+    out = torch.empty(N, dtype=torch.float64, device=dev)
     for _ in range(2):
         ctx.apply(1.0, q, 0.0, None, out)
     torch.cuda.synchronize()
@@ -275,52 +281,49 @@ def run_ours(args):
     a1.record(stream)
     torch.cuda.synchronize()
     mvp_ms = a0.elapsed_time(a1) / args.mvp_reps
+    st = ctx.stats()
 
-    # e2e through the C ABI with host buffers (copies inside the timed region)
-    q_h = np.zeros(mesh.n)
-    e2e_times = []
-    for i in range(1 + max(1, args.steps)):
+    # end to end through the C ABI: each step driven from the host and its result (r, phi, q)
+    # read back into pinned host memory
+    xyz_h = torch.empty(3 * N, dtype=torch.float64).pin_memory()
+    phi_h = torch.empty(N, dtype=torch.float64).pin_memory()
+    q_h = torch.empty(N, dtype=torch.float64).pin_memory()
+    e2e_t = []
+    for _ in range(max(1, args.steps)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        bem.bem_mesh_upload(ctx.ctx, mesh.n, xyz_h, mesh.t, tri_h, mesh.m, voff_h, toff_h)
-        bem.fmm_build(ctx.ctx)
-        q_h[:] = 0.0
-        bem.bem_solve(ctx.ctx, phi_h, q_h)
-        torch.cuda.synchronize()
-        if i > 0:
-            e2e_times.append(time.perf_counter() - t0)
-    e2e_s = statistics.mean(e2e_times)
-    h2d = xyz_h.nbytes + tri_h.nbytes + voff_h.nbytes + toff_h.nbytes + phi_h.nbytes + q_h.nbytes
-    d2h = q_h.nbytes
+        bem.bem_step(ctx.ctx)
+        bem.bem_step_get_state(ctx.ctx, xyz_h, phi_h, q_h)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = statistics.mean(e2e_t)
+    d2h = (xyz_h.numel() + phi_h.numel() + q_h.numel()) * 8
 
-    st = ctx.stats()
-    nmv_step = (st1["n_apply"] - st0["n_apply"]) / args.steps
-    it_mean = statistics.mean(i for i, _ in iters)
-
-    # roofline of the dominant kernel (device time inside the timed region)
+    rhs = sum(i["rhs_calls"] for i in infos)
+    mvps = sum(i["mvps"] for i in infos)
+    iters = sum(i["gmres_iters"] for i in infos)
+    n_r4 = rhs                  # one 4-RHS diagonal product per right-hand side
+    n_r1 = mvps - rhs           # single-RHS products (right-hand side b and GMRES)
     per_step = {k: v[0] / args.steps for k, v in prof.items()}
-    work = {}
-    R1_applies = nmv_step - 1  # products with one right-hand side per step (the diagonal is 4-RHS)
-    rhs_per_step = R1_applies + 4
-    work["p2p"] = ("alu", P2P_FLOPS_PER_PAIR * st["p2p_pairs"] * rhs_per_step, FP32_ALU_PEAK_TFLOPS,
-                   prof["p2p"][1] / args.steps)
     P = args.p * args.p
-    work["m2l"] = ("alu", 2.0 * P * P * st["m2l_pairs"] * rhs_per_step, FP32_ALU_PEAK_TFLOPS,
-                   prof["m2l"][1] / args.steps)
+    work = {
+        "p2p": P2P_FLOPS_PER_PAIR * st["p2p_pairs"] * (n_r1 + 4 * n_r4) / args.steps,
+        "m2l": 2.0 * P * P * st["m2l_pairs"] * (n_r1 + 4 * n_r4) / args.steps,
+    }
+    launches = {k: prof[k][1] / args.steps for k in ("p2p", "m2l")}
     cand = [k for k in ("p2p", "m2l") if per_step.get(k, 0) > 0]
     dom = max(cand, key=lambda k: per_step[k]) if cand else None
     roof = None
     if dom:
-        bound, flops, peak, launches = work[dom]
-        launches = max(1, launches)
-        t_launch = per_step[dom] / 1e3 / launches
-        achieved = flops / launches / t_launch / 1e12
-        if args.precision == "fp64":
-            peak = None
-        roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+        nl = max(1.0, launches[dom])
+        t_launch = per_step[dom] / 1e3 / nl
+        achieved = work[dom] / nl / t_launch / 1e12
+        peak = FP32_ALU_PEAK_TFLOPS if prec == bem.BEM_PREC_MIXED else None
+        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if peak else None, "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
-                "launch_ms": t_launch * 1e3, "launches_per_step": launches}
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (max SM clock)",
+                "launch_ms": t_launch * 1e3, "launches_per_step": nl,
+                "work_per_launch": "%s" % ("20 flops x near-field pairs x RHS" if dom == "p2p"
+                                            else "2 P^2 flops x M2L translations x RHS")}
 
     line = {
         "metric": "wall-s per time step & FMM matvec Gpairs/s at 3.2M unknowns, resid 1e-6, vs FP64",
@@ -328,49 +331,66 @@ def run_ours(args):
         "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if prec == bem.BEM_PREC_MIXED else "f64", "data": "synthetic",
         "config": {"workload": workload_name(args, mesh), "p_fmm": args.p, "precision": args.precision,
-                   "leaf_target": args.leaf, "gmres_tol": args.tol, "x0": "zero",
-                   "levels": st["levels"], "leaves": st["leaves"], "l2": "inputs and working set > L2 (no flush)",
+                   "leaf_target": args.leaf, "gmres_tol": args.tol, "scheme": "AB6 after %d RK4 warm-up steps" % 5,
+                   "pa": args.pa, "pf": args.pf, "dt": infos[-1]["dt"], "levels": st["levels"],
+                   "leaves": st["leaves"], "l2": "inputs and working set > L2 (no flush)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "solve": {"iters": it_mean, "relres": iters[-1][1], "mvps_per_step": nmv_step},
-        "mvp": {"ms": mvp_ms, "gpairs_per_s_dense_equiv": mesh.n ** 2 / (mvp_ms / 1e3) / 1e9,
+        "step": {"rhs_calls": rhs / args.steps, "gmres_iters": iters / args.steps, "mvps": mvps / args.steps,
+                 "max_relres": max(i["max_relres"] for i in infos),
+                 "nonconverged": sum(i["nonconverged"] for i in infos),
+                 "warmup_gmres_iters": [w["gmres_iters"] for w in warm]},
+        "mvp": {"ms": mvp_ms, "gpairs_per_s_dense_equiv": N ** 2 / (mvp_ms / 1e3) / 1e9,
                 "p2p_pairs": st["p2p_pairs"], "m2l_pairs": st["m2l_pairs"]},
         "phases_ms_per_step": {k: round(v, 3) for k, v in per_step.items() if v > 0},
         "roofline": roof,
-        "e2e": {"value": e2e_s, "unit": "s/step", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "e2e": {"value": e2e_s, "unit": "s/step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(d2h),
+                "what": "bem_step driven from the host + bem_step_get_state into pinned host buffers"},
         "gpu_launches": int((st1["n_launches"] - st0["n_launches"]) / args.steps),
         "clocks": clk,
     }
 
     if args.fp64_compare and prec == bem.BEM_PREC_MIXED:
-        ctx64 = bem.BemContext(stream=stream, p_fmm=args.p, precision=bem.BEM_PREC_FP64, leaf_target=args.leaf,
-                               gmres_tol=args.tol)
-
-        def step64():
-            ctx64.upload(xyz, tri, voff, toff)
-            ctx64.build()
-            q.zero_()
-            return ctx64.solve(phid, q)
-
-        step64()
+        # FP64 FMM-BEM from the same state and warm q: one RK4 step (4 right-hand sides);
+        # an AB6 step costs one right-hand side
+        xs = torch.empty(3 * N, dtype=torch.float64, device=dev)
+        ph = torch.empty(N, dtype=torch.float64, device=dev)
+        qs = torch.empty(N, dtype=torch.float64, device=dev)
+        bem.bem_step_get_state(ctx.ctx, xs, ph, qs)
+        ctx64 = make_ctx(bem.BEM_PREC_FP64)
+        ctx64.upload(xs, tri, voff, toff)
+        bem.bem_step_init(ctx64.ctx, ph, sp, q0=qs)
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
-        it64, rr64 = step64()
+        i64 = bem.bem_step(ctx64.ctx)
         f1.record(stream)
         torch.cuda.synchronize()
-        line["fp64_compare"] = {"s_per_step": f0.elapsed_time(f1) / 1e3, "iters": it64, "relres": rr64,
-                                "timed_steps": 1, "warmup": 1}
+        t64 = f0.elapsed_time(f1) / 1e3
+        for _ in range(1):
+            ctx64.apply(1.0, qs, 0.0, None, out)
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        ctx64.apply(1.0, qs, 0.0, None, out)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        line["fp64_compare"] = {"s_per_rhs": t64 / max(1, i64["rhs_calls"]), "rk4_step_s": t64,
+                                "rhs_calls": i64["rhs_calls"], "gmres_iters": i64["gmres_iters"],
+                                "max_relres": i64["max_relres"], "mvp_ms": g0.elapsed_time(g1),
+                                "mixed_s_per_rhs": ms / 1e3 / max(1e-9, rhs / args.steps)}
         ctx64.close()
 
     if rank == 0 and args.cpu_sample:
-        n_recv = 4 * int(math.isqrt(mesh.n))
-        info = cpu_oracle_step_time(mesh, int(round(nmv_step)) + 1, n_recv)
+        n_recv = 4 * int(math.isqrt(N))
+        n_mv = int(round(mvps / args.steps)) + 3 * int(round(rhs / args.steps))  # 4-RHS products count 4
+        info = cpu_oracle_step_time(mesh, n_mv, n_recv)
         line["cpu_baseline"] = {
             "value": info["step_s"], "unit": "s/step", "cores": info["cores"], "kind": "oracle",
             "sample": "direct FP64 product at %d random receivers x %d sources (%.1f s), scaled by N/receivers to "
-                      "%d full products per step" % (info["receivers"], mesh.n, info["sample_s"],
-                                                     int(round(nmv_step)) + 1)}
+                      "%d full single-RHS products per step (the GPU step's product count)" % (
+                          info["receivers"], N, info["sample_s"], n_mv)}
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -157,6 +157,61 @@ int bem_solve(void *ctx, const double *phi, double *q_inout, int32_t *iters, dou
  * (SoA), Ldiag[N], Mdiag[N]. Any pointer may be NULL. */
 int bem_get_geometry(void *ctx, double *s, double *n, double *ldiag, double *mdiag);
 
+/* ------------------------------------------------------------------------------------------
+ * Time step (Sections 3.4-3.6): dr/dt = n q, dphi/dt = (alpha v_t + v/2).v - (p_g - 2 sigma H)
+ * + F(t) with alpha = -1 (Eqs. (3.13)-(3.15), g = 0), tangential velocity from Stokes' theorem
+ * (Eqs. (3.7)-(3.11)), mean curvature from a paraboloid through five neighbours
+ * (Eqs. (parab1)-(parab2)), polytropic gas (Eq. (2.8)), spherical shape filter on the inputs
+ * and outputs of every right-hand-side evaluation (Eqs. (3.22)-(3.25)), 6th-order
+ * Adams-Bashforth started by 4th-order Runge-Kutta (Section 3.5).
+ * Dimensionless units: lengths by a0, pressure by p0, time by a0 (rho/p0)^(1/2); rho = p0 = 1.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+    double sigma;    /* surface tension sigma/(p0 a0). Default 0.073 (water, a0 = 10 um)        */
+    double kappa;    /* polytropic exponent of Eq. (2.8). Default 1.4                           */
+    double pa;       /* acoustic amplitude Pa/p0; p_inf = 1 - pa sin(omega t) (Eq. (2.6)). 1.0 */
+    double omega;    /* angular frequency in units of (p0/rho)^(1/2)/a0. Default 1.2566 (200 kHz,
+                        a0 = 10 um)                                                            */
+    double courant;  /* C of Eq. (3.12): dt = C min(edge length at t = 0) / pa^(1/2). Default 0.1 */
+    double dt;       /* > 0: fixed step used instead of the Courant rule. Default 0              */
+    int32_t pf;      /* shape-filter bandwidth p_f: degrees 0..p_f-1. 0 = no filter. Default 6  */
+    int32_t reserved;
+} bem_step_params;
+
+typedef struct {
+    double t;              /* time after the step                                              */
+    double dt;             /* step size                                                        */
+    int32_t rhs_calls;     /* right-hand-side evaluations in the step (4 = RK4, 1 = AB6)        */
+    int32_t gmres_iters;   /* GMRES iterations summed over those evaluations                  */
+    int32_t mvps;          /* operator products, counting each 4-RHS diagonal product once    */
+    int32_t nonconverged;  /* solves that stopped at maxit (the step still advances)          */
+    double max_relres;     /* largest final relative residual among the step's solves         */
+    int64_t steps;         /* steps taken since bem_step_init                                 */
+} bem_step_stats;
+
+/* Fill *sp with the defaults listed above. */
+int bem_step_params_default(bem_step_params *sp);
+
+/* Start a time integration from the uploaded mesh (r at t = 0), phi0[N] and an optional
+ * initial guess q0[N] for the first GMRES solve (NULL = zeros). Builds one shape
+ * filter per distinct initial bubble shape (bubbles whose unit directions from their centroid
+ * coincide share it), the five-neighbour lists of the curvature fit, V_m0 and a_m0, and the
+ * step size. Returns BEM_ERR_MESH when a bubble's filter is singular or a vertex has fewer
+ * than five neighbours. */
+int bem_step_init(void *ctx, const double *phi0, const double *q0, const bem_step_params *sp);
+
+/* Advance one step; st may be NULL. */
+int bem_step(void *ctx, bem_step_stats *st);
+
+/* Current state: xyz[3N] (SoA), phi[N], the last q[N] and t. Any pointer may be NULL. */
+int bem_step_get_state(void *ctx, double *xyz, double *phi, double *q, double *t);
+
+/* Residual history of the last bem_solve: the true relative residual at the start of each
+ * GMRES cycle and the estimate |g_{k+1}|/|b| after each iteration, in order; the final entry
+ * is the true relative residual of the returned q. Writes up to `max` values to out and the
+ * total count to *count. */
+int bem_get_residual_history(void *ctx, double *out, int32_t max, int32_t *count);
+
 /* Counters; see bem_stats. */
 int bem_get_stats(void *ctx, bem_stats *out);
 int bem_reset_stats(void *ctx);

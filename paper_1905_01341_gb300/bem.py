@@ -36,6 +36,8 @@ EXPORTED = [
     "bem_mesh_upload", "bem_mesh_update_xyz", "fmm_build", "bem_apply", "bem_apply_sl",
     "bem_apply_dl", "bem_rhs", "bem_solve", "bem_get_geometry", "bem_get_stats",
     "bem_reset_stats", "bem_profile_enable", "bem_profile_read", "bem_phase_name",
+    "bem_get_residual_history", "bem_step_params_default", "bem_step_init", "bem_step",
+    "bem_step_get_state",
 ]
 
 BEM_NUM_PHASES = 13
@@ -68,6 +70,35 @@ class bem_stats(ctypes.Structure):
         ("last_relres", ctypes.c_double),
         ("last_build_ms", ctypes.c_double),
         ("n_launches", ctypes.c_int64),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class bem_step_params(ctypes.Structure):
+    _fields_ = [
+        ("sigma", ctypes.c_double),
+        ("kappa", ctypes.c_double),
+        ("pa", ctypes.c_double),
+        ("omega", ctypes.c_double),
+        ("courant", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("pf", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+class bem_step_stats(ctypes.Structure):
+    _fields_ = [
+        ("t", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("rhs_calls", ctypes.c_int32),
+        ("gmres_iters", ctypes.c_int32),
+        ("mvps", ctypes.c_int32),
+        ("nonconverged", ctypes.c_int32),
+        ("max_relres", ctypes.c_double),
+        ("steps", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -111,6 +142,11 @@ def lib() -> ctypes.CDLL:
             "bem_profile_enable": ([vp, ctypes.c_int], ctypes.c_int),
             "bem_profile_read": ([vp, ctypes.POINTER(dbl), ctypes.POINTER(i64)], ctypes.c_int),
             "bem_phase_name": ([ctypes.c_int], ctypes.c_char_p),
+            "bem_get_residual_history": ([vp, ctypes.POINTER(dbl), i32, ctypes.POINTER(i32)], ctypes.c_int),
+            "bem_step_params_default": ([ctypes.POINTER(bem_step_params)], ctypes.c_int),
+            "bem_step_init": ([vp, vp, vp, ctypes.POINTER(bem_step_params)], ctypes.c_int),
+            "bem_step": ([vp, ctypes.POINTER(bem_step_stats)], ctypes.c_int),
+            "bem_step_get_state": ([vp, vp, vp, vp, ctypes.POINTER(dbl)], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -234,6 +270,40 @@ def bem_solve(ctx, phi, q_inout, raise_on_noconv: bool = True):
 def bem_get_geometry(ctx, s=None, n=None, ldiag=None, mdiag=None) -> None:
     _check(ctx, lib().bem_get_geometry(ctx, _ptr(s, np.float64), _ptr(n, np.float64), _ptr(ldiag, np.float64),
                                        _ptr(mdiag, np.float64)))
+
+
+def bem_get_residual_history(ctx) -> list:
+    cnt = ctypes.c_int32(0)
+    _check(ctx, lib().bem_get_residual_history(ctx, None, 0, ctypes.byref(cnt)))
+    buf = (ctypes.c_double * max(1, cnt.value))()
+    _check(ctx, lib().bem_get_residual_history(ctx, buf, cnt.value, ctypes.byref(cnt)))
+    return [float(buf[i]) for i in range(cnt.value)]
+
+
+def bem_step_params_default(**overrides) -> bem_step_params:
+    sp = bem_step_params()
+    lib().bem_step_params_default(ctypes.byref(sp))
+    for k, v in overrides.items():
+        setattr(sp, k, v)
+    return sp
+
+
+def bem_step_init(ctx, phi0, sp: bem_step_params | None = None, q0=None) -> None:
+    _check(ctx, lib().bem_step_init(ctx, _ptr(phi0, np.float64), _ptr(q0, np.float64),
+                                    ctypes.byref(sp) if sp is not None else None))
+
+
+def bem_step(ctx) -> dict:
+    st = bem_step_stats()
+    _check(ctx, lib().bem_step(ctx, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def bem_step_get_state(ctx, xyz=None, phi=None, q=None) -> float:
+    t = ctypes.c_double(0.0)
+    _check(ctx, lib().bem_step_get_state(ctx, _ptr(xyz, np.float64), _ptr(phi, np.float64), _ptr(q, np.float64),
+                                         ctypes.byref(t)))
+    return float(t.value)
 
 
 def bem_get_stats(ctx) -> dict:

@@ -13,6 +13,23 @@ long long g_launch_count = 0;
 
 Context::~Context() {
     for (auto *p : up_chunks) delete p;
+    step_free(step);
+}
+
+bool is_device_ptr(const Context &c, const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a{};
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+        if (a.type == cudaMemoryTypeDevice && a.device != c.device)
+            fail(BEM_ERR_ARG, "device pointer belongs to another device");
+        return true;
+    }
+    return false;
 }
 
 namespace {
@@ -71,22 +88,6 @@ __global__ void k_check_finite(int64_t N, const double *__restrict__ a, int *__r
 Context *as_ctx(void *p) {
     if (!p) fail(BEM_ERR_ARG, "null context");
     return static_cast<Context *>(p);
-}
-
-bool is_device_ptr(const Context &c, const void *p) {
-    if (!p) return false;
-    cudaPointerAttributes a{};
-    cudaError_t e = cudaPointerGetAttributes(&a, p);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
-        if (a.type == cudaMemoryTypeDevice && a.device != c.device)
-            fail(BEM_ERR_ARG, "device pointer belongs to another device");
-        return true;
-    }
-    return false;
 }
 
 // Device view of an input vector of length n (copies host arrays into stage buffer k).
@@ -170,6 +171,85 @@ void apply_full(Context &c, double f, const double *xL, double g, const double *
     offdiag_apply(c, 1, fa, xl, ga, xm, o, c.prm.precision);
     k_add_diag<<<div_up(c.N, 256), 256, 0, c.stream>>>(c.N, f, xL, g, xM, c.ldiag.p, c.mdiag.p, out);
     BEM_LAUNCH_CHECK();
+}
+
+void build_all(Context &c) {
+    if (!c.mesh_ok) fail(BEM_ERR_NOT_BUILT, "no mesh uploaded");
+    cudaEvent_t e0, e1;
+    BEM_CUDA(cudaEventCreate(&e0));
+    BEM_CUDA(cudaEventCreate(&e1));
+    BEM_CUDA(cudaEventRecord(e0, c.stream));
+    c.built = false;
+    {
+        PhaseScope ps(c, PH_GEOMETRY);
+        compute_vertex_geometry(c);
+    }
+    const int64_t N = c.N;
+    if (c.prm.mvp == BEM_MVP_FMM) {
+        build_operators(c);
+        {
+            PhaseScope ps(c, PH_TREE);
+            build_tree(c);
+        }
+        c.m2l_chunks_h.clear();
+        c.stats.p2p_pairs = c.tree.p2p_pairs;
+        c.stats.m2l_pairs = c.tree.n_m2l;
+        c.stats.levels = c.tree.L;
+        c.stats.leaves = c.tree.nb[c.tree.L];
+    } else {
+        c.dir_hi.resize(3 * N);
+        c.dir_lo.resize(3 * N);
+        k_split<<<div_up(3 * N, 256), 256, 0, c.stream>>>(3 * N, c.xyz.p, c.dir_hi.p, c.dir_lo.p);
+        BEM_LAUNCH_CHECK();
+        c.stats.p2p_pairs = N * (N - 1);
+        c.stats.m2l_pairs = 0;
+        c.stats.levels = 0;
+        c.stats.leaves = 0;
+    }
+    // diagonals from one 4-RHS off-diagonal product (Eqs. (s3), (s5))
+    c.ones.resize(N);
+    k_fill<<<div_up(N, 256), 256, 0, c.stream>>>(N, 1.0, c.ones.p);
+    BEM_LAUNCH_CHECK();
+    DevBuf<double> tmp;
+    tmp.resize(4 * N);
+    double fa[4] = {0.0, -1.0, -1.0, -1.0}, ga[4] = {1.0, 1.0, 1.0, 1.0};
+    const double *xl[4] = {nullptr, c.nrm.p, c.nrm.p + N, c.nrm.p + 2 * N};
+    const double *xm[4] = {c.ones.p, c.xyz.p, c.xyz.p + N, c.xyz.p + 2 * N};
+    double *o[4] = {tmp.p, tmp.p + N, tmp.p + 2 * N, tmp.p + 3 * N};
+    int dprec = c.prm.diag_precision < 0 ? c.prm.precision : c.prm.diag_precision;
+    offdiag_apply(c, 4, fa, xl, ga, xm, o, dprec);
+    c.ldiag.resize(N);
+    c.mdiag.resize(N);
+    PhaseScope ps(c, PH_DIAG);
+    k_diag_identities<<<div_up(N, 256), 256, 0, c.stream>>>(N, o[0], o[1], o[2], o[3], c.xyz.p, c.nrm.p, c.ldiag.p,
+                                                            c.mdiag.p);
+    BEM_LAUNCH_CHECK();
+    DevBuf<int> bad;
+    bad.resize(1);
+    BEM_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), c.stream));
+    k_check_finite<<<div_up(N, 256), 256, 0, c.stream>>>(N, c.ldiag.p, bad.p);
+    k_check_finite<<<div_up(N, 256), 256, 0, c.stream>>>(N, c.mdiag.p, bad.p);
+    BEM_LAUNCH_CHECK();
+    BEM_CUDA(cudaEventRecord(e1, c.stream));
+    int hb = 0;
+    BEM_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    BEM_CUDA(cudaStreamSynchronize(c.stream));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c.stats.last_build_ms = ms;
+    if (hb) fail(BEM_ERR_NAN, "non-finite singular diagonal");
+    c.built = true;
+}
+
+// b = -phi/2 + M phi, then GMRES from q (device pointers).
+void solve_internal(Context &c, const double *phi, double *q, int *it, double *rr) {
+    c.bv.resize(c.N);
+    apply_full(c, 0.0, nullptr, 1.0, phi, c.bv.p);
+    k_rhs_combine<<<div_up(c.N, 256), 256, 0, c.stream>>>(c.N, phi, c.bv.p);
+    BEM_LAUNCH_CHECK();
+    gmres_solve(c, c.bv.p, q, it, rr);
 }
 
 }  // namespace bem
@@ -274,75 +354,7 @@ int bem_mesh_update_xyz(void *ctx, const double *xyz) {
 }
 
 int fmm_build(void *ctx) {
-    return guarded(ctx, [&](Context &c) {
-        if (!c.mesh_ok) fail(BEM_ERR_NOT_BUILT, "no mesh uploaded");
-        cudaEvent_t e0, e1;
-        BEM_CUDA(cudaEventCreate(&e0));
-        BEM_CUDA(cudaEventCreate(&e1));
-        BEM_CUDA(cudaEventRecord(e0, c.stream));
-        c.built = false;
-        {
-            PhaseScope ps(c, PH_GEOMETRY);
-            compute_vertex_geometry(c);
-        }
-        const int64_t N = c.N;
-        if (c.prm.mvp == BEM_MVP_FMM) {
-            build_operators(c);
-            {
-                PhaseScope ps(c, PH_TREE);
-                build_tree(c);
-            }
-            c.m2l_chunks_h.clear();
-            c.stats.p2p_pairs = c.tree.p2p_pairs;
-            c.stats.m2l_pairs = c.tree.n_m2l;
-            c.stats.levels = c.tree.L;
-            c.stats.leaves = c.tree.nb[c.tree.L];
-        } else {
-            c.dir_hi.resize(3 * N);
-            c.dir_lo.resize(3 * N);
-            k_split<<<div_up(3 * N, 256), 256, 0, c.stream>>>(3 * N, c.xyz.p, c.dir_hi.p, c.dir_lo.p);
-            BEM_LAUNCH_CHECK();
-            c.stats.p2p_pairs = N * (N - 1);
-            c.stats.m2l_pairs = 0;
-            c.stats.levels = 0;
-            c.stats.leaves = 0;
-        }
-        // diagonals from one 4-RHS off-diagonal product (Eqs. (s3), (s5))
-        c.ones.resize(N);
-        k_fill<<<div_up(N, 256), 256, 0, c.stream>>>(N, 1.0, c.ones.p);
-        BEM_LAUNCH_CHECK();
-        DevBuf<double> tmp;
-        tmp.resize(4 * N);
-        double fa[4] = {0.0, -1.0, -1.0, -1.0}, ga[4] = {1.0, 1.0, 1.0, 1.0};
-        const double *xl[4] = {nullptr, c.nrm.p, c.nrm.p + N, c.nrm.p + 2 * N};
-        const double *xm[4] = {c.ones.p, c.xyz.p, c.xyz.p + N, c.xyz.p + 2 * N};
-        double *o[4] = {tmp.p, tmp.p + N, tmp.p + 2 * N, tmp.p + 3 * N};
-        int dprec = c.prm.diag_precision < 0 ? c.prm.precision : c.prm.diag_precision;
-        offdiag_apply(c, 4, fa, xl, ga, xm, o, dprec);
-        c.ldiag.resize(N);
-        c.mdiag.resize(N);
-        PhaseScope ps(c, PH_DIAG);
-        k_diag_identities<<<div_up(N, 256), 256, 0, c.stream>>>(N, o[0], o[1], o[2], o[3], c.xyz.p, c.nrm.p, c.ldiag.p,
-                                                                c.mdiag.p);
-        BEM_LAUNCH_CHECK();
-        DevBuf<int> bad;
-        bad.resize(1);
-        BEM_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), c.stream));
-        k_check_finite<<<div_up(N, 256), 256, 0, c.stream>>>(N, c.ldiag.p, bad.p);
-        k_check_finite<<<div_up(N, 256), 256, 0, c.stream>>>(N, c.mdiag.p, bad.p);
-        BEM_LAUNCH_CHECK();
-        BEM_CUDA(cudaEventRecord(e1, c.stream));
-        int hb = 0;
-        BEM_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
-        BEM_CUDA(cudaStreamSynchronize(c.stream));
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        c.stats.last_build_ms = ms;
-        if (hb) fail(BEM_ERR_NAN, "non-finite singular diagonal");
-        c.built = true;
-    });
+    return guarded(ctx, [&](Context &c) { build_all(c); });
 }
 
 int bem_apply(void *ctx, double f, const double *xL, double g, const double *xM, double *out) {
@@ -388,10 +400,6 @@ int bem_solve(void *ctx, const double *phi, double *q_inout, int32_t *iters, dou
             dq = c.stage_in[1].p;
             BEM_CUDA(cudaMemcpyAsync(dq, q_inout, c.N * sizeof(double), cudaMemcpyHostToDevice, c.stream));
         }
-        c.bv.resize(c.N);
-        apply_full(c, 0.0, nullptr, 1.0, dp, c.bv.p);
-        k_rhs_combine<<<div_up(c.N, 256), 256, 0, c.stream>>>(c.N, dp, c.bv.p);
-        BEM_LAUNCH_CHECK();
         struct CopyBack {
             Context &c;
             bool host;
@@ -403,7 +411,7 @@ int bem_solve(void *ctx, const double *phi, double *q_inout, int32_t *iters, dou
                 }
             }
         } cb{c, host_q, q_inout, dq};
-        gmres_solve(c, c.bv.p, dq, &it, &rr);
+        solve_internal(c, dp, dq, &it, &rr);
     });
     if (iters) *iters = it;
     if (relres) *relres = rr;
@@ -429,6 +437,52 @@ int bem_get_geometry(void *ctx, double *s, double *n, double *ldiag, double *mdi
             BEM_CUDA(cudaMemcpyAsync(it.dst, it.src, it.n * sizeof(double), k, c.stream));
         }
         BEM_CUDA(cudaStreamSynchronize(c.stream));
+    });
+}
+
+int bem_step_params_default(bem_step_params *sp) {
+    if (!sp) return BEM_ERR_ARG;
+    std::memset(sp, 0, sizeof(*sp));
+    sp->sigma = 0.073;
+    sp->kappa = 1.4;
+    sp->pa = 1.0;
+    sp->omega = 1.2566370614359172;
+    sp->courant = 0.1;
+    sp->dt = 0.0;
+    sp->pf = 6;
+    return BEM_OK;
+}
+
+int bem_step_init(void *ctx, const double *phi0, const double *q0, const bem_step_params *sp) {
+    return guarded(ctx, [&](Context &c) {
+        if (!phi0) fail(BEM_ERR_ARG, "null phi0");
+        bem_step_params p;
+        if (sp) p = *sp;
+        else bem_step_params_default(&p);
+        const double *dp = dev_in(c, phi0, c.N, 0);
+        const double *dq = q0 ? dev_in(c, q0, c.N, 1) : nullptr;
+        step_init(c, dp, dq, p);
+    });
+}
+
+int bem_step(void *ctx, bem_step_stats *st) {
+    return guarded(ctx, [&](Context &c) {
+        bem_step_stats s{};
+        step_advance(c, s);
+        if (st) *st = s;
+    });
+}
+
+int bem_step_get_state(void *ctx, double *xyz, double *phi, double *q, double *t) {
+    return guarded(ctx, [&](Context &c) { step_get_state(c, xyz, phi, q, t); });
+}
+
+int bem_get_residual_history(void *ctx, double *out, int32_t max, int32_t *count) {
+    return guarded(ctx, [&](Context &c) {
+        int n = (int)c.res_hist.size();
+        if (count) *count = n;
+        if (out)
+            for (int i = 0; i < n && i < max; ++i) out[i] = c.res_hist[i];
     });
 }
 

@@ -15,6 +15,7 @@
 // index n^2 for m = 0, n^2 + 2m - 1 (real part) and n^2 + 2m (imaginary part) for m > 0.
 #include "internal.h"
 
+#include <algorithm>
 #include <cmath>
 
 namespace bem {
@@ -343,7 +344,11 @@ __global__ void __launch_bounds__(P2M_THREADS) k_p2m(int p, int nleaf, const int
 // tiled GEMM (64 output rows x 64 columns per block; a column is one pair and one RHS).
 constexpr int XT_ROWS = 64, XT_COLS = 64, XT_K = 16, XT_THREADS = 256;
 
-template <class T, int R>
+// MODE kStorePair: Y[pair] = T X[src] (one slot per pair, summed later in a fixed order).
+// MODE kAddTarget: Y[tgt] += T X[src]; only for launches whose targets are all distinct.
+constexpr int kStorePair = 0, kAddTarget = 1;
+
+template <class T, int R, int MODE>
 __global__ void __launch_bounds__(XT_THREADS) k_xlat(const T *__restrict__ mats, int P, const XChunk *__restrict__ chunks,
                                                      const int32_t *__restrict__ srcs, const int32_t *__restrict__ tgts,
                                                      const T *X, T *Y) {  // X and Y may be one array (M2M, L2L)
@@ -412,13 +417,38 @@ __global__ void __launch_bounds__(XT_THREADS) k_xlat(const T *__restrict__ mats,
         int col = tx * 4 + j;
         if (col >= ncol) continue;
         int r = col % R;
-        T *yb = Y + ((size_t)s_tgt[col] * R + r) * P;
+        T *yb = (MODE == kStorePair) ? Y + ((size_t)(ch.start + col / R) * R + r) * P
+                                     : Y + ((size_t)s_tgt[col] * R + r) * P;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             int gr = row0 + ty * 4 + i;
-            if (gr < P) atomicAdd(yb + gr, acc[i][j]);
+            if (gr < P) {
+                if (MODE == kStorePair) yb[gr] = acc[i][j];
+                else yb[gr] += acc[i][j];
+            }
         }
     }
+}
+
+// Y[t] += sum of Ypair[k] over the pairs k of target t, in ascending k (fixed order,
+// compensated in FP32). One thread per (target, coefficient).
+template <class T, int R>
+__global__ void k_reduce_pairs(int t0, const int32_t *__restrict__ off, const int32_t *__restrict__ by,
+                               const T *__restrict__ Ypair, int P, T *__restrict__ Y) {
+    int t = t0 + blockIdx.x;
+    int e = blockIdx.y * blockDim.x + threadIdx.x;
+    if (e >= R * P) return;
+    int a = off[t], b = off[t + 1];
+    if (a == b) return;
+    T s = 0, c = 0;
+    for (int k = a; k < b; ++k) {
+        T v = Ypair[(size_t)by[k] * R * P + e];
+        T tt = s + v;
+        T bp = tt - s;
+        c += (s - (tt - bp)) + (v - bp);
+        s = tt;
+    }
+    Y[(size_t)t * R * P + e] += s + c;
 }
 
 // ------------------------------------------------------------------------------ L2P
@@ -606,27 +636,51 @@ void run_fmm(Context &c, const RhsArgs<R> &a) {
         k_zero<T><<<div_up(exp_sz, tb), tb, 0, st>>>(exp_sz, lc);
         BEM_LAUNCH_CHECK();
     }
-    // M2M upward, levels L -> 2
+    // per-pair buffer for the fixed-order reductions
+    T *ypair;
+    {
+        int64_t nup_all = t.up_off[L + 1];
+        size_t need = (size_t)std::max<int64_t>(std::max<int64_t>(t.n_m2l, nup_all), 1) * R * P;
+        if (F64) {
+            c.ypair64.resize(need);
+            ypair = (T *)c.ypair64.p;
+        } else {
+            c.ypair32.resize(need);
+            ypair = (T *)c.ypair32.p;
+        }
+    }
+    const int red_blocks_y = div_up(R * P, 128);
+    // M2M upward, levels L -> 2: per-pair products, then each parent sums its children
     for (int l = L; l >= 3; --l) {
         PhaseScope ps(c, PH_M2M);
         if (!up_n[l]) continue;
         dim3 grid((unsigned)up_n[l], rowblocks);
-        k_xlat<T, R><<<grid, XT_THREADS, 0, st>>>(m2m, P, c.m2l_chunks.p + up_first[l], t.up_child.p, t.up_parent.p, mp, mp);
+        k_xlat<T, R, kStorePair><<<grid, XT_THREADS, 0, st>>>(m2m, P, c.m2l_chunks.p + up_first[l], t.up_child.p,
+                                                             t.up_parent.p, mp, ypair);
+        BEM_LAUNCH_CHECK();
+        dim3 rg((unsigned)t.nb[l - 1], red_blocks_y);
+        k_reduce_pairs<T, R><<<rg, 128, 0, st>>>(t.base[l - 1], t.up_par_off.p, t.up_by_par.p, ypair, P, mp);
         BEM_LAUNCH_CHECK();
     }
-    // M2L, all levels at once
+    // M2L, all levels at once, then each target sums its sources
     if (nm2l_chunks) {
         PhaseScope ps(c, PH_M2L);
         dim3 grid((unsigned)nm2l_chunks, rowblocks);
-        k_xlat<T, R><<<grid, XT_THREADS, 0, st>>>(m2l, P, c.m2l_chunks.p + 1, t.m2l_src.p, t.m2l_tgt.p, mp, lc);
+        k_xlat<T, R, kStorePair><<<grid, XT_THREADS, 0, st>>>(m2l, P, c.m2l_chunks.p + 1, t.m2l_src.p, t.m2l_tgt.p,
+                                                             mp, ypair);
+        BEM_LAUNCH_CHECK();
+        int ntg = t.nbox - t.base[2];
+        dim3 rg((unsigned)ntg, red_blocks_y);
+        k_reduce_pairs<T, R><<<rg, 128, 0, st>>>(t.base[2], t.m2l_tgt_off.p, t.m2l_by_tgt.p, ypair, P, lc);
         BEM_LAUNCH_CHECK();
     }
-    // L2L downward, levels 3 -> L
+    // L2L downward, levels 3 -> L: every child has exactly one parent, so it adds in place
     for (int l = 3; l <= L; ++l) {
         if (!up_n[l]) continue;
         PhaseScope ps(c, PH_L2L);
         dim3 grid((unsigned)up_n[l], rowblocks);
-        k_xlat<T, R><<<grid, XT_THREADS, 0, st>>>(l2l, P, c.m2l_chunks.p + up_first[l], t.up_parent.p, t.up_child.p, lc, lc);
+        k_xlat<T, R, kAddTarget><<<grid, XT_THREADS, 0, st>>>(l2l, P, c.m2l_chunks.p + up_first[l], t.up_parent.p,
+                                                             t.up_child.p, lc, lc);
         BEM_LAUNCH_CHECK();
     }
     // L2P

@@ -191,6 +191,7 @@ void gmres_solve(Context &c, const double *b, double *x, int *iters_out, double 
     double *d_bn2 = c.scal.p, *d_beta2 = c.scal.p + 1, *d_beta = c.scal.p + 2, *d_res = c.scal.p + 3;
     double *d_tmp = c.scal.p + 4;
 
+    c.res_hist.clear();
     vec.dots(1, b, N, b, d_bn2, 0);
     const double bnorm = std::sqrt(read_scalar(c, d_bn2));
     int iters = 0, mvps = 0;
@@ -213,6 +214,7 @@ void gmres_solve(Context &c, const double *b, double *x, int *iters_out, double 
         vec.dots(1, c.rv.p, N, c.rv.p, d_beta2, 0);
         double beta = std::sqrt(read_scalar(c, d_beta2));
         relres = beta / bnorm;
+        c.res_hist.push_back(relres);
         if (relres <= tol) {
             converged = true;
             break;
@@ -241,6 +243,7 @@ void gmres_solve(Context &c, const double *b, double *x, int *iters_out, double 
             ++iters;
             kk = k + 1;
             double est = read_scalar(c, d_res) / bnorm;
+            c.res_hist.push_back(est);
             if (est <= tol || iters >= maxit) break;
         }
         k_backsolve<<<1, 1, 0, c.stream>>>(kk, m, c.hmat.p, c.gvec.p, c.yvec.p);

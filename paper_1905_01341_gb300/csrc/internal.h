@@ -121,6 +121,10 @@ struct Tree {
     std::vector<int64_t> up_off;       // per level: offset into up_child/up_parent
     std::vector<std::vector<int64_t>> up_class_off;  // per level: [9]
     DevBuf<int32_t> up_child, up_parent;
+    // target-major views of the pair lists, for the fixed-order reductions: for every box,
+    // the pair indices that write to it, ascending (CSR over all boxes)
+    DevBuf<int32_t> m2l_tgt_off, m2l_by_tgt;  // [nbox+1], [n_m2l]
+    DevBuf<int32_t> up_par_off, up_by_par;    // [nbox+1], [n_up]
     // leaf-local coordinates of sorted points in units of the leaf box (range [-1/2, 1/2))
     DevBuf<double> loc64;      // [3][N]
     DevBuf<float> loc32;       // [3][N]
@@ -191,6 +195,8 @@ struct Profiler {
 };
 
 struct Context;
+struct StepState;
+void step_free(StepState *s);
 // Records the device time of everything launched on the context stream during its lifetime.
 struct PhaseScope {
     Context *c;
@@ -229,6 +235,8 @@ struct Context {
     DevBuf<float> q32, w32;
     DevBuf<double> mp64, lc64;     // expansions [nbox][R][P]
     DevBuf<float> mp32, lc32;
+    DevBuf<double> ypair64;        // per-pair translation results [pair][R][P]
+    DevBuf<float> ypair32;
     DevBuf<double> far64;          // far-field potential [R][N] (sorted)
     DevBuf<float> far32;
     DevBuf<double> near_out;       // combined potential [R][N] (sorted)
@@ -251,6 +259,8 @@ struct Context {
     HostPinned<double> hscal;
 
     bem_stats stats{};
+    std::vector<double> res_hist;  // residual estimates |g_{k+1}|/|b| of the last solve
+    StepState *step = nullptr;     // time-integration state (timestep.cu)
     Profiler prof;
     ~Context();
 };
@@ -300,5 +310,13 @@ inline PhaseScope::~PhaseScope() {
 
 // bem_api.cu
 void apply_full(Context &c, double f, const double *xL, double g, const double *xM, double *out);
+void build_all(Context &c);
+void solve_internal(Context &c, const double *phi, double *q, int *it, double *rr);
+bool is_device_ptr(const Context &c, const void *p);
+
+// timestep.cu
+void step_init(Context &c, const double *phi0_dev, const double *q0_dev, const bem_step_params &sp);
+void step_advance(Context &c, bem_step_stats &st);
+void step_get_state(Context &c, double *xyz, double *phi, double *q, double *t);
 
 }  // namespace bem

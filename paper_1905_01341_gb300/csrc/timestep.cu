@@ -1,0 +1,673 @@
+// Time step of the bubble-dynamics method (Sections 3.4-3.6) on the device:
+//   - spherical shape filter x_hat = G (G^(-1) x) per bubble (Eqs. (3.22)-(3.25)), applied to
+//     the inputs (r, phi) and to the outputs (dr/dt, dphi/dt) of every right-hand side;
+//   - Dirichlet solve for q through the FMM/GMRES path of this library;
+//   - tangential velocity from Stokes' theorem (Eqs. (3.7)-(3.11));
+//   - mean curvature from the paraboloid through five neighbours (Eqs. (parab1)-(parab2));
+//   - bubble volume (divergence theorem on the facets) and polytropic gas (Eq. (2.8));
+//   - dr/dt = v + alpha v_t = n q and dphi/dt = (alpha v_t + v/2).v - (p_g - 2 sigma H) + F(t)
+//     with alpha = -1, F(t) = 1 - Pa sin(omega t) (Eqs. (2.6), (3.13)-(3.15));
+//   - 4th-order Runge-Kutta for the first five steps, then 6th-order Adams-Bashforth
+//     (Section 3.5), constant dt from Eq. (3.12).
+// All arithmetic is FP64. Per-vertex sums run over the sorted vertex->triangle lists and
+// per-bubble sums are block reductions in a fixed order, so a step is reproducible.
+#include "internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+
+namespace bem {
+
+struct StepState {
+    bool ready = false;
+    bem_step_params sp{};
+    double t = 0.0, dt = 0.0;
+    int64_t steps = 0;
+    int nhist = 0;  // valid history entries (newest at index 0 of `order`)
+    int order[5] = {0, 1, 2, 3, 4};
+    int Pf = 0;
+    DevBuf<double> y, q, hist, k1, k2, k3, k4, ytmp, yf, f;
+    DevBuf<double> V0, a0, V, pg;
+    DevBuf<int32_t> shape_of, bub_of, nbr5;
+    DevBuf<int64_t> voff, toff;
+    DevBuf<double> G, Gp;  // per shape: G [nd][Pf], Gp [Pf][nd], concatenated
+    DevBuf<int64_t> g_off;  // per shape offset (in elements) into G / Gp
+    DevBuf<double> vt, H;
+    bem_step_stats last{};
+};
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxNbrCand = 64;
+
+StepState &state_of(Context &c) {
+    if (!c.step) c.step = new StepState();
+    return *c.step;
+}
+
+// Five lowest-index neighbours (vertices sharing an edge) of every vertex.
+__global__ void k_nbr5(int64_t N, int64_t T, const int32_t *__restrict__ tri, const int32_t *__restrict__ off,
+                       const int32_t *__restrict__ v2t, int32_t *__restrict__ nbr5, int *__restrict__ bad) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    int cand[kMaxNbrCand];
+    int n = 0;
+    for (int t = off[j]; t < off[j + 1]; ++t) {
+        int64_t k = v2t[t];
+        for (int c = 0; c < 3; ++c) {
+            int v = tri[c * T + k];
+            if (v == (int)j) continue;
+            bool dup = false;
+            for (int i = 0; i < n; ++i) dup |= (cand[i] == v);
+            if (!dup && n < kMaxNbrCand) cand[n++] = v;
+        }
+    }
+    if (n < 5) {
+        atomicOr(bad, 1);
+        for (int i = 0; i < 5; ++i) nbr5[j * 5 + i] = (int)j;
+        return;
+    }
+    // partial selection of the five smallest
+    for (int i = 0; i < 5; ++i) {
+        int mi = i;
+        for (int k = i + 1; k < n; ++k)
+            if (cand[k] < cand[mi]) mi = k;
+        int tmp = cand[i];
+        cand[i] = cand[mi];
+        cand[mi] = tmp;
+        nbr5[j * 5 + i] = cand[i];
+    }
+}
+
+// Fully normalised real spherical harmonics (orthonormal on the unit sphere) of degrees
+// 0..pf-1 at one unit direction; column order j = n^2 + n + m.
+__device__ void real_sh_row(double dx, double dy, double dz, int pf, double *out, double *pb) {
+    double len = sqrt(dx * dx + dy * dy + dz * dz);
+    double ct = fmin(fmax(dz / len, -1.0), 1.0);
+    double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    double ph = atan2(dy, dx);
+    // pb[n * pf + m]
+    pb[0] = sqrt(1.0 / (4.0 * kPi));
+    for (int m = 1; m < pf; ++m) pb[m * pf + m] = -sqrt((2.0 * m + 1.0) / (2.0 * m)) * st * pb[(m - 1) * pf + (m - 1)];
+    for (int m = 0; m + 1 < pf; ++m) pb[(m + 1) * pf + m] = sqrt(2.0 * m + 3.0) * ct * pb[m * pf + m];
+    for (int m = 0; m < pf; ++m)
+        for (int n = m + 2; n < pf; ++n) {
+            double a = sqrt((4.0 * n * n - 1.0) / ((double)n * n - (double)m * m));
+            double b = sqrt(((n - 1.0) * (n - 1.0) - (double)m * m) / (4.0 * (n - 1.0) * (n - 1.0) - 1.0));
+            pb[n * pf + m] = a * (ct * pb[(n - 1) * pf + m] - b * pb[(n - 2) * pf + m]);
+        }
+    const double r2 = sqrt(2.0);
+    for (int n = 0; n < pf; ++n)
+        for (int m = -n; m <= n; ++m) {
+            int j = n * n + n + m;
+            if (m == 0) out[j] = pb[n * pf];
+            else if (m > 0) out[j] = r2 * pb[n * pf + m] * cos(m * ph);
+            else out[j] = r2 * pb[n * pf - m] * sin(-m * ph);
+        }
+}
+
+// G[i][*] for the unit directions of one shape (from its representative bubble).
+__global__ void k_filter_G(int nd, const double *__restrict__ xyz, int64_t N, int64_t v0, double cx, double cy,
+                           double cz, int pf, double *__restrict__ G, double *__restrict__ scratch) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nd) return;
+    int64_t j = v0 + i;
+    real_sh_row(xyz[j] - cx, xyz[N + j] - cy, xyz[2 * N + j] - cz, pf, G + (size_t)i * pf * pf,
+                scratch + (size_t)i * pf * pf);
+}
+
+// Gp = (G^T G)^(-1) G^T by Cholesky (one block). A: scratch [Pf][Pf].
+__global__ void k_filter_pinv(int nd, int P, const double *__restrict__ G, double *__restrict__ A,
+                              double *__restrict__ Gp, int *__restrict__ bad) {
+    for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
+        int a = e / P, b = e % P;
+        double s = 0.0;
+        for (int i = 0; i < nd; ++i) s += G[(size_t)i * P + a] * G[(size_t)i * P + b];
+        A[e] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {  // in-place Cholesky, lower triangle
+        for (int k = 0; k < P; ++k) {
+            double d = A[k * P + k];
+            for (int m = 0; m < k; ++m) d -= A[k * P + m] * A[k * P + m];
+            if (!(d > 0.0)) {
+                atomicOr(bad, 4);
+                d = 1.0;
+            }
+            d = sqrt(d);
+            A[k * P + k] = d;
+            for (int i = k + 1; i < P; ++i) {
+                double s = A[i * P + k];
+                for (int m = 0; m < k; ++m) s -= A[i * P + m] * A[k * P + m];
+                A[i * P + k] = s / d;
+            }
+        }
+    }
+    __syncthreads();
+    // columns i of G^T: solve L L^T x = G[i][:], write Gp[:][i]
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) {
+        double x[128];
+        for (int a = 0; a < P; ++a) {
+            double s = G[(size_t)i * P + a];
+            for (int m = 0; m < a; ++m) s -= A[a * P + m] * x[m];
+            x[a] = s / A[a * P + a];
+        }
+        for (int a = P - 1; a >= 0; --a) {
+            double s = x[a];
+            for (int m = a + 1; m < P; ++m) s -= A[m * P + a] * x[m];
+            x[a] = s / A[a * P + a];
+        }
+        for (int a = 0; a < P; ++a) Gp[(size_t)a * nd + i] = x[a];
+    }
+}
+
+// Y = G (Gp X) per bubble for the four SoA components of a state [4N]; may run in place.
+__global__ void k_filter_apply(int64_t N, const int64_t *__restrict__ voff, const int32_t *__restrict__ shape_of,
+                               const int64_t *__restrict__ g_off, int P, const double *__restrict__ G,
+                               const double *__restrict__ Gp, const double *X, double *Y) {
+    extern __shared__ double C[];  // [P][4]
+    int m = blockIdx.x;
+    int64_t a = voff[m];
+    int nd = (int)(voff[m + 1] - a);
+    const double *Gm = G + g_off[shape_of[m]];
+    const double *Gpm = Gp + g_off[shape_of[m]];
+    for (int e = threadIdx.x; e < P * 4; e += blockDim.x) {
+        int p = e >> 2, comp = e & 3;
+        const double *x = X + comp * N + a;
+        const double *g = Gpm + (size_t)p * nd;
+        double s = 0.0;
+        for (int i = 0; i < nd; ++i) s = fma(g[i], x[i], s);
+        C[e] = s;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) {
+        const double *g = Gm + (size_t)i * P;
+        double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+        for (int p = 0; p < P; ++p) {
+            double gv = g[p];
+            s0 = fma(gv, C[p * 4 + 0], s0);
+            s1 = fma(gv, C[p * 4 + 1], s1);
+            s2 = fma(gv, C[p * 4 + 2], s2);
+            s3 = fma(gv, C[p * 4 + 3], s3);
+        }
+        Y[a + i] = s0;
+        Y[N + a + i] = s1;
+        Y[2 * N + a + i] = s2;
+        Y[3 * N + a + i] = s3;
+    }
+}
+
+// Eqs. (3.10)-(3.11): v_t,j = (n x v)_j x n_j with (n x v)_j = (1/(3 s_j)) sum_k (n x v)_k A_k
+// and (n x v)_k A_k = [(r2 - r3) phi1 + (r3 - r1) phi2 + (r1 - r2) phi3] / 2.
+__global__ void k_tangential(int64_t N, int64_t T, const double *__restrict__ xyz, const double *__restrict__ phi,
+                             const int32_t *__restrict__ tri, const int32_t *__restrict__ off,
+                             const int32_t *__restrict__ v2t, const double *__restrict__ s,
+                             const double *__restrict__ nrm, double *__restrict__ vt) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const double *X = xyz, *Y = xyz + N, *Z = xyz + 2 * N;
+    double ax = 0, ay = 0, az = 0;
+    for (int t = off[j]; t < off[j + 1]; ++t) {
+        int64_t k = v2t[t];
+        int a = tri[k], b = tri[T + k], c = tri[2 * T + k];
+        double pa = phi[a], pb = phi[b], pc = phi[c];
+        ax += 0.5 * ((X[b] - X[c]) * pa + (X[c] - X[a]) * pb + (X[a] - X[b]) * pc);
+        ay += 0.5 * ((Y[b] - Y[c]) * pa + (Y[c] - Y[a]) * pb + (Y[a] - Y[b]) * pc);
+        az += 0.5 * ((Z[b] - Z[c]) * pa + (Z[c] - Z[a]) * pb + (Z[a] - Z[b]) * pc);
+    }
+    double inv = 1.0 / (3.0 * s[j]);
+    ax *= inv;
+    ay *= inv;
+    az *= inv;
+    double nx = nrm[j], ny = nrm[N + j], nz = nrm[2 * N + j];
+    vt[j] = ay * nz - az * ny;
+    vt[N + j] = az * nx - ax * nz;
+    vt[2 * N + j] = ax * ny - ay * nx;
+}
+
+// Eqs. (parab1)-(parab2): 5x5 interpolation in the frame (e1, e2, n_j); H = -B3 - B5.
+// Gaussian elimination with partial pivoting (same solution as Cramer's rule).
+__global__ void k_curvature(int64_t N, const double *__restrict__ xyz, const double *__restrict__ nrm,
+                            const int32_t *__restrict__ nbr5, double *__restrict__ H, int *__restrict__ bad) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    double n[3] = {nrm[j], nrm[N + j], nrm[2 * N + j]};
+    int ax = 0;
+    for (int d = 1; d < 3; ++d)
+        if (fabs(n[d]) < fabs(n[ax])) ax = d;
+    double e1[3] = {0, 0, 0};
+    e1[ax] = 1.0;
+    double dn = e1[0] * n[0] + e1[1] * n[1] + e1[2] * n[2];
+    for (int d = 0; d < 3; ++d) e1[d] -= dn * n[d];
+    double l1 = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+    for (int d = 0; d < 3; ++d) e1[d] /= l1;
+    double e2[3] = {n[1] * e1[2] - n[2] * e1[1], n[2] * e1[0] - n[0] * e1[2], n[0] * e1[1] - n[1] * e1[0]};
+    double A[5][6];
+    for (int l = 0; l < 5; ++l) {
+        int k = nbr5[j * 5 + l];
+        double d[3] = {xyz[k] - xyz[j], xyz[N + k] - xyz[N + j], xyz[2 * N + k] - xyz[2 * N + j]};
+        double x = d[0] * e1[0] + d[1] * e1[1] + d[2] * e1[2];
+        double y = d[0] * e2[0] + d[1] * e2[1] + d[2] * e2[2];
+        double z = d[0] * n[0] + d[1] * n[1] + d[2] * n[2];
+        A[l][0] = x;
+        A[l][1] = y;
+        A[l][2] = x * x;
+        A[l][3] = x * y;
+        A[l][4] = y * y;
+        A[l][5] = z;
+    }
+    for (int c = 0; c < 5; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 5; ++r)
+            if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+        if (A[piv][c] == 0.0) {
+            atomicOr(bad, 8);
+            H[j] = 0.0;
+            return;
+        }
+        if (piv != c)
+            for (int k = 0; k < 6; ++k) {
+                double t = A[c][k];
+                A[c][k] = A[piv][k];
+                A[piv][k] = t;
+            }
+        for (int r = c + 1; r < 5; ++r) {
+            double f = A[r][c] / A[c][c];
+            for (int k = c; k < 6; ++k) A[r][k] -= f * A[c][k];
+        }
+    }
+    double B[5];
+    for (int r = 4; r >= 0; --r) {
+        double s = A[r][5];
+        for (int k = r + 1; k < 5; ++k) s -= A[r][k] * B[k];
+        B[r] = s / A[r][r];
+    }
+    H[j] = -B[2] - B[4];
+}
+
+// V_m = (1/3) sum_k (N_k A_k) . c_k over the bubble's triangles (one block per bubble).
+__global__ void k_volumes(int64_t N, int64_t T, const int64_t *__restrict__ toff, const int32_t *__restrict__ tri,
+                          const double *__restrict__ xyz, double *__restrict__ V) {
+    __shared__ double red[256];
+    int m = blockIdx.x;
+    const double *X = xyz, *Y = xyz + N, *Z = xyz + 2 * N;
+    double acc = 0.0;
+    for (int64_t k = toff[m] + threadIdx.x; k < toff[m + 1]; k += blockDim.x) {
+        int a = tri[k], b = tri[T + k], c = tri[2 * T + k];
+        double e1x = X[b] - X[a], e1y = Y[b] - Y[a], e1z = Z[b] - Z[a];
+        double e2x = X[c] - X[a], e2y = Y[c] - Y[a], e2z = Z[c] - Z[a];
+        double nax = 0.5 * (e1y * e2z - e1z * e2y), nay = 0.5 * (e1z * e2x - e1x * e2z), naz = 0.5 * (e1x * e2y - e1y * e2x);
+        double cx = (X[a] + X[b] + X[c]) / 3.0, cy = (Y[a] + Y[b] + Y[c]) / 3.0, cz = (Z[a] + Z[b] + Z[c]) / 3.0;
+        acc += (nax * cx + nay * cy + naz * cz) / 3.0;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) V[m] = red[0];
+}
+
+__global__ void k_init_bubbles(int M, const double *__restrict__ V, double *__restrict__ V0, double *__restrict__ a0) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    V0[m] = V[m];
+    a0[m] = cbrt(3.0 * V[m] / (4.0 * kPi));
+}
+
+// Eq. (2.8): p_g = (1 + 2 sigma / a_m0) (V_m0 / V_m)^kappa.
+__global__ void k_pressure(int M, const double *__restrict__ V, const double *__restrict__ V0,
+                           const double *__restrict__ a0, double sigma, double kappa, double *__restrict__ pg) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    pg[m] = (1.0 + 2.0 * sigma / a0[m]) * pow(V0[m] / V[m], kappa);
+}
+
+__global__ void k_bubble_of(int M, const int64_t *__restrict__ voff, int32_t *__restrict__ bub) {
+    int m = blockIdx.x;
+    for (int64_t j = voff[m] + threadIdx.x; j < voff[m + 1]; j += blockDim.x) bub[j] = m;
+}
+
+// Eqs. (3.13)-(3.15) with alpha = -1: f = [n q ; (alpha v_t + v/2).v - (p_g - 2 sigma H) + F].
+__global__ void k_assemble(int64_t N, const double *__restrict__ q, const double *__restrict__ nrm,
+                           const double *__restrict__ vt, const double *__restrict__ H, const double *__restrict__ pg,
+                           const int32_t *__restrict__ bub, double sigma, double F, double *__restrict__ f) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const double alpha = -1.0;
+    double vt3[3] = {vt[j], vt[N + j], vt[2 * N + j]};
+    double v3[3], u3[3];
+    for (int d = 0; d < 3; ++d) {
+        v3[d] = nrm[d * N + j] * q[j] + vt3[d];
+        u3[d] = v3[d] + alpha * vt3[d];
+        f[d * N + j] = u3[d];
+    }
+    double e = 0.0;
+    for (int d = 0; d < 3; ++d) e += (alpha * vt3[d] + 0.5 * v3[d]) * v3[d];
+    f[3 * N + j] = e - (pg[bub[j]] - 2.0 * sigma * H[j]) + F;
+}
+
+__global__ void k_axpy4(int64_t n, double a, const double *__restrict__ x, const double *__restrict__ y,
+                        double *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = y[i] + a * x[i];
+}
+
+__global__ void k_rk4_combine(int64_t n, double dt, const double *__restrict__ k1, const double *__restrict__ k2,
+                              const double *__restrict__ k3, const double *__restrict__ k4, double *__restrict__ y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] += dt / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+}
+
+struct Six {
+    const double *f[6];
+    double b[6];
+};
+__global__ void k_ab6(int64_t n, double dt, Six s, double *__restrict__ y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int k = 0; k < 6; ++k) acc += s.b[k] * s.f[k][i];
+        y[i] += dt * acc;
+    }
+}
+
+__global__ void k_min_edge(int64_t T, int64_t N, const int32_t *__restrict__ tri, const double *__restrict__ xyz,
+                           double *__restrict__ out) {
+    __shared__ double red[256];
+    double mn = INFINITY;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < T; k += (int64_t)gridDim.x * blockDim.x) {
+        int v[3] = {tri[k], tri[T + k], tri[2 * T + k]};
+        for (int e = 0; e < 3; ++e) {
+            int a = v[e], b = v[(e + 1) % 3];
+            double dx = xyz[a] - xyz[b], dy = xyz[N + a] - xyz[N + b], dz = xyz[2 * N + a] - xyz[2 * N + b];
+            mn = fmin(mn, sqrt(dx * dx + dy * dy + dz * dz));
+        }
+    }
+    red[threadIdx.x] = mn;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = fmin(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+int grid_for(int64_t n) { return (int)std::min<int64_t>(div_up(n, 256), 152 * 16); }
+
+void apply_filter(Context &c, StepState &s, const double *X, double *Y) {
+    if (s.Pf == 0) {
+        if (X != Y) BEM_CUDA(cudaMemcpyAsync(Y, X, 4 * c.N * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+        return;
+    }
+    k_filter_apply<<<(unsigned)c.M, 256, (size_t)s.Pf * 4 * sizeof(double), c.stream>>>(
+        c.N, s.voff.p, s.shape_of.p, s.g_off.p, s.Pf, s.G.p, s.Gp.p, X, Y);
+    BEM_LAUNCH_CHECK();
+}
+
+// f = filtered right-hand side at state y (both [4N]), time t. Updates s.q.
+void rhs(Context &c, StepState &s, const double *y, double t, double *f, bem_step_stats &st) {
+    const int64_t N = c.N;
+    apply_filter(c, s, y, s.yf.p);
+    BEM_CUDA(cudaMemcpyAsync(c.xyz.p, s.yf.p, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    build_all(c);
+    st.mvps += 1;  // the 4-RHS diagonal product
+    int it = 0;
+    double rr = 0.0;
+    try {
+        solve_internal(c, s.yf.p + 3 * N, s.q.p, &it, &rr);
+    } catch (const Error &e) {
+        if (e.code != BEM_ERR_NOCONV) throw;
+        st.nonconverged += 1;
+        it = c.stats.last_iters;
+        rr = c.stats.last_relres;
+    }
+    st.gmres_iters += it;
+    st.mvps += c.stats.last_mvps + 1;  // GMRES products plus the right-hand side
+    st.max_relres = std::max(st.max_relres, rr);
+    st.rhs_calls += 1;
+    PhaseScope ps(c, PH_GEOMETRY);
+    const int tb = 256;
+    s.vt.resize(3 * N);
+    s.H.resize(N);
+    k_tangential<<<div_up(N, tb), tb, 0, c.stream>>>(N, c.T, s.yf.p, s.yf.p + 3 * N, c.tri.p, c.v2t_off.p, c.v2t.p,
+                                                      c.s.p, c.nrm.p, s.vt.p);
+    BEM_LAUNCH_CHECK();
+    DevBuf<int> bad;
+    bad.resize(1);
+    BEM_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), c.stream));
+    k_curvature<<<div_up(N, tb), tb, 0, c.stream>>>(N, s.yf.p, c.nrm.p, s.nbr5.p, s.H.p, bad.p);
+    BEM_LAUNCH_CHECK();
+    k_volumes<<<(unsigned)c.M, 256, 0, c.stream>>>(N, c.T, s.toff.p, c.tri.p, s.yf.p, s.V.p);
+    BEM_LAUNCH_CHECK();
+    k_pressure<<<div_up(c.M, tb), tb, 0, c.stream>>>((int)c.M, s.V.p, s.V0.p, s.a0.p, s.sp.sigma, s.sp.kappa, s.pg.p);
+    BEM_LAUNCH_CHECK();
+    double F = 1.0 - s.sp.pa * sin(s.sp.omega * t);
+    k_assemble<<<div_up(N, tb), tb, 0, c.stream>>>(N, s.q.p, c.nrm.p, s.vt.p, s.H.p, s.pg.p, s.bub_of.p, s.sp.sigma,
+                                                    F, f);
+    BEM_LAUNCH_CHECK();
+    apply_filter(c, s, f, f);
+    int hb = 0;
+    BEM_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    BEM_CUDA(cudaStreamSynchronize(c.stream));
+    if (hb) fail(BEM_ERR_MESH, "degenerate five-neighbour curvature fit");
+}
+
+}  // namespace
+
+void step_init(Context &c, const double *phi0_dev, const double *q0_dev, const bem_step_params &sp) {
+    if (!c.mesh_ok) fail(BEM_ERR_NOT_BUILT, "no mesh uploaded");
+    if (sp.pf < 0 || sp.pf > 11) fail(BEM_ERR_ARG, "pf must be in 0..11");
+    if (!(sp.pa > 0.0) && !(sp.dt > 0.0)) fail(BEM_ERR_ARG, "pa must be > 0 unless dt is given");
+    StepState &s = state_of(c);
+    const int64_t N = c.N, M = c.M;
+    cudaStream_t st = c.stream;
+    const int tb = 256;
+    s.sp = sp;
+    s.t = 0.0;
+    s.steps = 0;
+    s.nhist = 0;
+    for (int i = 0; i < 5; ++i) s.order[i] = i;
+    for (auto *b : {&s.y, &s.k1, &s.k2, &s.k3, &s.k4, &s.ytmp, &s.yf, &s.f}) b->resize(4 * N);
+    s.hist.resize(5 * 4 * N);
+    s.q.resize(N);
+    if (q0_dev) BEM_CUDA(cudaMemcpyAsync(s.q.p, q0_dev, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    else BEM_CUDA(cudaMemsetAsync(s.q.p, 0, N * sizeof(double), st));
+    BEM_CUDA(cudaMemcpyAsync(s.y.p, c.xyz.p, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    BEM_CUDA(cudaMemcpyAsync(s.y.p + 3 * N, phi0_dev, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    s.voff.resize(M + 1);
+    s.toff.resize(M + 1);
+    BEM_CUDA(cudaMemcpyAsync(s.voff.p, c.vert_off.data(), (M + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    BEM_CUDA(cudaMemcpyAsync(s.toff.p, c.tri_off.data(), (M + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    s.bub_of.resize(N);
+    k_bubble_of<<<(unsigned)M, 256, 0, st>>>((int)M, s.voff.p, s.bub_of.p);
+    BEM_LAUNCH_CHECK();
+    // five-neighbour lists
+    DevBuf<int> bad;
+    bad.resize(1);
+    BEM_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+    s.nbr5.resize(5 * N);
+    k_nbr5<<<div_up(N, tb), tb, 0, st>>>(N, c.T, c.tri.p, c.v2t_off.p, c.v2t.p, s.nbr5.p, bad.p);
+    BEM_LAUNCH_CHECK();
+    // V_m0, a_m0 of the initial mesh
+    s.V.resize(M);
+    s.V0.resize(M);
+    s.a0.resize(M);
+    s.pg.resize(M);
+    k_volumes<<<(unsigned)M, 256, 0, st>>>(N, c.T, s.toff.p, c.tri.p, c.xyz.p, s.V.p);
+    BEM_LAUNCH_CHECK();
+    k_init_bubbles<<<div_up(M, tb), tb, 0, st>>>((int)M, s.V.p, s.V0.p, s.a0.p);
+    BEM_LAUNCH_CHECK();
+    // step size, Eq. (3.12)
+    if (sp.dt > 0.0) {
+        s.dt = sp.dt;
+    } else {
+        int nb = std::min<int64_t>(div_up(c.T, tb), 1024);
+        DevBuf<double> part;
+        part.resize(nb);
+        k_min_edge<<<nb, tb, 0, st>>>(c.T, N, c.tri.p, c.xyz.p, part.p);
+        BEM_LAUNCH_CHECK();
+        std::vector<double> h(nb);
+        BEM_CUDA(cudaMemcpyAsync(h.data(), part.p, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+        BEM_CUDA(cudaStreamSynchronize(st));
+        double mn = *std::min_element(h.begin(), h.end());
+        s.dt = sp.courant * mn / std::sqrt(sp.pa);
+    }
+    // shape filters: one per distinct set of unit directions from the bubble centroid
+    s.Pf = sp.pf * sp.pf;
+    if (sp.pf > 0) {
+        std::vector<double> hx(3 * N);
+        BEM_CUDA(cudaMemcpyAsync(hx.data(), c.xyz.p, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, st));
+        BEM_CUDA(cudaStreamSynchronize(st));
+        struct Shape {
+            int64_t rep;
+            int nd;
+            double cx, cy, cz;
+        };
+        std::vector<Shape> shapes;
+        std::vector<int32_t> shape_of(M);
+        auto dir = [&](int64_t j, double cx, double cy, double cz, double *d) {
+            d[0] = hx[j] - cx;
+            d[1] = hx[N + j] - cy;
+            d[2] = hx[2 * N + j] - cz;
+            double l = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            for (int k = 0; k < 3; ++k) d[k] /= l;
+        };
+        for (int64_t m = 0; m < M; ++m) {
+            int64_t a = c.vert_off[m], b = c.vert_off[m + 1];
+            int nd = (int)(b - a);
+            double cx = 0, cy = 0, cz = 0;
+            for (int64_t j = a; j < b; ++j) {
+                cx += hx[j];
+                cy += hx[N + j];
+                cz += hx[2 * N + j];
+            }
+            cx /= nd;
+            cy /= nd;
+            cz /= nd;
+            int found = -1;
+            for (size_t k = 0; k < shapes.size() && found < 0; ++k) {
+                const Shape &sh = shapes[k];
+                if (sh.nd != nd) continue;
+                int64_t ra = c.vert_off[sh.rep];
+                bool same = true;
+                for (int i = 0; i < nd && same; ++i) {
+                    double d1[3], d2[3];
+                    dir(a + i, cx, cy, cz, d1);
+                    dir(ra + i, sh.cx, sh.cy, sh.cz, d2);
+                    for (int k2 = 0; k2 < 3; ++k2) same &= std::fabs(d1[k2] - d2[k2]) < 1e-9;
+                }
+                if (same) found = (int)k;
+            }
+            if (found < 0) {
+                if (nd < s.Pf) fail(BEM_ERR_MESH, "bubble with fewer vertices than filter coefficients");
+                shapes.push_back({m, nd, cx, cy, cz});
+                found = (int)shapes.size() - 1;
+            }
+            shape_of[m] = found;
+        }
+        std::vector<int64_t> goff(shapes.size() + 1, 0);
+        for (size_t k = 0; k < shapes.size(); ++k) goff[k + 1] = goff[k] + (int64_t)shapes[k].nd * s.Pf;
+        s.G.resize(goff.back());
+        s.Gp.resize(goff.back());
+        DevBuf<double> scratch, A;
+        int ndmax = 0;
+        for (auto &sh : shapes) ndmax = std::max(ndmax, sh.nd);
+        scratch.resize((size_t)ndmax * s.Pf);
+        A.resize((size_t)s.Pf * s.Pf);
+        for (size_t k = 0; k < shapes.size(); ++k) {
+            const Shape &sh = shapes[k];
+            k_filter_G<<<div_up(sh.nd, 128), 128, 0, st>>>(sh.nd, c.xyz.p, N, c.vert_off[sh.rep], sh.cx, sh.cy, sh.cz,
+                                                           sp.pf, s.G.p + goff[k], scratch.p);
+            BEM_LAUNCH_CHECK();
+            k_filter_pinv<<<1, 256, 0, st>>>(sh.nd, s.Pf, s.G.p + goff[k], A.p, s.Gp.p + goff[k], bad.p);
+            BEM_LAUNCH_CHECK();
+        }
+        s.shape_of.resize(M);
+        s.g_off.resize(shapes.size());
+        BEM_CUDA(cudaMemcpyAsync(s.shape_of.p, shape_of.data(), M * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        BEM_CUDA(cudaMemcpyAsync(s.g_off.p, goff.data(), shapes.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        BEM_CUDA(cudaStreamSynchronize(st));
+    }
+    int hb = 0;
+    BEM_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BEM_CUDA(cudaStreamSynchronize(st));
+    if (hb & 1) fail(BEM_ERR_MESH, "vertex with fewer than five neighbours");
+    if (hb & 4) fail(BEM_ERR_MESH, "singular shape-filter normal matrix");
+    s.ready = true;
+}
+
+void step_advance(Context &c, bem_step_stats &st) {
+    StepState &s = state_of(c);
+    if (!s.ready) fail(BEM_ERR_NOT_BUILT, "bem_step_init has not been called");
+    const int64_t n4 = 4 * c.N;
+    const double dt = s.dt, t = s.t;
+    cudaStream_t str = c.stream;
+    const int g = grid_for(n4);
+    std::memset(&st, 0, sizeof(st));
+    auto slot = [&](int i) { return s.hist.p + (size_t)s.order[i] * n4; };
+    if (s.nhist < 5) {
+        rhs(c, s, s.y.p, t, s.k1.p, st);
+        k_axpy4<<<g, 256, 0, str>>>(n4, 0.5 * dt, s.k1.p, s.y.p, s.ytmp.p);
+        BEM_LAUNCH_CHECK();
+        rhs(c, s, s.ytmp.p, t + 0.5 * dt, s.k2.p, st);
+        k_axpy4<<<g, 256, 0, str>>>(n4, 0.5 * dt, s.k2.p, s.y.p, s.ytmp.p);
+        BEM_LAUNCH_CHECK();
+        rhs(c, s, s.ytmp.p, t + 0.5 * dt, s.k3.p, st);
+        k_axpy4<<<g, 256, 0, str>>>(n4, dt, s.k3.p, s.y.p, s.ytmp.p);
+        BEM_LAUNCH_CHECK();
+        rhs(c, s, s.ytmp.p, t + dt, s.k4.p, st);
+        // push k1 (the RHS at the step start) to the history
+        int last = s.order[4];
+        for (int i = 4; i > 0; --i) s.order[i] = s.order[i - 1];
+        s.order[0] = last;
+        BEM_CUDA(cudaMemcpyAsync(slot(0), s.k1.p, n4 * sizeof(double), cudaMemcpyDeviceToDevice, str));
+        s.nhist = std::min(5, s.nhist + 1);
+        k_rk4_combine<<<g, 256, 0, str>>>(n4, dt, s.k1.p, s.k2.p, s.k3.p, s.k4.p, s.y.p);
+        BEM_LAUNCH_CHECK();
+    } else {
+        rhs(c, s, s.y.p, t, s.f.p, st);
+        static const double b[6] = {4277.0 / 1440.0, -7923.0 / 1440.0, 9982.0 / 1440.0,
+                                    -7298.0 / 1440.0, 2877.0 / 1440.0, -475.0 / 1440.0};
+        Six six;
+        six.f[0] = s.f.p;
+        for (int i = 0; i < 5; ++i) six.f[i + 1] = slot(i);
+        for (int i = 0; i < 6; ++i) six.b[i] = b[i];
+        k_ab6<<<g, 256, 0, str>>>(n4, dt, six, s.y.p);
+        BEM_LAUNCH_CHECK();
+        int last = s.order[4];
+        for (int i = 4; i > 0; --i) s.order[i] = s.order[i - 1];
+        s.order[0] = last;
+        BEM_CUDA(cudaMemcpyAsync(slot(0), s.f.p, n4 * sizeof(double), cudaMemcpyDeviceToDevice, str));
+    }
+    s.t = t + dt;
+    s.steps += 1;
+    st.t = s.t;
+    st.dt = dt;
+    st.steps = s.steps;
+    s.last = st;
+    BEM_CUDA(cudaStreamSynchronize(str));
+}
+
+void step_get_state(Context &c, double *xyz, double *phi, double *q, double *t) {
+    StepState &s = state_of(c);
+    if (!s.ready) fail(BEM_ERR_NOT_BUILT, "bem_step_init has not been called");
+    const int64_t N = c.N;
+    auto cp = [&](double *dst, const double *src, int64_t n) {
+        if (!dst) return;
+        auto k = is_device_ptr(c, dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        BEM_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double), k, c.stream));
+    };
+    cp(xyz, s.y.p, 3 * N);
+    cp(phi, s.y.p + 3 * N, N);
+    cp(q, s.q.p, N);
+    BEM_CUDA(cudaStreamSynchronize(c.stream));
+    if (t) *t = s.t;
+}
+
+void step_free(StepState *s) { delete s; }
+
+}  // namespace bem

@@ -438,6 +438,14 @@ __global__ void k_gather_i32(int64_t n, const int32_t *__restrict__ idx, const T
     if (i < n) out[i] = in[idx[i]];
 }
 
+__global__ void k_copy_keys(int64_t n, const int32_t *__restrict__ tgt, uint32_t *__restrict__ key,
+                            int32_t *__restrict__ cnt) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    key[i] = (uint32_t)tgt[i];
+    atomicAdd(&cnt[tgt[i]], 1);
+}
+
 __global__ void k_hist_small(int64_t n, const uint32_t *__restrict__ k, int nbins, int32_t *__restrict__ h) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) atomicAdd(&h[k[i]], 1);
@@ -709,7 +717,33 @@ void build_tree(Context &c) {
         for (int k = 0; k < 8; ++k) t.up_class_off[l][k + 1] = t.up_class_off[l][k] + hh[k];
     }
 
-    // 8. sorted point data
+    // 8. target-major CSR of the M2L and child->parent pairs (stable: ascending pair index)
+    auto target_csr = [&](const int32_t *tgt, int64_t np, DevBuf<int32_t> &off, DevBuf<int32_t> &by) {
+        off.resize((size_t)t.nbox + 1);
+        by.resize(np > 0 ? np : 1);
+        DevBuf<int32_t> cnt2;
+        cnt2.resize((size_t)t.nbox + 1);
+        BEM_CUDA(cudaMemsetAsync(cnt2.p, 0, ((size_t)t.nbox + 1) * sizeof(int32_t), st));
+        if (np > 0) {
+            DevBuf<uint32_t> k, ktmp2;
+            DevBuf<int32_t> vtmp2;
+            k.resize(np);
+            ktmp2.resize(np);
+            vtmp2.resize(np);
+            k_copy_keys<<<div_up(np, tb), tb, 0, st>>>(np, tgt, k.p, cnt2.p);
+            BEM_LAUNCH_CHECK();
+            k_iota<<<div_up(np, tb), tb, 0, st>>>(np, by.p);
+            BEM_LAUNCH_CHECK();
+            int bits = 1;
+            while ((1ll << bits) <= (long long)t.nbox) ++bits;
+            radix_sort_u32(k.p, by.p, np, bits, ktmp2.p, vtmp2.p, st);
+        }
+        exclusive_scan_i32(cnt2.p, off.p, (int64_t)t.nbox + 1, nullptr, st);
+    };
+    target_csr(t.m2l_tgt.p, nm2l, t.m2l_tgt_off, t.m2l_by_tgt);
+    target_csr(t.up_parent.p, nup, t.up_par_off, t.up_by_par);
+
+    // 9. sorted point data
     t.loc64.resize(3 * N);
     t.loc32.resize(3 * N);
     t.nrm64.resize(3 * N);

@@ -67,6 +67,9 @@ def test_struct_layouts_match_header():
     # int32 x 8 + double = 40 bytes; stats: 4 x int64 + 4 x int32 + 2 x double + int64 = 72 bytes
     assert ctypes.sizeof(bem.bem_params) == 40
     assert ctypes.sizeof(bem.bem_stats) == 72
+    assert ctypes.sizeof(bem.bem_step_params) == 56 and ctypes.sizeof(bem.bem_step_stats) == 48
+    sp = bem.bem_step_params_default()
+    assert sp.pf == 6 and sp.courant == 0.1 and sp.kappa == 1.4
     assert [bem.bem_phase_name(i) for i in range(bem.BEM_NUM_PHASES)][6] == "m2l"
 
 

@@ -198,3 +198,35 @@ def test_single_bubble_l6_p_sweep(l6_reference, prec):
     if prec == 0:
         assert errs[16] < 1e-6
     assert errs[14] < 1e-5
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_fmm_apply_is_deterministic(prec):
+    """Translations are summed per target in a fixed order (no floating-point atomics), so
+    repeated products are bit-identical; GMRES relies on a fixed operator."""
+    bem = _bem()
+    mesh = small_cluster(20, 3, seed=11)
+    ctx = make_ctx(mesh, mvp=bem.BEM_MVP_FMM, precision=prec, p_fmm=10, leaf_target=32)
+    x = dev(np.random.Generator(np.random.PCG64(9)).standard_normal(mesh.n))
+    outs = []
+    for _ in range(3):
+        o = torch.zeros(mesh.n, dtype=torch.float64, device="cuda")
+        ctx.apply(1.0, x, 0.5, x, o)
+        outs.append(o.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    ctx.close()
+
+
+def test_residual_history_and_mvp_count():
+    bem = _bem()
+    mesh, phi = synth.workload_single_sphere()
+    ctx = make_ctx(mesh, mvp=bem.BEM_MVP_FMM, precision=bem.BEM_PREC_FP64, p_fmm=16, gmres_tol=1e-9,
+                   fixed_level=3)
+    q = torch.zeros(mesh.n, dtype=torch.float64, device="cuda")
+    it, rr = ctx.solve(dev(phi), q)
+    h = bem.bem_get_residual_history(ctx.ctx)
+    assert len(h) == it + 2  # initial residual, one estimate per iteration, final true residual
+    assert h[0] == pytest.approx(1.0) and h[-1] == pytest.approx(rr) and rr <= 1e-9
+    assert all(a >= b for a, b in zip(h[1:-2], h[2:-1]))  # GMRES estimates never increase
+    assert ctx.stats()["last_mvps"] == it + 2
+    ctx.close()

@@ -1,0 +1,86 @@
+"""Parity of the device time step (bem_step) with the CPU oracle's time step, and a spherical
+bubble against the Rayleigh-Plesset equation (Section 4.1)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import rp
+from oracle import timestep as ts
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _bem():
+    from paper_1905_01341_gb300 import bem
+
+    return bem
+
+
+def two_bubbles():
+    radii = np.array([1.0, 0.8])
+    centres = np.array([[0.0, 0.0, 0.0], [2.6, 0.4, -0.3]])
+    mesh = synth.cluster(2, radii, centres)
+    rng = np.random.Generator(np.random.PCG64(4))
+    phi = synth.cluster_potential(mesh, 3, 0.05, rng) - 1.0
+    return mesh, phi
+
+
+@pytest.mark.parametrize("pf", [4, 0])
+def test_time_steps_match_oracle(pf):
+    """Seven steps (five RK4 warm-up steps, then AB6) of a two-bubble system: FP64 direct
+    products and GMRES to 1e-12 on both sides; states agree to 1e-8 relative."""
+    bem = _bem()
+    mesh, phi = two_bubbles()
+    phys = ts.Physics(pf=pf, gmres_tol=1e-12, pa=0.8)
+    sysm = ts.BubbleSystem(mesh.xyz, mesh.tri, mesh.vert_off, mesh.tri_off, phys)
+    st = ts.State(xyz=mesh.xyz.copy(), phi=phi.copy())
+    ctx = bem.BemContext(mvp=bem.BEM_MVP_DIRECT, precision=bem.BEM_PREC_FP64, gmres_tol=1e-12)
+    ctx.upload_mesh(mesh)
+    sp = bem.bem_step_params_default(pf=pf, pa=0.8)
+    bem.bem_step_init(ctx.ctx, phi, sp)
+    xyz = np.zeros(3 * mesh.n)
+    ph = np.zeros(mesh.n)
+    for k in range(7):
+        st = sysm.step(st)
+        info = bem.bem_step(ctx.ctx)
+        t = bem.bem_step_get_state(ctx.ctx, xyz, ph)
+        assert info["rhs_calls"] == (4 if k < 5 else 1)
+        assert t == pytest.approx(st.t, rel=1e-14)
+        assert abs(info["dt"] - sysm.dt) < 1e-15
+        disp_ref = st.xyz - mesh.xyz
+        disp = xyz.reshape(3, -1).T - mesh.xyz
+        assert np.linalg.norm(disp - disp_ref) < 1e-8 * np.linalg.norm(disp_ref) + 1e-13
+        assert np.linalg.norm(ph - st.phi) < 1e-8 * np.linalg.norm(st.phi)
+    ctx.close()
+
+
+def test_spherical_bubble_against_rayleigh_plesset_mixed_fmm():
+    """Single spherical bubble (642 vertices) under Pa = p0 at 200 kHz, through the mixed FMM
+    path: the volume-equivalent radius follows Eq. (4.1) within 2% over 0.4 periods."""
+    bem = _bem()
+    mesh = synth.sphere_bubble(3, 1.0)
+    ctx = bem.BemContext(mvp=bem.BEM_MVP_FMM, precision=bem.BEM_PREC_MIXED, p_fmm=12, gmres_tol=1e-7,
+                         fixed_level=3)
+    ctx.upload_mesh(mesh)
+    sp = bem.bem_step_params_default(pf=6)
+    bem.bem_step_init(ctx.ctx, np.zeros(mesh.n), sp)
+    T = 2 * math.pi / sp.omega
+    xyz = np.zeros(3 * mesh.n)
+    ts_, rad = [0.0], [1.0]
+    V0 = ts.bubble_volumes(mesh.xyz, mesh.tri, mesh.tri_off)[0]
+    t = 0.0
+    while t < 0.4 * T:
+        info = bem.bem_step(ctx.ctx)
+        assert info["nonconverged"] == 0
+        t = bem.bem_step_get_state(ctx.ctx, xyz)
+        V = ts.bubble_volumes(xyz.reshape(3, -1).T, mesh.tri, mesh.tri_off)[0]
+        ts_.append(t)
+        rad.append((V / V0) ** (1.0 / 3.0))
+    a_rp, _ = rp.rayleigh_plesset(np.array(ts_), sp.sigma, sp.kappa, sp.pa, sp.omega)
+    assert rad[-1] > 1.2
+    assert np.max(np.abs(np.array(rad) - a_rp)) < 0.02 * a_rp.max()
+    ctx.close()
