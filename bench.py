@@ -38,14 +38,21 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cluster", choices=["cluster", "batched", "learned"],
+                    help="cluster: the 5000-bubble headline; batched: 64 uneven independent clusters in "
+                         "one launch per phase; learned: record/train/use the learned GMRES guess")
+    ap.add_argument("--learn-bubbles", type=int, default=1000)
+    ap.add_argument("--learn-steps", type=int, default=100, help="recorded steps, then as many compared")
     ap.add_argument("--bubbles", type=int, default=5000)
     ap.add_argument("--level", type=int, default=3)
     ap.add_argument("--p", type=int, default=14)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--leaf", type=int, default=64)
+    ap.add_argument("--tree-level", type=int, default=0, help="fixed octree depth (0 = from --leaf)")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--maxit", type=int, default=400)
     ap.add_argument("--restart", type=int, default=100)
+    ap.add_argument("--precond", type=int, default=0, help="1 = right Jacobi preconditioning of GMRES")
     ap.add_argument("--pa", type=float, default=0.5, help="acoustic amplitude Pa/p0")
     ap.add_argument("--pf", type=int, default=6, help="shape-filter bandwidth")
     ap.add_argument("--fp64-compare", type=int, default=1, help="also time FP64 right-hand sides (0 = skip)")
@@ -232,7 +239,8 @@ def run_ours(args):
 
     def make_ctx(precision):
         c = bem.BemContext(stream=stream, p_fmm=args.p, precision=precision, leaf_target=args.leaf,
-                           gmres_tol=args.tol, gmres_maxit=args.maxit, gmres_restart=args.restart)
+                           fixed_level=args.tree_level, gmres_tol=args.tol, gmres_maxit=args.maxit,
+                           gmres_restart=args.restart, gmres_precond=args.precond)
         return c
 
     ctx = make_ctx(prec)
@@ -331,7 +339,7 @@ def run_ours(args):
         "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if prec == bem.BEM_PREC_MIXED else "f64", "data": "synthetic",
         "config": {"workload": workload_name(args, mesh), "p_fmm": args.p, "precision": args.precision,
-                   "leaf_target": args.leaf, "gmres_tol": args.tol, "scheme": "AB6 after %d RK4 warm-up steps" % 5,
+                   "leaf_target": args.leaf, "gmres_tol": args.tol, "gmres_precond": args.precond, "scheme": "AB6 after %d RK4 warm-up steps" % 5,
                    "pa": args.pa, "pf": args.pf, "dt": infos[-1]["dt"], "levels": st["levels"],
                    "leaves": st["leaves"], "l2": "inputs and working set > L2 (no flush)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -357,7 +365,7 @@ def run_ours(args):
         qs = torch.empty(N, dtype=torch.float64, device=dev)
         bem.bem_step_get_state(ctx.ctx, xs, ph, qs)
         ctx64 = make_ctx(bem.BEM_PREC_FP64)
-        ctx64.upload(xs, tri, voff, toff)
+        ctx64.upload(xs.view(3, N), tri, voff, toff)
         bem.bem_step_init(ctx64.ctx, ph, sp, q0=qs)
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
@@ -396,8 +404,146 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
 
 
+def run_batched(args):
+    """64 independent clusters of uneven size stepped together: one octree per cluster (cluster
+    id in the key), one launch per phase for all of them, one GMRES over the block-diagonal
+    system. Every cluster's step completes with the batch, so its latency is the batch step
+    time; a sample of clusters is also stepped alone for the unbatched latency."""
+    import torch
+    import synth
+    from paper_1905_01341_gb300 import bem, build
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    cl = synth.workload_uneven_clusters(64, seed=5)
+    mesh, phi, boff = synth.concat_meshes([c[0] for c in cl], [c[1] for c in cl])
+    prec = bem.BEM_PREC_MIXED if args.precision == "mixed" else bem.BEM_PREC_FP64
+
+    def stepper(m, ph, clusters=None):
+        c = bem.BemContext(stream=stream, p_fmm=args.p, precision=prec, leaf_target=args.leaf, gmres_tol=args.tol,
+                           gmres_maxit=args.maxit, gmres_restart=args.restart, gmres_precond=args.precond)
+        c.upload_mesh(m)
+        if clusters is not None:
+            bem.bem_mesh_set_clusters(c.ctx, len(clusters) - 1, clusters)
+        bem.bem_step_init(c.ctx, ph, bem.bem_step_params_default(pa=args.pa, pf=args.pf))
+        return c
+
+    ctx = stepper(mesh, phi, boff)
+    for _ in range(args.warmup):
+        bem.bem_step(ctx.ctx)
+    torch.cuda.synchronize()
+    st0 = ctx.stats()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = [bem.bem_step(ctx.ctx) for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    st1 = ctx.stats()
+    batch_s = e0.elapsed_time(e1) / 1e3 / args.steps
+    ctx.close()
+    # unbatched latency of a few clusters (smallest, median, largest)
+    order = np.argsort([c[0].n for c in cl])
+    alone = {}
+    for k in (order[0], order[len(order) // 2], order[-1]):
+        m, ph = cl[k]
+        c = stepper(m, ph)
+        for _ in range(args.warmup):
+            bem.bem_step(c.ctx)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            bem.bem_step(c.ctx)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        alone[int(m.n)] = f0.elapsed_time(f1) / 1e3 / args.steps
+        c.close()
+    seq_estimate = None
+    line = {
+        "metric": "batched step of 64 independent uneven clusters", "workload": "batched",
+        "value": batch_s, "unit": "s/step", "higher_is_better": False, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "dtype": "f32+f64" if prec == bem.BEM_PREC_MIXED else "f64", "data": "synthetic",
+        "config": {"workload": "64 clusters, 1-200 bubbles each, icosphere levels 2-4, seed 5 (%d unknowns, %d bubbles)"
+                               % (mesh.n, mesh.m), "p_fmm": args.p, "gmres_tol": args.tol},
+        "aggregate_unknown_steps_per_s": mesh.n / batch_s,
+        "per_cluster_latency_s": {"p50": batch_s, "p99": batch_s,
+                                  "note": "every cluster completes with its batch step"},
+        "alone_latency_s_by_size": alone,
+        "step": {"gmres_iters": sum(i["gmres_iters"] for i in infos) / args.steps,
+                 "max_relres": max(i["max_relres"] for i in infos)},
+        "gpu_launches": int((st1["n_launches"] - st0["n_launches"]) / args.steps),
+    }
+    del seq_estimate
+    print(json.dumps(line), flush=True)
+
+
+def run_learned(args):
+    """Learned GMRES initial guess: record the solves of the first steps, train the network on
+    the device, then step on with the learned guess while also solving from the previous-step
+    q (the fallback) for the comparison."""
+    import torch
+    import synth
+    from paper_1905_01341_gb300 import bem, build
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    rng = np.random.Generator(np.random.PCG64(4))
+    nb = args.learn_bubbles
+    radii = np.exp(0.3 * rng.standard_normal(nb))
+    centres = synth._place_centres(radii, 4.0 * nb ** (1 / 3), 0.5, rng)
+    levels = rng.choice(np.array([3, 4]), size=nb)
+    mesh = synth.cluster(levels, radii, centres)
+    phi = synth.cluster_potential(mesh, 6, 0.1, rng)
+    prec = bem.BEM_PREC_MIXED if args.precision == "mixed" else bem.BEM_PREC_FP64
+    ctx = bem.BemContext(stream=stream, p_fmm=args.p, precision=prec, leaf_target=args.leaf, gmres_tol=args.tol,
+                         gmres_maxit=args.maxit, gmres_restart=args.restart, gmres_precond=args.precond)
+    ctx.upload_mesh(mesh)
+    bem.bem_step_init(ctx.ctx, phi, bem.bem_step_params_default(pa=args.pa, pf=args.pf))
+    bem.bem_mlp_init(ctx.ctx, hidden=256, lmax=10, seed=1)
+    bem.bem_mlp_set_mode(ctx.ctx, record=True)
+    t0 = time.perf_counter()
+    for _ in range(args.learn_steps):
+        bem.bem_step(ctx.ctx)
+    t_rec = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    l0 = bem.bem_mlp_train(ctx.ctx, epochs=1, batch=1024, lr=1e-3)
+    l1 = bem.bem_mlp_train(ctx.ctx, epochs=30, batch=1024, lr=1e-3)
+    t_train = time.perf_counter() - t0
+    bem.bem_mlp_set_mode(ctx.ctx, record=False, use_guess=True, compare=True)
+    for _ in range(args.learn_steps):
+        bem.bem_step(ctx.ctx)
+    info = bem.bem_mlp_info(ctx.ctx)
+    n = max(1, info["compared_solves"])
+    line = {
+        "metric": "GMRES iterations per solve, learned guess vs previous-step guess", "workload": "learned",
+        "value": info["iters_guess"] / n, "unit": "iterations/solve", "higher_is_better": False,
+        "fallback_value": info["iters_fallback"] / n,
+        "initial_relres": {"learned": info["res0_guess"] / n, "previous_step": info["res0_fallback"] / n},
+        "train": {"samples": info["samples"], "loss_first_epoch": l0, "loss_last_epoch": l1, "seconds": t_train,
+                  "params": info["num_params"], "dims": info["dims"]},
+        "record_seconds": t_rec, "compared_solves": info["compared_solves"],
+        "config": {"workload": "%d bubbles, icosphere level 3 or 4, seed 4 (%d unknowns)" % (nb, mesh.n),
+                   "steps": "%d recorded + %d compared" % (args.learn_steps, args.learn_steps),
+                   "p_fmm": args.p, "gmres_tol": args.tol},
+        "data": "synthetic",
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
+    if args.impl == "ours" and args.workload == "batched":
+        run_batched(args)
+        return
+    if args.impl == "ours" and args.workload == "learned":
+        run_learned(args)
+        return
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -77,6 +77,14 @@ typedef struct {
     int32_t mvp;            /* bem_mvp_kind. Default BEM_MVP_FMM.                              */
     int32_t diag_precision; /* precision of the 4-RHS product that feeds Eqs. (s3)/(s5);
                                -1 = same as `precision`. Default -1.                           */
+    int32_t m2l_tensor_cores; /* 1: mixed-precision M2L on the tensor cores (3-pass TF32 split,
+                               FP32 accumulation) when p_fmm^2 is a multiple of 4 and <= 256;
+                               0: FP32 CUDA cores. Default 1.                                  */
+    int32_t gmres_precond;  /* 0: unpreconditioned GMRES, as in the paper (Section 3.8);
+                               1: right Jacobi preconditioning x = D^-1 y with D = diag(L_ii)
+                               (same solution and true-residual test; removes the spread of
+                               the single layer's scale across bubbles of different radii).
+                               Default 0.                                                      */
     int32_t gmres_maxit;    /* maximum GMRES iterations. Default 100.                          */
     int32_t gmres_restart;  /* restart length; 0 = no restart (= maxit). Default 0.            */
     double gmres_tol;       /* stop when |b - L q| / |b| <= tol (Section 3.8). Default 1e-6.  */
@@ -124,6 +132,21 @@ const char *bem_last_error(const void *ctx);
  * any previous build. Returns BEM_ERR_ARG for bad sizes or offsets. */
 int bem_mesh_upload(void *ctx, int64_t N, const double *xyz, int64_t T, const int32_t *tri,
                     int64_t M, const int64_t *vert_off, const int64_t *tri_off);
+
+/* Independent clusters stepped together (one launch per phase for all of them): after
+ * bem_mesh_upload, group the bubbles into C clusters, cluster c owning bubbles
+ * bubble_off[c]..bubble_off[c+1]-1 (bubble_off[C+1]: 0 .. M, every cluster non-empty,
+ * C <= 256). Each cluster gets its own octree cube (the cluster id sits in the high bits of
+ * the Morton key, depth <= 8 per cluster), no interaction crosses clusters, and the singular
+ * diagonals use each cluster's own sums; the products and solves therefore equal those of the
+ * clusters taken one by one. Invalidates the build; a new bem_mesh_upload resets to one
+ * cluster. */
+int bem_mesh_set_clusters(void *ctx, int64_t C, const int64_t *bubble_off);
+
+/* Section 3.9 (Table 1): upload N free points (SoA xyz[3N]) instead of a mesh, for the FMM's
+ * accuracy study with monopoles. Weights are 1 and there is no singular diagonal, so after
+ * fmm_build, bem_apply(ctx, 1, q, 0, NULL, out) gives out_i = sum_{j != i} q_j / (4 pi |r_i - r_j|). */
+int bem_points_upload(void *ctx, int64_t N, const double *xyz);
 
 /* Replace the vertex coordinates of the uploaded mesh (same N, same triangles), as a
  * time step does (Eq. (3.14)); invalidates the build. */
@@ -205,6 +228,56 @@ int bem_step(void *ctx, bem_step_stats *st);
 
 /* Current state: xyz[3N] (SoA), phi[N], the last q[N] and t. Any pointer may be NULL. */
 int bem_step_get_state(void *ctx, double *xyz, double *phi, double *q, double *t);
+
+/* ------------------------------------------------------------------------------------------
+ * Learned GMRES initial guess. The paper starts each solve from the previous step's q
+ * (Sections 3.5, 3.8); that remains the fallback. Per bubble, the features are the
+ * least-squares real spherical-harmonic coefficients (degree <= lmax, on the bubble's initial
+ * directions, as in the shape filter, Eqs. (3.22)-(3.23)) of phi, of the previous q, and of the
+ * previous q minus the q before it; a multilayer perceptron (3 hidden relu layers) predicts
+ * the change of q's coefficients and the guess is q_prev + G y. Samples are recorded and the
+ * guess is used in the Adams-Bashforth phase of bem_step (one solve per step). Products run on the tensor cores in BF16 with FP32
+ * accumulation; weights keep an FP32 master copy; training is Adam on the mean squared error.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+    int32_t dims[5];          /* layer widths: 3 (lmax+1)^2, hidden, hidden, hidden, (lmax+1)^2 */
+    int32_t reserved;
+    int64_t num_params;       /* weights and biases: W1, b1, ..., W4, b4 (W row-major [out][in]) */
+    int64_t samples;          /* recorded (features, target) rows, one per bubble per solve      */
+    int64_t compared_solves;  /* solves run from both starts (compare mode)                      */
+    int64_t iters_guess;      /* their GMRES iterations from the learned guess                    */
+    int64_t iters_fallback;   /* ... and from q_prev                                              */
+    double res0_guess;        /* summed initial relative residuals from the learned guess         */
+    double res0_fallback;     /* ... and from q_prev                                              */
+} bem_mlp_summary;
+
+/* Create the network (He initialisation from `seed`, output layer scaled by 0.1) after
+ * bem_step_init. hidden: multiple of 16 in 16..256; lmax in 0..10. */
+int bem_mlp_init(void *ctx, int32_t hidden, int32_t lmax, uint64_t seed);
+
+/* record: store (features, c(q) - c(q_prev)) of every bubble at every solve of bem_step;
+ * use_guess: start every solve from the learned guess; compare: with use_guess, also solve from
+ * q_prev (the result of that solve is discarded) and accumulate both iteration counts. */
+int bem_mlp_set_mode(void *ctx, int32_t record, int32_t use_guess, int32_t compare);
+
+/* Adam (lr, beta = 0.9/0.999) over the recorded rows, in minibatches of `batch` rows, for
+ * `epochs` passes; *last_loss = mean loss of the last pass. */
+int bem_mlp_train(void *ctx, int32_t epochs, int32_t batch, double lr, double *last_loss);
+
+/* Loss and gradients for one batch: F[B][dims[0]], T[B][dims[4]] -> *loss,
+ * grads[num_params] in parameter order. */
+int bem_mlp_loss_grad(void *ctx, int32_t B, const double *F, const double *T, double *loss, double *grads);
+
+/* Network output Y[B][dims[4]] for features F[B][dims[0]]. */
+int bem_mlp_forward(void *ctx, int32_t B, const double *F, double *Y);
+
+/* Parameters as one FP64 vector of num_params entries, in parameter order. */
+int bem_mlp_get_params(void *ctx, double *out);
+int bem_mlp_set_params(void *ctx, const double *in);
+
+/* Sizes, sample count and compare-mode counters. */
+int bem_mlp_info(void *ctx, bem_mlp_summary *out);
+
 
 /* Residual history of the last bem_solve: the true relative residual at the start of each
  * GMRES cycle and the estimate |g_{k+1}|/|b| after each iteration, in order; the final entry

@@ -33,11 +33,12 @@ BEM_MVP_DIRECT = 1
 
 EXPORTED = [
     "bem_params_default", "bem_create", "bem_destroy", "bem_set_stream", "bem_last_error",
-    "bem_mesh_upload", "bem_mesh_update_xyz", "fmm_build", "bem_apply", "bem_apply_sl",
+    "bem_mesh_upload", "bem_points_upload", "bem_mesh_set_clusters", "bem_mesh_update_xyz", "fmm_build", "bem_apply", "bem_apply_sl",
     "bem_apply_dl", "bem_rhs", "bem_solve", "bem_get_geometry", "bem_get_stats",
     "bem_reset_stats", "bem_profile_enable", "bem_profile_read", "bem_phase_name",
     "bem_get_residual_history", "bem_step_params_default", "bem_step_init", "bem_step",
-    "bem_step_get_state",
+    "bem_step_get_state", "bem_mlp_init", "bem_mlp_set_mode", "bem_mlp_train",
+    "bem_mlp_loss_grad", "bem_mlp_forward", "bem_mlp_get_params", "bem_mlp_set_params", "bem_mlp_info",
 ]
 
 BEM_NUM_PHASES = 13
@@ -51,6 +52,8 @@ class bem_params(ctypes.Structure):
         ("precision", ctypes.c_int32),
         ("mvp", ctypes.c_int32),
         ("diag_precision", ctypes.c_int32),
+        ("m2l_tensor_cores", ctypes.c_int32),
+        ("gmres_precond", ctypes.c_int32),
         ("gmres_maxit", ctypes.c_int32),
         ("gmres_restart", ctypes.c_int32),
         ("gmres_tol", ctypes.c_double),
@@ -105,6 +108,25 @@ class bem_step_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class bem_mlp_summary(ctypes.Structure):
+    _fields_ = [
+        ("dims", ctypes.c_int32 * 5),
+        ("reserved", ctypes.c_int32),
+        ("num_params", ctypes.c_int64),
+        ("samples", ctypes.c_int64),
+        ("compared_solves", ctypes.c_int64),
+        ("iters_guess", ctypes.c_int64),
+        ("iters_fallback", ctypes.c_int64),
+        ("res0_guess", ctypes.c_double),
+        ("res0_fallback", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "dims"}
+        d["dims"] = list(self.dims)
+        return d
+
+
 class BemError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__("bem status %d: %s" % (code, msg))
@@ -130,6 +152,8 @@ def lib() -> ctypes.CDLL:
             "bem_last_error": ([vp], ctypes.c_char_p),
             "bem_mesh_upload": ([vp, i64, vp, i64, vp, i64, vp, vp], ctypes.c_int),
             "bem_mesh_update_xyz": ([vp, vp], ctypes.c_int),
+            "bem_points_upload": ([vp, i64, vp], ctypes.c_int),
+            "bem_mesh_set_clusters": ([vp, i64, vp], ctypes.c_int),
             "fmm_build": ([vp], ctypes.c_int),
             "bem_apply": ([vp, dbl, vp, dbl, vp, vp], ctypes.c_int),
             "bem_apply_sl": ([vp, vp, vp], ctypes.c_int),
@@ -147,6 +171,14 @@ def lib() -> ctypes.CDLL:
             "bem_step_init": ([vp, vp, vp, ctypes.POINTER(bem_step_params)], ctypes.c_int),
             "bem_step": ([vp, ctypes.POINTER(bem_step_stats)], ctypes.c_int),
             "bem_step_get_state": ([vp, vp, vp, vp, ctypes.POINTER(dbl)], ctypes.c_int),
+            "bem_mlp_init": ([vp, i32, i32, ctypes.c_uint64], ctypes.c_int),
+            "bem_mlp_set_mode": ([vp, i32, i32, i32], ctypes.c_int),
+            "bem_mlp_train": ([vp, i32, i32, dbl, ctypes.POINTER(dbl)], ctypes.c_int),
+            "bem_mlp_loss_grad": ([vp, i32, vp, vp, ctypes.POINTER(dbl), vp], ctypes.c_int),
+            "bem_mlp_forward": ([vp, i32, vp, vp], ctypes.c_int),
+            "bem_mlp_get_params": ([vp, vp], ctypes.c_int),
+            "bem_mlp_set_params": ([vp, vp], ctypes.c_int),
+            "bem_mlp_info": ([vp, ctypes.POINTER(bem_mlp_summary)], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -231,6 +263,14 @@ def bem_mesh_upload(ctx, N, xyz, T, tri, M, vert_off, tri_off) -> None:
                                       _ptr(vert_off, np.int64), _ptr(tri_off, np.int64)))
 
 
+def bem_points_upload(ctx, N, xyz) -> None:
+    _check(ctx, lib().bem_points_upload(ctx, int(N), _ptr(xyz, np.float64)))
+
+
+def bem_mesh_set_clusters(ctx, C, bubble_off) -> None:
+    _check(ctx, lib().bem_mesh_set_clusters(ctx, int(C), _ptr(bubble_off, np.int64)))
+
+
 def bem_mesh_update_xyz(ctx, xyz) -> None:
     _check(ctx, lib().bem_mesh_update_xyz(ctx, _ptr(xyz, np.float64)))
 
@@ -304,6 +344,46 @@ def bem_step_get_state(ctx, xyz=None, phi=None, q=None) -> float:
     _check(ctx, lib().bem_step_get_state(ctx, _ptr(xyz, np.float64), _ptr(phi, np.float64), _ptr(q, np.float64),
                                          ctypes.byref(t)))
     return float(t.value)
+
+
+def bem_mlp_init(ctx, hidden=256, lmax=10, seed=0) -> None:
+    _check(ctx, lib().bem_mlp_init(ctx, int(hidden), int(lmax), int(seed)))
+
+
+def bem_mlp_set_mode(ctx, record=False, use_guess=False, compare=False) -> None:
+    _check(ctx, lib().bem_mlp_set_mode(ctx, int(bool(record)), int(bool(use_guess)), int(bool(compare))))
+
+
+def bem_mlp_train(ctx, epochs, batch, lr) -> float:
+    loss = ctypes.c_double(0.0)
+    _check(ctx, lib().bem_mlp_train(ctx, int(epochs), int(batch), float(lr), ctypes.byref(loss)))
+    return float(loss.value)
+
+
+def bem_mlp_loss_grad(ctx, F, T, grads):
+    """F [B, d_in], T [B, d_out] (float64); grads [num_params] receives the gradient."""
+    loss = ctypes.c_double(0.0)
+    _check(ctx, lib().bem_mlp_loss_grad(ctx, int(F.shape[0]), _ptr(F, np.float64), _ptr(T, np.float64),
+                                        ctypes.byref(loss), _ptr(grads, np.float64)))
+    return float(loss.value)
+
+
+def bem_mlp_forward(ctx, F, Y) -> None:
+    _check(ctx, lib().bem_mlp_forward(ctx, int(F.shape[0]), _ptr(F, np.float64), _ptr(Y, np.float64)))
+
+
+def bem_mlp_get_params(ctx, out) -> None:
+    _check(ctx, lib().bem_mlp_get_params(ctx, _ptr(out, np.float64)))
+
+
+def bem_mlp_set_params(ctx, params) -> None:
+    _check(ctx, lib().bem_mlp_set_params(ctx, _ptr(params, np.float64)))
+
+
+def bem_mlp_info(ctx) -> dict:
+    st = bem_mlp_summary()
+    _check(ctx, lib().bem_mlp_info(ctx, ctypes.byref(st)))
+    return st.as_dict()
 
 
 def bem_get_stats(ctx) -> dict:

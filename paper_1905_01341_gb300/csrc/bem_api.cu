@@ -14,6 +14,7 @@ long long g_launch_count = 0;
 Context::~Context() {
     for (auto *p : up_chunks) delete p;
     step_free(step);
+    mlp_free(mlp);
 }
 
 bool is_device_ptr(const Context &c, const void *p) {
@@ -156,7 +157,9 @@ void check_params(const bem_params &p) {
     if (p.diag_precision != -1 && p.diag_precision != BEM_PREC_FP64 && p.diag_precision != BEM_PREC_MIXED)
         fail(BEM_ERR_ARG, "bad diag_precision");
     if (p.mvp != BEM_MVP_FMM && p.mvp != BEM_MVP_DIRECT) fail(BEM_ERR_ARG, "bad mvp kind");
+    if (p.m2l_tensor_cores != 0 && p.m2l_tensor_cores != 1) fail(BEM_ERR_ARG, "m2l_tensor_cores must be 0 or 1");
     if (p.gmres_maxit < 1 || p.gmres_restart < 0 || p.gmres_restart > 127) fail(BEM_ERR_ARG, "bad GMRES limits");
+    if (p.gmres_precond != 0 && p.gmres_precond != 1) fail(BEM_ERR_ARG, "gmres_precond must be 0 or 1");
     if (!(p.gmres_tol > 0.0)) fail(BEM_ERR_ARG, "gmres_tol must be > 0");
 }
 
@@ -175,18 +178,30 @@ void apply_full(Context &c, double f, const double *xL, double g, const double *
 
 void build_all(Context &c) {
     if (!c.mesh_ok) fail(BEM_ERR_NOT_BUILT, "no mesh uploaded");
+    if (c.C > 1 && c.prm.mvp != BEM_MVP_FMM) fail(BEM_ERR_ARG, "independent clusters need the FMM product");
     cudaEvent_t e0, e1;
     BEM_CUDA(cudaEventCreate(&e0));
     BEM_CUDA(cudaEventCreate(&e1));
     BEM_CUDA(cudaEventRecord(e0, c.stream));
     c.built = false;
-    {
+    const int64_t N = c.N;
+    if (c.points_only) {  // unit weights, normals along z (unused: products use f only)
+        c.s.resize(N);
+        c.nrm.resize(3 * N);
+        k_fill<<<div_up(N, 256), 256, 0, c.stream>>>(N, 1.0, c.s.p);
+        k_fill<<<div_up(2 * N, 256), 256, 0, c.stream>>>(2 * N, 0.0, c.nrm.p);
+        k_fill<<<div_up(N, 256), 256, 0, c.stream>>>(N, 1.0, c.nrm.p + 2 * N);
+        BEM_LAUNCH_CHECK();
+    } else {
         PhaseScope ps(c, PH_GEOMETRY);
         compute_vertex_geometry(c);
     }
-    const int64_t N = c.N;
     if (c.prm.mvp == BEM_MVP_FMM) {
         build_operators(c);
+        if (c.prm.m2l_tensor_cores && m2l_tc_supported(c.ops.P) && c.ops.tc_Npad == 0) build_tc_tables(c);
+        c.tc_chunks_r = 0;
+        c.tc_err.resize(1);
+        BEM_CUDA(cudaMemsetAsync(c.tc_err.p, 0, sizeof(int), c.stream));
         {
             PhaseScope ps(c, PH_TREE);
             build_tree(c);
@@ -205,6 +220,21 @@ void build_all(Context &c) {
         c.stats.m2l_pairs = 0;
         c.stats.levels = 0;
         c.stats.leaves = 0;
+    }
+    if (c.points_only) {  // no singular diagonal for point sources
+        c.ldiag.resize(N);
+        c.mdiag.resize(N);
+        BEM_CUDA(cudaMemsetAsync(c.ldiag.p, 0, N * sizeof(double), c.stream));
+        BEM_CUDA(cudaMemsetAsync(c.mdiag.p, 0, N * sizeof(double), c.stream));
+        BEM_CUDA(cudaEventRecord(e1, c.stream));
+        BEM_CUDA(cudaStreamSynchronize(c.stream));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        c.stats.last_build_ms = ms;
+        c.built = true;
+        return;
     }
     // diagonals from one 4-RHS off-diagonal product (Eqs. (s3), (s5))
     c.ones.resize(N);
@@ -240,6 +270,11 @@ void build_all(Context &c) {
     cudaEventDestroy(e1);
     c.stats.last_build_ms = ms;
     if (hb) fail(BEM_ERR_NAN, "non-finite singular diagonal");
+    if (c.prm.mvp == BEM_MVP_FMM) {
+        int he = 0;
+        BEM_CUDA(cudaMemcpy(&he, c.tc_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+        if (he) fail(BEM_ERR_TIMEOUT, "tensor-core M2L wait ran out");
+    }
     c.built = true;
 }
 
@@ -267,6 +302,8 @@ int bem_params_default(bem_params *p) {
     p->precision = BEM_PREC_MIXED;
     p->mvp = BEM_MVP_FMM;
     p->diag_precision = -1;
+    p->m2l_tensor_cores = 1;
+    p->gmres_precond = 0;
     p->gmres_maxit = 100;
     p->gmres_restart = 0;
     p->gmres_tol = 1e-6;
@@ -319,6 +356,9 @@ int bem_mesh_upload(void *ctx, int64_t N, const double *xyz, int64_t T, const in
         if (N > (int64_t)INT32_MAX / 2 || T > (int64_t)INT32_MAX / 3) fail(BEM_ERR_ARG, "mesh too large for 32-bit indices");
         c.built = false;
         c.mesh_ok = false;
+        c.points_only = false;
+        c.C = 1;
+        c.cluster_boff.clear();
         c.N = N;
         c.T = T;
         c.M = M;
@@ -338,7 +378,64 @@ int bem_mesh_upload(void *ctx, int64_t N, const double *xyz, int64_t T, const in
         for (int64_t m = 0; m < M; ++m)
             if (c.vert_off[m + 1] < c.vert_off[m] || c.tri_off[m + 1] < c.tri_off[m])
                 fail(BEM_ERR_ARG, "offsets must be non-decreasing");
+        c.voff_d.resize(M + 1);
+        BEM_CUDA(cudaMemcpyAsync(c.voff_d.p, c.vert_off.data(), (M + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
+                                 c.stream));
         build_vertex_triangle_csr(c);
+        c.mesh_ok = true;
+    });
+}
+
+__global__ void k_fill_cluster(const int64_t *__restrict__ cvoff, int32_t *__restrict__ vcid) {
+    const int c = blockIdx.x;
+    for (int64_t i = cvoff[c] + threadIdx.x; i < cvoff[c + 1]; i += blockDim.x) vcid[i] = c;
+}
+
+int bem_mesh_set_clusters(void *ctx, int64_t C, const int64_t *bubble_off) {
+    return guarded(ctx, [&](Context &c) {
+        if (!c.mesh_ok || c.points_only) fail(BEM_ERR_NOT_BUILT, "upload a mesh first");
+        if (C < 1 || C > 256 || !bubble_off) fail(BEM_ERR_ARG, "cluster count must be in 1..256");
+        std::vector<int64_t> bo(C + 1);
+        auto k = is_device_ptr(c, bubble_off) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+        BEM_CUDA(cudaMemcpy(bo.data(), bubble_off, (C + 1) * sizeof(int64_t), k));
+        if (bo[0] != 0 || bo[C] != c.M) fail(BEM_ERR_ARG, "bubble offsets must start at 0 and end at M");
+        for (int64_t i = 0; i < C; ++i)
+            if (bo[i + 1] <= bo[i]) fail(BEM_ERR_ARG, "every cluster needs at least one bubble");
+        c.built = false;
+        c.C = C;
+        c.cluster_boff = bo;
+        if (C > 1) {
+            std::vector<int64_t> cv(C + 1);
+            for (int64_t i = 0; i <= C; ++i) cv[i] = c.vert_off[bo[i]];
+            DevBuf<int64_t> dcv;
+            dcv.resize(C + 1);
+            BEM_CUDA(cudaMemcpyAsync(dcv.p, cv.data(), (C + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c.stream));
+            c.vcid.resize(c.N);
+            k_fill_cluster<<<(unsigned)C, 256, 0, c.stream>>>(dcv.p, c.vcid.p);
+            BEM_LAUNCH_CHECK();
+            BEM_CUDA(cudaStreamSynchronize(c.stream));
+        }
+    });
+}
+
+int bem_points_upload(void *ctx, int64_t N, const double *xyz) {
+    return guarded(ctx, [&](Context &c) {
+        if (N < 2 || !xyz) fail(BEM_ERR_ARG, "bad point count or null array");
+        if (N > (int64_t)INT32_MAX / 2) fail(BEM_ERR_ARG, "too many points for 32-bit indices");
+        c.built = false;
+        c.mesh_ok = false;
+        c.points_only = true;
+        c.C = 1;
+        c.cluster_boff.clear();
+        c.N = N;
+        c.T = 0;
+        c.M = 1;
+        c.xyz.resize(3 * N);
+        auto k = is_device_ptr(c, xyz) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        BEM_CUDA(cudaMemcpyAsync(c.xyz.p, xyz, 3 * N * sizeof(double), k, c.stream));
+        c.vert_off = {0, N};
+        c.tri_off = {0, 0};
+        BEM_CUDA(cudaStreamSynchronize(c.stream));
         c.mesh_ok = true;
     });
 }
@@ -475,6 +572,85 @@ int bem_step(void *ctx, bem_step_stats *st) {
 
 int bem_step_get_state(void *ctx, double *xyz, double *phi, double *q, double *t) {
     return guarded(ctx, [&](Context &c) { step_get_state(c, xyz, phi, q, t); });
+}
+
+int bem_mlp_init(void *ctx, int32_t hidden, int32_t lmax, uint64_t seed) {
+    return guarded(ctx, [&](Context &c) { mlp_init(c, hidden, lmax, seed, step_initial_xyz(c)); });
+}
+
+int bem_mlp_set_mode(void *ctx, int32_t record, int32_t use_guess, int32_t compare) {
+    return guarded(ctx, [&](Context &c) { mlp_set_mode(c, record, use_guess, compare); });
+}
+
+int bem_mlp_train(void *ctx, int32_t epochs, int32_t batch, double lr, double *last_loss) {
+    return guarded(ctx, [&](Context &c) {
+        if (epochs < 1 || batch < 1 || !(lr > 0.0)) fail(BEM_ERR_ARG, "epochs, batch and lr must be positive");
+        double l = mlp_train(c, epochs, batch, lr);
+        if (last_loss) *last_loss = l;
+    });
+}
+
+int bem_mlp_loss_grad(void *ctx, int32_t B, const double *F, const double *T, double *loss, double *grads) {
+    return guarded(ctx, [&](Context &c) {
+        if (B < 1 || !F || !T || !grads) fail(BEM_ERR_ARG, "bad batch or null array");
+        const int *d = mlp_dims(c);
+        const double *dF = dev_in(c, F, (int64_t)B * d[0], 0);
+        const double *dT = dev_in(c, T, (int64_t)B * d[4], 1);
+        int64_t np = mlp_num_params(*c.mlp);
+        OutView ov(c, grads, np);
+        double l = mlp_loss_grad(c, B, dF, dT, ov.dev);
+        ov.finish();
+        if (loss) *loss = l;
+    });
+}
+
+int bem_mlp_forward(void *ctx, int32_t B, const double *F, double *Y) {
+    return guarded(ctx, [&](Context &c) {
+        if (B < 1 || !F || !Y) fail(BEM_ERR_ARG, "bad batch or null array");
+        const int *d = mlp_dims(c);
+        const double *dF = dev_in(c, F, (int64_t)B * d[0], 0);
+        OutView ov(c, Y, (int64_t)B * d[4]);
+        mlp_forward(c, B, dF, ov.dev);
+        ov.finish();
+    });
+}
+
+int bem_mlp_get_params(void *ctx, double *out) {
+    return guarded(ctx, [&](Context &c) {
+        if (!out) fail(BEM_ERR_ARG, "null output");
+        std::vector<double> h(mlp_num_params(*c.mlp));
+        mlp_get_params(c, h.data());
+        auto k = is_device_ptr(c, out) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+        BEM_CUDA(cudaMemcpy(out, h.data(), h.size() * sizeof(double), k));
+    });
+}
+
+int bem_mlp_set_params(void *ctx, const double *in) {
+    return guarded(ctx, [&](Context &c) {
+        if (!in) fail(BEM_ERR_ARG, "null input");
+        std::vector<double> h(mlp_num_params(*c.mlp));
+        auto k = is_device_ptr(c, in) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+        BEM_CUDA(cudaMemcpy(h.data(), in, h.size() * sizeof(double), k));
+        mlp_set_params(c, h.data());
+    });
+}
+
+int bem_mlp_info(void *ctx, bem_mlp_summary *out) {
+    return guarded(ctx, [&](Context &c) {
+        if (!out) fail(BEM_ERR_ARG, "null output");
+        if (!c.mlp) fail(BEM_ERR_NOT_BUILT, "bem_mlp_init has not been called");
+        const int *d = mlp_dims(c);
+        for (int i = 0; i < 5; ++i) out->dims[i] = d[i];
+        out->reserved = 0;
+        out->num_params = mlp_num_params(*c.mlp);
+        out->samples = mlp_samples(c);
+        const MlpStats &ms = mlp_stats(c);
+        out->compared_solves = ms.solves;
+        out->iters_guess = ms.iters_guess;
+        out->iters_fallback = ms.iters_fallback;
+        out->res0_guess = ms.res0_guess;
+        out->res0_fallback = ms.res0_fallback;
+    });
 }
 
 int bem_get_residual_history(void *ctx, double *out, int32_t max, int32_t *count) {

@@ -199,11 +199,12 @@ struct RhsArgs {
 // (leaf-box units), gathered into Morton order.
 template <class T, int R>
 __global__ void k_strengths(int64_t N, const int32_t *__restrict__ perm, const double *__restrict__ s,
-                            RhsArgs<R> a, double inv_h, T *__restrict__ q, T *__restrict__ w) {
+                            RhsArgs<R> a, const double *__restrict__ ih, T *__restrict__ q, T *__restrict__ w) {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= N) return;
     int j = perm[k];
     double sk = s[k] * kInv4Pi;
+    const double inv_h = ih[k];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         double qq = a.f[r] != 0.0 ? a.f[r] * sk * a.xL[r][j] : 0.0;
@@ -214,68 +215,85 @@ __global__ void k_strengths(int64_t N, const int32_t *__restrict__ perm, const d
 }
 
 // ------------------------------------------------------------------------------ P2M
-constexpr int P2M_THREADS = 128;
-constexpr int P2M_PC = 8;  // points per chunk
+// One block per leaf. Points are taken 32 at a time: their regular harmonics R_n^m (m >= 0)
+// are built column by column (the recurrence in n for each m) into shared memory, then each
+// thread owns one complex coefficient (n, m) and accumulates
+//   M_n^m += q conj(R_n^m) + w conj(n . grad R_n^m),
+//   n . grad R_n^m = n_z R_{n-1}^m - (n_x + i n_y)/2 R_{n-1}^{m-1} + (n_x - i n_y)/2 R_{n-1}^{m+1},
+// over the points, for the real and imaginary part together.
+constexpr int P2M_PC = 32;  // points per chunk
+
+template <class T>
+struct Vec2 {
+    using type = float2;
+};
+template <>
+struct Vec2<double> {
+    using type = double2;
+};
 
 template <class T, int R>
-__global__ void __launch_bounds__(P2M_THREADS) k_p2m(int p, int nleaf, const int32_t *__restrict__ bstart,
-                                                     const int32_t *__restrict__ bcount, int64_t N,
-                                                     const T *__restrict__ loc, const T *__restrict__ nrm,
-                                                     const T *__restrict__ q, const T *__restrict__ w,
-                                                     T *__restrict__ mp) {
+__global__ void __launch_bounds__(256) k_p2m(int p, int nleaf, const int32_t *__restrict__ bstart,
+                                             const int32_t *__restrict__ bcount, int64_t N,
+                                             const T *__restrict__ loc, const T *__restrict__ nrm,
+                                             const T *__restrict__ q, const T *__restrict__ w,
+                                             T *__restrict__ mp) {
+    using T2 = typename Vec2<T>::type;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int P = p * p;
     const int ntri = p * (p + 1) / 2;
-    T *Rre = reinterpret_cast<T *>(smraw);
-    T *Rim = Rre + P2M_PC * ntri;
-    T *pn = Rim + P2M_PC * ntri;      // [PC][3]
-    T *pq = pn + P2M_PC * 3;          // [PC][R]
-    T *pw = pq + P2M_PC * R;          // [PC][R]
-    int b = blockIdx.x;
-    int s0 = bstart[b], cnt = bcount[b];
-    constexpr int MAXO = 4;  // outputs per thread: P <= 4 * 128
-    T acc[MAXO][R];
+    T2 *Rt = reinterpret_cast<T2 *>(smraw);          // [PC][ntri]
+    T *pn = reinterpret_cast<T *>(Rt + P2M_PC * ntri);  // [PC][3]
+    T *pq = pn + P2M_PC * 3;                            // [PC][R]
+    T *pw = pq + P2M_PC * R;                            // [PC][R]
+    const int b = blockIdx.x;
+    const int s0 = bstart[b], cnt = bcount[b];
+    constexpr int MAXC = 2;  // complex coefficients per thread (ntri <= 2 * blockDim)
+    int cn[MAXC], cm[MAXC];
+    T are[MAXC][R], aim[MAXC][R];
 #pragma unroll
-    for (int o = 0; o < MAXO; ++o)
+    for (int o = 0; o < MAXC; ++o) {
+        int c = threadIdx.x + o * blockDim.x;
+        int n = 0;
+        while ((n + 1) * (n + 2) / 2 <= c) ++n;
+        cn[o] = (c < ntri) ? n : -1;
+        cm[o] = c - n * (n + 1) / 2;
 #pragma unroll
-        for (int r = 0; r < R; ++r) acc[o][r] = (T)0;
+        for (int r = 0; r < R; ++r) are[o][r] = aim[o][r] = (T)0;
+    }
     for (int c0 = 0; c0 < cnt; c0 += P2M_PC) {
-        int pc = min(P2M_PC, cnt - c0);
+        const int pc = min(P2M_PC, cnt - c0);
         __syncthreads();
-        if (threadIdx.x < pc * 3) {
-            int jj = threadIdx.x / 3, d = threadIdx.x % 3;
+        for (int e = threadIdx.x; e < pc * 3; e += blockDim.x) {
+            int jj = e / 3, d = e % 3;
             pn[jj * 3 + d] = nrm[d * N + s0 + c0 + jj];
-        } else if (threadIdx.x >= 32 && threadIdx.x < 32 + pc * R) {
-            int t = threadIdx.x - 32, jj = t / R, r = t % R;
+        }
+        for (int e = threadIdx.x; e < pc * R; e += blockDim.x) {
+            int jj = e / R, r = e % R;
             pq[jj * R + r] = q[r * N + s0 + c0 + jj];
             pw[jj * R + r] = w[r * N + s0 + c0 + jj];
         }
-        for (int task = threadIdx.x; task < pc * p; task += P2M_THREADS) {
-            int jj = task / p, m = task % p;
-            int64_t i = s0 + c0 + jj;
-            T x = loc[i], y = loc[N + i], z = loc[2 * N + i];
-            T r2 = x * x + y * y + z * z;
+        for (int task = threadIdx.x; task < pc * p; task += blockDim.x) {
+            const int jj = task / p, m = task % p;
+            const int64_t i = s0 + c0 + jj;
+            const T x = loc[i], y = loc[N + i], z = loc[2 * N + i];
+            const T r2 = x * x + y * y + z * z;
             T mr = 1, mi = 0;
             for (int k = 1; k <= m; ++k) {
-                T f = (T)(-0.5) / (T)k;
-                T nr = f * (x * mr - y * mi), ni = f * (x * mi + y * mr);
+                const T f = (T)(-0.5) / (T)k;
+                const T nr = f * (x * mr - y * mi), ni = f * (x * mi + y * mr);
                 mr = nr;
                 mi = ni;
             }
-            T *re = Rre + jj * ntri, *im = Rim + jj * ntri;
-            re[tri_idx(m, m)] = mr;
-            im[tri_idx(m, m)] = mi;
+            T2 *col = Rt + jj * ntri;
+            col[tri_idx(m, m)] = T2{mr, mi};
             T p2r = mr, p2i = mi, p1r = z * mr, p1i = z * mi;
-            if (m + 1 < p) {
-                re[tri_idx(m + 1, m)] = p1r;
-                im[tri_idx(m + 1, m)] = p1i;
-            }
+            if (m + 1 < p) col[tri_idx(m + 1, m)] = T2{p1r, p1i};
             for (int n = m + 2; n < p; ++n) {
-                T d = (T)1 / ((T)(n + m) * (T)(n - m));
-                T cr = ((T)(2 * n - 1) * z * p1r - r2 * p2r) * d;
-                T ci = ((T)(2 * n - 1) * z * p1i - r2 * p2i) * d;
-                re[tri_idx(n, m)] = cr;
-                im[tri_idx(n, m)] = ci;
+                const T d = (T)1 / ((T)(n + m) * (T)(n - m));
+                const T cr = ((T)(2 * n - 1) * z * p1r - r2 * p2r) * d;
+                const T ci = ((T)(2 * n - 1) * z * p1i - r2 * p2i) * d;
+                col[tri_idx(n, m)] = T2{cr, ci};
                 p2r = p1r;
                 p2i = p1i;
                 p1r = cr;
@@ -284,58 +302,50 @@ __global__ void __launch_bounds__(P2M_THREADS) k_p2m(int p, int nleaf, const int
         }
         __syncthreads();
 #pragma unroll
-        for (int o = 0; o < MAXO; ++o) {
-            int ro = threadIdx.x + o * P2M_THREADS;
-            if (ro >= P) break;
-            int n, m, part;
-            decode(ro, n, m, part);
+        for (int o = 0; o < MAXC; ++o) {
+            const int n = cn[o], m = cm[o];
+            if (n < 0) continue;
+            const int iA = tri_idx(n, m);
+            const int iB = (n >= 1 && m <= n - 1) ? tri_idx(n - 1, m) : -1;
+            const int iL = (n >= 1 && m >= 1) ? tri_idx(n - 1, m - 1) : ((n >= 2) ? tri_idx(n - 1, 1) : -1);
+            const int iU = (n >= 1 && m + 1 <= n - 1) ? tri_idx(n - 1, m + 1) : -1;
+            const bool neg1 = (m == 0);  // R^{-1} = -conj(R^1)
             for (int jj = 0; jj < pc; ++jj) {
-                const T *re = Rre + jj * ntri, *im = Rim + jj * ntri;
-                T cr = re[tri_idx(n, m)], ci = -im[tri_idx(n, m)];  // conj(R_n^m)
-                // conj(n . grad R_n^m) for the unit normal of the point
-                T dr = 0, di = 0;
+                const T2 *col = Rt + jj * ntri;
+                const T2 A = col[iA];
+                T gr = 0, gi = 0;
                 if (n >= 1) {
-                    T nx = pn[jj * 3], ny = pn[jj * 3 + 1], nz = pn[jj * 3 + 2];
-                    T ar = 0, ai = 0;  // R_{n-1}^m
-                    if (m <= n - 1) {
-                        ar = re[tri_idx(n - 1, m)];
-                        ai = im[tri_idx(n - 1, m)];
-                    }
-                    T br, bi;  // R_{n-1}^{m-1}
-                    if (m >= 1) {
-                        br = re[tri_idx(n - 1, m - 1)];
-                        bi = im[tri_idx(n - 1, m - 1)];
-                    } else if (n - 1 >= 1) {  // R^{-1} = -conj(R^1)
-                        br = -re[tri_idx(n - 1, 1)];
-                        bi = im[tri_idx(n - 1, 1)];
-                    } else {
-                        br = 0;
-                        bi = 0;
-                    }
-                    T er = 0, ei = 0;  // R_{n-1}^{m+1}
-                    if (m + 1 <= n - 1) {
-                        er = re[tri_idx(n - 1, m + 1)];
-                        ei = im[tri_idx(n - 1, m + 1)];
-                    }
-                    // nz*A - (nx + i ny)/2 * B + (nx - i ny)/2 * E
-                    T gr = nz * ar - (T)0.5 * (nx * br - ny * bi) + (T)0.5 * (nx * er + ny * ei);
-                    T gi = nz * ai - (T)0.5 * (nx * bi + ny * br) + (T)0.5 * (nx * ei - ny * er);
-                    dr = gr;
-                    di = -gi;
+                    const T nx = pn[jj * 3], ny = pn[jj * 3 + 1], nz = pn[jj * 3 + 2];
+                    T2 Bm = iB >= 0 ? col[iB] : T2{0, 0};
+                    T2 Bl = iL >= 0 ? col[iL] : T2{0, 0};
+                    if (neg1) Bl = T2{-Bl.x, Bl.y};
+                    T2 Bu = iU >= 0 ? col[iU] : T2{0, 0};
+                    gr = nz * Bm.x - (T)0.5 * (nx * Bl.x - ny * Bl.y) + (T)0.5 * (nx * Bu.x + ny * Bu.y);
+                    gi = nz * Bm.y - (T)0.5 * (nx * Bl.y + ny * Bl.x) + (T)0.5 * (nx * Bu.y - ny * Bu.x);
                 }
-                T vm = part ? ci : cr;
-                T vd = part ? di : dr;
 #pragma unroll
-                for (int r = 0; r < R; ++r) acc[o][r] += pq[jj * R + r] * vm + pw[jj * R + r] * vd;
+                for (int r = 0; r < R; ++r) {
+                    const T qq = pq[jj * R + r], ww = pw[jj * R + r];
+                    are[o][r] += qq * A.x + ww * gr;
+                    aim[o][r] -= qq * A.y + ww * gi;
+                }
             }
         }
     }
 #pragma unroll
-    for (int o = 0; o < MAXO; ++o) {
-        int ro = threadIdx.x + o * P2M_THREADS;
-        if (ro >= P) break;
+    for (int o = 0; o < MAXC; ++o) {
+        const int n = cn[o], m = cm[o];
+        if (n < 0) continue;
 #pragma unroll
-        for (int r = 0; r < R; ++r) mp[((size_t)b * R + r) * P + ro] = acc[o][r];
+        for (int r = 0; r < R; ++r) {
+            T *dst = mp + ((size_t)b * R + r) * P;
+            if (m == 0) {
+                dst[n * n] = are[o][r];
+            } else {
+                dst[n * n + 2 * m - 1] = are[o][r];
+                dst[n * n + 2 * m] = aim[o][r];
+            }
+        }
     }
 }
 
@@ -560,7 +570,6 @@ void run_fmm(Context &c, const RhsArgs<R> &a) {
     cudaStream_t st = c.stream;
     const int64_t N = c.N;
     const int L = t.L, p = c.ops.p, P = c.ops.P;
-    const double inv_h = (double)(1 << L) / t.size;
     const int tb = 256;
     constexpr bool F64 = sizeof(T) == 8;
     T *q, *w, *mp, *lc, *far;
@@ -588,7 +597,7 @@ void run_fmm(Context &c, const RhsArgs<R> &a) {
     }
     {
         PhaseScope ps(c, PH_STRENGTHS);
-        k_strengths<T, R><<<div_up(N, tb), tb, 0, st>>>(N, t.perm.p, t.s_sorted.p, a, inv_h, q, w);
+        k_strengths<T, R><<<div_up(N, tb), tb, 0, st>>>(N, t.perm.p, t.s_sorted.p, a, t.ih.p, q, w);
         BEM_LAUNCH_CHECK();
     }
 
@@ -624,9 +633,12 @@ void run_fmm(Context &c, const RhsArgs<R> &a) {
     const int nleaf = t.nb[L];
     {
         PhaseScope ps(c, PH_P2M);
-        size_t sm = ((size_t)2 * P2M_PC * (p * (p + 1) / 2) + P2M_PC * 3 + 2 * P2M_PC * R) * sizeof(T);
-        k_p2m<T, R><<<nleaf, P2M_THREADS, sm, st>>>(p, nleaf, t.bstart.p + t.base[L], t.bcount.p + t.base[L], N, loc, nrm,
-                                                   q, w, mp + (size_t)t.base[L] * R * P);
+        const int ntri = p * (p + 1) / 2;
+        size_t sm = ((size_t)2 * P2M_PC * ntri + P2M_PC * 3 + 2 * P2M_PC * R) * sizeof(T);
+        const int threads = std::min(256, std::max(64, (ntri + 63) / 64 * 32));  // ntri <= 2 * threads
+        if (sm > 48 * 1024) BEM_CUDA(cudaFuncSetAttribute(k_p2m<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_p2m<T, R><<<nleaf, threads, sm, st>>>(p, nleaf, t.bstart.p + t.base[L], t.bcount.p + t.base[L], N, loc, nrm,
+                                                q, w, mp + (size_t)t.base[L] * R * P);
         BEM_LAUNCH_CHECK();
     }
     // zero the multipoles above the leaves and all locals
@@ -665,10 +677,25 @@ void run_fmm(Context &c, const RhsArgs<R> &a) {
     // M2L, all levels at once, then each target sums its sources
     if (nm2l_chunks) {
         PhaseScope ps(c, PH_M2L);
-        dim3 grid((unsigned)nm2l_chunks, rowblocks);
-        k_xlat<T, R, kStorePair><<<grid, XT_THREADS, 0, st>>>(m2l, P, c.m2l_chunks.p + 1, t.m2l_src.p, t.m2l_tgt.p,
-                                                             mp, ypair);
-        BEM_LAUNCH_CHECK();
+        if (!F64 && c.prm.m2l_tensor_cores && m2l_tc_supported(P) && c.ops.tc_Npad > 0) {
+            if (c.tc_chunks_r != R) {
+                std::vector<XChunk> tc;
+                make_chunks(t.m2l_class_off, 0, 128 / R, tc);
+                c.tc_chunks.resize(std::max<size_t>(tc.size(), 1));
+                if (!tc.empty())
+                    BEM_CUDA(cudaMemcpyAsync(c.tc_chunks.p, tc.data(), tc.size() * sizeof(XChunk),
+                                             cudaMemcpyHostToDevice, st));
+                c.n_tc_chunks = (int64_t)tc.size();
+                c.tc_chunks_r = R;
+            }
+            if (c.n_tc_chunks)
+                launch_m2l_tc<R>(c, c.tc_chunks.p, c.n_tc_chunks, (const float *)mp, (float *)ypair, c.tc_err.p);
+        } else {
+            dim3 grid((unsigned)nm2l_chunks, rowblocks);
+            k_xlat<T, R, kStorePair><<<grid, XT_THREADS, 0, st>>>(m2l, P, c.m2l_chunks.p + 1, t.m2l_src.p,
+                                                                 t.m2l_tgt.p, mp, ypair);
+            BEM_LAUNCH_CHECK();
+        }
         int ntg = t.nbox - t.base[2];
         dim3 rg((unsigned)ntg, red_blocks_y);
         k_reduce_pairs<T, R><<<rg, 128, 0, st>>>(t.base[2], t.m2l_tgt_off.p, t.m2l_by_tgt.p, ypair, P, lc);

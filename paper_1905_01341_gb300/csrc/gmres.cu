@@ -118,6 +118,18 @@ __global__ void k_givens(int k, int m, const double *__restrict__ h, double *__r
     resid[0] = fabs(g[k + 1]);
 }
 
+// z = d .* v (right preconditioning by the inverse diagonal)
+__global__ void k_scale_by(int64_t N, const double *__restrict__ d, const double *__restrict__ v, double *__restrict__ z) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        z[i] = v[i] / d[i];
+}
+
+// x += t ./ d
+__global__ void k_add_scaled(int64_t N, const double *__restrict__ d, const double *__restrict__ t, double *__restrict__ x) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += t[i] / d[i];
+}
+
 // Back substitution: H(0:kk,0:kk) y = g(0:kk).
 __global__ void k_backsolve(int kk, int m, const double *__restrict__ H, const double *__restrict__ g,
                             double *__restrict__ y) {
@@ -177,6 +189,8 @@ void gmres_solve(Context &c, const double *b, double *x, int *iters_out, double 
     const int m = std::min({maxit, c.prm.gmres_restart > 0 ? c.prm.gmres_restart : maxit, 127});
     const double tol = c.prm.gmres_tol;
     Vec vec(c);
+    const bool precond = c.prm.gmres_precond == 1;
+    if (precond) c.zv.resize(N);
     c.V.resize((size_t)(m + 1) * N);
     c.wv.resize(N);
     c.rv.resize(N);
@@ -226,7 +240,13 @@ void gmres_solve(Context &c, const double *b, double *x, int *iters_out, double 
         int kk = 0;
         for (int k = 0; k < m; ++k) {
             double *vk = c.V.p + (size_t)k * N;
-            apply_full(c, 1.0, vk, 0.0, nullptr, c.wv.p);
+            if (precond) {  // w = A D^-1 v_k
+                k_scale_by<<<vec.grid, 256, 0, c.stream>>>(N, c.ldiag.p, vk, c.zv.p);
+                BEM_LAUNCH_CHECK();
+                apply_full(c, 1.0, c.zv.p, 0.0, nullptr, c.wv.p);
+            } else {
+                apply_full(c, 1.0, vk, 0.0, nullptr, c.wv.p);
+            }
             ++mvps;
             // classical Gram-Schmidt, twice
             vec.dots(k + 1, c.V.p, N, c.wv.p, c.hcol.p, 0);
@@ -248,7 +268,14 @@ void gmres_solve(Context &c, const double *b, double *x, int *iters_out, double 
         }
         k_backsolve<<<1, 1, 0, c.stream>>>(kk, m, c.hmat.p, c.gvec.p, c.yvec.p);
         BEM_LAUNCH_CHECK();
-        vec.multiaxpy(kk, c.V.p, N, c.yvec.p, 1.0, x);
+        if (precond) {  // x += D^-1 V y
+            BEM_CUDA(cudaMemsetAsync(c.zv.p, 0, N * sizeof(double), c.stream));
+            vec.multiaxpy(kk, c.V.p, N, c.yvec.p, 1.0, c.zv.p);
+            k_add_scaled<<<vec.grid, 256, 0, c.stream>>>(N, c.ldiag.p, c.zv.p, x);
+            BEM_LAUNCH_CHECK();
+        } else {
+            vec.multiaxpy(kk, c.V.p, N, c.yvec.p, 1.0, x);
+        }
     }
     c.stats.last_iters = iters;
     c.stats.last_mvps = mvps;

@@ -95,6 +95,8 @@ constexpr int kNumM2LClasses = 316;  // offsets in [-3,3]^3 minus the 27 near on
 // ------------------------------------------------------------------------------ octree
 struct Tree {
     int L = 0;                 // leaf level l_max
+    int deep = kDeepLevel;     // depth of the point keys (8 when the key carries a cluster id)
+    DevBuf<double> ih;         // [N] 1 / (leaf box size) of each sorted point's cluster
     double origin[3] = {0, 0, 0};
     double size = 1.0;         // bounding cube edge
     int64_t N = 0;
@@ -139,6 +141,10 @@ struct Operators {
     int p = 0, P = 0;
     DevBuf<double> m2l64, m2m64, l2l64;  // [316][P][P], [8][P][P], [8][P][P]
     DevBuf<float> m2l32, m2m32, l2l32;
+    // tensor-core M2L: per class, per 32-wide K chunk, an Npad x 32 block in the K-major
+    // core-matrix layout (m2l_tc.cu)
+    int tc_Npad = 0, tc_Kpad = 0;
+    DevBuf<float> m2l_tc;
 };
 
 // Work chunk of the class-grouped translation product.
@@ -194,9 +200,20 @@ struct Profiler {
     }
 };
 
+// Per-shape least-squares spherical-harmonic basis (Eqs. (3.22)-(3.23)): for every distinct
+// initial bubble shape, G [nd][Pf] and G+ = (G^T G)^(-1) G^T [Pf][nd], concatenated.
+struct ShBasis {
+    int pf = 0, Pf = 0;
+    DevBuf<double> G, Gp;
+    DevBuf<int64_t> g_off;     // per shape offset (elements) into G / Gp
+    DevBuf<int32_t> shape_of;  // [M] shape index of each bubble
+};
+
 struct Context;
 struct StepState;
+struct Mlp;
 void step_free(StepState *s);
+void mlp_free(Mlp *m);
 // Records the device time of everything launched on the context stream during its lifetime.
 struct PhaseScope {
     Context *c;
@@ -219,6 +236,12 @@ struct Context {
     std::vector<int64_t> vert_off, tri_off;
     DevBuf<int32_t> v2t_off, v2t;  // vertex -> triangle CSR (sorted triangle ids)
     bool mesh_ok = false;
+    bool points_only = false;      // bem_points_upload: unit weights, no triangles, no diagonals
+    // independent clusters (bem_mesh_set_clusters): cluster c owns bubbles
+    // cluster_boff[c]..cluster_boff[c+1]-1; no interaction crosses clusters
+    int64_t C = 1;
+    std::vector<int64_t> cluster_boff;
+    DevBuf<int32_t> vcid;          // [N] cluster of every vertex (when C > 1)
 
     // geometry (caller order)
     DevBuf<double> s, nrm;         // [N], [3][N]
@@ -242,6 +265,10 @@ struct Context {
     DevBuf<double> near_out;       // combined potential [R][N] (sorted)
     DevBuf<XChunk> m2l_chunks;
     std::vector<XChunk> m2l_chunks_h;
+    DevBuf<XChunk> tc_chunks;        // M2L chunks of <= 128/R pairs for the tensor-core kernel
+    int tc_chunks_r = 0;             // R the table was built for (0 = none)
+    int64_t n_tc_chunks = 0;
+    DevBuf<int> tc_err;              // set by a tensor-core block whose wait ran out
     std::vector<DevBuf<XChunk> *> up_chunks;  // per level
     std::vector<std::vector<XChunk>> up_chunks_h;
     DevBuf<double> ones;
@@ -255,12 +282,14 @@ struct Context {
     DevBuf<double> stage_out;
 
     // GMRES
-    DevBuf<double> V, wv, rv, bv, hcol, hmat, givens, gvec, yvec, partial, scal;
+    DevBuf<double> V, wv, rv, bv, zv, hcol, hmat, givens, gvec, yvec, partial, scal;
     HostPinned<double> hscal;
 
     bem_stats stats{};
     std::vector<double> res_hist;  // residual estimates |g_{k+1}|/|b| of the last solve
     StepState *step = nullptr;     // time-integration state (timestep.cu)
+    Mlp *mlp = nullptr;            // learned initial guess (mlp.cu)
+    DevBuf<int64_t> voff_d;        // [M+1] device copy of vert_off
     Profiler prof;
     ~Context();
 };
@@ -291,6 +320,12 @@ template <int R>
 void launch_direct(Context &c, int prec, const double *f, const double *const *xL,
                    const double *g, const double *const *xM, double *const *out);
 
+// m2l_tc.cu
+bool m2l_tc_supported(int P);
+void build_tc_tables(Context &c);
+template <int R>
+void launch_m2l_tc(Context &c, const XChunk *chunks, int64_t nchunks, const float *X, float *Ypair, int *err);
+
 // gmres.cu
 void gmres_solve(Context &c, const double *b, double *x, int *iters, double *relres);
 
@@ -318,5 +353,32 @@ bool is_device_ptr(const Context &c, const void *p);
 void step_init(Context &c, const double *phi0_dev, const double *q0_dev, const bem_step_params &sp);
 void step_advance(Context &c, bem_step_stats &st);
 void step_get_state(Context &c, double *xyz, double *phi, double *q, double *t);
+void build_sh_basis(Context &c, int pf, ShBasis &B, int *bad, const double *xyz = nullptr);
+const double *step_initial_xyz(Context &c);
+
+// mlp.cu
+struct MlpStats {
+    int64_t solves = 0;          // solves that used the learned guess
+    int64_t iters_guess = 0;     // their GMRES iterations
+    int64_t iters_fallback = 0;  // iterations of the same solves from q_prev (compare mode)
+    double res0_guess = 0.0;     // summed initial relative residuals of each start
+    double res0_fallback = 0.0;
+};
+void mlp_init(Context &c, int hidden, int lmax, uint64_t seed, const double *xyz0);
+void mlp_set_mode(Context &c, int record, int use, int compare);
+bool mlp_active(Context &c);
+bool mlp_compare(Context &c);
+void mlp_before_solve(Context &c, const double *phi, double *q, bool uniform);
+const double *mlp_qprev(Context &c);
+void mlp_after_solve(Context &c, const double *q);
+double mlp_train(Context &c, int epochs, int batch, double lr);
+double mlp_loss_grad(Context &c, int B, const double *F, const double *T, double *grads_dev);
+void mlp_forward(Context &c, int B, const double *F, double *Y);
+void mlp_get_params(Context &c, double *out);
+void mlp_set_params(Context &c, const double *in);
+int64_t mlp_samples(Context &c);
+int64_t mlp_num_params(const Mlp &m);
+const int *mlp_dims(Context &c);
+MlpStats &mlp_stats(Context &c);
 
 }  // namespace bem

@@ -34,16 +34,32 @@ struct Comp {
     __device__ __forceinline__ double get() const { return (double)s + (double)c; }
 };
 
+template <class T>
+struct V4 {
+    using type = float4;
+};
+template <>
+struct V4<double> {
+    using type = double4;
+};
+
+// One block per target leaf. Sources of the (up to 27) neighbour leaves are staged tile by tile
+// in shared memory as (x, y, z, q) and (n_x, n_y, n_z, w), positions relative to the target
+// leaf's centre in leaf-box units; each thread keeps up to KMAX receivers in registers, so a
+// staged source feeds several pairs. The self pair has r^2 = 0 exactly (same coordinates, zero
+// offset) and is skipped; the paper's quadrature excludes j = i (Eq. (ns1)).
+constexpr int P2P_KMAX = 4;
+
 template <class T, int R>
 __global__ void __launch_bounds__(P2P_THREADS) k_p2p_list(
     const int32_t *__restrict__ bstart, const int32_t *__restrict__ bcount, const int32_t *__restrict__ nbr,
     const int32_t *__restrict__ ncnt, const int8_t *__restrict__ nd, int64_t N, const T *__restrict__ loc,
     const T *__restrict__ nrm, const T *__restrict__ q, const T *__restrict__ w, const T *__restrict__ far,
-    double inv_h, double *__restrict__ out) {
-    __shared__ T sx[P2P_THREADS], sy[P2P_THREADS], sz[P2P_THREADS];
-    __shared__ T snx[P2P_THREADS], sny[P2P_THREADS], snz[P2P_THREADS];
-    __shared__ T sq[R][P2P_THREADS], sw[R][P2P_THREADS];
-    __shared__ int sidx[P2P_THREADS];
+    const double *__restrict__ ih, double *__restrict__ out) {
+    using T4 = typename V4<T>::type;
+    __shared__ T4 sA[P2P_THREADS];            // x, y, z, q (first RHS)
+    __shared__ T4 sB[P2P_THREADS];            // n_x, n_y, n_z, w (first RHS)
+    __shared__ T sQ[R > 1 ? R - 1 : 1][P2P_THREADS], sW[R > 1 ? R - 1 : 1][P2P_THREADS];
     __shared__ int nb_start[27], nb_pre[28];
     __shared__ T nb_d[27][3];
     const int b = blockIdx.x, tid = threadIdx.x;
@@ -64,55 +80,70 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_list(
     __syncthreads();
     const int S = nb_pre[nn];
     const int s0 = bstart[b], cnt = bcount[b];
-    for (int rc0 = 0; rc0 < cnt; rc0 += P2P_THREADS) {
-        const bool vr = rc0 + tid < cnt;
-        const int64_t i = s0 + rc0 + (vr ? tid : 0);
-        const T xi = loc[i], yi = loc[N + i], zi = loc[2 * N + i];
-        Comp<T> acc[R];
+    for (int rc0 = 0; rc0 < cnt; rc0 += P2P_THREADS * P2P_KMAX) {
+        const int kr = min(P2P_KMAX, (cnt - rc0 + P2P_THREADS - 1) / P2P_THREADS);  // uniform in the block
+        T xi[P2P_KMAX], yi[P2P_KMAX], zi[P2P_KMAX];
+        Comp<T> acc[P2P_KMAX][R];
+#pragma unroll
+        for (int k = 0; k < P2P_KMAX; ++k) {
+            const int li = rc0 + k * P2P_THREADS + tid;
+            const int64_t i = s0 + (li < cnt ? li : 0);
+            xi[k] = loc[i];
+            yi[k] = loc[N + i];
+            zi[k] = loc[2 * N + i];
+        }
         for (int t0 = 0; t0 < S; t0 += P2P_THREADS) {
             __syncthreads();
-            int f = t0 + tid;
+            const int f = t0 + tid;
             if (f < S) {
                 int k = 0;
                 while (nb_pre[k + 1] <= f) ++k;
-                int j = nb_start[k] + (f - nb_pre[k]);
-                sx[tid] = loc[j] + nb_d[k][0];
-                sy[tid] = loc[N + j] + nb_d[k][1];
-                sz[tid] = loc[2 * N + j] + nb_d[k][2];
-                snx[tid] = nrm[j];
-                sny[tid] = nrm[N + j];
-                snz[tid] = nrm[2 * N + j];
+                const int j = nb_start[k] + (f - nb_pre[k]);
+                sA[tid] = T4{loc[j] + nb_d[k][0], loc[N + j] + nb_d[k][1], loc[2 * N + j] + nb_d[k][2], q[j]};
+                sB[tid] = T4{nrm[j], nrm[N + j], nrm[2 * N + j], w[j]};
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    sq[r][tid] = q[r * N + j];
-                    sw[r][tid] = w[r * N + j];
+                for (int r = 1; r < R; ++r) {
+                    sQ[r - 1][tid] = q[r * N + j];
+                    sW[r - 1][tid] = w[r * N + j];
                 }
-                sidx[tid] = j;
             }
             __syncthreads();
             const int ns = min(P2P_THREADS, S - t0);
-            T part[R];
+            T part[P2P_KMAX][R];
 #pragma unroll
-            for (int r = 0; r < R; ++r) part[r] = (T)0;
-            if (vr) {
-#pragma unroll 4
-                for (int s = 0; s < ns; ++s) {
-                    T dx = xi - sx[s], dy = yi - sy[s], dz = zi - sz[s];
-                    T r2 = dx * dx + dy * dy + dz * dz;
-                    bool self = sidx[s] == (int)i;
-                    T rinv = self ? (T)0 : rsqrt_t<T>(r2);
-                    T rinv3 = rinv * rinv * rinv;
-                    T nd3 = (snx[s] * dx + sny[s] * dy + snz[s] * dz) * rinv3;
+            for (int k = 0; k < P2P_KMAX; ++k)
 #pragma unroll
-                    for (int r = 0; r < R; ++r) part[r] += sq[r][s] * rinv + sw[r][s] * nd3;
+                for (int r = 0; r < R; ++r) part[k][r] = (T)0;
+#pragma unroll 2
+            for (int sI = 0; sI < ns; ++sI) {
+                const T4 a = sA[sI], bb = sB[sI];
+#pragma unroll
+                for (int k = 0; k < P2P_KMAX; ++k) {
+                    if (k < kr) {
+                        const T dx = xi[k] - a.x, dy = yi[k] - a.y, dz = zi[k] - a.z;
+                        const T r2 = dx * dx + dy * dy + dz * dz;
+                        const T rinv = r2 > (T)0 ? rsqrt_t<T>(r2) : (T)0;
+                        const T rinv3 = rinv * rinv * rinv;
+                        const T nd3 = (bb.x * dx + bb.y * dy + bb.z * dz) * rinv3;
+                        part[k][0] += a.w * rinv + bb.w * nd3;
+#pragma unroll
+                        for (int r = 1; r < R; ++r) part[k][r] += sQ[r - 1][sI] * rinv + sW[r - 1][sI] * nd3;
+                    }
                 }
             }
 #pragma unroll
-            for (int r = 0; r < R; ++r) acc[r].add(part[r]);
-        }
-        if (vr) {
+            for (int k = 0; k < P2P_KMAX; ++k)
 #pragma unroll
-            for (int r = 0; r < R; ++r) out[r * N + i] = ((double)far[r * N + i] + acc[r].get()) * inv_h;
+                for (int r = 0; r < R; ++r) acc[k][r].add(part[k][r]);
+        }
+#pragma unroll
+        for (int k = 0; k < P2P_KMAX; ++k) {
+            const int li = rc0 + k * P2P_THREADS + tid;
+            if (k < kr && li < cnt) {
+                const int64_t i = s0 + li;
+#pragma unroll
+                for (int r = 0; r < R; ++r) out[r * N + i] = ((double)far[r * N + i] + acc[k][r].get()) * ih[i];
+            }
         }
     }
 }
@@ -245,12 +276,11 @@ template <class T, int R>
 void launch_p2p_list(Context &c, const T *q, const T *w, const T *far, double *out_sorted) {
     Tree &t = c.tree;
     const int L = t.L;
-    const double inv_h = (double)(1 << L) / t.size;
     const T *loc = sizeof(T) == 8 ? (const T *)t.loc64.p : (const T *)t.loc32.p;
     const T *nrm = sizeof(T) == 8 ? (const T *)t.nrm64.p : (const T *)t.nrm32.p;
     int nleaf = t.nb[L];
     k_p2p_list<T, R><<<nleaf, P2P_THREADS, 0, c.stream>>>(t.bstart.p + t.base[L], t.bcount.p + t.base[L], t.nbr.p,
-                                                          t.nbr_cnt.p, t.nbr_d.p, c.N, loc, nrm, q, w, far, inv_h,
+                                                          t.nbr_cnt.p, t.nbr_d.p, c.N, loc, nrm, q, w, far, t.ih.p,
                                                           out_sorted);
     BEM_LAUNCH_CHECK();
 }

@@ -30,10 +30,10 @@ struct StepState {
     int Pf = 0;
     DevBuf<double> y, q, hist, k1, k2, k3, k4, ytmp, yf, f;
     DevBuf<double> V0, a0, V, pg;
-    DevBuf<int32_t> shape_of, bub_of, nbr5;
+    DevBuf<int32_t> bub_of, nbr5;
     DevBuf<int64_t> voff, toff;
-    DevBuf<double> G, Gp;  // per shape: G [nd][Pf], Gp [Pf][nd], concatenated
-    DevBuf<int64_t> g_off;  // per shape offset (in elements) into G / Gp
+    ShBasis filt;  // shape filter basis (bandwidth p_f)
+    DevBuf<double> x0;  // r at t = 0 (SoA)
     DevBuf<double> vt, H;
     bem_step_stats last{};
 };
@@ -404,7 +404,7 @@ void apply_filter(Context &c, StepState &s, const double *X, double *Y) {
         return;
     }
     k_filter_apply<<<(unsigned)c.M, 256, (size_t)s.Pf * 4 * sizeof(double), c.stream>>>(
-        c.N, s.voff.p, s.shape_of.p, s.g_off.p, s.Pf, s.G.p, s.Gp.p, X, Y);
+        c.N, s.voff.p, s.filt.shape_of.p, s.filt.g_off.p, s.Pf, s.filt.G.p, s.filt.Gp.p, X, Y);
     BEM_LAUNCH_CHECK();
 }
 
@@ -417,13 +417,46 @@ void rhs(Context &c, StepState &s, const double *y, double t, double *f, bem_ste
     st.mvps += 1;  // the 4-RHS diagonal product
     int it = 0;
     double rr = 0.0;
-    try {
-        solve_internal(c, s.yf.p + 3 * N, s.q.p, &it, &rr);
-    } catch (const Error &e) {
-        if (e.code != BEM_ERR_NOCONV) throw;
-        st.nonconverged += 1;
-        it = c.stats.last_iters;
-        rr = c.stats.last_relres;
+    const double *phi_hat = s.yf.p + 3 * N;
+    auto solve_from = [&](double *q, int &iters, double &relres, double &res0) {
+        try {
+            solve_internal(c, phi_hat, q, &iters, &relres);
+        } catch (const Error &e) {
+            if (e.code != BEM_ERR_NOCONV) throw;
+            st.nonconverged += 1;
+            iters = c.stats.last_iters;
+            relres = c.stats.last_relres;
+        }
+        res0 = c.res_hist.empty() ? 0.0 : c.res_hist.front();
+    };
+    const bool learned = mlp_active(c);
+    if (learned) {
+        // samples and guesses only in the Adams-Bashforth phase (one solve per step)
+        mlp_before_solve(c, phi_hat, s.q.p, s.nhist >= 5);  // with the network in use, s.q becomes its guess
+        if (mlp_compare(c)) {                 // the same solve from the fallback q_prev, for the record
+            s.ytmp.resize(4 * N);
+            DevBuf<double> qf;
+            qf.resize(N);
+            BEM_CUDA(cudaMemcpyAsync(qf.p, mlp_qprev(c), N * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+            int itf = 0;
+            double rrf = 0.0, r0f = 0.0;
+            solve_from(qf.p, itf, rrf, r0f);
+            MlpStats &ms = mlp_stats(c);
+            ms.iters_fallback += itf;
+            ms.res0_fallback += r0f;
+            st.mvps += c.stats.last_mvps + 1;
+        }
+    }
+    double res0 = 0.0;
+    solve_from(s.q.p, it, rr, res0);
+    if (learned) {
+        mlp_after_solve(c, s.q.p);
+        if (mlp_compare(c)) {
+            MlpStats &ms = mlp_stats(c);
+            ms.solves += 1;
+            ms.iters_guess += it;
+            ms.res0_guess += res0;
+        }
     }
     st.gmres_iters += it;
     st.mvps += c.stats.last_mvps + 1;  // GMRES products plus the right-hand side
@@ -458,69 +491,17 @@ void rhs(Context &c, StepState &s, const double *y, double t, double *f, bem_ste
 
 }  // namespace
 
-void step_init(Context &c, const double *phi0_dev, const double *q0_dev, const bem_step_params &sp) {
-    if (!c.mesh_ok) fail(BEM_ERR_NOT_BUILT, "no mesh uploaded");
-    if (sp.pf < 0 || sp.pf > 11) fail(BEM_ERR_ARG, "pf must be in 0..11");
-    if (!(sp.pa > 0.0) && !(sp.dt > 0.0)) fail(BEM_ERR_ARG, "pa must be > 0 unless dt is given");
-    StepState &s = state_of(c);
+// One least-squares spherical-harmonic basis (degrees 0..pf-1) per distinct initial bubble
+// shape: bubbles whose unit directions from their centroid coincide share G and G+.
+void build_sh_basis(Context &c, int pf, ShBasis &B, int *bad, const double *xyz) {
     const int64_t N = c.N, M = c.M;
     cudaStream_t st = c.stream;
-    const int tb = 256;
-    s.sp = sp;
-    s.t = 0.0;
-    s.steps = 0;
-    s.nhist = 0;
-    for (int i = 0; i < 5; ++i) s.order[i] = i;
-    for (auto *b : {&s.y, &s.k1, &s.k2, &s.k3, &s.k4, &s.ytmp, &s.yf, &s.f}) b->resize(4 * N);
-    s.hist.resize(5 * 4 * N);
-    s.q.resize(N);
-    if (q0_dev) BEM_CUDA(cudaMemcpyAsync(s.q.p, q0_dev, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    else BEM_CUDA(cudaMemsetAsync(s.q.p, 0, N * sizeof(double), st));
-    BEM_CUDA(cudaMemcpyAsync(s.y.p, c.xyz.p, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    BEM_CUDA(cudaMemcpyAsync(s.y.p + 3 * N, phi0_dev, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    s.voff.resize(M + 1);
-    s.toff.resize(M + 1);
-    BEM_CUDA(cudaMemcpyAsync(s.voff.p, c.vert_off.data(), (M + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-    BEM_CUDA(cudaMemcpyAsync(s.toff.p, c.tri_off.data(), (M + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-    s.bub_of.resize(N);
-    k_bubble_of<<<(unsigned)M, 256, 0, st>>>((int)M, s.voff.p, s.bub_of.p);
-    BEM_LAUNCH_CHECK();
-    // five-neighbour lists
-    DevBuf<int> bad;
-    bad.resize(1);
-    BEM_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
-    s.nbr5.resize(5 * N);
-    k_nbr5<<<div_up(N, tb), tb, 0, st>>>(N, c.T, c.tri.p, c.v2t_off.p, c.v2t.p, s.nbr5.p, bad.p);
-    BEM_LAUNCH_CHECK();
-    // V_m0, a_m0 of the initial mesh
-    s.V.resize(M);
-    s.V0.resize(M);
-    s.a0.resize(M);
-    s.pg.resize(M);
-    k_volumes<<<(unsigned)M, 256, 0, st>>>(N, c.T, s.toff.p, c.tri.p, c.xyz.p, s.V.p);
-    BEM_LAUNCH_CHECK();
-    k_init_bubbles<<<div_up(M, tb), tb, 0, st>>>((int)M, s.V.p, s.V0.p, s.a0.p);
-    BEM_LAUNCH_CHECK();
-    // step size, Eq. (3.12)
-    if (sp.dt > 0.0) {
-        s.dt = sp.dt;
-    } else {
-        int nb = std::min<int64_t>(div_up(c.T, tb), 1024);
-        DevBuf<double> part;
-        part.resize(nb);
-        k_min_edge<<<nb, tb, 0, st>>>(c.T, N, c.tri.p, c.xyz.p, part.p);
-        BEM_LAUNCH_CHECK();
-        std::vector<double> h(nb);
-        BEM_CUDA(cudaMemcpyAsync(h.data(), part.p, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
-        BEM_CUDA(cudaStreamSynchronize(st));
-        double mn = *std::min_element(h.begin(), h.end());
-        s.dt = sp.courant * mn / std::sqrt(sp.pa);
-    }
-    // shape filters: one per distinct set of unit directions from the bubble centroid
-    s.Pf = sp.pf * sp.pf;
-    if (sp.pf > 0) {
+    if (!xyz) xyz = c.xyz.p;
+    B.pf = pf;
+    B.Pf = pf * pf;
+    if (pf > 0) {
         std::vector<double> hx(3 * N);
-        BEM_CUDA(cudaMemcpyAsync(hx.data(), c.xyz.p, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, st));
+        BEM_CUDA(cudaMemcpyAsync(hx.data(), xyz, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, st));
         BEM_CUDA(cudaStreamSynchronize(st));
         struct Shape {
             int64_t rep;
@@ -563,35 +544,100 @@ void step_init(Context &c, const double *phi0_dev, const double *q0_dev, const b
                 if (same) found = (int)k;
             }
             if (found < 0) {
-                if (nd < s.Pf) fail(BEM_ERR_MESH, "bubble with fewer vertices than filter coefficients");
+                if (nd < B.Pf) fail(BEM_ERR_MESH, "bubble with fewer vertices than filter coefficients");
                 shapes.push_back({m, nd, cx, cy, cz});
                 found = (int)shapes.size() - 1;
             }
             shape_of[m] = found;
         }
         std::vector<int64_t> goff(shapes.size() + 1, 0);
-        for (size_t k = 0; k < shapes.size(); ++k) goff[k + 1] = goff[k] + (int64_t)shapes[k].nd * s.Pf;
-        s.G.resize(goff.back());
-        s.Gp.resize(goff.back());
+        for (size_t k = 0; k < shapes.size(); ++k) goff[k + 1] = goff[k] + (int64_t)shapes[k].nd * B.Pf;
+        B.G.resize(goff.back());
+        B.Gp.resize(goff.back());
         DevBuf<double> scratch, A;
         int ndmax = 0;
         for (auto &sh : shapes) ndmax = std::max(ndmax, sh.nd);
-        scratch.resize((size_t)ndmax * s.Pf);
-        A.resize((size_t)s.Pf * s.Pf);
+        scratch.resize((size_t)ndmax * B.Pf);
+        A.resize((size_t)B.Pf * B.Pf);
         for (size_t k = 0; k < shapes.size(); ++k) {
             const Shape &sh = shapes[k];
-            k_filter_G<<<div_up(sh.nd, 128), 128, 0, st>>>(sh.nd, c.xyz.p, N, c.vert_off[sh.rep], sh.cx, sh.cy, sh.cz,
-                                                           sp.pf, s.G.p + goff[k], scratch.p);
+            k_filter_G<<<div_up(sh.nd, 128), 128, 0, st>>>(sh.nd, xyz, N, c.vert_off[sh.rep], sh.cx, sh.cy, sh.cz,
+                                                           pf, B.G.p + goff[k], scratch.p);
             BEM_LAUNCH_CHECK();
-            k_filter_pinv<<<1, 256, 0, st>>>(sh.nd, s.Pf, s.G.p + goff[k], A.p, s.Gp.p + goff[k], bad.p);
+            k_filter_pinv<<<1, 256, 0, st>>>(sh.nd, B.Pf, B.G.p + goff[k], A.p, B.Gp.p + goff[k], bad);
             BEM_LAUNCH_CHECK();
         }
-        s.shape_of.resize(M);
-        s.g_off.resize(shapes.size());
-        BEM_CUDA(cudaMemcpyAsync(s.shape_of.p, shape_of.data(), M * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        BEM_CUDA(cudaMemcpyAsync(s.g_off.p, goff.data(), shapes.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        B.shape_of.resize(M);
+        B.g_off.resize(shapes.size());
+        BEM_CUDA(cudaMemcpyAsync(B.shape_of.p, shape_of.data(), M * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        BEM_CUDA(cudaMemcpyAsync(B.g_off.p, goff.data(), shapes.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
         BEM_CUDA(cudaStreamSynchronize(st));
     }
+}
+
+void step_init(Context &c, const double *phi0_dev, const double *q0_dev, const bem_step_params &sp) {
+    if (!c.mesh_ok) fail(BEM_ERR_NOT_BUILT, "no mesh uploaded");
+    if (sp.pf < 0 || sp.pf > 11) fail(BEM_ERR_ARG, "pf must be in 0..11");
+    if (!(sp.pa > 0.0) && !(sp.dt > 0.0)) fail(BEM_ERR_ARG, "pa must be > 0 unless dt is given");
+    StepState &s = state_of(c);
+    const int64_t N = c.N, M = c.M;
+    cudaStream_t st = c.stream;
+    const int tb = 256;
+    s.sp = sp;
+    s.t = 0.0;
+    s.steps = 0;
+    s.nhist = 0;
+    for (int i = 0; i < 5; ++i) s.order[i] = i;
+    for (auto *b : {&s.y, &s.k1, &s.k2, &s.k3, &s.k4, &s.ytmp, &s.yf, &s.f}) b->resize(4 * N);
+    s.hist.resize(5 * 4 * N);
+    s.q.resize(N);
+    if (q0_dev) BEM_CUDA(cudaMemcpyAsync(s.q.p, q0_dev, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    else BEM_CUDA(cudaMemsetAsync(s.q.p, 0, N * sizeof(double), st));
+    BEM_CUDA(cudaMemcpyAsync(s.y.p, c.xyz.p, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    s.x0.resize(3 * N);
+    BEM_CUDA(cudaMemcpyAsync(s.x0.p, c.xyz.p, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    BEM_CUDA(cudaMemcpyAsync(s.y.p + 3 * N, phi0_dev, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    s.voff.resize(M + 1);
+    s.toff.resize(M + 1);
+    BEM_CUDA(cudaMemcpyAsync(s.voff.p, c.vert_off.data(), (M + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    BEM_CUDA(cudaMemcpyAsync(s.toff.p, c.tri_off.data(), (M + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    s.bub_of.resize(N);
+    k_bubble_of<<<(unsigned)M, 256, 0, st>>>((int)M, s.voff.p, s.bub_of.p);
+    BEM_LAUNCH_CHECK();
+    // five-neighbour lists
+    DevBuf<int> bad;
+    bad.resize(1);
+    BEM_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+    s.nbr5.resize(5 * N);
+    k_nbr5<<<div_up(N, tb), tb, 0, st>>>(N, c.T, c.tri.p, c.v2t_off.p, c.v2t.p, s.nbr5.p, bad.p);
+    BEM_LAUNCH_CHECK();
+    // V_m0, a_m0 of the initial mesh
+    s.V.resize(M);
+    s.V0.resize(M);
+    s.a0.resize(M);
+    s.pg.resize(M);
+    k_volumes<<<(unsigned)M, 256, 0, st>>>(N, c.T, s.toff.p, c.tri.p, c.xyz.p, s.V.p);
+    BEM_LAUNCH_CHECK();
+    k_init_bubbles<<<div_up(M, tb), tb, 0, st>>>((int)M, s.V.p, s.V0.p, s.a0.p);
+    BEM_LAUNCH_CHECK();
+    // step size, Eq. (3.12)
+    if (sp.dt > 0.0) {
+        s.dt = sp.dt;
+    } else {
+        int nb = std::min<int64_t>(div_up(c.T, tb), 1024);
+        DevBuf<double> part;
+        part.resize(nb);
+        k_min_edge<<<nb, tb, 0, st>>>(c.T, N, c.tri.p, c.xyz.p, part.p);
+        BEM_LAUNCH_CHECK();
+        std::vector<double> h(nb);
+        BEM_CUDA(cudaMemcpyAsync(h.data(), part.p, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+        BEM_CUDA(cudaStreamSynchronize(st));
+        double mn = *std::min_element(h.begin(), h.end());
+        s.dt = sp.courant * mn / std::sqrt(sp.pa);
+    }
+    // shape filters: one per distinct set of unit directions from the bubble centroid
+    build_sh_basis(c, sp.pf, s.filt, bad.p);
+    s.Pf = s.filt.Pf;
     int hb = 0;
     BEM_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     BEM_CUDA(cudaStreamSynchronize(st));
@@ -669,5 +715,11 @@ void step_get_state(Context &c, double *xyz, double *phi, double *q, double *t) 
 }
 
 void step_free(StepState *s) { delete s; }
+
+const double *step_initial_xyz(Context &c) {
+    StepState &s = state_of(c);
+    if (!s.ready) fail(BEM_ERR_NOT_BUILT, "bem_step_init has not been called");
+    return s.x0.p;
+}
 
 }  // namespace bem

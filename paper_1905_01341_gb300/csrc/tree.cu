@@ -284,13 +284,61 @@ __global__ void k_keys(int64_t N, const double *__restrict__ xyz, double ox, dou
     idx[i] = (int32_t)i;
 }
 
+// Clusters: the key is (cluster << 24) | 24-bit Morton key of depth 8 in the cluster's own cube,
+// so sorting groups clusters and shifting right by 3 (8 - l) gives (cluster << 3l) | box key.
+constexpr int kClusterDeep = 8;
+
+__global__ void k_cluster_bbox(const int64_t *__restrict__ cvoff, int64_t N, const double *__restrict__ xyz,
+                               double *__restrict__ out) {
+    __shared__ double sm[6][256];
+    const int c = blockIdx.x;
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = cvoff[c] + threadIdx.x; i < cvoff[c + 1]; i += blockDim.x)
+        for (int d = 0; d < 3; ++d) {
+            double v = xyz[d * N + i];
+            mn[d] = fmin(mn[d], v);
+            mx[d] = fmax(mx[d], v);
+        }
+    for (int d = 0; d < 3; ++d) {
+        sm[d][threadIdx.x] = mn[d];
+        sm[3 + d][threadIdx.x] = mx[d];
+    }
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int d = 0; d < 3; ++d) {
+                sm[d][threadIdx.x] = fmin(sm[d][threadIdx.x], sm[d][threadIdx.x + s]);
+                sm[3 + d][threadIdx.x] = fmax(sm[3 + d][threadIdx.x], sm[3 + d][threadIdx.x + s]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x < 6) out[c * 6 + threadIdx.x] = sm[threadIdx.x][0];
+}
+
+// cube[c] = (origin x, y, z, 1 / size)
+__global__ void k_keys_clusters(int64_t N, const double *__restrict__ xyz, const int32_t *__restrict__ vcid,
+                                const double *__restrict__ cube, uint32_t *__restrict__ key, int32_t *__restrict__ idx) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int c = vcid[i];
+    const double scale = cube[4 * c + 3] * (double)(1 << kClusterDeep);
+    int g[3];
+    for (int d = 0; d < 3; ++d) {
+        double u = (xyz[d * N + i] - cube[4 * c + d]) * scale;
+        int gi = (int)floor(u);
+        g[d] = min(max(gi, 0), (1 << kClusterDeep) - 1);
+    }
+    key[i] = ((uint32_t)c << (3 * kClusterDeep)) | morton(g[0], g[1], g[2]);
+    idx[i] = (int32_t)i;
+}
+
 // unique[l] += number of i in [1, N) where the level-l prefix of the key changes
-__global__ void k_level_counts(int64_t N, const uint32_t *__restrict__ key, int32_t *__restrict__ cnt) {
+__global__ void k_level_counts(int64_t N, int deep, const uint32_t *__restrict__ key, int32_t *__restrict__ cnt) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     bool valid = i >= 1 && i < N;
     uint32_t a = valid ? key[i] : 0u, b = valid ? key[i - 1] : 0u;
-    for (int l = 0; l <= kDeepLevel; ++l) {
-        int sh = 3 * (kDeepLevel - l);
+    for (int l = 0; l <= deep; ++l) {
+        int sh = 3 * (deep - l);
         int f = (valid && (a >> sh) != (b >> sh)) ? 1 : 0;
         int tot = __reduce_add_sync(0xffffffffu, f);
         if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&cnt[l], tot);
@@ -353,7 +401,8 @@ __global__ void k_neighbours(int nleaf, int L, const uint32_t *__restrict__ lkey
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nleaf) return;
     int gx, gy, gz;
-    demorton(lkey[b], gx, gy, gz);
+    const uint32_t mask = (1u << (3 * L)) - 1u, pre = lkey[b] & ~mask;  // cluster prefix
+    demorton(lkey[b] & mask, gx, gy, gz);
     int lim = 1 << L, c = 0;
     long long src = 0;
     for (int dx = -1; dx <= 1; ++dx)
@@ -361,7 +410,7 @@ __global__ void k_neighbours(int nleaf, int L, const uint32_t *__restrict__ lkey
             for (int dz = -1; dz <= 1; ++dz) {
                 int x = gx + dx, y = gy + dy, z = gz + dz;
                 if (x < 0 || y < 0 || z < 0 || x >= lim || y >= lim || z >= lim) continue;
-                int f = find_box(lkey, nleaf, morton(x, y, z));
+                int f = find_box(lkey, nleaf, pre | morton(x, y, z));
                 if (f < 0) continue;
                 nbr[b * 27 + c] = f;
                 nd[(b * 27 + c) * 4 + 0] = (int8_t)dx;
@@ -399,7 +448,10 @@ __global__ void k_m2l_lists(int n, int l, const uint32_t *__restrict__ key, cons
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n) return;
     int gx, gy, gz;
-    demorton(key[b], gx, gy, gz);
+    const uint32_t mask = (1u << (3 * l)) - 1u;
+    const uint32_t cl = key[b] >> (3 * l);  // cluster id (0 without clusters)
+    const uint32_t pre = cl << (3 * l), ppre = cl << (3 * (l - 1));
+    demorton(key[b] & mask, gx, gy, gz);
     int px = gx >> 1, py = gy >> 1, pz = gz >> 1;
     int plim = 1 << (l - 1);
     int c = 0;
@@ -409,12 +461,12 @@ __global__ void k_m2l_lists(int n, int l, const uint32_t *__restrict__ key, cons
             for (int dz = -1; dz <= 1; ++dz) {
                 int x = px + dx, y = py + dy, z = pz + dz;
                 if (x < 0 || y < 0 || z < 0 || x >= plim || y >= plim || z >= plim) continue;
-                if (find_box(pkey, np, morton(x, y, z)) < 0) continue;
+                if (find_box(pkey, np, ppre | morton(x, y, z)) < 0) continue;
                 for (int oc = 0; oc < 8; ++oc) {
                     int cx = 2 * x + ((oc >> 2) & 1), cy = 2 * y + ((oc >> 1) & 1), cz = 2 * z + (oc & 1);
                     int ddx = cx - gx, ddy = cy - gy, ddz = cz - gz;
                     if (ddx >= -1 && ddx <= 1 && ddy >= -1 && ddy <= 1 && ddz >= -1 && ddz <= 1) continue;
-                    int f = find_box(key, n, morton(cx, cy, cz));
+                    int f = find_box(key, n, pre | morton(cx, cy, cz));
                     if (f < 0) continue;
                     if (pass) {
                         tgt[o + c] = gbase + b;
@@ -470,20 +522,22 @@ __global__ void k_up_pairs(int n, const int32_t *__restrict__ id, int base, cons
 
 // Sorted-order point data: leaf-local coordinates (units of the leaf box, centred), normals
 // and weights.
-__global__ void k_sorted_points(int64_t N, int L, const int32_t *__restrict__ perm,
+__global__ void k_sorted_points(int64_t N, int L, int deep, const int32_t *__restrict__ perm,
                                 const uint32_t *__restrict__ key, const double *__restrict__ xyz,
                                 const double *__restrict__ nrm, const double *__restrict__ s,
-                                double ox, double oy, double oz, double inv_size,
+                                const double *__restrict__ cube, const int32_t *__restrict__ vcid,
                                 double *__restrict__ loc64, float *__restrict__ loc32,
                                 double *__restrict__ n64, float *__restrict__ n32,
-                                double *__restrict__ s_sorted) {
+                                double *__restrict__ s_sorted, double *__restrict__ ih) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N) return;
     int j = perm[i];
     int g[3];
-    demorton(key[i] >> (3 * (kDeepLevel - L)), g[0], g[1], g[2]);
-    double o[3] = {ox, oy, oz};
-    double scale = inv_size * (double)(1 << L);
+    demorton((key[i] >> (3 * (deep - L))) & ((1u << (3 * L)) - 1u), g[0], g[1], g[2]);
+    const int c = vcid ? vcid[j] : 0;
+    double o[3] = {cube[4 * c], cube[4 * c + 1], cube[4 * c + 2]};
+    double scale = cube[4 * c + 3] * (double)(1 << L);
+    ih[i] = scale;
     for (int d = 0; d < 3; ++d) {
         double u = (xyz[d * N + j] - o[d]) * scale - ((double)g[d] + 0.5);
         loc64[d * N + i] = u;
@@ -504,7 +558,12 @@ void build_tree(Context &c) {
     t.N = N;
     const int tb = 256;
 
-    // 1. bounding cube
+    const bool clusters = c.C > 1;
+    t.deep = clusters ? kClusterDeep : kDeepLevel;
+    DevBuf<double> cube;  // per cluster: origin x, y, z, 1 / size
+    cube.resize(4 * std::max<int64_t>(c.C, 1));
+    std::vector<double> hcube(4 * std::max<int64_t>(c.C, 1));
+    // 1. bounding cube (one per cluster)
     int nbb = std::min<int64_t>(div_up(N, tb), 1024);
     DevBuf<double> part;
     part.resize((size_t)nbb * 6);
@@ -527,33 +586,61 @@ void build_tree(Context &c) {
     if (ext <= 0.0) ext = 1.0;
     t.size = ext * (1.0 + 1.0 / 1024.0);
     for (int d = 0; d < 3; ++d) t.origin[d] = 0.5 * (mn[d] + mx[d]) - 0.5 * t.size;
+    for (int d = 0; d < 3; ++d) hcube[d] = t.origin[d];
+    hcube[3] = 1.0 / t.size;
+    if (clusters) {
+        std::vector<int64_t> cvoff(c.C + 1);
+        for (int64_t k = 0; k <= c.C; ++k) cvoff[k] = c.vert_off[c.cluster_boff[k]];
+        DevBuf<int64_t> dcv;
+        DevBuf<double> cb;
+        dcv.resize(c.C + 1);
+        cb.resize(6 * c.C);
+        BEM_CUDA(cudaMemcpyAsync(dcv.p, cvoff.data(), (c.C + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        k_cluster_bbox<<<(unsigned)c.C, 256, 0, st>>>(dcv.p, N, c.xyz.p, cb.p);
+        BEM_LAUNCH_CHECK();
+        std::vector<double> hb(6 * c.C);
+        BEM_CUDA(cudaMemcpyAsync(hb.data(), cb.p, hb.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        BEM_CUDA(cudaStreamSynchronize(st));
+        for (int64_t k = 0; k < c.C; ++k) {
+            double e = 0.0;
+            for (int d = 0; d < 3; ++d) e = std::max(e, hb[6 * k + 3 + d] - hb[6 * k + d]);
+            if (!(e > 0.0)) e = 1.0;
+            double size = e * (1.0 + 1.0 / 1024.0);
+            for (int d = 0; d < 3; ++d) hcube[4 * k + d] = 0.5 * (hb[6 * k + d] + hb[6 * k + 3 + d]) - 0.5 * size;
+            hcube[4 * k + 3] = 1.0 / size;
+        }
+    }
+    BEM_CUDA(cudaMemcpyAsync(cube.p, hcube.data(), hcube.size() * sizeof(double), cudaMemcpyHostToDevice, st));
 
-    // 2. Morton keys at depth kDeepLevel and sort
+    // 2. Morton keys at the key depth and sort
     t.key.resize(N);
     t.perm.resize(N);
     DevBuf<uint32_t> ktmp;
     DevBuf<int32_t> vtmp;
     ktmp.resize(N);
     vtmp.resize(N);
-    k_keys<<<div_up(N, tb), tb, 0, st>>>(N, c.xyz.p, t.origin[0], t.origin[1], t.origin[2], 1.0 / t.size,
-                                          t.key.p, t.perm.p);
+    if (clusters)
+        k_keys_clusters<<<div_up(N, tb), tb, 0, st>>>(N, c.xyz.p, c.vcid.p, cube.p, t.key.p, t.perm.p);
+    else
+        k_keys<<<div_up(N, tb), tb, 0, st>>>(N, c.xyz.p, t.origin[0], t.origin[1], t.origin[2], 1.0 / t.size,
+                                              t.key.p, t.perm.p);
     BEM_LAUNCH_CHECK();
-    radix_sort_u32(t.key.p, t.perm.p, N, 3 * kDeepLevel, ktmp.p, vtmp.p, st);
+    radix_sort_u32(t.key.p, t.perm.p, N, clusters ? 32 : 3 * kDeepLevel, ktmp.p, vtmp.p, st);
 
     // 3. unique boxes per level; choose l_max
     DevBuf<int32_t> lc;
     lc.resize(kDeepLevel + 1);
     BEM_CUDA(cudaMemsetAsync(lc.p, 0, (kDeepLevel + 1) * sizeof(int32_t), st));
-    k_level_counts<<<div_up(N, tb), tb, 0, st>>>(N, t.key.p, lc.p);
+    k_level_counts<<<div_up(N, tb), tb, 0, st>>>(N, t.deep, t.key.p, lc.p);
     BEM_LAUNCH_CHECK();
-    int32_t hc[kDeepLevel + 1];
-    BEM_CUDA(cudaMemcpyAsync(hc, lc.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    int32_t hc[kDeepLevel + 1] = {};
+    BEM_CUDA(cudaMemcpyAsync(hc, lc.p, (t.deep + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     BEM_CUDA(cudaStreamSynchronize(st));
     int L = 2;
     if (c.prm.fixed_level > 0) {
-        L = c.prm.fixed_level;
+        L = std::min(c.prm.fixed_level, t.deep);
     } else {
-        for (int l = 2; l <= kDeepLevel; ++l)
+        for (int l = 2; l <= t.deep; ++l)
             if ((double)N / (double)(hc[l] + 1) >= (double)c.prm.leaf_target) L = l;
     }
     t.L = L;
@@ -574,7 +661,7 @@ void build_tree(Context &c) {
     DevBuf<int32_t> flag, ex;
     flag.resize(N);
     ex.resize(N);
-    int shiftL = 3 * (kDeepLevel - L);
+    int shiftL = 3 * (t.deep - L);
     k_flags_points<<<div_up(N, tb), tb, 0, st>>>(N, t.key.p, shiftL, flag.p);
     BEM_LAUNCH_CHECK();
     exclusive_scan_i32(flag.p, ex.p, N, nullptr, st);
@@ -591,7 +678,7 @@ void build_tree(Context &c) {
                                                       t.parent.p + t.base[l], t.base[l - 1]);
         BEM_LAUNCH_CHECK();
     }
-    BEM_CUDA(cudaMemsetAsync(t.parent.p, 0xff, sizeof(int32_t), st));  // root has no parent
+    BEM_CUDA(cudaMemsetAsync(t.parent.p, 0xff, t.nb[0] * sizeof(int32_t), st));  // roots have no parent
     for (int l = 0; l <= L; ++l) {
         int n = t.nb[l];
         k_box_counts<<<div_up(n, tb), tb, 0, st>>>(n, t.bstart.p + t.base[l], (int32_t)N, t.bcount.p + t.base[l]);
@@ -749,9 +836,10 @@ void build_tree(Context &c) {
     t.nrm64.resize(3 * N);
     t.nrm32.resize(3 * N);
     t.s_sorted.resize(N);
-    k_sorted_points<<<div_up(N, tb), tb, 0, st>>>(N, L, t.perm.p, t.key.p, c.xyz.p, c.nrm.p, c.s.p, t.origin[0],
-                                                   t.origin[1], t.origin[2], 1.0 / t.size, t.loc64.p, t.loc32.p,
-                                                   t.nrm64.p, t.nrm32.p, t.s_sorted.p);
+    t.ih.resize(N);
+    k_sorted_points<<<div_up(N, tb), tb, 0, st>>>(N, L, t.deep, t.perm.p, t.key.p, c.xyz.p, c.nrm.p, c.s.p, cube.p,
+                                                   clusters ? c.vcid.p : nullptr, t.loc64.p, t.loc32.p, t.nrm64.p,
+                                                   t.nrm32.p, t.s_sorted.p, t.ih.p);
     BEM_LAUNCH_CHECK();
     unsigned long long hpairs = 0;
     BEM_CUDA(cudaMemcpyAsync(&hpairs, pairs.p, sizeof(hpairs), cudaMemcpyDeviceToHost, st));

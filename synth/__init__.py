@@ -32,6 +32,7 @@ __all__ = [
     "workload_single_bubble_l6",
     "workload_cluster",
     "workload_uneven_clusters",
+    "concat_meshes",
 ]
 
 
@@ -388,3 +389,23 @@ def workload_uneven_clusters(n_clusters: int = 64, seed: int = 5, max_bubbles: i
         phi = cluster_potential(mesh, 6, 0.1, rng)
         out.append((mesh, phi))
     return out
+
+
+def concat_meshes(meshes, phis=None):
+    """Concatenate independent meshes (e.g. separate clusters) into one Mesh; returns
+    (mesh, phi or None, bubble_off) where cluster c owns bubbles bubble_off[c]..bubble_off[c+1]-1."""
+    xs, ts, voff, toff, boff, cen, rad = [], [], [0], [0], [0], [], []
+    for m in meshes:
+        ts.append(m.tri + voff[-1])
+        xs.append(m.xyz)
+        for b in range(m.m):
+            voff.append(voff[-1] + int(m.vert_off[b + 1] - m.vert_off[b]))
+            toff.append(toff[-1] + int(m.tri_off[b + 1] - m.tri_off[b]))
+        boff.append(boff[-1] + m.m)
+        cen.append(m.centres)
+        rad.append(m.radii)
+    mesh = Mesh(xyz=np.ascontiguousarray(np.concatenate(xs)), tri=np.ascontiguousarray(np.concatenate(ts), np.int32),
+                vert_off=np.asarray(voff, np.int64), tri_off=np.asarray(toff, np.int64),
+                centres=np.concatenate(cen), radii=np.concatenate(rad), meta={"kind": "clusters", "clusters": len(meshes)})
+    phi = None if phis is None else np.ascontiguousarray(np.concatenate(phis))
+    return mesh, phi, np.asarray(boff, np.int64)

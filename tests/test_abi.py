@@ -54,7 +54,7 @@ def test_params_default_host_only(lib):
 
     p = bem.bem_params_default()
     assert p.p_fmm == 14 and p.precision == bem.BEM_PREC_MIXED and p.gmres_tol == 1e-6
-    assert p.gmres_maxit == 100 and p.diag_precision == -1
+    assert p.gmres_maxit == 100 and p.diag_precision == -1 and p.m2l_tensor_cores == 1
     p2 = bem.bem_params_default(p_fmm=16, precision=bem.BEM_PREC_FP64)
     assert p2.p_fmm == 16 and p2.precision == 0
 
@@ -64,10 +64,12 @@ def test_struct_layouts_match_header():
 
     from paper_1905_01341_gb300 import bem
 
-    # int32 x 8 + double = 40 bytes; stats: 4 x int64 + 4 x int32 + 2 x double + int64 = 72 bytes
-    assert ctypes.sizeof(bem.bem_params) == 40
+    # int32 x 10 + double = 48 bytes; stats: 4 x int64 + 4 x int32 + 2 x double + int64 = 72
+    assert ctypes.sizeof(bem.bem_params) == 48
+    assert bem.bem_params_default().gmres_precond == 0
     assert ctypes.sizeof(bem.bem_stats) == 72
     assert ctypes.sizeof(bem.bem_step_params) == 56 and ctypes.sizeof(bem.bem_step_stats) == 48
+    assert ctypes.sizeof(bem.bem_mlp_summary) == 80
     sp = bem.bem_step_params_default()
     assert sp.pf == 6 and sp.courant == 0.1 and sp.kappa == 1.4
     assert [bem.bem_phase_name(i) for i in range(bem.BEM_NUM_PHASES)][6] == "m2l"

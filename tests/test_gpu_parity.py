@@ -230,3 +230,68 @@ def test_residual_history_and_mvp_count():
     assert all(a >= b for a, b in zip(h[1:-2], h[2:-1]))  # GMRES estimates never increase
     assert ctx.stats()["last_mvps"] == it + 2
     ctx.close()
+
+
+@pytest.mark.parametrize("p", [8, 14, 16])
+def test_tensor_core_m2l_matches_cuda_core_m2l(p):
+    """The tcgen05 M2L (three-piece TF32 split, FP32 accumulation) against the FP32 CUDA-core
+    M2L: measured against the FP64 FMM at the same p (same truncation, so only arithmetic
+    error is left), the tensor-core product is as accurate as the CUDA-core one, and both stay
+    within the mixed-precision bound of the oracle."""
+    bem = _bem()
+    mesh = small_cluster(20, 3, seed=11)
+    rng = np.random.Generator(np.random.PCG64(12))
+    xL, xM = rng.standard_normal(mesh.n), rng.standard_normal(mesh.n)
+    outs = {}
+    for key, prec, tc in (("tc", 1, 1), ("cc", 1, 0), ("f64", 0, 0)):
+        ctx = make_ctx(mesh, mvp=bem.BEM_MVP_FMM, precision=prec, p_fmm=p, leaf_target=32, m2l_tensor_cores=tc,
+                       diag_precision=0)
+        o = torch.zeros(mesh.n, dtype=torch.float64, device="cuda")
+        ctx.apply(0.7, dev(xL), -1.3, dev(xM), o)
+        outs[key] = o.cpu().numpy()
+        ctx.close()
+    e_tc, e_cc = rel(outs["tc"], outs["f64"]), rel(outs["cc"], outs["f64"])
+    print("p=%d arithmetic error vs FP64 FMM: tensor cores %.2e, CUDA cores %.2e" % (p, e_tc, e_cc))
+    assert e_tc < 2.0 * e_cc + 1e-7
+    if p >= 14:
+        ref = oracle.BemOperator(mesh.xyz, mesh.tri).apply(0.7, xL, -1.3, xM)
+        assert rel(outs["tc"], ref) < 1e-5
+
+
+def test_mixed_tensor_core_solve_converges_below_1e6():
+    """GMRES on the mixed-precision operator (tensor-core M2L) reaches 1e-7: the operator's
+    rounding noise stays below the tolerance the method is run at."""
+    bem = _bem()
+    mesh = small_cluster(20, 3, seed=11)
+    rng = np.random.Generator(np.random.PCG64(15))
+    phi = synth.cluster_potential(mesh, 4, 0.1, rng) + 1.0
+    ctx = make_ctx(mesh, mvp=bem.BEM_MVP_FMM, precision=bem.BEM_PREC_MIXED, p_fmm=14, leaf_target=32,
+                   gmres_tol=1e-7, gmres_maxit=300, gmres_restart=100)
+    q = torch.zeros(mesh.n, dtype=torch.float64, device="cuda")
+    it, rr = ctx.solve(dev(phi), q, raise_on_noconv=False)
+    print("mixed tensor-core solve: %d iterations, relres %.2e" % (it, rr))
+    assert rr <= 1e-7
+    ctx.close()
+
+
+def test_jacobi_preconditioned_gmres_same_solution_fewer_iterations():
+    """Right Jacobi preconditioning (optional; the paper's GMRES is unpreconditioned) solves
+    the same system: both solutions agree with the oracle's to the solve tolerance, and on a
+    cluster of bubbles with different radii it needs fewer iterations."""
+    bem = _bem()
+    mesh = small_cluster(12, 3, seed=13)
+    rng = np.random.Generator(np.random.PCG64(14))
+    phi = synth.cluster_potential(mesh, 4, 0.1, rng) + 1.0
+    ref = oracle.BemOperator(mesh.xyz, mesh.tri)
+    qref, _, _, _ = oracle.solve(ref, phi, tol=1e-12, maxit=400, restart=100)
+    res = {}
+    for pc in (0, 1):
+        ctx = make_ctx(mesh, mvp=bem.BEM_MVP_DIRECT, precision=bem.BEM_PREC_FP64, gmres_tol=1e-10,
+                       gmres_maxit=400, gmres_restart=100, gmres_precond=pc)
+        q = torch.zeros(mesh.n, dtype=torch.float64, device="cuda")
+        it, rr = ctx.solve(dev(phi), q)
+        assert rr <= 1e-10
+        res[pc] = (it, q.cpu().numpy())
+        ctx.close()
+    assert rel(res[0][1], qref) < 1e-8 and rel(res[1][1], qref) < 1e-8
+    assert res[1][0] < res[0][0]

@@ -1,0 +1,53 @@
+"""FMM accuracy on random monopoles in the unit cube, the setting of Table 1 (Section 3.9):
+relative L2 error of the product at sqrt(N) random checkpoints against the direct sum,
+for p_fmm = 4..20, FP64 and mixed precision."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "table1_fmm_error.txt")
+
+
+def table1():
+    rows = {}
+    for line in open(GOLDEN):
+        if line.strip() and not line.startswith("#"):
+            v = line.split()
+            rows[int(v[0])] = {"single": float(v[1]), "double": float(v[2])}
+    return rows
+
+
+def test_table1_error_levels_131072():
+    from paper_1905_01341_gb300 import bem
+
+    N = 131072
+    xyz, q = synth.random_cube_points(N, seed=31)
+    recv = oracle.checkpoint_receivers(N, oracle.sqrt_n(N), seed=32)
+    ref = oracle.offdiag_apply(xyz, np.ones(N), np.tile([0.0, 0.0, 1.0], (N, 1)), 1.0, q, 0.0, None, recv)
+    paper = table1()
+    errs = {}
+    for prec, col in ((bem.BEM_PREC_FP64, "double"), (bem.BEM_PREC_MIXED, "single")):
+        for p in (4, 8, 12, 16, 20):
+            ctx = bem.BemContext(p_fmm=p, precision=prec, leaf_target=64)
+            bem.bem_points_upload(ctx.ctx, N, np.ascontiguousarray(xyz.T))
+            ctx.build()
+            out = torch.zeros(N, dtype=torch.float64, device="cuda")
+            ctx.apply(1.0, torch.from_numpy(q).cuda(), 0.0, None, out)
+            o = out.cpu().numpy()[recv]
+            errs[(col, p)] = float(np.linalg.norm(o - ref) / np.linalg.norm(ref))
+            ctx.close()
+    print("Table 1 replica (N=131072):", {k: "%.1e" % v for k, v in errs.items()})
+    for p in (4, 8, 12, 16):
+        # the same decade as the paper's figure or better
+        assert errs[("double", p)] < 5 * paper[p]["double"]
+    assert errs[("double", 20)] < 1e-7
+    for p in (4, 8, 12):
+        assert errs[("single", p)] < 5 * paper[p]["single"]
+    assert errs[("double", 4)] > errs[("double", 8)] > errs[("double", 12)] > errs[("double", 16)]
