@@ -122,7 +122,8 @@ void bem_destroy(void *ctx);
 /* Change the stream of an existing context. */
 int bem_set_stream(void *ctx, void *stream);
 
-/* Message of the last failed call on ctx (or of the last failed bem_create when ctx is NULL). */
+/* Message of the last failed call on ctx (or, when ctx is NULL, of the last failed call on
+ * this host thread that takes no context: bem_create, bem_apply_direct_noalloc). */
 const char *bem_last_error(const void *ctx);
 
 /* Section 2.1/3.1: upload the surface mesh. N vertices (collocation points) with SoA
@@ -278,6 +279,26 @@ int bem_mlp_set_params(void *ctx, const double *in);
 /* Sizes, sample count and compare-mode counters. */
 int bem_mlp_info(void *ctx, bem_mlp_summary *out);
 
+/* Allocation-free direct product. The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory at the time of the call, such as code running
+ * inside another framework's fixed memory pool or a latency-critical loop where a device
+ * allocation (which synchronises the device) is not acceptable.
+ * Computes out = f L xL + g M xM (diagonals included) by the direct all-pairs sum with the
+ * FP32 kernel of BEM_PREC_MIXED + BEM_MVP_DIRECT, the same result as bem_apply on a context
+ * with those parameters. Takes no context: xyz[3N] (SoA), s[N], n[3N] (SoA), ldiag[N],
+ * mdiag[N] (for example from bem_get_geometry), xL[N], xM[N] and out[N] are device memory
+ * of the current device; the caller owns them. Runs on `stream` (a cudaStream_t; NULL = the
+ * legacy default stream) and returns without waiting for the result.
+ * It allocates nothing: its only scratch, the hi + lo FP32 split of the coordinates, lives in
+ * a file-scope device array sized for N <= 262144 (6 MiB, held by every GPU that loads the
+ * library until the process exits). N outside 2..262144 returns BEM_ERR_ARG with a message in
+ * bem_last_error(NULL). The first call on a device looks up that array's device address, with
+ * that device current; make this first call before any stream capture. Every call shares the
+ * array and overwrites it, so calls that overlap on the GPU (different streams, or different
+ * host threads) race. */
+int bem_apply_direct_noalloc(int64_t N, const double *xyz, const double *s, const double *n, const double *ldiag,
+                             const double *mdiag, double f, const double *xL, double g, const double *xM,
+                             double *out, void *stream);
 
 /* Residual history of the last bem_solve: the true relative residual at the start of each
  * GMRES cycle and the estimate |g_{k+1}|/|b| after each iteration, in order; the final entry

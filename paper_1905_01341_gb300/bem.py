@@ -37,7 +37,7 @@ EXPORTED = [
     "bem_apply_dl", "bem_rhs", "bem_solve", "bem_get_geometry", "bem_get_stats",
     "bem_reset_stats", "bem_profile_enable", "bem_profile_read", "bem_phase_name",
     "bem_get_residual_history", "bem_step_params_default", "bem_step_init", "bem_step",
-    "bem_step_get_state", "bem_mlp_init", "bem_mlp_set_mode", "bem_mlp_train",
+    "bem_step_get_state", "bem_apply_direct_noalloc", "bem_mlp_init", "bem_mlp_set_mode", "bem_mlp_train",
     "bem_mlp_loss_grad", "bem_mlp_forward", "bem_mlp_get_params", "bem_mlp_set_params", "bem_mlp_info",
 ]
 
@@ -171,6 +171,7 @@ def lib() -> ctypes.CDLL:
             "bem_step_init": ([vp, vp, vp, ctypes.POINTER(bem_step_params)], ctypes.c_int),
             "bem_step": ([vp, ctypes.POINTER(bem_step_stats)], ctypes.c_int),
             "bem_step_get_state": ([vp, vp, vp, vp, ctypes.POINTER(dbl)], ctypes.c_int),
+            "bem_apply_direct_noalloc": ([i64, vp, vp, vp, vp, vp, dbl, vp, dbl, vp, vp, vp], ctypes.c_int),
             "bem_mlp_init": ([vp, i32, i32, ctypes.c_uint64], ctypes.c_int),
             "bem_mlp_set_mode": ([vp, i32, i32, i32], ctypes.c_int),
             "bem_mlp_train": ([vp, i32, i32, dbl, ctypes.POINTER(dbl)], ctypes.c_int),
@@ -344,6 +345,16 @@ def bem_step_get_state(ctx, xyz=None, phi=None, q=None) -> float:
     _check(ctx, lib().bem_step_get_state(ctx, _ptr(xyz, np.float64), _ptr(phi, np.float64), _ptr(q, np.float64),
                                          ctypes.byref(t)))
     return float(t.value)
+
+
+def bem_apply_direct_noalloc(N, xyz, s, n, ldiag, mdiag, f, xL, g, xM, out, stream=0) -> None:
+    """Allocation-free direct product on caller-owned device arrays (see include/bem.h)."""
+    handle = stream if isinstance(stream, int) else stream.cuda_stream
+    rc = lib().bem_apply_direct_noalloc(int(N), _ptr(xyz, np.float64), _ptr(s, np.float64), _ptr(n, np.float64),
+                                        _ptr(ldiag, np.float64), _ptr(mdiag, np.float64), float(f),
+                                        _ptr(xL, np.float64), float(g), _ptr(xM, np.float64),
+                                        _ptr(out, np.float64), ctypes.c_void_p(handle))
+    _check(None, rc)
 
 
 def bem_mlp_init(ctx, hidden=256, lmax=10, seed=0) -> None:

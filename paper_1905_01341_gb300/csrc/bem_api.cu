@@ -33,9 +33,9 @@ bool is_device_ptr(const Context &c, const void *p) {
     return false;
 }
 
-namespace {
-
 thread_local std::string g_create_error;
+
+namespace {
 
 __global__ void k_add_diag(int64_t N, double f, const double *__restrict__ xL, double g,
                            const double *__restrict__ xM, const double *__restrict__ ld,

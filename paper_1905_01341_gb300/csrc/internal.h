@@ -29,6 +29,10 @@ struct Error {
                             __FILE__ + ":" + std::to_string(__LINE__));                    \
     } while (0)
 
+// Message of the last failure that has no context (bem_create, context-free entry points),
+// returned by bem_last_error(NULL); one per host thread.
+extern thread_local std::string g_create_error;
+
 // Every kernel launch of the library is followed by this check, which also counts it.
 extern long long g_launch_count;
 #define BEM_LAUNCH_CHECK()                 \
@@ -319,6 +323,10 @@ void launch_p2p_list(Context &c, const T *q, const T *w, const T *far, double *o
 template <int R>
 void launch_direct(Context &c, int prec, const double *f, const double *const *xL,
                    const double *g, const double *const *xM, double *const *out);
+
+// Direct FP32 product (k_direct32, one right-hand side) on caller-provided split coordinates.
+void launch_direct32_raw(int64_t N, const float *hi, const float *lo, const double *s, const double *nrm, double f,
+                         const double *xL, double g, const double *xM, double *out, cudaStream_t st);
 
 // m2l_tc.cu
 bool m2l_tc_supported(int P);

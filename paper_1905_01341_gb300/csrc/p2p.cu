@@ -310,6 +310,18 @@ void launch_direct(Context &c, int prec, const double *f, const double *const *x
     BEM_LAUNCH_CHECK();
 }
 
+void launch_direct32_raw(int64_t N, const float *hi, const float *lo, const double *s, const double *nrm, double f,
+                         const double *xL, double g, const double *xM, double *out, cudaStream_t st) {
+    DirArgs<1> a{};
+    a.f[0] = f;
+    a.g[0] = g;
+    a.xL[0] = xL;
+    a.xM[0] = xM;
+    a.out[0] = out;
+    k_direct32<1><<<div_up(N, P2P_THREADS), P2P_THREADS, 0, st>>>(N, hi, lo, s, nrm, a);
+    BEM_LAUNCH_CHECK();
+}
+
 template void launch_direct<1>(Context &, int, const double *, const double *const *, const double *,
                                const double *const *, double *const *);
 template void launch_direct<4>(Context &, int, const double *, const double *const *, const double *,
