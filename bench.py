@@ -29,7 +29,25 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flops x max clock
-P2P_FLOPS_PER_PAIR = 20  # per right-hand side: 3 sub, 5 for r^2, rsqrt, 2 for r^-3, 5 for n.d, 4 accumulate
+# Algorithmic FP32 flops per near-field pair, per kernel variant (rsqrt counted as one):
+#   single layer: 3 (r_i - r_j) + 5 (r^2) + 1 (rsqrt) + 2 (q / r accumulated)          = 11
+#   double layer: 3 + 5 + 1 + 2 (r^-3) + 5 (n . d) + 1 (scale) + 2 (w n.d / r^3 acc.)  = 19
+#   both layers, 4 RHS (diagonal product): 3 + 5 + 1 + 2 + 5 + 1 + 4 x (2 + 2)         = 33
+P2P_FLOPS_SL, P2P_FLOPS_DL, P2P_FLOPS_4RHS = 11, 19, 33
+
+
+def _load_peaks() -> dict:
+    """Measured HBM / BF16 peaks of this GPU pool, when present beside this file."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+PEAKS = _load_peaks()
+# Tensor-core M2L: six BF16 products per translation (three-piece split of both operands).
+M2L_TC_PRODUCTS = 6
 
 
 def parse():
@@ -53,6 +71,7 @@ def parse():
     ap.add_argument("--maxit", type=int, default=400)
     ap.add_argument("--restart", type=int, default=100)
     ap.add_argument("--precond", type=int, default=0, help="1 = right Jacobi preconditioning of GMRES")
+    ap.add_argument("--m2l-tc", type=int, default=1, help="1 = M2L of single-RHS products on the tensor cores")
     ap.add_argument("--pa", type=float, default=0.5, help="acoustic amplitude Pa/p0")
     ap.add_argument("--pf", type=int, default=6, help="shape-filter bandwidth")
     ap.add_argument("--fp64-compare", type=int, default=1, help="also time FP64 right-hand sides (0 = skip)")
@@ -240,7 +259,7 @@ def run_ours(args):
     def make_ctx(precision):
         c = bem.BemContext(stream=stream, p_fmm=args.p, precision=precision, leaf_target=args.leaf,
                            fixed_level=args.tree_level, gmres_tol=args.tol, gmres_maxit=args.maxit,
-                           gmres_restart=args.restart, gmres_precond=args.precond)
+                           gmres_restart=args.restart, gmres_precond=args.precond, m2l_tensor_cores=args.m2l_tc)
         return c
 
     ctx = make_ctx(prec)
@@ -313,8 +332,11 @@ def run_ours(args):
     n_r1 = mvps - rhs           # single-RHS products (right-hand side b and GMRES)
     per_step = {k: v[0] / args.steps for k, v in prof.items()}
     P = args.p * args.p
+    n_dl = rhs                  # b = -phi/2 + M phi: double layer only, once per right-hand side
+    n_sl = n_r1 - n_dl          # GMRES products (and restart residuals): single layer only
+    pairs = st["p2p_pairs"]
     work = {
-        "p2p": P2P_FLOPS_PER_PAIR * st["p2p_pairs"] * (n_r1 + 4 * n_r4) / args.steps,
+        "p2p": (P2P_FLOPS_SL * n_sl + P2P_FLOPS_DL * n_dl + P2P_FLOPS_4RHS * n_r4) * pairs / args.steps,
         "m2l": 2.0 * P * P * st["m2l_pairs"] * (n_r1 + 4 * n_r4) / args.steps,
     }
     launches = {k: prof[k][1] / args.steps for k in ("p2p", "m2l")}
@@ -330,8 +352,24 @@ def run_ours(args):
                 "frac": (achieved / peak) if peak else None, "traffic": None,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (max SM clock)",
                 "launch_ms": t_launch * 1e3, "launches_per_step": nl,
-                "work_per_launch": "%s" % ("20 flops x near-field pairs x RHS" if dom == "p2p"
+                "work_per_launch": "%s" % ("11 (single layer) / 19 (double layer) / 33 (both, 4 RHS) flops x "
+                                            "near-field pairs" if dom == "p2p"
                                             else "2 P^2 flops x M2L translations x RHS")}
+
+    # the tensor-core M2L (single-RHS products), against the measured BF16 peak; the phase also
+    # holds the multipole split, the per-target reduction and the 4-RHS CUDA-core translations
+    roof_m2l = None
+    if prec == bem.BEM_PREC_MIXED and args.m2l_tc and per_step.get("m2l", 0) > 0:
+        nl = max(1.0, launches["m2l"])
+        t_launch = per_step["m2l"] / 1e3 / nl
+        w_tc = M2L_TC_PRODUCTS * 2.0 * P * P * st["m2l_pairs"] * (n_sl + n_dl) / args.steps
+        achieved = w_tc / nl / t_launch / 1e12
+        pk = PEAKS.get("bf16_tflops_sustained")
+        roof_m2l = {"kernel": "m2l", "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                    "frac": achieved / pk if pk else None, "traffic": None,
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS, long loop)",
+                    "launch_ms": t_launch * 1e3, "launches_per_step": nl,
+                    "work_per_launch": "6 BF16 products x 2 P^2 flops x M2L translations"}
 
     line = {
         "metric": "wall-s per time step & FMM matvec Gpairs/s at 3.2M unknowns, resid 1e-6, vs FP64",
@@ -339,7 +377,8 @@ def run_ours(args):
         "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if prec == bem.BEM_PREC_MIXED else "f64", "data": "synthetic",
         "config": {"workload": workload_name(args, mesh), "p_fmm": args.p, "precision": args.precision,
-                   "leaf_target": args.leaf, "gmres_tol": args.tol, "gmres_precond": args.precond, "scheme": "AB6 after %d RK4 warm-up steps" % 5,
+                   "leaf_target": args.leaf, "gmres_tol": args.tol, "gmres_precond": args.precond,
+                   "m2l_tensor_cores": args.m2l_tc, "scheme": "AB6 after %d RK4 warm-up steps" % 5,
                    "pa": args.pa, "pf": args.pf, "dt": infos[-1]["dt"], "levels": st["levels"],
                    "leaves": st["leaves"], "l2": "inputs and working set > L2 (no flush)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -351,6 +390,7 @@ def run_ours(args):
                 "p2p_pairs": st["p2p_pairs"], "m2l_pairs": st["m2l_pairs"]},
         "phases_ms_per_step": {k: round(v, 3) for k, v in per_step.items() if v > 0},
         "roofline": roof,
+        "roofline_m2l": roof_m2l,
         "e2e": {"value": e2e_s, "unit": "s/step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(d2h),
                 "what": "bem_step driven from the host + bem_step_get_state into pinned host buffers"},
         "gpu_launches": int((st1["n_launches"] - st0["n_launches"]) / args.steps),

@@ -77,9 +77,12 @@ typedef struct {
     int32_t mvp;            /* bem_mvp_kind. Default BEM_MVP_FMM.                              */
     int32_t diag_precision; /* precision of the 4-RHS product that feeds Eqs. (s3)/(s5);
                                -1 = same as `precision`. Default -1.                           */
-    int32_t m2l_tensor_cores; /* 1: mixed-precision M2L on the tensor cores (3-pass TF32 split,
-                               FP32 accumulation) when p_fmm^2 is a multiple of 4 and <= 256;
-                               0: FP32 CUDA cores. Default 1.                                  */
+    int32_t m2l_tensor_cores; /* 1: mixed-precision single-RHS products (every GMRES product)
+                               run M2L on the tensor cores (three-piece BF16 split, FP32
+                               accumulation) when p_fmm^2 is a multiple of 4 and <= 256;
+                               0: FP32 CUDA cores. The 4-RHS product behind the diagonals
+                               always uses the CUDA cores: Eqs. (s3)/(s5) form M_ii and L_ii
+                               by cancellation, which magnifies rounding. Default 1.          */
     int32_t gmres_precond;  /* 0: unpreconditioned GMRES, as in the paper (Section 3.8);
                                1: right Jacobi preconditioning x = D^-1 y with D = diag(L_ii)
                                (same solution and true-residual test; removes the spread of

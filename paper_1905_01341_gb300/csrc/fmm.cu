@@ -232,7 +232,7 @@ struct Vec2<double> {
     using type = double2;
 };
 
-template <class T, int R>
+template <class T, int R, bool HW>
 __global__ void __launch_bounds__(256) k_p2m(int p, int nleaf, const int32_t *__restrict__ bstart,
                                              const int32_t *__restrict__ bcount, int64_t N,
                                              const T *__restrict__ loc, const T *__restrict__ nrm,
@@ -264,14 +264,15 @@ __global__ void __launch_bounds__(256) k_p2m(int p, int nleaf, const int32_t *__
     for (int c0 = 0; c0 < cnt; c0 += P2M_PC) {
         const int pc = min(P2M_PC, cnt - c0);
         __syncthreads();
-        for (int e = threadIdx.x; e < pc * 3; e += blockDim.x) {
-            int jj = e / 3, d = e % 3;
-            pn[jj * 3 + d] = nrm[d * N + s0 + c0 + jj];
-        }
+        if (HW)
+            for (int e = threadIdx.x; e < pc * 3; e += blockDim.x) {
+                int jj = e / 3, d = e % 3;
+                pn[jj * 3 + d] = nrm[d * N + s0 + c0 + jj];
+            }
         for (int e = threadIdx.x; e < pc * R; e += blockDim.x) {
             int jj = e / R, r = e % R;
             pq[jj * R + r] = q[r * N + s0 + c0 + jj];
-            pw[jj * R + r] = w[r * N + s0 + c0 + jj];
+            pw[jj * R + r] = HW ? w[r * N + s0 + c0 + jj] : (T)0;
         }
         for (int task = threadIdx.x; task < pc * p; task += blockDim.x) {
             const int jj = task / p, m = task % p;
@@ -314,7 +315,7 @@ __global__ void __launch_bounds__(256) k_p2m(int p, int nleaf, const int32_t *__
                 const T2 *col = Rt + jj * ntri;
                 const T2 A = col[iA];
                 T gr = 0, gi = 0;
-                if (n >= 1) {
+                if (HW && n >= 1) {
                     const T nx = pn[jj * 3], ny = pn[jj * 3 + 1], nz = pn[jj * 3 + 2];
                     T2 Bm = iB >= 0 ? col[iB] : T2{0, 0};
                     T2 Bl = iL >= 0 ? col[iL] : T2{0, 0};
@@ -325,9 +326,15 @@ __global__ void __launch_bounds__(256) k_p2m(int p, int nleaf, const int32_t *__
                 }
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const T qq = pq[jj * R + r], ww = pw[jj * R + r];
-                    are[o][r] += qq * A.x + ww * gr;
-                    aim[o][r] -= qq * A.y + ww * gi;
+                    const T qq = pq[jj * R + r];
+                    if (HW) {
+                        const T ww = pw[jj * R + r];
+                        are[o][r] += qq * A.x + ww * gr;
+                        aim[o][r] -= qq * A.y + ww * gi;
+                    } else {
+                        are[o][r] += qq * A.x;
+                        aim[o][r] -= qq * A.y;
+                    }
                 }
             }
         }
@@ -635,10 +642,13 @@ void run_fmm(Context &c, const RhsArgs<R> &a) {
         PhaseScope ps(c, PH_P2M);
         const int ntri = p * (p + 1) / 2;
         size_t sm = ((size_t)2 * P2M_PC * ntri + P2M_PC * 3 + 2 * P2M_PC * R) * sizeof(T);
-        const int threads = std::min(256, std::max(64, (ntri + 63) / 64 * 32));  // ntri <= 2 * threads
-        if (sm > 48 * 1024) BEM_CUDA(cudaFuncSetAttribute(k_p2m<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_p2m<T, R><<<nleaf, threads, sm, st>>>(p, nleaf, t.bstart.p + t.base[L], t.bcount.p + t.base[L], N, loc, nrm,
-                                                q, w, mp + (size_t)t.base[L] * R * P);
+        const int threads = ntri <= 256 ? 128 : 256;  // ntri <= 2 * threads
+        bool hw = false;
+        for (int r = 0; r < R; ++r) hw = hw || a.g[r] != 0.0;
+        auto kern = hw ? k_p2m<T, R, true> : k_p2m<T, R, false>;
+        if (sm > 48 * 1024) BEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        kern<<<nleaf, threads, sm, st>>>(p, nleaf, t.bstart.p + t.base[L], t.bcount.p + t.base[L], N, loc, nrm, q, w,
+                                         mp + (size_t)t.base[L] * R * P);
         BEM_LAUNCH_CHECK();
     }
     // zero the multipoles above the leaves and all locals
@@ -677,10 +687,12 @@ void run_fmm(Context &c, const RhsArgs<R> &a) {
     // M2L, all levels at once, then each target sums its sources
     if (nm2l_chunks) {
         PhaseScope ps(c, PH_M2L);
-        if (!F64 && c.prm.m2l_tensor_cores && m2l_tc_supported(P) && c.ops.tc_Npad > 0) {
+        // The 4-RHS product behind the diagonals stays on the CUDA cores: M_ii and L_ii are formed
+        // by cancellation (Eqs. (s3), (s5)), which magnifies the tensor path's rounding.
+        if (!F64 && R == 1 && c.prm.m2l_tensor_cores && m2l_tc_supported(P) && c.ops.tc_Npad > 0) {
             if (c.tc_chunks_r != R) {
                 std::vector<XChunk> tc;
-                make_chunks(t.m2l_class_off, 0, 128 / R, tc);
+                make_chunks(t.m2l_class_off, 0, m2l_tc_pairs_per_chunk(R), tc);
                 c.tc_chunks.resize(std::max<size_t>(tc.size(), 1));
                 if (!tc.empty())
                     BEM_CUDA(cudaMemcpyAsync(c.tc_chunks.p, tc.data(), tc.size() * sizeof(XChunk),
@@ -689,7 +701,8 @@ void run_fmm(Context &c, const RhsArgs<R> &a) {
                 c.tc_chunks_r = R;
             }
             if (c.n_tc_chunks)
-                launch_m2l_tc<R>(c, c.tc_chunks.p, c.n_tc_chunks, (const float *)mp, (float *)ypair, c.tc_err.p);
+                launch_m2l_tc<R>(c, c.tc_chunks.p, c.n_tc_chunks, (const float *)mp, (int64_t)t.nbox * R, (float *)ypair,
+                                 c.tc_err.p);
         } else {
             dim3 grid((unsigned)nm2l_chunks, rowblocks);
             k_xlat<T, R, kStorePair><<<grid, XT_THREADS, 0, st>>>(m2l, P, c.m2l_chunks.p + 1, t.m2l_src.p,
@@ -722,7 +735,12 @@ void run_fmm(Context &c, const RhsArgs<R> &a) {
     c.near_out.resize((size_t)R * N);
     {
         PhaseScope ps(c, PH_P2P);
-        launch_p2p_list<T, R>(c, q, w, far, c.near_out.p);
+        bool hq = false, hw = false;
+        for (int r = 0; r < R; ++r) {
+            hq = hq || a.f[r] != 0.0;
+            hw = hw || a.g[r] != 0.0;
+        }
+        launch_p2p_list<T, R>(c, q, w, far, c.near_out.p, hq, hw);
     }
     RhsArgs<kMaxRhs> o{};
     for (int r = 0; r < R; ++r) o.out[r] = a.out[r];
@@ -738,6 +756,7 @@ void build_operators(Context &c) {
     Operators &o = c.ops;
     o.p = p;
     o.P = p * p;
+    o.tc_Npad = o.tc_Kpad = 0;  // tensor-core tables follow the operators
     size_t PP = (size_t)o.P * o.P;
     o.m2l64.resize(kNumM2LClasses * PP);
     o.m2l32.resize(kNumM2LClasses * PP);

@@ -138,6 +138,9 @@ struct Tree {
     DevBuf<float> nrm32;
     DevBuf<double> s_sorted;   // [N]
     int64_t p2p_pairs = 0;
+    // near-field work units: (leaf, first receiver), up to 64 receivers of one leaf each
+    DevBuf<int2> p2p_units;
+    int64_t n_p2p_units = 0;
 };
 
 // ------------------------------------------------------------------------------ FMM operators
@@ -145,10 +148,10 @@ struct Operators {
     int p = 0, P = 0;
     DevBuf<double> m2l64, m2m64, l2l64;  // [316][P][P], [8][P][P], [8][P][P]
     DevBuf<float> m2l32, m2m32, l2l32;
-    // tensor-core M2L: per class, per 32-wide K chunk, an Npad x 32 block in the K-major
-    // core-matrix layout (m2l_tc.cu)
+    // tensor-core M2L: per class, per 16-wide K step, three BF16 pieces of an N_pad x 16 block
+    // in the K-major core-matrix layout (m2l_tc.cu); stored as raw 16-bit words
     int tc_Npad = 0, tc_Kpad = 0;
-    DevBuf<float> m2l_tc;
+    DevBuf<uint16_t> m2l_tc;
 };
 
 // Work chunk of the class-grouped translation product.
@@ -269,7 +272,8 @@ struct Context {
     DevBuf<double> near_out;       // combined potential [R][N] (sorted)
     DevBuf<XChunk> m2l_chunks;
     std::vector<XChunk> m2l_chunks_h;
-    DevBuf<XChunk> tc_chunks;        // M2L chunks of <= 128/R pairs for the tensor-core kernel
+    DevBuf<XChunk> tc_chunks;        // M2L chunks of <= 256/R pairs for the tensor-core kernel
+    DevBuf<uint16_t> xsplit;         // multipoles split into three BF16 planes (tensor-core M2L)
     int tc_chunks_r = 0;             // R the table was built for (0 = none)
     int64_t n_tc_chunks = 0;
     DevBuf<int> tc_err;              // set by a tensor-core block whose wait ran out
@@ -319,7 +323,7 @@ void offdiag_apply(Context &c, int R, const double *f, const double *const *xL,
 
 // p2p.cu
 template <class T, int R>
-void launch_p2p_list(Context &c, const T *q, const T *w, const T *far, double *out_sorted);
+void launch_p2p_list(Context &c, const T *q, const T *w, const T *far, double *out_sorted, bool hq, bool hw);
 template <int R>
 void launch_direct(Context &c, int prec, const double *f, const double *const *xL,
                    const double *g, const double *const *xM, double *const *out);
@@ -332,7 +336,9 @@ void launch_direct32_raw(int64_t N, const float *hi, const float *lo, const doub
 bool m2l_tc_supported(int P);
 void build_tc_tables(Context &c);
 template <int R>
-void launch_m2l_tc(Context &c, const XChunk *chunks, int64_t nchunks, const float *X, float *Ypair, int *err);
+void launch_m2l_tc(Context &c, const XChunk *chunks, int64_t nchunks, const float *X, int64_t xrows, float *Ypair,
+                   int *err);
+int m2l_tc_pairs_per_chunk(int R);
 
 // gmres.cu
 void gmres_solve(Context &c, const double *b, double *x, int *iters, double *relres);

@@ -1,34 +1,44 @@
 // M2L translations on the 5th-generation tensor cores (tcgen05, TMEM accumulators).
 //
-// For one offset class c and a chunk of up to 128/R (source, target) pairs, the product
+// For one offset class c and a chunk of up to 256/R (source, target) pairs, the product
 //   Y[pair, rhs][n] = sum_k T_c[n][k] X[src, rhs][k]
-// is one MMA tile D = A B^T with M = 128 rows (pair, rhs), N = P rounded up to 16 output
-// coefficients and K = P input coefficients: A = the gathered multipole rows, B = T_c (row n of
-// T_c is K-contiguous, i.e. K-major). Accuracy: both operands are split into three TF32 pieces,
-// x = x0 + x1 + x2 (x0 = tf32(x), x1 = tf32(x - x0), x2 = the rest), and D accumulates the six
-// products x0 y0 + x0 y1 + x1 y0 + x0 y2 + x1 y1 + x2 y0 in FP32; the dropped terms are ~2^-33
-// of the product, so the translation is as accurate as an FP32 product. (Translation sums
-// cancel strongly, so a two-piece split, ~2^-21 per product, leaves noise near 1e-6 in the
-// operator, which a GMRES solve to 1e-6 cannot tolerate.)
+// is two MMA tiles D_t = A_t B^T (t = 0, 1) with M = 128 rows (pair, rhs) each, N = P rounded
+// up to 16 output coefficients and K = P input coefficients: A_t = gathered multipole rows,
+// B = T_c (row n of T_c is K-contiguous, i.e. K-major). The two tiles share every staged
+// block of T_c, which halves its traffic.
 //
-// Operands are staged through shared memory in the canonical K-major layout without swizzle:
-// 8-row x 16-byte core matrices, core matrices adjacent in K are 128 B apart (leading byte
-// offset) and 8-row groups are 1024 B apart (stride byte offset) within a 32-wide K chunk.
-// One elected thread issues the MMAs; completion is signalled through an mbarrier whose
-// waits are bounded: a wait that runs out sets an error flag and the block skips ahead,
-// releasing its tensor memory.
+// Accuracy: both operands are split into three BF16 pieces, x = x0 + x1 + x2 (x0 = bf16(x),
+// x1 = bf16(x - x0), x2 = bf16(x - x0 - x1)), and D accumulates in FP32 the six products with
+// i + j <= 2: x0 y0 + (x0 y1 + x1 y0) + (x0 y2 + x1 y1 + x2 y0). The dropped terms and the
+// rest of x beyond x2 are ~2^-24 of the product, so the translation is as accurate as an FP32
+// product. (Translation sums cancel strongly, so a two-piece split leaves noise near 1e-6 in
+// the operator, which a GMRES solve to 1e-6 cannot tolerate.) T_c is split once per operator
+// build from its FP64 values; the multipoles are split once per product (k_split_x).
+//
+// Data movement: K advances 16 at a time (one kind::f16 MMA); each 16-wide K step is one
+// pipeline stage holding A (3 pieces x 2 tiles x 128 x 16) and B (3 pieces x N_pad x 16) in
+// the canonical K-major layout without swizzle (8-row x 16-byte core matrices, K-adjacent core
+// matrices 128 B apart, 8-row groups 256 B apart). All threads fill stages with cp.async
+// (16-byte copies; rows past the chunk read as zeros), four stages deep; one elected thread
+// issues the MMAs of a stage as soon as it has landed and commits them to the stage's
+// mbarrier, which releases the stage for refilling. Every wait is bounded: one that runs out
+// sets an error flag and the block skips ahead, waiting (bounded) for its MMAs in flight
+// before it releases its tensor memory.
+#include <cuda_bf16.h>
+
 #include "internal.h"
 
 namespace bem {
 namespace {
 
-constexpr int TC_M = 128;          // rows per tile
-constexpr int TC_KC = 32;          // K chunk staged per round
+constexpr int TC_M = 128;        // rows per tile
+constexpr int TC_TILES = 2;      // tiles per block (same class, shared B stages)
+constexpr int TC_K = 16;         // K per stage (one kind::f16 MMA)
+constexpr int TC_STAGES = 4;
 constexpr int TC_THREADS = 128;
-constexpr int TC_KGROUPS = TC_KC / 4;  // 16-byte core-matrix columns per chunk
-constexpr uint32_t TC_LBO = 128;       // bytes between K-adjacent core matrices
-constexpr uint32_t TC_SBO = 128 * TC_KGROUPS;  // bytes between 8-row groups (1024)
-constexpr long long kWaitLimit = 1ll << 24;    // iterations before a wait gives up
+constexpr uint32_t TC_LBO = 128;  // bytes between K-adjacent core matrices
+constexpr uint32_t TC_SBO = 256;  // bytes between 8-row groups
+constexpr long long kWaitLimit = 1ll << 20;  // iterations before a wait gives up
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -43,30 +53,16 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
     return d;
 }
 
-// kind::tf32 instruction descriptor: D = F32, A = B = TF32, both K-major, N and M given.
+// kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, N and M given.
 __host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ float tf32_head(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
-// x = x0 + x1 + x2 with x0, x1 TF32-representable (x2 is truncated to TF32 by the MMA).
-__device__ __forceinline__ void split3(float4 v, float4 &x0, float4 &x1, float4 &x2) {
-    x0 = make_float4(tf32_head(v.x), tf32_head(v.y), tf32_head(v.z), tf32_head(v.w));
-    float4 r = make_float4(v.x - x0.x, v.y - x0.y, v.z - x0.z, v.w - x0.w);
-    x1 = make_float4(tf32_head(r.x), tf32_head(r.y), tf32_head(r.z), tf32_head(r.w));
-    x2 = make_float4(r.x - x1.x, r.y - x1.y, r.z - x1.z, r.w - x1.w);
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accum) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
 }
 
@@ -89,54 +85,122 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
     return false;
 }
 
-// Row-major T_c [P][P] (FP32) -> per class, per K chunk, an N_pad x 32 block in the canonical
-// K-major core-matrix layout, zero-padded (n >= P or k >= P).
-__global__ void k_build_tc_table(int P, int Npad, int Kpad, const float *__restrict__ T, float *__restrict__ out) {
+// 16-byte global -> shared copy; src_bytes = 0 writes zeros without reading.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// element offset of (row, kk) inside one 16-wide K step of a K-major operand block
+__host__ __device__ constexpr int kmajor_off(int row, int kk) {
+    return (row >> 3) * 128 + (kk >> 3) * 64 + (row & 7) * 8 + (kk & 7);
+}
+
+// three-piece BF16 split of an FP64 value (operator tables)
+__device__ __forceinline__ void split3_d(double v, __nv_bfloat16 &b0, __nv_bfloat16 &b1, __nv_bfloat16 &b2) {
+    b0 = __double2bfloat16(v);
+    double r = v - (double)__bfloat162float(b0);
+    b1 = __double2bfloat16(r);
+    r -= (double)__bfloat162float(b1);
+    b2 = __double2bfloat16(r);
+}
+
+// three-piece BF16 split of an FP32 value (each difference is exact in FP32)
+__device__ __forceinline__ void split3_f(float v, __nv_bfloat16 &b0, __nv_bfloat16 &b1, __nv_bfloat16 &b2) {
+    b0 = __float2bfloat16_rn(v);
+    float r = v - __bfloat162float(b0);
+    b1 = __float2bfloat16_rn(r);
+    r -= __bfloat162float(b1);
+    b2 = __float2bfloat16_rn(r);
+}
+
+// Row-major T_c [P][P] (FP64) -> per class, per 16-wide K step, per piece, an N_pad x 16
+// block in the canonical K-major layout, zero-padded (n >= P or k >= P).
+__global__ void k_build_tc_table(int P, int Npad, const double *__restrict__ T, __nv_bfloat16 *__restrict__ out) {
     const int cls = blockIdx.y;
-    const size_t block = (size_t)Npad * TC_KC;
-    const int nchunk = Kpad / TC_KC;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < block * nchunk;
+    const int nsteps = Npad / TC_K;
+    const size_t blk = (size_t)Npad * TC_K;  // one piece of one K step
+    const size_t per_cls = blk * 3 * nsteps;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < blk * nsteps;
          e += (size_t)gridDim.x * blockDim.x) {
-        int kc = (int)(e / block);
-        int rem = (int)(e % block);
-        // inverse of the canonical offset: rem = (n/8)*256 + (kk/4)*32 + (n%8)*4 + kk%4
-        int g = rem / 256, r2 = rem % 256;
-        int j = r2 / 32, r3 = r2 % 32;
-        int n = g * 8 + r3 / 4, kk = j * 4 + r3 % 4;
-        int k = kc * TC_KC + kk;
-        float v = (n < P && k < P) ? T[((size_t)cls * P + n) * P + k] : 0.f;
-        out[(size_t)cls * block * nchunk + e] = v;
+        const int ks = (int)(e / blk);
+        const int rem = (int)(e % blk);
+        // inverse of kmajor_off: rem = (n/8)*128 + (kk/8)*64 + (n%8)*8 + kk%8
+        const int g = rem >> 7, r2 = rem & 127;
+        const int j = r2 >> 6, r3 = r2 & 63;
+        const int n = g * 8 + (r3 >> 3), kk = j * 8 + (r3 & 7);
+        const int k = ks * TC_K + kk;
+        const double v = (n < P && k < P) ? T[((size_t)cls * P + n) * P + k] : 0.0;
+        __nv_bfloat16 b0, b1, b2;
+        split3_d(v, b0, b1, b2);
+        __nv_bfloat16 *o = out + (size_t)cls * per_cls + (size_t)ks * 3 * blk + rem;
+        o[0] = b0;
+        o[blk] = b1;
+        o[2 * blk] = b2;
     }
 }
 
+// Multipoles X [rows][P] (FP32) -> three BF16 planes [3][rows][Kp], zero-padded to Kp.
+__global__ void k_split_x(int64_t rows, int P, int Kp, const float *__restrict__ X, __nv_bfloat16 *__restrict__ Xs) {
+    const int64_t plane = rows * Kp;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < plane; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / Kp;
+        const int k = (int)(e % Kp);
+        const float v = k < P ? X[r * P + k] : 0.f;
+        __nv_bfloat16 b0, b1, b2;
+        split3_f(v, b0, b1, b2);
+        Xs[e] = b0;
+        Xs[plane + e] = b1;
+        Xs[2 * plane + e] = b2;
+    }
+}
+
+struct TcLayout {
+    size_t a_bytes, b_bytes, stage_bytes, total;
+};
+
+__host__ __device__ inline TcLayout tc_layout(int Npad) {
+    TcLayout L;
+    L.a_bytes = (size_t)3 * TC_TILES * TC_M * TC_K * 2;
+    L.b_bytes = (size_t)3 * Npad * TC_K * 2;
+    L.stage_bytes = L.a_bytes + L.b_bytes;
+    L.total = TC_STAGES * L.stage_bytes + TC_STAGES * 8 + 16 + 1024;
+    return L;
+}
+
 template <int R>
-__global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, int Kpad, const float *__restrict__ tcB,
+__global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __nv_bfloat16 *__restrict__ tcB,
                                                        const XChunk *__restrict__ chunks,
-                                                       const int32_t *__restrict__ srcs,
-                                                       const float *__restrict__ X, float *__restrict__ Ypair,
+                                                       const int32_t *__restrict__ srcs, int64_t xrows,
+                                                       const __nv_bfloat16 *__restrict__ Xs, float *__restrict__ Ypair,
                                                        int *__restrict__ err) {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    // layout: A0, A1, A2 [128 x 32] each, B0, B1, B2 [Npad x 32] each, then barrier + tmem slot
-    float *A0 = reinterpret_cast<float *>(smem);
-    float *A1 = A0 + TC_M * TC_KC;
-    float *A2 = A1 + TC_M * TC_KC;
-    float *B0 = A2 + TC_M * TC_KC;
-    float *B1 = B0 + Npad * TC_KC;
-    float *B2 = B1 + Npad * TC_KC;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(B2 + Npad * TC_KC);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 1);
-    __shared__ int s_src[TC_M];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte aligned base for the operand stages
+    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    const TcLayout Lo = tc_layout(Npad);
+    uint64_t *empty = reinterpret_cast<uint64_t *>(smem + TC_STAGES * Lo.stage_bytes);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(empty + TC_STAGES);
+    __shared__ int s_src[TC_TILES * TC_M];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // once a block has reported a wait that ran out, the rest skip their work
+    if (*reinterpret_cast<volatile int *>(err) != 0) return;
     const XChunk ch = chunks[blockIdx.x];
     const int nrows = ch.count * R;
-    if (tid < TC_M) s_src[tid] = (tid < nrows) ? srcs[ch.start + tid / R] : -1;
+    const int ntiles = nrows > TC_M ? 2 : 1;
+    const int nsteps = Npad / TC_K;
+    for (int r = tid; r < TC_TILES * TC_M; r += TC_THREADS) s_src[r] = (r < nrows) ? srcs[ch.start + r / R] : -1;
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+        for (int s = 0; s < TC_STAGES; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(tmem_slot)));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -144,141 +208,179 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, int Kpad
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
     const uint32_t idesc = make_idesc(TC_M, Npad);
-    const int nchunk = Kpad / TC_KC;
-    const size_t bblock = (size_t)Npad * TC_KC;
-    const float *Bc = tcB + (size_t)ch.cls * bblock * nchunk;
-    uint32_t phase = 0;
-    bool ok = true;
+    const int Kp = Npad;
+    const int64_t plane = xrows * Kp;
+    const __nv_bfloat16 *Bc = tcB + (size_t)ch.cls * nsteps * 3 * Npad * TC_K;
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t apiece = TC_TILES * TC_M * TC_K * 2, atile = TC_M * TC_K * 2;
+    const uint32_t bpiece = (uint32_t)Npad * TC_K * 2;
 
-    for (int kc = 0; kc < nchunk && ok; ++kc) {
-        // A: thread -> (row within an 8-row group, 16-byte K column); rows = 2 groups per pass
-        {
-            const int t64 = tid & 63, r8 = t64 & 7, j = t64 >> 3;
-            const int k0 = kc * TC_KC + j * 4;
-            for (int gp = (tid >> 6); gp < TC_M / 8; gp += 2) {
-                const int row = gp * 8 + r8;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                const int s = s_src[row];
-                if (s >= 0 && k0 < P) {
-                    const float *src = X + ((size_t)s * R + (row % R)) * P + k0;
-                    v = *reinterpret_cast<const float4 *>(src);  // P % 4 == 0, k0 % 4 == 0
-                }
-                float4 x0, x1, x2;
-                split3(v, x0, x1, x2);
-                const int off = gp * 256 + j * 32 + r8 * 4;  // floats
-                *reinterpret_cast<float4 *>(A0 + off) = x0;
-                *reinterpret_cast<float4 *>(A1 + off) = x1;
-                *reinterpret_cast<float4 *>(A2 + off) = x2;
-            }
+    // fill stage `st` with K step `ks`
+    auto load_stage = [&](int ks, int st) {
+        const uint32_t sa = sbase + st * (uint32_t)Lo.stage_bytes;
+        const uint32_t sb = sa + (uint32_t)Lo.a_bytes;
+        // A: u -> (piece, tile row, j); 16 bytes = 8 consecutive k of one row
+        for (int u = tid; u < 3 * TC_TILES * TC_M * 2; u += TC_THREADS) {
+            const int j = u & 1;
+            const int row2 = (u >> 1) % (TC_TILES * TC_M), piece = (u >> 1) / (TC_TILES * TC_M);
+            const int t = row2 / TC_M, row = row2 % TC_M;
+            const int s = s_src[row2];
+            const int rr = row2 % R;
+            const __nv_bfloat16 *src =
+                Xs + (size_t)piece * plane + ((size_t)(s >= 0 ? s : 0) * R + rr) * Kp + ks * TC_K + j * 8;
+            const uint32_t dst = sa + piece * apiece + t * atile + (uint32_t)kmajor_off(row, j * 8) * 2;
+            cp_async16(dst, src, s >= 0 ? 16u : 0u);
         }
-        // B: linear copy of the pre-tiled chunk block, split on the way
-        {
-            const float4 *src = reinterpret_cast<const float4 *>(Bc + (size_t)kc * bblock);
-            for (int e = tid; e < (int)(bblock / 4); e += TC_THREADS) {
-                float4 x0, x1, x2;
-                split3(src[e], x0, x1, x2);
-                reinterpret_cast<float4 *>(B0)[e] = x0;
-                reinterpret_cast<float4 *>(B1)[e] = x1;
-                reinterpret_cast<float4 *>(B2)[e] = x2;
-            }
-        }
+        // B: contiguous pre-tiled block of the three pieces
+        const unsigned char *bsrc = reinterpret_cast<const unsigned char *>(Bc + (size_t)ks * 3 * Npad * TC_K);
+        for (int u = tid; u < (int)(Lo.b_bytes / 16); u += TC_THREADS) cp_async16(sb + u * 16, bsrc + (size_t)u * 16, 16u);
+    };
+
+#pragma unroll 1
+    for (int s = 0; s < TC_STAGES - 1; ++s) {
+        if (s < nsteps) load_stage(s, s);
+        cp_async_commit();
+    }
+    bool ok = true;
+    int last_stage = 0;
+    uint32_t last_parity = 0;
+#pragma unroll 1
+    for (int ks = 0; ks < nsteps; ++ks) {
+        const int st = ks % TC_STAGES;
+        cp_async_wait<TC_STAGES - 2>();  // this thread's copies of step ks have landed
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const int kvalid = min(TC_KC, P - kc * TC_KC);
-            const int nsteps = (kvalid + 7) / 8;
-            const uint32_t a0 = smem_u32(A0), a1 = smem_u32(A1), a2 = smem_u32(A2);
-            const uint32_t b0 = smem_u32(B0), b1 = smem_u32(B1), b2 = smem_u32(B2);
-            for (int s = 0; s < nsteps; ++s) {
-                const uint32_t o = s * 2 * TC_LBO;  // 8 K-elements = two core matrices
-                const uint32_t acc = (kc > 0 || s > 0) ? 1u : 0u;
-                // smallest terms first
-                mma_tf32(tmem, make_desc(a2 + o), make_desc(b0 + o), idesc, acc);
-                mma_tf32(tmem, make_desc(a1 + o), make_desc(b1 + o), idesc, 1u);
-                mma_tf32(tmem, make_desc(a0 + o), make_desc(b2 + o), idesc, 1u);
-                mma_tf32(tmem, make_desc(a1 + o), make_desc(b0 + o), idesc, 1u);
-                mma_tf32(tmem, make_desc(a0 + o), make_desc(b1 + o), idesc, 1u);
-                mma_tf32(tmem, make_desc(a0 + o), make_desc(b0 + o), idesc, 1u);
+            const uint32_t sa = sbase + st * (uint32_t)Lo.stage_bytes;
+            const uint32_t sb = sa + (uint32_t)Lo.a_bytes;
+            for (int t = 0; t < ntiles; ++t) {
+                const uint32_t d = tmem + (uint32_t)(t * 256);
+                const uint32_t a0 = sa + t * atile;
+                // smallest terms first: (2,0) (1,1) (0,2) (1,0) (0,1) (0,0)
+                mma_bf16(d, make_desc(a0 + 2 * apiece), make_desc(sb), idesc, ks > 0 ? 1u : 0u);
+                mma_bf16(d, make_desc(a0 + apiece), make_desc(sb + bpiece), idesc, 1u);
+                mma_bf16(d, make_desc(a0), make_desc(sb + 2 * bpiece), idesc, 1u);
+                mma_bf16(d, make_desc(a0 + apiece), make_desc(sb), idesc, 1u);
+                mma_bf16(d, make_desc(a0), make_desc(sb + bpiece), idesc, 1u);
+                mma_bf16(d, make_desc(a0), make_desc(sb), idesc, 1u);
             }
-            mma_commit(smem_u32(mbar));
+            mma_commit(smem_u32(&empty[st]));
         }
         __syncwarp();
-        const int timed_out = __syncthreads_or(mbar_wait(smem_u32(mbar), phase) ? 0 : 1);
-        if (timed_out) {
-            // give the in-flight MMAs one more bounded wait before the tensor memory is freed
-            mbar_wait(smem_u32(mbar), phase);
-            if (tid == 0) atomicOr(err, 1);
-            ok = false;
+        last_stage = st;
+        last_parity = (uint32_t)((ks / TC_STAGES) & 1);
+        // refill the stage read by step ks - 1 with step ks + STAGES - 1, once those MMAs are done
+        const int nk = ks + TC_STAGES - 1;
+        if (nk < nsteps) {
+            if (ks >= 1) {
+                const int ps = (ks - 1) % TC_STAGES;
+                const uint32_t pp = (uint32_t)(((ks - 1) / TC_STAGES) & 1);
+                const int bad = __syncthreads_or(mbar_wait(smem_u32(&empty[ps]), pp) ? 0 : 1);
+                if (bad) {
+                    ok = false;
+                    break;
+                }
+            }
+            load_stage(nk, nk % TC_STAGES);
         }
-        phase ^= 1u;
-        __syncthreads();
+        cp_async_commit();
+    }
+    cp_async_wait<0>();
+    // every MMA of this block is tracked by its last commit
+    const int done = __syncthreads_and(mbar_wait(smem_u32(&empty[last_stage]), last_parity) ? 1 : 0);
+    if (!ok || !done) {
+        mbar_wait(smem_u32(&empty[last_stage]), last_parity);  // one more bounded wait before freeing TMEM
+        if (tid == 0) atomicOr(err, 1);
+        ok = false;
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (ok) {
         // epilogue: warp w holds TMEM lanes 32w..32w+31 = tile rows; 16 columns per load
-        const int row = warp * 32 + lane;
-        const bool vrow = row < nrows;
-        float *yrow = vrow ? Ypair + ((size_t)(ch.start + row / R) * R + (row % R)) * P : nullptr;
-        for (int c0 = 0; c0 < Npad; c0 += 16) {
-            uint32_t v[16];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                  "=r"(v[15])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (vrow) {
+        for (int t = 0; t < ntiles; ++t) {
+            const int row = t * TC_M + warp * 32 + lane;
+            const bool vrow = row < nrows;
+            float *yrow = Ypair + ((size_t)ch.start * R + row) * P;  // rows of a chunk are consecutive
+            for (int c0 = 0; c0 < Npad; c0 += 16) {
+                uint32_t v[16];
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * 256 + c0);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (vrow) {
+                    if (c0 + 16 <= P) {  // P % 4 == 0 and rows start 16-byte aligned
 #pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    if (c0 + i < P) yrow[c0 + i] = __uint_as_float(v[i]);
+                        for (int i = 0; i < 16; i += 4)
+                            *reinterpret_cast<float4 *>(yrow + c0 + i) =
+                                make_float4(__uint_as_float(v[i]), __uint_as_float(v[i + 1]),
+                                            __uint_as_float(v[i + 2]), __uint_as_float(v[i + 3]));
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            if (c0 + i < P) yrow[c0 + i] = __uint_as_float(v[i]);
+                    }
+                }
             }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
 }
 
 }  // namespace
 
 bool m2l_tc_supported(int P) { return P % 4 == 0 && P <= 256; }
 
+int m2l_tc_pairs_per_chunk(int R) { return TC_TILES * TC_M / R; }
+
 void build_tc_tables(Context &c) {
     Operators &o = c.ops;
     const int P = o.P;
     if (!m2l_tc_supported(P)) return;
     o.tc_Npad = (P + 15) / 16 * 16;
-    o.tc_Kpad = (P + TC_KC - 1) / TC_KC * TC_KC;
-    size_t per = (size_t)o.tc_Npad * o.tc_Kpad;
+    o.tc_Kpad = o.tc_Npad;
+    const size_t per = (size_t)3 * o.tc_Npad * o.tc_Kpad;
     o.m2l_tc.resize(kNumM2LClasses * per);
     dim3 grid(64, kNumM2LClasses);
-    k_build_tc_table<<<grid, 256, 0, c.stream>>>(P, o.tc_Npad, o.tc_Kpad, o.m2l32.p, o.m2l_tc.p);
+    k_build_tc_table<<<grid, 256, 0, c.stream>>>(P, o.tc_Npad, o.m2l64.p,
+                                                 reinterpret_cast<__nv_bfloat16 *>(o.m2l_tc.p));
     BEM_LAUNCH_CHECK();
-}
-
-size_t m2l_tc_smem_bytes(int Npad) {
-    return (size_t)(3 * TC_M * TC_KC + 3 * Npad * TC_KC) * sizeof(float) + 16 + 1024;
 }
 
 template <int R>
-void launch_m2l_tc(Context &c, const XChunk *chunks, int64_t nchunks, const float *X, float *Ypair, int *err) {
+void launch_m2l_tc(Context &c, const XChunk *chunks, int64_t nchunks, const float *X, int64_t xrows, float *Ypair,
+                   int *err) {
     const Operators &o = c.ops;
-    size_t sm = m2l_tc_smem_bytes(o.tc_Npad);
+    const int Npad = o.tc_Npad;
+    // split the multipoles once for all translations of this product
+    const size_t nxs = (size_t)3 * xrows * Npad;
+    c.xsplit.resize(nxs);
+    __nv_bfloat16 *xs = reinterpret_cast<__nv_bfloat16 *>(c.xsplit.p);
+    {
+        const int64_t plane = xrows * Npad;
+        const int nb = (int)std::min<int64_t>(div_up(plane, 256), 152 * 16);
+        k_split_x<<<nb, 256, 0, c.stream>>>(xrows, o.P, Npad, X, xs);
+        BEM_LAUNCH_CHECK();
+    }
+    const size_t sm = tc_layout(Npad).total;
     static bool attr_set[2] = {false, false};
     if (!attr_set[R == 4]) {  // once, for the largest tile (N_pad = 256)
         BEM_CUDA(cudaFuncSetAttribute(k_m2l_tc<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)m2l_tc_smem_bytes(256)));
+                                      (int)tc_layout(256).total));
         attr_set[R == 4] = true;
     }
-    k_m2l_tc<R><<<(unsigned)nchunks, TC_THREADS, sm, c.stream>>>(o.P, o.tc_Npad, o.tc_Kpad, o.m2l_tc.p, chunks,
-                                                                 c.tree.m2l_src.p, X, Ypair, err);
+    k_m2l_tc<R><<<(unsigned)nchunks, TC_THREADS, sm, c.stream>>>(
+        o.P, Npad, reinterpret_cast<const __nv_bfloat16 *>(o.m2l_tc.p), chunks, c.tree.m2l_src.p, xrows, xs, Ypair, err);
     BEM_LAUNCH_CHECK();
 }
 
-template void launch_m2l_tc<1>(Context &, const XChunk *, int64_t, const float *, float *, int *);
-template void launch_m2l_tc<4>(Context &, const XChunk *, int64_t, const float *, float *, int *);
+template void launch_m2l_tc<1>(Context &, const XChunk *, int64_t, const float *, int64_t, float *, int *);
+template void launch_m2l_tc<4>(Context &, const XChunk *, int64_t, const float *, int64_t, float *, int *);
 
 }  // namespace bem

@@ -43,107 +43,140 @@ struct V4<double> {
     using type = double4;
 };
 
-// One block per target leaf. Sources of the (up to 27) neighbour leaves are staged tile by tile
-// in shared memory as (x, y, z, q) and (n_x, n_y, n_z, w), positions relative to the target
-// leaf's centre in leaf-box units; each thread keeps up to KMAX receivers in registers, so a
-// staged source feeds several pairs. The self pair has r^2 = 0 exactly (same coordinates, zero
-// offset) and is skipped; the paper's quadrature excludes j = i (Eq. (ns1)).
-constexpr int P2P_KMAX = 4;
+// Near-field work is split into units of up to 64 receivers of one leaf (Tree::p2p_units);
+// one warp owns a unit, each lane keeps up to two receivers in registers, so a staged source
+// feeds two pairs and a leaf of n receivers wastes at most 31 lanes of its last unit. The warp
+// walks the (up to 27) neighbour leaves; each neighbour's sources are staged 32 at a time in
+// the warp's own shared-memory slice as (x, y, z, q) and (n_x, n_y, n_z, w), positions
+// relative to the target leaf's centre in leaf-box units. HQ / HW select the single- and
+// double-layer terms, so a product with one layer only (every GMRES product) pays for that
+// layer alone. The self pair has r^2 = 0 exactly (same coordinates, zero offset) and is
+// skipped; only the target leaf's own tiles can hold it, so only they test r^2 (the paper's
+// quadrature excludes j = i, Eq. (ns1); distinct vertices never coincide on a valid mesh).
+constexpr int P2P_WARPS = 4;   // warps (work units) per block
+constexpr int P2P_UNIT = 64;   // receivers per work unit
 
-template <class T, int R>
-__global__ void __launch_bounds__(P2P_THREADS) k_p2p_list(
-    const int32_t *__restrict__ bstart, const int32_t *__restrict__ bcount, const int32_t *__restrict__ nbr,
-    const int32_t *__restrict__ ncnt, const int8_t *__restrict__ nd, int64_t N, const T *__restrict__ loc,
-    const T *__restrict__ nrm, const T *__restrict__ q, const T *__restrict__ w, const T *__restrict__ far,
-    const double *__restrict__ ih, double *__restrict__ out) {
+template <class T, int R, bool HQ, bool HW>
+struct P2PStage {
     using T4 = typename V4<T>::type;
-    __shared__ T4 sA[P2P_THREADS];            // x, y, z, q (first RHS)
-    __shared__ T4 sB[P2P_THREADS];            // n_x, n_y, n_z, w (first RHS)
-    __shared__ T sQ[R > 1 ? R - 1 : 1][P2P_THREADS], sW[R > 1 ? R - 1 : 1][P2P_THREADS];
-    __shared__ int nb_start[27], nb_pre[28];
-    __shared__ T nb_d[27][3];
-    const int b = blockIdx.x, tid = threadIdx.x;
-    const int nn = ncnt[b];
-    if (tid < nn) {
-        int f = nbr[b * 27 + tid];
-        nb_start[tid] = bstart[f];
-        nb_pre[tid + 1] = bcount[f];
-        nb_d[tid][0] = (T)nd[(b * 27 + tid) * 4 + 0];
-        nb_d[tid][1] = (T)nd[(b * 27 + tid) * 4 + 1];
-        nb_d[tid][2] = (T)nd[(b * 27 + tid) * 4 + 2];
-    }
-    __syncthreads();
-    if (tid == 0) {
-        nb_pre[0] = 0;
-        for (int k = 0; k < nn; ++k) nb_pre[k + 1] += nb_pre[k];
-    }
-    __syncthreads();
-    const int S = nb_pre[nn];
-    const int s0 = bstart[b], cnt = bcount[b];
-    for (int rc0 = 0; rc0 < cnt; rc0 += P2P_THREADS * P2P_KMAX) {
-        const int kr = min(P2P_KMAX, (cnt - rc0 + P2P_THREADS - 1) / P2P_THREADS);  // uniform in the block
-        T xi[P2P_KMAX], yi[P2P_KMAX], zi[P2P_KMAX];
-        Comp<T> acc[P2P_KMAX][R];
+    T4 a[32];                                  // x, y, z, q (first RHS)
+    T4 b[HW ? 32 : 1];                         // n_x, n_y, n_z, w (first RHS)
+    T q[(R > 1 && HQ) ? R - 1 : 1][32];        // q of the other RHS
+    T w[(R > 1 && HW) ? R - 1 : 1][32];        // w of the other RHS
+};
+
+template <class T, int R, int KR, bool HQ, bool HW, bool SELF>
+__device__ __forceinline__ void p2p_tile(const P2PStage<T, R, HQ, HW> &sg, int ns, const T *xi, const T *yi,
+                                         const T *zi, Comp<T> (*acc)[R]) {
+    using T4 = typename V4<T>::type;
+    T part[KR][R];
 #pragma unroll
-        for (int k = 0; k < P2P_KMAX; ++k) {
-            const int li = rc0 + k * P2P_THREADS + tid;
-            const int64_t i = s0 + (li < cnt ? li : 0);
-            xi[k] = loc[i];
-            yi[k] = loc[N + i];
-            zi[k] = loc[2 * N + i];
+    for (int k = 0; k < KR; ++k)
+#pragma unroll
+        for (int r = 0; r < R; ++r) part[k][r] = (T)0;
+#pragma unroll 4
+    for (int s = 0; s < ns; ++s) {
+        const T4 a = sg.a[s];
+        T4 bb;
+        if (HW) bb = sg.b[s];
+#pragma unroll
+        for (int k = 0; k < KR; ++k) {
+            const T dx = xi[k] - a.x, dy = yi[k] - a.y, dz = zi[k] - a.z;
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            const T rinv = SELF ? (r2 > (T)0 ? rsqrt_t<T>(r2) : (T)0) : rsqrt_t<T>(r2);
+            if (HQ) {
+                part[k][0] += a.w * rinv;
+#pragma unroll
+                for (int r = 1; r < R; ++r) part[k][r] += sg.q[r - 1][s] * rinv;
+            }
+            if (HW) {
+                const T nd3 = (bb.x * dx + bb.y * dy + bb.z * dz) * (rinv * rinv * rinv);
+                part[k][0] += bb.w * nd3;
+#pragma unroll
+                for (int r = 1; r < R; ++r) part[k][r] += sg.w[r - 1][s] * nd3;
+            }
         }
-        for (int t0 = 0; t0 < S; t0 += P2P_THREADS) {
-            __syncthreads();
-            const int f = t0 + tid;
-            if (f < S) {
-                int k = 0;
-                while (nb_pre[k + 1] <= f) ++k;
-                const int j = nb_start[k] + (f - nb_pre[k]);
-                sA[tid] = T4{loc[j] + nb_d[k][0], loc[N + j] + nb_d[k][1], loc[2 * N + j] + nb_d[k][2], q[j]};
-                sB[tid] = T4{nrm[j], nrm[N + j], nrm[2 * N + j], w[j]};
+    }
+#pragma unroll
+    for (int k = 0; k < KR; ++k)
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[k][r].add(part[k][r]);
+}
+
+template <class T, int R, bool HQ, bool HW>
+__global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_units(
+    const int2 *__restrict__ units, int64_t nunits, const int32_t *__restrict__ bstart,
+    const int32_t *__restrict__ bcount, const int32_t *__restrict__ nbr, const int32_t *__restrict__ ncnt,
+    const int8_t *__restrict__ nd, int64_t N, const T *__restrict__ loc, const T *__restrict__ nrm,
+    const T *__restrict__ q, const T *__restrict__ w, const T *__restrict__ far, const double *__restrict__ ih,
+    double *__restrict__ out) {
+    __shared__ P2PStage<T, R, HQ, HW> stage[P2P_WARPS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t u = (int64_t)blockIdx.x * P2P_WARPS + warp;
+    if (u >= nunits) return;  // the whole warp leaves; only warp-level barriers follow
+    P2PStage<T, R, HQ, HW> &sg = stage[warp];
+    const int2 un = units[u];
+    const int b = un.x, r0 = un.y;
+    const int s0 = bstart[b];
+    const int nr = min(P2P_UNIT, bcount[b] - r0);
+    const bool two = nr > 32;  // uniform in the warp
+    T xi[2], yi[2], zi[2];
+    Comp<T> acc[2][R];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int li = k * 32 + lane;
+        const int64_t i = s0 + r0 + (li < nr ? li : 0);
+        xi[k] = loc[i];
+        yi[k] = loc[N + i];
+        zi[k] = loc[2 * N + i];
+    }
+    // neighbour table of the target leaf, one entry per lane, broadcast by shuffles
+    const int nn = ncnt[b];
+    int my_f = 0;
+    T my_d[3] = {(T)0, (T)0, (T)0};
+    if (lane < nn) {
+        my_f = nbr[b * 27 + lane];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) my_d[d] = (T)nd[(b * 27 + lane) * 4 + d];
+    }
+    for (int k = 0; k < nn; ++k) {
+        const int f = __shfl_sync(0xffffffffu, my_f, k);
+        const T ox = __shfl_sync(0xffffffffu, my_d[0], k);
+        const T oy = __shfl_sync(0xffffffffu, my_d[1], k);
+        const T oz = __shfl_sync(0xffffffffu, my_d[2], k);
+        const int fs = bstart[f], fc = bcount[f];
+        const bool self = (f == b);
+        for (int t0 = 0; t0 < fc; t0 += 32) {
+            if (t0 + lane < fc) {
+                const int64_t j = fs + t0 + lane;
+                sg.a[lane] = typename V4<T>::type{loc[j] + ox, loc[N + j] + oy, loc[2 * N + j] + oz,
+                                                  HQ ? q[j] : (T)0};
+                if (HW) sg.b[lane] = typename V4<T>::type{nrm[j], nrm[N + j], nrm[2 * N + j], w[j]};
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    sQ[r - 1][tid] = q[r * N + j];
-                    sW[r - 1][tid] = w[r * N + j];
+                    if (HQ) sg.q[r - 1][lane] = q[r * N + j];
+                    if (HW) sg.w[r - 1][lane] = w[r * N + j];
                 }
             }
-            __syncthreads();
-            const int ns = min(P2P_THREADS, S - t0);
-            T part[P2P_KMAX][R];
-#pragma unroll
-            for (int k = 0; k < P2P_KMAX; ++k)
-#pragma unroll
-                for (int r = 0; r < R; ++r) part[k][r] = (T)0;
-#pragma unroll 2
-            for (int sI = 0; sI < ns; ++sI) {
-                const T4 a = sA[sI], bb = sB[sI];
-#pragma unroll
-                for (int k = 0; k < P2P_KMAX; ++k) {
-                    if (k < kr) {
-                        const T dx = xi[k] - a.x, dy = yi[k] - a.y, dz = zi[k] - a.z;
-                        const T r2 = dx * dx + dy * dy + dz * dz;
-                        const T rinv = r2 > (T)0 ? rsqrt_t<T>(r2) : (T)0;
-                        const T rinv3 = rinv * rinv * rinv;
-                        const T nd3 = (bb.x * dx + bb.y * dy + bb.z * dz) * rinv3;
-                        part[k][0] += a.w * rinv + bb.w * nd3;
-#pragma unroll
-                        for (int r = 1; r < R; ++r) part[k][r] += sQ[r - 1][sI] * rinv + sW[r - 1][sI] * nd3;
-                    }
-                }
+            __syncwarp();
+            const int ns = min(32, fc - t0);
+            if (self) {
+                if (two) p2p_tile<T, R, 2, HQ, HW, true>(sg, ns, xi, yi, zi, acc);
+                else p2p_tile<T, R, 1, HQ, HW, true>(sg, ns, xi, yi, zi, acc);
+            } else {
+                if (two) p2p_tile<T, R, 2, HQ, HW, false>(sg, ns, xi, yi, zi, acc);
+                else p2p_tile<T, R, 1, HQ, HW, false>(sg, ns, xi, yi, zi, acc);
             }
-#pragma unroll
-            for (int k = 0; k < P2P_KMAX; ++k)
-#pragma unroll
-                for (int r = 0; r < R; ++r) acc[k][r].add(part[k][r]);
+            __syncwarp();
         }
+    }
 #pragma unroll
-        for (int k = 0; k < P2P_KMAX; ++k) {
-            const int li = rc0 + k * P2P_THREADS + tid;
-            if (k < kr && li < cnt) {
-                const int64_t i = s0 + li;
+    for (int k = 0; k < 2; ++k) {
+        const int li = k * 32 + lane;
+        if (li < nr) {
+            const int64_t i = s0 + r0 + li;
 #pragma unroll
-                for (int r = 0; r < R; ++r) out[r * N + i] = ((double)far[r * N + i] + acc[k][r].get()) * ih[i];
-            }
+            for (int r = 0; r < R; ++r) out[r * N + i] = ((double)far[r * N + i] + acc[k][r].get()) * ih[i];
         }
     }
 }
@@ -272,23 +305,33 @@ __global__ void __launch_bounds__(P2P_THREADS) k_direct32(int64_t N, const float
 
 }  // namespace
 
-template <class T, int R>
-void launch_p2p_list(Context &c, const T *q, const T *w, const T *far, double *out_sorted) {
+template <class T, int R, bool HQ, bool HW>
+static void launch_units(Context &c, const T *q, const T *w, const T *far, double *out_sorted) {
     Tree &t = c.tree;
     const int L = t.L;
     const T *loc = sizeof(T) == 8 ? (const T *)t.loc64.p : (const T *)t.loc32.p;
     const T *nrm = sizeof(T) == 8 ? (const T *)t.nrm64.p : (const T *)t.nrm32.p;
-    int nleaf = t.nb[L];
-    k_p2p_list<T, R><<<nleaf, P2P_THREADS, 0, c.stream>>>(t.bstart.p + t.base[L], t.bcount.p + t.base[L], t.nbr.p,
-                                                          t.nbr_cnt.p, t.nbr_d.p, c.N, loc, nrm, q, w, far, t.ih.p,
-                                                          out_sorted);
+    const int64_t nu = t.n_p2p_units;
+    if (nu == 0) return;
+    k_p2p_units<T, R, HQ, HW><<<(unsigned)div_up(nu, P2P_WARPS), P2P_WARPS * 32, 0, c.stream>>>(
+        t.p2p_units.p, nu, t.bstart.p + t.base[L], t.bcount.p + t.base[L], t.nbr.p, t.nbr_cnt.p, t.nbr_d.p, c.N, loc,
+        nrm, q, w, far, t.ih.p, out_sorted);
     BEM_LAUNCH_CHECK();
 }
 
-template void launch_p2p_list<float, 1>(Context &, const float *, const float *, const float *, double *);
-template void launch_p2p_list<float, 4>(Context &, const float *, const float *, const float *, double *);
-template void launch_p2p_list<double, 1>(Context &, const double *, const double *, const double *, double *);
-template void launch_p2p_list<double, 4>(Context &, const double *, const double *, const double *, double *);
+template <class T, int R>
+void launch_p2p_list(Context &c, const T *q, const T *w, const T *far, double *out_sorted, bool hq, bool hw) {
+    if (R > 1 || (hq && hw)) launch_units<T, R, true, true>(c, q, w, far, out_sorted);
+    else if (hw) launch_units<T, R, false, true>(c, q, w, far, out_sorted);
+    else launch_units<T, R, true, false>(c, q, w, far, out_sorted);  // also the all-zero product
+}
+
+template void launch_p2p_list<float, 1>(Context &, const float *, const float *, const float *, double *, bool, bool);
+template void launch_p2p_list<float, 4>(Context &, const float *, const float *, const float *, double *, bool, bool);
+template void launch_p2p_list<double, 1>(Context &, const double *, const double *, const double *, double *, bool,
+                                         bool);
+template void launch_p2p_list<double, 4>(Context &, const double *, const double *, const double *, double *, bool,
+                                         bool);
 
 template <int R>
 void launch_direct(Context &c, int prec, const double *f, const double *const *xL, const double *g,

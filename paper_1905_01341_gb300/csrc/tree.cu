@@ -548,6 +548,20 @@ __global__ void k_sorted_points(int64_t N, int L, int deep, const int32_t *__res
     }
     s_sorted[i] = s[j];
 }
+// Near-field work units: leaf b gets ceil(n_b / 64) units (b, 64 u).
+__global__ void k_p2p_unit_count(int nleaf, const int32_t *__restrict__ bcount, int32_t *__restrict__ cnt) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nleaf) cnt[b] = (bcount[b] + 63) / 64;
+}
+
+__global__ void k_p2p_unit_emit(int nleaf, const int32_t *__restrict__ bcount, const int32_t *__restrict__ off,
+                                int2 *__restrict__ units) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nleaf) return;
+    const int n = (bcount[b] + 63) / 64;
+    for (int u = 0; u < n; ++u) units[off[b] + u] = make_int2(b, 64 * u);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------------ build
@@ -696,6 +710,22 @@ void build_tree(Context &c) {
     k_neighbours<<<div_up(nleaf, tb), tb, 0, st>>>(nleaf, L, t.bkey.p + t.base[L], t.bcount.p + t.base[L],
                                                     t.nbr.p, t.nbr_cnt.p, t.nbr_d.p, pairs.p);
     BEM_LAUNCH_CHECK();
+    {
+        DevBuf<int32_t> ucnt, uoff, utot;
+        ucnt.resize(nleaf + 1);
+        uoff.resize(nleaf + 1);
+        utot.resize(1);
+        k_p2p_unit_count<<<div_up(nleaf, tb), tb, 0, st>>>(nleaf, t.bcount.p + t.base[L], ucnt.p);
+        BEM_LAUNCH_CHECK();
+        exclusive_scan_i32(ucnt.p, uoff.p, nleaf, utot.p, st);
+        int32_t nu = 0;
+        BEM_CUDA(cudaMemcpyAsync(&nu, utot.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        BEM_CUDA(cudaStreamSynchronize(st));
+        t.n_p2p_units = nu;
+        t.p2p_units.resize(std::max<int64_t>(nu, 1));
+        k_p2p_unit_emit<<<div_up(nleaf, tb), tb, 0, st>>>(nleaf, t.bcount.p + t.base[L], uoff.p, t.p2p_units.p);
+        BEM_LAUNCH_CHECK();
+    }
 
     // 6. M2L pairs of levels 2..L, then sorted by offset class
     std::vector<int64_t> lvl_off(L + 2, 0);
