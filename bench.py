@@ -36,6 +36,11 @@ FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 fl
 P2P_FLOPS_SL, P2P_FLOPS_DL, P2P_FLOPS_4RHS = 11, 19, 33
 
 
+def progress(msg: str) -> None:
+    """One line of progress on stderr (the JSON result goes to stdout)."""
+    print("[bench] " + msg, file=sys.stderr, flush=True)
+
+
 def _load_peaks() -> dict:
     """Measured HBM / BF16 peaks of this GPU pool, when present beside this file."""
     try:
@@ -262,6 +267,7 @@ def run_ours(args):
                            gmres_restart=args.restart, gmres_precond=args.precond, m2l_tensor_cores=args.m2l_tc)
         return c
 
+    progress("workload ready: %d unknowns, %d bubbles" % (N, mesh.m))
     ctx = make_ctx(prec)
     ctx.upload(xyz, tri, voff, toff)
     sp = bem.bem_step_params_default(pa=args.pa, pf=args.pf)
@@ -269,7 +275,11 @@ def run_ours(args):
 
     warm = []
     for _ in range(args.warmup):
+        t0 = time.perf_counter()
         warm.append(bem.bem_step(ctx.ctx))
+        progress("warm-up step %d: %.2f s, %d GMRES iterations, %d not converged, levels %d" % (
+            len(warm), time.perf_counter() - t0, warm[-1]["gmres_iters"], warm[-1]["nonconverged"],
+            ctx.stats()["levels"]))
     torch.cuda.synchronize()
     st0 = ctx.stats()
     bem.bem_profile_enable(ctx.ctx, True)
@@ -283,6 +293,7 @@ def run_ours(args):
     infos = []
     for _ in range(args.steps):
         infos.append(bem.bem_step(ctx.ctx))
+        progress("timed step %d: %d GMRES iterations" % (len(infos), infos[-1]["gmres_iters"]))
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(world)

@@ -71,7 +71,10 @@ typedef struct {
     int32_t p_fmm;          /* truncation number: degrees 0..p_fmm-1, p_fmm^2 coefficients
                                per expansion (Section 3.7). Range 2..20. Default 14.           */
     int32_t leaf_target;    /* target mean points per non-empty leaf box (the clustering
-                               parameter s of Section 3.6). Default 64.                        */
+                               parameter s of Section 3.6); 0 = autotune: the first build after
+                               a mesh upload times one product at the depth for 64 points per
+                               leaf and one level either side and keeps the fastest depth.
+                               Default 64.                                                     */
     int32_t fixed_level;    /* > 0: force the octree depth l_max to this value (2..10).        */
     int32_t precision;      /* bem_precision. Default BEM_PREC_MIXED.                          */
     int32_t mvp;            /* bem_mvp_kind. Default BEM_MVP_FMM.                              */
@@ -85,8 +88,15 @@ typedef struct {
                                by cancellation, which magnifies rounding. Default 1.          */
     int32_t gmres_precond;  /* 0: unpreconditioned GMRES, as in the paper (Section 3.8);
                                1: right Jacobi preconditioning x = D^-1 y with D = diag(L_ii)
-                               (same solution and true-residual test; removes the spread of
-                               the single layer's scale across bubbles of different radii).
+                               (removes the spread of the single layer's scale across bubbles
+                               of different radii);
+                               2: right bubble-block preconditioning: per distinct bubble shape,
+                               the inverse of the isolated bubble's single-layer block (built
+                               from the geometry of the first solve after a mesh upload and
+                               kept), scaled by each bubble's current size; removes the spread
+                               of each bubble's own spectrum (R/(2n+1) on a sphere). Needs
+                               bubbles; memory n^2 per distinct shape of n vertices.
+                               Every mode stops on the same true residual |b - L q| / |b|.
                                Default 0.                                                      */
     int32_t gmres_maxit;    /* maximum GMRES iterations. Default 100.                          */
     int32_t gmres_restart;  /* restart length; 0 = no restart (= maxit). Default 0.            */

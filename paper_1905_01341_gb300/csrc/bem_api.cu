@@ -150,7 +150,7 @@ int guarded(void *ctx, F &&fn) {
 
 void check_params(const bem_params &p) {
     if (p.p_fmm < 2 || p.p_fmm > kMaxPfmm) fail(BEM_ERR_ARG, "p_fmm must be in 2..20");
-    if (p.leaf_target < 1) fail(BEM_ERR_ARG, "leaf_target must be >= 1");
+    if (p.leaf_target < 0) fail(BEM_ERR_ARG, "leaf_target must be >= 0 (0 = autotune the depth)");
     if (p.fixed_level < 0 || p.fixed_level > kDeepLevel || p.fixed_level == 1)
         fail(BEM_ERR_ARG, "fixed_level must be 0 or in 2..10");
     if (p.precision != BEM_PREC_FP64 && p.precision != BEM_PREC_MIXED) fail(BEM_ERR_ARG, "bad precision");
@@ -159,7 +159,7 @@ void check_params(const bem_params &p) {
     if (p.mvp != BEM_MVP_FMM && p.mvp != BEM_MVP_DIRECT) fail(BEM_ERR_ARG, "bad mvp kind");
     if (p.m2l_tensor_cores != 0 && p.m2l_tensor_cores != 1) fail(BEM_ERR_ARG, "m2l_tensor_cores must be 0 or 1");
     if (p.gmres_maxit < 1 || p.gmres_restart < 0 || p.gmres_restart > 127) fail(BEM_ERR_ARG, "bad GMRES limits");
-    if (p.gmres_precond != 0 && p.gmres_precond != 1) fail(BEM_ERR_ARG, "gmres_precond must be 0 or 1");
+    if (p.gmres_precond < 0 || p.gmres_precond > 2) fail(BEM_ERR_ARG, "gmres_precond must be 0, 1 or 2");
     if (!(p.gmres_tol > 0.0)) fail(BEM_ERR_ARG, "gmres_tol must be > 0");
 }
 
@@ -174,6 +174,58 @@ void apply_full(Context &c, double f, const double *xL, double g, const double *
     offdiag_apply(c, 1, fa, xl, ga, xm, o, c.prm.precision);
     k_add_diag<<<div_up(c.N, 256), 256, 0, c.stream>>>(c.N, f, xL, g, xM, c.ldiag.p, c.mdiag.p, out);
     BEM_LAUNCH_CHECK();
+}
+
+// Octree depth autotuner (leaf_target = 0): times one single-layer product at the depth the
+// leaf-count rule gives for 64 points per leaf and at one level either side, and keeps the
+// fastest for this mesh. Points on surfaces fill ~4x more boxes per level, not 8x, so the
+// near-field / far-field balance moves in coarse steps and is cheapest to settle by timing.
+void tune_tree_level(Context &c) {
+    const int64_t N = c.N;
+    c.ones.resize(N);
+    k_fill<<<div_up(N, 256), 256, 0, c.stream>>>(N, 1.0, c.ones.p);
+    BEM_LAUNCH_CHECK();
+    DevBuf<double> out;
+    out.resize(N);
+    const auto saved_apply = c.stats.n_apply, saved_apply_rhs = c.stats.n_apply_rhs;
+    const int saved_target = c.prm.leaf_target;
+    c.prm.leaf_target = 64;
+    c.level_override = 0;
+    build_tree(c);
+    c.prm.leaf_target = saved_target;
+    const int L0 = c.tree.L;
+    cudaEvent_t e0, e1;
+    BEM_CUDA(cudaEventCreate(&e0));
+    BEM_CUDA(cudaEventCreate(&e1));
+    int best = L0;
+    float best_ms = 0.f;
+    for (int L = std::max(2, L0 - 1); L <= std::min(L0 + 1, c.tree.deep); ++L) {
+        c.level_override = L;
+        build_tree(c);
+        c.m2l_chunks_h.clear();
+        c.tc_chunks_r = 0;
+        double f = 1.0, g = 0.0;
+        const double *xl[1] = {c.ones.p};
+        const double *xm[1] = {nullptr};
+        double *o[1] = {out.p};
+        offdiag_apply(c, 1, &f, xl, &g, xm, o, c.prm.precision);  // warm-up (chunk tables, buffers)
+        BEM_CUDA(cudaEventRecord(e0, c.stream));
+        offdiag_apply(c, 1, &f, xl, &g, xm, o, c.prm.precision);
+        BEM_CUDA(cudaEventRecord(e1, c.stream));
+        BEM_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        BEM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (L == std::max(2, L0 - 1) || ms < best_ms) {
+            best = L;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c.level_override = 0;
+    c.tuned_level = best;
+    c.stats.n_apply = saved_apply;  // the timing products are not the caller's
+    c.stats.n_apply_rhs = saved_apply_rhs;
 }
 
 void build_all(Context &c) {
@@ -202,6 +254,8 @@ void build_all(Context &c) {
         c.tc_chunks_r = 0;
         c.tc_err.resize(1);
         BEM_CUDA(cudaMemsetAsync(c.tc_err.p, 0, sizeof(int), c.stream));
+        if (c.prm.leaf_target == 0 && c.prm.fixed_level == 0 && c.tuned_level == 0) tune_tree_level(c);
+        c.level_override = c.prm.fixed_level == 0 ? c.tuned_level : 0;
         {
             PhaseScope ps(c, PH_TREE);
             build_tree(c);
@@ -357,6 +411,8 @@ int bem_mesh_upload(void *ctx, int64_t N, const double *xyz, int64_t T, const in
         c.built = false;
         c.mesh_ok = false;
         c.points_only = false;
+        c.bp.ready = false;
+        c.tuned_level = 0;
         c.C = 1;
         c.cluster_boff.clear();
         c.N = N;
@@ -425,6 +481,8 @@ int bem_points_upload(void *ctx, int64_t N, const double *xyz) {
         c.built = false;
         c.mesh_ok = false;
         c.points_only = true;
+        c.bp.ready = false;
+        c.tuned_level = 0;
         c.C = 1;
         c.cluster_boff.clear();
         c.N = N;

@@ -1,5 +1,5 @@
-// Unpreconditioned GMRES (Saad and Schultz) for L q = b, Section 3.8, kept on the device in
-// FP64. The Krylov basis V, the Hessenberg matrix, the Givens rotations and the rotated
+// GMRES (Saad and Schultz) for L q = b, Section 3.8, kept on the device in FP64: unpreconditioned
+// as in the paper, or right-preconditioned (Jacobi, or the bubble blocks of precond.cu). The Krylov basis V, the Hessenberg matrix, the Givens rotations and the rotated
 // right-hand side live in device memory; the host only reads the residual estimate once
 // per iteration to decide whether to stop.
 //
@@ -16,26 +16,42 @@ namespace bem {
 namespace {
 
 constexpr int RED_THREADS = 256;
-constexpr int RED_BLOCKS = 512;  // fixed grid: fixed summation order
+constexpr int RED_BLOCKS = 152 * 3;  // fixed grid: fixed summation order
+constexpr int RED_JB = 8;            // basis vectors per pass over w
 
-// partial[j * RED_BLOCKS + block] = sum over the block's slice of V_j . w, j = 0..nv-1
+// partial[j * RED_BLOCKS + block] = sum over the block's slice of V_j . w, j = 0..nv-1.
+// Each pass reads w once for RED_JB vectors (independent accumulators), then reduces the
+// RED_JB sums across the block in a fixed order.
 __global__ void __launch_bounds__(RED_THREADS) k_multidot(int nv, int64_t N, const double *__restrict__ V,
                                                           size_t ldv, const double *__restrict__ w,
                                                           double *__restrict__ partial) {
-    __shared__ double red[RED_THREADS / 32];
+    __shared__ double red[RED_THREADS / 32][RED_JB];
     const int64_t chunk = (N + RED_BLOCKS - 1) / RED_BLOCKS;
     const int64_t i0 = blockIdx.x * chunk, i1 = (N < i0 + chunk) ? N : i0 + chunk;
-    for (int j = 0; j < nv; ++j) {
-        const double *v = V + j * ldv;
-        double s = 0.0;
-        for (int64_t i = i0 + threadIdx.x; i < i1; i += RED_THREADS) s = fma(v[i], w[i], s);
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j0 = 0; j0 < nv; j0 += RED_JB) {
+        const int nj = min(RED_JB, nv - j0);
+        double s[RED_JB];
+#pragma unroll
+        for (int jj = 0; jj < RED_JB; ++jj) s[jj] = 0.0;
+#pragma unroll 2
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += RED_THREADS) {
+            const double wi = w[i];
+#pragma unroll
+            for (int jj = 0; jj < RED_JB; ++jj)
+                if (jj < nj) s[jj] = fma(V[(size_t)(j0 + jj) * ldv + i], wi, s[jj]);
+        }
+#pragma unroll
+        for (int jj = 0; jj < RED_JB; ++jj) {
+            double t = s[jj];
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (lane == 0) red[warp][jj] = t;
+        }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < nj) {
             double t = 0.0;
-            for (int k = 0; k < RED_THREADS / 32; ++k) t += red[k];
-            partial[(size_t)j * RED_BLOCKS + blockIdx.x] = t;
+            for (int k = 0; k < RED_THREADS / 32; ++k) t += red[k][threadIdx.x];
+            partial[(size_t)(j0 + threadIdx.x) * RED_BLOCKS + blockIdx.x] = t;
         }
         __syncthreads();
     }
@@ -63,6 +79,7 @@ __global__ void k_multiaxpy(int nv, int64_t N, const double *__restrict__ V, siz
     __syncthreads();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         double acc = 0.0;
+#pragma unroll 8
         for (int j = 0; j < nv; ++j) acc = fma(hs[j], V[j * ldv + i], acc);
         w[i] += sign * acc;
     }
@@ -189,8 +206,10 @@ void gmres_solve(Context &c, const double *b, double *x, int *iters_out, double 
     const int m = std::min({maxit, c.prm.gmres_restart > 0 ? c.prm.gmres_restart : maxit, 127});
     const double tol = c.prm.gmres_tol;
     Vec vec(c);
-    const bool precond = c.prm.gmres_precond == 1;
+    const int pmode = c.prm.gmres_precond;  // 0 none, 1 Jacobi, 2 bubble blocks
+    const bool precond = pmode != 0;
     if (precond) c.zv.resize(N);
+    if (pmode == 2) block_precond_prepare(c);
     c.V.resize((size_t)(m + 1) * N);
     c.wv.resize(N);
     c.rv.resize(N);
@@ -240,9 +259,15 @@ void gmres_solve(Context &c, const double *b, double *x, int *iters_out, double 
         int kk = 0;
         for (int k = 0; k < m; ++k) {
             double *vk = c.V.p + (size_t)k * N;
-            if (precond) {  // w = A D^-1 v_k
+            if (pmode == 1) {  // w = A D^-1 v_k
                 k_scale_by<<<vec.grid, 256, 0, c.stream>>>(N, c.ldiag.p, vk, c.zv.p);
                 BEM_LAUNCH_CHECK();
+                apply_full(c, 1.0, c.zv.p, 0.0, nullptr, c.wv.p);
+            } else if (pmode == 2) {  // w = A P v_k
+                {
+                    PhaseScope ps(c, PH_GMRES);
+                    block_precond_apply(c, vk, c.zv.p);
+                }
                 apply_full(c, 1.0, c.zv.p, 0.0, nullptr, c.wv.p);
             } else {
                 apply_full(c, 1.0, vk, 0.0, nullptr, c.wv.p);
@@ -268,11 +293,19 @@ void gmres_solve(Context &c, const double *b, double *x, int *iters_out, double 
         }
         k_backsolve<<<1, 1, 0, c.stream>>>(kk, m, c.hmat.p, c.gvec.p, c.yvec.p);
         BEM_LAUNCH_CHECK();
-        if (precond) {  // x += D^-1 V y
+        if (pmode == 1) {  // x += D^-1 V y
             BEM_CUDA(cudaMemsetAsync(c.zv.p, 0, N * sizeof(double), c.stream));
             vec.multiaxpy(kk, c.V.p, N, c.yvec.p, 1.0, c.zv.p);
             k_add_scaled<<<vec.grid, 256, 0, c.stream>>>(N, c.ldiag.p, c.zv.p, x);
             BEM_LAUNCH_CHECK();
+        } else if (pmode == 2) {  // x += P V y
+            BEM_CUDA(cudaMemsetAsync(c.zv.p, 0, N * sizeof(double), c.stream));
+            vec.multiaxpy(kk, c.V.p, N, c.yvec.p, 1.0, c.zv.p);
+            {
+                PhaseScope ps(c, PH_GMRES);
+                block_precond_apply(c, c.zv.p, c.rv.p);
+            }
+            vec.axpby(1.0, c.rv.p, 1.0, x);
         } else {
             vec.multiaxpy(kk, c.V.p, N, c.yvec.p, 1.0, x);
         }

@@ -209,6 +209,14 @@ struct Profiler {
 
 // Per-shape least-squares spherical-harmonic basis (Eqs. (3.22)-(3.23)): for every distinct
 // initial bubble shape, G [nd][Pf] and G+ = (G^T G)^(-1) G^T [Pf][nd], concatenated.
+// Bubbles whose vertex directions from their centroid coincide (same vertex count and
+// order) share one shape; `rep` is the first bubble of the shape.
+struct BubbleShape {
+    int64_t rep;
+    int nd;
+    double cx, cy, cz;  // centroid of the representative
+};
+
 struct ShBasis {
     int pf = 0, Pf = 0;
     DevBuf<double> G, Gp;
@@ -248,6 +256,9 @@ struct Context {
     // cluster_boff[c]..cluster_boff[c+1]-1; no interaction crosses clusters
     int64_t C = 1;
     std::vector<int64_t> cluster_boff;
+    // octree depth: level_override > 0 forces l_max (depth autotuning); tuned_level is the
+    // depth the autotuner chose for this mesh (0 = not tuned yet)
+    int level_override = 0, tuned_level = 0;
     DevBuf<int32_t> vcid;          // [N] cluster of every vertex (when C > 1)
 
     // geometry (caller order)
@@ -291,6 +302,19 @@ struct Context {
 
     // GMRES
     DevBuf<double> V, wv, rv, bv, zv, hcol, hmat, givens, gvec, yvec, partial, scal;
+    // bubble-block preconditioner (gmres_precond = 2, precond.cu): per distinct bubble shape,
+    // the inverse of the isolated unit-size bubble's single-layer block, built from the
+    // geometry of the first solve after a mesh upload
+    struct BlockPrecond {
+        bool ready = false;
+        std::vector<int> nd;              // vertices per shape
+        std::vector<int64_t> inv_off;     // [shapes + 1] offsets (elements) into inv64 / inv32
+        std::vector<int64_t> first;       // [shapes + 1] offsets into the grouped bubble lists
+        DevBuf<double> inv64;             // row-major nd x nd per shape, unit size
+        DevBuf<float> inv32;
+        DevBuf<int64_t> bub_voff;         // [M] first vertex of each bubble, grouped by shape
+        DevBuf<double> bub_scale;         // [M] 1 / (mean centroid distance) at the current geometry
+    } bp;
     HostPinned<double> hscal;
 
     bem_stats stats{};
@@ -368,6 +392,12 @@ void step_init(Context &c, const double *phi0_dev, const double *q0_dev, const b
 void step_advance(Context &c, bem_step_stats &st);
 void step_get_state(Context &c, double *xyz, double *phi, double *q, double *t);
 void build_sh_basis(Context &c, int pf, ShBasis &B, int *bad, const double *xyz = nullptr);
+// Groups the bubbles by shape from host coordinates hx [3][N] (timestep.cu).
+void find_shapes(const Context &c, const std::vector<double> &hx, std::vector<BubbleShape> &shapes,
+                 std::vector<int32_t> &shape_of);
+// precond.cu: bubble-block preconditioner of GMRES
+void block_precond_prepare(Context &c);                     // build once, refresh the per-bubble scales
+void block_precond_apply(Context &c, const double *y, double *z);  // z = P y
 const double *step_initial_xyz(Context &c);
 
 // mlp.cu

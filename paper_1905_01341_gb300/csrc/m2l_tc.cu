@@ -1,11 +1,13 @@
 // M2L translations on the 5th-generation tensor cores (tcgen05, TMEM accumulators).
 //
-// For one offset class c and a chunk of up to 256/R (source, target) pairs, the product
+// For one offset class c and a chunk of up to 128/R (source, target) pairs, the product
 //   Y[pair, rhs][n] = sum_k T_c[n][k] X[src, rhs][k]
-// is two MMA tiles D_t = A_t B^T (t = 0, 1) with M = 128 rows (pair, rhs) each, N = P rounded
-// up to 16 output coefficients and K = P input coefficients: A_t = gathered multipole rows,
-// B = T_c (row n of T_c is K-contiguous, i.e. K-major). The two tiles share every staged
-// block of T_c, which halves its traffic.
+// is one MMA tile D = A B^T with M = 128 rows (pair, rhs), N = P rounded up to 16 output
+// coefficients and K = P input coefficients: A = gathered multipole rows, B = T_c (row n of
+// T_c is K-contiguous, i.e. K-major). A block holds 256 TMEM columns and under 113 KB of
+// shared memory, so two blocks share an SM and one's MMAs overlap the other's pipeline fill
+// and epilogue. (The code also supports TC_TILES = 2 tiles of one class per block sharing the
+// staged blocks of T_c.)
 //
 // Accuracy: both operands are split into three BF16 pieces, x = x0 + x1 + x2 (x0 = bf16(x),
 // x1 = bf16(x - x0), x2 = bf16(x - x0 - x1)), and D accumulates in FP32 the six products with
@@ -16,10 +18,10 @@
 // build from its FP64 values; the multipoles are split once per product (k_split_x).
 //
 // Data movement: K advances 16 at a time (one kind::f16 MMA); each 16-wide K step is one
-// pipeline stage holding A (3 pieces x 2 tiles x 128 x 16) and B (3 pieces x N_pad x 16) in
+// pipeline stage holding A (3 pieces x tiles x 128 x 16) and B (3 pieces x N_pad x 16) in
 // the canonical K-major layout without swizzle (8-row x 16-byte core matrices, K-adjacent core
 // matrices 128 B apart, 8-row groups 256 B apart). All threads fill stages with cp.async
-// (16-byte copies; rows past the chunk read as zeros), four stages deep; one elected thread
+// (16-byte copies; rows past the chunk read as zeros), three stages deep; one elected thread
 // issues the MMAs of a stage as soon as it has landed and commits them to the stage's
 // mbarrier, which releases the stage for refilling. Every wait is bounded: one that runs out
 // sets an error flag and the block skips ahead, waiting (bounded) for its MMAs in flight
@@ -32,9 +34,9 @@ namespace bem {
 namespace {
 
 constexpr int TC_M = 128;        // rows per tile
-constexpr int TC_TILES = 2;      // tiles per block (same class, shared B stages)
+constexpr int TC_TILES = 1;      // tiles per block (same class, shared B stages)
 constexpr int TC_K = 16;         // K per stage (one kind::f16 MMA)
-constexpr int TC_STAGES = 4;
+constexpr int TC_STAGES = 3;
 constexpr int TC_THREADS = 128;
 constexpr uint32_t TC_LBO = 128;  // bytes between K-adjacent core matrices
 constexpr uint32_t TC_SBO = 256;  // bytes between 8-row groups
@@ -173,7 +175,7 @@ __host__ __device__ inline TcLayout tc_layout(int Npad) {
 }
 
 template <int R>
-__global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __nv_bfloat16 *__restrict__ tcB,
+__global__ void __launch_bounds__(TC_THREADS, 2) k_m2l_tc(int P, int Npad, const __nv_bfloat16 *__restrict__ tcB,
                                                        const XChunk *__restrict__ chunks,
                                                        const int32_t *__restrict__ srcs, int64_t xrows,
                                                        const __nv_bfloat16 *__restrict__ Xs, float *__restrict__ Ypair,
@@ -191,7 +193,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
     if (*reinterpret_cast<volatile int *>(err) != 0) return;
     const XChunk ch = chunks[blockIdx.x];
     const int nrows = ch.count * R;
-    const int ntiles = nrows > TC_M ? 2 : 1;
+    const int ntiles = (nrows + TC_M - 1) / TC_M;  // <= TC_TILES
     const int nsteps = Npad / TC_K;
     for (int r = tid; r < TC_TILES * TC_M; r += TC_THREADS) s_src[r] = (r < nrows) ? srcs[ch.start + r / R] : -1;
     if (tid == 0) {
@@ -200,7 +202,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot)));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "n"(TC_TILES * 256));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -330,7 +333,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TC_TILES * 256));
 }
 
 }  // namespace

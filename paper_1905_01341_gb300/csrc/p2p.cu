@@ -17,8 +17,15 @@ constexpr double kInv4Pi = 0.0795774715459476678844418816862571810;
 
 template <class T>
 __device__ __forceinline__ T rsqrt_t(T x);
+// The hardware approximation (relative error below 2^-22) without the denormal handling of
+// rsqrtf: r^2 is never denormal here (coordinates are in leaf-box units), and r^2 = 0 gives
+// +inf, which the self-pair test replaces by 0.
 template <>
-__device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+__device__ __forceinline__ float rsqrt_t<float>(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 template <>
 __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
 
@@ -66,36 +73,45 @@ struct P2PStage {
 };
 
 template <class T, int R, int KR, bool HQ, bool HW, bool SELF>
+__device__ __forceinline__ void p2p_source(const P2PStage<T, R, HQ, HW> &sg, int s, const T *xi, const T *yi,
+                                           const T *zi, T (*part)[R]) {
+    using T4 = typename V4<T>::type;
+    const T4 a = sg.a[s];
+    T4 bb;
+    if (HW) bb = sg.b[s];
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+        const T dx = xi[k] - a.x, dy = yi[k] - a.y, dz = zi[k] - a.z;
+        const T r2 = dx * dx + dy * dy + dz * dz;
+        const T rinv = SELF ? (r2 > (T)0 ? rsqrt_t<T>(r2) : (T)0) : rsqrt_t<T>(r2);
+        if (HQ) {
+            part[k][0] += a.w * rinv;
+#pragma unroll
+            for (int r = 1; r < R; ++r) part[k][r] += sg.q[r - 1][s] * rinv;
+        }
+        if (HW) {
+            const T nd3 = (bb.x * dx + bb.y * dy + bb.z * dz) * (rinv * rinv * rinv);
+            part[k][0] += bb.w * nd3;
+#pragma unroll
+            for (int r = 1; r < R; ++r) part[k][r] += sg.w[r - 1][s] * nd3;
+        }
+    }
+}
+
+template <class T, int R, int KR, bool HQ, bool HW, bool SELF>
 __device__ __forceinline__ void p2p_tile(const P2PStage<T, R, HQ, HW> &sg, int ns, const T *xi, const T *yi,
                                          const T *zi, Comp<T> (*acc)[R]) {
-    using T4 = typename V4<T>::type;
     T part[KR][R];
 #pragma unroll
     for (int k = 0; k < KR; ++k)
 #pragma unroll
         for (int r = 0; r < R; ++r) part[k][r] = (T)0;
-#pragma unroll 4
-    for (int s = 0; s < ns; ++s) {
-        const T4 a = sg.a[s];
-        T4 bb;
-        if (HW) bb = sg.b[s];
-#pragma unroll
-        for (int k = 0; k < KR; ++k) {
-            const T dx = xi[k] - a.x, dy = yi[k] - a.y, dz = zi[k] - a.z;
-            const T r2 = dx * dx + dy * dy + dz * dz;
-            const T rinv = SELF ? (r2 > (T)0 ? rsqrt_t<T>(r2) : (T)0) : rsqrt_t<T>(r2);
-            if (HQ) {
-                part[k][0] += a.w * rinv;
-#pragma unroll
-                for (int r = 1; r < R; ++r) part[k][r] += sg.q[r - 1][s] * rinv;
-            }
-            if (HW) {
-                const T nd3 = (bb.x * dx + bb.y * dy + bb.z * dz) * (rinv * rinv * rinv);
-                part[k][0] += bb.w * nd3;
-#pragma unroll
-                for (int r = 1; r < R; ++r) part[k][r] += sg.w[r - 1][s] * nd3;
-            }
-        }
+    if (ns == 32) {  // full tile: fixed trip count
+#pragma unroll 8
+        for (int s = 0; s < 32; ++s) p2p_source<T, R, KR, HQ, HW, SELF>(sg, s, xi, yi, zi, part);
+    } else {
+#pragma unroll 2
+        for (int s = 0; s < ns; ++s) p2p_source<T, R, KR, HQ, HW, SELF>(sg, s, xi, yi, zi, part);
     }
 #pragma unroll
     for (int k = 0; k < KR; ++k)

@@ -493,6 +493,52 @@ void rhs(Context &c, StepState &s, const double *y, double t, double *f, bem_ste
 
 // One least-squares spherical-harmonic basis (degrees 0..pf-1) per distinct initial bubble
 // shape: bubbles whose unit directions from their centroid coincide share G and G+.
+void find_shapes(const Context &c, const std::vector<double> &hx, std::vector<BubbleShape> &shapes,
+                 std::vector<int32_t> &shape_of) {
+    const int64_t N = c.N, M = c.M;
+    shapes.clear();
+    shape_of.assign(M, 0);
+    auto dir = [&](int64_t j, double cx, double cy, double cz, double *d) {
+        d[0] = hx[j] - cx;
+        d[1] = hx[N + j] - cy;
+        d[2] = hx[2 * N + j] - cz;
+        double l = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        for (int k = 0; k < 3; ++k) d[k] /= l;
+    };
+    for (int64_t m = 0; m < M; ++m) {
+        int64_t a = c.vert_off[m], b = c.vert_off[m + 1];
+        int nd = (int)(b - a);
+        double cx = 0, cy = 0, cz = 0;
+        for (int64_t j = a; j < b; ++j) {
+            cx += hx[j];
+            cy += hx[N + j];
+            cz += hx[2 * N + j];
+        }
+        cx /= nd;
+        cy /= nd;
+        cz /= nd;
+        int found = -1;
+        for (size_t k = 0; k < shapes.size() && found < 0; ++k) {
+            const BubbleShape &sh = shapes[k];
+            if (sh.nd != nd) continue;
+            int64_t ra = c.vert_off[sh.rep];
+            bool same = true;
+            for (int i = 0; i < nd && same; ++i) {
+                double d1[3], d2[3];
+                dir(a + i, cx, cy, cz, d1);
+                dir(ra + i, sh.cx, sh.cy, sh.cz, d2);
+                for (int k2 = 0; k2 < 3; ++k2) same &= std::fabs(d1[k2] - d2[k2]) < 1e-9;
+            }
+            if (same) found = (int)k;
+        }
+        if (found < 0) {
+            shapes.push_back({m, nd, cx, cy, cz});
+            found = (int)shapes.size() - 1;
+        }
+        shape_of[m] = found;
+    }
+}
+
 void build_sh_basis(Context &c, int pf, ShBasis &B, int *bad, const double *xyz) {
     const int64_t N = c.N, M = c.M;
     cudaStream_t st = c.stream;
@@ -503,53 +549,11 @@ void build_sh_basis(Context &c, int pf, ShBasis &B, int *bad, const double *xyz)
         std::vector<double> hx(3 * N);
         BEM_CUDA(cudaMemcpyAsync(hx.data(), xyz, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, st));
         BEM_CUDA(cudaStreamSynchronize(st));
-        struct Shape {
-            int64_t rep;
-            int nd;
-            double cx, cy, cz;
-        };
-        std::vector<Shape> shapes;
-        std::vector<int32_t> shape_of(M);
-        auto dir = [&](int64_t j, double cx, double cy, double cz, double *d) {
-            d[0] = hx[j] - cx;
-            d[1] = hx[N + j] - cy;
-            d[2] = hx[2 * N + j] - cz;
-            double l = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-            for (int k = 0; k < 3; ++k) d[k] /= l;
-        };
-        for (int64_t m = 0; m < M; ++m) {
-            int64_t a = c.vert_off[m], b = c.vert_off[m + 1];
-            int nd = (int)(b - a);
-            double cx = 0, cy = 0, cz = 0;
-            for (int64_t j = a; j < b; ++j) {
-                cx += hx[j];
-                cy += hx[N + j];
-                cz += hx[2 * N + j];
-            }
-            cx /= nd;
-            cy /= nd;
-            cz /= nd;
-            int found = -1;
-            for (size_t k = 0; k < shapes.size() && found < 0; ++k) {
-                const Shape &sh = shapes[k];
-                if (sh.nd != nd) continue;
-                int64_t ra = c.vert_off[sh.rep];
-                bool same = true;
-                for (int i = 0; i < nd && same; ++i) {
-                    double d1[3], d2[3];
-                    dir(a + i, cx, cy, cz, d1);
-                    dir(ra + i, sh.cx, sh.cy, sh.cz, d2);
-                    for (int k2 = 0; k2 < 3; ++k2) same &= std::fabs(d1[k2] - d2[k2]) < 1e-9;
-                }
-                if (same) found = (int)k;
-            }
-            if (found < 0) {
-                if (nd < B.Pf) fail(BEM_ERR_MESH, "bubble with fewer vertices than filter coefficients");
-                shapes.push_back({m, nd, cx, cy, cz});
-                found = (int)shapes.size() - 1;
-            }
-            shape_of[m] = found;
-        }
+        std::vector<BubbleShape> shapes;
+        std::vector<int32_t> shape_of;
+        find_shapes(c, hx, shapes, shape_of);
+        for (const BubbleShape &sh : shapes)
+            if (sh.nd < B.Pf) fail(BEM_ERR_MESH, "bubble with fewer vertices than filter coefficients");
         std::vector<int64_t> goff(shapes.size() + 1, 0);
         for (size_t k = 0; k < shapes.size(); ++k) goff[k + 1] = goff[k] + (int64_t)shapes[k].nd * B.Pf;
         B.G.resize(goff.back());
@@ -560,7 +564,7 @@ void build_sh_basis(Context &c, int pf, ShBasis &B, int *bad, const double *xyz)
         scratch.resize((size_t)ndmax * B.Pf);
         A.resize((size_t)B.Pf * B.Pf);
         for (size_t k = 0; k < shapes.size(); ++k) {
-            const Shape &sh = shapes[k];
+            const BubbleShape &sh = shapes[k];
             k_filter_G<<<div_up(sh.nd, 128), 128, 0, st>>>(sh.nd, xyz, N, c.vert_off[sh.rep], sh.cx, sh.cy, sh.cz,
                                                            pf, B.G.p + goff[k], scratch.p);
             BEM_LAUNCH_CHECK();

@@ -651,11 +651,12 @@ void build_tree(Context &c) {
     BEM_CUDA(cudaMemcpyAsync(hc, lc.p, (t.deep + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     BEM_CUDA(cudaStreamSynchronize(st));
     int L = 2;
-    if (c.prm.fixed_level > 0) {
-        L = std::min(c.prm.fixed_level, t.deep);
+    const int forced = c.level_override > 0 ? c.level_override : c.prm.fixed_level;
+    if (forced > 0) {
+        L = std::min(forced, t.deep);
     } else {
         for (int l = 2; l <= t.deep; ++l)
-            if ((double)N / (double)(hc[l] + 1) >= (double)c.prm.leaf_target) L = l;
+            if ((double)N / (double)(hc[l] + 1) >= (double)std::max(c.prm.leaf_target, 1)) L = l;
     }
     t.L = L;
     t.nb.assign(L + 1, 0);
