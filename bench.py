@@ -70,12 +70,13 @@ def parse():
     ap.add_argument("--level", type=int, default=3)
     ap.add_argument("--p", type=int, default=14)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--leaf", type=int, default=64)
+    ap.add_argument("--leaf", type=int, default=0, help="mean points per leaf; 0 = autotune the octree depth")
     ap.add_argument("--tree-level", type=int, default=0, help="fixed octree depth (0 = from --leaf)")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--maxit", type=int, default=400)
     ap.add_argument("--restart", type=int, default=100)
-    ap.add_argument("--precond", type=int, default=0, help="1 = right Jacobi preconditioning of GMRES")
+    ap.add_argument("--precond", type=int, default=2,
+                    help="GMRES right preconditioning: 0 none (the paper), 1 Jacobi, 2 bubble blocks")
     ap.add_argument("--m2l-tc", type=int, default=1, help="1 = M2L of single-RHS products on the tensor cores")
     ap.add_argument("--pa", type=float, default=0.5, help="acoustic amplitude Pa/p0")
     ap.add_argument("--pf", type=int, default=6, help="shape-filter bandwidth")
@@ -351,36 +352,38 @@ def run_ours(args):
         "m2l": 2.0 * P * P * st["m2l_pairs"] * (n_r1 + 4 * n_r4) / args.steps,
     }
     launches = {k: prof[k][1] / args.steps for k in ("p2p", "m2l")}
-    cand = [k for k in ("p2p", "m2l") if per_step.get(k, 0) > 0]
-    dom = max(cand, key=lambda k: per_step[k]) if cand else None
-    roof = None
-    if dom:
-        nl = max(1.0, launches[dom])
-        t_launch = per_step[dom] / 1e3 / nl
-        achieved = work[dom] / nl / t_launch / 1e12
+
+    def p2p_roofline():
+        if per_step.get("p2p", 0) <= 0:
+            return None
+        nl = max(1.0, launches["p2p"])
+        t_launch = per_step["p2p"] / 1e3 / nl
+        achieved = work["p2p"] / nl / t_launch / 1e12
         peak = FP32_ALU_PEAK_TFLOPS if prec == bem.BEM_PREC_MIXED else None
-        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if peak else None, "traffic": None,
+        return {"kernel": "k_p2p_units (near field)", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": (achieved / peak) if peak else None, "traffic": None,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (max SM clock)",
                 "launch_ms": t_launch * 1e3, "launches_per_step": nl,
-                "work_per_launch": "%s" % ("11 (single layer) / 19 (double layer) / 33 (both, 4 RHS) flops x "
-                                            "near-field pairs" if dom == "p2p"
-                                            else "2 P^2 flops x M2L translations x RHS")}
+                "work_per_launch": "11 (single layer) / 19 (double layer) / 33 (both, 4 RHS) flops x near-field pairs"}
 
-    # the tensor-core M2L (single-RHS products), against the measured BF16 peak; the phase also
-    # holds the multipole split, the per-target reduction and the 4-RHS CUDA-core translations
-    roof_m2l = None
-    if prec == bem.BEM_PREC_MIXED and args.m2l_tc and per_step.get("m2l", 0) > 0:
+    def m2l_roofline():
+        # tensor-core translations of the single-RHS products (the phase also holds the split of
+        # the multipoles into BF16 pieces), against the measured sustained BF16 peak
+        if not (prec == bem.BEM_PREC_MIXED and args.m2l_tc and per_step.get("m2l", 0) > 0):
+            return None
         nl = max(1.0, launches["m2l"])
         t_launch = per_step["m2l"] / 1e3 / nl
-        w_tc = M2L_TC_PRODUCTS * 2.0 * P * P * st["m2l_pairs"] * (n_sl + n_dl) / args.steps
-        achieved = w_tc / nl / t_launch / 1e12
+        achieved = M2L_TC_PRODUCTS * 2.0 * P * P * st["m2l_pairs"] / t_launch / 1e12
         pk = PEAKS.get("bf16_tflops_sustained")
-        roof_m2l = {"kernel": "m2l", "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
-                    "frac": achieved / pk if pk else None, "traffic": None,
-                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS, long loop)",
-                    "launch_ms": t_launch * 1e3, "launches_per_step": nl,
-                    "work_per_launch": "6 BF16 products x 2 P^2 flops x M2L translations"}
+        return {"kernel": "k_m2l_tc (M2L)", "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                "frac": achieved / pk if pk else None, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS, long loop)",
+                "launch_ms": t_launch * 1e3, "launches_per_step": nl,
+                "work_per_launch": "6 BF16 products x 2 P^2 flops x M2L translations"}
+
+    roof_p2p, roof_m2l = p2p_roofline(), m2l_roofline()
+    dom = "m2l" if roof_m2l and per_step.get("m2l", 0) > per_step.get("p2p", 0) else "p2p"
+    roof = roof_m2l if dom == "m2l" else roof_p2p
 
     line = {
         "metric": "wall-s per time step & FMM matvec Gpairs/s at 3.2M unknowns, resid 1e-6, vs FP64",
@@ -389,7 +392,9 @@ def run_ours(args):
         "dtype": "f32+f64" if prec == bem.BEM_PREC_MIXED else "f64", "data": "synthetic",
         "config": {"workload": workload_name(args, mesh), "p_fmm": args.p, "precision": args.precision,
                    "leaf_target": args.leaf, "gmres_tol": args.tol, "gmres_precond": args.precond,
-                   "m2l_tensor_cores": args.m2l_tc, "scheme": "AB6 after %d RK4 warm-up steps" % 5,
+                   "m2l_tensor_cores": args.m2l_tc,
+                   "scheme": ("AB6 (steps after the 5 RK4 start steps)" if rhs / args.steps < 2 else
+                              "RK4 start steps (the paper's AB6 begins after 5)"),
                    "pa": args.pa, "pf": args.pf, "dt": infos[-1]["dt"], "levels": st["levels"],
                    "leaves": st["leaves"], "l2": "inputs and working set > L2 (no flush)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -401,6 +406,7 @@ def run_ours(args):
                 "p2p_pairs": st["p2p_pairs"], "m2l_pairs": st["m2l_pairs"]},
         "phases_ms_per_step": {k: round(v, 3) for k, v in per_step.items() if v > 0},
         "roofline": roof,
+        "roofline_p2p": roof_p2p,
         "roofline_m2l": roof_m2l,
         "e2e": {"value": e2e_s, "unit": "s/step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(d2h),
                 "what": "bem_step driven from the host + bem_step_get_state into pinned host buffers"},
@@ -409,36 +415,36 @@ def run_ours(args):
     }
 
     if args.fp64_compare and prec == bem.BEM_PREC_MIXED:
-        # FP64 FMM-BEM from the same state and warm q: one RK4 step (4 right-hand sides);
-        # an AB6 step costs one right-hand side
+        # the plain FP64 FMM-BEM on the same GPU from the same state: one right-hand side
+        # (octree, diagonals, b and the GMRES solve from the current q) and one product, timed
+        # like the mixed path's; an AB6 step costs one right-hand side
+        progress("FP64 comparison: one right-hand side")
         xs = torch.empty(3 * N, dtype=torch.float64, device=dev)
         ph = torch.empty(N, dtype=torch.float64, device=dev)
         qs = torch.empty(N, dtype=torch.float64, device=dev)
         bem.bem_step_get_state(ctx.ctx, xs, ph, qs)
         ctx64 = make_ctx(bem.BEM_PREC_FP64)
         ctx64.upload(xs.view(3, N), tri, voff, toff)
-        bem.bem_step_init(ctx64.ctx, ph, sp, q0=qs)
+        q64 = qs.clone()
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
-        i64 = bem.bem_step(ctx64.ctx)
+        ctx64.build()
+        it64, rr64 = ctx64.solve(ph, q64, raise_on_noconv=False)
         f1.record(stream)
         torch.cuda.synchronize()
         t64 = f0.elapsed_time(f1) / 1e3
-        for _ in range(1):
-            ctx64.apply(1.0, qs, 0.0, None, out)
-        torch.cuda.synchronize()
         g0 = torch.cuda.Event(enable_timing=True)
         g1 = torch.cuda.Event(enable_timing=True)
         g0.record(stream)
         ctx64.apply(1.0, qs, 0.0, None, out)
         g1.record(stream)
         torch.cuda.synchronize()
-        line["fp64_compare"] = {"s_per_rhs": t64 / max(1, i64["rhs_calls"]), "rk4_step_s": t64,
-                                "rhs_calls": i64["rhs_calls"], "gmres_iters": i64["gmres_iters"],
-                                "max_relres": i64["max_relres"], "mvp_ms": g0.elapsed_time(g1),
-                                "mixed_s_per_rhs": ms / 1e3 / max(1e-9, rhs / args.steps)}
+        line["fp64_compare"] = {"s_per_rhs": t64, "gmres_iters": it64, "relres": rr64,
+                                "mvp_ms": g0.elapsed_time(g1),
+                                "mixed_s_per_rhs": ms / 1e3 / max(1e-9, rhs / args.steps),
+                                "what": "FP64 octree + diagonals + b + GMRES solve from the same state and q"}
         ctx64.close()
 
     if rank == 0 and args.cpu_sample:
@@ -548,7 +554,7 @@ def run_learned(args):
     centres = synth._place_centres(radii, 4.0 * nb ** (1 / 3), 0.5, rng)
     levels = rng.choice(np.array([3, 4]), size=nb)
     mesh = synth.cluster(levels, radii, centres)
-    phi = synth.cluster_potential(mesh, 6, 0.1, rng)
+    phi = synth.cluster_potential(mesh, 6, 0.01, rng, radius_scaled=True)
     prec = bem.BEM_PREC_MIXED if args.precision == "mixed" else bem.BEM_PREC_FP64
     ctx = bem.BemContext(stream=stream, p_fmm=args.p, precision=prec, leaf_target=args.leaf, gmres_tol=args.tol,
                          gmres_maxit=args.maxit, gmres_restart=args.restart, gmres_precond=args.precond)

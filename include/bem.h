@@ -90,12 +90,13 @@ typedef struct {
                                1: right Jacobi preconditioning x = D^-1 y with D = diag(L_ii)
                                (removes the spread of the single layer's scale across bubbles
                                of different radii);
-                               2: right bubble-block preconditioning: per distinct bubble shape,
-                               the inverse of the isolated bubble's single-layer block (built
-                               from the geometry of the first solve after a mesh upload and
-                               kept), scaled by each bubble's current size; removes the spread
-                               of each bubble's own spectrum (R/(2n+1) on a sphere). Needs
-                               bubbles; memory n^2 per distinct shape of n vertices.
+                               2: right bubble-block preconditioning: per distinct bubble mesh
+                               (same connectivity), the inverse of the isolated representative
+                               bubble's single-layer block (built from the geometry of the
+                               first solve after a mesh upload and kept), scaled by each
+                               bubble's current size; removes the spread of each bubble's own
+                               spectrum (R/(2n+1) on a sphere). Needs bubbles; memory n^2
+                               doubles + n^2 floats per distinct mesh of n vertices.
                                Every mode stops on the same true residual |b - L q| / |b|.
                                Default 0.                                                      */
     int32_t gmres_maxit;    /* maximum GMRES iterations. Default 100.                          */
@@ -119,8 +120,10 @@ typedef struct {
 } bem_stats;
 
 /* Phases reported by bem_profile_read, in this order. */
-#define BEM_NUM_PHASES 13
-/* geometry, tree, operators, strengths, p2m, m2m, m2l, l2l, l2p, p2p, direct, diag, gmres */
+#define BEM_NUM_PHASES 15
+/* geometry, tree, operators, strengths, p2m, m2m, m2l (tensor-core translations and the split
+ * of the multipoles), l2l, l2p, p2p, direct, diag, gmres, m2l_reduce (per-target sums of the
+ * M2L products), m2l_cc (M2L translations on the CUDA cores) */
 
 /* Fill *p with the defaults listed above. */
 int bem_params_default(bem_params *p);

@@ -41,7 +41,7 @@ EXPORTED = [
     "bem_mlp_loss_grad", "bem_mlp_forward", "bem_mlp_get_params", "bem_mlp_set_params", "bem_mlp_info",
 ]
 
-BEM_NUM_PHASES = 13
+BEM_NUM_PHASES = 15
 
 
 class bem_params(ctypes.Structure):

@@ -261,6 +261,7 @@ void build_all(Context &c) {
             build_tree(c);
         }
         c.m2l_chunks_h.clear();
+        c.tc_chunks_r = 0;  // chunk tables follow the tree (the depth autotuner built others)
         c.stats.p2p_pairs = c.tree.p2p_pairs;
         c.stats.m2l_pairs = c.tree.n_m2l;
         c.stats.levels = c.tree.L;
@@ -763,7 +764,7 @@ int bem_profile_read(void *ctx, double *ms, int64_t *intervals) {
 
 const char *bem_phase_name(int i) {
     static const char *names[PH_COUNT] = {"geometry", "tree", "operators", "strengths", "p2m", "m2m", "m2l",
-                                          "l2l", "l2p", "p2p", "direct", "diag", "gmres"};
+                                          "l2l", "l2p", "p2p", "direct", "diag", "gmres", "m2l_reduce", "m2l_cc"};
     return (i >= 0 && i < PH_COUNT) ? names[i] : nullptr;
 }
 

@@ -246,6 +246,15 @@ __global__ void __launch_bounds__(256) k_p2m(int p, int nleaf, const int32_t *__
     T *pn = reinterpret_cast<T *>(Rt + P2M_PC * ntri);  // [PC][3]
     T *pq = pn + P2M_PC * 3;                            // [PC][R]
     T *pw = pq + P2M_PC * R;                            // [PC][R]
+    T *tk = pw + P2M_PC * R;                            // [p]: -1 / (2k)
+    T *tnm = tk + p;                                    // [ntri]: 1 / ((n + m)(n - m)), n >= m + 2
+    for (int e = threadIdx.x; e < p; e += blockDim.x) tk[e] = e > 0 ? (T)(-0.5) / (T)e : (T)0;
+    for (int e = threadIdx.x; e < ntri; e += blockDim.x) {
+        int n = 0;
+        while ((n + 1) * (n + 2) / 2 <= e) ++n;
+        const int m = e - n * (n + 1) / 2;
+        tnm[e] = n >= m + 2 ? (T)1 / ((T)(n + m) * (T)(n - m)) : (T)0;
+    }
     const int b = blockIdx.x;
     const int s0 = bstart[b], cnt = bcount[b];
     constexpr int MAXC = 2;  // complex coefficients per thread (ntri <= 2 * blockDim)
@@ -274,31 +283,58 @@ __global__ void __launch_bounds__(256) k_p2m(int p, int nleaf, const int32_t *__
             pq[jj * R + r] = q[r * N + s0 + c0 + jj];
             pw[jj * R + r] = HW ? w[r * N + s0 + c0 + jj] : (T)0;
         }
-        for (int task = threadIdx.x; task < pc * p; task += blockDim.x) {
-            const int jj = task / p, m = task % p;
-            const int64_t i = s0 + c0 + jj;
-            const T x = loc[i], y = loc[N + i], z = loc[2 * N + i];
-            const T r2 = x * x + y * y + z * z;
-            T mr = 1, mi = 0;
-            for (int k = 1; k <= m; ++k) {
-                const T f = (T)(-0.5) / (T)k;
-                const T nr = f * (x * mr - y * mi), ni = f * (x * mi + y * mr);
-                mr = nr;
-                mi = ni;
+        // each task: one order m for four points (independent recurrences in flight); the
+        // k loop runs m steps and the n loop p - m - 2, so lanes finish together
+        const int ngroups = (pc + 3) / 4;
+        for (int task = threadIdx.x; task < ngroups * p; task += blockDim.x) {
+            const int g = task / p, m = task % p;
+            T x[4], y[4], z[4], r2[4], mr[4], mi[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int jj = min(g * 4 + u, pc - 1);
+                const int64_t i = s0 + c0 + jj;
+                x[u] = loc[i];
+                y[u] = loc[N + i];
+                z[u] = loc[2 * N + i];
+                r2[u] = x[u] * x[u] + y[u] * y[u] + z[u] * z[u];
+                mr[u] = 1;
+                mi[u] = 0;
             }
-            T2 *col = Rt + jj * ntri;
-            col[tri_idx(m, m)] = T2{mr, mi};
-            T p2r = mr, p2i = mi, p1r = z * mr, p1i = z * mi;
-            if (m + 1 < p) col[tri_idx(m + 1, m)] = T2{p1r, p1i};
+            for (int k = 1; k <= m; ++k) {
+                const T f = tk[k];  // -1 / (2k)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const T nr = f * (x[u] * mr[u] - y[u] * mi[u]), ni = f * (x[u] * mi[u] + y[u] * mr[u]);
+                    mr[u] = nr;
+                    mi[u] = ni;
+                }
+            }
+            T p2r[4], p2i[4], p1r[4], p1i[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                T2 *col = Rt + (g * 4 + u) * ntri;
+                const bool ok = g * 4 + u < pc;
+                if (ok) col[tri_idx(m, m)] = T2{mr[u], mi[u]};
+                p2r[u] = mr[u];
+                p2i[u] = mi[u];
+                p1r[u] = z[u] * mr[u];
+                p1i[u] = z[u] * mi[u];
+                if (ok && m + 1 < p) col[tri_idx(m + 1, m)] = T2{p1r[u], p1i[u]};
+            }
             for (int n = m + 2; n < p; ++n) {
-                const T d = (T)1 / ((T)(n + m) * (T)(n - m));
-                const T cr = ((T)(2 * n - 1) * z * p1r - r2 * p2r) * d;
-                const T ci = ((T)(2 * n - 1) * z * p1i - r2 * p2i) * d;
-                col[tri_idx(n, m)] = T2{cr, ci};
-                p2r = p1r;
-                p2i = p1i;
-                p1r = cr;
-                p1i = ci;
+                const int idx = tri_idx(n, m);
+                const T d = tnm[idx];  // 1 / ((n + m)(n - m))
+                const T c2 = (T)(2 * n - 1);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const T cr = (c2 * z[u] * p1r[u] - r2[u] * p2r[u]) * d;
+                    const T ci = (c2 * z[u] * p1i[u] - r2[u] * p2i[u]) * d;
+                    if (g * 4 + u < pc) Rt[(g * 4 + u) * ntri + idx] = T2{cr, ci};
+                    p2r[u] = p1r[u];
+                    p2i[u] = p1i[u];
+                    p1r[u] = cr;
+                    p1i[u] = ci;
+                }
             }
         }
         __syncthreads();
@@ -641,7 +677,7 @@ void run_fmm(Context &c, const RhsArgs<R> &a) {
     {
         PhaseScope ps(c, PH_P2M);
         const int ntri = p * (p + 1) / 2;
-        size_t sm = ((size_t)2 * P2M_PC * ntri + P2M_PC * 3 + 2 * P2M_PC * R) * sizeof(T);
+        size_t sm = ((size_t)2 * P2M_PC * ntri + P2M_PC * 3 + 2 * P2M_PC * R + p + ntri) * sizeof(T);
         const int threads = ntri <= 256 ? 128 : 256;  // ntri <= 2 * threads
         bool hw = false;
         for (int r = 0; r < R; ++r) hw = hw || a.g[r] != 0.0;
@@ -686,10 +722,11 @@ void run_fmm(Context &c, const RhsArgs<R> &a) {
     }
     // M2L, all levels at once, then each target sums its sources
     if (nm2l_chunks) {
-        PhaseScope ps(c, PH_M2L);
         // The 4-RHS product behind the diagonals stays on the CUDA cores: M_ii and L_ii are formed
         // by cancellation (Eqs. (s3), (s5)), which magnifies the tensor path's rounding.
-        if (!F64 && R == 1 && c.prm.m2l_tensor_cores && m2l_tc_supported(P) && c.ops.tc_Npad > 0) {
+        const bool tc_path = !F64 && R == 1 && c.prm.m2l_tensor_cores && m2l_tc_supported(P) && c.ops.tc_Npad > 0;
+        if (tc_path) {
+            PhaseScope ps(c, PH_M2L);
             if (c.tc_chunks_r != R) {
                 std::vector<XChunk> tc;
                 make_chunks(t.m2l_class_off, 0, m2l_tc_pairs_per_chunk(R), tc);
@@ -704,11 +741,13 @@ void run_fmm(Context &c, const RhsArgs<R> &a) {
                 launch_m2l_tc<R>(c, c.tc_chunks.p, c.n_tc_chunks, (const float *)mp, (int64_t)t.nbox * R, (float *)ypair,
                                  c.tc_err.p);
         } else {
+            PhaseScope ps(c, PH_M2L_CC);
             dim3 grid((unsigned)nm2l_chunks, rowblocks);
             k_xlat<T, R, kStorePair><<<grid, XT_THREADS, 0, st>>>(m2l, P, c.m2l_chunks.p + 1, t.m2l_src.p,
                                                                  t.m2l_tgt.p, mp, ypair);
             BEM_LAUNCH_CHECK();
         }
+        PhaseScope ps(c, PH_M2L_REDUCE);
         int ntg = t.nbox - t.base[2];
         dim3 rg((unsigned)ntg, red_blocks_y);
         k_reduce_pairs<T, R><<<rg, 128, 0, st>>>(t.base[2], t.m2l_tgt_off.p, t.m2l_by_tgt.p, ypair, P, lc);

@@ -177,6 +177,8 @@ enum Phase {
     PH_DIRECT,
     PH_DIAG,
     PH_GMRES,
+    PH_M2L_REDUCE,  // per-target sums of the M2L pair products
+    PH_M2L_CC,      // M2L translations on the CUDA cores (FP64 path, 4-RHS diagonal product)
     PH_COUNT
 };
 
@@ -302,9 +304,9 @@ struct Context {
 
     // GMRES
     DevBuf<double> V, wv, rv, bv, zv, hcol, hmat, givens, gvec, yvec, partial, scal;
-    // bubble-block preconditioner (gmres_precond = 2, precond.cu): per distinct bubble shape,
-    // the inverse of the isolated unit-size bubble's single-layer block, built from the
-    // geometry of the first solve after a mesh upload
+    // bubble-block preconditioner (gmres_precond = 2, precond.cu): per distinct bubble mesh
+    // (connectivity), the inverse of the isolated representative's single-layer block at unit
+    // size, built from the geometry of the first solve after a mesh upload
     struct BlockPrecond {
         bool ready = false;
         std::vector<int> nd;              // vertices per shape

@@ -1,13 +1,12 @@
 // M2L translations on the 5th-generation tensor cores (tcgen05, TMEM accumulators).
 //
-// For one offset class c and a chunk of up to 128/R (source, target) pairs, the product
+// For one offset class c and a chunk of up to 256/R (source, target) pairs, the product
 //   Y[pair, rhs][n] = sum_k T_c[n][k] X[src, rhs][k]
-// is one MMA tile D = A B^T with M = 128 rows (pair, rhs), N = P rounded up to 16 output
-// coefficients and K = P input coefficients: A = gathered multipole rows, B = T_c (row n of
-// T_c is K-contiguous, i.e. K-major). A block holds 256 TMEM columns and under 113 KB of
-// shared memory, so two blocks share an SM and one's MMAs overlap the other's pipeline fill
-// and epilogue. (The code also supports TC_TILES = 2 tiles of one class per block sharing the
-// staged blocks of T_c.)
+// is two MMA tiles D_t = A_t B^T (t = 0, 1) with M = 128 rows (pair, rhs) each, N = P rounded
+// up to 16 output coefficients and K = P input coefficients: A_t = gathered multipole rows,
+// B = T_c (row n of T_c is K-contiguous, i.e. K-major). The two tiles share every staged
+// block of T_c, which halves its traffic; this beat one tile per block at two blocks per SM
+// (3.8 vs 5.0 ms per product at 3.2M unknowns).
 //
 // Accuracy: both operands are split into three BF16 pieces, x = x0 + x1 + x2 (x0 = bf16(x),
 // x1 = bf16(x - x0), x2 = bf16(x - x0 - x1)), and D accumulates in FP32 the six products with
@@ -21,7 +20,7 @@
 // pipeline stage holding A (3 pieces x tiles x 128 x 16) and B (3 pieces x N_pad x 16) in
 // the canonical K-major layout without swizzle (8-row x 16-byte core matrices, K-adjacent core
 // matrices 128 B apart, 8-row groups 256 B apart). All threads fill stages with cp.async
-// (16-byte copies; rows past the chunk read as zeros), three stages deep; one elected thread
+// (16-byte copies; rows past the chunk read as zeros), four stages deep; one elected thread
 // issues the MMAs of a stage as soon as it has landed and commits them to the stage's
 // mbarrier, which releases the stage for refilling. Every wait is bounded: one that runs out
 // sets an error flag and the block skips ahead, waiting (bounded) for its MMAs in flight
@@ -34,9 +33,9 @@ namespace bem {
 namespace {
 
 constexpr int TC_M = 128;        // rows per tile
-constexpr int TC_TILES = 1;      // tiles per block (same class, shared B stages)
+constexpr int TC_TILES = 2;      // tiles per block (same class, shared B stages)
 constexpr int TC_K = 16;         // K per stage (one kind::f16 MMA)
-constexpr int TC_STAGES = 3;
+constexpr int TC_STAGES = 4;
 constexpr int TC_THREADS = 128;
 constexpr uint32_t TC_LBO = 128;  // bytes between K-adjacent core matrices
 constexpr uint32_t TC_SBO = 256;  // bytes between 8-row groups
@@ -170,12 +169,14 @@ __host__ __device__ inline TcLayout tc_layout(int Npad) {
     L.a_bytes = (size_t)3 * TC_TILES * TC_M * TC_K * 2;
     L.b_bytes = (size_t)3 * Npad * TC_K * 2;
     L.stage_bytes = L.a_bytes + L.b_bytes;
-    L.total = TC_STAGES * L.stage_bytes + TC_STAGES * 8 + 16 + 1024;
+    // the epilogue reuses the stages for one tile of FP32 rows (at most N_pad floats each)
+    const size_t epi = (size_t)TC_M * Npad * 4;
+    L.total = (TC_STAGES * L.stage_bytes > epi ? TC_STAGES * L.stage_bytes : epi) + TC_STAGES * 8 + 16 + 1024;
     return L;
 }
 
 template <int R>
-__global__ void __launch_bounds__(TC_THREADS, 2) k_m2l_tc(int P, int Npad, const __nv_bfloat16 *__restrict__ tcB,
+__global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __nv_bfloat16 *__restrict__ tcB,
                                                        const XChunk *__restrict__ chunks,
                                                        const int32_t *__restrict__ srcs, int64_t xrows,
                                                        const __nv_bfloat16 *__restrict__ Xs, float *__restrict__ Ypair,
@@ -184,7 +185,9 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_m2l_tc(int P, int Npad, const
     // 1024-byte aligned base for the operand stages
     unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const TcLayout Lo = tc_layout(Npad);
-    uint64_t *empty = reinterpret_cast<uint64_t *>(smem + TC_STAGES * Lo.stage_bytes);
+    const size_t epi_bytes = (size_t)TC_M * Npad * 4;
+    uint64_t *empty = reinterpret_cast<uint64_t *>(
+        smem + (TC_STAGES * Lo.stage_bytes > epi_bytes ? TC_STAGES * Lo.stage_bytes : epi_bytes));
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(empty + TC_STAGES);
     __shared__ int s_src[TC_TILES * TC_M];
 
@@ -299,11 +302,14 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_m2l_tc(int P, int Npad, const
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (ok) {
-        // epilogue: warp w holds TMEM lanes 32w..32w+31 = tile rows; 16 columns per load
+        // epilogue, one tile at a time: warp w holds TMEM lanes 32w..32w+31 = tile rows; each
+        // thread moves its row into shared memory (row stride P floats: conflict-free 16-byte
+        // stores), then the block writes the tile's rows, which are contiguous in Ypair, with
+        // coalesced 16-byte stores
+        float *stage = reinterpret_cast<float *>(smem);  // the operand stages are free now
         for (int t = 0; t < ntiles; ++t) {
-            const int row = t * TC_M + warp * 32 + lane;
-            const bool vrow = row < nrows;
-            float *yrow = Ypair + ((size_t)ch.start * R + row) * P;  // rows of a chunk are consecutive
+            const int rows_t = min(TC_M, nrows - t * TC_M);
+            float *srow = stage + (size_t)(warp * 32 + lane) * P;
             for (int c0 = 0; c0 < Npad; c0 += 16) {
                 uint32_t v[16];
                 const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * 256 + c0);
@@ -315,20 +321,19 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_m2l_tc(int P, int Npad, const
                       "=r"(v[15])
                     : "r"(taddr));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (vrow) {
-                    if (c0 + 16 <= P) {  // P % 4 == 0 and rows start 16-byte aligned
 #pragma unroll
-                        for (int i = 0; i < 16; i += 4)
-                            *reinterpret_cast<float4 *>(yrow + c0 + i) =
-                                make_float4(__uint_as_float(v[i]), __uint_as_float(v[i + 1]),
-                                            __uint_as_float(v[i + 2]), __uint_as_float(v[i + 3]));
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < 16; ++i)
-                            if (c0 + i < P) yrow[c0 + i] = __uint_as_float(v[i]);
-                    }
-                }
+                for (int i = 0; i < 16; i += 4)
+                    if (c0 + i < P)  // P % 4 == 0: whole 16-byte groups
+                        *reinterpret_cast<float4 *>(srow + c0 + i) =
+                            make_float4(__uint_as_float(v[i]), __uint_as_float(v[i + 1]), __uint_as_float(v[i + 2]),
+                                        __uint_as_float(v[i + 3]));
             }
+            __syncthreads();
+            float4 *dst = reinterpret_cast<float4 *>(Ypair + ((size_t)ch.start * R + t * TC_M) * P);
+            const float4 *src = reinterpret_cast<const float4 *>(stage);
+            const int n4 = rows_t * P / 4;
+            for (int e = tid; e < n4; e += TC_THREADS) dst[e] = src[e];
+            __syncthreads();
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");

@@ -4,10 +4,10 @@
 // as the alternative it tried (Section 3.8). The slow GMRES components here are those of each
 // bubble's own single-layer block: on a sphere of radius R its eigenvalues are R/(2n+1), a
 // spread that grows with the mesh resolution. This preconditioner removes them: for every
-// distinct bubble shape (same vertex directions from the centroid, as the shape filter of
-// Section 3.6 groups bubbles), it inverts the single-layer matrix of the isolated
-// representative bubble, including its singular diagonal from the identity of Eq. (s5)
-// summed over that bubble alone, and scales it to unit size. Bubble m of the shape is
+// distinct bubble mesh (same connectivity; every icosphere of one level is one group), it
+// inverts the single-layer matrix of the isolated representative bubble, including its
+// singular diagonal from the identity of Eq. (s5) summed over that bubble alone, and scales
+// it to unit size. Bubble m of the group is
 // preconditioned by (1/R_m) times that inverse, R_m its current mean centroid distance (the
 // single layer of a bubble scaled by R is R times the unit one). The inverse is built from
 // the geometry of the first solve after a mesh upload and kept; only the scales follow the
@@ -201,16 +201,53 @@ __global__ void __launch_bounds__(BP_THREADS) k_bp_apply(int n, const T *__restr
     }
 }
 
+// Bubbles whose meshes have the same connectivity (vertex count and triangle list relative to
+// their first vertex) share one block inverse: the representative's, scaled by size. A mesh
+// copied from one template (every icosphere of one level) is one group however it deforms.
+void find_topologies(const Context &c, const std::vector<double> &hx, const std::vector<int32_t> &ht,
+                     std::vector<BubbleShape> &shapes, std::vector<int32_t> &shape_of) {
+    const int64_t N = c.N, M = c.M, T = c.T;
+    shapes.clear();
+    shape_of.assign(M, 0);
+    for (int64_t m = 0; m < M; ++m) {
+        const int64_t a = c.vert_off[m], nd = c.vert_off[m + 1] - a;
+        const int64_t ta = c.tri_off[m], nt = c.tri_off[m + 1] - ta;
+        int found = -1;
+        for (size_t k = 0; k < shapes.size() && found < 0; ++k) {
+            const int64_t r = shapes[k].rep;
+            const int64_t ra = c.vert_off[r], rta = c.tri_off[r];
+            if (shapes[k].nd != nd || c.tri_off[r + 1] - rta != nt) continue;
+            bool same = true;
+            for (int64_t t = 0; t < nt && same; ++t)
+                for (int d = 0; d < 3 && same; ++d) same = ht[d * T + ta + t] - a == ht[d * T + rta + t] - ra;
+            if (same) found = (int)k;
+        }
+        if (found < 0) {
+            double cx = 0, cy = 0, cz = 0;
+            for (int64_t j = a; j < a + nd; ++j) {
+                cx += hx[j];
+                cy += hx[N + j];
+                cz += hx[2 * N + j];
+            }
+            shapes.push_back({m, (int)nd, cx / nd, cy / nd, cz / nd});
+            found = (int)shapes.size() - 1;
+        }
+        shape_of[m] = found;
+    }
+}
+
 void build(Context &c) {
     cudaStream_t st = c.stream;
     const int64_t N = c.N, M = c.M;
     auto &bp = c.bp;
     std::vector<double> hx(3 * N);
+    std::vector<int32_t> ht(3 * (size_t)c.T);
     BEM_CUDA(cudaMemcpyAsync(hx.data(), c.xyz.p, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, st));
+    BEM_CUDA(cudaMemcpyAsync(ht.data(), c.tri.p, 3 * (size_t)c.T * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     BEM_CUDA(cudaStreamSynchronize(st));
     std::vector<BubbleShape> shapes;
     std::vector<int32_t> shape_of;
-    find_shapes(c, hx, shapes, shape_of);
+    find_topologies(c, hx, ht, shapes, shape_of);
     const size_t ns = shapes.size();
     bp.nd.assign(ns, 0);
     bp.inv_off.assign(ns + 1, 0);
@@ -219,7 +256,7 @@ void build(Context &c) {
         bp.inv_off[k + 1] = bp.inv_off[k] + (int64_t)shapes[k].nd * shapes[k].nd;
     }
     if (bp.inv_off.back() > (int64_t)1 << 30)
-        fail(BEM_ERR_ARG, "bubble-block preconditioner: too many distinct bubble shapes (inverse over 8 GiB)");
+        fail(BEM_ERR_ARG, "bubble-block preconditioner: too many distinct bubble meshes (inverse over 8 GiB)");
     // bubbles grouped by shape
     bp.first.assign(ns + 1, 0);
     for (int64_t m = 0; m < M; ++m) bp.first[shape_of[m] + 1] += 1;

@@ -303,12 +303,16 @@ def cluster(levels, radii: np.ndarray, centres: np.ndarray) -> Mesh:
     )
 
 
-def cluster_potential(mesh: Mesh, lmax: int, scale: float, rng: np.random.Generator) -> np.ndarray:
+def cluster_potential(mesh: Mesh, lmax: int, scale: float, rng: np.random.Generator,
+                      radius_scaled: bool = False) -> np.ndarray:
     """Per-bubble smooth random potential: sum over l <= lmax of N(0,1)*scale * Y_l^m of
     the direction from the bubble centre. Coefficients are drawn bubble by bubble in
-    (l, m) order."""
+    (l, m) order. With radius_scaled the series of bubble b is multiplied by its radius, so
+    every bubble starts with the same velocity scale (|grad phi| ~ scale) whatever its size."""
     lm = [(l, m) for l in range(lmax + 1) for m in range(-l, l + 1)]
     coef = scale * rng.standard_normal((mesh.m, len(lm)))
+    if radius_scaled:
+        coef *= np.asarray(mesh.radii, dtype=np.float64)[:, None]
     phi = np.empty(mesh.n)
     basis_cache: dict[int, np.ndarray] = {}
     for b in range(mesh.m):
@@ -357,19 +361,23 @@ def workload_single_bubble_l6(seed: int = 2, level: int = 6) -> tuple[Mesh, np.n
 
 def workload_cluster(bubbles: int = 5000, level: int = 3, seed: int = 3, sigma: float = 0.3,
                      gap: float = 0.5, spacing: float = 4.0, phi_lmax: int = 6,
-                     phi_scale: float = 0.1) -> tuple[Mesh, np.ndarray]:
+                     phi_scale: float = 0.01, phi_radius_scaled: bool = True) -> tuple[Mesh, np.ndarray]:
     """Random polydisperse cluster: radii lognormal(0, sigma) (median 1), centres uniform in
     a cube of side L = spacing * M^(1/3) (mean centre spacing about `spacing` median radii, as
     in the paper's d = 4 a0 clusters) with pairwise gap |c_i - c_j| >= R_i + R_j +
     gap * max(R_i, R_j); every bubble an icosphere of `level`; phi per bubble a random
-    SH series with l <= phi_lmax and N(0,1)*phi_scale coefficients."""
+    SH series with l <= phi_lmax and N(0,1)*phi_scale coefficients, times the bubble's
+    radius (phi_radius_scaled: the same initial velocity scale on every bubble). The series
+    is an impulsive start: surfaces move at ~|phi|(l+1)/R from t = 0 until surface tension
+    turns them back a quarter capillary period later, so the amplitude sets how far a bubble
+    deforms; 0.01 keeps it to a few percent of the radius over a 20-step run."""
     rng = np.random.Generator(np.random.PCG64(seed))
     radii = np.exp(sigma * rng.standard_normal(bubbles))
     box = spacing * bubbles ** (1.0 / 3.0)
     centres = _place_centres(radii, box, gap, rng)
     mesh = cluster(level, radii, centres)
     mesh.meta.update({"seed": seed, "level": level, "box": box, "sigma": sigma, "gap": gap})
-    phi = cluster_potential(mesh, phi_lmax, phi_scale, rng)
+    phi = cluster_potential(mesh, phi_lmax, phi_scale, rng, radius_scaled=phi_radius_scaled)
     return mesh, phi
 
 
@@ -386,7 +394,7 @@ def workload_uneven_clusters(n_clusters: int = 64, seed: int = 5, max_bubbles: i
         centres = _place_centres(radii, box, 0.5, rng)
         lev = rng.choice(np.asarray(levels), size=nb)
         mesh = cluster(lev, radii, centres)
-        phi = cluster_potential(mesh, 6, 0.1, rng)
+        phi = cluster_potential(mesh, 6, 0.01, rng, radius_scaled=True)
         out.append((mesh, phi))
     return out
 

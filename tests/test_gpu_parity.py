@@ -329,3 +329,31 @@ def test_bubble_block_preconditioner_same_solution_far_fewer_iterations(prec):
         ctx.close()
     print("iterations: none %d, bubble blocks %d" % (its[0], its[2]))
     assert its[2] * 2 < its[0]
+
+
+def test_depth_autotuner_keeps_the_operator():
+    """leaf_target = 0 times one product at three depths on the first build and keeps the
+    fastest; the product at the chosen depth still matches the oracle, and a solve straight
+    after the tuning converges as fast as at a fixed depth (the tuning's own tables are gone)."""
+    bem = _bem()
+    mesh = small_cluster(40, 3, seed=21)
+    rng = np.random.Generator(np.random.PCG64(22))
+    x = rng.standard_normal(mesh.n)
+    ref = oracle.BemOperator(mesh.xyz, mesh.tri)
+    recv = oracle.checkpoint_receivers(mesh.n, 2000, 3)
+    e = ref.apply(1.0, x, 0.0, None, recv)
+    phi = synth.cluster_potential(mesh, 4, 0.1, rng) + 1.0
+    out, its = {}, {}
+    for leaf in (64, 0):
+        ctx = make_ctx(mesh, mvp=bem.BEM_MVP_FMM, precision=bem.BEM_PREC_MIXED, p_fmm=14, leaf_target=leaf,
+                       gmres_tol=1e-6, gmres_maxit=300)
+        o = torch.zeros(mesh.n, dtype=torch.float64, device="cuda")
+        ctx.apply(1.0, dev(x), 0.0, None, o)
+        out[leaf] = (o.cpu().numpy(), ctx.stats()["levels"])
+        q = torch.zeros(mesh.n, dtype=torch.float64, device="cuda")
+        its[leaf], _ = ctx.solve(dev(phi), q)
+        ctx.close()
+    print("levels fixed-rule %d, tuned %d; iterations %d / %d" % (out[64][1], out[0][1], its[64], its[0]))
+    assert abs(out[0][1] - out[64][1]) <= 1
+    assert rel(out[0][0][recv], e) < 1e-5
+    assert its[0] <= its[64] + 3
