@@ -80,6 +80,14 @@ typedef struct {
     int32_t mvp;            /* bem_mvp_kind. Default BEM_MVP_FMM.                              */
     int32_t diag_precision; /* precision of the 4-RHS product that feeds Eqs. (s3)/(s5);
                                -1 = same as `precision`. Default -1.                           */
+    int32_t diag_p_fmm;     /* truncation number of that 4-RHS product (2..20); -1 = p_fmm + 2,
+                               at most 20. The identities form L_ii and M_ii by cancelling
+                               O(1) sums down to O(h), which magnifies the far field's
+                               truncation error; the products of GMRES do not need it (on the
+                               3.21M-unknown cluster at p_fmm = 14 the off-diagonal part of a
+                               product is within 6e-7 of the direct sum, L_ii within 4e-5).
+                               Default -1.                                                     */
+    int32_t reserved;       /* 0                                                               */
     int32_t m2l_tensor_cores; /* 1: mixed-precision single-RHS products (every GMRES product)
                                run M2L on the tensor cores (three-piece BF16 split, FP32
                                accumulation) when p_fmm^2 is a multiple of 4 and <= 256;

@@ -52,6 +52,8 @@ class bem_params(ctypes.Structure):
         ("precision", ctypes.c_int32),
         ("mvp", ctypes.c_int32),
         ("diag_precision", ctypes.c_int32),
+        ("diag_p_fmm", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
         ("m2l_tensor_cores", ctypes.c_int32),
         ("gmres_precond", ctypes.c_int32),
         ("gmres_maxit", ctypes.c_int32),

@@ -156,6 +156,8 @@ void check_params(const bem_params &p) {
     if (p.precision != BEM_PREC_FP64 && p.precision != BEM_PREC_MIXED) fail(BEM_ERR_ARG, "bad precision");
     if (p.diag_precision != -1 && p.diag_precision != BEM_PREC_FP64 && p.diag_precision != BEM_PREC_MIXED)
         fail(BEM_ERR_ARG, "bad diag_precision");
+    if (p.diag_p_fmm != -1 && (p.diag_p_fmm < 2 || p.diag_p_fmm > kMaxPfmm))
+        fail(BEM_ERR_ARG, "diag_p_fmm must be -1 or in 2..20");
     if (p.mvp != BEM_MVP_FMM && p.mvp != BEM_MVP_DIRECT) fail(BEM_ERR_ARG, "bad mvp kind");
     if (p.m2l_tensor_cores != 0 && p.m2l_tensor_cores != 1) fail(BEM_ERR_ARG, "m2l_tensor_cores must be 0 or 1");
     if (p.gmres_maxit < 1 || p.gmres_restart < 0 || p.gmres_restart > 127) fail(BEM_ERR_ARG, "bad GMRES limits");
@@ -249,7 +251,7 @@ void build_all(Context &c) {
         compute_vertex_geometry(c);
     }
     if (c.prm.mvp == BEM_MVP_FMM) {
-        build_operators(c);
+        build_operators(c, c.ops, c.prm.p_fmm);
         if (c.prm.m2l_tensor_cores && m2l_tc_supported(c.ops.P) && c.ops.tc_Npad == 0) build_tc_tables(c);
         c.tc_chunks_r = 0;
         c.tc_err.resize(1);
@@ -302,7 +304,15 @@ void build_all(Context &c) {
     const double *xm[4] = {c.ones.p, c.xyz.p, c.xyz.p + N, c.xyz.p + 2 * N};
     double *o[4] = {tmp.p, tmp.p + N, tmp.p + 2 * N, tmp.p + 3 * N};
     int dprec = c.prm.diag_precision < 0 ? c.prm.precision : c.prm.diag_precision;
-    offdiag_apply(c, 4, fa, xl, ga, xm, o, dprec);
+    const Operators *dops = nullptr;
+    if (c.prm.mvp == BEM_MVP_FMM) {
+        const int dp = c.prm.diag_p_fmm > 0 ? c.prm.diag_p_fmm : std::min(c.prm.p_fmm + 2, kMaxPfmm);
+        if (dp != c.prm.p_fmm) {
+            build_operators(c, c.ops_diag, dp);
+            dops = &c.ops_diag;
+        }
+    }
+    offdiag_apply(c, 4, fa, xl, ga, xm, o, dprec, dops);
     c.ldiag.resize(N);
     c.mdiag.resize(N);
     PhaseScope ps(c, PH_DIAG);
@@ -357,6 +367,8 @@ int bem_params_default(bem_params *p) {
     p->precision = BEM_PREC_MIXED;
     p->mvp = BEM_MVP_FMM;
     p->diag_precision = -1;
+    p->diag_p_fmm = -1;
+    p->reserved = 0;
     p->m2l_tensor_cores = 1;
     p->gmres_precond = 0;
     p->gmres_maxit = 100;

@@ -401,12 +401,29 @@ constexpr int XT_ROWS = 64, XT_COLS = 64, XT_K = 16, XT_THREADS = 256;
 // MODE kAddTarget: Y[tgt] += T X[src]; only for launches whose targets are all distinct.
 constexpr int kStorePair = 0, kAddTarget = 1;
 
+__device__ __forceinline__ void vec4_load(const float *p, float *v) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+}
+__device__ __forceinline__ void vec4_load(const double *p, double *v) {
+    const double2 t0 = reinterpret_cast<const double2 *>(p)[0], t1 = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = t0.x;
+    v[1] = t0.y;
+    v[2] = t1.x;
+    v[3] = t1.y;
+}
+
 template <class T, int R, int MODE>
 __global__ void __launch_bounds__(XT_THREADS) k_xlat(const T *__restrict__ mats, int P, const XChunk *__restrict__ chunks,
                                                      const int32_t *__restrict__ srcs, const int32_t *__restrict__ tgts,
                                                      const T *X, T *Y) {  // X and Y may be one array (M2M, L2L)
-    __shared__ T As[XT_K][XT_ROWS + 4];
-    __shared__ T Bs[XT_K][XT_COLS + 4];
+    // two shared-memory buffers: the next K tile's global loads are in flight (in registers)
+    // while the current tile is multiplied
+    __shared__ __align__(16) T As[2][XT_K][XT_ROWS + 4];  // row pitch a multiple of 16 bytes
+    __shared__ __align__(16) T Bs[2][XT_K][XT_COLS + 4];
     __shared__ int s_src[XT_COLS], s_tgt[XT_COLS];
     const XChunk ch = chunks[blockIdx.x];
     const int row0 = blockIdx.y * XT_ROWS;
@@ -430,39 +447,58 @@ __global__ void __launch_bounds__(XT_THREADS) k_xlat(const T *__restrict__ mats,
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
-    for (int k0 = 0; k0 < P; k0 += XT_K) {
+    constexpr int NA = (XT_ROWS * XT_K) / XT_THREADS, NB = (XT_COLS * XT_K) / XT_THREADS;
+    T ra[NA], rb[NB];
+    auto gload = [&](int k0) {
 #pragma unroll
-        for (int it = 0; it < (XT_ROWS * XT_K) / XT_THREADS; ++it) {
-            int e = tid + it * XT_THREADS;
-            int row = e / XT_K, kk = e % XT_K;
-            int gr = row0 + row, gk = k0 + kk;
-            As[kk][row] = (gr < P && gk < P) ? A[(size_t)gr * P + gk] : (T)0;
+        for (int it = 0; it < NA; ++it) {
+            const int e = tid + it * XT_THREADS;
+            const int row = e / XT_K, kk = e % XT_K;
+            const int gr = row0 + row, gk = k0 + kk;
+            ra[it] = (gr < P && gk < P) ? A[(size_t)gr * P + gk] : (T)0;
         }
 #pragma unroll
-        for (int it = 0; it < (XT_COLS * XT_K) / XT_THREADS; ++it) {
-            int e = tid + it * XT_THREADS;
-            int col = e / XT_K, kk = e % XT_K;
-            int gk = k0 + kk;
-            T v = (T)0;
-            if (col < ncol && gk < P) {
-                int r = col % R;
-                v = X[((size_t)s_src[col] * R + r) * P + gk];
+        for (int it = 0; it < NB; ++it) {
+            const int e = tid + it * XT_THREADS;
+            const int col = e / XT_K, kk = e % XT_K;
+            const int gk = k0 + kk;
+            rb[it] = (col < ncol && gk < P) ? X[((size_t)s_src[col] * R + col % R) * P + gk] : (T)0;
+        }
+    };
+    auto sstore = [&](int buf) {
+#pragma unroll
+        for (int it = 0; it < NA; ++it) {
+            const int e = tid + it * XT_THREADS;
+            As[buf][e % XT_K][e / XT_K] = ra[it];
+        }
+#pragma unroll
+        for (int it = 0; it < NB; ++it) {
+            const int e = tid + it * XT_THREADS;
+            Bs[buf][e % XT_K][e / XT_K] = rb[it];
+        }
+    };
+    const int nk = (P + XT_K - 1) / XT_K;
+    gload(0);
+    sstore(0);
+    __syncthreads();
+    for (int t = 0; t < nk; ++t) {
+        const int buf = t & 1;
+        if (t + 1 < nk) gload((t + 1) * XT_K);
+        if (row0 + ty * 4 < P) {  // rows past P (the last row tile) skip the products
+#pragma unroll
+            for (int kk = 0; kk < XT_K; ++kk) {
+                // four consecutive rows / columns per thread: one 16-byte (float) or two
+                // (double) shared-memory loads each
+                T a[4], bv[4];
+                vec4_load(&As[buf][kk][ty * 4], a);
+                vec4_load(&Bs[buf][kk][tx * 4], bv);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bv[j];
             }
-            Bs[kk][col] = v;
         }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < XT_K; ++kk) {
-            T a[4], bv[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx * 4 + j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bv[j];
-        }
+        if (t + 1 < nk) sstore(buf ^ 1);  // that buffer was last read before the previous barrier
         __syncthreads();
     }
 #pragma unroll
@@ -608,11 +644,11 @@ void make_chunks(const std::vector<int64_t> &class_off, int64_t base, int per, s
 }
 
 template <class T, int R>
-void run_fmm(Context &c, const RhsArgs<R> &a) {
+void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
     Tree &t = c.tree;
     cudaStream_t st = c.stream;
     const int64_t N = c.N;
-    const int L = t.L, p = c.ops.p, P = c.ops.P;
+    const int L = t.L, p = opr.p, P = opr.P;
     const int tb = 256;
     constexpr bool F64 = sizeof(T) == 8;
     T *q, *w, *mp, *lc, *far;
@@ -627,7 +663,7 @@ void run_fmm(Context &c, const RhsArgs<R> &a) {
         c.far64.resize((size_t)R * N);
         q = (T *)c.q64.p; w = (T *)c.w64.p; mp = (T *)c.mp64.p; lc = (T *)c.lc64.p; far = (T *)c.far64.p;
         loc = (const T *)t.loc64.p; nrm = (const T *)t.nrm64.p;
-        m2l = (const T *)c.ops.m2l64.p; m2m = (const T *)c.ops.m2m64.p; l2l = (const T *)c.ops.l2l64.p;
+        m2l = (const T *)opr.m2l64.p; m2m = (const T *)opr.m2m64.p; l2l = (const T *)opr.l2l64.p;
     } else {
         c.q32.resize((size_t)R * N);
         c.w32.resize((size_t)R * N);
@@ -636,7 +672,7 @@ void run_fmm(Context &c, const RhsArgs<R> &a) {
         c.far32.resize((size_t)R * N);
         q = (T *)c.q32.p; w = (T *)c.w32.p; mp = (T *)c.mp32.p; lc = (T *)c.lc32.p; far = (T *)c.far32.p;
         loc = (const T *)t.loc32.p; nrm = (const T *)t.nrm32.p;
-        m2l = (const T *)c.ops.m2l32.p; m2m = (const T *)c.ops.m2m32.p; l2l = (const T *)c.ops.l2l32.p;
+        m2l = (const T *)opr.m2l32.p; m2m = (const T *)opr.m2m32.p; l2l = (const T *)opr.l2l32.p;
     }
     {
         PhaseScope ps(c, PH_STRENGTHS);
@@ -724,7 +760,8 @@ void run_fmm(Context &c, const RhsArgs<R> &a) {
     if (nm2l_chunks) {
         // The 4-RHS product behind the diagonals stays on the CUDA cores: M_ii and L_ii are formed
         // by cancellation (Eqs. (s3), (s5)), which magnifies the tensor path's rounding.
-        const bool tc_path = !F64 && R == 1 && c.prm.m2l_tensor_cores && m2l_tc_supported(P) && c.ops.tc_Npad > 0;
+        const bool tc_path = !F64 && R == 1 && c.prm.m2l_tensor_cores && m2l_tc_supported(P) && opr.tc_Npad > 0 &&
+                             &opr == &c.ops;
         if (tc_path) {
             PhaseScope ps(c, PH_M2L);
             if (c.tc_chunks_r != R) {
@@ -789,10 +826,8 @@ void run_fmm(Context &c, const RhsArgs<R> &a) {
 
 }  // namespace
 
-void build_operators(Context &c) {
-    int p = c.prm.p_fmm;
-    if (c.ops_ready && c.ops_p == p) return;
-    Operators &o = c.ops;
+void build_operators(Context &c, Operators &o, int p) {
+    if (o.ready && o.p == p) return;
     o.p = p;
     o.P = p * p;
     o.tc_Npad = o.tc_Kpad = 0;  // tensor-core tables follow the operators
@@ -812,13 +847,12 @@ void build_operators(Context &c) {
     BEM_LAUNCH_CHECK();
     k_build_ops<<<8, 256, sm_up, c.stream>>>(kOpL2L, p, o.l2l64.p, o.l2l32.p);
     BEM_LAUNCH_CHECK();
-    c.ops_ready = true;
-    c.ops_p = p;
+    o.ready = true;
 }
 
 template <int R>
 static void offdiag_R(Context &c, const double *f, const double *const *xL, const double *g,
-                      const double *const *xM, double *const *out, int prec) {
+                      const double *const *xM, double *const *out, int prec, const Operators &o) {
     RhsArgs<R> a{};
     for (int r = 0; r < R; ++r) {
         a.f[r] = f[r];
@@ -827,12 +861,13 @@ static void offdiag_R(Context &c, const double *f, const double *const *xL, cons
         a.xM[r] = xM[r];
         a.out[r] = out[r];
     }
-    if (prec == BEM_PREC_FP64) run_fmm<double, R>(c, a);
-    else run_fmm<float, R>(c, a);
+    if (prec == BEM_PREC_FP64) run_fmm<double, R>(c, a, o);
+    else run_fmm<float, R>(c, a, o);
 }
 
 void offdiag_apply(Context &c, int R, const double *f, const double *const *xL, const double *g,
-                   const double *const *xM, double *const *out, int prec) {
+                   const double *const *xM, double *const *out, int prec, const Operators *ops) {
+    const Operators &o = ops ? *ops : c.ops;
     c.stats.n_apply += 1;
     c.stats.n_apply_rhs += R;
     if (c.prm.mvp == BEM_MVP_DIRECT) {
@@ -841,8 +876,8 @@ void offdiag_apply(Context &c, int R, const double *f, const double *const *xL, 
         else fail(BEM_ERR_ARG, "unsupported RHS count");
         return;
     }
-    if (R == 1) offdiag_R<1>(c, f, xL, g, xM, out, prec);
-    else if (R == 4) offdiag_R<4>(c, f, xL, g, xM, out, prec);
+    if (R == 1) offdiag_R<1>(c, f, xL, g, xM, out, prec, o);
+    else if (R == 4) offdiag_R<4>(c, f, xL, g, xM, out, prec, o);
     else fail(BEM_ERR_ARG, "unsupported RHS count");
 }
 

@@ -145,6 +145,7 @@ struct Tree {
 
 // ------------------------------------------------------------------------------ FMM operators
 struct Operators {
+    bool ready = false;
     int p = 0, P = 0;
     DevBuf<double> m2l64, m2m64, l2l64;  // [316][P][P], [8][P][P], [8][P][P]
     DevBuf<float> m2l32, m2m32, l2l32;
@@ -270,8 +271,7 @@ struct Context {
 
     Tree tree;
     Operators ops;
-    bool ops_ready = false;
-    int ops_p = -1;
+    Operators ops_diag;  // operators of the 4-RHS diagonal product when diag_p_fmm != p_fmm
 
     // FMM work arrays
     DevBuf<double> q64, w64;       // strengths [R][N] sorted order
@@ -341,11 +341,12 @@ void exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *tot
                         cudaStream_t st);
 
 // fmm.cu
-void build_operators(Context &c);
+void build_operators(Context &c, Operators &o, int p);
 // out[r][i] (caller order) = sum over the R right-hand sides of the off-diagonal product:
 // f[r] (L_off xL[r]) + g[r] (M_off xM[r]); prec = bem_precision.
 void offdiag_apply(Context &c, int R, const double *f, const double *const *xL,
-                   const double *g, const double *const *xM, double *const *out, int prec);
+                   const double *g, const double *const *xM, double *const *out, int prec,
+                   const Operators *ops = nullptr);
 
 // p2p.cu
 template <class T, int R>
