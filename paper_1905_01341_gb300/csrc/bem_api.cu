@@ -12,6 +12,11 @@ namespace bem {
 long long g_launch_count = 0;
 
 Context::~Context() {
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (ev_far) cudaEventDestroy(ev_far);
+    if (side) cudaStreamDestroy(side);
+    if (hi) cudaStreamDestroy(hi);
     for (auto *p : up_chunks) delete p;
     step_free(step);
     mlp_free(mlp);

@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(256) k_p2m(int p, int nleaf, const int32_t *__
 // ------------------------------------------------------------------------------ translations
 // Class-grouped product: for every pair (src, tgt) of a chunk, Y[tgt] += T_cls X[src], as a
 // tiled GEMM (64 output rows x 64 columns per block; a column is one pair and one RHS).
-constexpr int XT_ROWS = 64, XT_COLS = 64, XT_K = 16, XT_THREADS = 256;
+constexpr int XT_COLS = 64, XT_K = 16, XT_THREADS = 256;
 
 // MODE kStorePair: Y[pair] = T X[src] (one slot per pair, summed later in a fixed order).
 // MODE kAddTarget: Y[tgt] += T X[src]; only for launches whose targets are all distinct.
@@ -416,17 +416,25 @@ __device__ __forceinline__ void vec4_load(const double *p, double *v) {
     v[3] = t1.y;
 }
 
+// rows per thread and per block: 8 x 4 outputs per thread in FP32 (a 128-row tile), 4 x 4 in
+// FP64 (64 rows, keeping the double-buffered tiles under the static shared-memory limit)
+template <class T>
+__host__ __device__ constexpr int xt_rt() { return sizeof(T) == 4 ? 8 : 4; }
+template <class T>
+__host__ __device__ constexpr int xt_rows() { return 16 * xt_rt<T>(); }
+
 template <class T, int R, int MODE>
 __global__ void __launch_bounds__(XT_THREADS) k_xlat(const T *__restrict__ mats, int P, const XChunk *__restrict__ chunks,
                                                      const int32_t *__restrict__ srcs, const int32_t *__restrict__ tgts,
                                                      const T *X, T *Y) {  // X and Y may be one array (M2M, L2L)
+    constexpr int RT = xt_rt<T>(), ROWS = xt_rows<T>();
     // two shared-memory buffers: the next K tile's global loads are in flight (in registers)
     // while the current tile is multiplied
-    __shared__ __align__(16) T As[2][XT_K][XT_ROWS + 4];  // row pitch a multiple of 16 bytes
+    __shared__ __align__(16) T As[2][XT_K][ROWS + 4];  // row pitch a multiple of 16 bytes
     __shared__ __align__(16) T Bs[2][XT_K][XT_COLS + 4];
     __shared__ int s_src[XT_COLS], s_tgt[XT_COLS];
     const XChunk ch = chunks[blockIdx.x];
-    const int row0 = blockIdx.y * XT_ROWS;
+    const int row0 = blockIdx.y * ROWS;
     const T *A = mats + (size_t)ch.cls * P * P;
     const int ncol = ch.count * R;
     int tid = threadIdx.x;
@@ -441,13 +449,13 @@ __global__ void __launch_bounds__(XT_THREADS) k_xlat(const T *__restrict__ mats,
         }
     }
     __syncthreads();
-    const int tx = tid % 16, ty = tid / 16;
-    T acc[4][4];
+    const int tx = tid % 16, ty = tid / 16;  // columns tx*4.., rows ty*RT..
+    T acc[RT][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < RT; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
-    constexpr int NA = (XT_ROWS * XT_K) / XT_THREADS, NB = (XT_COLS * XT_K) / XT_THREADS;
+    constexpr int NA = (ROWS * XT_K) / XT_THREADS, NB = (XT_COLS * XT_K) / XT_THREADS;
     T ra[NA], rb[NB];
     auto gload = [&](int k0) {
 #pragma unroll
@@ -484,16 +492,16 @@ __global__ void __launch_bounds__(XT_THREADS) k_xlat(const T *__restrict__ mats,
     for (int t = 0; t < nk; ++t) {
         const int buf = t & 1;
         if (t + 1 < nk) gload((t + 1) * XT_K);
-        if (row0 + ty * 4 < P) {  // rows past P (the last row tile) skip the products
+        if (row0 + ty * RT < P) {  // rows past P (the last row tile) skip the products
 #pragma unroll
             for (int kk = 0; kk < XT_K; ++kk) {
-                // four consecutive rows / columns per thread: one 16-byte (float) or two
-                // (double) shared-memory loads each
-                T a[4], bv[4];
-                vec4_load(&As[buf][kk][ty * 4], a);
+                // consecutive rows / columns per thread through 16-byte shared-memory loads
+                T a[RT], bv[4];
+#pragma unroll
+                for (int i = 0; i < RT; i += 4) vec4_load(&As[buf][kk][ty * RT + i], a + i);
                 vec4_load(&Bs[buf][kk][tx * 4], bv);
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < RT; ++i)
 #pragma unroll
                     for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bv[j];
             }
@@ -509,8 +517,8 @@ __global__ void __launch_bounds__(XT_THREADS) k_xlat(const T *__restrict__ mats,
         T *yb = (MODE == kStorePair) ? Y + ((size_t)(ch.start + col / R) * R + r) * P
                                      : Y + ((size_t)s_tgt[col] * R + r) * P;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            int gr = row0 + ty * 4 + i;
+        for (int i = 0; i < RT; ++i) {
+            int gr = row0 + ty * RT + i;
             if (gr < P) {
                 if (MODE == kStorePair) yb[gr] = acc[i][j];
                 else yb[gr] += acc[i][j];
@@ -623,12 +631,15 @@ __global__ void k_zero(size_t n, T *a) {
     if (i < n) a[i] = (T)0;
 }
 
-__global__ void k_scatter_out(int64_t N, int R, const int32_t *__restrict__ perm, const double *__restrict__ src,
-                              RhsArgs<kMaxRhs> a) {
+// out[perm[k]] = (far_k + near_k) / h_leaf: the far field (L2P) and the near field (P2P, run
+// concurrently on the side stream) meet here, back in the caller's vertex order.
+template <class T>
+__global__ void k_combine_out(int64_t N, int R, const int32_t *__restrict__ perm, const T *__restrict__ far,
+                              const double *__restrict__ near, const double *__restrict__ ih, RhsArgs<kMaxRhs> a) {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= N) return;
     int j = perm[k];
-    for (int r = 0; r < R; ++r) a.out[r][j] = src[r * N + k];
+    for (int r = 0; r < R; ++r) a.out[r][j] = ((double)far[r * N + k] + near[r * N + k]) * ih[k];
 }
 
 // Chunks of at most `per` pairs within each class.
@@ -679,6 +690,35 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
         k_strengths<T, R><<<div_up(N, tb), tb, 0, st>>>(N, t.perm.p, t.s_sorted.p, a, t.ih.p, q, w);
         BEM_LAUNCH_CHECK();
     }
+    // The near field needs only the strengths: it runs on the low-priority side stream,
+    // overlapped with the whole far field below (the two meet in k_combine_out). P2P keeps the
+    // FP32 cores busy while M2L occupies the tensor cores with few warps per SM.
+    c.near_out.resize((size_t)R * N);
+    if (!c.side) {
+        int least = 0, greatest = 0;
+        BEM_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        BEM_CUDA(cudaStreamCreateWithPriority(&c.side, cudaStreamNonBlocking, least));
+        BEM_CUDA(cudaStreamCreateWithPriority(&c.hi, cudaStreamNonBlocking, greatest));
+        BEM_CUDA(cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming));
+        BEM_CUDA(cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming));
+        BEM_CUDA(cudaEventCreateWithFlags(&c.ev_far, cudaEventDisableTiming));
+    }
+    BEM_CUDA(cudaEventRecord(c.ev_fork, st));
+    BEM_CUDA(cudaStreamWaitEvent(c.side, c.ev_fork, 0));
+    {
+        PhaseScope ps(c, PH_P2P, c.side);
+        bool hq = false, hw = false;
+        for (int r = 0; r < R; ++r) {
+            hq = hq || a.f[r] != 0.0;
+            hw = hw || a.g[r] != 0.0;
+        }
+        launch_p2p_list<T, R>(c, q, w, c.near_out.p, hq, hw, c.side);
+    }
+    BEM_CUDA(cudaEventRecord(c.ev_join, c.side));
+    // the far field runs on a high-priority stream, so its blocks (the tensor-core M2L's in
+    // particular) are placed as soon as an SM has room and the near field fills the rest
+    cudaStream_t fs = c.hi;
+    BEM_CUDA(cudaStreamWaitEvent(fs, c.ev_fork, 0));
 
     // chunk tables for this R (built once per build)
     const int per = XT_COLS / R;
@@ -691,7 +731,7 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
         for (int l = 3; l <= L; ++l) make_chunks(t.up_class_off[l], t.up_off[l], per, all);
         mch = all;
         c.m2l_chunks.resize(all.size());
-        BEM_CUDA(cudaMemcpyAsync(c.m2l_chunks.p, all.data(), all.size() * sizeof(XChunk), cudaMemcpyHostToDevice, st));
+        BEM_CUDA(cudaMemcpyAsync(c.m2l_chunks.p, all.data(), all.size() * sizeof(XChunk), cudaMemcpyHostToDevice, fs));
     }
     // locate the per-phase ranges in the chunk table
     int64_t nm2l_chunks = 0;
@@ -706,12 +746,12 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
         up_n[l] = k;
         cur += k;
     }
-    const int rowblocks = div_up(P, XT_ROWS);
+    const int rowblocks = div_up(P, xt_rows<T>());
 
     // P2M at the leaves
     const int nleaf = t.nb[L];
     {
-        PhaseScope ps(c, PH_P2M);
+        PhaseScope ps(c, PH_P2M, fs);
         const int ntri = p * (p + 1) / 2;
         size_t sm = ((size_t)2 * P2M_PC * ntri + P2M_PC * 3 + 2 * P2M_PC * R + p + ntri) * sizeof(T);
         const int threads = ntri <= 256 ? 128 : 256;  // ntri <= 2 * threads
@@ -719,15 +759,15 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
         for (int r = 0; r < R; ++r) hw = hw || a.g[r] != 0.0;
         auto kern = hw ? k_p2m<T, R, true> : k_p2m<T, R, false>;
         if (sm > 48 * 1024) BEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        kern<<<nleaf, threads, sm, st>>>(p, nleaf, t.bstart.p + t.base[L], t.bcount.p + t.base[L], N, loc, nrm, q, w,
+        kern<<<nleaf, threads, sm, fs>>>(p, nleaf, t.bstart.p + t.base[L], t.bcount.p + t.base[L], N, loc, nrm, q, w,
                                          mp + (size_t)t.base[L] * R * P);
         BEM_LAUNCH_CHECK();
     }
     // zero the multipoles above the leaves and all locals
     {
         size_t nup = (size_t)t.base[L] * R * P;
-        if (nup) k_zero<T><<<div_up(nup, tb), tb, 0, st>>>(nup, mp);
-        k_zero<T><<<div_up(exp_sz, tb), tb, 0, st>>>(exp_sz, lc);
+        if (nup) k_zero<T><<<div_up(nup, tb), tb, 0, fs>>>(nup, mp);
+        k_zero<T><<<div_up(exp_sz, tb), tb, 0, fs>>>(exp_sz, lc);
         BEM_LAUNCH_CHECK();
     }
     // per-pair buffer for the fixed-order reductions
@@ -746,14 +786,14 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
     const int red_blocks_y = div_up(R * P, 128);
     // M2M upward, levels L -> 2: per-pair products, then each parent sums its children
     for (int l = L; l >= 3; --l) {
-        PhaseScope ps(c, PH_M2M);
+        PhaseScope ps(c, PH_M2M, fs);
         if (!up_n[l]) continue;
         dim3 grid((unsigned)up_n[l], rowblocks);
-        k_xlat<T, R, kStorePair><<<grid, XT_THREADS, 0, st>>>(m2m, P, c.m2l_chunks.p + up_first[l], t.up_child.p,
+        k_xlat<T, R, kStorePair><<<grid, XT_THREADS, 0, fs>>>(m2m, P, c.m2l_chunks.p + up_first[l], t.up_child.p,
                                                              t.up_parent.p, mp, ypair);
         BEM_LAUNCH_CHECK();
         dim3 rg((unsigned)t.nb[l - 1], red_blocks_y);
-        k_reduce_pairs<T, R><<<rg, 128, 0, st>>>(t.base[l - 1], t.up_par_off.p, t.up_by_par.p, ypair, P, mp);
+        k_reduce_pairs<T, R><<<rg, 128, 0, fs>>>(t.base[l - 1], t.up_par_off.p, t.up_by_par.p, ypair, P, mp);
         BEM_LAUNCH_CHECK();
     }
     // M2L, all levels at once, then each target sums its sources
@@ -763,64 +803,57 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
         const bool tc_path = !F64 && R == 1 && c.prm.m2l_tensor_cores && m2l_tc_supported(P) && opr.tc_Npad > 0 &&
                              &opr == &c.ops;
         if (tc_path) {
-            PhaseScope ps(c, PH_M2L);
+            PhaseScope ps(c, PH_M2L, fs);
             if (c.tc_chunks_r != R) {
                 std::vector<XChunk> tc;
                 make_chunks(t.m2l_class_off, 0, m2l_tc_pairs_per_chunk(R), tc);
                 c.tc_chunks.resize(std::max<size_t>(tc.size(), 1));
                 if (!tc.empty())
                     BEM_CUDA(cudaMemcpyAsync(c.tc_chunks.p, tc.data(), tc.size() * sizeof(XChunk),
-                                             cudaMemcpyHostToDevice, st));
+                                             cudaMemcpyHostToDevice, fs));
                 c.n_tc_chunks = (int64_t)tc.size();
                 c.tc_chunks_r = R;
             }
             if (c.n_tc_chunks)
                 launch_m2l_tc<R>(c, c.tc_chunks.p, c.n_tc_chunks, (const float *)mp, (int64_t)t.nbox * R, (float *)ypair,
-                                 c.tc_err.p);
+                                 c.tc_err.p, fs);
         } else {
-            PhaseScope ps(c, PH_M2L_CC);
+            PhaseScope ps(c, PH_M2L_CC, fs);
             dim3 grid((unsigned)nm2l_chunks, rowblocks);
-            k_xlat<T, R, kStorePair><<<grid, XT_THREADS, 0, st>>>(m2l, P, c.m2l_chunks.p + 1, t.m2l_src.p,
+            k_xlat<T, R, kStorePair><<<grid, XT_THREADS, 0, fs>>>(m2l, P, c.m2l_chunks.p + 1, t.m2l_src.p,
                                                                  t.m2l_tgt.p, mp, ypair);
             BEM_LAUNCH_CHECK();
         }
-        PhaseScope ps(c, PH_M2L_REDUCE);
+        PhaseScope ps(c, PH_M2L_REDUCE, fs);
         int ntg = t.nbox - t.base[2];
         dim3 rg((unsigned)ntg, red_blocks_y);
-        k_reduce_pairs<T, R><<<rg, 128, 0, st>>>(t.base[2], t.m2l_tgt_off.p, t.m2l_by_tgt.p, ypair, P, lc);
+        k_reduce_pairs<T, R><<<rg, 128, 0, fs>>>(t.base[2], t.m2l_tgt_off.p, t.m2l_by_tgt.p, ypair, P, lc);
         BEM_LAUNCH_CHECK();
     }
     // L2L downward, levels 3 -> L: every child has exactly one parent, so it adds in place
     for (int l = 3; l <= L; ++l) {
         if (!up_n[l]) continue;
-        PhaseScope ps(c, PH_L2L);
+        PhaseScope ps(c, PH_L2L, fs);
         dim3 grid((unsigned)up_n[l], rowblocks);
-        k_xlat<T, R, kAddTarget><<<grid, XT_THREADS, 0, st>>>(l2l, P, c.m2l_chunks.p + up_first[l], t.up_parent.p,
+        k_xlat<T, R, kAddTarget><<<grid, XT_THREADS, 0, fs>>>(l2l, P, c.m2l_chunks.p + up_first[l], t.up_parent.p,
                                                              t.up_child.p, lc, lc);
         BEM_LAUNCH_CHECK();
     }
     // L2P
     {
-        PhaseScope ps(c, PH_L2P);
+        PhaseScope ps(c, PH_L2P, fs);
         size_t sm = (size_t)R * P * sizeof(T);
-        k_l2p<T, R><<<nleaf, L2P_THREADS, sm, st>>>(p, t.bstart.p + t.base[L], t.bcount.p + t.base[L], N, loc,
+        k_l2p<T, R><<<nleaf, L2P_THREADS, sm, fs>>>(p, t.bstart.p + t.base[L], t.bcount.p + t.base[L], N, loc,
                                                     lc + (size_t)t.base[L] * R * P, far);
         BEM_LAUNCH_CHECK();
     }
-    // P2P (adds far, scales by 1/h), then back to the caller's order
-    c.near_out.resize((size_t)R * N);
-    {
-        PhaseScope ps(c, PH_P2P);
-        bool hq = false, hw = false;
-        for (int r = 0; r < R; ++r) {
-            hq = hq || a.f[r] != 0.0;
-            hw = hw || a.g[r] != 0.0;
-        }
-        launch_p2p_list<T, R>(c, q, w, far, c.near_out.p, hq, hw);
-    }
+    BEM_CUDA(cudaEventRecord(c.ev_far, fs));
+    // join the near field, add the far field, scale by 1/h and return to the caller's order
+    BEM_CUDA(cudaStreamWaitEvent(st, c.ev_far, 0));
+    BEM_CUDA(cudaStreamWaitEvent(st, c.ev_join, 0));
     RhsArgs<kMaxRhs> o{};
     for (int r = 0; r < R; ++r) o.out[r] = a.out[r];
-    k_scatter_out<<<div_up(N, tb), tb, 0, st>>>(N, R, t.perm.p, c.near_out.p, o);
+    k_combine_out<T><<<div_up(N, tb), tb, 0, st>>>(N, R, t.perm.p, far, c.near_out.p, t.ih.p, o);
     BEM_LAUNCH_CHECK();
 }
 

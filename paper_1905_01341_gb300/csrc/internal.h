@@ -236,8 +236,10 @@ void mlp_free(Mlp *m);
 struct PhaseScope {
     Context *c;
     int phase;
+    cudaStream_t s;  // the stream the phase's kernels run on
     cudaEvent_t a = nullptr;
     PhaseScope(Context &cc, int ph);
+    PhaseScope(Context &cc, int ph, cudaStream_t st);
     ~PhaseScope();
 };
 
@@ -245,6 +247,10 @@ struct PhaseScope {
 struct Context {
     bem_params prm{};
     cudaStream_t stream = nullptr;
+    // streams of the FMM product: after the strengths, the near field and the far field run
+    // concurrently on two internal streams and join back into `stream` (created on first use)
+    cudaStream_t side = nullptr, hi = nullptr;  // near field (lowest priority), far field (highest)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_far = nullptr;
     int device = 0;
     std::string err;
 
@@ -350,7 +356,7 @@ void offdiag_apply(Context &c, int R, const double *f, const double *const *xL,
 
 // p2p.cu
 template <class T, int R>
-void launch_p2p_list(Context &c, const T *q, const T *w, const T *far, double *out_sorted, bool hq, bool hw);
+void launch_p2p_list(Context &c, const T *q, const T *w, double *near_sorted, bool hq, bool hw, cudaStream_t st);
 template <int R>
 void launch_direct(Context &c, int prec, const double *f, const double *const *xL,
                    const double *g, const double *const *xM, double *const *out);
@@ -364,22 +370,23 @@ bool m2l_tc_supported(int P);
 void build_tc_tables(Context &c);
 template <int R>
 void launch_m2l_tc(Context &c, const XChunk *chunks, int64_t nchunks, const float *X, int64_t xrows, float *Ypair,
-                   int *err);
+                   int *err, cudaStream_t st);
 int m2l_tc_pairs_per_chunk(int R);
 
 // gmres.cu
 void gmres_solve(Context &c, const double *b, double *x, int *iters, double *relres);
 
-inline PhaseScope::PhaseScope(Context &cc, int ph) : c(&cc), phase(ph) {
+inline PhaseScope::PhaseScope(Context &cc, int ph) : PhaseScope(cc, ph, cc.stream) {}
+inline PhaseScope::PhaseScope(Context &cc, int ph, cudaStream_t st) : c(&cc), phase(ph), s(st) {
     if (c->prof.on) {
         a = c->prof.take();
-        BEM_CUDA(cudaEventRecord(a, c->stream));
+        BEM_CUDA(cudaEventRecord(a, s));
     }
 }
 inline PhaseScope::~PhaseScope() {
     if (a) {
         cudaEvent_t b = c->prof.take();
-        cudaEventRecord(b, c->stream);
+        cudaEventRecord(b, s);
         c->prof.recs.push_back({phase, a, b});
     }
 }

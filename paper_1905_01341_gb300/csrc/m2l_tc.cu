@@ -363,7 +363,7 @@ void build_tc_tables(Context &c) {
 
 template <int R>
 void launch_m2l_tc(Context &c, const XChunk *chunks, int64_t nchunks, const float *X, int64_t xrows, float *Ypair,
-                   int *err) {
+                   int *err, cudaStream_t st) {
     const Operators &o = c.ops;
     const int Npad = o.tc_Npad;
     // split the multipoles once for all translations of this product
@@ -373,7 +373,7 @@ void launch_m2l_tc(Context &c, const XChunk *chunks, int64_t nchunks, const floa
     {
         const int64_t plane = xrows * Npad;
         const int nb = (int)std::min<int64_t>(div_up(plane, 256), 152 * 16);
-        k_split_x<<<nb, 256, 0, c.stream>>>(xrows, o.P, Npad, X, xs);
+        k_split_x<<<nb, 256, 0, st>>>(xrows, o.P, Npad, X, xs);
         BEM_LAUNCH_CHECK();
     }
     const size_t sm = tc_layout(Npad).total;
@@ -383,12 +383,14 @@ void launch_m2l_tc(Context &c, const XChunk *chunks, int64_t nchunks, const floa
                                       (int)tc_layout(256).total));
         attr_set[R == 4] = true;
     }
-    k_m2l_tc<R><<<(unsigned)nchunks, TC_THREADS, sm, c.stream>>>(
+    k_m2l_tc<R><<<(unsigned)nchunks, TC_THREADS, sm, st>>>(
         o.P, Npad, reinterpret_cast<const __nv_bfloat16 *>(o.m2l_tc.p), chunks, c.tree.m2l_src.p, xrows, xs, Ypair, err);
     BEM_LAUNCH_CHECK();
 }
 
-template void launch_m2l_tc<1>(Context &, const XChunk *, int64_t, const float *, int64_t, float *, int *);
-template void launch_m2l_tc<4>(Context &, const XChunk *, int64_t, const float *, int64_t, float *, int *);
+template void launch_m2l_tc<1>(Context &, const XChunk *, int64_t, const float *, int64_t, float *, int *,
+                               cudaStream_t);
+template void launch_m2l_tc<4>(Context &, const XChunk *, int64_t, const float *, int64_t, float *, int *,
+                               cudaStream_t);
 
 }  // namespace bem

@@ -124,8 +124,7 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_units(
     const int2 *__restrict__ units, int64_t nunits, const int32_t *__restrict__ bstart,
     const int32_t *__restrict__ bcount, const int32_t *__restrict__ nbr, const int32_t *__restrict__ ncnt,
     const int8_t *__restrict__ nd, int64_t N, const T *__restrict__ loc, const T *__restrict__ nrm,
-    const T *__restrict__ q, const T *__restrict__ w, const T *__restrict__ far, const double *__restrict__ ih,
-    double *__restrict__ out) {
+    const T *__restrict__ q, const T *__restrict__ w, double *__restrict__ out) {
     __shared__ P2PStage<T, R, HQ, HW> stage[P2P_WARPS];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t u = (int64_t)blockIdx.x * P2P_WARPS + warp;
@@ -192,7 +191,7 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_units(
         if (li < nr) {
             const int64_t i = s0 + r0 + li;
 #pragma unroll
-            for (int r = 0; r < R; ++r) out[r * N + i] = ((double)far[r * N + i] + acc[k][r].get()) * ih[i];
+            for (int r = 0; r < R; ++r) out[r * N + i] = acc[k][r].get();  // the far field is added later
         }
     }
 }
@@ -322,32 +321,34 @@ __global__ void __launch_bounds__(P2P_THREADS) k_direct32(int64_t N, const float
 }  // namespace
 
 template <class T, int R, bool HQ, bool HW>
-static void launch_units(Context &c, const T *q, const T *w, const T *far, double *out_sorted) {
+static void launch_units(Context &c, const T *q, const T *w, double *out_sorted, cudaStream_t st) {
     Tree &t = c.tree;
     const int L = t.L;
     const T *loc = sizeof(T) == 8 ? (const T *)t.loc64.p : (const T *)t.loc32.p;
     const T *nrm = sizeof(T) == 8 ? (const T *)t.nrm64.p : (const T *)t.nrm32.p;
     const int64_t nu = t.n_p2p_units;
     if (nu == 0) return;
-    k_p2p_units<T, R, HQ, HW><<<(unsigned)div_up(nu, P2P_WARPS), P2P_WARPS * 32, 0, c.stream>>>(
+    k_p2p_units<T, R, HQ, HW><<<(unsigned)div_up(nu, P2P_WARPS), P2P_WARPS * 32, 0, st>>>(
         t.p2p_units.p, nu, t.bstart.p + t.base[L], t.bcount.p + t.base[L], t.nbr.p, t.nbr_cnt.p, t.nbr_d.p, c.N, loc,
-        nrm, q, w, far, t.ih.p, out_sorted);
+        nrm, q, w, out_sorted);
     BEM_LAUNCH_CHECK();
 }
 
 template <class T, int R>
-void launch_p2p_list(Context &c, const T *q, const T *w, const T *far, double *out_sorted, bool hq, bool hw) {
-    if (R > 1 || (hq && hw)) launch_units<T, R, true, true>(c, q, w, far, out_sorted);
-    else if (hw) launch_units<T, R, false, true>(c, q, w, far, out_sorted);
-    else launch_units<T, R, true, false>(c, q, w, far, out_sorted);  // also the all-zero product
+void launch_p2p_list(Context &c, const T *q, const T *w, double *near_sorted, bool hq, bool hw, cudaStream_t st) {
+    if (R > 1 || (hq && hw)) launch_units<T, R, true, true>(c, q, w, near_sorted, st);
+    else if (hw) launch_units<T, R, false, true>(c, q, w, near_sorted, st);
+    else launch_units<T, R, true, false>(c, q, w, near_sorted, st);  // also the all-zero product
 }
 
-template void launch_p2p_list<float, 1>(Context &, const float *, const float *, const float *, double *, bool, bool);
-template void launch_p2p_list<float, 4>(Context &, const float *, const float *, const float *, double *, bool, bool);
-template void launch_p2p_list<double, 1>(Context &, const double *, const double *, const double *, double *, bool,
-                                         bool);
-template void launch_p2p_list<double, 4>(Context &, const double *, const double *, const double *, double *, bool,
-                                         bool);
+template void launch_p2p_list<float, 1>(Context &, const float *, const float *, double *, bool, bool,
+                                         cudaStream_t);
+template void launch_p2p_list<float, 4>(Context &, const float *, const float *, double *, bool, bool,
+                                         cudaStream_t);
+template void launch_p2p_list<double, 1>(Context &, const double *, const double *, double *, bool, bool,
+                                         cudaStream_t);
+template void launch_p2p_list<double, 4>(Context &, const double *, const double *, double *, bool, bool,
+                                         cudaStream_t);
 
 template <int R>
 void launch_direct(Context &c, int prec, const double *f, const double *const *xL, const double *g,
