@@ -78,6 +78,7 @@ def parse():
     ap.add_argument("--precond", type=int, default=2,
                     help="GMRES right preconditioning: 0 none (the paper), 1 Jacobi, 2 bubble blocks")
     ap.add_argument("--m2l-tc", type=int, default=1, help="1 = M2L of single-RHS products on the tensor cores")
+    ap.add_argument("--overlap", type=int, default=1, help="1 = near field on its own stream, overlapping the far field")
     ap.add_argument("--pa", type=float, default=0.5, help="acoustic amplitude Pa/p0")
     ap.add_argument("--pf", type=int, default=6, help="shape-filter bandwidth")
     ap.add_argument("--fp64-compare", type=int, default=1, help="also time FP64 right-hand sides (0 = skip)")
@@ -262,10 +263,12 @@ def run_ours(args):
     toff = torch.from_numpy(np.ascontiguousarray(mesh.tri_off, np.int64)).to(dev)
     phid = torch.from_numpy(np.ascontiguousarray(phi)).to(dev)
 
-    def make_ctx(precision):
+    def make_ctx(precision, overlap=None, fixed_level=None):
+        overlap = args.overlap if overlap is None else overlap
         c = bem.BemContext(stream=stream, p_fmm=args.p, precision=precision, leaf_target=args.leaf,
-                           fixed_level=args.tree_level, gmres_tol=args.tol, gmres_maxit=args.maxit,
-                           gmres_restart=args.restart, gmres_precond=args.precond, m2l_tensor_cores=args.m2l_tc)
+                           fixed_level=args.tree_level if fixed_level is None else fixed_level, gmres_tol=args.tol,
+                           gmres_maxit=args.maxit, gmres_restart=args.restart, gmres_precond=args.precond,
+                           m2l_tensor_cores=args.m2l_tc, overlap=overlap)
         return c
 
     progress("workload ready: %d unknowns, %d bubbles" % (N, mesh.m))
@@ -322,6 +325,25 @@ def run_ours(args):
     mvp_ms = a0.elapsed_time(a1) / args.mvp_reps
     st = ctx.stats()
 
+    # per-kernel timings for the rooflines: in the step the near field overlaps the far field on
+    # two streams, so each kernel's own duration is taken from single-layer products of the same
+    # geometry and depth on a context that runs the phases one after another
+    xs_now = torch.empty(3 * N, dtype=torch.float64, device=dev)
+    bem.bem_step_get_state(ctx.ctx, xs_now, None, None)
+    ctx_iso = make_ctx(prec, overlap=0, fixed_level=st["levels"])
+    ctx_iso.upload(xs_now.view(3, N), tri, voff, toff)
+    ctx_iso.build()
+    for _ in range(2):
+        ctx_iso.apply(1.0, q, 0.0, None, out)
+    torch.cuda.synchronize()
+    bem.bem_profile_enable(ctx_iso.ctx, True)
+    for _ in range(args.mvp_reps):
+        ctx_iso.apply(1.0, q, 0.0, None, out)
+    iso = bem.bem_profile_read(ctx_iso.ctx)
+    st_iso = ctx_iso.stats()
+    ctx_iso.close()
+    del xs_now
+
     # end to end through the C ABI: each step driven from the host and its result (r, phi, q)
     # read back into pinned host memory
     xyz_h = torch.empty(3 * N, dtype=torch.float64).pin_memory()
@@ -354,35 +376,39 @@ def run_ours(args):
     launches = {k: prof[k][1] / args.steps for k in ("p2p", "m2l")}
 
     def p2p_roofline():
-        if per_step.get("p2p", 0) <= 0:
+        ms_i, n_i = iso.get("p2p", (0.0, 0))
+        if n_i <= 0 or ms_i <= 0:
             return None
-        nl = max(1.0, launches["p2p"])
-        t_launch = per_step["p2p"] / 1e3 / nl
-        achieved = work["p2p"] / nl / t_launch / 1e12
+        t_launch = ms_i / 1e3 / n_i
+        achieved = P2P_FLOPS_SL * st_iso["p2p_pairs"] / t_launch / 1e12
         peak = FP32_ALU_PEAK_TFLOPS if prec == bem.BEM_PREC_MIXED else None
-        return {"kernel": "k_p2p_units (near field)", "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": (achieved / peak) if peak else None, "traffic": None,
+        return {"kernel": "k_p2p_units (near field, single layer)", "bound": "alu", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if peak else None, "traffic": None,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (max SM clock)",
-                "launch_ms": t_launch * 1e3, "launches_per_step": nl,
-                "work_per_launch": "11 (single layer) / 19 (double layer) / 33 (both, 4 RHS) flops x near-field pairs"}
+                "launch_ms": t_launch * 1e3, "launches_timed": n_i,
+                "launch_ms_in_step": per_step.get("p2p", 0) / max(1.0, launches["p2p"]),
+                "work_per_launch": "11 flops x %d near-field pairs" % st_iso["p2p_pairs"],
+                "timing": "single-layer products on the step's geometry, phases run one after another"}
 
     def m2l_roofline():
-        # tensor-core translations of the single-RHS products (the phase also holds the split of
-        # the multipoles into BF16 pieces), against the measured sustained BF16 peak
-        if not (prec == bem.BEM_PREC_MIXED and args.m2l_tc and per_step.get("m2l", 0) > 0):
+        # tensor-core translations (with the split of the multipoles into BF16 pieces) against
+        # the measured sustained BF16 peak
+        ms_i, n_i = iso.get("m2l", (0.0, 0))
+        if not (prec == bem.BEM_PREC_MIXED and args.m2l_tc and n_i > 0 and ms_i > 0):
             return None
-        nl = max(1.0, launches["m2l"])
-        t_launch = per_step["m2l"] / 1e3 / nl
-        achieved = M2L_TC_PRODUCTS * 2.0 * P * P * st["m2l_pairs"] / t_launch / 1e12
+        t_launch = ms_i / 1e3 / n_i
+        achieved = M2L_TC_PRODUCTS * 2.0 * P * P * st_iso["m2l_pairs"] / t_launch / 1e12
         pk = PEAKS.get("bf16_tflops_sustained")
         return {"kernel": "k_m2l_tc (M2L)", "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
                 "frac": achieved / pk if pk else None, "traffic": None,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS, long loop)",
-                "launch_ms": t_launch * 1e3, "launches_per_step": nl,
-                "work_per_launch": "6 BF16 products x 2 P^2 flops x M2L translations"}
+                "launch_ms": t_launch * 1e3, "launches_timed": n_i,
+                "launch_ms_in_step": per_step.get("m2l", 0) / max(1.0, launches["m2l"]),
+                "work_per_launch": "6 BF16 products x 2 P^2 flops x %d M2L translations" % st_iso["m2l_pairs"],
+                "timing": "single-layer products on the step's geometry, phases run one after another"}
 
     roof_p2p, roof_m2l = p2p_roofline(), m2l_roofline()
-    dom = "m2l" if roof_m2l and per_step.get("m2l", 0) > per_step.get("p2p", 0) else "p2p"
+    dom = "m2l" if roof_m2l and iso.get("m2l", (0, 0))[0] > iso.get("p2p", (0, 0))[0] else "p2p"
     roof = roof_m2l if dom == "m2l" else roof_p2p
 
     line = {
@@ -392,7 +418,7 @@ def run_ours(args):
         "dtype": "f32+f64" if prec == bem.BEM_PREC_MIXED else "f64", "data": "synthetic",
         "config": {"workload": workload_name(args, mesh), "p_fmm": args.p, "precision": args.precision,
                    "leaf_target": args.leaf, "gmres_tol": args.tol, "gmres_precond": args.precond,
-                   "m2l_tensor_cores": args.m2l_tc,
+                   "m2l_tensor_cores": args.m2l_tc, "overlap": args.overlap,
                    "scheme": ("AB6 (steps after the 5 RK4 start steps)" if rhs / args.steps < 2 else
                               "RK4 start steps (the paper's AB6 begins after 5)"),
                    "pa": args.pa, "pf": args.pf, "dt": infos[-1]["dt"], "levels": st["levels"],
@@ -405,6 +431,8 @@ def run_ours(args):
         "mvp": {"ms": mvp_ms, "gpairs_per_s_dense_equiv": N ** 2 / (mvp_ms / 1e3) / 1e9,
                 "p2p_pairs": st["p2p_pairs"], "m2l_pairs": st["m2l_pairs"]},
         "phases_ms_per_step": {k: round(v, 3) for k, v in per_step.items() if v > 0},
+        "phases_note": "per-stream device time; the near field (p2p) overlaps the far field",
+        "kernel_ms_per_product": {k: round(v[0] / max(1, v[1]), 4) for k, v in iso.items() if v[1] > 0},
         "roofline": roof,
         "roofline_p2p": roof_p2p,
         "roofline_m2l": roof_m2l,

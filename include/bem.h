@@ -87,7 +87,10 @@ typedef struct {
                                3.21M-unknown cluster at p_fmm = 14 the off-diagonal part of a
                                product is within 6e-7 of the direct sum, L_ii within 4e-5).
                                Default -1.                                                     */
-    int32_t reserved;       /* 0                                                               */
+    int32_t overlap;        /* 1: within a product, the near field runs on its own stream,
+                               concurrently with the far field; 0: one stream, phase after
+                               phase (the per-kernel timings of a profile then do not
+                               overlap). Same results either way. Default 1.                  */
     int32_t m2l_tensor_cores; /* 1: mixed-precision single-RHS products (every GMRES product)
                                run M2L on the tensor cores (three-piece BF16 split, FP32
                                accumulation) when p_fmm^2 is a multiple of 4 and <= 256;

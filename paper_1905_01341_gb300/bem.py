@@ -53,7 +53,7 @@ class bem_params(ctypes.Structure):
         ("mvp", ctypes.c_int32),
         ("diag_precision", ctypes.c_int32),
         ("diag_p_fmm", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("overlap", ctypes.c_int32),
         ("m2l_tensor_cores", ctypes.c_int32),
         ("gmres_precond", ctypes.c_int32),
         ("gmres_maxit", ctypes.c_int32),
@@ -90,7 +90,7 @@ class bem_step_params(ctypes.Structure):
         ("courant", ctypes.c_double),
         ("dt", ctypes.c_double),
         ("pf", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("overlap", ctypes.c_int32),
     ]
 
 
@@ -113,7 +113,7 @@ class bem_step_stats(ctypes.Structure):
 class bem_mlp_summary(ctypes.Structure):
     _fields_ = [
         ("dims", ctypes.c_int32 * 5),
-        ("reserved", ctypes.c_int32),
+        ("overlap", ctypes.c_int32),
         ("num_params", ctypes.c_int64),
         ("samples", ctypes.c_int64),
         ("compared_solves", ctypes.c_int64),

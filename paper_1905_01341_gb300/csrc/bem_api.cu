@@ -163,6 +163,7 @@ void check_params(const bem_params &p) {
         fail(BEM_ERR_ARG, "bad diag_precision");
     if (p.diag_p_fmm != -1 && (p.diag_p_fmm < 2 || p.diag_p_fmm > kMaxPfmm))
         fail(BEM_ERR_ARG, "diag_p_fmm must be -1 or in 2..20");
+    if (p.overlap != 0 && p.overlap != 1) fail(BEM_ERR_ARG, "overlap must be 0 or 1");
     if (p.mvp != BEM_MVP_FMM && p.mvp != BEM_MVP_DIRECT) fail(BEM_ERR_ARG, "bad mvp kind");
     if (p.m2l_tensor_cores != 0 && p.m2l_tensor_cores != 1) fail(BEM_ERR_ARG, "m2l_tensor_cores must be 0 or 1");
     if (p.gmres_maxit < 1 || p.gmres_restart < 0 || p.gmres_restart > 127) fail(BEM_ERR_ARG, "bad GMRES limits");
@@ -373,7 +374,7 @@ int bem_params_default(bem_params *p) {
     p->mvp = BEM_MVP_FMM;
     p->diag_precision = -1;
     p->diag_p_fmm = -1;
-    p->reserved = 0;
+    p->overlap = 1;
     p->m2l_tensor_cores = 1;
     p->gmres_precond = 0;
     p->gmres_maxit = 100;

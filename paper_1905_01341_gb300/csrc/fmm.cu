@@ -703,22 +703,24 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
         BEM_CUDA(cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming));
         BEM_CUDA(cudaEventCreateWithFlags(&c.ev_far, cudaEventDisableTiming));
     }
+    const bool ovl = c.prm.overlap != 0;
+    cudaStream_t ns = ovl ? c.side : st;  // near-field stream
     BEM_CUDA(cudaEventRecord(c.ev_fork, st));
-    BEM_CUDA(cudaStreamWaitEvent(c.side, c.ev_fork, 0));
+    if (ovl) BEM_CUDA(cudaStreamWaitEvent(ns, c.ev_fork, 0));
     {
-        PhaseScope ps(c, PH_P2P, c.side);
+        PhaseScope ps(c, PH_P2P, ns);
         bool hq = false, hw = false;
         for (int r = 0; r < R; ++r) {
             hq = hq || a.f[r] != 0.0;
             hw = hw || a.g[r] != 0.0;
         }
-        launch_p2p_list<T, R>(c, q, w, c.near_out.p, hq, hw, c.side);
+        launch_p2p_list<T, R>(c, q, w, c.near_out.p, hq, hw, ns);
     }
-    BEM_CUDA(cudaEventRecord(c.ev_join, c.side));
+    BEM_CUDA(cudaEventRecord(c.ev_join, ns));
     // the far field runs on a high-priority stream, so its blocks (the tensor-core M2L's in
     // particular) are placed as soon as an SM has room and the near field fills the rest
-    cudaStream_t fs = c.hi;
-    BEM_CUDA(cudaStreamWaitEvent(fs, c.ev_fork, 0));
+    cudaStream_t fs = ovl ? c.hi : st;
+    if (ovl) BEM_CUDA(cudaStreamWaitEvent(fs, c.ev_fork, 0));
 
     // chunk tables for this R (built once per build)
     const int per = XT_COLS / R;
@@ -849,8 +851,10 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
     }
     BEM_CUDA(cudaEventRecord(c.ev_far, fs));
     // join the near field, add the far field, scale by 1/h and return to the caller's order
-    BEM_CUDA(cudaStreamWaitEvent(st, c.ev_far, 0));
-    BEM_CUDA(cudaStreamWaitEvent(st, c.ev_join, 0));
+    if (ovl) {
+        BEM_CUDA(cudaStreamWaitEvent(st, c.ev_far, 0));
+        BEM_CUDA(cudaStreamWaitEvent(st, c.ev_join, 0));
+    }
     RhsArgs<kMaxRhs> o{};
     for (int r = 0; r < R; ++r) o.out[r] = a.out[r];
     k_combine_out<T><<<div_up(N, tb), tb, 0, st>>>(N, R, t.perm.p, far, c.near_out.p, t.ih.p, o);

@@ -67,6 +67,7 @@ def test_struct_layouts_match_header():
     # int32 x 10 + double = 48 bytes; stats: 4 x int64 + 4 x int32 + 2 x double + int64 = 72
     assert ctypes.sizeof(bem.bem_params) == 56
     assert bem.bem_params_default().gmres_precond == 0
+    assert bem.bem_params_default().overlap == 1 and bem.bem_params_default().diag_p_fmm == -1
     assert ctypes.sizeof(bem.bem_stats) == 72
     assert ctypes.sizeof(bem.bem_step_params) == 56 and ctypes.sizeof(bem.bem_step_stats) == 48
     assert ctypes.sizeof(bem.bem_mlp_summary) == 80
