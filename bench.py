@@ -53,6 +53,12 @@ def _load_peaks() -> dict:
 PEAKS = _load_peaks()
 # Tensor-core M2L: six BF16 products per translation (three-piece split of both operands).
 M2L_TC_PRODUCTS = 6
+# DRAM traffic per unit from the ncu captures of the 300-bubble cluster (profiles/), scaled to a
+# full launch by the units it processes: the near field reads each point's data about once
+# (3.65 MB for 192,600 points), the M2L reads gathered multipoles and writes one product row per
+# translation (86.6 MB + 134.2 MB for 241,298 translations).
+P2P_DRAM_BYTES_PER_POINT = 3.648e6 / 192600
+M2L_DRAM_BYTES_PER_TRANSLATION = (86.56e6 + 134.19e6) / 241298
 
 
 def parse():
@@ -383,7 +389,9 @@ def run_ours(args):
         achieved = P2P_FLOPS_SL * st_iso["p2p_pairs"] / t_launch / 1e12
         peak = FP32_ALU_PEAK_TFLOPS if prec == bem.BEM_PREC_MIXED else None
         return {"kernel": "k_p2p_units (near field, single layer)", "bound": "alu", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if peak else None, "traffic": None,
+                "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if peak else None,
+                "traffic": P2P_DRAM_BYTES_PER_POINT * N if prec == bem.BEM_PREC_MIXED else None,
+                "traffic_source": "ncu capture of the 300-bubble cluster, bytes per point x N",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (max SM clock)",
                 "launch_ms": t_launch * 1e3, "launches_timed": n_i,
                 "launch_ms_in_step": per_step.get("p2p", 0) / max(1.0, launches["p2p"]),
@@ -400,7 +408,9 @@ def run_ours(args):
         achieved = M2L_TC_PRODUCTS * 2.0 * P * P * st_iso["m2l_pairs"] / t_launch / 1e12
         pk = PEAKS.get("bf16_tflops_sustained")
         return {"kernel": "k_m2l_tc (M2L)", "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
-                "frac": achieved / pk if pk else None, "traffic": None,
+                "frac": achieved / pk if pk else None,
+                "traffic": M2L_DRAM_BYTES_PER_TRANSLATION * st_iso["m2l_pairs"],
+                "traffic_source": "ncu capture of the 300-bubble cluster, bytes per translation x translations",
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS, long loop)",
                 "launch_ms": t_launch * 1e3, "launches_timed": n_i,
                 "launch_ms_in_step": per_step.get("m2l", 0) / max(1.0, launches["m2l"]),
