@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(256) k_p2m(int p, int nleaf, const int32_t *__
 // ------------------------------------------------------------------------------ translations
 // Class-grouped product: for every pair (src, tgt) of a chunk, Y[tgt] += T_cls X[src], as a
 // tiled GEMM (64 output rows x 64 columns per block; a column is one pair and one RHS).
-constexpr int XT_COLS = 64, XT_K = 16, XT_THREADS = 256;
+constexpr int XT_K = 16, XT_THREADS = 256;
 
 // MODE kStorePair: Y[pair] = T X[src] (one slot per pair, summed later in a fixed order).
 // MODE kAddTarget: Y[tgt] += T X[src]; only for launches whose targets are all distinct.
@@ -416,46 +416,49 @@ __device__ __forceinline__ void vec4_load(const double *p, double *v) {
     v[3] = t1.y;
 }
 
-// rows per thread and per block: 8 x 4 outputs per thread in FP32 (a 128-row tile), 4 x 4 in
-// FP64 (64 rows, keeping the double-buffered tiles under the static shared-memory limit)
+// outputs per thread and block: 8 x 8 per thread in FP32 (a 128 x 128 tile: 16 FMAs per shared
+// load, and each operator tile serves 128 (pair, rhs) columns), 4 x 4 in FP64 (64 x 64, keeping
+// the double-buffered tiles under the static shared-memory limit)
 template <class T>
 __host__ __device__ constexpr int xt_rt() { return sizeof(T) == 4 ? 8 : 4; }
 template <class T>
 __host__ __device__ constexpr int xt_rows() { return 16 * xt_rt<T>(); }
+template <class T>
+__host__ __device__ constexpr int xt_cols() { return 16 * xt_rt<T>(); }
 
 template <class T, int R, int MODE>
-__global__ void __launch_bounds__(XT_THREADS) k_xlat(const T *__restrict__ mats, int P, const XChunk *__restrict__ chunks,
+__global__ void __launch_bounds__(XT_THREADS, 2) k_xlat(const T *__restrict__ mats, int P, const XChunk *__restrict__ chunks,
                                                      const int32_t *__restrict__ srcs, const int32_t *__restrict__ tgts,
                                                      const T *X, T *Y) {  // X and Y may be one array (M2M, L2L)
-    constexpr int RT = xt_rt<T>(), ROWS = xt_rows<T>();
+    constexpr int RT = xt_rt<T>(), CT = RT, ROWS = xt_rows<T>(), COLS = xt_cols<T>();
     // two shared-memory buffers: the next K tile's global loads are in flight (in registers)
     // while the current tile is multiplied
     __shared__ __align__(16) T As[2][XT_K][ROWS + 4];  // row pitch a multiple of 16 bytes
-    __shared__ __align__(16) T Bs[2][XT_K][XT_COLS + 4];
-    __shared__ int s_src[XT_COLS], s_tgt[XT_COLS];
+    __shared__ __align__(16) T Bs[2][XT_K][COLS + 4];
+    __shared__ int s_src[COLS], s_tgt[COLS];
     const XChunk ch = chunks[blockIdx.x];
     const int row0 = blockIdx.y * ROWS;
     const T *A = mats + (size_t)ch.cls * P * P;
     const int ncol = ch.count * R;
     int tid = threadIdx.x;
-    if (tid < XT_COLS) {
-        int pr = tid / R;
+    for (int e = tid; e < COLS; e += XT_THREADS) {
+        int pr = e / R;
         if (pr < ch.count) {
-            s_src[tid] = srcs[ch.start + pr];
-            s_tgt[tid] = tgts[ch.start + pr];
+            s_src[e] = srcs[ch.start + pr];
+            s_tgt[e] = tgts[ch.start + pr];
         } else {
-            s_src[tid] = -1;
-            s_tgt[tid] = -1;
+            s_src[e] = -1;
+            s_tgt[e] = -1;
         }
     }
     __syncthreads();
-    const int tx = tid % 16, ty = tid / 16;  // columns tx*4.., rows ty*RT..
-    T acc[RT][4];
+    const int tx = tid % 16, ty = tid / 16;  // columns tx*CT.., rows ty*RT..
+    T acc[RT][CT];
 #pragma unroll
     for (int i = 0; i < RT; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
-    constexpr int NA = (ROWS * XT_K) / XT_THREADS, NB = (XT_COLS * XT_K) / XT_THREADS;
+        for (int j = 0; j < CT; ++j) acc[i][j] = (T)0;
+    constexpr int NA = (ROWS * XT_K) / XT_THREADS, NB = (COLS * XT_K) / XT_THREADS;
     T ra[NA], rb[NB];
     auto gload = [&](int k0) {
 #pragma unroll
@@ -492,26 +495,27 @@ __global__ void __launch_bounds__(XT_THREADS) k_xlat(const T *__restrict__ mats,
     for (int t = 0; t < nk; ++t) {
         const int buf = t & 1;
         if (t + 1 < nk) gload((t + 1) * XT_K);
-        if (row0 + ty * RT < P) {  // rows past P (the last row tile) skip the products
+        if (row0 + ty * RT < P && tx * CT < ncol) {  // rows past P and empty columns skip the products
 #pragma unroll
             for (int kk = 0; kk < XT_K; ++kk) {
                 // consecutive rows / columns per thread through 16-byte shared-memory loads
-                T a[RT], bv[4];
+                T a[RT], bv[CT];
 #pragma unroll
                 for (int i = 0; i < RT; i += 4) vec4_load(&As[buf][kk][ty * RT + i], a + i);
-                vec4_load(&Bs[buf][kk][tx * 4], bv);
+#pragma unroll
+                for (int j = 0; j < CT; j += 4) vec4_load(&Bs[buf][kk][tx * CT + j], bv + j);
 #pragma unroll
                 for (int i = 0; i < RT; ++i)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bv[j];
+                    for (int j = 0; j < CT; ++j) acc[i][j] += a[i] * bv[j];
             }
         }
         if (t + 1 < nk) sstore(buf ^ 1);  // that buffer was last read before the previous barrier
         __syncthreads();
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        int col = tx * 4 + j;
+    for (int j = 0; j < CT; ++j) {
+        int col = tx * CT + j;
         if (col >= ncol) continue;
         int r = col % R;
         T *yb = (MODE == kStorePair) ? Y + ((size_t)(ch.start + col / R) * R + r) * P
@@ -723,7 +727,7 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
     if (ovl) BEM_CUDA(cudaStreamWaitEvent(fs, c.ev_fork, 0));
 
     // chunk tables for this R (built once per build)
-    const int per = XT_COLS / R;
+    const int per = xt_cols<T>() / R;
     auto &mch = c.m2l_chunks_h;
     if (mch.empty() || mch.front().cls != -R) {
         std::vector<XChunk> all;

@@ -36,7 +36,7 @@ constexpr int TC_M = 128;        // rows per tile
 constexpr int TC_TILES = 2;      // tiles per block (same class, shared B stages)
 constexpr int TC_K = 16;         // K per stage (one kind::f16 MMA)
 constexpr int TC_STAGES = 4;
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 256;  // 8 warps: two warp groups share the loads and the epilogue
 constexpr uint32_t TC_LBO = 128;  // bytes between K-adjacent core matrices
 constexpr uint32_t TC_SBO = 256;  // bytes between 8-row groups
 constexpr long long kWaitLimit = 1ll << 20;  // iterations before a wait gives up
@@ -309,10 +309,14 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
         float *stage = reinterpret_cast<float *>(smem);  // the operand stages are free now
         for (int t = 0; t < ntiles; ++t) {
             const int rows_t = min(TC_M, nrows - t * TC_M);
-            float *srow = stage + (size_t)(warp * 32 + lane) * P;
-            for (int c0 = 0; c0 < Npad; c0 += 16) {
+            // a warp reads its own quarter of the TMEM lanes (warp % 4); the two warp groups take
+            // the lower and the upper half of the 16-column groups
+            const int q4 = warp & 3, half = warp >> 2;
+            const int ngroups = Npad / 16, g0 = half ? (ngroups + 1) / 2 : 0, g1 = half ? ngroups : (ngroups + 1) / 2;
+            float *srow = stage + (size_t)(q4 * 32 + lane) * P;
+            for (int c0 = g0 * 16; c0 < g1 * 16; c0 += 16) {
                 uint32_t v[16];
-                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * 256 + c0);
+                const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(t * 256 + c0);
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
                     "[%16];"
