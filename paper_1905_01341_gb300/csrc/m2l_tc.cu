@@ -35,7 +35,7 @@ namespace {
 constexpr int TC_M = 128;        // rows per tile
 constexpr int TC_TILES = 2;      // tiles per block (same class, shared B stages)
 constexpr int TC_K = 16;         // K per stage (one kind::f16 MMA)
-constexpr int TC_STAGES = 4;
+constexpr int TC_MAX_SMEM = 225 * 1024;  // dynamic shared memory per block (227 KB less the static part)
 constexpr int TC_THREADS = 256;  // 8 warps: two warp groups share the loads and the epilogue
 constexpr uint32_t TC_LBO = 128;  // bytes between K-adjacent core matrices
 constexpr uint32_t TC_SBO = 256;  // bytes between 8-row groups
@@ -164,18 +164,19 @@ struct TcLayout {
     size_t a_bytes, b_bytes, stage_bytes, total;
 };
 
-__host__ __device__ inline TcLayout tc_layout(int Npad) {
+// ST pipeline stages; the epilogue reuses the stages for one tile of FP32 rows (at most N_pad
+// floats each)
+__host__ __device__ inline TcLayout tc_layout(int Npad, int ST) {
     TcLayout L;
     L.a_bytes = (size_t)3 * TC_TILES * TC_M * TC_K * 2;
     L.b_bytes = (size_t)3 * Npad * TC_K * 2;
     L.stage_bytes = L.a_bytes + L.b_bytes;
-    // the epilogue reuses the stages for one tile of FP32 rows (at most N_pad floats each)
     const size_t epi = (size_t)TC_M * Npad * 4;
-    L.total = (TC_STAGES * L.stage_bytes > epi ? TC_STAGES * L.stage_bytes : epi) + TC_STAGES * 8 + 16 + 1024;
+    L.total = (ST * L.stage_bytes > epi ? ST * L.stage_bytes : epi) + ST * 8 + 16 + 1024;
     return L;
 }
 
-template <int R>
+template <int R, int TC_STAGES>
 __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __nv_bfloat16 *__restrict__ tcB,
                                                        const XChunk *__restrict__ chunks,
                                                        const int32_t *__restrict__ srcs, int64_t xrows,
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned base for the operand stages
     unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    const TcLayout Lo = tc_layout(Npad);
+    const TcLayout Lo = tc_layout(Npad, TC_STAGES);
     const size_t epi_bytes = (size_t)TC_M * Npad * 4;
     uint64_t *empty = reinterpret_cast<uint64_t *>(
         smem + (TC_STAGES * Lo.stage_bytes > epi_bytes ? TC_STAGES * Lo.stage_bytes : epi_bytes));
@@ -380,15 +381,14 @@ void launch_m2l_tc(Context &c, const XChunk *chunks, int64_t nchunks, const floa
         k_split_x<<<nb, 256, 0, st>>>(xrows, o.P, Npad, X, xs);
         BEM_LAUNCH_CHECK();
     }
-    const size_t sm = tc_layout(Npad).total;
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[R == 4]) {  // once, for the largest tile (N_pad = 256)
-        BEM_CUDA(cudaFuncSetAttribute(k_m2l_tc<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)tc_layout(256).total));
-        attr_set[R == 4] = true;
-    }
-    k_m2l_tc<R><<<(unsigned)nchunks, TC_THREADS, sm, st>>>(
-        o.P, Npad, reinterpret_cast<const __nv_bfloat16 *>(o.m2l_tc.p), chunks, c.tree.m2l_src.p, xrows, xs, Ypair, err);
+    // five stages (the copies of a step start four steps ahead) where they fit, else four
+    const bool five = tc_layout(Npad, 5).total <= (size_t)TC_MAX_SMEM;
+    const size_t sm = tc_layout(Npad, five ? 5 : 4).total;
+    auto kern = five ? k_m2l_tc<R, 5> : k_m2l_tc<R, 4>;
+    // set on every launch: the attribute belongs to the current device (~1 us against a ms kernel)
+    BEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_MAX_SMEM));
+    kern<<<(unsigned)nchunks, TC_THREADS, sm, st>>>(o.P, Npad, reinterpret_cast<const __nv_bfloat16 *>(o.m2l_tc.p),
+                                                   chunks, c.tree.m2l_src.p, xrows, xs, Ypair, err);
     BEM_LAUNCH_CHECK();
 }
 
