@@ -90,7 +90,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
@@ -172,7 +171,7 @@ __host__ __device__ inline TcLayout tc_layout(int Npad, int ST) {
     L.b_bytes = (size_t)3 * Npad * TC_K * 2;
     L.stage_bytes = L.a_bytes + L.b_bytes;
     const size_t epi = (size_t)TC_M * Npad * 4;
-    L.total = (ST * L.stage_bytes > epi ? ST * L.stage_bytes : epi) + ST * 8 + 16 + 1024;
+    L.total = (ST * L.stage_bytes > epi ? ST * L.stage_bytes : epi) + 2 * ST * 8 + 16 + 1024;
     return L;
 }
 
@@ -189,7 +188,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
     const size_t epi_bytes = (size_t)TC_M * Npad * 4;
     uint64_t *empty = reinterpret_cast<uint64_t *>(
         smem + (TC_STAGES * Lo.stage_bytes > epi_bytes ? TC_STAGES * Lo.stage_bytes : epi_bytes));
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(empty + TC_STAGES);
+    uint64_t *full = empty + TC_STAGES;  // NPROD producer arrivals per use
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(full + TC_STAGES);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    constexpr int NPROD = TC_THREADS - 32;  // warps 1.. fill the stages, warp 0 issues the MMAs
     __shared__ int s_src[TC_TILES * TC_M];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -201,8 +203,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
     const int nsteps = Npad / TC_K;
     for (int r = tid; r < TC_TILES * TC_M; r += TC_THREADS) s_src[r] = (r < nrows) ? srcs[ch.start + r / R] : -1;
     if (tid == 0) {
-        for (int s = 0; s < TC_STAGES; ++s)
+        for (int s = 0; s < TC_STAGES; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[s])), "r"(NPROD));
+        }
+        *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (warp == 0) {
@@ -223,11 +228,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
     const uint32_t bpiece = (uint32_t)Npad * TC_K * 2;
 
     // fill stage `st` with K step `ks`
-    auto load_stage = [&](int ks, int st) {
+    auto load_stage = [&](int ks, int st, int pt) {
         const uint32_t sa = sbase + st * (uint32_t)Lo.stage_bytes;
         const uint32_t sb = sa + (uint32_t)Lo.a_bytes;
         // A: u -> (piece, tile row, j); 16 bytes = 8 consecutive k of one row
-        for (int u = tid; u < 3 * TC_TILES * TC_M * 2; u += TC_THREADS) {
+        for (int u = pt; u < 3 * TC_TILES * TC_M * 2; u += NPROD) {
             const int j = u & 1;
             const int row2 = (u >> 1) % (TC_TILES * TC_M), piece = (u >> 1) / (TC_TILES * TC_M);
             const int t = row2 / TC_M, row = row2 % TC_M;
@@ -240,67 +245,67 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
         }
         // B: contiguous pre-tiled block of the three pieces
         const unsigned char *bsrc = reinterpret_cast<const unsigned char *>(Bc + (size_t)ks * 3 * Npad * TC_K);
-        for (int u = tid; u < (int)(Lo.b_bytes / 16); u += TC_THREADS) cp_async16(sb + u * 16, bsrc + (size_t)u * 16, 16u);
+        for (int u = pt; u < (int)(Lo.b_bytes / 16); u += NPROD) cp_async16(sb + u * 16, bsrc + (size_t)u * 16, 16u);
     };
 
-#pragma unroll 1
-    for (int s = 0; s < TC_STAGES - 1; ++s) {
-        if (s < nsteps) load_stage(s, s);
-        cp_async_commit();
-    }
-    bool ok = true;
-    int last_stage = 0;
-    uint32_t last_parity = 0;
-#pragma unroll 1
-    for (int ks = 0; ks < nsteps; ++ks) {
-        const int st = ks % TC_STAGES;
-        cp_async_wait<TC_STAGES - 2>();  // this thread's copies of step ks have landed
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t sa = sbase + st * (uint32_t)Lo.stage_bytes;
-            const uint32_t sb = sa + (uint32_t)Lo.a_bytes;
-            for (int t = 0; t < ntiles; ++t) {
-                const uint32_t d = tmem + (uint32_t)(t * 256);
-                const uint32_t a0 = sa + t * atile;
-                // smallest terms first: (2,0) (1,1) (0,2) (1,0) (0,1) (0,0)
-                mma_bf16(d, make_desc(a0 + 2 * apiece), make_desc(sb), idesc, ks > 0 ? 1u : 0u);
-                mma_bf16(d, make_desc(a0 + apiece), make_desc(sb + bpiece), idesc, 1u);
-                mma_bf16(d, make_desc(a0), make_desc(sb + 2 * bpiece), idesc, 1u);
-                mma_bf16(d, make_desc(a0 + apiece), make_desc(sb), idesc, 1u);
-                mma_bf16(d, make_desc(a0), make_desc(sb + bpiece), idesc, 1u);
-                mma_bf16(d, make_desc(a0), make_desc(sb), idesc, 1u);
-            }
-            mma_commit(smem_u32(&empty[st]));
-        }
-        __syncwarp();
-        last_stage = st;
-        last_parity = (uint32_t)((ks / TC_STAGES) & 1);
-        // refill the stage read by step ks - 1 with step ks + STAGES - 1, once those MMAs are done
-        const int nk = ks + TC_STAGES - 1;
-        if (nk < nsteps) {
-            if (ks >= 1) {
-                const int ps = (ks - 1) % TC_STAGES;
-                const uint32_t pp = (uint32_t)(((ks - 1) / TC_STAGES) & 1);
-                const int bad = __syncthreads_or(mbar_wait(smem_u32(&empty[ps]), pp) ? 0 : 1);
-                if (bad) {
-                    ok = false;
+    // Warp-specialised pipeline. Producers (warps 1..) wait until the MMAs that last read a stage
+    // are done (its empty barrier), copy their share of the next K step into it and let the
+    // stage's full barrier count their arrival once those copies have landed
+    // (cp.async.mbarrier.arrive.noinc). One thread of warp 0 waits for full, makes the copies
+    // visible to the tensor core (proxy fence), issues the step's MMAs and commits them to empty.
+    // No block-wide barrier inside the loop; every wait is bounded and a timeout raises the shared
+    // abort flag, which stops the other side at its next wait.
+    __shared__ int s_last_ks;
+    if (warp == 0) {
+        if (lane == 0) {
+            int ks = 0;
+            for (; ks < nsteps; ++ks) {
+                const int st = ks % TC_STAGES;
+                if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((ks / TC_STAGES) & 1)) || *abort_flag) {
+                    *abort_flag = 1;
                     break;
                 }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t sa = sbase + st * (uint32_t)Lo.stage_bytes;
+                const uint32_t sb = sa + (uint32_t)Lo.a_bytes;
+                for (int t = 0; t < ntiles; ++t) {
+                    const uint32_t d = tmem + (uint32_t)(t * 256);
+                    const uint32_t a0 = sa + t * atile;
+                    // smallest terms first: (2,0) (1,1) (0,2) (1,0) (0,1) (0,0)
+                    mma_bf16(d, make_desc(a0 + 2 * apiece), make_desc(sb), idesc, ks > 0 ? 1u : 0u);
+                    mma_bf16(d, make_desc(a0 + apiece), make_desc(sb + bpiece), idesc, 1u);
+                    mma_bf16(d, make_desc(a0), make_desc(sb + 2 * bpiece), idesc, 1u);
+                    mma_bf16(d, make_desc(a0 + apiece), make_desc(sb), idesc, 1u);
+                    mma_bf16(d, make_desc(a0), make_desc(sb + bpiece), idesc, 1u);
+                    mma_bf16(d, make_desc(a0), make_desc(sb), idesc, 1u);
+                }
+                mma_commit(smem_u32(&empty[st]));
             }
-            load_stage(nk, nk % TC_STAGES);
+            s_last_ks = ks - 1;  // last committed step (-1: none)
         }
-        cp_async_commit();
+        __syncwarp();
+    } else {
+        const int pt = tid - 32;
+        for (int ks = 0; ks < nsteps; ++ks) {
+            const int st = ks % TC_STAGES;
+            // the stage's previous use (step ks - ST) must be consumed: completion ks / ST - 1
+            if (ks >= TC_STAGES &&
+                (!mbar_wait(smem_u32(&empty[st]), (uint32_t)((ks / TC_STAGES - 1) & 1)) || *abort_flag)) {
+                *abort_flag = 1;
+                break;
+            }
+            load_stage(ks, st, pt);
+            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&full[st])) : "memory");
+        }
+        cp_async_wait<0>();  // nothing of this thread in flight past this point
     }
-    cp_async_wait<0>();
-    // every MMA of this block is tracked by its last commit
-    const int done = __syncthreads_and(mbar_wait(smem_u32(&empty[last_stage]), last_parity) ? 1 : 0);
-    if (!ok || !done) {
-        mbar_wait(smem_u32(&empty[last_stage]), last_parity);  // one more bounded wait before freeing TMEM
-        if (tid == 0) atomicOr(err, 1);
-        ok = false;
-    }
+    __syncthreads();
+    // tcgen05.commit tracks every earlier MMA of the issuing thread: the last commit covers all
+    const int lk = s_last_ks;
+    const bool done = lk >= 0 && mbar_wait(smem_u32(&empty[lk % TC_STAGES]), (uint32_t)((lk / TC_STAGES) & 1));
+    bool ok = !*abort_flag && lk == nsteps - 1 && done;
+    if (!ok && tid == 0) atomicOr(err, 1);
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (ok) {
         // epilogue, one tile at a time: warp w holds TMEM lanes 32w..32w+31 = tile rows; each
