@@ -401,19 +401,22 @@ constexpr int XT_K = 16, XT_THREADS = 256;
 // MODE kAddTarget: Y[tgt] += T X[src]; only for launches whose targets are all distinct.
 constexpr int kStorePair = 0, kAddTarget = 1;
 
-__device__ __forceinline__ void vec4_load(const float *p, float *v) {
+// N consecutive elements (16 bytes) from shared memory
+template <int N>
+__device__ __forceinline__ void vec_load(const float *p, float *v) {
+    static_assert(N == 4, "16-byte loads");
     const float4 t = *reinterpret_cast<const float4 *>(p);
     v[0] = t.x;
     v[1] = t.y;
     v[2] = t.z;
     v[3] = t.w;
 }
-__device__ __forceinline__ void vec4_load(const double *p, double *v) {
-    const double2 t0 = reinterpret_cast<const double2 *>(p)[0], t1 = reinterpret_cast<const double2 *>(p)[1];
-    v[0] = t0.x;
-    v[1] = t0.y;
-    v[2] = t1.x;
-    v[3] = t1.y;
+template <int N>
+__device__ __forceinline__ void vec_load(const double *p, double *v) {
+    static_assert(N == 2, "16-byte loads");
+    const double2 t = *reinterpret_cast<const double2 *>(p);
+    v[0] = t.x;
+    v[1] = t.y;
 }
 
 // outputs per thread and block: 8 x 8 per thread in FP32 (a 128 x 128 tile: 16 FMAs per shared
@@ -452,7 +455,15 @@ __global__ void __launch_bounds__(XT_THREADS, 2) k_xlat(const T *__restrict__ ma
         }
     }
     __syncthreads();
-    const int tx = tid % 16, ty = tid / 16;  // columns tx*CT.., rows ty*RT..
+    // a warp is an 8 x 4 grid of lanes (8 column groups, 4 row groups) and the block 2 x 4 warps;
+    // thread (tx, ty) owns the columns tx*CH.. and COLS/2 + tx*CH.. and the rows ty*RH.. and
+    // ROWS/2 + ty*RH.., so each 16-byte shared-memory load of a warp reads one contiguous run of
+    // 128 bytes (multipoles) or 64 bytes (operator, broadcast within the warp): one wavefront
+    constexpr int RH = RT / 2, CH = CT / 2;
+    const int lane = tid & 31, wid = tid >> 5;
+    const int tx = (wid & 1) * 8 + (lane & 7), ty = (wid >> 1) * 4 + (lane >> 3);
+    auto row_of = [&](int i) { return i < RH ? ty * RH + i : ROWS / 2 + ty * RH + (i - RH); };
+    auto col_of = [&](int j) { return j < CH ? tx * CH + j : COLS / 2 + tx * CH + (j - CH); };
     T acc[RT][CT];
 #pragma unroll
     for (int i = 0; i < RT; ++i)
@@ -495,15 +506,15 @@ __global__ void __launch_bounds__(XT_THREADS, 2) k_xlat(const T *__restrict__ ma
     for (int t = 0; t < nk; ++t) {
         const int buf = t & 1;
         if (t + 1 < nk) gload((t + 1) * XT_K);
-        if (row0 + ty * RT < P && tx * CT < ncol) {  // rows past P and empty columns skip the products
+        if (row0 + ty * RH < P && tx * CH < ncol) {  // rows past P and empty columns skip the products
 #pragma unroll
             for (int kk = 0; kk < XT_K; ++kk) {
-                // consecutive rows / columns per thread through 16-byte shared-memory loads
+                // two runs of consecutive rows / columns per thread, 16 bytes per load
                 T a[RT], bv[CT];
-#pragma unroll
-                for (int i = 0; i < RT; i += 4) vec4_load(&As[buf][kk][ty * RT + i], a + i);
-#pragma unroll
-                for (int j = 0; j < CT; j += 4) vec4_load(&Bs[buf][kk][tx * CT + j], bv + j);
+                vec_load<RH>(&As[buf][kk][ty * RH], a);
+                vec_load<RH>(&As[buf][kk][ROWS / 2 + ty * RH], a + RH);
+                vec_load<CH>(&Bs[buf][kk][tx * CH], bv);
+                vec_load<CH>(&Bs[buf][kk][COLS / 2 + tx * CH], bv + CH);
 #pragma unroll
                 for (int i = 0; i < RT; ++i)
 #pragma unroll
@@ -515,14 +526,14 @@ __global__ void __launch_bounds__(XT_THREADS, 2) k_xlat(const T *__restrict__ ma
     }
 #pragma unroll
     for (int j = 0; j < CT; ++j) {
-        int col = tx * CT + j;
+        int col = col_of(j);
         if (col >= ncol) continue;
         int r = col % R;
         T *yb = (MODE == kStorePair) ? Y + ((size_t)(ch.start + col / R) * R + r) * P
                                      : Y + ((size_t)s_tgt[col] * R + r) * P;
 #pragma unroll
         for (int i = 0; i < RT; ++i) {
-            int gr = row0 + ty * RT + i;
+            int gr = row0 + row_of(i);
             if (gr < P) {
                 if (MODE == kStorePair) yb[gr] = acc[i][j];
                 else yb[gr] += acc[i][j];
