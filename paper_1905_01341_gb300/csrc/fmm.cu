@@ -428,16 +428,34 @@ template <class T>
 __host__ __device__ constexpr int xt_rows() { return 16 * xt_rt<T>(); }
 template <class T>
 __host__ __device__ constexpr int xt_cols() { return 16 * xt_rt<T>(); }
+// row pitches of the shared-memory stages: multiples of 16 bytes
+template <class T>
+__host__ __device__ constexpr int xt_apitch() { return xt_rows<T>() + 4; }
+template <class T>
+__host__ __device__ constexpr int xt_bpitch() { return xt_cols<T>() + 4; }
+constexpr int XT_STAGES = 3;
+template <class T>
+constexpr size_t xt_smem() { return (size_t)XT_STAGES * XT_K * (xt_apitch<T>() + xt_bpitch<T>()) * sizeof(T); }
+
+// one element global -> shared without a register round trip; ok = false writes zero
+template <class T>
+__device__ __forceinline__ void cp_async_elem(T *dst, const T *src, bool ok) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(src), "n"((int)sizeof(T)),
+                 "r"(ok ? (int)sizeof(T) : 0)
+                 : "memory");
+}
 
 template <class T, int R, int MODE>
 __global__ void __launch_bounds__(XT_THREADS, 2) k_xlat(const T *__restrict__ mats, int P, const XChunk *__restrict__ chunks,
                                                      const int32_t *__restrict__ srcs, const int32_t *__restrict__ tgts,
                                                      const T *X, T *Y) {  // X and Y may be one array (M2M, L2L)
     constexpr int RT = xt_rt<T>(), CT = RT, ROWS = xt_rows<T>(), COLS = xt_cols<T>();
-    // two shared-memory buffers: the next K tile's global loads are in flight (in registers)
-    // while the current tile is multiplied
-    __shared__ __align__(16) T As[2][XT_K][ROWS + 4];  // row pitch a multiple of 16 bytes
-    __shared__ __align__(16) T Bs[2][XT_K][COLS + 4];
+    constexpr int AP = xt_apitch<T>(), BP = xt_bpitch<T>(), VW = 16 / (int)sizeof(T);
+    // XT_STAGES shared-memory stages of one K tile each: As[st][kk][row], Bs[st][kk][col]
+    extern __shared__ __align__(16) unsigned char xt_smem_raw[];
+    T *As = reinterpret_cast<T *>(xt_smem_raw);
+    T *Bs = As + XT_STAGES * XT_K * AP;
     __shared__ int s_src[COLS], s_tgt[COLS];
     const XChunk ch = chunks[blockIdx.x];
     const int row0 = blockIdx.y * ROWS;
@@ -470,59 +488,63 @@ __global__ void __launch_bounds__(XT_THREADS, 2) k_xlat(const T *__restrict__ ma
 #pragma unroll
         for (int j = 0; j < CT; ++j) acc[i][j] = (T)0;
     constexpr int NA = (ROWS * XT_K) / XT_THREADS, NB = (COLS * XT_K) / XT_THREADS;
-    T ra[NA], rb[NB];
-    auto gload = [&](int k0) {
+    // stage st <- the K tile at k0, copied straight from global memory (element-wise cp.async;
+    // zero-filled outside the operator and past the last column); one commit group per call
+    auto cpload = [&](int k0, int st) {
 #pragma unroll
         for (int it = 0; it < NA; ++it) {
             const int e = tid + it * XT_THREADS;
             const int row = e / XT_K, kk = e % XT_K;
             const int gr = row0 + row, gk = k0 + kk;
-            ra[it] = (gr < P && gk < P) ? A[(size_t)gr * P + gk] : (T)0;
+            const bool ok = gr < P && gk < P;
+            const T *src = A + (ok ? (size_t)gr * P + gk : 0);
+            cp_async_elem(As + (st * XT_K + kk) * AP + row, src, ok);
         }
 #pragma unroll
         for (int it = 0; it < NB; ++it) {
             const int e = tid + it * XT_THREADS;
             const int col = e / XT_K, kk = e % XT_K;
             const int gk = k0 + kk;
-            rb[it] = (col < ncol && gk < P) ? X[((size_t)s_src[col] * R + col % R) * P + gk] : (T)0;
+            const bool ok = col < ncol && gk < P;
+            const T *src = X + (ok ? ((size_t)s_src[col] * R + col % R) * P + gk : 0);
+            cp_async_elem(Bs + (st * XT_K + kk) * BP + col, src, ok);
         }
-    };
-    auto sstore = [&](int buf) {
-#pragma unroll
-        for (int it = 0; it < NA; ++it) {
-            const int e = tid + it * XT_THREADS;
-            As[buf][e % XT_K][e / XT_K] = ra[it];
-        }
-#pragma unroll
-        for (int it = 0; it < NB; ++it) {
-            const int e = tid + it * XT_THREADS;
-            Bs[buf][e % XT_K][e / XT_K] = rb[it];
-        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
     };
     const int nk = (P + XT_K - 1) / XT_K;
-    gload(0);
-    sstore(0);
-    __syncthreads();
+    // three stages: tiles t + 1 and t + 2 are in flight while tile t is multiplied
+    cpload(0, 0);
+    if (nk > 1) cpload(XT_K, 1);
+    else asm volatile("cp.async.commit_group;" ::: "memory");
     for (int t = 0; t < nk; ++t) {
-        const int buf = t & 1;
-        if (t + 1 < nk) gload((t + 1) * XT_K);
+        const int buf = t % XT_STAGES;
+        asm volatile("cp.async.wait_group 1;" ::: "memory");  // tile t has landed (this thread's part)
+        // every thread's part of tile t is visible, and the stage of tile t - 1 is no longer read
+        __syncthreads();
+        if (t + 2 < nk) cpload((t + 2) * XT_K, (t + 2) % XT_STAGES);
+        else asm volatile("cp.async.commit_group;" ::: "memory");  // keeps one group per iteration
         if (row0 + ty * RH < P && tx * CH < ncol) {  // rows past P and empty columns skip the products
 #pragma unroll
             for (int kk = 0; kk < XT_K; ++kk) {
                 // two runs of consecutive rows / columns per thread, 16 bytes per load
+                const T *as = As + (buf * XT_K + kk) * AP, *bs = Bs + (buf * XT_K + kk) * BP;
                 T a[RT], bv[CT];
-                vec_load<RH>(&As[buf][kk][ty * RH], a);
-                vec_load<RH>(&As[buf][kk][ROWS / 2 + ty * RH], a + RH);
-                vec_load<CH>(&Bs[buf][kk][tx * CH], bv);
-                vec_load<CH>(&Bs[buf][kk][COLS / 2 + tx * CH], bv + CH);
+#pragma unroll
+                for (int v = 0; v < RH; v += VW) {
+                    vec_load<VW>(as + ty * RH + v, a + v);
+                    vec_load<VW>(as + ROWS / 2 + ty * RH + v, a + RH + v);
+                }
+#pragma unroll
+                for (int v = 0; v < CH; v += VW) {
+                    vec_load<VW>(bs + tx * CH + v, bv + v);
+                    vec_load<VW>(bs + COLS / 2 + tx * CH + v, bv + CH + v);
+                }
 #pragma unroll
                 for (int i = 0; i < RT; ++i)
 #pragma unroll
                     for (int j = 0; j < CT; ++j) acc[i][j] += a[i] * bv[j];
             }
         }
-        if (t + 1 < nk) sstore(buf ^ 1);  // that buffer was last read before the previous barrier
-        __syncthreads();
     }
 #pragma unroll
     for (int j = 0; j < CT; ++j) {
@@ -540,6 +562,13 @@ __global__ void __launch_bounds__(XT_THREADS, 2) k_xlat(const T *__restrict__ ma
             }
         }
     }
+}
+
+// dynamic shared memory above the 48 KB default needs an opt-in, which belongs to the current
+// device: set before every launch (a host call of about a microsecond)
+template <class K>
+void xlat_smem_attr(K kern, size_t bytes) {
+    if (bytes > 48 * 1024) BEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
 }
 
 // Y[t] += sum of Ypair[k] over the pairs k of target t, in ascending k (fixed order,
@@ -806,8 +835,9 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
         PhaseScope ps(c, PH_M2M, fs);
         if (!up_n[l]) continue;
         dim3 grid((unsigned)up_n[l], rowblocks);
-        k_xlat<T, R, kStorePair><<<grid, XT_THREADS, 0, fs>>>(m2m, P, c.m2l_chunks.p + up_first[l], t.up_child.p,
-                                                             t.up_parent.p, mp, ypair);
+        xlat_smem_attr(k_xlat<T, R, kStorePair>, xt_smem<T>());
+        k_xlat<T, R, kStorePair><<<grid, XT_THREADS, xt_smem<T>(), fs>>>(m2m, P, c.m2l_chunks.p + up_first[l],
+                                                                         t.up_child.p, t.up_parent.p, mp, ypair);
         BEM_LAUNCH_CHECK();
         dim3 rg((unsigned)t.nb[l - 1], red_blocks_y);
         k_reduce_pairs<T, R><<<rg, 128, 0, fs>>>(t.base[l - 1], t.up_par_off.p, t.up_by_par.p, ypair, P, mp);
@@ -837,8 +867,9 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
         } else {
             PhaseScope ps(c, PH_M2L_CC, fs);
             dim3 grid((unsigned)nm2l_chunks, rowblocks);
-            k_xlat<T, R, kStorePair><<<grid, XT_THREADS, 0, fs>>>(m2l, P, c.m2l_chunks.p + 1, t.m2l_src.p,
-                                                                 t.m2l_tgt.p, mp, ypair);
+            xlat_smem_attr(k_xlat<T, R, kStorePair>, xt_smem<T>());
+            k_xlat<T, R, kStorePair><<<grid, XT_THREADS, xt_smem<T>(), fs>>>(m2l, P, c.m2l_chunks.p + 1,
+                                                                             t.m2l_src.p, t.m2l_tgt.p, mp, ypair);
             BEM_LAUNCH_CHECK();
         }
         PhaseScope ps(c, PH_M2L_REDUCE, fs);
@@ -852,8 +883,9 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
         if (!up_n[l]) continue;
         PhaseScope ps(c, PH_L2L, fs);
         dim3 grid((unsigned)up_n[l], rowblocks);
-        k_xlat<T, R, kAddTarget><<<grid, XT_THREADS, 0, fs>>>(l2l, P, c.m2l_chunks.p + up_first[l], t.up_parent.p,
-                                                             t.up_child.p, lc, lc);
+        xlat_smem_attr(k_xlat<T, R, kAddTarget>, xt_smem<T>());
+        k_xlat<T, R, kAddTarget><<<grid, XT_THREADS, xt_smem<T>(), fs>>>(l2l, P, c.m2l_chunks.p + up_first[l],
+                                                                         t.up_parent.p, t.up_child.p, lc, lc);
         BEM_LAUNCH_CHECK();
     }
     // L2P
