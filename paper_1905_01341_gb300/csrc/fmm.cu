@@ -283,11 +283,13 @@ __global__ void __launch_bounds__(256) k_p2m(int p, int nleaf, const int32_t *__
             pq[jj * R + r] = q[r * N + s0 + c0 + jj];
             pw[jj * R + r] = HW ? w[r * N + s0 + c0 + jj] : (T)0;
         }
-        // each task: one order m for four points (independent recurrences in flight); the
-        // k loop runs m steps and the n loop p - m - 2, so lanes finish together
+        // each task: one order m for four points (independent recurrences in flight). The point
+        // groups vary fastest, so a warp's lanes share a few neighbouring orders and run nearly
+        // the same trip counts through the m loop and the n loop (orders mixed across the lanes
+        // made every warp run the longest of both loops)
         const int ngroups = (pc + 3) / 4;
         for (int task = threadIdx.x; task < ngroups * p; task += blockDim.x) {
-            const int g = task / p, m = task % p;
+            const int g = task % ngroups, m = task / ngroups;
             T x[4], y[4], z[4], r2[4], mr[4], mi[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -593,7 +595,9 @@ __global__ void k_reduce_pairs(int t0, const int32_t *__restrict__ off, const in
 }
 
 // ------------------------------------------------------------------------------ L2P
-constexpr int L2P_THREADS = 128;
+// One warp per leaf: leaves hold about 70-150 points, and a 128-thread block left most of its
+// lanes idle on the second pass over a leaf's points.
+constexpr int L2P_THREADS = 32;
 
 // TwoSum-compensated accumulation in T; for double the compensation is harmless.
 template <class T>
@@ -608,15 +612,28 @@ struct CompSum {
     __device__ __forceinline__ T get() const { return s + c; }
 };
 
+// far_i = sum_{n,m} L_n^m R_n^m(x_i) at the leaf's points (real form: m = 0 once, m > 0 twice the
+// real part). The regular harmonics come from the same recurrences as in P2M, column by column
+// (fixed m, rising n), with tabulated divisors; each column is summed plainly and the columns are
+// merged with compensation.
 template <class T, int R>
 __global__ void __launch_bounds__(L2P_THREADS) k_l2p(int p, const int32_t *__restrict__ bstart, const int32_t *__restrict__ bcount,
                                                      int64_t N, const T *__restrict__ loc, const T *__restrict__ lc,
                                                      T *__restrict__ far) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    T *Ls = reinterpret_cast<T *>(smraw);
-    const int P = p * p;
+    const int P = p * p, ntri = p * (p + 1) / 2;
+    T *Ls = reinterpret_cast<T *>(smraw);  // [R][P]
+    T *tk = Ls + R * P;                     // [p]: -1 / (2k)
+    T *tnm = tk + p;                        // [ntri]: 1 / ((n + m)(n - m)), n >= m + 2
     int b = blockIdx.x;
     for (int e = threadIdx.x; e < R * P; e += L2P_THREADS) Ls[e] = lc[(size_t)b * R * P + e];
+    for (int e = threadIdx.x; e < p; e += L2P_THREADS) tk[e] = e > 0 ? (T)(-0.5) / (T)e : (T)0;
+    for (int e = threadIdx.x; e < ntri; e += L2P_THREADS) {
+        int n = 0;
+        while ((n + 1) * (n + 2) / 2 <= e) ++n;
+        const int m = e - n * (n + 1) / 2;
+        tnm[e] = n >= m + 2 ? (T)1 / ((T)(n + m) * (T)(n - m)) : (T)0;
+    }
     __syncthreads();
     int s0 = bstart[b], cnt = bcount[b];
     for (int c0 = threadIdx.x; c0 < cnt; c0 += L2P_THREADS) {
@@ -627,42 +644,40 @@ __global__ void __launch_bounds__(L2P_THREADS) k_l2p(int p, const int32_t *__res
         T mr = 1, mi = 0;
         for (int m = 0; m < p; ++m) {
             if (m > 0) {
-                T f = (T)(-0.5) / (T)m;
+                const T f = tk[m];
                 T nr = f * (x * mr - y * mi), ni = f * (x * mi + y * mr);
                 mr = nr;
                 mi = ni;
             }
-            T p2r = 0, p2i = 0, p1r = mr, p1i = mi;
-            for (int n = m; n < p; ++n) {
-                T cr, ci;
-                if (n == m) {
-                    cr = mr;
-                    ci = mi;
-                } else if (n == m + 1) {
-                    cr = z * mr;
-                    ci = z * mi;
-                    p2r = mr;
-                    p2i = mi;
-                    p1r = cr;
-                    p1i = ci;
-                } else {
-                    T d = (T)1 / ((T)(n + m) * (T)(n - m));
-                    cr = ((T)(2 * n - 1) * z * p1r - r2 * p2r) * d;
-                    ci = ((T)(2 * n - 1) * z * p1i - r2 * p2i) * d;
+            T col[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) col[r] = (T)0;
+            // L_n^m against R_n^m = cr + i ci
+            auto term = [&](int n, T cr, T ci) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const T *Lr = Ls + r * P + n * n;
+                    col[r] += (m == 0) ? Lr[0] * cr : (T)2 * (Lr[2 * m - 1] * cr - Lr[2 * m] * ci);
+                }
+            };
+            term(m, mr, mi);
+            if (m + 1 < p) {
+                T p2r = mr, p2i = mi, p1r = z * mr, p1i = z * mi;
+                term(m + 1, p1r, p1i);
+                for (int n = m + 2; n < p; ++n) {
+                    const T d = tnm[tri_idx(n, m)];
+                    const T c2z = (T)(2 * n - 1) * z;
+                    const T cr = (c2z * p1r - r2 * p2r) * d;
+                    const T ci = (c2z * p1i - r2 * p2i) * d;
+                    term(n, cr, ci);
                     p2r = p1r;
                     p2i = p1i;
                     p1r = cr;
                     p1i = ci;
                 }
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const T *Lr = Ls + r * P;
-                    T v;
-                    if (m == 0) v = Lr[n * n] * cr;
-                    else v = (T)2 * (Lr[n * n + 2 * m - 1] * cr - Lr[n * n + 2 * m] * ci);
-                    acc[r].add(v);
-                }
             }
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r].add(col[r]);
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) far[r * N + i] = acc[r].get();
@@ -891,7 +906,7 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
     // L2P
     {
         PhaseScope ps(c, PH_L2P, fs);
-        size_t sm = (size_t)R * P * sizeof(T);
+        size_t sm = ((size_t)R * P + p + (size_t)p * (p + 1) / 2) * sizeof(T);  // expansion + divisor tables
         k_l2p<T, R><<<nleaf, L2P_THREADS, sm, fs>>>(p, t.bstart.p + t.base[L], t.bcount.p + t.base[L], N, loc,
                                                     lc + (size_t)t.base[L] * R * P, far);
         BEM_LAUNCH_CHECK();
