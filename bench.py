@@ -84,7 +84,9 @@ def parse():
     ap.add_argument("--restart", type=int, default=100)
     ap.add_argument("--precond", type=int, default=2,
                     help="GMRES right preconditioning: 0 none (the paper), 1 Jacobi, 2 bubble blocks")
-    ap.add_argument("--m2l-tc", type=int, default=1, help="1 = M2L of single-RHS products on the tensor cores")
+    ap.add_argument("--m2l-tc", type=int, default=3,
+                    help="M2L on the tensor cores: 1 single-RHS products, 2 also the 4-RHS diagonal product, "
+                         "3 (default) as 2 for bubbles of at most 2562 vertices, 0 none")
     ap.add_argument("--overlap", type=int, default=1, help="1 = near field on its own stream, overlapping the far field")
     ap.add_argument("--pa", type=float, default=0.5, help="acoustic amplitude Pa/p0")
     ap.add_argument("--pf", type=int, default=6, help="shape-filter bandwidth")

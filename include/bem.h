@@ -91,12 +91,15 @@ typedef struct {
                                concurrently with the far field; 0: one stream, phase after
                                phase (the per-kernel timings of a profile then do not
                                overlap). Same results either way. Default 1.                  */
-    int32_t m2l_tensor_cores; /* 1: mixed-precision single-RHS products (every GMRES product)
-                               run M2L on the tensor cores (three-piece BF16 split, FP32
-                               accumulation) when p_fmm^2 is a multiple of 4 and <= 256;
-                               0: FP32 CUDA cores. The 4-RHS product behind the diagonals
-                               always uses the CUDA cores: Eqs. (s3)/(s5) form M_ii and L_ii
-                               by cancellation, which magnifies rounding. Default 1.          */
+    int32_t m2l_tensor_cores; /* Mixed precision only. 1: single-RHS products (every GMRES
+                               product) run M2L on the tensor cores (three-piece BF16 split,
+                               FP32 accumulation) when p^2 is a multiple of 4 and <= 256;
+                               2: the 4-RHS product behind the diagonals (Eqs. (s3)/(s5)) as
+                               well, at diag_p_fmm; 3: as 2 while every bubble has at most
+                               2562 vertices, else as 1 (the identities magnify the far
+                               field's rounding by about R/h); 0: FP32 CUDA cores throughout.
+                               Orders with p^2 > 256 use the CUDA cores in every mode.
+                               Default 3.                                                      */
     int32_t gmres_precond;  /* 0: unpreconditioned GMRES, as in the paper (Section 3.8);
                                1: right Jacobi preconditioning x = D^-1 y with D = diag(L_ii)
                                (removes the spread of the single layer's scale across bubbles

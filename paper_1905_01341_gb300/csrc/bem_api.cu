@@ -165,7 +165,7 @@ void check_params(const bem_params &p) {
         fail(BEM_ERR_ARG, "diag_p_fmm must be -1 or in 2..20");
     if (p.overlap != 0 && p.overlap != 1) fail(BEM_ERR_ARG, "overlap must be 0 or 1");
     if (p.mvp != BEM_MVP_FMM && p.mvp != BEM_MVP_DIRECT) fail(BEM_ERR_ARG, "bad mvp kind");
-    if (p.m2l_tensor_cores != 0 && p.m2l_tensor_cores != 1) fail(BEM_ERR_ARG, "m2l_tensor_cores must be 0 or 1");
+    if (p.m2l_tensor_cores < 0 || p.m2l_tensor_cores > 3) fail(BEM_ERR_ARG, "m2l_tensor_cores must be 0..3");
     if (p.gmres_maxit < 1 || p.gmres_restart < 0 || p.gmres_restart > 127) fail(BEM_ERR_ARG, "bad GMRES limits");
     if (p.gmres_precond < 0 || p.gmres_precond > 2) fail(BEM_ERR_ARG, "gmres_precond must be 0, 1 or 2");
     if (!(p.gmres_tol > 0.0)) fail(BEM_ERR_ARG, "gmres_tol must be > 0");
@@ -211,7 +211,7 @@ void tune_tree_level(Context &c) {
         c.level_override = L;
         build_tree(c);
         c.m2l_chunks_h.clear();
-        c.tc_chunks_r = 0;
+        c.tc_chunks_ok[0] = c.tc_chunks_ok[1] = false;
         double f = 1.0, g = 0.0;
         const double *xl[1] = {c.ones.p};
         const double *xm[1] = {nullptr};
@@ -258,8 +258,8 @@ void build_all(Context &c) {
     }
     if (c.prm.mvp == BEM_MVP_FMM) {
         build_operators(c, c.ops, c.prm.p_fmm);
-        if (c.prm.m2l_tensor_cores && m2l_tc_supported(c.ops.P) && c.ops.tc_Npad == 0) build_tc_tables(c);
-        c.tc_chunks_r = 0;
+        if (c.prm.m2l_tensor_cores && m2l_tc_supported(c.ops.P) && c.ops.tc_Npad == 0) build_tc_tables(c, c.ops);
+        c.tc_chunks_ok[0] = c.tc_chunks_ok[1] = false;
         c.tc_err.resize(1);
         BEM_CUDA(cudaMemsetAsync(c.tc_err.p, 0, sizeof(int), c.stream));
         if (c.prm.leaf_target == 0 && c.prm.fixed_level == 0 && c.tuned_level == 0) tune_tree_level(c);
@@ -269,7 +269,7 @@ void build_all(Context &c) {
             build_tree(c);
         }
         c.m2l_chunks_h.clear();
-        c.tc_chunks_r = 0;  // chunk tables follow the tree (the depth autotuner built others)
+        c.tc_chunks_ok[0] = c.tc_chunks_ok[1] = false;  // chunk tables follow the tree (the autotuner built others)
         c.stats.p2p_pairs = c.tree.p2p_pairs;
         c.stats.m2l_pairs = c.tree.n_m2l;
         c.stats.levels = c.tree.L;
@@ -313,9 +313,18 @@ void build_all(Context &c) {
     const Operators *dops = nullptr;
     if (c.prm.mvp == BEM_MVP_FMM) {
         const int dp = c.prm.diag_p_fmm > 0 ? c.prm.diag_p_fmm : std::min(c.prm.p_fmm + 2, kMaxPfmm);
+        // tensor cores for the diagonal product: always in mode 2; in mode 3 (automatic) only while
+        // every bubble has at most kDiagTcMaxVerts vertices. The identities cancel O(1) sums down
+        // to O(h), so the far field's rounding is magnified by about R/h: on a 40962-vertex
+        // bubble the BF16 split doubled the product error at p = 14, on 642-vertex bubbles it
+        // left it unchanged.
+        int64_t maxv = 0;
+        for (size_t b = 0; b + 1 < c.vert_off.size(); ++b) maxv = std::max(maxv, c.vert_off[b + 1] - c.vert_off[b]);
+        c.diag_tc = c.prm.m2l_tensor_cores == 2 || (c.prm.m2l_tensor_cores == 3 && maxv <= kDiagTcMaxVerts);
         if (dp != c.prm.p_fmm) {
             build_operators(c, c.ops_diag, dp);
             dops = &c.ops_diag;
+            if (c.diag_tc && m2l_tc_supported(c.ops_diag.P) && c.ops_diag.tc_Npad == 0) build_tc_tables(c, c.ops_diag);
         }
     }
     offdiag_apply(c, 4, fa, xl, ga, xm, o, dprec, dops);
@@ -375,7 +384,7 @@ int bem_params_default(bem_params *p) {
     p->diag_precision = -1;
     p->diag_p_fmm = -1;
     p->overlap = 1;
-    p->m2l_tensor_cores = 1;
+    p->m2l_tensor_cores = 3;
     p->gmres_precond = 0;
     p->gmres_maxit = 100;
     p->gmres_restart = 0;

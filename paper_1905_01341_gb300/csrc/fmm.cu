@@ -860,25 +860,27 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
     }
     // M2L, all levels at once, then each target sums its sources
     if (nm2l_chunks) {
-        // The 4-RHS product behind the diagonals stays on the CUDA cores: M_ii and L_ii are formed
-        // by cancellation (Eqs. (s3), (s5)), which magnifies the tensor path's rounding.
-        const bool tc_path = !F64 && R == 1 && c.prm.m2l_tensor_cores && m2l_tc_supported(P) && opr.tc_Npad > 0 &&
-                             &opr == &c.ops;
+        // Single-RHS products (every GMRES product) use the tensor cores with m2l_tensor_cores >= 1;
+        // the 4-RHS product behind the diagonals where build decided so (diag_tc): M_ii and L_ii
+        // are formed by cancellation (Eqs. (s3), (s5)), which magnifies the far field's rounding.
+        const bool tc_path = !F64 && (R == 1 ? c.prm.m2l_tensor_cores >= 1 : R == 4 && c.diag_tc) &&
+                             m2l_tc_supported(P) && opr.tc_Npad > 0;
         if (tc_path) {
             PhaseScope ps(c, PH_M2L, fs);
-            if (c.tc_chunks_r != R) {
+            const int ti = R == 1 ? 0 : 1;
+            if (!c.tc_chunks_ok[ti]) {
                 std::vector<XChunk> tc;
                 make_chunks(t.m2l_class_off, 0, m2l_tc_pairs_per_chunk(R), tc);
-                c.tc_chunks.resize(std::max<size_t>(tc.size(), 1));
+                c.tc_chunks[ti].resize(std::max<size_t>(tc.size(), 1));
                 if (!tc.empty())
-                    BEM_CUDA(cudaMemcpyAsync(c.tc_chunks.p, tc.data(), tc.size() * sizeof(XChunk),
+                    BEM_CUDA(cudaMemcpyAsync(c.tc_chunks[ti].p, tc.data(), tc.size() * sizeof(XChunk),
                                              cudaMemcpyHostToDevice, fs));
-                c.n_tc_chunks = (int64_t)tc.size();
-                c.tc_chunks_r = R;
+                c.n_tc_chunks[ti] = (int64_t)tc.size();
+                c.tc_chunks_ok[ti] = true;
             }
-            if (c.n_tc_chunks)
-                launch_m2l_tc<R>(c, c.tc_chunks.p, c.n_tc_chunks, (const float *)mp, (int64_t)t.nbox * R, (float *)ypair,
-                                 c.tc_err.p, fs);
+            if (c.n_tc_chunks[ti])
+                launch_m2l_tc<R>(c, opr, c.tc_chunks[ti].p, c.n_tc_chunks[ti], (const float *)mp, (int64_t)t.nbox * R,
+                                 (float *)ypair, c.tc_err.p, fs);
         } else {
             PhaseScope ps(c, PH_M2L_CC, fs);
             dim3 grid((unsigned)nm2l_chunks, rowblocks);

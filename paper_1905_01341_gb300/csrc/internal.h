@@ -94,6 +94,9 @@ inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
 constexpr int kMaxRhs = 4;
 constexpr int kDeepLevel = 10;       // Morton keys are computed at this depth (30 bits)
 constexpr int kMaxPfmm = 20;
+// largest bubble (vertices; icosphere level 4) for which the automatic mode runs the diagonal
+// product's M2L on the tensor cores
+constexpr int64_t kDiagTcMaxVerts = 2562;
 constexpr int kNumM2LClasses = 316;  // offsets in [-3,3]^3 minus the 27 near ones
 
 // ------------------------------------------------------------------------------ octree
@@ -291,10 +294,12 @@ struct Context {
     DevBuf<double> near_out;       // combined potential [R][N] (sorted)
     DevBuf<XChunk> m2l_chunks;
     std::vector<XChunk> m2l_chunks_h;
-    DevBuf<XChunk> tc_chunks;        // M2L chunks of <= 256/R pairs for the tensor-core kernel
+    // M2L chunks of <= 256/R pairs for the tensor-core kernel: [0] for R = 1, [1] for R = 4
+    DevBuf<XChunk> tc_chunks[2];
+    bool tc_chunks_ok[2] = {false, false};  // built for the current tree
+    bool diag_tc = false;                     // the 4-RHS diagonal product uses the tensor-core M2L
+    int64_t n_tc_chunks[2] = {0, 0};
     DevBuf<uint16_t> xsplit;         // multipoles split into three BF16 planes (tensor-core M2L)
-    int tc_chunks_r = 0;             // R the table was built for (0 = none)
-    int64_t n_tc_chunks = 0;
     DevBuf<int> tc_err;              // set by a tensor-core block whose wait ran out
     std::vector<DevBuf<XChunk> *> up_chunks;  // per level
     std::vector<std::vector<XChunk>> up_chunks_h;
@@ -367,9 +372,9 @@ void launch_direct32_raw(int64_t N, const float *hi, const float *lo, const doub
 
 // m2l_tc.cu
 bool m2l_tc_supported(int P);
-void build_tc_tables(Context &c);
+void build_tc_tables(Context &c, Operators &o);
 template <int R>
-void launch_m2l_tc(Context &c, const XChunk *chunks, int64_t nchunks, const float *X, int64_t xrows, float *Ypair,
+void launch_m2l_tc(Context &c, const Operators &o, const XChunk *chunks, int64_t nchunks, const float *X, int64_t xrows, float *Ypair,
                    int *err, cudaStream_t st);
 int m2l_tc_pairs_per_chunk(int R);
 

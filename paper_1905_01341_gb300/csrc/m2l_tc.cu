@@ -357,8 +357,7 @@ bool m2l_tc_supported(int P) { return P % 4 == 0 && P <= 256; }
 
 int m2l_tc_pairs_per_chunk(int R) { return TC_TILES * TC_M / R; }
 
-void build_tc_tables(Context &c) {
-    Operators &o = c.ops;
+void build_tc_tables(Context &c, Operators &o) {
     const int P = o.P;
     if (!m2l_tc_supported(P)) return;
     o.tc_Npad = (P + 15) / 16 * 16;
@@ -372,9 +371,8 @@ void build_tc_tables(Context &c) {
 }
 
 template <int R>
-void launch_m2l_tc(Context &c, const XChunk *chunks, int64_t nchunks, const float *X, int64_t xrows, float *Ypair,
-                   int *err, cudaStream_t st) {
-    const Operators &o = c.ops;
+void launch_m2l_tc(Context &c, const Operators &o, const XChunk *chunks, int64_t nchunks, const float *X,
+                   int64_t xrows, float *Ypair, int *err, cudaStream_t st) {
     const int Npad = o.tc_Npad;
     // split the multipoles once for all translations of this product
     const size_t nxs = (size_t)3 * xrows * Npad;
@@ -397,9 +395,9 @@ void launch_m2l_tc(Context &c, const XChunk *chunks, int64_t nchunks, const floa
     BEM_LAUNCH_CHECK();
 }
 
-template void launch_m2l_tc<1>(Context &, const XChunk *, int64_t, const float *, int64_t, float *, int *,
-                               cudaStream_t);
-template void launch_m2l_tc<4>(Context &, const XChunk *, int64_t, const float *, int64_t, float *, int *,
-                               cudaStream_t);
+template void launch_m2l_tc<1>(Context &, const Operators &, const XChunk *, int64_t, const float *, int64_t, float *,
+                               int *, cudaStream_t);
+template void launch_m2l_tc<4>(Context &, const Operators &, const XChunk *, int64_t, const float *, int64_t, float *,
+                               int *, cudaStream_t);
 
 }  // namespace bem

@@ -54,7 +54,7 @@ def test_params_default_host_only(lib):
 
     p = bem.bem_params_default()
     assert p.p_fmm == 14 and p.precision == bem.BEM_PREC_MIXED and p.gmres_tol == 1e-6
-    assert p.gmres_maxit == 100 and p.diag_precision == -1 and p.m2l_tensor_cores == 1
+    assert p.gmres_maxit == 100 and p.diag_precision == -1 and p.m2l_tensor_cores == 3
     p2 = bem.bem_params_default(p_fmm=16, precision=bem.BEM_PREC_FP64)
     assert p2.p_fmm == 16 and p2.precision == 0
 

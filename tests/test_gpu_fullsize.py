@@ -28,11 +28,15 @@ def fullsize():
     return mesh, phi, x, recv, ld, md, offL + ld * x[recv], offM + md * phi[recv]
 
 
-def test_fullsize_cluster_products_and_diagonals_at_sampled_receivers(fullsize):
+@pytest.mark.parametrize("tc", [1, 2])
+def test_fullsize_cluster_products_and_diagonals_at_sampled_receivers(fullsize, tc):
+    """tc = 1: tensor-core M2L in the single-RHS products; tc = 2: also in the 4-RHS product
+    behind the identity diagonals."""
     from paper_1905_01341_gb300 import bem
 
     mesh, phi, x, recv, ld, md, eL, eM = fullsize
-    ctx = bem.BemContext(mvp=bem.BEM_MVP_FMM, precision=bem.BEM_PREC_MIXED, p_fmm=14, leaf_target=0)
+    ctx = bem.BemContext(mvp=bem.BEM_MVP_FMM, precision=bem.BEM_PREC_MIXED, p_fmm=14, leaf_target=0,
+                         m2l_tensor_cores=tc)
     ctx.upload_mesh(mesh)
     ctx.build()
     N = mesh.n
@@ -49,7 +53,44 @@ def test_fullsize_cluster_products_and_diagonals_at_sampled_receivers(fullsize):
     gl, gm = gl.cpu().numpy()[recv], gm.cpu().numpy()[recv]
     errs = {"L": rel(o1.cpu().numpy()[recv], eL), "M": rel(o2.cpu().numpy()[recv], eM),
             "Ldiag": rel(gl, ld), "Mdiag": rel(gm, md)}
-    print("full-size errors at 400 receivers:", {k: "%.2e" % v for k, v in errs.items()},
-          "levels", ctx.stats()["levels"])
+    print("m2l_tensor_cores=%d full-size errors at 400 receivers:" % tc, {k: "%.2e" % v for k, v in errs.items()},
+          "levels", ctx.stats()["levels"], "build ms %.1f" % ctx.stats()["last_build_ms"])
     ctx.close()
     assert errs["L"] < 1e-5 and errs["M"] < 1e-5
+
+
+@pytest.mark.parametrize("level,bubbles", [(3, 800), (4, 200), (5, 50)])
+def test_tensor_core_diagonal_product_by_bubble_resolution(level, bubbles):
+    """Clusters of about 0.5M unknowns whose bubbles have 642, 2562 or 10242 vertices: the
+    products with the 4-RHS diagonal product's M2L on the tensor cores (mode 2) against the same
+    on the CUDA cores (mode 1), at 400 sampled receivers against the direct FP64 oracle. Up to
+    2562 vertices per bubble the tensor cores leave the error unchanged (within 1.5x), and the
+    automatic mode (3) gives mode 2's results there and mode 1's above."""
+    from paper_1905_01341_gb300 import bem
+
+    mesh, phi = synth.workload_cluster(bubbles=bubbles, level=level, seed=21)
+    s, n = oracle.vertex_geometry(mesh.xyz, mesh.tri)
+    recv = oracle.checkpoint_receivers(mesh.n, 400, 22)
+    ld, md = oracle.diagonals(mesh.xyz, s, n, recv)
+    eM = oracle.offdiag_apply(mesh.xyz, s, n, 0.0, None, 1.0, phi, recv) + md * phi[recv]
+    eL = oracle.offdiag_apply(mesh.xyz, s, n, 1.0, phi, 0.0, None, recv) + ld * phi[recv]
+    outs, errs = {}, {}
+    for tc in (1, 2, 3):
+        ctx = bem.BemContext(mvp=bem.BEM_MVP_FMM, precision=bem.BEM_PREC_MIXED, p_fmm=14, leaf_target=0,
+                             m2l_tensor_cores=tc)
+        ctx.upload_mesh(mesh)
+        ctx.build()
+        o1 = np.zeros(mesh.n)
+        o2 = np.zeros(mesh.n)
+        ctx.apply(1.0, phi, 0.0, None, o1)
+        ctx.apply(0.0, None, 1.0, phi, o2)
+        ctx.close()
+        outs[tc] = (o1, o2)
+        errs[tc] = (rel(o1[recv], eL), rel(o2[recv], eM))
+    print("level %d (%d vertices per bubble): (L, M) errors by m2l_tensor_cores:" % (level, mesh.n // bubbles),
+          {k: "%.2e %.2e" % v for k, v in errs.items()})
+    auto_like = 2 if mesh.n // bubbles <= 2562 else 1
+    assert all(np.array_equal(a, b) for a, b in zip(outs[3], outs[auto_like]))
+    if level <= 4:
+        assert max(errs[2]) < 1e-5
+        assert errs[2][0] < 1.5 * errs[1][0] and errs[2][1] < 1.5 * errs[1][1]

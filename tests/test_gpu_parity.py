@@ -200,6 +200,29 @@ def test_single_bubble_l6_p_sweep(l6_reference, prec):
     assert errs[14] < 1e-5
 
 
+def test_tensor_core_diagonal_product_single_bubble_l6(l6_reference):
+    """On the 40962-vertex bubble the identities (Eqs. (s3), (s5)) magnify the far field's
+    rounding enough that the 4-RHS diagonal product on the tensor cores (mode 2) about doubles
+    the product error at p = 14; the automatic mode (3, the default) keeps that product on the
+    CUDA cores for bubbles this fine and reproduces mode 1 exactly."""
+    bem = _bem()
+    mesh, phi, ref, x, eL, eM = l6_reference
+    errs, outs = {}, {}
+    for tc in (1, 2, 3):
+        ctx = make_ctx(mesh, mvp=bem.BEM_MVP_FMM, precision=bem.BEM_PREC_MIXED, p_fmm=14, m2l_tensor_cores=tc)
+        o1 = torch.zeros(mesh.n, dtype=torch.float64, device="cuda")
+        o2 = torch.zeros(mesh.n, dtype=torch.float64, device="cuda")
+        ctx.apply(1.0, dev(x), 0.0, None, o1)
+        ctx.apply(0.0, None, 1.0, dev(phi), o2)
+        outs[tc] = (o1.cpu().numpy(), o2.cpu().numpy())
+        errs[tc] = (rel(outs[tc][0], eL), rel(outs[tc][1], eM))
+        ctx.close()
+    print("single bubble L6, p=14, mixed: (L, M) errors by m2l_tensor_cores:",
+          {k: "%.2e %.2e" % v for k, v in errs.items()})
+    assert all(np.array_equal(a, b) for a, b in zip(outs[3], outs[1]))
+    assert max(errs[1]) < 1e-5
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_fmm_apply_is_deterministic(prec):
     """Translations are summed per target in a fixed order (no floating-point atomics), so
