@@ -88,6 +88,8 @@ def parse():
                     help="M2L on the tensor cores: 1 single-RHS products, 2 also the 4-RHS diagonal product, "
                          "3 (default) as 2 for bubbles of at most 2562 vertices, 0 none")
     ap.add_argument("--overlap", type=int, default=1, help="1 = near field on its own stream, overlapping the far field")
+    ap.add_argument("--guess", type=int, default=2,
+                    help="step-start GMRES guess: 0 previous q (the paper), 1/2 linear/quadratic extrapolation in t")
     ap.add_argument("--pa", type=float, default=0.5, help="acoustic amplitude Pa/p0")
     ap.add_argument("--pf", type=int, default=6, help="shape-filter bandwidth")
     ap.add_argument("--fp64-compare", type=int, default=1, help="also time FP64 right-hand sides (0 = skip)")
@@ -283,7 +285,7 @@ def run_ours(args):
     progress("workload ready: %d unknowns, %d bubbles" % (N, mesh.m))
     ctx = make_ctx(prec)
     ctx.upload(xyz, tri, voff, toff)
-    sp = bem.bem_step_params_default(pa=args.pa, pf=args.pf)
+    sp = bem.bem_step_params_default(pa=args.pa, pf=args.pf, guess=args.guess)
     bem.bem_step_init(ctx.ctx, phid, sp)
 
     warm = []
@@ -358,13 +360,22 @@ def run_ours(args):
     xyz_h = torch.empty(3 * N, dtype=torch.float64).pin_memory()
     phi_h = torch.empty(N, dtype=torch.float64).pin_memory()
     q_h = torch.empty(N, dtype=torch.float64).pin_memory()
-    e2e_t = []
+    # (these are the steps after the timed ones: their GMRES iteration counts and device times
+    # are reported beside the host-clock value)
+    e2e_t, e2e_dev, e2e_it = [], [], []
     for _ in range(max(1, args.steps)):
         torch.cuda.synchronize()
+        d0 = torch.cuda.Event(enable_timing=True)
+        d1 = torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
-        bem.bem_step(ctx.ctx)
+        d0.record(stream)
+        info = bem.bem_step(ctx.ctx)
+        d1.record(stream)
         bem.bem_step_get_state(ctx.ctx, xyz_h, phi_h, q_h)
         e2e_t.append(time.perf_counter() - t0)
+        torch.cuda.synchronize()
+        e2e_dev.append(d0.elapsed_time(d1) / 1e3)
+        e2e_it.append(info["gmres_iters"])
     e2e_s = statistics.mean(e2e_t)
     d2h = (xyz_h.numel() + phi_h.numel() + q_h.numel()) * 8
 
@@ -431,7 +442,7 @@ def run_ours(args):
         "dtype": "f32+f64" if prec == bem.BEM_PREC_MIXED else "f64", "data": "synthetic",
         "config": {"workload": workload_name(args, mesh), "p_fmm": args.p, "precision": args.precision,
                    "leaf_target": args.leaf, "gmres_tol": args.tol, "gmres_precond": args.precond,
-                   "m2l_tensor_cores": args.m2l_tc, "overlap": args.overlap,
+                   "m2l_tensor_cores": args.m2l_tc, "overlap": args.overlap, "guess": args.guess,
                    "scheme": ("AB6 (steps after the 5 RK4 start steps)" if rhs / args.steps < 2 else
                               "RK4 start steps (the paper's AB6 begins after 5)"),
                    "pa": args.pa, "pf": args.pf, "dt": infos[-1]["dt"], "levels": st["levels"],
@@ -450,6 +461,7 @@ def run_ours(args):
         "roofline_p2p": roof_p2p,
         "roofline_m2l": roof_m2l,
         "e2e": {"value": e2e_s, "unit": "s/step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(d2h),
+                "device_s_per_step": statistics.mean(e2e_dev), "gmres_iters_per_step": statistics.mean(e2e_it),
                 "what": "bem_step driven from the host + bem_step_get_state into pinned host buffers"},
         "gpu_launches": int((st1["n_launches"] - st0["n_launches"]) / args.steps),
         "clocks": clk,
@@ -524,7 +536,7 @@ def run_batched(args):
         c.upload_mesh(m)
         if clusters is not None:
             bem.bem_mesh_set_clusters(c.ctx, len(clusters) - 1, clusters)
-        bem.bem_step_init(c.ctx, ph, bem.bem_step_params_default(pa=args.pa, pf=args.pf))
+        bem.bem_step_init(c.ctx, ph, bem.bem_step_params_default(pa=args.pa, pf=args.pf, guess=args.guess))
         return c
 
     ctx = stepper(mesh, phi, boff)
@@ -600,7 +612,7 @@ def run_learned(args):
     ctx = bem.BemContext(stream=stream, p_fmm=args.p, precision=prec, leaf_target=args.leaf, gmres_tol=args.tol,
                          gmres_maxit=args.maxit, gmres_restart=args.restart, gmres_precond=args.precond)
     ctx.upload_mesh(mesh)
-    bem.bem_step_init(ctx.ctx, phi, bem.bem_step_params_default(pa=args.pa, pf=args.pf))
+    bem.bem_step_init(ctx.ctx, phi, bem.bem_step_params_default(pa=args.pa, pf=args.pf, guess=args.guess))
     bem.bem_mlp_init(ctx.ctx, hidden=256, lmax=10, seed=1)
     bem.bem_mlp_set_mode(ctx.ctx, record=True)
     t0 = time.perf_counter()

@@ -90,7 +90,7 @@ class bem_step_params(ctypes.Structure):
         ("courant", ctypes.c_double),
         ("dt", ctypes.c_double),
         ("pf", ctypes.c_int32),
-        ("overlap", ctypes.c_int32),
+        ("guess", ctypes.c_int32),
     ]
 
 

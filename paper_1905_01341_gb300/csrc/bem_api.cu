@@ -633,6 +633,7 @@ int bem_step_params_default(bem_step_params *sp) {
     sp->courant = 0.1;
     sp->dt = 0.0;
     sp->pf = 6;
+    sp->guess = 2;
     return BEM_OK;
 }
 

@@ -36,6 +36,12 @@ struct StepState {
     DevBuf<double> x0;  // r at t = 0 (SoA)
     DevBuf<double> vt, H;
     bem_step_stats last{};
+    // q of the last three step-start solves (newest first through qh_order) and their times,
+    // for the extrapolated initial guess
+    DevBuf<double> qh;  // [3][N]
+    double qh_time[3] = {0.0, 0.0, 0.0};  // per slot
+    int qh_order[3] = {0, 1, 2};
+    int qh_n = 0;
 };
 
 namespace {
@@ -409,7 +415,58 @@ void apply_filter(Context &c, StepState &s, const double *X, double *Y) {
 }
 
 // f = filtered right-hand side at state y (both [4N]), time t. Updates s.q.
-void rhs(Context &c, StepState &s, const double *y, double t, double *f, bem_step_stats &st) {
+// out = sum_j w[j] a_j over the first n of three vectors
+__global__ void k_combine3(int64_t N, int n, double w0, double w1, double w2, const double *__restrict__ a0,
+                           const double *__restrict__ a1, const double *__restrict__ a2, double *__restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double v = w0 * a0[i];
+    if (n > 1) v += w1 * a1[i];
+    if (n > 2) v += w2 * a2[i];
+    out[i] = v;
+}
+
+// s.q <- the Lagrange polynomial in t through the recorded step-start solutions (degree
+// min(guess, recorded - 1)), evaluated at t; unchanged below degree 1
+void extrapolate_guess(Context &c, StepState &s, double t) {
+    const int k = std::min(s.sp.guess, s.qh_n - 1);
+    if (k < 1) return;
+    double w[3] = {0.0, 0.0, 0.0};
+    const double *a[3] = {nullptr, nullptr, nullptr};
+    for (int j = 0; j <= k; ++j) {
+        const double tj = s.qh_time[s.qh_order[j]];
+        double v = 1.0;
+        for (int m = 0; m <= k; ++m)
+            if (m != j) {
+                const double tm = s.qh_time[s.qh_order[m]];
+                v *= (t - tm) / (tj - tm);
+            }
+        w[j] = v;
+        a[j] = s.qh.p + (size_t)s.qh_order[j] * c.N;
+    }
+    k_combine3<<<div_up(c.N, 256), 256, 0, c.stream>>>(c.N, k + 1, w[0], w[1], w[2], a[0], a[1] ? a[1] : a[0],
+                                                       a[2] ? a[2] : a[0], s.q.p);
+    BEM_LAUNCH_CHECK();
+}
+
+// record s.q as the solution at step-start time t (the oldest of three is dropped)
+void record_start_solution(Context &c, StepState &s, double t) {
+    s.qh.resize(3 * (size_t)c.N);
+    const int last = s.qh_order[2];
+    s.qh_order[2] = s.qh_order[1];
+    s.qh_order[1] = s.qh_order[0];
+    s.qh_order[0] = last;
+    s.qh_time[last] = t;
+    BEM_CUDA(cudaMemcpyAsync(s.qh.p + (size_t)last * c.N, s.q.p, c.N * sizeof(double), cudaMemcpyDeviceToDevice,
+                             c.stream));
+    s.qh_n = std::min(3, s.qh_n + 1);
+}
+
+// start: the evaluation at the start of a step (the state y_n at t_n), whose solution is
+// recorded; extrap: that solve starts from the extrapolated guess. Runge-Kutta steps do not
+// extrapolate: their previous solve (k4) is already at the new step's time.
+void rhs(Context &c, StepState &s, const double *y, double t, double *f, bem_step_stats &st, bool start,
+         bool extrap) {
     const int64_t N = c.N;
     apply_filter(c, s, y, s.yf.p);
     BEM_CUDA(cudaMemcpyAsync(c.xyz.p, s.yf.p, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
@@ -447,8 +504,10 @@ void rhs(Context &c, StepState &s, const double *y, double t, double *f, bem_ste
             st.mvps += c.stats.last_mvps + 1;
         }
     }
+    if (start && extrap && !learned) extrapolate_guess(c, s, t);
     double res0 = 0.0;
     solve_from(s.q.p, it, rr, res0);
+    if (start) record_start_solution(c, s, t);
     if (learned) {
         mlp_after_solve(c, s.q.p);
         if (mlp_compare(c)) {
@@ -582,6 +641,7 @@ void build_sh_basis(Context &c, int pf, ShBasis &B, int *bad, const double *xyz)
 void step_init(Context &c, const double *phi0_dev, const double *q0_dev, const bem_step_params &sp) {
     if (!c.mesh_ok) fail(BEM_ERR_NOT_BUILT, "no mesh uploaded");
     if (sp.pf < 0 || sp.pf > 11) fail(BEM_ERR_ARG, "pf must be in 0..11");
+    if (sp.guess < 0 || sp.guess > 2) fail(BEM_ERR_ARG, "guess must be 0, 1 or 2");
     if (!(sp.pa > 0.0) && !(sp.dt > 0.0)) fail(BEM_ERR_ARG, "pa must be > 0 unless dt is given");
     StepState &s = state_of(c);
     const int64_t N = c.N, M = c.M;
@@ -591,6 +651,7 @@ void step_init(Context &c, const double *phi0_dev, const double *q0_dev, const b
     s.t = 0.0;
     s.steps = 0;
     s.nhist = 0;
+    s.qh_n = 0;
     for (int i = 0; i < 5; ++i) s.order[i] = i;
     for (auto *b : {&s.y, &s.k1, &s.k2, &s.k3, &s.k4, &s.ytmp, &s.yf, &s.f}) b->resize(4 * N);
     s.hist.resize(5 * 4 * N);
@@ -660,16 +721,16 @@ void step_advance(Context &c, bem_step_stats &st) {
     std::memset(&st, 0, sizeof(st));
     auto slot = [&](int i) { return s.hist.p + (size_t)s.order[i] * n4; };
     if (s.nhist < 5) {
-        rhs(c, s, s.y.p, t, s.k1.p, st);
+        rhs(c, s, s.y.p, t, s.k1.p, st, true, false);
         k_axpy4<<<g, 256, 0, str>>>(n4, 0.5 * dt, s.k1.p, s.y.p, s.ytmp.p);
         BEM_LAUNCH_CHECK();
-        rhs(c, s, s.ytmp.p, t + 0.5 * dt, s.k2.p, st);
+        rhs(c, s, s.ytmp.p, t + 0.5 * dt, s.k2.p, st, false, false);
         k_axpy4<<<g, 256, 0, str>>>(n4, 0.5 * dt, s.k2.p, s.y.p, s.ytmp.p);
         BEM_LAUNCH_CHECK();
-        rhs(c, s, s.ytmp.p, t + 0.5 * dt, s.k3.p, st);
+        rhs(c, s, s.ytmp.p, t + 0.5 * dt, s.k3.p, st, false, false);
         k_axpy4<<<g, 256, 0, str>>>(n4, dt, s.k3.p, s.y.p, s.ytmp.p);
         BEM_LAUNCH_CHECK();
-        rhs(c, s, s.ytmp.p, t + dt, s.k4.p, st);
+        rhs(c, s, s.ytmp.p, t + dt, s.k4.p, st, false, false);
         // push k1 (the RHS at the step start) to the history
         int last = s.order[4];
         for (int i = 4; i > 0; --i) s.order[i] = s.order[i - 1];
@@ -679,7 +740,7 @@ void step_advance(Context &c, bem_step_stats &st) {
         k_rk4_combine<<<g, 256, 0, str>>>(n4, dt, s.k1.p, s.k2.p, s.k3.p, s.k4.p, s.y.p);
         BEM_LAUNCH_CHECK();
     } else {
-        rhs(c, s, s.y.p, t, s.f.p, st);
+        rhs(c, s, s.y.p, t, s.f.p, st, true, true);
         static const double b[6] = {4277.0 / 1440.0, -7923.0 / 1440.0, 9982.0 / 1440.0,
                                     -7298.0 / 1440.0, 2877.0 / 1440.0, -475.0 / 1440.0};
         Six six;

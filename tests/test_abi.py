@@ -72,7 +72,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(bem.bem_step_params) == 56 and ctypes.sizeof(bem.bem_step_stats) == 48
     assert ctypes.sizeof(bem.bem_mlp_summary) == 80
     sp = bem.bem_step_params_default()
-    assert sp.pf == 6 and sp.courant == 0.1 and sp.kappa == 1.4
+    assert sp.pf == 6 and sp.courant == 0.1 and sp.kappa == 1.4 and sp.guess == 2
     assert [bem.bem_phase_name(i) for i in range(bem.BEM_NUM_PHASES)][6] == "m2l"
 
 

@@ -84,3 +84,34 @@ def test_spherical_bubble_against_rayleigh_plesset_mixed_fmm():
     assert rad[-1] > 1.2
     assert np.max(np.abs(np.array(rad) - a_rp)) < 0.02 * a_rp.max()
     ctx.close()
+
+
+def test_extrapolated_guess_same_states_fewer_iterations():
+    """Adams-Bashforth solves that start from the quadratic extrapolation in t of the last three
+    step-start solutions (guess = 2) reach the same states as solves that start from the
+    previous solve's q (guess = 0, the paper's start), in fewer GMRES iterations. The tolerance
+    is the benchmark's 1e-6, above the mixed path's rounding floor near 1e-7."""
+    bem = _bem()
+    mesh, phi = synth.workload_cluster(bubbles=30, level=3, seed=9)
+    res = {}
+    for g in (0, 2):
+        ctx = bem.BemContext(mvp=bem.BEM_MVP_FMM, precision=bem.BEM_PREC_MIXED, p_fmm=14, gmres_tol=1e-6,
+                             gmres_precond=2)
+        ctx.upload_mesh(mesh)
+        bem.bem_step_init(ctx.ctx, phi, bem.bem_step_params_default(pf=6, guess=g))
+        iters = 0
+        for k in range(10):
+            info = bem.bem_step(ctx.ctx)
+            assert info["nonconverged"] == 0
+            if k >= 5:
+                iters += info["gmres_iters"]
+        xyz = np.zeros(3 * mesh.n)
+        ph = np.zeros(mesh.n)
+        bem.bem_step_get_state(ctx.ctx, xyz, ph)
+        res[g] = (iters, xyz.reshape(3, -1).T.copy(), ph)
+        ctx.close()
+    print("AB6 GMRES iterations over 5 steps: guess 0 %d, guess 2 %d" % (res[0][0], res[2][0]))
+    assert res[2][0] < res[0][0]
+    disp = np.linalg.norm(res[0][1] - mesh.xyz)
+    assert np.linalg.norm(res[2][1] - res[0][1]) < 1e-4 * disp
+    assert np.linalg.norm(res[2][2] - res[0][2]) < 1e-5 * np.linalg.norm(res[0][2])
