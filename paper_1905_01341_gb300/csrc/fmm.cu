@@ -594,6 +594,67 @@ __global__ void k_reduce_pairs(int t0, const int32_t *__restrict__ off, const in
     Y[(size_t)t * R * P + e] += s + c;
 }
 
+// FP32 with R*P a multiple of 4: one 64-thread block per target, each thread four consecutive
+// coefficients through 16-byte loads, two product rows in flight. Per coefficient the order and
+// the arithmetic are those of k_reduce_pairs, so the results are the same bit for bit.
+__device__ __forceinline__ void comp_add(float &s, float &c, float v) {
+    const float tt = s + v;
+    const float bp = tt - s;
+    c += (s - (tt - bp)) + (v - bp);
+    s = tt;
+}
+template <int R>
+__global__ void __launch_bounds__(64) k_reduce_pairs4(int t0, const int32_t *__restrict__ off,
+                                                      const int32_t *__restrict__ by, const float *__restrict__ Ypair,
+                                                      int P, float *__restrict__ Y) {
+    const int t = t0 + blockIdx.x;
+    const int a = off[t], b = off[t + 1];
+    if (a == b) return;
+    const int rp4 = R * P / 4;
+    const float4 *Y4 = reinterpret_cast<const float4 *>(Ypair);
+    for (int e = threadIdx.x; e < rp4; e += blockDim.x) {
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+        auto add = [&](const float4 v) {
+            comp_add(s0, c0, v.x);
+            comp_add(s1, c1, v.y);
+            comp_add(s2, c2, v.z);
+            comp_add(s3, c3, v.w);
+        };
+        int k = a;
+        for (; k + 1 < b; k += 2) {
+            const float4 v0 = Y4[(size_t)by[k] * rp4 + e];
+            const float4 v1 = Y4[(size_t)by[k + 1] * rp4 + e];
+            add(v0);
+            add(v1);
+        }
+        if (k < b) add(Y4[(size_t)by[k] * rp4 + e]);
+        float4 *dst = reinterpret_cast<float4 *>(Y) + (size_t)t * rp4 + e;
+        float4 y = *dst;
+        y.x += s0 + c0;
+        y.y += s1 + c1;
+        y.z += s2 + c2;
+        y.w += s3 + c3;
+        *dst = y;
+    }
+}
+
+// Y[t] += sum over the pairs of t, for the targets t0 .. t0 + ntg - 1
+template <class T, int R>
+void launch_reduce_pairs(int t0, int ntg, const int32_t *off, const int32_t *by, const T *Ypair, int P, T *Y,
+                         cudaStream_t st) {
+    if (ntg <= 0) return;
+    if constexpr (sizeof(T) == 4) {
+        if ((R * P) % 4 == 0) {
+            k_reduce_pairs4<R><<<ntg, 64, 0, st>>>(t0, off, by, Ypair, P, Y);
+            BEM_LAUNCH_CHECK();
+            return;
+        }
+    }
+    dim3 rg((unsigned)ntg, div_up(R * P, 128));
+    k_reduce_pairs<T, R><<<rg, 128, 0, st>>>(t0, off, by, Ypair, P, Y);
+    BEM_LAUNCH_CHECK();
+}
+
 // ------------------------------------------------------------------------------ L2P
 // One warp per leaf: leaves hold about 70-150 points, and a 128-thread block left most of its
 // lanes idle on the second pass over a leaf's points.
@@ -844,7 +905,6 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
             ypair = (T *)c.ypair32.p;
         }
     }
-    const int red_blocks_y = div_up(R * P, 128);
     // M2M upward, levels L -> 2: per-pair products, then each parent sums its children
     for (int l = L; l >= 3; --l) {
         PhaseScope ps(c, PH_M2M, fs);
@@ -854,9 +914,7 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
         k_xlat<T, R, kStorePair><<<grid, XT_THREADS, xt_smem<T>(), fs>>>(m2m, P, c.m2l_chunks.p + up_first[l],
                                                                          t.up_child.p, t.up_parent.p, mp, ypair);
         BEM_LAUNCH_CHECK();
-        dim3 rg((unsigned)t.nb[l - 1], red_blocks_y);
-        k_reduce_pairs<T, R><<<rg, 128, 0, fs>>>(t.base[l - 1], t.up_par_off.p, t.up_by_par.p, ypair, P, mp);
-        BEM_LAUNCH_CHECK();
+        launch_reduce_pairs<T, R>(t.base[l - 1], t.nb[l - 1], t.up_par_off.p, t.up_by_par.p, ypair, P, mp, fs);
     }
     // M2L, all levels at once, then each target sums its sources
     if (nm2l_chunks) {
@@ -890,10 +948,7 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
             BEM_LAUNCH_CHECK();
         }
         PhaseScope ps(c, PH_M2L_REDUCE, fs);
-        int ntg = t.nbox - t.base[2];
-        dim3 rg((unsigned)ntg, red_blocks_y);
-        k_reduce_pairs<T, R><<<rg, 128, 0, fs>>>(t.base[2], t.m2l_tgt_off.p, t.m2l_by_tgt.p, ypair, P, lc);
-        BEM_LAUNCH_CHECK();
+        launch_reduce_pairs<T, R>(t.base[2], t.nbox - t.base[2], t.m2l_tgt_off.p, t.m2l_by_tgt.p, ypair, P, lc, fs);
     }
     // L2L downward, levels 3 -> L: every child has exactly one parent, so it adds in place
     for (int l = 3; l <= L; ++l) {
