@@ -226,9 +226,10 @@ def run_reference(args):
     mesh, phi = workload(args)
     # The oracle solve at 3.21M unknowns is ~1e13 pair evaluations per product; each step is
     # a bounded sample: the direct product at 4 sqrt(N) receivers, scaled to the step's
-    # products as the GPU path counts them for an AB6 step at this size (4 for the diagonals,
-    # 1 for the right-hand side, 20 GMRES iterations and 3 true-residual products).
-    n_mvps = 4 + 1 + 20 + 3
+    # products as the GPU path counts them for an AB6 step at this size with the default solver
+    # settings (4 for the diagonals, 1 for the right-hand side, 11 GMRES iterations from the
+    # extrapolated guess and 3 initial/true-residual products).
+    n_mvps = 4 + 1 + 11 + 3
     n_recv = 4 * int(math.isqrt(mesh.n))
     times = []
     info = None
