@@ -19,12 +19,16 @@
 // Data movement: K advances 16 at a time (one kind::f16 MMA); each 16-wide K step is one
 // pipeline stage holding A (3 pieces x tiles x 128 x 16) and B (3 pieces x N_pad x 16) in
 // the canonical K-major layout without swizzle (8-row x 16-byte core matrices, K-adjacent core
-// matrices 128 B apart, 8-row groups 256 B apart). All threads fill stages with cp.async
-// (16-byte copies; rows past the chunk read as zeros), four stages deep; one elected thread
-// issues the MMAs of a stage as soon as it has landed and commits them to the stage's
-// mbarrier, which releases the stage for refilling. Every wait is bounded: one that runs out
-// sets an error flag and the block skips ahead, waiting (bounded) for its MMAs in flight
-// before it releases its tensor memory.
+// matrices 128 B apart, 8-row groups 256 B apart). The block is warp-specialised: warps 1-7
+// fill the stages with cp.async (16-byte copies; rows past the chunk read as zeros), five
+// stages deep where they fit in shared memory, else four, and let each stage's "full"
+// mbarrier count their copies' arrival (cp.async.mbarrier.arrive.noinc); one thread of warp 0
+// waits on "full", issues the stage's MMAs and commits them to the stage's "empty" mbarrier,
+// which releases the stage for refilling. No block-wide barrier runs inside the K loop. Every
+// wait is bounded: one that runs out raises a shared abort flag that stops the other side at
+// its next wait, sets the error flag, and the block waits (bounded) for its MMAs in flight
+// before it releases its tensor memory. The same kernel serves the 4-RHS diagonal product
+// (R = 4, N_pad up to 256).
 #include <cuda_bf16.h>
 
 #include "internal.h"
