@@ -89,7 +89,7 @@ def parse():
                          "3 (default) as 2 for bubbles of at most 2562 vertices, 0 none")
     ap.add_argument("--overlap", type=int, default=1, help="1 = near field on its own stream, overlapping the far field")
     ap.add_argument("--guess", type=int, default=2,
-                    help="step-start GMRES guess: 0 previous q (the paper), 1/2 linear/quadratic extrapolation in t")
+                    help="AB6 GMRES start: 0 previous q (the paper), 1/2/3 extrapolation in t of that degree")
     ap.add_argument("--pa", type=float, default=0.5, help="acoustic amplitude Pa/p0")
     ap.add_argument("--pf", type=int, default=6, help="shape-filter bandwidth")
     ap.add_argument("--fp64-compare", type=int, default=1, help="also time FP64 right-hand sides (0 = skip)")

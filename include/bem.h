@@ -230,13 +230,13 @@ typedef struct {
     double dt;       /* > 0: fixed step used instead of the Courant rule. Default 0              */
     int32_t pf;      /* shape-filter bandwidth p_f: degrees 0..p_f-1. 0 = no filter. Default 6  */
     int32_t guess;   /* initial guess of each Adams-Bashforth step's solve: 0 = the q of the
-                        previous solve (the paper, Sections 3.5, 3.8); k = 1 or 2 = the
+                        previous solve (the paper, Sections 3.5, 3.8); k = 1, 2 or 3 = the
                         polynomial of degree k in t through the solutions at the last k + 1
                         step starts, evaluated at the new step's time. Runge-Kutta steps
                         always start from the previous solve (their k4 solve is at the new
                         step's time). Only the starting point of GMRES changes: every solve
                         still runs to gmres_tol. Not used while the learned guess is active.
-                        Default 2.                                                            */
+                        Default 2 (degree 3 extrapolates the solves' rounding further).       */
 } bem_step_params;
 
 typedef struct {

@@ -20,6 +20,9 @@
 
 namespace bem {
 
+constexpr int kGuessMax = 3;        // highest degree of the extrapolated initial guess
+constexpr int kQh = kGuessMax + 1;  // step-start solutions kept for it
+
 struct StepState {
     bool ready = false;
     bem_step_params sp{};
@@ -36,11 +39,11 @@ struct StepState {
     DevBuf<double> x0;  // r at t = 0 (SoA)
     DevBuf<double> vt, H;
     bem_step_stats last{};
-    // q of the last three step-start solves (newest first through qh_order) and their times,
-    // for the extrapolated initial guess
-    DevBuf<double> qh;  // [3][N]
-    double qh_time[3] = {0.0, 0.0, 0.0};  // per slot
-    int qh_order[3] = {0, 1, 2};
+    // q of the last kQh step-start solves (newest first through qh_order) and their times, for
+    // the extrapolated initial guess
+    DevBuf<double> qh;  // [kQh][N]
+    double qh_time[kQh] = {};  // per slot
+    int qh_order[kQh] = {0, 1, 2, 3};
     int qh_n = 0;
 };
 
@@ -414,15 +417,17 @@ void apply_filter(Context &c, StepState &s, const double *X, double *Y) {
     BEM_LAUNCH_CHECK();
 }
 
-// f = filtered right-hand side at state y (both [4N]), time t. Updates s.q.
-// out = sum_j w[j] a_j over the first n of three vectors
-__global__ void k_combine3(int64_t N, int n, double w0, double w1, double w2, const double *__restrict__ a0,
-                           const double *__restrict__ a1, const double *__restrict__ a2, double *__restrict__ out) {
+// out = sum_{j < n} w[j] a[j][.]
+struct GuessTerms {
+    double w[kQh];
+    const double *a[kQh];
+    int n;
+};
+__global__ void k_combine(int64_t N, GuessTerms cb, double *__restrict__ out) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N) return;
-    double v = w0 * a0[i];
-    if (n > 1) v += w1 * a1[i];
-    if (n > 2) v += w2 * a2[i];
+    double v = cb.w[0] * cb.a[0][i];
+    for (int j = 1; j < cb.n; ++j) v += cb.w[j] * cb.a[j][i];
     out[i] = v;
 }
 
@@ -431,8 +436,8 @@ __global__ void k_combine3(int64_t N, int n, double w0, double w1, double w2, co
 void extrapolate_guess(Context &c, StepState &s, double t) {
     const int k = std::min(s.sp.guess, s.qh_n - 1);
     if (k < 1) return;
-    double w[3] = {0.0, 0.0, 0.0};
-    const double *a[3] = {nullptr, nullptr, nullptr};
+    GuessTerms cb{};
+    cb.n = k + 1;
     for (int j = 0; j <= k; ++j) {
         const double tj = s.qh_time[s.qh_order[j]];
         double v = 1.0;
@@ -441,27 +446,26 @@ void extrapolate_guess(Context &c, StepState &s, double t) {
                 const double tm = s.qh_time[s.qh_order[m]];
                 v *= (t - tm) / (tj - tm);
             }
-        w[j] = v;
-        a[j] = s.qh.p + (size_t)s.qh_order[j] * c.N;
+        cb.w[j] = v;
+        cb.a[j] = s.qh.p + (size_t)s.qh_order[j] * c.N;
     }
-    k_combine3<<<div_up(c.N, 256), 256, 0, c.stream>>>(c.N, k + 1, w[0], w[1], w[2], a[0], a[1] ? a[1] : a[0],
-                                                       a[2] ? a[2] : a[0], s.q.p);
+    k_combine<<<div_up(c.N, 256), 256, 0, c.stream>>>(c.N, cb, s.q.p);
     BEM_LAUNCH_CHECK();
 }
 
-// record s.q as the solution at step-start time t (the oldest of three is dropped)
+// record s.q as the solution at step-start time t (the oldest of kQh is dropped)
 void record_start_solution(Context &c, StepState &s, double t) {
-    s.qh.resize(3 * (size_t)c.N);
-    const int last = s.qh_order[2];
-    s.qh_order[2] = s.qh_order[1];
-    s.qh_order[1] = s.qh_order[0];
+    s.qh.resize(kQh * (size_t)c.N);
+    const int last = s.qh_order[kQh - 1];
+    for (int j = kQh - 1; j > 0; --j) s.qh_order[j] = s.qh_order[j - 1];
     s.qh_order[0] = last;
     s.qh_time[last] = t;
     BEM_CUDA(cudaMemcpyAsync(s.qh.p + (size_t)last * c.N, s.q.p, c.N * sizeof(double), cudaMemcpyDeviceToDevice,
                              c.stream));
-    s.qh_n = std::min(3, s.qh_n + 1);
+    s.qh_n = std::min(kQh, s.qh_n + 1);
 }
 
+// f = filtered right-hand side at state y (both [4N]), time t. Updates s.q.
 // start: the evaluation at the start of a step (the state y_n at t_n), whose solution is
 // recorded; extrap: that solve starts from the extrapolated guess. Runge-Kutta steps do not
 // extrapolate: their previous solve (k4) is already at the new step's time.
@@ -641,7 +645,7 @@ void build_sh_basis(Context &c, int pf, ShBasis &B, int *bad, const double *xyz)
 void step_init(Context &c, const double *phi0_dev, const double *q0_dev, const bem_step_params &sp) {
     if (!c.mesh_ok) fail(BEM_ERR_NOT_BUILT, "no mesh uploaded");
     if (sp.pf < 0 || sp.pf > 11) fail(BEM_ERR_ARG, "pf must be in 0..11");
-    if (sp.guess < 0 || sp.guess > 2) fail(BEM_ERR_ARG, "guess must be 0, 1 or 2");
+    if (sp.guess < 0 || sp.guess > kGuessMax) fail(BEM_ERR_ARG, "guess must be in 0..3");
     if (!(sp.pa > 0.0) && !(sp.dt > 0.0)) fail(BEM_ERR_ARG, "pa must be > 0 unless dt is given");
     StepState &s = state_of(c);
     const int64_t N = c.N, M = c.M;
