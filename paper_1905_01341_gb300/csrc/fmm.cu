@@ -396,7 +396,8 @@ __global__ void __launch_bounds__(256) k_p2m(int p, int nleaf, const int32_t *__
 
 // ------------------------------------------------------------------------------ translations
 // Class-grouped product: for every pair (src, tgt) of a chunk, Y[tgt] += T_cls X[src], as a
-// tiled GEMM (64 output rows x 64 columns per block; a column is one pair and one RHS).
+// tiled GEMM (128 output rows x 128 columns per block in FP32, 64 x 64 in FP64; a column is one
+// pair and one RHS).
 constexpr int XT_K = 16, XT_THREADS = 256;
 
 // MODE kStorePair: Y[pair] = T X[src] (one slot per pair, summed later in a fixed order).
@@ -422,8 +423,8 @@ __device__ __forceinline__ void vec_load(const double *p, double *v) {
 }
 
 // outputs per thread and block: 8 x 8 per thread in FP32 (a 128 x 128 tile: 16 FMAs per shared
-// load, and each operator tile serves 128 (pair, rhs) columns), 4 x 4 in FP64 (64 x 64, keeping
-// the double-buffered tiles under the static shared-memory limit)
+// load, and each operator tile serves 128 (pair, rhs) columns), 4 x 4 in FP64 (64 x 64, which
+// keeps two blocks of three stages per SM)
 template <class T>
 __host__ __device__ constexpr int xt_rt() { return sizeof(T) == 4 ? 8 : 4; }
 template <class T>
