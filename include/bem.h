@@ -14,8 +14,9 @@
  *   - the combined product (f L + g M) X (Eq. (3.27)) by the fast multipole method
  *     (Section 3.7: octree to uniform depth, multipole/local expansions truncated at degree
  *     p_fmm - 1) or by the direct O(N^2) sum (Section 3.9, "GPU" brute force);
- *   - the Dirichlet solve L q = b, b = -phi/2 + M phi (Eqs. (3.1)-(3.2)) by unpreconditioned
- *     GMRES started from a caller-given guess (Section 3.8).
+ *   - the Dirichlet solve L q = b, b = -phi/2 + M phi (Eqs. (3.1)-(3.2)) by GMRES started from
+ *     a caller-given guess (Section 3.8): unpreconditioned as in the paper, or right-
+ *     preconditioned (bem_params.gmres_precond); every variant stops on the same true residual.
  *
  * Conventions (all entry points):
  *   - Every function returns a bem_status (0 = BEM_OK). No C++ exception crosses the ABI.
@@ -51,7 +52,7 @@ typedef enum {
     BEM_ERR_NOCONV = 4,    /* GMRES hit maxit; q holds the last iterate, relres is set        */
     BEM_ERR_TIMEOUT = 5,   /* a bounded device wait ran out                                   */
     BEM_ERR_CUDA = 6,      /* CUDA runtime error                                              */
-    BEM_ERR_NAN = 7,       /* non-finite value in a result                                    */
+    BEM_ERR_NAN = 7,       /* non-finite vertex coordinate (fmm_build) or value in a result   */
     BEM_ERR_NOMEM = 8      /* device allocation failed                                        */
 } bem_status;
 
@@ -186,7 +187,8 @@ int bem_mesh_update_xyz(void *ctx, const double *xyz);
 /* Section 3.2 and 3.7: vertex weights and normals (Eq. (ns1)), the octree (bounding cube,
  * Morton keys, radix sort, level boxes, neighbour and M2L lists), the FMM translation
  * operators, and the singular diagonals (Eqs. (s3), (s5)) from one 4-RHS product.
- * Returns BEM_ERR_MESH for an isolated vertex or a zero area-weighted normal. */
+ * Returns BEM_ERR_NAN for a non-finite vertex coordinate (checked first) or diagonal, and
+ * BEM_ERR_MESH for an isolated vertex or a zero area-weighted normal. */
 int fmm_build(void *ctx);
 
 /* Eq. (3.27): out = f L xL + g M xM (diagonals included). xL may be NULL when f == 0 and
@@ -329,10 +331,14 @@ int bem_mlp_info(void *ctx, bem_mlp_summary *out);
  * It allocates nothing: its only scratch, the hi + lo FP32 split of the coordinates, lives in
  * a file-scope device array sized for N <= 262144 (6 MiB, held by every GPU that loads the
  * library until the process exits). N outside 2..262144 returns BEM_ERR_ARG with a message in
- * bem_last_error(NULL). The first call on a device looks up that array's device address, with
- * that device current; make this first call before any stream capture. Every call shares the
- * array and overwrites it, so calls that overlap on the GPU (different streams, or different
- * host threads) race. */
+ * bem_last_error(NULL). Every array must be device memory of the current device (or managed
+ * memory); a host or unregistered pointer returns BEM_ERR_ARG before anything is launched (the
+ * library cannot check lengths: the caller guarantees them). The first call on a device looks
+ * up that array's device address, with that device current (safe from several host threads);
+ * make this first call before any stream capture. The address is cached for the process, so do
+ * not call this entry point on a device after cudaDeviceReset. Every call shares the array and
+ * overwrites it, so calls that overlap on the GPU (different streams, or different host
+ * threads) race. */
 int bem_apply_direct_noalloc(int64_t N, const double *xyz, const double *s, const double *n, const double *ldiag,
                              const double *mdiag, double f, const double *xL, double g, const double *xM,
                              double *out, void *stream);

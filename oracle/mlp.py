@@ -13,6 +13,14 @@ variant keeps that as the fallback and predicts a better start from per-bubble d
   guess     q0_m = q_prev,m + G (y), i.e. the network predicts the change of q's coefficients;
   loss      mean over bubbles of |y - (c(q_m) - c(q_prev,m))|^2 / 2.
 Row vectors: a batch F [B x d_in] maps to Y [B x d_out] with Y = relu(...) @ W^T + b.
+
+The learned part fixes its arithmetic as BF16 weights with FP32 accumulation: every matrix
+product takes BF16 operands. `forward_bf16` and `loss_and_grads_bf16` are the same network
+with each product's operands rounded to BF16 (round to nearest, ties to even) and the sums,
+biases, losses and bias gradients kept in full precision: the weights, the features, the
+hidden activations after the relu, and the back-propagated errors where they enter a product.
+They are the reference for a BF16 implementation; `forward` and `loss_and_grads` (no rounding)
+measure what the BF16 rounding itself costs.
 """
 from __future__ import annotations
 
@@ -40,6 +48,47 @@ def forward(params, F):
         h = np.maximum(z, 0.0) if i + 1 < len(params) else z
         acts.append(h)
     return h, (acts, pre)
+
+
+def bf16(x):
+    """Nearest bfloat16 value (sign, 8 exponent bits, 8 significant bits), ties to even, of
+    the float32 value of x: the float32 word rounded to its upper 16 bits. Returns float64."""
+    f = np.ascontiguousarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward_bf16(params, F, rnd=bf16):
+    """forward() with BF16 operands in every product (see the module docstring): layer i
+    computes z = rnd(h) @ rnd(W_i)^T + b_i and passes rnd(relu(z)) on. Returns (Y, cache)
+    with cache = (the rounded layer inputs, the pre-activations)."""
+    acts = [rnd(F)]
+    pre = []
+    for i, (W, b) in enumerate(params):
+        z = acts[-1] @ rnd(W).T + b
+        pre.append(z)
+        if i + 1 < len(params):
+            acts.append(rnd(np.maximum(z, 0.0)))
+    return pre[-1], (acts, pre)
+
+
+def loss_and_grads_bf16(params, F, T, rnd=bf16):
+    """loss_and_grads() with BF16 operands in every product: the error g of a layer's output
+    enters dW_i = rnd(g)^T a_i and the back-propagated error rnd(g) rnd(W_i) rounded; the bias
+    gradient sums the unrounded g."""
+    Y, (acts, pre) = forward_bf16(params, F, rnd)
+    B = F.shape[0]
+    L = 0.5 * float(np.sum((Y - T) ** 2)) / B
+    g = (Y - T) / B
+    grads = [None] * len(params)
+    for i in range(len(params) - 1, -1, -1):
+        W, _ = params[i]
+        gr = rnd(g)
+        grads[i] = [gr.T @ acts[i], g.sum(axis=0)]
+        if i > 0:
+            g = (gr @ rnd(W)) * (pre[i - 1] > 0.0)
+    return L, grads
 
 
 def loss_and_grads(params, F, T):

@@ -349,10 +349,36 @@ def bem_step_get_state(ctx, xyz=None, phi=None, q=None) -> float:
     return float(t.value)
 
 
+def _noalloc_arg(name, x, count):
+    """A float64 CUDA tensor of the current device with at least `count` elements: the C entry
+    point takes raw device pointers and cannot check lengths."""
+    import torch
+
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise BemError(BEM_ERR_ARG, "bem_apply_direct_noalloc: %s must be a CUDA tensor" % name)
+    if x.device.index != torch.cuda.current_device():
+        raise BemError(BEM_ERR_ARG, "bem_apply_direct_noalloc: %s is on another device" % name)
+    if x.dtype != torch.float64 or not x.is_contiguous():
+        raise BemError(BEM_ERR_ARG, "bem_apply_direct_noalloc: %s must be contiguous float64" % name)
+    if x.numel() < count:
+        raise BemError(BEM_ERR_ARG, "bem_apply_direct_noalloc: %s has %d elements, needs %d" % (name, x.numel(), count))
+    return x
+
+
 def bem_apply_direct_noalloc(N, xyz, s, n, ldiag, mdiag, f, xL, g, xM, out, stream=0) -> None:
-    """Allocation-free direct product on caller-owned device arrays (see include/bem.h)."""
+    """Allocation-free direct product on caller-owned device arrays (see include/bem.h): every
+    array a contiguous float64 CUDA tensor of the current device, xyz and n with 3N elements,
+    the others with N (xL may be None when f == 0, xM when g == 0)."""
+    N = int(N)
+    for name, x, cnt in (("xyz", xyz, 3 * N), ("s", s, N), ("n", n, 3 * N), ("ldiag", ldiag, N),
+                         ("mdiag", mdiag, N), ("out", out, N)):
+        _noalloc_arg(name, x, cnt)
+    if float(f) != 0.0:
+        _noalloc_arg("xL", xL, N)
+    if float(g) != 0.0:
+        _noalloc_arg("xM", xM, N)
     handle = stream if isinstance(stream, int) else stream.cuda_stream
-    rc = lib().bem_apply_direct_noalloc(int(N), _ptr(xyz, np.float64), _ptr(s, np.float64), _ptr(n, np.float64),
+    rc = lib().bem_apply_direct_noalloc(N, _ptr(xyz, np.float64), _ptr(s, np.float64), _ptr(n, np.float64),
                                         _ptr(ldiag, np.float64), _ptr(mdiag, np.float64), float(f),
                                         _ptr(xL, np.float64), float(g), _ptr(xM, np.float64),
                                         _ptr(out, np.float64), ctypes.c_void_p(handle))

@@ -173,6 +173,17 @@ void check_params(const bem_params &p) {
 
 }  // namespace
 
+void launch_add_diag(int64_t N, double f, const double *xL, double g, const double *xM, const double *ld,
+                     const double *md, double *out, cudaStream_t st) {
+    k_add_diag<<<div_up(N, 256), 256, 0, st>>>(N, f, xL, g, xM, ld, md, out);
+    BEM_LAUNCH_CHECK();
+}
+
+void launch_split_hilo(int64_t n, const double *x, float *hi, float *lo, cudaStream_t st) {
+    k_split<<<div_up(n, 256), 256, 0, st>>>(n, x, hi, lo);
+    BEM_LAUNCH_CHECK();
+}
+
 // out = f (L_off + diag(Ldiag)) xL + g (M_off + diag(Mdiag)) xM, all device pointers.
 void apply_full(Context &c, double f, const double *xL, double g, const double *xM, double *out) {
     double fa[1] = {f}, ga[1] = {g};
@@ -180,8 +191,7 @@ void apply_full(Context &c, double f, const double *xL, double g, const double *
     const double *xm[1] = {xM};
     double *o[1] = {out};
     offdiag_apply(c, 1, fa, xl, ga, xm, o, c.prm.precision);
-    k_add_diag<<<div_up(c.N, 256), 256, 0, c.stream>>>(c.N, f, xL, g, xM, c.ldiag.p, c.mdiag.p, out);
-    BEM_LAUNCH_CHECK();
+    launch_add_diag(c.N, f, xL, g, xM, c.ldiag.p, c.mdiag.p, out, c.stream);
 }
 
 // Octree depth autotuner (leaf_target = 0): times one single-layer product at the depth the
@@ -245,6 +255,19 @@ void build_all(Context &c) {
     BEM_CUDA(cudaEventRecord(e0, c.stream));
     c.built = false;
     const int64_t N = c.N;
+    {
+        // a non-finite coordinate (an uploaded NaN, or a time step that blew up) is reported as
+        // such before any geometry or key is formed from it
+        DevBuf<int> badx;
+        badx.resize(1);
+        BEM_CUDA(cudaMemsetAsync(badx.p, 0, sizeof(int), c.stream));
+        k_check_finite<<<div_up(3 * N, 256), 256, 0, c.stream>>>(3 * N, c.xyz.p, badx.p);
+        BEM_LAUNCH_CHECK();
+        int hx = 0;
+        BEM_CUDA(cudaMemcpyAsync(&hx, badx.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+        BEM_CUDA(cudaStreamSynchronize(c.stream));
+        if (hx) fail(BEM_ERR_NAN, "non-finite vertex coordinate");
+    }
     if (c.points_only) {  // unit weights, normals along z (unused: products use f only)
         c.s.resize(N);
         c.nrm.resize(3 * N);
@@ -277,8 +300,7 @@ void build_all(Context &c) {
     } else {
         c.dir_hi.resize(3 * N);
         c.dir_lo.resize(3 * N);
-        k_split<<<div_up(3 * N, 256), 256, 0, c.stream>>>(3 * N, c.xyz.p, c.dir_hi.p, c.dir_lo.p);
-        BEM_LAUNCH_CHECK();
+        launch_split_hilo(3 * N, c.xyz.p, c.dir_hi.p, c.dir_lo.p, c.stream);
         c.stats.p2p_pairs = N * (N - 1);
         c.stats.m2l_pairs = 0;
         c.stats.levels = 0;

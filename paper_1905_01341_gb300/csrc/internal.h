@@ -397,6 +397,11 @@ inline PhaseScope::~PhaseScope() {
 }
 
 // bem_api.cu
+// out[i] += f ld[i] xL[i] + g md[i] xM[i] (the identity diagonals of Eqs. (s3), (s5))
+void launch_add_diag(int64_t N, double f, const double *xL, double g, const double *xM, const double *ld,
+                     const double *md, double *out, cudaStream_t st);
+// hi[i] = fp32(x[i]), lo[i] = fp32(x[i] - hi[i]) (coordinates of the FP32 direct product)
+void launch_split_hilo(int64_t n, const double *x, float *hi, float *lo, cudaStream_t st);
 void apply_full(Context &c, double f, const double *xL, double g, const double *xM, double *out);
 void build_all(Context &c);
 void solve_internal(Context &c, const double *phi, double *q, int *it, double *rr);

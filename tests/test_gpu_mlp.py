@@ -67,20 +67,33 @@ def test_forward_and_gradients_match_reference():
     T = rng.standard_normal((B, dims[4])) * 0.3
     Y = np.zeros((B, dims[4]))
     bem.bem_mlp_forward(ctx.ctx, F, Y)
-    Yref, _ = omlp.forward(params, F)
-    assert np.linalg.norm(Y - Yref) / np.linalg.norm(Yref) < 2e-2  # BF16 operands, FP32 sums
+    # the reference takes the products' operands in BF16, as the network's arithmetic is
+    # stated (BF16 weights, features, activations and back-propagated errors; FP32 sums on the
+    # device, FP64 in the reference): the two agree to the sums' rounding
+    Yref, _ = omlp.forward_bf16(params, F)
+    ef = np.linalg.norm(Y - Yref) / np.linalg.norm(Yref)
     g = np.zeros(info["num_params"])
     loss = bem.bem_mlp_loss_grad(ctx.ctx, F, T, g)
-    Lref, gref = omlp.loss_and_grads(params, F, T)
-    assert abs(loss - Lref) / Lref < 2e-2
+    Lref, gref = omlp.loss_and_grads_bf16(params, F, T)
+    el = abs(loss - Lref) / Lref
     gflat = _flatten(gref)
-    assert np.linalg.norm(g - gflat) / np.linalg.norm(gflat) < 2e-2
-    # each layer's weight gradient separately (a transposed operand in one product would give
-    # an O(1) error here); BF16 rounding of activations and back-propagated errors at every
-    # layer leaves a few per cent
-    errs = [np.linalg.norm(a[0] - b[0]) / np.linalg.norm(b[0]) for a, b in zip(_unflatten(g, dims), gref)]
-    print("per-layer weight-gradient errors:", ["%.3g" % e for e in errs])
-    assert max(errs) < 1e-1
+    eg = np.linalg.norm(g - gflat) / np.linalg.norm(gflat)
+    # each layer's weight and bias gradient separately (a transposed operand in one product
+    # would give an O(1) error here)
+    gl = _unflatten(g, dims)
+    ew = [np.linalg.norm(a[0] - b[0]) / np.linalg.norm(b[0]) for a, b in zip(gl, gref)]
+    eb = [np.linalg.norm(a[1] - b[1]) / np.linalg.norm(b[1]) for a, b in zip(gl, gref)]
+    # for the record: the same network without rounding (the BF16 rounding's own cost)
+    Y64, _ = omlp.forward(params, F)
+    _, g64 = omlp.loss_and_grads(params, F, T)
+    print("vs BF16-operand reference: forward %.3g, loss %.3g, gradient %.3g, per-layer W %s, b %s; "
+          "vs FP64 without rounding: forward %.3g, per-layer W %s" % (
+              ef, el, eg, ["%.3g" % e for e in ew], ["%.3g" % e for e in eb],
+              np.linalg.norm(Y - Y64) / np.linalg.norm(Y64),
+              ["%.3g" % (np.linalg.norm(a[0] - b[0]) / np.linalg.norm(b[0])) for a, b in zip(gl, g64)]))
+    tol = 1e-2  # relative L2, the contract for the BF16 network's forward pass, loss and gradients
+    assert ef < tol and el < tol and eg < tol
+    assert max(ew) < tol and max(eb) < tol
     ctx.close()
 
 

@@ -257,7 +257,7 @@ def test_residual_history_and_mvp_count():
 
 @pytest.mark.parametrize("p", [8, 14, 16])
 def test_tensor_core_m2l_matches_cuda_core_m2l(p):
-    """The tcgen05 M2L (three-piece TF32 split, FP32 accumulation) against the FP32 CUDA-core
+    """The tcgen05 M2L (three-piece BF16 split of both operands, FP32 accumulation) against the FP32 CUDA-core
     M2L: measured against the FP64 FMM at the same p (same truncation, so only arithmetic
     error is left), the tensor-core product is as accurate as the CUDA-core one, and both stay
     within the mixed-precision bound of the oracle."""

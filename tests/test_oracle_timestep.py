@@ -148,3 +148,30 @@ def test_spherical_bubble_follows_rayleigh_plesset():
     err = np.max(np.abs(np.array(radii) - a_rp))
     assert radii[-1] > 1.1  # it grew under the rarefaction
     assert err < 0.02 * np.max(a_rp)
+
+
+@pytest.mark.parametrize("pf", [0, 4])
+def test_dphi_dt_on_a_sphere_converges_to_the_closed_form(pf):
+    # Eq. (3.15) with alpha = -1 and v = n q + v_t (v_t normal to n) reduces to
+    #   dphi/dt = q^2/2 - |v_t|^2/2 - (p_g - 2 sigma H) + F(t).
+    # On a sphere of radius R with phi = cos(theta) at t = 0: the exterior Dirichlet solution
+    # gives q = -2 cos(theta)/R, the surface gradient gives |v_t|^2 = sin(theta)^2/R^2,
+    # p_g = p_g0 = 1 + 2 sigma/a0 and F(0) = 1, so as h -> 0 (H -> 1/R, a0 -> R)
+    #   dphi/dt -> 2 cos(theta)^2/R^2 - sin(theta)^2/(2 R^2).
+    # A sign or factor slip in the alpha v_t . v term changes the limit by O(|v_t|^2) = O(1).
+    # Both sides of the time step are band-limited (degrees 1 and 2), so the shape filter
+    # (p_f = 4 keeps degrees 0..3) leaves them unchanged.
+    R = 1.3
+    errs = []
+    for lev in (2, 3, 4, 5) if pf == 0 else (2, 3, 4):
+        m = synth.sphere_bubble(lev, R)
+        sysm = ts.BubbleSystem(m.xyz, m.tri, m.vert_off, m.tri_off, ts.Physics(pf=pf, gmres_tol=1e-12))
+        ct = m.xyz[:, 2] / np.linalg.norm(m.xyz, axis=1)
+        _, dphi, q = sysm.rhs(m.xyz, ct.copy(), 0.0, None)
+        assert np.max(np.abs(q + 2.0 * ct / R)) < 0.05
+        exact = (2.0 * ct ** 2 - 0.5 * (1.0 - ct ** 2)) / R ** 2
+        errs.append(np.max(np.abs(dphi - exact)))
+    print("dphi/dt errors over levels:", ["%.3g" % e for e in errs])
+    # measured: 7.1e-2, 2.0e-2, 5.6e-3, 1.9e-3 (about O(h^1.7))
+    assert all(a / b > 2.5 for a, b in zip(errs[:-1], errs[1:]))
+    assert errs[-1] < (2.5e-3 if pf == 0 else 7e-3)

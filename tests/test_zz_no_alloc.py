@@ -6,6 +6,8 @@ framework, a latency-critical loop) use the allocation-free entry point; it must
 result as the regular path. This file is collected last so that a failure here does not hide
 the other tests, and it runs on its own too.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -48,8 +50,56 @@ def test_noalloc_direct_product_matches_context_product_twice():
         bem.bem_apply_direct_noalloc(N, xyz, s, n, ld, md, f, xL, g, xM, out, stream)
         torch.cuda.synchronize()
         assert rel(out.cpu().numpy(), ref.cpu().numpy()) <= 1e-12
-    # sizes beyond the fixed scratch are rejected with a clear error
-    with pytest.raises(bem.BemError) as e:
-        bem.bem_apply_direct_noalloc(262145, xyz, s, n, ld, md, 1.0, xL, 0.0, None, out, stream)
-    assert e.value.code == bem.BEM_ERR_ARG and "262144" in str(e.value)
+    # sizes beyond the fixed scratch are rejected by the C entry point with a clear error,
+    # before any pointer is used
+    P = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    rc = bem.lib().bem_apply_direct_noalloc(262145, P(xyz), P(s), P(n), P(ld), P(md), 1.0, P(xL), 0.0, None,
+                                            P(out), ctypes.c_void_p(stream.cuda_stream))
+    assert rc == bem.BEM_ERR_ARG and "262144" in bem.bem_last_error(None)
+    # a host array is rejected by the C entry point (nothing is launched)
+    host = np.zeros(N)
+    rc = bem.lib().bem_apply_direct_noalloc(N, P(xyz), P(s), P(n), P(ld), P(md), 1.0,
+                                            ctypes.c_void_p(host.ctypes.data), 0.0, None, P(out),
+                                            ctypes.c_void_p(stream.cuda_stream))
+    assert rc == bem.BEM_ERR_ARG and "xL" in bem.bem_last_error(None)
+    # and by the binding, as are short tensors
+    with pytest.raises(bem.BemError):
+        bem.bem_apply_direct_noalloc(N, xyz, s, n, ld, md, 1.0, host, 0.0, None, out, stream)
+    with pytest.raises(bem.BemError):
+        bem.bem_apply_direct_noalloc(N, xyz[:N], s, n, ld, md, 1.0, xL, 0.0, None, out, stream)
+    ctx.close()
+
+
+def test_noalloc_at_the_largest_accepted_size():
+    """N = 262144 fills the whole scratch array (hi and lo of all three coordinates). Free
+    points (unit weights, normals along z, zero diagonals) against the context's direct FP32
+    product of the same points: the same kernels on the same inputs. Also the single-layer-only
+    call with a null double-layer input."""
+    from paper_1905_01341_gb300 import bem, build
+
+    build.build()
+    N = 262144
+    pts, _ = synth.random_cube_points(N, seed=23)
+    xyz = torch.from_numpy(np.ascontiguousarray(pts.T)).cuda()
+    ctx = bem.BemContext(mvp=bem.BEM_MVP_DIRECT, precision=bem.BEM_PREC_MIXED)
+    bem.bem_points_upload(ctx.ctx, N, xyz)
+    ctx.build()
+    s = torch.ones(N, dtype=torch.float64, device="cuda")
+    n = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    n[2 * N:] = 1.0
+    zero = torch.zeros(N, dtype=torch.float64, device="cuda")
+    rng = np.random.Generator(np.random.PCG64(24))
+    stream = torch.cuda.current_stream()
+    flat = xyz.reshape(-1)
+    for f, g in ((1.0, 0.0), (0.4, 2.5)):
+        xL = torch.from_numpy(rng.standard_normal(N)).cuda()
+        xM = torch.from_numpy(rng.standard_normal(N)).cuda() if g != 0.0 else None
+        ref = torch.empty(N, dtype=torch.float64, device="cuda")
+        ctx.apply(f, xL, g, xM, ref)
+        out = torch.full((N,), np.nan, dtype=torch.float64, device="cuda")
+        bem.bem_apply_direct_noalloc(N, flat, s, n, zero, zero, f, xL, g, xM, out, stream)
+        torch.cuda.synchronize()
+        o, r = out.cpu().numpy(), ref.cpu().numpy()
+        assert np.isfinite(o).all()
+        assert rel(o, r) <= 1e-12
     ctx.close()
