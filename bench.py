@@ -92,8 +92,12 @@ def parse():
                     help="AB6 GMRES start: 0 previous q (the paper), 1/2/3 extrapolation in t of that degree")
     ap.add_argument("--pa", type=float, default=0.5, help="acoustic amplitude Pa/p0")
     ap.add_argument("--pf", type=int, default=6, help="shape-filter bandwidth")
-    ap.add_argument("--fp64-compare", type=int, default=1, help="also time FP64 right-hand sides (0 = skip)")
+    ap.add_argument("--fp64-compare", type=int, default=1,
+                    help="also time the plain FP64 FMM-BEM step from the same checkpoint (0 = skip)")
+    ap.add_argument("--fp64-steps", type=int, default=3, help="FP64 steps timed (at most --steps)")
     ap.add_argument("--mvp-reps", type=int, default=5)
+    ap.add_argument("--eps-bubbles", type=int, default=300, help="cluster size of the dynamics-error run (0 = skip)")
+    ap.add_argument("--eps-steps", type=int, default=20, help="steps of the dynamics-error run")
     ap.add_argument("--cpu-sample", type=int, default=1, help="run the CPU oracle baseline (rank 0)")
     return ap.parse_args()
 
@@ -180,6 +184,26 @@ def cpu_oracle_step_time(mesh, n_mvps: int, n_recv: int, seed: int = 0) -> dict:
     per_mvp = dt * mesh.n / len(recv)
     return {"sample_s": dt, "receivers": int(len(recv)), "per_mvp_s": per_mvp, "step_s": per_mvp * n_mvps,
             "cores": oracle.num_threads()}
+
+
+def oracle_solve_residual(case, tri, n_recv: int, seed: int) -> dict:
+    """True relative residual of a GPU solution q of L q = b, b = -phi/2 + M phi, against the
+    oracle's dense discrete operator (FP64 direct sums, identity diagonals), estimated at
+    n_recv random receivers (the paper's checkpoint method): |(b - L q)_recv| / |b_recv|."""
+    import oracle
+
+    xyz, phi, q = case["xyz"], case["phi"], case["q"]
+    s, nrm = oracle.vertex_geometry(xyz, tri)
+    recv = oracle.checkpoint_receivers(xyz.shape[0], n_recv, seed)
+    t0 = time.perf_counter()
+    ld, md = oracle.diagonals(xyz, s, nrm, recv)
+    b = -0.5 * phi[recv] + oracle.offdiag_apply(xyz, s, nrm, 0.0, None, 1.0, phi, recv) + md * phi[recv]
+    lq = oracle.offdiag_apply(xyz, s, nrm, 1.0, q, 0.0, None, recv) + ld * q[recv]
+    rr = float(np.linalg.norm(b - lq) / np.linalg.norm(b))
+    return {"oracle_relres_at_receivers": rr, "receivers": int(len(recv)), "gpu_relres": case["gpu_relres"],
+            "gmres_iters": case["gmres_iters"], "oracle_s": time.perf_counter() - t0,
+            "what": "GPU solve (mixed, tolerance as configured) of the current state; true residual against the "
+                    "CPU FP64 oracle's operator at sampled receivers"}
 
 
 # ------------------------------------------------------------------ distributed helpers
@@ -297,6 +321,10 @@ def run_ours(args):
             len(warm), time.perf_counter() - t0, warm[-1]["gmres_iters"], warm[-1]["nonconverged"],
             ctx.stats()["levels"]))
     torch.cuda.synchronize()
+    # checkpoint of the state after the warm-up: the FP64 comparison below replays the timed
+    # steps from it
+    ck = torch.empty(bem.bem_step_save(ctx.ctx), dtype=torch.uint8, device=dev)
+    bem.bem_step_save(ctx.ctx, ck)
     st0 = ctx.stats()
     bem.bem_profile_enable(ctx.ctx, True)
     clocks = ClockSampler(torch.cuda.current_device())
@@ -307,13 +335,18 @@ def run_ours(args):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     infos = []
-    for _ in range(args.steps):
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for k in range(args.steps):
         infos.append(bem.bem_step(ctx.ctx))
+        ev[k + 1].record(stream)
         progress("timed step %d: %d GMRES iterations" % (len(infos), infos[-1]["gmres_iters"]))
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
     ms = e0.elapsed_time(e1) / args.steps
+    for k in range(args.steps):
+        infos[k]["dev_s"] = ev[k].elapsed_time(ev[k + 1]) / 1e3
     clk = clocks.stop()
     prof = bem.bem_profile_read(ctx.ctx)
     bem.bem_profile_enable(ctx.ctx, False)
@@ -353,8 +386,17 @@ def run_ours(args):
         ctx_iso.apply(1.0, q, 0.0, None, out)
     iso = bem.bem_profile_read(ctx_iso.ctx)
     st_iso = ctx_iso.stats()
+    # one Dirichlet solve on the current geometry and potential with the step's solver settings,
+    # for the full-size solve parity (its true residual against the oracle's operator is
+    # evaluated at sampled receivers in the CPU oracle leg below)
+    ph_now = torch.empty(N, dtype=torch.float64, device=dev)
+    bem.bem_step_get_state(ctx.ctx, None, ph_now, None)
+    q_sol = q.clone()
+    sol_it, sol_rr = ctx_iso.solve(ph_now, q_sol, raise_on_noconv=False)
+    solve_case = {"xyz": xs_now.cpu().numpy().reshape(3, N).T.copy(), "phi": ph_now.cpu().numpy(),
+                  "q": q_sol.cpu().numpy(), "gpu_relres": sol_rr, "gmres_iters": sol_it}
     ctx_iso.close()
-    del xs_now
+    del xs_now, q_sol
 
     # end to end through the C ABI: each step driven from the host and its result (r, phi, q)
     # read back into pinned host memory
@@ -469,37 +511,46 @@ def run_ours(args):
     }
 
     if args.fp64_compare and prec == bem.BEM_PREC_MIXED:
-        # the plain FP64 FMM-BEM on the same GPU from the same state: one right-hand side
-        # (octree, diagonals, b and the GMRES solve from the current q) and one product, timed
-        # like the mixed path's; an AB6 step costs one right-hand side
-        progress("FP64 comparison: one right-hand side")
-        xs = torch.empty(3 * N, dtype=torch.float64, device=dev)
-        ph = torch.empty(N, dtype=torch.float64, device=dev)
-        qs = torch.empty(N, dtype=torch.float64, device=dev)
-        bem.bem_step_get_state(ctx.ctx, xs, ph, qs)
-        ctx64 = make_ctx(bem.BEM_PREC_FP64)
-        ctx64.upload(xs.view(3, N), tri, voff, toff)
-        q64 = qs.clone()
+        # the plain FP64 FMM-BEM on the same GPU, like for like: the same checkpoint (state,
+        # Adams-Bashforth history, extrapolation history), the same octree depth, preconditioner,
+        # initial guess and tolerance; its operators, buffers and preconditioner are built by one
+        # untimed step from the checkpoint, then the checkpoint is loaded again and the same
+        # steps as the mixed path's timed ones are timed with CUDA events
+        n64 = max(1, min(args.steps, args.fp64_steps))
+        progress("FP64 comparison: %d AB6 steps from the warm-up checkpoint" % n64)
+        ctx64 = make_ctx(bem.BEM_PREC_FP64, fixed_level=st["levels"])
+        ctx64.upload(xyz, tri, voff, toff)
+        bem.bem_step_load(ctx64.ctx, ck)
+        bem.bem_step(ctx64.ctx)
+        bem.bem_step_load(ctx64.ctx, ck)
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
-        ctx64.build()
-        it64, rr64 = ctx64.solve(ph, q64, raise_on_noconv=False)
+        infos64 = [bem.bem_step(ctx64.ctx) for _ in range(n64)]
         f1.record(stream)
         torch.cuda.synchronize()
-        t64 = f0.elapsed_time(f1) / 1e3
+        s64 = f0.elapsed_time(f1) / 1e3 / n64
         g0 = torch.cuda.Event(enable_timing=True)
         g1 = torch.cuda.Event(enable_timing=True)
         g0.record(stream)
-        ctx64.apply(1.0, qs, 0.0, None, out)
+        ctx64.apply(1.0, q, 0.0, None, out)
         g1.record(stream)
         torch.cuda.synchronize()
-        line["fp64_compare"] = {"s_per_rhs": t64, "gmres_iters": it64, "relres": rr64,
-                                "mvp_ms": g0.elapsed_time(g1),
-                                "mixed_s_per_rhs": ms / 1e3 / max(1e-9, rhs / args.steps),
-                                "what": "FP64 octree + diagonals + b + GMRES solve from the same state and q"}
+        mixed_same = sum(e["dev_s"] for e in infos[:n64]) / n64
+        line["fp64_compare"] = {
+            "s_per_step": s64, "steps": n64, "gmres_iters_per_step": sum(i["gmres_iters"] for i in infos64) / n64,
+            "max_relres": max(i["max_relres"] for i in infos64), "mvp_ms": g0.elapsed_time(g1),
+            "mixed_s_per_step_same_steps": mixed_same,
+            "mixed_gmres_iters_same_steps": sum(i["gmres_iters"] for i in infos[:n64]) / n64,
+            "speedup_mixed_vs_fp64": s64 / mixed_same,
+            "what": "AB6 steps from the same checkpoint as the mixed path's first timed steps: same depth, "
+                    "preconditioner, guess and GMRES tolerance; FP64 throughout"}
         ctx64.close()
+    del ck
+
+    if args.eps_steps > 0 and args.eps_bubbles > 0 and prec == bem.BEM_PREC_MIXED:
+        line["dynamics_error"] = dynamics_error(args, bem, stream)
 
     if rank == 0 and args.cpu_sample:
         n_recv = 4 * int(math.isqrt(N))
@@ -510,9 +561,50 @@ def run_ours(args):
             "sample": "direct FP64 product at %d random receivers x %d sources (%.1f s), scaled by N/receivers to "
                       "%d full single-RHS products per step (the GPU step's product count)" % (
                           info["receivers"], N, info["sample_s"], n_mv)}
+        line["solve_parity"] = oracle_solve_residual(solve_case, mesh.tri, 400, seed=41)
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def dynamics_error(args, bem, stream) -> dict:
+    """Eq. (eqErr): eps(t) = |x(t) - x_ref(t)|_2 / max_{tau <= t} |x_ref(tau) - x_ref(0)|_2 over the
+    surface-point coordinates, of this benchmark's mixed-precision step against the FP64 path at
+    p + 2 with GMRES to 1e-10 (the reference run), on a smaller cluster of the same recipe."""
+    import synth
+    import torch
+
+    mesh, phi = synth.workload_cluster(bubbles=args.eps_bubbles, level=args.level, seed=3)
+    sp = bem.bem_step_params_default(pa=args.pa, pf=args.pf, guess=args.guess)
+    runs, secs = {}, {}
+    for key, prm in (("mixed", dict(precision=bem.BEM_PREC_MIXED, p_fmm=args.p, gmres_tol=args.tol)),
+                     ("ref", dict(precision=bem.BEM_PREC_FP64, p_fmm=min(args.p + 2, 20), gmres_tol=1e-10))):
+        progress("dynamics error: %s run, %d steps of %d bubbles" % (key, args.eps_steps, args.eps_bubbles))
+        c = bem.BemContext(stream=stream, leaf_target=args.leaf, gmres_maxit=args.maxit, gmres_restart=args.restart,
+                           gmres_precond=args.precond, m2l_tensor_cores=args.m2l_tc, **prm)
+        c.upload_mesh(mesh)
+        bem.bem_step_init(c.ctx, phi, sp)
+        xs, nc = [], 0
+        t0 = time.perf_counter()
+        for _ in range(args.eps_steps):
+            nc += bem.bem_step(c.ctx)["nonconverged"]
+            x = np.zeros(3 * mesh.n)
+            bem.bem_step_get_state(c.ctx, x)
+            xs.append(x)
+        torch.cuda.synchronize()
+        secs[key] = time.perf_counter() - t0
+        runs[key] = (xs, nc)
+        c.close()
+    x0 = mesh.xyz_soa().reshape(-1)
+    span, eps = 0.0, []
+    for x, xr in zip(runs["mixed"][0], runs["ref"][0]):
+        span = max(span, float(np.linalg.norm(xr - x0)))
+        eps.append(float(np.linalg.norm(x - xr)) / span)
+    return {"eps_final": eps[-1], "eps_max": max(eps), "eps_by_step": [float("%.3e" % e) for e in eps],
+            "steps": args.eps_steps, "nonconverged": {k: v[1] for k, v in runs.items()},
+            "wall_s": secs,
+            "config": "%d icosphere-L%d bubbles (%d unknowns), seed 3; test: this benchmark's configuration; reference: "
+                      "FP64, p = %d, GMRES 1e-10" % (args.eps_bubbles, args.level, mesh.n, min(args.p + 2, 20))}
 
 
 def run_batched(args):

@@ -269,6 +269,26 @@ int bem_step(void *ctx, bem_step_stats *st);
 /* Current state: xyz[3N] (SoA), phi[N], the last q[N] and t. Any pointer may be NULL. */
 int bem_step_get_state(void *ctx, double *xyz, double *phi, double *q, double *t);
 
+/* Checkpoint and resume of a time integration (the paper has none; Sections 3.5-3.6 define
+ * what a step depends on). A checkpoint holds what evolves: r and phi, the last q, t, dt, the
+ * step count, the right-hand sides of the last five step starts (the Adams-Bashforth history,
+ * Section 3.5) and the step-start solutions behind the extrapolated initial guess; and what
+ * the fixed parts are rebuilt from: r at t = 0, the step parameters and the tuned octree depth.
+ * It is a byte buffer of *size bytes (host or device memory of the context's device): call
+ * bem_step_save with buf = NULL to get the size, then with a buffer of at least that many
+ * bytes (cap). Learned-guess weights are saved separately (bem_mlp_get_params).
+ * bem_step_load needs a context holding the same mesh connectivity (N, T, M and offsets as
+ * uploaded; coordinates are replaced): it rebuilds the shape filters, V_m0, a_m0, neighbour
+ * lists and step size from r(0) as bem_step_init does, restores the evolving state, and the
+ * next bem_step continues the saved run. With identical context parameters, a fixed octree
+ * depth (fixed_level, or a saved tuned depth) and gmres_precond 0 or 1, the continued run
+ * repeats the original bit for bit on the same GPU; the bubble-block preconditioner
+ * (gmres_precond 2) is rebuilt from the geometry at the first solve after the load, so those
+ * solves start differently and agree with the original within the GMRES tolerance. Returns
+ * BEM_ERR_ARG for a buffer that is too small, not a checkpoint, or of another mesh size. */
+int bem_step_save(void *ctx, void *buf, int64_t cap, int64_t *size);
+int bem_step_load(void *ctx, const void *buf, int64_t size);
+
 /* ------------------------------------------------------------------------------------------
  * Learned GMRES initial guess. The paper starts each solve from the previous step's q
  * (Sections 3.5, 3.8); that remains the fallback. Per bubble, the features are the

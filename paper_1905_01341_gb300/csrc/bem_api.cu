@@ -683,6 +683,22 @@ int bem_step_get_state(void *ctx, double *xyz, double *phi, double *q, double *t
     return guarded(ctx, [&](Context &c) { step_get_state(c, xyz, phi, q, t); });
 }
 
+int bem_step_save(void *ctx, void *buf, int64_t cap, int64_t *size) {
+    return guarded(ctx, [&](Context &c) {
+        if (!c.mesh_ok) fail(BEM_ERR_NOT_BUILT, "no mesh uploaded");
+        const int64_t need = step_checkpoint_size(c);
+        if (size) *size = need;
+        if (buf) step_save(c, buf, cap);
+    });
+}
+
+int bem_step_load(void *ctx, const void *buf, int64_t size) {
+    return guarded(ctx, [&](Context &c) {
+        if (!buf) fail(BEM_ERR_ARG, "null checkpoint");
+        step_load(c, buf, size);
+    });
+}
+
 int bem_mlp_init(void *ctx, int32_t hidden, int32_t lmax, uint64_t seed) {
     return guarded(ctx, [&](Context &c) { mlp_init(c, hidden, lmax, seed, step_initial_xyz(c)); });
 }

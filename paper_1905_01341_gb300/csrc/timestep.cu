@@ -783,6 +783,114 @@ void step_get_state(Context &c, double *xyz, double *phi, double *q, double *t) 
     if (t) *t = s.t;
 }
 
+// ------------------------------------------------------------------------------ checkpoint
+// Layout of a checkpoint: this header, then FP64 arrays r(0) [3N], y = (r, phi) [4N], q [N],
+// the right-hand-side history [5][4N] (slots in storage order; `order` says which is newest)
+// and the step-start solutions of the extrapolated guess [kQh][N].
+struct CkptHeader {
+    char magic[8];
+    int32_t version, tuned_level;
+    int64_t N, T, M;
+    bem_step_params sp;
+    double t, dt;
+    int64_t steps;
+    int32_t nhist, order[5];
+    int32_t qh_n, qh_order[kQh];
+    double qh_time[kQh];
+};
+constexpr char kCkptMagic[8] = {'B', 'E', 'M', 'S', 'T', 'E', 'P', '1'};
+
+int64_t step_checkpoint_size(const Context &c) {
+    return (int64_t)sizeof(CkptHeader) + (int64_t)(3 + 4 + 1 + 5 * 4 + kQh) * c.N * (int64_t)sizeof(double);
+}
+
+void step_save(Context &c, void *buf, int64_t cap) {
+    StepState &s = state_of(c);
+    if (!s.ready) fail(BEM_ERR_NOT_BUILT, "bem_step_init has not been called");
+    const int64_t N = c.N, need = step_checkpoint_size(c);
+    if (cap < need) fail(BEM_ERR_ARG, "checkpoint buffer too small: " + std::to_string(cap) + " < " + std::to_string(need));
+    CkptHeader h{};
+    std::memcpy(h.magic, kCkptMagic, 8);
+    h.version = 1;
+    h.tuned_level = c.tuned_level;
+    h.N = N;
+    h.T = c.T;
+    h.M = c.M;
+    h.sp = s.sp;
+    h.t = s.t;
+    h.dt = s.dt;
+    h.steps = s.steps;
+    h.nhist = s.nhist;
+    for (int i = 0; i < 5; ++i) h.order[i] = s.order[i];
+    h.qh_n = s.qh_n;
+    for (int i = 0; i < kQh; ++i) {
+        h.qh_order[i] = s.qh_order[i];
+        h.qh_time[i] = s.qh_time[i];
+    }
+    s.qh.resize((size_t)kQh * N);  // allocated at the first recorded solve; zeros before
+    if (s.qh_n == 0) BEM_CUDA(cudaMemsetAsync(s.qh.p, 0, (size_t)kQh * N * sizeof(double), c.stream));
+    unsigned char *o = static_cast<unsigned char *>(buf);
+    BEM_CUDA(cudaMemcpyAsync(o, &h, sizeof(h), cudaMemcpyDefault, c.stream));
+    int64_t off = sizeof(h);
+    auto put = [&](const double *src, int64_t n) {
+        BEM_CUDA(cudaMemcpyAsync(o + off, src, n * sizeof(double), cudaMemcpyDefault, c.stream));
+        off += n * (int64_t)sizeof(double);
+    };
+    put(s.x0.p, 3 * N);
+    put(s.y.p, 4 * N);
+    put(s.q.p, N);
+    put(s.hist.p, 5 * 4 * N);
+    put(s.qh.p, kQh * N);
+    BEM_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+void step_load(Context &c, const void *buf, int64_t size) {
+    if (!c.mesh_ok || c.points_only) fail(BEM_ERR_NOT_BUILT, "upload the mesh (same connectivity) first");
+    CkptHeader h{};
+    if (size < (int64_t)sizeof(h)) fail(BEM_ERR_ARG, "checkpoint too small");
+    BEM_CUDA(cudaMemcpy(&h, buf, sizeof(h), cudaMemcpyDefault));
+    if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1) fail(BEM_ERR_ARG, "not a time-step checkpoint");
+    if (h.N != c.N || h.T != c.T || h.M != c.M)
+        fail(BEM_ERR_ARG, "checkpoint of another mesh (N, T or M differ)");
+    const int64_t N = c.N;
+    if (size < step_checkpoint_size(c)) fail(BEM_ERR_ARG, "checkpoint truncated");
+    const unsigned char *in = static_cast<const unsigned char *>(buf);
+    int64_t off = sizeof(h);
+    auto at = [&](int64_t n) {
+        const double *p = reinterpret_cast<const double *>(in + off);
+        off += n * (int64_t)sizeof(double);
+        return p;
+    };
+    const double *x0 = at(3 * N), *y = at(4 * N), *q = at(N), *hist = at(5 * 4 * N), *qh = at(kQh * N);
+    // the fixed parts (filters, V0, a0, neighbour lists, dt) are rebuilt from r(0) as
+    // bem_step_init builds them; phi0 and q0 are placeholders overwritten below
+    BEM_CUDA(cudaMemcpyAsync(c.xyz.p, x0, 3 * N * sizeof(double), cudaMemcpyDefault, c.stream));
+    c.built = false;
+    c.bp.ready = false;
+    DevBuf<double> tmp;
+    tmp.resize(2 * N);
+    BEM_CUDA(cudaMemcpyAsync(tmp.p, y + 3 * N, N * sizeof(double), cudaMemcpyDefault, c.stream));
+    BEM_CUDA(cudaMemcpyAsync(tmp.p + N, q, N * sizeof(double), cudaMemcpyDefault, c.stream));
+    step_init(c, tmp.p, tmp.p + N, h.sp);
+    StepState &s = state_of(c);
+    BEM_CUDA(cudaMemcpyAsync(s.y.p, y, 4 * N * sizeof(double), cudaMemcpyDefault, c.stream));
+    BEM_CUDA(cudaMemcpyAsync(s.hist.p, hist, 5 * 4 * N * sizeof(double), cudaMemcpyDefault, c.stream));
+    s.qh.resize((size_t)kQh * N);
+    BEM_CUDA(cudaMemcpyAsync(s.qh.p, qh, (size_t)kQh * N * sizeof(double), cudaMemcpyDefault, c.stream));
+    s.t = h.t;
+    s.dt = h.dt;
+    s.steps = h.steps;
+    s.nhist = h.nhist;
+    for (int i = 0; i < 5; ++i) s.order[i] = h.order[i];
+    s.qh_n = h.qh_n;
+    for (int i = 0; i < kQh; ++i) {
+        s.qh_order[i] = h.qh_order[i];
+        s.qh_time[i] = h.qh_time[i];
+    }
+    if (h.tuned_level > 0) c.tuned_level = h.tuned_level;
+    BEM_CUDA(cudaStreamSynchronize(c.stream));
+}
+
 void step_free(StepState *s) { delete s; }
 
 const double *step_initial_xyz(Context &c) {

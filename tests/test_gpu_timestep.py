@@ -115,3 +115,89 @@ def test_extrapolated_guess_same_states_fewer_iterations():
     disp = np.linalg.norm(res[0][1] - mesh.xyz)
     assert np.linalg.norm(res[2][1] - res[0][1]) < 1e-4 * disp
     assert np.linalg.norm(res[2][2] - res[0][2]) < 1e-5 * np.linalg.norm(res[0][2])
+
+
+def _state(ctx, n):
+    bem = _bem()
+    xyz, ph, q = np.zeros(3 * n), np.zeros(n), np.zeros(n)
+    t = bem.bem_step_get_state(ctx.ctx, xyz, ph, q)
+    return xyz, ph, q, t
+
+
+def test_checkpoint_resume_repeats_the_run_bit_for_bit():
+    """A run saved after its sixth step (the first Adams-Bashforth step follows five RK4 steps)
+    and resumed in a fresh context, from a host and from a device buffer, repeats the original's
+    next three steps exactly: FP64 FMM at a fixed depth with Jacobi-preconditioned GMRES."""
+    bem = _bem()
+    mesh, phi = synth.workload_cluster(bubbles=6, level=3, seed=31)
+    prm = dict(mvp=bem.BEM_MVP_FMM, precision=bem.BEM_PREC_FP64, p_fmm=10, fixed_level=3, gmres_tol=1e-9,
+               gmres_precond=1)
+    sp = bem.bem_step_params_default(pf=6, pa=0.5, guess=2)
+    ctx = bem.BemContext(**prm)
+    ctx.upload_mesh(mesh)
+    bem.bem_step_init(ctx.ctx, phi, sp)
+    for _ in range(6):
+        bem.bem_step(ctx.ctx)
+    size = bem.bem_step_save(ctx.ctx)
+    host = np.zeros(size, np.uint8)
+    assert bem.bem_step_save(ctx.ctx, host) == size
+    devbuf = torch.from_numpy(host).cuda()
+    ref = []
+    for _ in range(3):
+        ref.append((bem.bem_step(ctx.ctx), _state(ctx, mesh.n)))
+    ctx.close()
+    for buf in (host, devbuf):
+        c2 = bem.BemContext(**prm)
+        c2.upload_mesh(mesh)
+        bem.bem_step_load(c2.ctx, buf)
+        for info0, st0 in ref:
+            info = bem.bem_step(c2.ctx)
+            st = _state(c2, mesh.n)
+            assert info["gmres_iters"] == info0["gmres_iters"] and info["steps"] == info0["steps"]
+            assert st[3] == st0[3]
+            for a, b in zip(st[:3], st0[:3]):
+                assert np.array_equal(a, b)
+        c2.close()
+    # a checkpoint of another mesh size is refused
+    other, _ = synth.workload_cluster(bubbles=5, level=3, seed=31)
+    c3 = bem.BemContext(**prm)
+    c3.upload_mesh(other)
+    with pytest.raises(bem.BemError) as ei:
+        bem.bem_step_load(c3.ctx, host)
+    assert ei.value.code == bem.BEM_ERR_ARG
+    with pytest.raises(bem.BemError):
+        bem.bem_step_load(c3.ctx, host[:100])
+    c3.close()
+
+
+def test_dynamics_error_of_the_mixed_step_against_fp64():
+    """The dynamics error of Eq. (eqErr), eps(t) = |x(t) - x_ref(t)| / max_tau |x_ref(tau) - x_ref(0)|
+    over the surface-point coordinates, of the benchmark's mixed-precision step (p = 14, FP32 near
+    field, BF16-split tensor-core M2L, GMRES to 1e-6) against the FP64 path at p = 16 with GMRES
+    to 1e-10, over 20 steps of a 40-bubble cluster. The paper reports 5.3e-3 (single precision,
+    p = 8, tolerance 1e-4) and 2.5e-4 (double, p = 12, 1e-5) at step 200; the bound here is the
+    GMRES tolerance's share: 1e-3."""
+    bem = _bem()
+    mesh, phi = synth.workload_cluster(bubbles=40, level=3, seed=32)
+    sp = bem.bem_step_params_default(pf=6, pa=0.5, guess=2)
+    runs = {}
+    for key, prm in (("mixed", dict(precision=bem.BEM_PREC_MIXED, p_fmm=14, gmres_tol=1e-6)),
+                     ("ref", dict(precision=bem.BEM_PREC_FP64, p_fmm=16, gmres_tol=1e-10))):
+        ctx = bem.BemContext(mvp=bem.BEM_MVP_FMM, gmres_precond=2, gmres_maxit=200, **prm)
+        ctx.upload_mesh(mesh)
+        bem.bem_step_init(ctx.ctx, phi, sp)
+        xs = []
+        for _ in range(20):
+            info = bem.bem_step(ctx.ctx)
+            assert info["nonconverged"] == 0
+            xs.append(_state(ctx, mesh.n)[0])
+        runs[key] = xs
+        ctx.close()
+    x0 = mesh.xyz_soa().reshape(-1)
+    span = 0.0
+    eps = []
+    for x, xr in zip(runs["mixed"], runs["ref"]):
+        span = max(span, np.linalg.norm(xr - x0))
+        eps.append(np.linalg.norm(x - xr) / span)
+    print("eps(t) over 20 steps:", ["%.2e" % e for e in eps])
+    assert max(eps) < 1e-3
