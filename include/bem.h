@@ -73,9 +73,11 @@ typedef struct {
                                per expansion (Section 3.7). Range 2..20. Default 14.           */
     int32_t leaf_target;    /* target mean points per non-empty leaf box (the clustering
                                parameter s of Section 3.6); 0 = autotune: the first build after
-                               a mesh upload times one product at the depth for 64 points per
-                               leaf and one level either side and keeps the fastest depth.
-                               Default 64.                                                     */
+                               a mesh upload times single-layer products at the depth for 64
+                               points per leaf and one level either side, and at that depth the
+                               tensor-core M2L's pipeline depth and the near field's grid
+                               (m2l_stages, p2p_blocks_per_sm where set to automatic), and keeps
+                               the fastest combination for this mesh. Default 64.             */
     int32_t fixed_level;    /* > 0: force the octree depth l_max to this value (2..10).        */
     int32_t precision;      /* bem_precision. Default BEM_PREC_MIXED.                          */
     int32_t mvp;            /* bem_mvp_kind. Default BEM_MVP_FMM.                              */
@@ -117,6 +119,17 @@ typedef struct {
     int32_t gmres_maxit;    /* maximum GMRES iterations. Default 100.                          */
     int32_t gmres_restart;  /* restart length; 0 = no restart (= maxit). Default 0.            */
     double gmres_tol;       /* stop when |b - L q| / |b| <= tol (Section 3.8). Default 1e-6.  */
+    int32_t m2l_stages;     /* shared-memory pipeline stages of the tensor-core M2L: 3, 4 or 5
+                               (5 only where it fits, p <= 14); 0 = automatic (the tile
+                               autotuner's choice when leaf_target = 0, else the deepest that
+                               fits). Fewer stages leave shared memory on each SM for the near
+                               field running concurrently. Default 0.                         */
+    int32_t p2p_blocks_per_sm; /* near-field grid: 0 = one warp per work unit (all units in one
+                               grid); k > 0 = a persistent grid of k blocks per SM looping over
+                               the units, which leaves room on every SM for the far-field
+                               kernels of the concurrent stream. Same results either way.
+                               -1 = automatic (the tile autotuner's choice when leaf_target = 0,
+                               else 0). Default -1.                                           */
 } bem_params;
 
 /* Run-time counters of a context (cumulative since bem_create or bem_reset_stats). */
@@ -132,6 +145,8 @@ typedef struct {
     double last_relres;     /* true relative residual of the last solve                        */
     double last_build_ms;   /* device time of the last fmm_build                               */
     int64_t n_launches;     /* kernels launched by the library in this process (all contexts)   */
+    int32_t m2l_stages;     /* tensor-core M2L pipeline stages in use (0 = deepest that fits)   */
+    int32_t p2p_blocks_per_sm; /* near-field grid in use (0 = one warp per work unit)           */
 } bem_stats;
 
 /* Phases reported by bem_profile_read, in this order. */

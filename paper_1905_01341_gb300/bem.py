@@ -59,6 +59,8 @@ class bem_params(ctypes.Structure):
         ("gmres_maxit", ctypes.c_int32),
         ("gmres_restart", ctypes.c_int32),
         ("gmres_tol", ctypes.c_double),
+        ("m2l_stages", ctypes.c_int32),
+        ("p2p_blocks_per_sm", ctypes.c_int32),
     ]
 
 
@@ -75,6 +77,8 @@ class bem_stats(ctypes.Structure):
         ("last_relres", ctypes.c_double),
         ("last_build_ms", ctypes.c_double),
         ("n_launches", ctypes.c_int64),
+        ("m2l_stages", ctypes.c_int32),
+        ("p2p_blocks_per_sm", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:

@@ -169,6 +169,8 @@ void check_params(const bem_params &p) {
     if (p.gmres_maxit < 1 || p.gmres_restart < 0 || p.gmres_restart > 127) fail(BEM_ERR_ARG, "bad GMRES limits");
     if (p.gmres_precond < 0 || p.gmres_precond > 2) fail(BEM_ERR_ARG, "gmres_precond must be 0, 1 or 2");
     if (!(p.gmres_tol > 0.0)) fail(BEM_ERR_ARG, "gmres_tol must be > 0");
+    if (p.m2l_stages != 0 && (p.m2l_stages < 3 || p.m2l_stages > 5)) fail(BEM_ERR_ARG, "m2l_stages must be 0 or 3..5");
+    if (p.p2p_blocks_per_sm < -1 || p.p2p_blocks_per_sm > 16) fail(BEM_ERR_ARG, "p2p_blocks_per_sm must be in -1..16");
 }
 
 }  // namespace
@@ -194,11 +196,15 @@ void apply_full(Context &c, double f, const double *xL, double g, const double *
     launch_add_diag(c.N, f, xL, g, xM, c.ldiag.p, c.mdiag.p, out, c.stream);
 }
 
-// Octree depth autotuner (leaf_target = 0): times one single-layer product at the depth the
-// leaf-count rule gives for 64 points per leaf and at one level either side, and keeps the
-// fastest for this mesh. Points on surfaces fill ~4x more boxes per level, not 8x, so the
-// near-field / far-field balance moves in coarse steps and is cheapest to settle by timing.
-void tune_tree_level(Context &c) {
+// Tile autotuner (leaf_target = 0). Times one single-layer product at the depth the leaf-count
+// rule gives for 64 points per leaf and at one level either side, and keeps the fastest depth
+// for this mesh: points on surfaces fill ~4x more boxes per level, not 8x, so the near-field /
+// far-field balance moves in coarse steps and is cheapest to settle by timing. At that depth it
+// then times the tile choices left automatic: the tensor-core M2L's pipeline depth (3, 4 or 5
+// shared-memory stages) and the near field's grid (one warp per unit, or a persistent grid of
+// k blocks per SM). Both decide how the near field and the far field share the SMs while they
+// run concurrently on two streams; neither changes a result.
+void tune_tiles(Context &c) {
     const int64_t N = c.N;
     c.ones.resize(N);
     k_fill<<<div_up(N, 256), 256, 0, c.stream>>>(N, 1.0, c.ones.p);
@@ -206,15 +212,32 @@ void tune_tree_level(Context &c) {
     DevBuf<double> out;
     out.resize(N);
     const auto saved_apply = c.stats.n_apply, saved_apply_rhs = c.stats.n_apply_rhs;
+    cudaEvent_t e0, e1;
+    BEM_CUDA(cudaEventCreate(&e0));
+    BEM_CUDA(cudaEventCreate(&e1));
+    auto time_product = [&](int reps) {
+        double f = 1.0, g = 0.0;
+        const double *xl[1] = {c.ones.p};
+        const double *xm[1] = {nullptr};
+        double *o[1] = {out.p};
+        offdiag_apply(c, 1, &f, xl, &g, xm, o, c.prm.precision);  // warm-up (chunk tables, buffers)
+        BEM_CUDA(cudaEventRecord(e0, c.stream));
+        for (int r = 0; r < reps; ++r) offdiag_apply(c, 1, &f, xl, &g, xm, o, c.prm.precision);
+        BEM_CUDA(cudaEventRecord(e1, c.stream));
+        BEM_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        BEM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        return ms / reps;
+    };
+    // 1. depth, with the default tiles
+    c.tuned_stages = c.prm.m2l_stages;
+    c.tuned_p2p_blocks = c.prm.p2p_blocks_per_sm > 0 ? c.prm.p2p_blocks_per_sm : 0;
     const int saved_target = c.prm.leaf_target;
     c.prm.leaf_target = 64;
     c.level_override = 0;
     build_tree(c);
     c.prm.leaf_target = saved_target;
     const int L0 = c.tree.L;
-    cudaEvent_t e0, e1;
-    BEM_CUDA(cudaEventCreate(&e0));
-    BEM_CUDA(cudaEventCreate(&e1));
     int best = L0;
     float best_ms = 0.f;
     for (int L = std::max(2, L0 - 1); L <= std::min(L0 + 1, c.tree.deep); ++L) {
@@ -222,21 +245,39 @@ void tune_tree_level(Context &c) {
         build_tree(c);
         c.m2l_chunks_h.clear();
         c.tc_chunks_ok[0] = c.tc_chunks_ok[1] = false;
-        double f = 1.0, g = 0.0;
-        const double *xl[1] = {c.ones.p};
-        const double *xm[1] = {nullptr};
-        double *o[1] = {out.p};
-        offdiag_apply(c, 1, &f, xl, &g, xm, o, c.prm.precision);  // warm-up (chunk tables, buffers)
-        BEM_CUDA(cudaEventRecord(e0, c.stream));
-        offdiag_apply(c, 1, &f, xl, &g, xm, o, c.prm.precision);
-        BEM_CUDA(cudaEventRecord(e1, c.stream));
-        BEM_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        BEM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        const float ms = time_product(1);
         if (L == std::max(2, L0 - 1) || ms < best_ms) {
             best = L;
             best_ms = ms;
         }
+    }
+    c.level_override = best;
+    // 2. tiles at that depth
+    std::vector<int> stages = {c.prm.m2l_stages};
+    if (c.prm.m2l_stages == 0 && c.prm.precision == BEM_PREC_MIXED && c.prm.m2l_tensor_cores) stages = {5, 4, 3};
+    std::vector<int> blocks = {c.tuned_p2p_blocks};
+    if (c.prm.p2p_blocks_per_sm < 0 && c.prm.overlap) blocks = {0, 2, 4};
+    if (stages.size() > 1 || blocks.size() > 1) {
+        build_tree(c);
+        c.m2l_chunks_h.clear();
+        c.tc_chunks_ok[0] = c.tc_chunks_ok[1] = false;
+        float tbest = 0.f;
+        int bs = stages[0], bb = blocks[0];
+        bool first = true;
+        for (int st : stages)
+            for (int bk : blocks) {
+                c.tuned_stages = st;
+                c.tuned_p2p_blocks = bk;
+                const float ms = time_product(2);
+                if (first || ms < tbest) {
+                    tbest = ms;
+                    bs = st;
+                    bb = bk;
+                    first = false;
+                }
+            }
+        c.tuned_stages = bs;
+        c.tuned_p2p_blocks = bb;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -285,7 +326,7 @@ void build_all(Context &c) {
         c.tc_chunks_ok[0] = c.tc_chunks_ok[1] = false;
         c.tc_err.resize(1);
         BEM_CUDA(cudaMemsetAsync(c.tc_err.p, 0, sizeof(int), c.stream));
-        if (c.prm.leaf_target == 0 && c.prm.fixed_level == 0 && c.tuned_level == 0) tune_tree_level(c);
+        if (c.prm.leaf_target == 0 && c.prm.fixed_level == 0 && c.tuned_level == 0) tune_tiles(c);
         c.level_override = c.prm.fixed_level == 0 ? c.tuned_level : 0;
         {
             PhaseScope ps(c, PH_TREE);
@@ -297,6 +338,8 @@ void build_all(Context &c) {
         c.stats.m2l_pairs = c.tree.n_m2l;
         c.stats.levels = c.tree.L;
         c.stats.leaves = c.tree.nb[c.tree.L];
+        c.stats.m2l_stages = c.tuned_stages;
+        c.stats.p2p_blocks_per_sm = c.tuned_p2p_blocks;
     } else {
         c.dir_hi.resize(3 * N);
         c.dir_lo.resize(3 * N);
@@ -411,6 +454,8 @@ int bem_params_default(bem_params *p) {
     p->gmres_maxit = 100;
     p->gmres_restart = 0;
     p->gmres_tol = 1e-6;
+    p->m2l_stages = 0;
+    p->p2p_blocks_per_sm = -1;
     return BEM_OK;
 }
 
@@ -427,6 +472,9 @@ int bem_create(void **ctx_out, const bem_params *p, void *stream) {
         c->prm = prm;
         c->stream = static_cast<cudaStream_t>(stream);
         BEM_CUDA(cudaGetDevice(&c->device));
+        BEM_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+        c->tuned_stages = prm.m2l_stages;
+        c->tuned_p2p_blocks = prm.p2p_blocks_per_sm < 0 ? 0 : prm.p2p_blocks_per_sm;
         *ctx_out = c;
         return BEM_OK;
     } catch (const Error &e) {

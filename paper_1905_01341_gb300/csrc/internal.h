@@ -271,6 +271,11 @@ struct Context {
     // octree depth: level_override > 0 forces l_max (depth autotuning); tuned_level is the
     // depth the autotuner chose for this mesh (0 = not tuned yet)
     int level_override = 0, tuned_level = 0;
+    // tile choices of the products: tensor-core M2L pipeline stages (0 = deepest that fits) and
+    // near-field blocks per SM (0 = one warp per unit); set from the parameters, or by the
+    // autotuner when those are automatic
+    int tuned_stages = 0, tuned_p2p_blocks = 0;
+    int num_sms = 1;
     DevBuf<int32_t> vcid;          // [N] cluster of every vertex (when C > 1)
 
     // geometry (caller order)

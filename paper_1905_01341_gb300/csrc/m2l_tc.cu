@@ -388,10 +388,12 @@ void launch_m2l_tc(Context &c, const Operators &o, const XChunk *chunks, int64_t
         k_split_x<<<nb, 256, 0, st>>>(xrows, o.P, Npad, X, xs);
         BEM_LAUNCH_CHECK();
     }
-    // five stages (the copies of a step start four steps ahead) where they fit, else four
-    const bool five = tc_layout(Npad, 5).total <= (size_t)TC_MAX_SMEM;
-    const size_t sm = tc_layout(Npad, five ? 5 : 4).total;
-    auto kern = five ? k_m2l_tc<R, 5> : k_m2l_tc<R, 4>;
+    // pipeline depth: the context's choice (parameter or autotuner), else five stages (the copies
+    // of a step start four steps ahead) where they fit, else four; never more than fit
+    int stages = c.tuned_stages > 0 ? c.tuned_stages : 5;
+    while (stages > 3 && tc_layout(Npad, stages).total > (size_t)TC_MAX_SMEM) --stages;
+    const size_t sm = tc_layout(Npad, stages).total;
+    auto kern = stages == 5 ? k_m2l_tc<R, 5> : stages == 4 ? k_m2l_tc<R, 4> : k_m2l_tc<R, 3>;
     // set on every launch: the attribute belongs to the current device (~1 us against a ms kernel)
     BEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_MAX_SMEM));
     kern<<<(unsigned)nchunks, TC_THREADS, sm, st>>>(o.P, Npad, reinterpret_cast<const __nv_bfloat16 *>(o.m2l_tc.p),

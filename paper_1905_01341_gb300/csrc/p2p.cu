@@ -9,6 +9,8 @@
 // formed per shared-memory tile in FP32 and merged with TwoSum compensation.
 #include "internal.h"
 
+#include <algorithm>
+
 namespace bem {
 namespace {
 
@@ -119,18 +121,14 @@ __device__ __forceinline__ void p2p_tile(const P2PStage<T, R, HQ, HW> &sg, int n
         for (int r = 0; r < R; ++r) acc[k][r].add(part[k][r]);
 }
 
+// One work unit (up to 64 receivers of one leaf) by one warp.
 template <class T, int R, bool HQ, bool HW>
-__global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_units(
-    const int2 *__restrict__ units, int64_t nunits, const int32_t *__restrict__ bstart,
-    const int32_t *__restrict__ bcount, const int32_t *__restrict__ nbr, const int32_t *__restrict__ ncnt,
-    const int8_t *__restrict__ nd, int64_t N, const T *__restrict__ loc, const T *__restrict__ nrm,
-    const T *__restrict__ q, const T *__restrict__ w, double *__restrict__ out) {
-    __shared__ P2PStage<T, R, HQ, HW> stage[P2P_WARPS];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t u = (int64_t)blockIdx.x * P2P_WARPS + warp;
-    if (u >= nunits) return;  // the whole warp leaves; only warp-level barriers follow
-    P2PStage<T, R, HQ, HW> &sg = stage[warp];
-    const int2 un = units[u];
+__device__ __forceinline__ void p2p_unit(P2PStage<T, R, HQ, HW> &sg, int lane, int2 un,
+                                         const int32_t *__restrict__ bstart, const int32_t *__restrict__ bcount,
+                                         const int32_t *__restrict__ nbr, const int32_t *__restrict__ ncnt,
+                                         const int8_t *__restrict__ nd, int64_t N, const T *__restrict__ loc,
+                                         const T *__restrict__ nrm, const T *__restrict__ q, const T *__restrict__ w,
+                                         double *__restrict__ out) {
     const int b = un.x, r0 = un.y;
     const int s0 = bstart[b];
     const int nr = min(P2P_UNIT, bcount[b] - r0);
@@ -194,6 +192,25 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_units(
             for (int r = 0; r < R; ++r) out[r * N + i] = acc[k][r].get();  // the far field is added later
         }
     }
+}
+
+// Each warp takes the units u = blockIdx.x * P2P_WARPS + warp, then every gridDim.x * P2P_WARPS
+// further: one unit per warp when the grid covers all units, or a persistent grid of a fixed
+// number of blocks per SM (leaving room on every SM for the far-field kernels that run
+// concurrently on the other stream). Every unit writes its own receivers, so the result does
+// not depend on the grid.
+template <class T, int R, bool HQ, bool HW>
+__global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_units(
+    const int2 *__restrict__ units, int64_t nunits, const int32_t *__restrict__ bstart,
+    const int32_t *__restrict__ bcount, const int32_t *__restrict__ nbr, const int32_t *__restrict__ ncnt,
+    const int8_t *__restrict__ nd, int64_t N, const T *__restrict__ loc, const T *__restrict__ nrm,
+    const T *__restrict__ q, const T *__restrict__ w, double *__restrict__ out) {
+    __shared__ P2PStage<T, R, HQ, HW> stage[P2P_WARPS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * P2P_WARPS;
+    // the loop bound is uniform in the warp; only warp-level barriers follow
+    for (int64_t u = (int64_t)blockIdx.x * P2P_WARPS + warp; u < nunits; u += stride)
+        p2p_unit<T, R, HQ, HW>(stage[warp], lane, units[u], bstart, bcount, nbr, ncnt, nd, N, loc, nrm, q, w, out);
 }
 
 template <int R>
@@ -328,7 +345,16 @@ static void launch_units(Context &c, const T *q, const T *w, double *out_sorted,
     const T *nrm = sizeof(T) == 8 ? (const T *)t.nrm64.p : (const T *)t.nrm32.p;
     const int64_t nu = t.n_p2p_units;
     if (nu == 0) return;
-    k_p2p_units<T, R, HQ, HW><<<(unsigned)div_up(nu, P2P_WARPS), P2P_WARPS * 32, 0, st>>>(
+    int64_t blocks = div_up(nu, P2P_WARPS);
+    if (c.tuned_p2p_blocks > 0) blocks = std::min<int64_t>(blocks, (int64_t)c.num_sms * c.tuned_p2p_blocks);
+    // With the far field running concurrently, ask for the SM configuration with the most shared
+    // memory: the tensor-core M2L needs it, and an SM whose resident near-field blocks had it
+    // configured for more L1 would first have to drain them. (A per-device attribute, set on
+    // every launch; about a microsecond.)
+    if (c.prm.overlap)
+        BEM_CUDA(cudaFuncSetAttribute(k_p2p_units<T, R, HQ, HW>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
+    k_p2p_units<T, R, HQ, HW><<<(unsigned)blocks, P2P_WARPS * 32, 0, st>>>(
         t.p2p_units.p, nu, t.bstart.p + t.base[L], t.bcount.p + t.base[L], t.nbr.p, t.nbr_cnt.p, t.nbr_d.p, c.N, loc,
         nrm, q, w, out_sorted);
     BEM_LAUNCH_CHECK();

@@ -789,7 +789,7 @@ void step_get_state(Context &c, double *xyz, double *phi, double *q, double *t) 
 // and the step-start solutions of the extrapolated guess [kQh][N].
 struct CkptHeader {
     char magic[8];
-    int32_t version, tuned_level;
+    int32_t version, tuned_level, tuned_stages, tuned_p2p_blocks;
     int64_t N, T, M;
     bem_step_params sp;
     double t, dt;
@@ -813,6 +813,8 @@ void step_save(Context &c, void *buf, int64_t cap) {
     std::memcpy(h.magic, kCkptMagic, 8);
     h.version = 1;
     h.tuned_level = c.tuned_level;
+    h.tuned_stages = c.tuned_stages;
+    h.tuned_p2p_blocks = c.tuned_p2p_blocks;
     h.N = N;
     h.T = c.T;
     h.M = c.M;
@@ -887,7 +889,12 @@ void step_load(Context &c, const void *buf, int64_t size) {
         s.qh_order[i] = h.qh_order[i];
         s.qh_time[i] = h.qh_time[i];
     }
-    if (h.tuned_level > 0) c.tuned_level = h.tuned_level;
+    if (h.tuned_level > 0 && c.prm.leaf_target == 0 && c.prm.fixed_level == 0) {
+        // the saved run's autotuned tiles (no new timing run on this mesh)
+        c.tuned_level = h.tuned_level;
+        c.tuned_stages = h.tuned_stages;
+        c.tuned_p2p_blocks = h.tuned_p2p_blocks;
+    }
     BEM_CUDA(cudaStreamSynchronize(c.stream));
 }
 
