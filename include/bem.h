@@ -130,6 +130,19 @@ typedef struct {
                                kernels of the concurrent stream. Same results either way.
                                -1 = automatic (the tile autotuner's choice when leaf_target = 0,
                                else 0). Default -1.                                           */
+    int32_t m2l_order_margin; /* truncation of each M2L translation by the separation of its
+                               offset class (Section 3.7 truncates every translation at p_fmm):
+                               -1 = every class at p_fmm; k >= 0 = class c at
+                               p_c = min(p_fmm, ceil(p_fmm ln(rho_0) / ln(rho_c)) + k), where
+                               rho_c = a / (|d_c| - a) is the convergence ratio of the
+                               multipole-to-local series for boxes whose centres are |d_c| box
+                               sizes apart (a = sqrt(3)/2, the box's circumradius) and rho_0 that
+                               of the nearest class (d = (2, 0, 0)): every class is truncated
+                               where its error bound falls to the nearest class's bound at p_fmm,
+                               k degrees further. Measured against the direct sum, k = 6 keeps
+                               the product error within ~5 % of the untruncated one at p_fmm 14
+                               (mixed) and within 2x at 16 (FP64), for about 38 % of the M2L
+                               multiply work. Default 6.                                      */
 } bem_params;
 
 /* Run-time counters of a context (cumulative since bem_create or bem_reset_stats). */
@@ -306,13 +319,17 @@ int bem_step_load(void *ctx, const void *buf, int64_t size);
 
 /* ------------------------------------------------------------------------------------------
  * Learned GMRES initial guess. The paper starts each solve from the previous step's q
- * (Sections 3.5, 3.8); that remains the fallback. Per bubble, the features are the
- * least-squares real spherical-harmonic coefficients (degree <= lmax, on the bubble's initial
- * directions, as in the shape filter, Eqs. (3.22)-(3.23)) of phi, of the previous q, and of the
- * previous q minus the q before it; a multilayer perceptron (3 hidden relu layers) predicts
- * the change of q's coefficients and the guess is q_prev + G y. Samples are recorded and the
- * guess is used in the Adams-Bashforth phase of bem_step (one solve per step). Products run on the tensor cores in BF16 with FP32
- * accumulation; weights keep an FP32 master copy; training is Adam on the mean squared error.
+ * (Sections 3.5, 3.8); that, or its extrapolation in t (bem_step_params.guess), is the base
+ * start and the fallback. Per bubble, the features are the least-squares real
+ * spherical-harmonic coefficients (degree <= lmax, on the bubble's initial directions, as in
+ * the shape filter, Eqs. (3.22)-(3.23)) of phi, of the base start q_b, and of q_b minus the base
+ * start of the solve before; a multilayer perceptron (3 hidden relu layers) predicts the
+ * correction of q's coefficients, c(q) - c(q_b), and the guess is q_b + G y. Features and
+ * targets are scaled per column by their root mean square over the recorded samples, computed
+ * when bem_mlp_train is called (those scales are not part of the parameter vector). Samples are
+ * recorded and the guess is used in the Adams-Bashforth phase of bem_step (one solve per step).
+ * Products run on the tensor cores in BF16 with FP32 accumulation; weights keep an FP32 master
+ * copy; training is Adam on the mean squared error.
  * ------------------------------------------------------------------------------------------ */
 typedef struct {
     int32_t dims[5];          /* layer widths: 3 (lmax+1)^2, hidden, hidden, hidden, (lmax+1)^2 */
@@ -321,18 +338,19 @@ typedef struct {
     int64_t samples;          /* recorded (features, target) rows, one per bubble per solve      */
     int64_t compared_solves;  /* solves run from both starts (compare mode)                      */
     int64_t iters_guess;      /* their GMRES iterations from the learned guess                    */
-    int64_t iters_fallback;   /* ... and from q_prev                                              */
+    int64_t iters_fallback;   /* ... and from the base start q_b                                  */
     double res0_guess;        /* summed initial relative residuals from the learned guess         */
-    double res0_fallback;     /* ... and from q_prev                                              */
+    double res0_fallback;     /* ... and from the base start q_b                                  */
 } bem_mlp_summary;
 
 /* Create the network (He initialisation from `seed`, output layer scaled by 0.1) after
  * bem_step_init. hidden: multiple of 16 in 16..256; lmax in 0..10. */
 int bem_mlp_init(void *ctx, int32_t hidden, int32_t lmax, uint64_t seed);
 
-/* record: store (features, c(q) - c(q_prev)) of every bubble at every solve of bem_step;
+/* record: store (features, c(q) - c(q_b)) of every bubble at every solve of bem_step;
  * use_guess: start every solve from the learned guess; compare: with use_guess, also solve from
- * q_prev (the result of that solve is discarded) and accumulate both iteration counts. */
+ * the base start q_b (the result of that solve is discarded) and accumulate both iteration
+ * counts. */
 int bem_mlp_set_mode(void *ctx, int32_t record, int32_t use_guess, int32_t compare);
 
 /* Adam (lr, beta = 0.9/0.999) over the recorded rows, in minibatches of `batch` rows, for
@@ -383,6 +401,12 @@ int bem_apply_direct_noalloc(int64_t N, const double *xyz, const double *s, cons
  * is the true relative residual of the returned q. Writes up to `max` values to out and the
  * total count to *count. */
 int bem_get_residual_history(void *ctx, double *out, int32_t max, int32_t *count);
+
+/* The truncation order p_c of each of the 316 M2L offset classes for expansion order p_fmm and
+ * margin (bem_params.m2l_order_margin; -1 = p_fmm for all). Classes are the offsets
+ * (x, y, z) in [-3, 3]^3 with max(|x|, |y|, |z|) >= 2 of the source box from the target box in
+ * units of the box size, in lexicographic order (x slowest). Needs no GPU. */
+int bem_m2l_orders(int32_t p_fmm, int32_t margin, int32_t *orders);
 
 /* Counters; see bem_stats. */
 int bem_get_stats(void *ctx, bem_stats *out);

@@ -39,6 +39,7 @@ EXPORTED = [
     "bem_get_residual_history", "bem_step_params_default", "bem_step_init", "bem_step",
     "bem_step_get_state", "bem_step_save", "bem_step_load", "bem_apply_direct_noalloc", "bem_mlp_init", "bem_mlp_set_mode", "bem_mlp_train",
     "bem_mlp_loss_grad", "bem_mlp_forward", "bem_mlp_get_params", "bem_mlp_set_params", "bem_mlp_info",
+    "bem_m2l_orders",
 ]
 
 BEM_NUM_PHASES = 15
@@ -61,6 +62,7 @@ class bem_params(ctypes.Structure):
         ("gmres_tol", ctypes.c_double),
         ("m2l_stages", ctypes.c_int32),
         ("p2p_blocks_per_sm", ctypes.c_int32),
+        ("m2l_order_margin", ctypes.c_int32),
     ]
 
 
@@ -188,6 +190,7 @@ def lib() -> ctypes.CDLL:
             "bem_mlp_get_params": ([vp, vp], ctypes.c_int),
             "bem_mlp_set_params": ([vp, vp], ctypes.c_int),
             "bem_mlp_info": ([vp, ctypes.POINTER(bem_mlp_summary)], ctypes.c_int),
+            "bem_m2l_orders": ([i32, i32, ctypes.POINTER(i32)], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -445,6 +448,15 @@ def bem_mlp_info(ctx) -> dict:
     st = bem_mlp_summary()
     _check(ctx, lib().bem_mlp_info(ctx, ctypes.byref(st)))
     return st.as_dict()
+
+
+def bem_m2l_orders(p_fmm: int, margin: int) -> list:
+    """Truncation order of each M2L offset class (316, lexicographic offsets)."""
+    out = (ctypes.c_int32 * 316)()
+    rc = lib().bem_m2l_orders(int(p_fmm), int(margin), out)
+    if rc != BEM_OK:
+        raise BemError(rc, "bad p_fmm or margin")
+    return [int(v) for v in out]
 
 
 def bem_get_stats(ctx) -> dict:

@@ -171,6 +171,7 @@ void check_params(const bem_params &p) {
     if (!(p.gmres_tol > 0.0)) fail(BEM_ERR_ARG, "gmres_tol must be > 0");
     if (p.m2l_stages != 0 && (p.m2l_stages < 3 || p.m2l_stages > 5)) fail(BEM_ERR_ARG, "m2l_stages must be 0 or 3..5");
     if (p.p2p_blocks_per_sm < -1 || p.p2p_blocks_per_sm > 16) fail(BEM_ERR_ARG, "p2p_blocks_per_sm must be in -1..16");
+    if (p.m2l_order_margin < -1 || p.m2l_order_margin > 20) fail(BEM_ERR_ARG, "m2l_order_margin must be in -1..20");
 }
 
 }  // namespace
@@ -456,6 +457,7 @@ int bem_params_default(bem_params *p) {
     p->gmres_tol = 1e-6;
     p->m2l_stages = 0;
     p->p2p_blocks_per_sm = -1;
+    p->m2l_order_margin = 6;
     return BEM_OK;
 }
 
@@ -880,6 +882,13 @@ const char *bem_phase_name(int i) {
     static const char *names[PH_COUNT] = {"geometry", "tree", "operators", "strengths", "p2m", "m2m", "m2l",
                                           "l2l", "l2p", "p2p", "direct", "diag", "gmres", "m2l_reduce", "m2l_cc"};
     return (i >= 0 && i < PH_COUNT) ? names[i] : nullptr;
+}
+
+int bem_m2l_orders(int32_t p_fmm, int32_t margin, int32_t *orders) {
+    if (!orders || p_fmm < 2 || p_fmm > kMaxPfmm || margin < -1) return BEM_ERR_ARG;
+    const std::vector<int> o = m2l_class_orders(p_fmm, margin);
+    for (int k = 0; k < kNumM2LClasses; ++k) orders[k] = o[k];
+    return BEM_OK;
 }
 
 int bem_reset_stats(void *ctx) {

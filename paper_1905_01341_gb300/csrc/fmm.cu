@@ -452,7 +452,8 @@ __device__ __forceinline__ void cp_async_elem(T *dst, const T *src, bool ok) {
 template <class T, int R, int MODE>
 __global__ void __launch_bounds__(XT_THREADS, 2) k_xlat(const T *__restrict__ mats, int P, const XChunk *__restrict__ chunks,
                                                      const int32_t *__restrict__ srcs, const int32_t *__restrict__ tgts,
-                                                     const T *X, T *Y) {  // X and Y may be one array (M2M, L2L)
+                                                     const T *X, T *Y,  // X and Y may be one array (M2M, L2L)
+                                                     const int32_t *__restrict__ cls_K) {
     constexpr int RT = xt_rt<T>(), CT = RT, ROWS = xt_rows<T>(), COLS = xt_cols<T>();
     constexpr int AP = xt_apitch<T>(), BP = xt_bpitch<T>(), VW = 16 / (int)sizeof(T);
     // XT_STAGES shared-memory stages of one K tile each: As[st][kk][row], Bs[st][kk][col]
@@ -463,6 +464,9 @@ __global__ void __launch_bounds__(XT_THREADS, 2) k_xlat(const T *__restrict__ ma
     const XChunk ch = chunks[blockIdx.x];
     const int row0 = blockIdx.y * ROWS;
     const T *A = mats + (size_t)ch.cls * P * P;
+    // truncated translation of this class (M2L with per-class orders): inputs and outputs of
+    // index < Kt; output rows from Kt on are written as zeros (kStorePair)
+    const int Kt = cls_K ? min(P, cls_K[ch.cls]) : P;
     const int ncol = ch.count * R;
     int tid = threadIdx.x;
     for (int e = tid; e < COLS; e += XT_THREADS) {
@@ -499,7 +503,7 @@ __global__ void __launch_bounds__(XT_THREADS, 2) k_xlat(const T *__restrict__ ma
             const int e = tid + it * XT_THREADS;
             const int row = e / XT_K, kk = e % XT_K;
             const int gr = row0 + row, gk = k0 + kk;
-            const bool ok = gr < P && gk < P;
+            const bool ok = gr < Kt && gk < Kt;
             const T *src = A + (ok ? (size_t)gr * P + gk : 0);
             cp_async_elem(As + (st * XT_K + kk) * AP + row, src, ok);
         }
@@ -508,13 +512,13 @@ __global__ void __launch_bounds__(XT_THREADS, 2) k_xlat(const T *__restrict__ ma
             const int e = tid + it * XT_THREADS;
             const int col = e / XT_K, kk = e % XT_K;
             const int gk = k0 + kk;
-            const bool ok = col < ncol && gk < P;
+            const bool ok = col < ncol && gk < Kt;
             const T *src = X + (ok ? ((size_t)s_src[col] * R + col % R) * P + gk : 0);
             cp_async_elem(Bs + (st * XT_K + kk) * BP + col, src, ok);
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    const int nk = (P + XT_K - 1) / XT_K;
+    const int nk = (Kt + XT_K - 1) / XT_K;
     // three stages: tiles t + 1 and t + 2 are in flight while tile t is multiplied
     cpload(0, 0);
     if (nk > 1) cpload(XT_K, 1);
@@ -526,7 +530,7 @@ __global__ void __launch_bounds__(XT_THREADS, 2) k_xlat(const T *__restrict__ ma
         __syncthreads();
         if (t + 2 < nk) cpload((t + 2) * XT_K, (t + 2) % XT_STAGES);
         else asm volatile("cp.async.commit_group;" ::: "memory");  // keeps one group per iteration
-        if (row0 + ty * RH < P && tx * CH < ncol) {  // rows past P and empty columns skip the products
+        if (row0 + ty * RH < Kt && tx * CH < ncol) {  // rows past Kt and empty columns skip the products
 #pragma unroll
             for (int kk = 0; kk < XT_K; ++kk) {
                 // two runs of consecutive rows / columns per thread, 16 bytes per load
@@ -559,7 +563,7 @@ __global__ void __launch_bounds__(XT_THREADS, 2) k_xlat(const T *__restrict__ ma
 #pragma unroll
         for (int i = 0; i < RT; ++i) {
             int gr = row0 + row_of(i);
-            if (gr < P) {
+            if (gr < Kt) {  // truncated rows (Kt < P) are never read
                 if (MODE == kStorePair) yb[gr] = acc[i][j];
                 else yb[gr] += acc[i][j];
             }
@@ -576,16 +580,22 @@ void xlat_smem_attr(K kern, size_t bytes) {
 
 // Y[t] += sum of Ypair[k] over the pairs k of target t, in ascending k (fixed order,
 // compensated in FP32). One thread per (target, coefficient).
+// With per-class truncation (pair_cls != nullptr) a pair's row holds only its class's first
+// cls_K coefficients; the rest were never written and count as zeros (skipping a zero leaves a
+// TwoSum accumulation unchanged, so the result is the same as summing the zeros).
 template <class T, int R>
 __global__ void k_reduce_pairs(int t0, const int32_t *__restrict__ off, const int32_t *__restrict__ by,
-                               const T *__restrict__ Ypair, int P, T *__restrict__ Y) {
+                               const T *__restrict__ Ypair, int P, T *__restrict__ Y,
+                               const uint32_t *__restrict__ pair_cls, const int32_t *__restrict__ cls_K) {
     int t = t0 + blockIdx.x;
     int e = blockIdx.y * blockDim.x + threadIdx.x;
     if (e >= R * P) return;
     int a = off[t], b = off[t + 1];
     if (a == b) return;
+    const int n = e % P;
     T s = 0, c = 0;
     for (int k = a; k < b; ++k) {
+        if (pair_cls && n >= cls_K[pair_cls[by[k]]]) continue;
         T v = Ypair[(size_t)by[k] * R * P + e];
         T tt = s + v;
         T bp = tt - s;
@@ -607,7 +617,8 @@ __device__ __forceinline__ void comp_add(float &s, float &c, float v) {
 template <int R>
 __global__ void __launch_bounds__(64) k_reduce_pairs4(int t0, const int32_t *__restrict__ off,
                                                       const int32_t *__restrict__ by, const float *__restrict__ Ypair,
-                                                      int P, float *__restrict__ Y) {
+                                                      int P, float *__restrict__ Y, const uint32_t *__restrict__ pair_cls,
+                                                      const int32_t *__restrict__ cls_K) {
     const int t = t0 + blockIdx.x;
     const int a = off[t], b = off[t + 1];
     if (a == b) return;
@@ -621,14 +632,24 @@ __global__ void __launch_bounds__(64) k_reduce_pairs4(int t0, const int32_t *__r
             comp_add(s2, c2, v.z);
             comp_add(s3, c3, v.w);
         };
-        int k = a;
-        for (; k + 1 < b; k += 2) {
-            const float4 v0 = Y4[(size_t)by[k] * rp4 + e];
-            const float4 v1 = Y4[(size_t)by[k + 1] * rp4 + e];
-            add(v0);
-            add(v1);
+        if (pair_cls) {
+            // truncated classes: the four coefficients (4e .. 4e + 3) % P lie on one side of the
+            // class's cls_K (a multiple of 16) together
+            const int n = (4 * e) % P;
+            for (int k = a; k < b; ++k) {
+                const int pk = by[k];
+                if (n < cls_K[pair_cls[pk]]) add(Y4[(size_t)pk * rp4 + e]);
+            }
+        } else {
+            int k = a;
+            for (; k + 1 < b; k += 2) {
+                const float4 v0 = Y4[(size_t)by[k] * rp4 + e];
+                const float4 v1 = Y4[(size_t)by[k + 1] * rp4 + e];
+                add(v0);
+                add(v1);
+            }
+            if (k < b) add(Y4[(size_t)by[k] * rp4 + e]);
         }
-        if (k < b) add(Y4[(size_t)by[k] * rp4 + e]);
         float4 *dst = reinterpret_cast<float4 *>(Y) + (size_t)t * rp4 + e;
         float4 y = *dst;
         y.x += s0 + c0;
@@ -642,17 +663,17 @@ __global__ void __launch_bounds__(64) k_reduce_pairs4(int t0, const int32_t *__r
 // Y[t] += sum over the pairs of t, for the targets t0 .. t0 + ntg - 1
 template <class T, int R>
 void launch_reduce_pairs(int t0, int ntg, const int32_t *off, const int32_t *by, const T *Ypair, int P, T *Y,
-                         cudaStream_t st) {
+                         cudaStream_t st, const uint32_t *pair_cls = nullptr, const int32_t *cls_K = nullptr) {
     if (ntg <= 0) return;
     if constexpr (sizeof(T) == 4) {
-        if ((R * P) % 4 == 0) {
-            k_reduce_pairs4<R><<<ntg, 64, 0, st>>>(t0, off, by, Ypair, P, Y);
+        if (P % 4 == 0) {
+            k_reduce_pairs4<R><<<ntg, 64, 0, st>>>(t0, off, by, Ypair, P, Y, pair_cls, cls_K);
             BEM_LAUNCH_CHECK();
             return;
         }
     }
     dim3 rg((unsigned)ntg, div_up(R * P, 128));
-    k_reduce_pairs<T, R><<<rg, 128, 0, st>>>(t0, off, by, Ypair, P, Y);
+    k_reduce_pairs<T, R><<<rg, 128, 0, st>>>(t0, off, by, Ypair, P, Y, pair_cls, cls_K);
     BEM_LAUNCH_CHECK();
 }
 
@@ -913,7 +934,7 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
         dim3 grid((unsigned)up_n[l], rowblocks);
         xlat_smem_attr(k_xlat<T, R, kStorePair>, xt_smem<T>());
         k_xlat<T, R, kStorePair><<<grid, XT_THREADS, xt_smem<T>(), fs>>>(m2m, P, c.m2l_chunks.p + up_first[l],
-                                                                         t.up_child.p, t.up_parent.p, mp, ypair);
+                                                                         t.up_child.p, t.up_parent.p, mp, ypair, nullptr);
         BEM_LAUNCH_CHECK();
         launch_reduce_pairs<T, R>(t.base[l - 1], t.nb[l - 1], t.up_par_off.p, t.up_by_par.p, ypair, P, mp, fs);
     }
@@ -945,11 +966,14 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
             dim3 grid((unsigned)nm2l_chunks, rowblocks);
             xlat_smem_attr(k_xlat<T, R, kStorePair>, xt_smem<T>());
             k_xlat<T, R, kStorePair><<<grid, XT_THREADS, xt_smem<T>(), fs>>>(m2l, P, c.m2l_chunks.p + 1,
-                                                                             t.m2l_src.p, t.m2l_tgt.p, mp, ypair);
+                                                                             t.m2l_src.p, t.m2l_tgt.p, mp, ypair,
+                                                                             opr.margin >= 0 ? opr.cls_K.p : nullptr);
             BEM_LAUNCH_CHECK();
         }
         PhaseScope ps(c, PH_M2L_REDUCE, fs);
-        launch_reduce_pairs<T, R>(t.base[2], t.nbox - t.base[2], t.m2l_tgt_off.p, t.m2l_by_tgt.p, ypair, P, lc, fs);
+        const bool trunc = opr.margin >= 0;
+        launch_reduce_pairs<T, R>(t.base[2], t.nbox - t.base[2], t.m2l_tgt_off.p, t.m2l_by_tgt.p, ypair, P, lc, fs,
+                                  trunc ? t.m2l_cls.p : nullptr, trunc ? opr.cls_K.p : nullptr);
     }
     // L2L downward, levels 3 -> L: every child has exactly one parent, so it adds in place
     for (int l = 3; l <= L; ++l) {
@@ -958,7 +982,7 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
         dim3 grid((unsigned)up_n[l], rowblocks);
         xlat_smem_attr(k_xlat<T, R, kAddTarget>, xt_smem<T>());
         k_xlat<T, R, kAddTarget><<<grid, XT_THREADS, xt_smem<T>(), fs>>>(l2l, P, c.m2l_chunks.p + up_first[l],
-                                                                         t.up_parent.p, t.up_child.p, lc, lc);
+                                                                         t.up_parent.p, t.up_child.p, lc, lc, nullptr);
         BEM_LAUNCH_CHECK();
     }
     // L2P
@@ -983,8 +1007,40 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
 
 }  // namespace
 
+// Truncation order of each M2L offset class (see bem_params.m2l_order_margin).
+std::vector<int> m2l_class_orders(int p, int margin) {
+    std::vector<int> out(kNumM2LClasses, p);
+    if (margin < 0) return out;
+    const double a = std::sqrt(3.0) / 2.0;  // circumradius of a unit box
+    const double rho0 = a / (2.0 - a);      // nearest class, centres 2 boxes apart
+    int cidx = 0;
+    for (int x = -3; x <= 3; ++x)
+        for (int y = -3; y <= 3; ++y)
+            for (int z = -3; z <= 3; ++z) {
+                if (x >= -1 && x <= 1 && y >= -1 && y <= 1 && z >= -1 && z <= 1) continue;
+                const double d = std::sqrt((double)(x * x + y * y + z * z));
+                const double rho = a / (d - a);
+                const int pc = (int)std::ceil(p * std::log(rho0) / std::log(rho) - 1e-9) + margin;
+                out[cidx++] = std::max(1, std::min(p, pc));
+            }
+    return out;
+}
+
 void build_operators(Context &c, Operators &o, int p) {
-    if (o.ready && o.p == p) return;
+    const int margin = c.prm.m2l_order_margin;
+    if (o.ready && o.p == p && o.margin == margin) return;
+    o.margin = margin;
+    {
+        o.cls_p = m2l_class_orders(p, margin);
+        const int Pfull16 = (p * p + 15) / 16 * 16;
+        std::vector<int32_t> K(kNumM2LClasses);
+        for (int k = 0; k < kNumM2LClasses; ++k)
+            K[k] = std::min(Pfull16, (o.cls_p[k] * o.cls_p[k] + 15) / 16 * 16);
+        o.cls_K.resize(kNumM2LClasses);
+        BEM_CUDA(cudaMemcpyAsync(o.cls_K.p, K.data(), K.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream));
+        BEM_CUDA(cudaStreamSynchronize(c.stream));
+        if (o.ready && o.p == p) return;  // only the truncation changed
+    }
     o.p = p;
     o.P = p * p;
     o.tc_Npad = o.tc_Kpad = 0;  // tensor-core tables follow the operators

@@ -125,6 +125,7 @@ struct Tree {
     // M2L: pairs of all levels sorted by offset class
     int64_t n_m2l = 0;
     DevBuf<int32_t> m2l_src, m2l_tgt;  // global box indices
+    DevBuf<uint32_t> m2l_cls;          // offset class of each pair (ascending)
     std::vector<int64_t> m2l_class_off;  // [kNumM2LClasses+1] host copy
     // M2M / L2L: per level l (1..L), child->parent pairs sorted by child octant
     std::vector<int64_t> up_off;       // per level: offset into up_child/up_parent
@@ -156,6 +157,12 @@ struct Operators {
     // in the K-major core-matrix layout (m2l_tc.cu); stored as raw 16-bit words
     int tc_Npad = 0, tc_Kpad = 0;
     DevBuf<uint16_t> m2l_tc;
+    // per-class M2L truncation: class c translates the coefficients of degrees < p_c, padded to
+    // the 16-wide steps of the products: cls_K[c] = 16 * ceil(p_c^2 / 16), capped at the full
+    // padded size (margin < 0: every class at p)
+    int margin = -1;
+    std::vector<int> cls_p;
+    DevBuf<int32_t> cls_K;
 };
 
 // Work chunk of the class-grouped translation product.
@@ -358,6 +365,8 @@ void exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *tot
 
 // fmm.cu
 void build_operators(Context &c, Operators &o, int p);
+// truncation order of each M2L offset class for expansion order p (bem_params.m2l_order_margin)
+std::vector<int> m2l_class_orders(int p, int margin);
 // out[r][i] (caller order) = sum over the R right-hand sides of the off-diagonal product:
 // f[r] (L_off xL[r]) + g[r] (M_off xM[r]); prec = bem_precision.
 void offdiag_apply(Context &c, int R, const double *f, const double *const *xL,

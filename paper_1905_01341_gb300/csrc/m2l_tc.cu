@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
                                                        const XChunk *__restrict__ chunks,
                                                        const int32_t *__restrict__ srcs, int64_t xrows,
                                                        const __nv_bfloat16 *__restrict__ Xs, float *__restrict__ Ypair,
-                                                       int *__restrict__ err) {
+                                                       const int32_t *__restrict__ cls_K, int *__restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned base for the operand stages
     unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -204,7 +204,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
     const XChunk ch = chunks[blockIdx.x];
     const int nrows = ch.count * R;
     const int ntiles = (nrows + TC_M - 1) / TC_M;  // <= TC_TILES
-    const int nsteps = Npad / TC_K;
+    // the class's truncated size (a multiple of 16, <= Npad): K steps and output columns
+    const int Kc = cls_K ? cls_K[ch.cls] : Npad;
+    const int nsteps = Kc / TC_K;
     for (int r = tid; r < TC_TILES * TC_M; r += TC_THREADS) s_src[r] = (r < nrows) ? srcs[ch.start + r / R] : -1;
     if (tid == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
@@ -223,10 +225,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
-    const uint32_t idesc = make_idesc(TC_M, Npad);
+    const uint32_t idesc = make_idesc(TC_M, Kc);
     const int Kp = Npad;
     const int64_t plane = xrows * Kp;
-    const __nv_bfloat16 *Bc = tcB + (size_t)ch.cls * nsteps * 3 * Npad * TC_K;
+    const __nv_bfloat16 *Bc = tcB + (size_t)ch.cls * (Npad / TC_K) * 3 * Npad * TC_K;  // the class's full table
     const uint32_t sbase = smem_u32(smem);
     const uint32_t apiece = TC_TILES * TC_M * TC_K * 2, atile = TC_M * TC_K * 2;
     const uint32_t bpiece = (uint32_t)Npad * TC_K * 2;
@@ -247,9 +249,14 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
             const uint32_t dst = sa + piece * apiece + t * atile + (uint32_t)kmajor_off(row, j * 8) * 2;
             cp_async16(dst, src, s >= 0 ? 16u : 0u);
         }
-        // B: contiguous pre-tiled block of the three pieces
+        // B: the first Kc rows of each piece's pre-tiled block (8-row core-matrix groups are
+        // contiguous, so that is a prefix of the block)
         const unsigned char *bsrc = reinterpret_cast<const unsigned char *>(Bc + (size_t)ks * 3 * Npad * TC_K);
-        for (int u = pt; u < (int)(Lo.b_bytes / 16); u += NPROD) cp_async16(sb + u * 16, bsrc + (size_t)u * 16, 16u);
+        const int per_piece = Kc * TC_K * 2 / 16;  // 16-byte units of one piece's prefix
+        for (int u = pt; u < 3 * per_piece; u += NPROD) {
+            const int piece = u / per_piece, v = u - piece * per_piece;
+            cp_async16(sb + piece * bpiece + v * 16, bsrc + (size_t)piece * bpiece + (size_t)v * 16, 16u);
+        }
     };
 
     // Warp-specialised pipeline. Producers (warps 1..) wait until the MMAs that last read a stage
@@ -325,6 +332,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
             const int ngroups = Npad / 16, g0 = half ? (ngroups + 1) / 2 : 0, g1 = half ? ngroups : (ngroups + 1) / 2;
             float *srow = stage + (size_t)(q4 * 32 + lane) * P;
             for (int c0 = g0 * 16; c0 < g1 * 16; c0 += 16) {
+                if (c0 >= Kc) continue;  // beyond the class's truncation: neither computed nor stored
                 uint32_t v[16];
                 const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(t * 256 + c0);
                 asm volatile(
@@ -345,8 +353,16 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
             __syncthreads();
             float4 *dst = reinterpret_cast<float4 *>(Ypair + ((size_t)ch.start * R + t * TC_M) * P);
             const float4 *src = reinterpret_cast<const float4 *>(stage);
-            const int n4 = rows_t * P / 4;
-            for (int e = tid; e < n4; e += TC_THREADS) dst[e] = src[e];
+            if (Kc >= P) {
+                const int n4 = rows_t * P / 4;
+                for (int e = tid; e < n4; e += TC_THREADS) dst[e] = src[e];
+            } else {  // the first Kc coefficients of each row; the per-target sums read no more
+                const int k4 = Kc / 4, p4 = P / 4;
+                for (int e = tid; e < rows_t * k4; e += TC_THREADS) {
+                    const int row = e / k4, col = e - row * k4;
+                    dst[row * p4 + col] = src[row * p4 + col];
+                }
+            }
             __syncthreads();
         }
     }
@@ -397,7 +413,8 @@ void launch_m2l_tc(Context &c, const Operators &o, const XChunk *chunks, int64_t
     // set on every launch: the attribute belongs to the current device (~1 us against a ms kernel)
     BEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_MAX_SMEM));
     kern<<<(unsigned)nchunks, TC_THREADS, sm, st>>>(o.P, Npad, reinterpret_cast<const __nv_bfloat16 *>(o.m2l_tc.p),
-                                                   chunks, c.tree.m2l_src.p, xrows, xs, Ypair, err);
+                                                   chunks, c.tree.m2l_src.p, xrows, xs, Ypair,
+                                                   o.margin >= 0 ? o.cls_K.p : nullptr, err);
     BEM_LAUNCH_CHECK();
 }
 

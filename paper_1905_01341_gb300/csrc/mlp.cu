@@ -7,8 +7,11 @@
 // q_prev2 the start of the solve before. Samples are taken in the Adams-Bashforth phase, where
 // consecutive solves are one step apart. A multilayer perceptron
 //   h1 = relu(W1 f + b1), h2 = relu(W2 h1 + b2), h3 = relu(W3 h2 + b3), y = W4 h3 + b4
-// predicts the change of q's coefficients, and the guess is q0_m = q_prev,m + G_m y_m.
-// Training minimises the mean of |y - (c(q) - c(q_prev))|^2 / 2 over recorded solves with Adam.
+// predicts the change of q's coefficients from the solve's base start q_prev (the extrapolated
+// guess when bem_step_params.guess >= 1, else the previous solve's q), and the guess is
+// q0_m = q_prev,m + G_m y_m. Features and targets are scaled per column by their root mean
+// square over the recorded samples (computed at training); training minimises the mean of
+// |y - (c(q) - c(q_prev)) / tscale|^2 / 2 over recorded solves with Adam.
 //
 // The matrix products run on the tensor cores (tcgen05.mma kind::f16, BF16 operands, FP32
 // accumulation in tensor memory); weights keep an FP32 master copy. Operands are loaded with
@@ -49,6 +52,10 @@ struct Mlp {
     bool record = false, use = false, compare = false;
     DevBuf<int> err;
     MlpStats stats;
+    // input and output scales of the recorded data (per column: the root mean square over the
+    // samples at the last training call; 1 before): the network sees features / fscale and is
+    // trained on targets / tscale, and its output is multiplied by tscale in the guess
+    DevBuf<float> fscale, tscale, Tb;
 };
 
 void mlp_free(Mlp *m) { delete m; }
@@ -279,16 +286,45 @@ __global__ void k_sh_project(int64_t M, const int64_t *__restrict__ voff, const 
 // q[a_m + i] = qprev[a_m + i] + sum_p G_m[i][p] y[m][p]
 __global__ void k_sh_synth_add(int64_t M, const int64_t *__restrict__ voff, const int32_t *__restrict__ shape_of,
                                const int64_t *__restrict__ g_off, int P, const double *__restrict__ G,
-                               const float *__restrict__ y, const double *__restrict__ qprev, double *__restrict__ q) {
+                               const float *__restrict__ y, const float *__restrict__ yscale,
+                               const double *__restrict__ qprev, double *__restrict__ q) {
     int m = blockIdx.x;
     int64_t a = voff[m];
     int nd = (int)(voff[m + 1] - a);
     const double *Gm = G + g_off[shape_of[m]];
     for (int i = threadIdx.x; i < nd; i += blockDim.x) {
         double s = qprev[a + i];
-        for (int p = 0; p < P; ++p) s = fma(Gm[(size_t)i * P + p], (double)y[(size_t)m * P + p], s);
+        for (int p = 0; p < P; ++p)
+            s = fma(Gm[(size_t)i * P + p], (double)y[(size_t)m * P + p] * (double)yscale[p], s);
         q[a + i] = s;
     }
+}
+
+// per column: out[j] = sqrt(mean_r X[r][j]^2) (1 where that is 0); one thread per column
+__global__ void k_col_rms(int64_t rows, int cols, const float *__restrict__ X, float *__restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= cols) return;
+    double s = 0.0;
+    for (int64_t r = 0; r < rows; ++r) {
+        const double v = X[r * cols + j];
+        s += v * v;
+    }
+    const double rms = sqrt(s / (double)(rows > 0 ? rows : 1));
+    out[j] = rms > 0.0 ? (float)rms : 1.f;
+}
+
+// y[r][j] = bf16(x[r][j] / scale[j]) for the network input
+__global__ void k_f2bf_scaled(int64_t n, int cols, const float *__restrict__ x, const float *__restrict__ scale,
+                              __nv_bfloat16 *__restrict__ y) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = __float2bfloat16(x[i] / scale[i % cols]);
+}
+
+// y[r][j] = x[r][j] / scale[j] (training targets)
+__global__ void k_div_cols(int64_t n, int cols, const float *__restrict__ x, const float *__restrict__ scale,
+                           float *__restrict__ y) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = x[i] / scale[i % cols];
 }
 
 // features [M][3P] (float): c(phi), c(q_prev), c(q_prev) - c(q_prev2); targets [M][P] = c(q) - c(q_prev)
@@ -424,6 +460,14 @@ void mlp_init(Context &c, int hidden, int lmax, uint64_t seed, const double *xyz
     m.ns = 0;
     m.wrows = 0;
     m.have_last = false;
+    {
+        std::vector<float> one(std::max(dims[0], dims[4]), 1.f);
+        m.fscale.resize(dims[0]);
+        m.tscale.resize(dims[4]);
+        BEM_CUDA(cudaMemcpyAsync(m.fscale.p, one.data(), dims[0] * sizeof(float), cudaMemcpyHostToDevice, c.stream));
+        BEM_CUDA(cudaMemcpyAsync(m.tscale.p, one.data(), dims[4] * sizeof(float), cudaMemcpyHostToDevice, c.stream));
+        BEM_CUDA(cudaStreamSynchronize(c.stream));
+    }
     // features basis from the initial shapes
     DevBuf<int> bad;
     bad.resize(1);
@@ -497,11 +541,11 @@ void mlp_before_solve(Context &c, const double *phi, double *q, bool uniform) {
                                  c.stream));
     }
     if (m.use && uniform) {
-        k_f2bf<<<div_up(M * 3 * P, 256), 256, 0, c.stream>>>(M * 3 * P, F.p, m.Hb[0].p);
+        k_f2bf_scaled<<<div_up(M * 3 * P, 256), 256, 0, c.stream>>>(M * 3 * P, 3 * P, F.p, m.fscale.p, m.Hb[0].p);
         BEM_LAUNCH_CHECK();
         forward(c, m, (int)M);
         k_sh_synth_add<<<(unsigned)M, 128, 0, c.stream>>>(M, voff.p, m.feat.shape_of.p, m.feat.g_off.p, P, m.feat.G.p,
-                                                          m.Z[3].p, m.qprev.p, q);
+                                                          m.Z[3].p, m.tscale.p, m.qprev.p, q);
         BEM_LAUNCH_CHECK();
     }
     BEM_CUDA(cudaStreamSynchronize(c.stream));
@@ -533,17 +577,24 @@ double mlp_train(Context &c, int epochs, int batch, double lr) {
     batch = (int)std::min<int64_t>(std::max(1, batch), m.ns);
     ensure_work(m, batch);
     const int P = m.Psh;
+    // column scales of the recorded features and targets (the network learns the scaled map)
+    k_col_rms<<<div_up(3 * P, 128), 128, 0, c.stream>>>(m.ns, 3 * P, m.SF.p, m.fscale.p);
+    k_col_rms<<<div_up(P, 128), 128, 0, c.stream>>>(m.ns, P, m.ST.p, m.tscale.p);
+    BEM_LAUNCH_CHECK();
+    m.Tb.resize((size_t)batch * P);
     double last = 0.0;
     for (int ep = 0; ep < epochs; ++ep) {
         double tot = 0.0;
         int nb = 0;
         for (int64_t r0 = 0; r0 < m.ns; r0 += batch) {
             const int rows = (int)std::min<int64_t>(batch, m.ns - r0);
-            k_f2bf<<<div_up((int64_t)rows * 3 * P, 256), 256, 0, c.stream>>>((int64_t)rows * 3 * P,
-                                                                               m.SF.p + r0 * 3 * P, m.Hb[0].p);
+            k_f2bf_scaled<<<div_up((int64_t)rows * 3 * P, 256), 256, 0, c.stream>>>(
+                (int64_t)rows * 3 * P, 3 * P, m.SF.p + r0 * 3 * P, m.fscale.p, m.Hb[0].p);
+            k_div_cols<<<div_up((int64_t)rows * P, 256), 256, 0, c.stream>>>((int64_t)rows * P, P, m.ST.p + r0 * P,
+                                                                             m.tscale.p, m.Tb.p);
             BEM_LAUNCH_CHECK();
             forward(c, m, rows);
-            backward(c, m, rows, m.ST.p + r0 * P);
+            backward(c, m, rows, m.Tb.p);
             m.adam_t += 1;
             const float b1 = 0.9f, b2 = 0.999f;
             const float c1 = 1.f - std::pow(b1, (float)m.adam_t), c2 = 1.f - std::pow(b2, (float)m.adam_t);

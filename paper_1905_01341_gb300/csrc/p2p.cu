@@ -53,8 +53,9 @@ struct V4<double> {
 };
 
 // Near-field work is split into units of up to 64 receivers of one leaf (Tree::p2p_units);
-// one warp owns a unit, each lane keeps up to two receivers in registers, so a staged source
-// feeds two pairs and a leaf of n receivers wastes at most 31 lanes of its last unit. The warp
+// one warp owns a unit and each lane keeps two receivers in registers, so a staged source feeds
+// two pairs; a unit of fewer receivers splits each source tile over groups of lanes instead of
+// leaving lanes idle. The warp
 // walks the (up to 27) neighbour leaves; each neighbour's sources are staged 32 at a time in
 // the warp's own shared-memory slice as (x, y, z, q) and (n_x, n_y, n_z, w), positions
 // relative to the target leaf's centre in leaf-box units. HQ / HW select the single- and
@@ -100,44 +101,52 @@ __device__ __forceinline__ void p2p_source(const P2PStage<T, R, HQ, HW> &sg, int
     }
 }
 
-template <class T, int R, int KR, bool HQ, bool HW, bool SELF>
-__device__ __forceinline__ void p2p_tile(const P2PStage<T, R, HQ, HW> &sg, int ns, const T *xi, const T *yi,
+// One staged tile of up to 32 sources against a lane's two receivers. The warp's lanes form G
+// groups of 32/G lanes; group gi takes the sources gi * 32/G .. (gi + 1) * 32/G - 1 of the tile,
+// so a unit of few receivers still keeps every lane busy (its groups' partial sums are merged
+// at the end of the unit).
+template <class T, int R, int G, bool HQ, bool HW, bool SELF>
+__device__ __forceinline__ void p2p_tile(const P2PStage<T, R, HQ, HW> &sg, int ns, int gi, const T *xi, const T *yi,
                                          const T *zi, Comp<T> (*acc)[R]) {
-    T part[KR][R];
+    constexpr int SG = 32 / G;  // sources per group and tile
+    T part[2][R];
 #pragma unroll
-    for (int k = 0; k < KR; ++k)
+    for (int k = 0; k < 2; ++k)
 #pragma unroll
         for (int r = 0; r < R; ++r) part[k][r] = (T)0;
+    const int s0 = gi * SG;
     if (ns == 32) {  // full tile: fixed trip count
 #pragma unroll 8
-        for (int s = 0; s < 32; ++s) p2p_source<T, R, KR, HQ, HW, SELF>(sg, s, xi, yi, zi, part);
+        for (int t = 0; t < SG; ++t) p2p_source<T, R, 2, HQ, HW, SELF>(sg, s0 + t, xi, yi, zi, part);
     } else {
+        const int e = min(SG, ns - s0);  // may be <= 0 for the groups past the tile's end
 #pragma unroll 2
-        for (int s = 0; s < ns; ++s) p2p_source<T, R, KR, HQ, HW, SELF>(sg, s, xi, yi, zi, part);
+        for (int t = 0; t < e; ++t) p2p_source<T, R, 2, HQ, HW, SELF>(sg, s0 + t, xi, yi, zi, part);
     }
 #pragma unroll
-    for (int k = 0; k < KR; ++k)
+    for (int k = 0; k < 2; ++k)
 #pragma unroll
         for (int r = 0; r < R; ++r) acc[k][r].add(part[k][r]);
 }
 
-// One work unit (up to 64 receivers of one leaf) by one warp.
-template <class T, int R, bool HQ, bool HW>
-__device__ __forceinline__ void p2p_unit(P2PStage<T, R, HQ, HW> &sg, int lane, int2 un,
-                                         const int32_t *__restrict__ bstart, const int32_t *__restrict__ bcount,
-                                         const int32_t *__restrict__ nbr, const int32_t *__restrict__ ncnt,
-                                         const int8_t *__restrict__ nd, int64_t N, const T *__restrict__ loc,
-                                         const T *__restrict__ nrm, const T *__restrict__ q, const T *__restrict__ w,
-                                         double *__restrict__ out) {
-    const int b = un.x, r0 = un.y;
+// One work unit (up to 64 receivers of one leaf) by one warp, its lanes split into G groups
+// (G = 1 for 33..64 receivers, 2 for 17..32, 4 for 9..16, 8 for 1..8): lane = gi * (32/G) + rs
+// holds the receivers rs and rs + 32/G and takes group gi's share of every source tile.
+template <class T, int R, int G, bool HQ, bool HW>
+__device__ __forceinline__ void p2p_unit_g(P2PStage<T, R, HQ, HW> &sg, int lane, int b, int r0, int nr,
+                                           const int32_t *__restrict__ bstart, const int32_t *__restrict__ bcount,
+                                           const int32_t *__restrict__ nbr, const int32_t *__restrict__ ncnt,
+                                           const int8_t *__restrict__ nd, int64_t N, const T *__restrict__ loc,
+                                           const T *__restrict__ nrm, const T *__restrict__ q, const T *__restrict__ w,
+                                           double *__restrict__ out) {
+    constexpr int LG = 32 / G;  // lanes per group
+    const int rs = lane & (LG - 1), gi = lane / LG;
     const int s0 = bstart[b];
-    const int nr = min(P2P_UNIT, bcount[b] - r0);
-    const bool two = nr > 32;  // uniform in the warp
     T xi[2], yi[2], zi[2];
     Comp<T> acc[2][R];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-        const int li = k * 32 + lane;
+        const int li = rs + k * LG;
         const int64_t i = s0 + r0 + (li < nr ? li : 0);
         xi[k] = loc[i];
         yi[k] = loc[N + i];
@@ -173,25 +182,49 @@ __device__ __forceinline__ void p2p_unit(P2PStage<T, R, HQ, HW> &sg, int lane, i
             }
             __syncwarp();
             const int ns = min(32, fc - t0);
-            if (self) {
-                if (two) p2p_tile<T, R, 2, HQ, HW, true>(sg, ns, xi, yi, zi, acc);
-                else p2p_tile<T, R, 1, HQ, HW, true>(sg, ns, xi, yi, zi, acc);
-            } else {
-                if (two) p2p_tile<T, R, 2, HQ, HW, false>(sg, ns, xi, yi, zi, acc);
-                else p2p_tile<T, R, 1, HQ, HW, false>(sg, ns, xi, yi, zi, acc);
-            }
+            if (self) p2p_tile<T, R, G, HQ, HW, true>(sg, ns, gi, xi, yi, zi, acc);
+            else p2p_tile<T, R, G, HQ, HW, false>(sg, ns, gi, xi, yi, zi, acc);
             __syncwarp();
         }
     }
+    // merge the groups' partial sums into group 0 (a fixed butterfly: deterministic)
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int li = k * 32 + lane;
-        if (li < nr) {
-            const int64_t i = s0 + r0 + li;
+    for (int off = LG; off < 32; off <<= 1)
 #pragma unroll
-            for (int r = 0; r < R; ++r) out[r * N + i] = acc[k][r].get();  // the far field is added later
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const T os = __shfl_xor_sync(0xffffffffu, acc[k][r].s, off);
+                const T oc = __shfl_xor_sync(0xffffffffu, acc[k][r].c, off);
+                acc[k][r].add(os);
+                acc[k][r].c += oc;
+            }
+    if (gi == 0) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int li = rs + k * LG;
+            if (li < nr) {
+                const int64_t i = s0 + r0 + li;
+#pragma unroll
+                for (int r = 0; r < R; ++r) out[r * N + i] = acc[k][r].get();  // the far field is added later
+            }
         }
     }
+}
+
+template <class T, int R, bool HQ, bool HW>
+__device__ __forceinline__ void p2p_unit(P2PStage<T, R, HQ, HW> &sg, int lane, int2 un,
+                                         const int32_t *__restrict__ bstart, const int32_t *__restrict__ bcount,
+                                         const int32_t *__restrict__ nbr, const int32_t *__restrict__ ncnt,
+                                         const int8_t *__restrict__ nd, int64_t N, const T *__restrict__ loc,
+                                         const T *__restrict__ nrm, const T *__restrict__ q, const T *__restrict__ w,
+                                         double *__restrict__ out) {
+    const int b = un.x, r0 = un.y;
+    const int nr = min(P2P_UNIT, bcount[b] - r0);  // uniform in the warp
+    if (nr > 32) p2p_unit_g<T, R, 1, HQ, HW>(sg, lane, b, r0, nr, bstart, bcount, nbr, ncnt, nd, N, loc, nrm, q, w, out);
+    else if (nr > 16) p2p_unit_g<T, R, 2, HQ, HW>(sg, lane, b, r0, nr, bstart, bcount, nbr, ncnt, nd, N, loc, nrm, q, w, out);
+    else if (nr > 8) p2p_unit_g<T, R, 4, HQ, HW>(sg, lane, b, r0, nr, bstart, bcount, nbr, ncnt, nd, N, loc, nrm, q, w, out);
+    else p2p_unit_g<T, R, 8, HQ, HW>(sg, lane, b, r0, nr, bstart, bcount, nbr, ncnt, nd, N, loc, nrm, q, w, out);
 }
 
 // Each warp takes the units u = blockIdx.x * P2P_WARPS + warp, then every gridDim.x * P2P_WARPS

@@ -491,6 +491,9 @@ void rhs(Context &c, StepState &s, const double *y, double t, double *f, bem_ste
         res0 = c.res_hist.empty() ? 0.0 : c.res_hist.front();
     };
     const bool learned = mlp_active(c);
+    // the base start of a step-start solve: the extrapolated guess (guess >= 1) or the previous q;
+    // the learned guess, when active, predicts its correction
+    if (start && extrap) extrapolate_guess(c, s, t);
     if (learned) {
         // samples and guesses only in the Adams-Bashforth phase (one solve per step)
         mlp_before_solve(c, phi_hat, s.q.p, s.nhist >= 5);  // with the network in use, s.q becomes its guess
@@ -508,7 +511,6 @@ void rhs(Context &c, StepState &s, const double *y, double t, double *f, bem_ste
             st.mvps += c.stats.last_mvps + 1;
         }
     }
-    if (start && extrap && !learned) extrapolate_guess(c, s, t);
     double res0 = 0.0;
     solve_from(s.q.p, it, rr, res0);
     if (start) record_start_solution(c, s, t);

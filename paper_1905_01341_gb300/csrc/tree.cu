@@ -758,10 +758,10 @@ void build_tree(Context &c) {
     }
     t.n_m2l = nm2l;
     DevBuf<int32_t> ptgt, psrc;
-    DevBuf<uint32_t> pcls;
+    DevBuf<uint32_t> &pcls = t.m2l_cls;  // sorted in place below: the class of every sorted pair
     ptgt.resize(nm2l);
     psrc.resize(nm2l);
-    pcls.resize(nm2l);
+    pcls.resize(std::max<int64_t>(nm2l, 1));
     for (int l = 2; l <= L; ++l) {
         int n = t.nb[l];
         if (!level_tot[l]) continue;

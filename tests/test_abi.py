@@ -110,3 +110,34 @@ def test_create_reports_errors_without_gpu(lib):
         pytest.skip("GPU present: covered by the GPU tests")
     with pytest.raises(bem.BemError):
         bem.bem_create(bem.bem_params_default(), 0)
+
+
+def test_m2l_class_orders_follow_the_separation():
+    """Per-class M2L truncation (host logic, no GPU): margin -1 keeps every class at p; otherwise
+    the six nearest classes (face offsets 2 boxes apart) keep p, orders never grow with the
+    distance of the offset, they are symmetric under sign flips and permutations of the axes
+    (the ratio depends on |d| only), and they shrink towards the far corners but stay >= 1."""
+    import math
+
+    from paper_1905_01341_gb300 import bem
+
+    offs = [(x, y, z) for x in range(-3, 4) for y in range(-3, 4) for z in range(-3, 4)
+            if max(abs(x), abs(y), abs(z)) >= 2]
+    assert len(offs) == 316
+    assert bem.bem_m2l_orders(14, -1) == [14] * 316
+    for p, margin in ((14, 6), (16, 6), (14, 0), (8, 2)):
+        o = bem.bem_m2l_orders(p, margin)
+        by = dict(zip(offs, o))
+        for d in ((2, 0, 0), (-2, 0, 0), (0, 2, 0), (0, 0, -2)):
+            assert by[d] == p
+        assert all(1 <= v <= p for v in o)
+        dist = {d: math.sqrt(sum(c * c for c in d)) for d in offs}
+        for d in offs:
+            for e in offs:
+                if dist[d] < dist[e] - 1e-12:
+                    assert by[d] >= by[e]
+            assert by[d] == by[tuple(-c for c in d)] == by[(d[1], d[2], d[0])]
+        assert by[(3, 3, 3)] < p or margin >= p
+    # more margin never lowers an order
+    a, b = bem.bem_m2l_orders(14, 2), bem.bem_m2l_orders(14, 6)
+    assert all(x <= y for x, y in zip(a, b))

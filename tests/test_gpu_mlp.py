@@ -42,11 +42,11 @@ def small_system(nb=8, level=3, seed=6):
     return mesh, phi
 
 
-def make_stepper(mesh, phi, **params):
+def make_stepper(mesh, phi, guess=0, **params):
     bem = _bem()
     ctx = bem.BemContext(**params)
     ctx.upload_mesh(mesh)
-    bem.bem_step_init(ctx.ctx, phi, bem.bem_step_params_default(pa=0.5, pf=6))
+    bem.bem_step_init(ctx.ctx, phi, bem.bem_step_params_default(pa=0.5, pf=6, guess=guess))
     return ctx
 
 
@@ -99,8 +99,11 @@ def test_forward_and_gradients_match_reference():
 
 def test_trained_guess_reduces_gmres_iterations():
     """Record the solves of 40 steps (35 in the Adams-Bashforth phase), train, then step on
-    with the learned guess while also solving from q_prev: the learned start has the smaller
-    initial residual and needs fewer GMRES iterations in total."""
+    with the learned guess while also solving from its base start, the previous step's q (the
+    paper's start, guess = 0): the learned start has the smaller initial residual and needs fewer
+    GMRES iterations in total. (Against the extrapolated start, guess = 2, the benchmark reports
+    the comparison; there the extrapolation already leaves a residual near the solves' own
+    accuracy and the learned correction gains little.)"""
     bem = _bem()
     mesh, phi = small_system(8)
     ctx = make_stepper(mesh, phi, mvp=bem.BEM_MVP_DIRECT, precision=bem.BEM_PREC_FP64, gmres_tol=1e-8)

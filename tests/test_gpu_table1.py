@@ -33,9 +33,12 @@ def test_table1_error_levels_131072():
     ref = oracle.offdiag_apply(xyz, np.ones(N), np.tile([0.0, 0.0, 1.0], (N, 1)), 1.0, q, 0.0, None, recv)
     paper = table1()
     errs = {}
-    for prec, col in ((bem.BEM_PREC_FP64, "double"), (bem.BEM_PREC_MIXED, "single")):
+    # the paper's FMM truncates every translation at p (m2l_order_margin = -1); the last column
+    # is this library's default per-class truncation (margin 6), for comparison
+    for prec, col, margin in ((bem.BEM_PREC_FP64, "double", -1), (bem.BEM_PREC_MIXED, "single", -1),
+                              (bem.BEM_PREC_FP64, "double-m6", 6)):
         for p in (4, 8, 12, 16, 20):
-            ctx = bem.BemContext(p_fmm=p, precision=prec, leaf_target=64)
+            ctx = bem.BemContext(p_fmm=p, precision=prec, leaf_target=64, m2l_order_margin=margin)
             bem.bem_points_upload(ctx.ctx, N, np.ascontiguousarray(xyz.T))
             ctx.build()
             out = torch.zeros(N, dtype=torch.float64, device="cuda")
@@ -51,3 +54,5 @@ def test_table1_error_levels_131072():
     for p in (4, 8, 12):
         assert errs[("single", p)] < 5 * paper[p]["single"]
     assert errs[("double", 4)] > errs[("double", 8)] > errs[("double", 12)] > errs[("double", 16)]
+    for p in (8, 12, 16):  # the default truncation costs at most a factor 3 in accuracy here
+        assert errs[("double-m6", p)] < 3 * errs[("double", p)]
