@@ -247,7 +247,9 @@ int bem_get_geometry(void *ctx, double *s, double *n, double *ldiag, double *mdi
  * (Eqs. (3.7)-(3.11)), mean curvature from a paraboloid through five neighbours
  * (Eqs. (parab1)-(parab2)), polytropic gas (Eq. (2.8)), spherical shape filter on the inputs
  * and outputs of every right-hand-side evaluation (Eqs. (3.22)-(3.25)), 6th-order
- * Adams-Bashforth started by 4th-order Runge-Kutta (Section 3.5).
+ * Adams-Bashforth started by 4th-order Runge-Kutta (Section 3.5) by default; the other schemes
+ * Section 3.5 names (Adams-Bashforth of orders 1-6, Adams-Bashforth-Moulton of orders 4-6,
+ * Runge-Kutta starts of orders 4-6) are selected in bem_step_params.
  * Dimensionless units: lengths by a0, pressure by p0, time by a0 (rho/p0)^(1/2); rho = p0 = 1.
  * ------------------------------------------------------------------------------------------ */
 typedef struct {
@@ -267,12 +269,20 @@ typedef struct {
                         step's time). Only the starting point of GMRES changes: every solve
                         still runs to gmres_tol. Not used while the learned guess is active.
                         Default 2 (degree 3 extrapolates the solves' rounding further).       */
+    int32_t ab_order;  /* order k of the Adams-Bashforth steps, 1..6 (Section 3.5). Default 6    */
+    int32_t corrector; /* 1: Adams-Moulton corrector of order k after each Adams-Bashforth
+                          prediction (a predictor-corrector, two right-hand sides per step; k in
+                          4..6). Default 0                                                    */
+    int32_t rk_order;  /* order of the Runge-Kutta steps that start the integration until k - 1
+                          past right-hand sides exist: 4 (classical), 5 (Butcher's six-stage) or
+                          6 (Butcher's seven-stage). Default 4                                 */
 } bem_step_params;
 
 typedef struct {
     double t;              /* time after the step                                              */
     double dt;             /* step size                                                        */
-    int32_t rhs_calls;     /* right-hand-side evaluations in the step (4 = RK4, 1 = AB6)        */
+    int32_t rhs_calls;     /* right-hand-side evaluations in the step (4/6/7 for an RK4/5/6 start
+                              step, 1 for Adams-Bashforth, 2 with the corrector)              */
     int32_t gmres_iters;   /* GMRES iterations summed over those evaluations                  */
     int32_t mvps;          /* operator products, counting each 4-RHS diagonal product once    */
     int32_t nonconverged;  /* solves that stopped at maxit (the step still advances)          */

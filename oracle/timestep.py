@@ -30,6 +30,43 @@ from . import BemOperator, solve
 
 AB6 = np.array([4277.0, -7923.0, 9982.0, -7298.0, 2877.0, -475.0]) / 1440.0  # f_n, f_{n-1}, ...
 
+# Section 3.5 names the schemes tried: Adams-Bashforth of orders 1-6, Adams-Bashforth-Moulton
+# predictor-correctors of orders 4-6, and Runge-Kutta starts of orders 4-6. Coefficients of the
+# k-step Adams-Bashforth formula y_{n+1} = y_n + dt sum_j b_j f_{n-j} (newest first), from the
+# integral of the interpolating polynomial through f_n .. f_{n-k+1}:
+ADAMS_BASHFORTH = {
+    1: np.array([1.0]),
+    2: np.array([3.0, -1.0]) / 2.0,
+    3: np.array([23.0, -16.0, 5.0]) / 12.0,
+    4: np.array([55.0, -59.0, 37.0, -9.0]) / 24.0,
+    5: np.array([1901.0, -2774.0, 2616.0, -1274.0, 251.0]) / 720.0,
+    6: AB6,
+}
+# Adams-Moulton correctors of order k: y_{n+1} = y_n + dt sum_j m_j f_{n+1-j}, j = 0 .. k-1
+# (f_{n+1} first, evaluated at the predicted state).
+ADAMS_MOULTON = {
+    4: np.array([9.0, 19.0, -5.0, 1.0]) / 24.0,
+    5: np.array([251.0, 646.0, -264.0, 106.0, -19.0]) / 720.0,
+    6: np.array([475.0, 1427.0, -798.0, 482.0, -173.0, 27.0]) / 1440.0,
+}
+# Runge-Kutta starts (Butcher tableaux: stage nodes c, coupling matrix a, weights b). Order 4:
+# the classical method; order 5: Butcher's six-stage method; order 6: Butcher's seven-stage
+# method with rational coefficients.
+RUNGE_KUTTA = {
+    4: (np.array([0.0, 0.5, 0.5, 1.0]),
+        [[], [0.5], [0.0, 0.5], [0.0, 0.0, 1.0]],
+        np.array([1.0, 2.0, 2.0, 1.0]) / 6.0),
+    5: (np.array([0.0, 0.25, 0.25, 0.5, 0.75, 1.0]),
+        [[], [0.25], [0.125, 0.125], [0.0, -0.5, 1.0], [3.0 / 16.0, 0.0, 0.0, 9.0 / 16.0],
+         [-3.0 / 7.0, 2.0 / 7.0, 12.0 / 7.0, -12.0 / 7.0, 8.0 / 7.0]],
+        np.array([7.0, 0.0, 32.0, 12.0, 32.0, 7.0]) / 90.0),
+    6: (np.array([0.0, 1.0 / 3.0, 2.0 / 3.0, 1.0 / 3.0, 0.5, 0.5, 1.0]),
+        [[], [1.0 / 3.0], [0.0, 2.0 / 3.0], [1.0 / 12.0, 1.0 / 3.0, -1.0 / 12.0],
+         [-1.0 / 16.0, 9.0 / 8.0, -3.0 / 16.0, -3.0 / 8.0], [0.0, 9.0 / 8.0, -3.0 / 8.0, -3.0 / 4.0, 0.5],
+         [9.0 / 44.0, -9.0 / 11.0, 63.0 / 44.0, 18.0 / 11.0, 0.0, -16.0 / 11.0]],
+        np.array([11.0, 0.0, 81.0, 81.0, -32.0, -32.0, 11.0]) / 120.0),
+}
+
 
 # ----------------------------------------------------------------------------- surface functions
 
@@ -161,6 +198,9 @@ class Physics:
     courant: float = 0.1       # C of Eq. (3.12)
     pf: int = 6                # filter bandwidth p_f
     gmres_tol: float = 1e-10
+    ab_order: int = 6          # Adams-Bashforth order k (1..6) after the Runge-Kutta start
+    corrector: bool = False    # Adams-Moulton corrector of order k (k = 4..6): two RHS per step
+    rk_order: int = 4          # Runge-Kutta order of the start steps (4, 5 or 6)
 
 
 @dataclass
@@ -246,11 +286,44 @@ class BubbleSystem:
             box["q"] = q
             return (dr, dp)
 
-        y, hist = ab6_rk4_step(f, (st.xyz, st.phi), st.t, self.dt, st.history)
+        ph = self.phys
+        y, hist = multistep(f, (st.xyz, st.phi), st.t, self.dt, st.history, ph.ab_order, ph.corrector, ph.rk_order)
         return State(xyz=y[0], phi=y[1], t=st.t + self.dt, q=box["q"], history=hist, steps=st.steps + 1)
 
     def equivalent_radius(self, xyz):
         return (3.0 * bubble_volumes(xyz, self.tri, self.tri_off) / (4.0 * math.pi)) ** (1.0 / 3.0)
+
+
+def multistep(f, y, t, dt, history, order=6, corrector=False, rk_order=4):
+    """One step of Section 3.5's family for y' = f(t, y), y a tuple of arrays.
+
+    history holds f at the previous step starts, newest first. While it has fewer than order - 1
+    entries the step is Runge-Kutta of rk_order (tableau RUNGE_KUTTA); afterwards Adams-Bashforth
+    of `order`, y* = y_n + dt sum_j b_j f_{n-j}; with `corrector`, y_{n+1} = y_n + dt (m_0 f(t+dt, y*)
+    + sum_{j>=1} m_j f_{n+1-j}) (Adams-Moulton of the same order, PECE). Returns (y_{n+1}, history
+    including f_n, at most 5 entries)."""
+    need = order - 1
+    if len(history) < need:
+        c, a, b = RUNGE_KUTTA[rk_order]
+        ks = []
+        for i in range(len(c)):
+            yi = y
+            for j, aij in enumerate(a[i]):
+                if aij != 0.0:
+                    yi = tuple(u + dt * aij * k for u, k in zip(yi, ks[j]))
+            ks.append(f(t + c[i] * dt, yi))
+        ynew = tuple(u + dt * sum(bi * k[m] for bi, k in zip(b, ks) if bi != 0.0) for m, u in enumerate(y))
+        return ynew, ([ks[0]] + list(history))[:5]
+    fn = f(t, y)
+    hist = [fn] + list(history[:5])
+    bb = ADAMS_BASHFORTH[order]
+    ynew = tuple(yi + dt * sum(cj * h[i] for cj, h in zip(bb, hist)) for i, yi in enumerate(y))
+    if corrector:
+        mm = ADAMS_MOULTON[order]
+        fp = f(t + dt, ynew)
+        terms = [fp] + hist[:order - 1]
+        ynew = tuple(yi + dt * sum(cj * h[i] for cj, h in zip(mm, terms)) for i, yi in enumerate(y))
+    return ynew, hist[:5]
 
 
 def ab6_rk4_step(f, y, t, dt, history):

@@ -97,6 +97,9 @@ class bem_step_params(ctypes.Structure):
         ("dt", ctypes.c_double),
         ("pf", ctypes.c_int32),
         ("guess", ctypes.c_int32),
+        ("ab_order", ctypes.c_int32),
+        ("corrector", ctypes.c_int32),
+        ("rk_order", ctypes.c_int32),
     ]
 
 

@@ -706,6 +706,9 @@ int bem_step_params_default(bem_step_params *sp) {
     sp->dt = 0.0;
     sp->pf = 6;
     sp->guess = 2;
+    sp->ab_order = 6;
+    sp->corrector = 0;
+    sp->rk_order = 4;
     return BEM_OK;
 }
 

@@ -23,6 +23,39 @@ namespace bem {
 constexpr int kGuessMax = 3;        // highest degree of the extrapolated initial guess
 constexpr int kQh = kGuessMax + 1;  // step-start solutions kept for it
 
+// Section 3.5's schemes. Adams-Bashforth of order k: y_{n+1} = y_n + dt sum_j b_j f_{n-j}
+// (newest first); Adams-Moulton corrector of order k: y_{n+1} = y_n + dt sum_j m_j f_{n+1-j}
+// (f_{n+1} first, at the predicted state); Runge-Kutta starts of order 4 (classical), 5
+// (Butcher's six-stage method) and 6 (Butcher's seven-stage method with rational coefficients).
+constexpr double kAB[6][6] = {
+    {1.0},
+    {3.0 / 2.0, -1.0 / 2.0},
+    {23.0 / 12.0, -16.0 / 12.0, 5.0 / 12.0},
+    {55.0 / 24.0, -59.0 / 24.0, 37.0 / 24.0, -9.0 / 24.0},
+    {1901.0 / 720.0, -2774.0 / 720.0, 2616.0 / 720.0, -1274.0 / 720.0, 251.0 / 720.0},
+    {4277.0 / 1440.0, -7923.0 / 1440.0, 9982.0 / 1440.0, -7298.0 / 1440.0, 2877.0 / 1440.0, -475.0 / 1440.0}};
+constexpr double kAM[3][6] = {  // orders 4, 5, 6
+    {9.0 / 24.0, 19.0 / 24.0, -5.0 / 24.0, 1.0 / 24.0},
+    {251.0 / 720.0, 646.0 / 720.0, -264.0 / 720.0, 106.0 / 720.0, -19.0 / 720.0},
+    {475.0 / 1440.0, 1427.0 / 1440.0, -798.0 / 1440.0, 482.0 / 1440.0, -173.0 / 1440.0, 27.0 / 1440.0}};
+struct Tableau {
+    int s;
+    double c[7], a[7][7], b[7];
+};
+const Tableau kRK[3] = {
+    {4, {0.0, 0.5, 0.5, 1.0}, {{0}, {0.5}, {0.0, 0.5}, {0.0, 0.0, 1.0}}, {1.0 / 6.0, 2.0 / 6.0, 2.0 / 6.0, 1.0 / 6.0}},
+    {6,
+     {0.0, 0.25, 0.25, 0.5, 0.75, 1.0},
+     {{0}, {0.25}, {0.125, 0.125}, {0.0, -0.5, 1.0}, {3.0 / 16.0, 0.0, 0.0, 9.0 / 16.0},
+      {-3.0 / 7.0, 2.0 / 7.0, 12.0 / 7.0, -12.0 / 7.0, 8.0 / 7.0}},
+     {7.0 / 90.0, 0.0, 32.0 / 90.0, 12.0 / 90.0, 32.0 / 90.0, 7.0 / 90.0}},
+    {7,
+     {0.0, 1.0 / 3.0, 2.0 / 3.0, 1.0 / 3.0, 0.5, 0.5, 1.0},
+     {{0}, {1.0 / 3.0}, {0.0, 2.0 / 3.0}, {1.0 / 12.0, 1.0 / 3.0, -1.0 / 12.0},
+      {-1.0 / 16.0, 9.0 / 8.0, -3.0 / 16.0, -3.0 / 8.0}, {0.0, 9.0 / 8.0, -3.0 / 8.0, -3.0 / 4.0, 0.5},
+      {9.0 / 44.0, -9.0 / 11.0, 63.0 / 44.0, 18.0 / 11.0, 0.0, -16.0 / 11.0}},
+     {11.0 / 120.0, 0.0, 81.0 / 120.0, 81.0 / 120.0, -32.0 / 120.0, -32.0 / 120.0, 11.0 / 120.0}}};
+
 struct StepState {
     bool ready = false;
     bem_step_params sp{};
@@ -31,7 +64,7 @@ struct StepState {
     int nhist = 0;  // valid history entries (newest at index 0 of `order`)
     int order[5] = {0, 1, 2, 3, 4};
     int Pf = 0;
-    DevBuf<double> y, q, hist, k1, k2, k3, k4, ytmp, yf, f;
+    DevBuf<double> y, q, hist, ks[7], ytmp, yf, f, fp;
     DevBuf<double> V0, a0, V, pg;
     DevBuf<int32_t> bub_of, nbr5;
     DevBuf<int64_t> voff, toff;
@@ -360,27 +393,17 @@ __global__ void k_assemble(int64_t N, const double *__restrict__ q, const double
     f[3 * N + j] = e - (pg[bub[j]] - 2.0 * sigma * H[j]) + F;
 }
 
-__global__ void k_axpy4(int64_t n, double a, const double *__restrict__ x, const double *__restrict__ y,
-                        double *__restrict__ out) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = y[i] + a * x[i];
-}
-
-__global__ void k_rk4_combine(int64_t n, double dt, const double *__restrict__ k1, const double *__restrict__ k2,
-                              const double *__restrict__ k3, const double *__restrict__ k4, double *__restrict__ y) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] += dt / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
-}
-
-struct Six {
-    const double *f[6];
-    double b[6];
+// out = y + dt * sum_j w_j f_j (j = 0 .. n-1, in order); out may alias y
+struct LinTerms {
+    const double *f[7];
+    double w[7];
+    int n;
 };
-__global__ void k_ab6(int64_t n, double dt, Six s, double *__restrict__ y) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+__global__ void k_lincomb(int64_t len, double dt, const double *__restrict__ y, LinTerms t, double *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
         double acc = 0.0;
-        for (int k = 0; k < 6; ++k) acc += s.b[k] * s.f[k][i];
-        y[i] += dt * acc;
+        for (int k = 0; k < t.n; ++k) acc += t.w[k] * t.f[k][i];
+        out[i] = y[i] + dt * acc;
     }
 }
 
@@ -496,7 +519,8 @@ void rhs(Context &c, StepState &s, const double *y, double t, double *f, bem_ste
     if (start && extrap) extrapolate_guess(c, s, t);
     if (learned) {
         // samples and guesses only in the Adams-Bashforth phase (one solve per step)
-        mlp_before_solve(c, phi_hat, s.q.p, s.nhist >= 5);  // with the network in use, s.q becomes its guess
+        // samples and guesses at the Adams-Bashforth step starts only (one per step)
+        mlp_before_solve(c, phi_hat, s.q.p, start && extrap);  // with the network in use, s.q becomes its guess
         if (mlp_compare(c)) {                 // the same solve from the fallback q_prev, for the record
             s.ytmp.resize(4 * N);
             DevBuf<double> qf;
@@ -648,6 +672,10 @@ void step_init(Context &c, const double *phi0_dev, const double *q0_dev, const b
     if (!c.mesh_ok) fail(BEM_ERR_NOT_BUILT, "no mesh uploaded");
     if (sp.pf < 0 || sp.pf > 11) fail(BEM_ERR_ARG, "pf must be in 0..11");
     if (sp.guess < 0 || sp.guess > kGuessMax) fail(BEM_ERR_ARG, "guess must be in 0..3");
+    if (sp.ab_order < 1 || sp.ab_order > 6) fail(BEM_ERR_ARG, "ab_order must be in 1..6");
+    if (sp.corrector != 0 && (sp.corrector != 1 || sp.ab_order < 4))
+        fail(BEM_ERR_ARG, "corrector must be 0, or 1 with ab_order 4..6");
+    if (sp.rk_order < 4 || sp.rk_order > 6) fail(BEM_ERR_ARG, "rk_order must be 4, 5 or 6");
     if (!(sp.pa > 0.0) && !(sp.dt > 0.0)) fail(BEM_ERR_ARG, "pa must be > 0 unless dt is given");
     StepState &s = state_of(c);
     const int64_t N = c.N, M = c.M;
@@ -659,7 +687,10 @@ void step_init(Context &c, const double *phi0_dev, const double *q0_dev, const b
     s.nhist = 0;
     s.qh_n = 0;
     for (int i = 0; i < 5; ++i) s.order[i] = i;
-    for (auto *b : {&s.y, &s.k1, &s.k2, &s.k3, &s.k4, &s.ytmp, &s.yf, &s.f}) b->resize(4 * N);
+    for (auto *b : {&s.y, &s.ytmp, &s.yf, &s.f}) b->resize(4 * N);
+    const int nstages = kRK[sp.rk_order - 4].s;
+    for (int i = 0; i < nstages; ++i) s.ks[i].resize(4 * N);
+    if (sp.corrector) s.fp.resize(4 * N);
     s.hist.resize(5 * 4 * N);
     s.q.resize(N);
     if (q0_dev) BEM_CUDA(cudaMemcpyAsync(s.q.p, q0_dev, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -724,41 +755,78 @@ void step_advance(Context &c, bem_step_stats &st) {
     const double dt = s.dt, t = s.t;
     cudaStream_t str = c.stream;
     const int g = grid_for(n4);
+    const int order = s.sp.ab_order;
     std::memset(&st, 0, sizeof(st));
     auto slot = [&](int i) { return s.hist.p + (size_t)s.order[i] * n4; };
-    if (s.nhist < 5) {
-        rhs(c, s, s.y.p, t, s.k1.p, st, true, false);
-        k_axpy4<<<g, 256, 0, str>>>(n4, 0.5 * dt, s.k1.p, s.y.p, s.ytmp.p);
-        BEM_LAUNCH_CHECK();
-        rhs(c, s, s.ytmp.p, t + 0.5 * dt, s.k2.p, st, false, false);
-        k_axpy4<<<g, 256, 0, str>>>(n4, 0.5 * dt, s.k2.p, s.y.p, s.ytmp.p);
-        BEM_LAUNCH_CHECK();
-        rhs(c, s, s.ytmp.p, t + 0.5 * dt, s.k3.p, st, false, false);
-        k_axpy4<<<g, 256, 0, str>>>(n4, dt, s.k3.p, s.y.p, s.ytmp.p);
-        BEM_LAUNCH_CHECK();
-        rhs(c, s, s.ytmp.p, t + dt, s.k4.p, st, false, false);
-        // push k1 (the RHS at the step start) to the history
-        int last = s.order[4];
+    // push f (the right-hand side at the step start) to the history, newest first
+    auto push = [&](const double *f) {
+        const int last = s.order[4];
         for (int i = 4; i > 0; --i) s.order[i] = s.order[i - 1];
         s.order[0] = last;
-        BEM_CUDA(cudaMemcpyAsync(slot(0), s.k1.p, n4 * sizeof(double), cudaMemcpyDeviceToDevice, str));
+        BEM_CUDA(cudaMemcpyAsync(slot(0), f, n4 * sizeof(double), cudaMemcpyDeviceToDevice, str));
         s.nhist = std::min(5, s.nhist + 1);
-        k_rk4_combine<<<g, 256, 0, str>>>(n4, dt, s.k1.p, s.k2.p, s.k3.p, s.k4.p, s.y.p);
+    };
+    auto lincomb = [&](const double *y, double h, const LinTerms &lt, double *out) {
+        k_lincomb<<<g, 256, 0, str>>>(n4, h, y, lt, out);
         BEM_LAUNCH_CHECK();
+    };
+    if (s.nhist < order - 1) {
+        // Runge-Kutta start: stage i at t + c_i dt from y + dt sum_j a_ij k_j
+        const Tableau &tb = kRK[s.sp.rk_order - 4];
+        for (int i = 0; i < tb.s; ++i) {
+            const double *yi = s.y.p;
+            if (i > 0) {
+                LinTerms lt{};
+                for (int j = 0; j < i; ++j)
+                    if (tb.a[i][j] != 0.0) {
+                        lt.f[lt.n] = s.ks[j].p;
+                        lt.w[lt.n] = tb.a[i][j];
+                        ++lt.n;
+                    }
+                lincomb(s.y.p, dt, lt, s.ytmp.p);
+                yi = s.ytmp.p;
+            }
+            rhs(c, s, yi, t + tb.c[i] * dt, s.ks[i].p, st, i == 0, false);
+        }
+        push(s.ks[0].p);
+        LinTerms lt{};
+        for (int i = 0; i < tb.s; ++i)
+            if (tb.b[i] != 0.0) {
+                lt.f[lt.n] = s.ks[i].p;
+                lt.w[lt.n] = tb.b[i];
+                ++lt.n;
+            }
+        lincomb(s.y.p, dt, lt, s.y.p);
     } else {
+        // Adams-Bashforth of the given order from f_n and the history
         rhs(c, s, s.y.p, t, s.f.p, st, true, true);
-        static const double b[6] = {4277.0 / 1440.0, -7923.0 / 1440.0, 9982.0 / 1440.0,
-                                    -7298.0 / 1440.0, 2877.0 / 1440.0, -475.0 / 1440.0};
-        Six six;
-        six.f[0] = s.f.p;
-        for (int i = 0; i < 5; ++i) six.f[i + 1] = slot(i);
-        for (int i = 0; i < 6; ++i) six.b[i] = b[i];
-        k_ab6<<<g, 256, 0, str>>>(n4, dt, six, s.y.p);
-        BEM_LAUNCH_CHECK();
-        int last = s.order[4];
-        for (int i = 4; i > 0; --i) s.order[i] = s.order[i - 1];
-        s.order[0] = last;
-        BEM_CUDA(cudaMemcpyAsync(slot(0), s.f.p, n4 * sizeof(double), cudaMemcpyDeviceToDevice, str));
+        LinTerms lt{};
+        lt.n = order;
+        lt.f[0] = s.f.p;
+        lt.w[0] = kAB[order - 1][0];
+        for (int j = 1; j < order; ++j) {
+            lt.f[j] = slot(j - 1);
+            lt.w[j] = kAB[order - 1][j];
+        }
+        if (s.sp.corrector) {
+            // predict, evaluate at t + dt, correct (Adams-Moulton of the same order)
+            lincomb(s.y.p, dt, lt, s.ytmp.p);
+            rhs(c, s, s.ytmp.p, t + dt, s.fp.p, st, false, false);
+            LinTerms lc{};
+            lc.n = order;
+            lc.f[0] = s.fp.p;
+            lc.w[0] = kAM[order - 4][0];
+            lc.f[1] = s.f.p;
+            lc.w[1] = kAM[order - 4][1];
+            for (int j = 2; j < order; ++j) {
+                lc.f[j] = slot(j - 2);
+                lc.w[j] = kAM[order - 4][j];
+            }
+            lincomb(s.y.p, dt, lc, s.y.p);
+        } else {
+            lincomb(s.y.p, dt, lt, s.y.p);
+        }
+        push(s.f.p);
     }
     s.t = t + dt;
     s.steps += 1;

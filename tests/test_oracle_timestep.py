@@ -175,3 +175,56 @@ def test_dphi_dt_on_a_sphere_converges_to_the_closed_form(pf):
     # measured: 7.1e-2, 2.0e-2, 5.6e-3, 1.9e-3 (about O(h^1.7))
     assert all(a / b > 2.5 for a, b in zip(errs[:-1], errs[1:]))
     assert errs[-1] < (2.5e-3 if pf == 0 else 7e-3)
+
+
+def _order_run(nsteps, **kw):
+    # y' = -y + cos t, y(0) = 1 on [0, 2]: y = (cos t + sin t)/2 + exp(-t)/2
+    def f(t, y):
+        return (-y[0] + math.cos(t),)
+
+    dt = 2.0 / nsteps
+    y, hist, t = (np.array(1.0),), [], 0.0
+    for _ in range(nsteps):
+        y, hist = ts.multistep(f, y, t, dt, hist, **kw)
+        t += dt
+    return abs(float(y[0]) - (0.5 * (math.cos(2.0) + math.sin(2.0)) + 0.5 * math.exp(-2.0)))
+
+
+@pytest.mark.parametrize("rk", [4, 5, 6])
+def test_runge_kutta_starts_reach_their_order(rk):
+    # only Runge-Kutta steps (order 7 never leaves the start phase): halving dt divides the error
+    # by about 2^rk
+    errs = []
+    for n in (10, 20, 40):
+        def f(t, y):
+            return (-y[0] + math.cos(t),)
+        dt = 2.0 / n
+        y, t = (np.array(1.0),), 0.0
+        for _ in range(n):
+            y, _h = ts.multistep(f, y, t, dt, [], 6, False, rk)  # empty history: always a start step
+            t += dt
+        errs.append(abs(float(y[0]) - (0.5 * (math.cos(2.0) + math.sin(2.0)) + 0.5 * math.exp(-2.0))))
+    rate = math.log2(errs[1] / errs[2])
+    assert rk - 0.3 < rate < rk + 0.7, (rk, errs)
+
+
+@pytest.mark.parametrize("order,corrector", [(1, False), (2, False), (3, False), (4, False), (5, False), (6, False),
+                                             (4, True), (5, True), (6, True)])
+def test_adams_schemes_reach_their_order(order, corrector):
+    # the multistep phase dominates at fine dt (the RK6 start is more accurate than any of them)
+    errs = [_order_run(n, order=order, corrector=corrector, rk_order=6) for n in (80, 160)]
+    rate = math.log2(errs[0] / errs[1])
+    assert order - 0.35 < rate < order + 0.8, (order, corrector, errs)
+    if corrector:  # the corrector is more accurate than the predictor of the same order
+        assert errs[1] < _order_run(160, order=order, corrector=False, rk_order=6)
+
+
+def test_ab6_rk4_default_is_the_family_default():
+    def f(t, y):
+        return (-y[0] + math.cos(t),)
+    y1, h1, y2, h2, t = (np.array(1.0),), [], (np.array(1.0),), [], 0.0
+    for _ in range(12):
+        y1, h1 = ts.ab6_rk4_step(f, y1, t, 0.1, h1)
+        y2, h2 = ts.multistep(f, y2, t, 0.1, h2)
+        t += 0.1
+    assert float(y1[0]) == float(y2[0])
