@@ -203,6 +203,15 @@ int bem_mesh_upload(void *ctx, int64_t N, const double *xyz, int64_t T, const in
  * cluster. */
 int bem_mesh_set_clusters(void *ctx, int64_t C, const int64_t *bubble_off);
 
+/* After a solve of a clustered mesh (bem_mesh_set_clusters with C > 1), per cluster: the GMRES
+ * iterations it took, its true relative residual |b_c - L_c q_c| / |b_c|, and the device ms from
+ * the start of that solve until its solution was final; *solve_ms gets the solve's device ms.
+ * Clustered solves run one GMRES per cluster in lockstep (Section 3.8 for each cluster's own
+ * system): one operator product per iteration serves all clusters, and each cluster stops and
+ * takes its solution at the iteration where its own residual meets gmres_tol (a single
+ * Krylov space over all clusters would stop on the global residual). Any array may be NULL. */
+int bem_get_cluster_stats(void *ctx, int64_t C, int32_t *iters, double *relres, double *done_ms, double *solve_ms);
+
 /* Section 3.9 (Table 1): upload N free points (SoA xyz[3N]) instead of a mesh, for the FMM's
  * accuracy study with monopoles. Weights are 1 and there is no singular diagonal, so after
  * fmm_build, bem_apply(ctx, 1, q, 0, NULL, out) gives out_i = sum_{j != i} q_j / (4 pi |r_i - r_j|). */

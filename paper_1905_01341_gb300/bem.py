@@ -39,7 +39,7 @@ EXPORTED = [
     "bem_get_residual_history", "bem_step_params_default", "bem_step_init", "bem_step",
     "bem_step_get_state", "bem_step_save", "bem_step_load", "bem_apply_direct_noalloc", "bem_mlp_init", "bem_mlp_set_mode", "bem_mlp_train",
     "bem_mlp_loss_grad", "bem_mlp_forward", "bem_mlp_get_params", "bem_mlp_set_params", "bem_mlp_info",
-    "bem_m2l_orders",
+    "bem_m2l_orders", "bem_get_cluster_stats",
 ]
 
 BEM_NUM_PHASES = 15
@@ -194,6 +194,7 @@ def lib() -> ctypes.CDLL:
             "bem_mlp_set_params": ([vp, vp], ctypes.c_int),
             "bem_mlp_info": ([vp, ctypes.POINTER(bem_mlp_summary)], ctypes.c_int),
             "bem_m2l_orders": ([i32, i32, ctypes.POINTER(i32)], ctypes.c_int),
+            "bem_get_cluster_stats": ([vp, i64, vp, vp, vp, ctypes.POINTER(dbl)], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -451,6 +452,17 @@ def bem_mlp_info(ctx) -> dict:
     st = bem_mlp_summary()
     _check(ctx, lib().bem_mlp_info(ctx, ctypes.byref(st)))
     return st.as_dict()
+
+
+def bem_get_cluster_stats(ctx, C) -> dict:
+    """Per-cluster GMRES iterations, true relative residuals and device ms until final of the
+    last clustered solve, and that solve's device ms."""
+    it = np.zeros(C, np.int32)
+    rr = np.zeros(C)
+    ms = np.zeros(C)
+    sm = ctypes.c_double(0.0)
+    _check(ctx, lib().bem_get_cluster_stats(ctx, int(C), _ptr(it), _ptr(rr), _ptr(ms), ctypes.byref(sm)))
+    return {"iters": it, "relres": rr, "done_ms": ms, "solve_ms": float(sm.value)}
 
 
 def bem_m2l_orders(p_fmm: int, margin: int) -> list:

@@ -12,6 +12,7 @@ namespace bem {
 long long g_launch_count = 0;
 
 Context::~Context() {
+    for (auto e : cl_events) cudaEventDestroy(e);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
     if (ev_far) cudaEventDestroy(ev_far);
@@ -430,7 +431,8 @@ void solve_internal(Context &c, const double *phi, double *q, int *it, double *r
     apply_full(c, 0.0, nullptr, 1.0, phi, c.bv.p);
     k_rhs_combine<<<div_up(c.N, 256), 256, 0, c.stream>>>(c.N, phi, c.bv.p);
     BEM_LAUNCH_CHECK();
-    gmres_solve(c, c.bv.p, q, it, rr);
+    if (c.C > 1) gmres_solve_batched(c, c.bv.p, q, it, rr);
+    else gmres_solve(c, c.bv.p, q, it, rr);
 }
 
 }  // namespace bem
@@ -885,6 +887,19 @@ const char *bem_phase_name(int i) {
     static const char *names[PH_COUNT] = {"geometry", "tree", "operators", "strengths", "p2m", "m2m", "m2l",
                                           "l2l", "l2p", "p2p", "direct", "diag", "gmres", "m2l_reduce", "m2l_cc"};
     return (i >= 0 && i < PH_COUNT) ? names[i] : nullptr;
+}
+
+int bem_get_cluster_stats(void *ctx, int64_t C, int32_t *iters, double *relres, double *done_ms, double *solve_ms) {
+    return guarded(ctx, [&](Context &c) {
+        if (C != c.C) fail(BEM_ERR_ARG, "C must equal the context's cluster count");
+        if (c.cl_iters.size() != (size_t)C) fail(BEM_ERR_NOT_BUILT, "no clustered solve has run");
+        for (int64_t k = 0; k < C; ++k) {
+            if (iters) iters[k] = c.cl_iters[k];
+            if (relres) relres[k] = c.cl_relres[k];
+            if (done_ms) done_ms[k] = c.cl_done_ms[k];
+        }
+        if (solve_ms) *solve_ms = c.cl_solve_ms;
+    });
 }
 
 int bem_m2l_orders(int32_t p_fmm, int32_t margin, int32_t *orders) {

@@ -341,6 +341,21 @@ struct Context {
         DevBuf<double> bub_scale;         // [M] 1 / (mean centroid distance) at the current geometry
     } bp;
     HostPinned<double> hscal;
+    // GMRES of independent clusters (gmres_batched.cu): reduction segments and per-cluster state
+    struct BatchedGmres {
+        int C = 0, nseg = 0;
+        int64_t N = 0;
+        DevBuf<int64_t> s0, s1;
+        DevBuf<int32_t> seg_off, active, sel, kk;
+        DevBuf<double> partial, h, h2, H, cs, sn, g, y, nrm2, res;
+    } gb;
+    // per cluster, for the last solve: GMRES iterations, true relative residual, device ms from
+    // the start of the solve until the cluster's solution was final; and the solve's device ms
+    std::vector<int> cl_iters;
+    std::vector<double> cl_relres, cl_done_ms;
+    double cl_solve_ms = 0.0;
+    std::vector<cudaEvent_t> cl_events;
+    int cl_events_used = 0;
 
     bem_stats stats{};
     std::vector<double> res_hist;  // residual estimates |g_{k+1}|/|b| of the last solve
@@ -392,8 +407,9 @@ void launch_m2l_tc(Context &c, const Operators &o, const XChunk *chunks, int64_t
                    int *err, cudaStream_t st);
 int m2l_tc_pairs_per_chunk(int R);
 
-// gmres.cu
+// gmres.cu, gmres_batched.cu (clusters: one GMRES per cluster, in lockstep)
 void gmres_solve(Context &c, const double *b, double *x, int *iters, double *relres);
+void gmres_solve_batched(Context &c, const double *b, double *x, int *iters, double *relres);
 
 inline PhaseScope::PhaseScope(Context &cc, int ph) : PhaseScope(cc, ph, cc.stream) {}
 inline PhaseScope::PhaseScope(Context &cc, int ph, cudaStream_t st) : c(&cc), phase(ph), s(st) {

@@ -71,6 +71,47 @@ def test_cluster_products_and_solve_match_separate_oracles(prec, p, tol, gtol):
         qr.append(qq)
         a += m.n
     assert rel(q, np.concatenate(qr)) < 50 * tol
+    # every cluster met the tolerance on its own system, and its solution matches its oracle
+    cs = bem.bem_get_cluster_stats(ctx.ctx, len(parts))
+    assert np.all(cs["relres"] <= gtol) and np.all(cs["iters"] >= 1) and np.all(cs["iters"] <= it)
+    assert np.all(cs["done_ms"] > 0) and np.all(cs["done_ms"] <= cs["solve_ms"] + 1e-6)
+    a = 0
+    for m, qq in zip(parts, qr):
+        assert rel(q[a:a + m.n], qq) < 50 * tol
+        a += m.n
+    ctx.close()
+
+
+def test_each_cluster_meets_its_own_tolerance():
+    """One cluster's right-hand side is 1e-4 of the others': a single Krylov space over the
+    stacked system stops on the global residual and would leave it far from converged; the
+    per-cluster solves stop on each cluster's own residual: every cluster's solution has a small
+    true residual against its own oracle operator."""
+    from paper_1905_01341_gb300 import bem
+
+    mesh, parts, boff = _clusters()
+    ctx = bem.BemContext(mvp=bem.BEM_MVP_FMM, precision=0, p_fmm=18, leaf_target=32, gmres_tol=1e-8,
+                         gmres_maxit=400, gmres_restart=100, gmres_precond=2)
+    ctx.upload_mesh(mesh)
+    bem.bem_mesh_set_clusters(ctx.ctx, len(parts), boff)
+    ctx.build()
+    rng = np.random.Generator(np.random.PCG64(43))
+    phi = rng.standard_normal(mesh.n) * 0.1 + 1.0
+    a0, a1 = parts[0].n, parts[0].n + parts[1].n
+    phi[a0:a1] *= 1e-4  # the second cluster
+    q = np.zeros(mesh.n)
+    it, rr = ctx.solve(phi, q)
+    cs = bem.bem_get_cluster_stats(ctx.ctx, len(parts))
+    print("per-cluster iterations", cs["iters"], "relres", ["%.1e" % v for v in cs["relres"]],
+          "done ms", ["%.2f" % v for v in cs["done_ms"]], "solve ms %.2f" % cs["solve_ms"])
+    assert np.all(cs["relres"] <= 1e-8)
+    a = 0
+    for m in parts:
+        op = oracle.BemOperator(m.xyz, m.tri)
+        b = op.rhs(phi[a:a + m.n])
+        true = np.linalg.norm(b - op.apply_L(q[a:a + m.n])) / np.linalg.norm(b)
+        assert true < 2e-6  # the FP64 FMM operator at p = 18 is within ~1e-6 of the oracle's
+        a += m.n
     ctx.close()
 
 
