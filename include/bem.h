@@ -305,9 +305,13 @@ int bem_step_params_default(bem_step_params *sp);
 /* Start a time integration from the uploaded mesh (r at t = 0), phi0[N] and an optional
  * initial guess q0[N] for the first GMRES solve (NULL = zeros). Builds one shape
  * filter per distinct initial bubble shape (bubbles whose unit directions from their centroid
- * coincide share it), the five-neighbour lists of the curvature fit, V_m0 and a_m0, and the
- * step size. Returns BEM_ERR_MESH when a bubble's filter is singular or a vertex has fewer
- * than five neighbours. */
+ * coincide share it): the spherical filter (real spherical harmonics of degrees 0..p_f-1) for a
+ * sphere-like bubble (Euler characteristic V - T/2 = 2), the toroidal filter (real 2D Fourier
+ * basis of the torus angles, |n|, |m| <= p_f/2, Eq. (spherical7)) for a ring-like one (0); the
+ * torus axis is the direction of least second moment of the bubble's initial vertices about its
+ * centroid. Also the five-neighbour lists of the curvature fit, V_m0 and a_m0, and the step
+ * size. Returns BEM_ERR_MESH when a bubble is neither sphere- nor ring-like, its filter is
+ * singular, or a vertex has fewer than five neighbours. */
 int bem_step_init(void *ctx, const double *phi0, const double *q0, const bem_step_params *sp);
 
 /* Advance one step; st may be NULL. */
@@ -363,7 +367,8 @@ typedef struct {
 } bem_mlp_summary;
 
 /* Create the network (He initialisation from `seed`, output layer scaled by 0.1) after
- * bem_step_init. hidden: multiple of 16 in 16..256; lmax in 0..10. */
+ * bem_step_init. hidden: multiple of 16 in 16..256; lmax in 0..10. The features use spherical
+ * harmonics: BEM_ERR_MESH when a bubble is not sphere-like. */
 int bem_mlp_init(void *ctx, int32_t hidden, int32_t lmax, uint64_t seed);
 
 /* record: store (features, c(q) - c(q_b)) of every bubble at every solve of bem_step;

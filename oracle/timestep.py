@@ -186,6 +186,51 @@ def filter_factors(dirs, pf):
     return G, Gp
 
 
+def euler_characteristic(n_vertices, n_triangles):
+    """V - E + F of a closed triangulated surface (E = 3F/2): 2 for a sphere, 0 for a torus."""
+    return n_vertices - n_triangles // 2
+
+
+def torus_angles(xyz):
+    """Toroidal and poloidal angles (phi, theta) of the points of a ring-shaped surface: the axis
+    is the principal direction of least spread about the centroid, phi the angle about it and
+    theta the angle about the centre circle (radius: the mean distance from the axis)."""
+    d = xyz - xyz.mean(axis=0)
+    w, v = np.linalg.eigh(d.T @ d)
+    a = v[:, 0]  # smallest second moment: the axis of the ring
+    e1 = v[:, 2]
+    e2 = np.cross(a, e1)
+    u, vv, z = d @ e1, d @ e2, d @ a
+    phi = np.arctan2(vv, u)
+    rho = np.hypot(u, vv)
+    theta = np.arctan2(z, rho - rho.mean())
+    return phi, theta
+
+
+def real_torus_basis(phi, theta, pf):
+    """The toroidal filter's basis (the 2D Fourier basis e^{i(n theta + m phi)}, |n|, |m| <= p_f/2,
+    in its real form, Eq. (spherical7)): 1, and cos/sin(n theta + m phi) for each pair +-(n, m)
+    with n > 0, or n = 0 and m > 0: (2h + 1)^2 columns, h = floor(p_f / 2)."""
+    h = pf // 2
+    cols = [np.ones_like(phi)]
+    for n in range(0, h + 1):
+        for m in range(-h, h + 1):
+            if n == 0 and m <= 0:
+                continue
+            arg = n * theta + m * phi
+            cols += [np.cos(arg), np.sin(arg)]
+    return np.stack(cols, axis=1)
+
+
+def torus_filter_factors(xyz, pf):
+    """The toroidal filter (Section 3.6, Eq. (spherical7)): G of real_torus_basis at the points'
+    torus angles and G^(-1) = (G^T G)^(-1) G^T."""
+    phi, theta = torus_angles(xyz)
+    G = real_torus_basis(phi, theta, pf)
+    Gp = np.linalg.solve(G.T @ G, G.T)
+    return G, Gp
+
+
 # ----------------------------------------------------------------------------- state and RHS
 
 
@@ -235,7 +280,15 @@ class BubbleSystem:
                     self.filter_of[m] = fi
                     break
             else:
-                G, Gp = filter_factors(d, phys.pf)
+                # sphere-like bubbles (Euler characteristic 2) take the spherical filter, ring-like
+                # ones (0) the toroidal filter of Eq. (spherical7)
+                chi = euler_characteristic(b - a, self.tri_off[m + 1] - self.tri_off[m])
+                if chi == 2:
+                    G, Gp = filter_factors(d, phys.pf)
+                elif chi == 0:
+                    G, Gp = torus_filter_factors(xyz0[a:b], phys.pf)
+                else:
+                    raise ValueError("bubble %d: no shape filter for Euler characteristic %d" % (m, chi))
                 self.filters.append((d, G, Gp))
                 self.filter_of[m] = len(self.filters) - 1
         self.V0 = bubble_volumes(xyz0, self.tri, self.tri_off)

@@ -444,7 +444,7 @@ void step_get_state(Context &c, double *xyz, double *phi, double *q, double *t);
 int64_t step_checkpoint_size(const Context &c);
 void step_save(Context &c, void *buf, int64_t cap);
 void step_load(Context &c, const void *buf, int64_t size);
-void build_sh_basis(Context &c, int pf, ShBasis &B, int *bad, const double *xyz = nullptr);
+void build_sh_basis(Context &c, int pf, ShBasis &B, int *bad, const double *xyz = nullptr, bool allow_torus = false);
 // Groups the bubbles by shape from host coordinates hx [3][N] (timestep.cu).
 void find_shapes(const Context &c, const std::vector<double> &hx, std::vector<BubbleShape> &shapes,
                  std::vector<int32_t> &shape_of);

@@ -153,23 +153,25 @@ __device__ void real_sh_row(double dx, double dy, double dz, int pf, double *out
 
 // G[i][*] for the unit directions of one shape (from its representative bubble).
 __global__ void k_filter_G(int nd, const double *__restrict__ xyz, int64_t N, int64_t v0, double cx, double cy,
-                           double cz, int pf, double *__restrict__ G, double *__restrict__ scratch) {
+                           double cz, int pf, int ld, double *__restrict__ G, double *__restrict__ scratch) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nd) return;
     int64_t j = v0 + i;
-    real_sh_row(xyz[j] - cx, xyz[N + j] - cy, xyz[2 * N + j] - cz, pf, G + (size_t)i * pf * pf,
+    real_sh_row(xyz[j] - cx, xyz[N + j] - cy, xyz[2 * N + j] - cz, pf, G + (size_t)i * ld,
                 scratch + (size_t)i * pf * pf);
 }
 
-// Gp = (G^T G)^(-1) G^T by Cholesky (one block). A: scratch [Pf][Pf].
-__global__ void k_filter_pinv(int nd, int P, const double *__restrict__ G, double *__restrict__ A,
+// Gp = (G^T G)^(-1) G^T by Cholesky (one block) for the first P columns of G (rows of length
+// ld); rows P..ld-1 of Gp are zero. A: scratch [P][P].
+__global__ void k_filter_pinv(int nd, int P, int ld, const double *__restrict__ G, double *__restrict__ A,
                               double *__restrict__ Gp, int *__restrict__ bad) {
     for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
         int a = e / P, b = e % P;
         double s = 0.0;
-        for (int i = 0; i < nd; ++i) s += G[(size_t)i * P + a] * G[(size_t)i * P + b];
+        for (int i = 0; i < nd; ++i) s += G[(size_t)i * ld + a] * G[(size_t)i * ld + b];
         A[e] = s;
     }
+    for (size_t e = threadIdx.x; e < (size_t)(ld - P) * nd; e += blockDim.x) Gp[(size_t)P * nd + e] = 0.0;
     __syncthreads();
     if (threadIdx.x == 0) {  // in-place Cholesky, lower triangle
         for (int k = 0; k < P; ++k) {
@@ -193,7 +195,7 @@ __global__ void k_filter_pinv(int nd, int P, const double *__restrict__ G, doubl
     for (int i = threadIdx.x; i < nd; i += blockDim.x) {
         double x[128];
         for (int a = 0; a < P; ++a) {
-            double s = G[(size_t)i * P + a];
+            double s = G[(size_t)i * ld + a];
             for (int m = 0; m < a; ++m) s -= A[a * P + m] * x[m];
             x[a] = s / A[a * P + a];
         }
@@ -628,7 +630,111 @@ void find_shapes(const Context &c, const std::vector<double> &hx, std::vector<Bu
     }
 }
 
-void build_sh_basis(Context &c, int pf, ShBasis &B, int *bad, const double *xyz) {
+// Eigenvector of the smallest eigenvalue of a symmetric 3x3 matrix (cyclic Jacobi rotations).
+static void smallest_eigvec3(double A[3][3], double out[3]) {
+    double V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    for (int sweep = 0; sweep < 50; ++sweep) {
+        const double off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+        if (off < 1e-30 * (A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2] + 1e-300)) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                if (A[p][q] == 0.0) continue;
+                const double th = 0.5 * (A[q][q] - A[p][p]) / A[p][q];
+                const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+                const double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
+                for (int k = 0; k < 3; ++k) {  // A <- A J
+                    const double akp = A[k][p], akq = A[k][q];
+                    A[k][p] = cs * akp - sn * akq;
+                    A[k][q] = sn * akp + cs * akq;
+                }
+                for (int k = 0; k < 3; ++k) {  // A <- J^T A
+                    const double apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = cs * apk - sn * aqk;
+                    A[q][k] = sn * apk + cs * aqk;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    const double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = cs * vkp - sn * vkq;
+                    V[k][q] = sn * vkp + cs * vkq;
+                }
+            }
+    }
+    int m = 0;
+    for (int k = 1; k < 3; ++k)
+        if (A[k][k] < A[m][m]) m = k;
+    for (int k = 0; k < 3; ++k) out[k] = V[k][m];
+}
+
+// Rows of the toroidal filter's basis (Section 3.6, Eq. (spherical7), in real form) for the nd
+// points of a ring-shaped bubble starting at vertex v0 of the host coordinates hx [3][N]: the
+// axis is the direction of least second moment about the centroid, phi the angle about it,
+// theta the angle about the centre circle (radius: the mean distance from the axis); columns 1
+// and cos / sin(n theta + m phi) for |n|, |m| <= h with n > 0, or n = 0 and m > 0.
+static void torus_rows(const std::vector<double> &hx, int64_t N, int64_t v0, int nd, int h, int ld,
+                       std::vector<double> &G) {
+    double c[3] = {0, 0, 0};
+    for (int i = 0; i < nd; ++i)
+        for (int d = 0; d < 3; ++d) c[d] += hx[d * N + v0 + i];
+    for (double &v : c) v /= nd;
+    double S[3][3] = {{0}};
+    for (int i = 0; i < nd; ++i) {
+        double d[3];
+        for (int k = 0; k < 3; ++k) d[k] = hx[k * N + v0 + i] - c[k];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) S[a][b] += d[a] * d[b];
+    }
+    double ax[3];
+    smallest_eigvec3(S, ax);
+    // e1: the coordinate axis least aligned with the ring axis, projected; e2 = ax x e1
+    int m0 = 0;
+    for (int k = 1; k < 3; ++k)
+        if (std::fabs(ax[k]) < std::fabs(ax[m0])) m0 = k;
+    double e1[3] = {0, 0, 0};
+    e1[m0] = 1.0;
+    const double dp = e1[0] * ax[0] + e1[1] * ax[1] + e1[2] * ax[2];
+    double n1 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        e1[k] -= dp * ax[k];
+        n1 += e1[k] * e1[k];
+    }
+    for (double &v : e1) v /= std::sqrt(n1);
+    const double e2[3] = {ax[1] * e1[2] - ax[2] * e1[1], ax[2] * e1[0] - ax[0] * e1[2], ax[0] * e1[1] - ax[1] * e1[0]};
+    std::vector<double> fphi(nd), rho(nd), z(nd);
+    double rmean = 0.0;
+    for (int i = 0; i < nd; ++i) {
+        double d[3];
+        for (int k = 0; k < 3; ++k) d[k] = hx[k * N + v0 + i] - c[k];
+        const double u = d[0] * e1[0] + d[1] * e1[1] + d[2] * e1[2];
+        const double v = d[0] * e2[0] + d[1] * e2[1] + d[2] * e2[2];
+        z[i] = d[0] * ax[0] + d[1] * ax[1] + d[2] * ax[2];
+        fphi[i] = std::atan2(v, u);
+        rho[i] = std::hypot(u, v);
+        rmean += rho[i];
+    }
+    rmean /= nd;
+    G.assign((size_t)nd * ld, 0.0);
+    for (int i = 0; i < nd; ++i) {
+        const double th = std::atan2(z[i], rho[i] - rmean);
+        double *row = G.data() + (size_t)i * ld;
+        int col = 0;
+        row[col++] = 1.0;
+        for (int n = 0; n <= h; ++n)
+            for (int m = -h; m <= h; ++m) {
+                if (n == 0 && m <= 0) continue;
+                const double arg = n * th + m * fphi[i];
+                row[col++] = std::cos(arg);
+                row[col++] = std::sin(arg);
+            }
+    }
+}
+
+// One least-squares basis per distinct initial bubble shape (bubbles whose unit directions from
+// their centroid coincide share it): the real spherical harmonics of degrees 0..pf-1 (pf^2
+// columns) for sphere-like bubbles (Euler characteristic 2), the real 2D Fourier basis of the
+// torus angles with |n|, |m| <= pf/2 ((2 floor(pf/2) + 1)^2 columns) for ring-like bubbles
+// (Euler characteristic 0) when allow_torus is set. Every shape's G is stored with B.Pf
+// columns, the largest count, zero-padded (a zero column adds nothing to the projection).
+void build_sh_basis(Context &c, int pf, ShBasis &B, int *bad, const double *xyz, bool allow_torus) {
     const int64_t N = c.N, M = c.M;
     cudaStream_t st = c.stream;
     if (!xyz) xyz = c.xyz.p;
@@ -641,23 +747,46 @@ void build_sh_basis(Context &c, int pf, ShBasis &B, int *bad, const double *xyz)
         std::vector<BubbleShape> shapes;
         std::vector<int32_t> shape_of;
         find_shapes(c, hx, shapes, shape_of);
-        for (const BubbleShape &sh : shapes)
-            if (sh.nd < B.Pf) fail(BEM_ERR_MESH, "bubble with fewer vertices than filter coefficients");
+        const int h = pf / 2, Ptor = (2 * h + 1) * (2 * h + 1);
+        std::vector<int> kind(shapes.size(), 0), Pk(shapes.size(), pf * pf);  // 0 sphere, 1 torus
+        for (size_t k = 0; k < shapes.size(); ++k) {
+            const int64_t r = shapes[k].rep;
+            const int64_t chi = (int64_t)shapes[k].nd - (c.tri_off[r + 1] - c.tri_off[r]) / 2;
+            if (chi == 0 && allow_torus) {
+                kind[k] = 1;
+                Pk[k] = Ptor;
+            } else if (chi != 2) {
+                fail(BEM_ERR_MESH, "shape filter: bubble " + std::to_string(r) + " is neither sphere- nor ring-like " +
+                                       "(Euler characteristic " + std::to_string(chi) + ")");
+            }
+        }
+        B.Pf = *std::max_element(Pk.begin(), Pk.end());
+        for (size_t k = 0; k < shapes.size(); ++k)
+            if (shapes[k].nd < Pk[k]) fail(BEM_ERR_MESH, "bubble with fewer vertices than filter coefficients");
         std::vector<int64_t> goff(shapes.size() + 1, 0);
         for (size_t k = 0; k < shapes.size(); ++k) goff[k + 1] = goff[k] + (int64_t)shapes[k].nd * B.Pf;
         B.G.resize(goff.back());
         B.Gp.resize(goff.back());
+        BEM_CUDA(cudaMemsetAsync(B.G.p, 0, goff.back() * sizeof(double), st));
         DevBuf<double> scratch, A;
         int ndmax = 0;
         for (auto &sh : shapes) ndmax = std::max(ndmax, sh.nd);
-        scratch.resize((size_t)ndmax * B.Pf);
+        scratch.resize((size_t)ndmax * pf * pf);
         A.resize((size_t)B.Pf * B.Pf);
+        std::vector<double> Gt;
         for (size_t k = 0; k < shapes.size(); ++k) {
             const BubbleShape &sh = shapes[k];
-            k_filter_G<<<div_up(sh.nd, 128), 128, 0, st>>>(sh.nd, xyz, N, c.vert_off[sh.rep], sh.cx, sh.cy, sh.cz,
-                                                           pf, B.G.p + goff[k], scratch.p);
-            BEM_LAUNCH_CHECK();
-            k_filter_pinv<<<1, 256, 0, st>>>(sh.nd, B.Pf, B.G.p + goff[k], A.p, B.Gp.p + goff[k], bad);
+            if (kind[k] == 0) {
+                k_filter_G<<<div_up(sh.nd, 128), 128, 0, st>>>(sh.nd, xyz, N, c.vert_off[sh.rep], sh.cx, sh.cy, sh.cz,
+                                                               pf, B.Pf, B.G.p + goff[k], scratch.p);
+                BEM_LAUNCH_CHECK();
+            } else {
+                torus_rows(hx, N, c.vert_off[sh.rep], sh.nd, h, B.Pf, Gt);
+                BEM_CUDA(cudaMemcpyAsync(B.G.p + goff[k], Gt.data(), Gt.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                         st));
+                BEM_CUDA(cudaStreamSynchronize(st));  // Gt is reused
+            }
+            k_filter_pinv<<<1, 256, 0, st>>>(sh.nd, Pk[k], B.Pf, B.G.p + goff[k], A.p, B.Gp.p + goff[k], bad);
             BEM_LAUNCH_CHECK();
         }
         B.shape_of.resize(M);
@@ -738,7 +867,7 @@ void step_init(Context &c, const double *phi0_dev, const double *q0_dev, const b
         s.dt = sp.courant * mn / std::sqrt(sp.pa);
     }
     // shape filters: one per distinct set of unit directions from the bubble centroid
-    build_sh_basis(c, sp.pf, s.filt, bad.p);
+    build_sh_basis(c, sp.pf, s.filt, bad.p, nullptr, true);
     s.Pf = s.filt.Pf;
     int hb = 0;
     BEM_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));

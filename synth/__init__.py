@@ -237,6 +237,41 @@ def perturbed_sphere(level: int, shape: dict[tuple[int, int], float]) -> Mesh:
                    {"kind": "perturbed_sphere", "level": level, "shape": {f"{k}": c for k, c in shape.items()}})
 
 
+def torus_bubble(R: float, r: float, n_phi: int, n_theta: int, centre=(0.0, 0.0, 0.0), axis=(0.0, 0.0, 1.0)) -> Mesh:
+    """A toroidal bubble: the surface ((R + r cos t) cos f, (R + r cos t) sin f, r sin t) about
+    `axis` through `centre`, sampled on an n_phi x n_theta grid of the toroidal angle f and the
+    poloidal angle t, each grid cell split into two triangles, counter-clockwise seen from the
+    liquid (outward normals)."""
+    a = np.asarray(axis, dtype=np.float64)
+    a = a / np.linalg.norm(a)
+    e1 = np.cross(a, [1.0, 0.0, 0.0] if abs(a[0]) < 0.9 else [0.0, 1.0, 0.0])
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(a, e1)
+    f = 2.0 * math.pi * np.arange(n_phi) / n_phi
+    t = 2.0 * math.pi * np.arange(n_theta) / n_theta
+    F, T = np.meshgrid(f, t, indexing="ij")
+    rho = R + r * np.cos(T)
+    pts = (rho * np.cos(F))[..., None] * e1 + (rho * np.sin(F))[..., None] * e2 + (r * np.sin(T))[..., None] * a
+    xyz = pts.reshape(-1, 3) + np.asarray(centre, dtype=np.float64)
+    idx = lambda i, j: (i % n_phi) * n_theta + (j % n_theta)  # noqa: E731
+    tri = []
+    for i in range(n_phi):
+        for j in range(n_theta):
+            p00, p10, p11, p01 = idx(i, j), idx(i + 1, j), idx(i + 1, j + 1), idx(i, j + 1)
+            tri += [(p00, p10, p11), (p00, p11, p01)]
+    tri = np.array(tri, dtype=np.int32)
+    # orient outward: the normal of the first triangle must point away from the tube's centre line
+    c0 = np.asarray(centre, dtype=np.float64)
+    v0, v1, v2 = xyz[tri[0, 0]], xyz[tri[0, 1]], xyz[tri[0, 2]]
+    nrm = np.cross(v1 - v0, v2 - v0)
+    mid = (v0 + v1 + v2) / 3.0 - c0
+    ring = mid - np.dot(mid, a) * a
+    ring = R * ring / np.linalg.norm(ring)
+    if np.dot(nrm, mid - ring) < 0.0:
+        tri = tri[:, [0, 2, 1]]
+    return _single(xyz, tri, c0, r, {"kind": "torus", "R": R, "r": r, "n_phi": n_phi, "n_theta": n_theta})
+
+
 # --------------------------------------------------------------------------------------
 # clusters
 # --------------------------------------------------------------------------------------

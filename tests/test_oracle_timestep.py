@@ -228,3 +228,42 @@ def test_ab6_rk4_default_is_the_family_default():
         y2, h2 = ts.multistep(f, y2, t, 0.1, h2)
         t += 0.1
     assert float(y1[0]) == float(y2[0])
+
+
+def test_torus_mesh_and_angles():
+    R, r = 2.0, 0.6
+    m = synth.torus_bubble(R, r, 32, 16, centre=(0.5, -1.0, 2.0), axis=(1.0, 1.0, 0.3))
+    assert ts.euler_characteristic(m.n, m.t) == 0
+    assert ts.euler_characteristic(*[x.shape[0] for x in synth.icosphere(3)]) == 2
+    # outward normals: positive volume close to 2 pi^2 R r^2 (inscribed polyhedron: a little less)
+    V = ts.bubble_volumes(m.xyz, m.tri, m.tri_off)[0]
+    assert 0.95 < V / (2 * math.pi ** 2 * R * r * r) < 1.0
+    # the recovered angles are the generating ones up to a constant shift and orientation
+    phi, theta = ts.torus_angles(m.xyz)
+    f = 2 * math.pi * np.repeat(np.arange(32), 16) / 32
+    t = 2 * math.pi * np.tile(np.arange(16), 32) / 16
+    for got, want in ((phi, f), (theta, t)):
+        ok = False
+        for sgn in (1, -1):
+            dd = np.angle(np.exp(1j * (sgn * got - want)))
+            ok = ok or np.std(np.angle(np.exp(1j * (dd - dd[0])))) < 1e-9
+        assert ok
+
+
+def test_toroidal_filter_is_an_orthogonal_projector_onto_low_frequencies():
+    m = synth.torus_bubble(2.0, 0.7, 36, 18)
+    G, Gp = ts.torus_filter_factors(m.xyz, 6)
+    assert G.shape == (m.n, 49)
+    F = G @ Gp
+    assert np.allclose(F, F.T, atol=1e-11) and np.allclose(F @ F, F, atol=1e-11)
+    phi, theta = ts.torus_angles(m.xyz)
+    low = np.cos(2 * theta - phi) + 0.5 * np.sin(3 * phi) - 0.2 * np.cos(theta + 3 * phi)
+    assert np.allclose(F @ low, low, atol=1e-10)
+    high = np.cos(7 * theta + phi)  # outside |n|, |m| <= 3
+    assert np.linalg.norm(F @ high) < 1e-8 * np.linalg.norm(high) + 1e-8
+    saw = (-1.0) ** np.arange(m.n)  # the grid-scale mode the filter exists to remove
+    assert np.linalg.norm(F @ saw) < 0.05 * np.linalg.norm(saw)
+    # a torus bubble in a system gets the toroidal filter; spheres keep the spherical one
+    mesh = synth.concat_meshes([m, synth.sphere_bubble(2, 0.5, centre=(0.0, 0.0, 3.0))])[0]
+    sysm = ts.BubbleSystem(mesh.xyz, mesh.tri, mesh.vert_off, mesh.tri_off, ts.Physics(pf=6))
+    assert [f[1].shape[1] for f in sysm.filters] == [49, 36]
