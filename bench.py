@@ -436,7 +436,7 @@ def run_ours(args):
     pairs = st["p2p_pairs"]
     work = {
         "p2p": (P2P_FLOPS_SL * n_sl + P2P_FLOPS_DL * n_dl + P2P_FLOPS_4RHS * n_r4) * pairs / args.steps,
-        "m2l": 2.0 * P * P * st["m2l_pairs"] * (n_r1 + 4 * n_r4) / args.steps,
+        "m2l": 2.0 * st["m2l_macs"] * (n_r1 + 4 * n_r4) / args.steps,
     }
     launches = {k: prof[k][1] / args.steps for k in ("p2p", "m2l")}
 
@@ -464,7 +464,7 @@ def run_ours(args):
         if not (prec == bem.BEM_PREC_MIXED and args.m2l_tc and n_i > 0 and ms_i > 0):
             return None
         t_launch = ms_i / 1e3 / n_i
-        achieved = M2L_TC_PRODUCTS * 2.0 * P * P * st_iso["m2l_pairs"] / t_launch / 1e12
+        achieved = M2L_TC_PRODUCTS * 2.0 * st_iso["m2l_macs"] / t_launch / 1e12
         pk = PEAKS.get("bf16_tflops_sustained")
         return {"kernel": "k_m2l_tc (M2L)", "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
                 "frac": achieved / pk if pk else None,
@@ -473,7 +473,9 @@ def run_ours(args):
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS, long loop)",
                 "launch_ms": t_launch * 1e3, "launches_timed": n_i,
                 "launch_ms_in_step": per_step.get("m2l", 0) / max(1.0, launches["m2l"]),
-                "work_per_launch": "6 BF16 products x 2 P^2 flops x %d M2L translations" % st_iso["m2l_pairs"],
+                "work_per_launch": "6 BF16 products x 2 flops x %d multiply-adds (%d M2L translations, each "
+                                   "truncated to its class's order, sizes padded to 16)" % (st_iso["m2l_macs"],
+                                                                                            st_iso["m2l_pairs"]),
                 "timing": "single-layer products on the step's geometry, phases run one after another"}
 
     roof_p2p, roof_m2l = p2p_roofline(), m2l_roofline()

@@ -160,6 +160,9 @@ typedef struct {
     int64_t n_launches;     /* kernels launched by the library in this process (all contexts)   */
     int32_t m2l_stages;     /* tensor-core M2L pipeline stages in use (0 = deepest that fits)   */
     int32_t p2p_blocks_per_sm; /* near-field grid in use (0 = one warp per work unit)           */
+    int64_t m2l_macs;       /* multiply-adds of one RHS's M2L, last build: sum over the pairs of
+                               (truncated size)^2, the size padded to a multiple of 16 (the
+                               tensor-core tiles): p_c^2 rounded up; = pairs x P^2 untruncated */
 } bem_stats;
 
 /* Phases reported by bem_profile_read, in this order. */

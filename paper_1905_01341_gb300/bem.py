@@ -81,6 +81,7 @@ class bem_stats(ctypes.Structure):
         ("n_launches", ctypes.c_int64),
         ("m2l_stages", ctypes.c_int32),
         ("p2p_blocks_per_sm", ctypes.c_int32),
+        ("m2l_macs", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:

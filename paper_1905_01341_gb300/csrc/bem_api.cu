@@ -342,6 +342,17 @@ void build_all(Context &c) {
         c.stats.leaves = c.tree.nb[c.tree.L];
         c.stats.m2l_stages = c.tuned_stages;
         c.stats.p2p_blocks_per_sm = c.tuned_p2p_blocks;
+        {
+            const int P16 = (c.ops.P + 15) / 16 * 16;
+            int64_t macs = 0;
+            for (int k = 0; k < kNumM2LClasses; ++k) {
+                const int64_t n = c.tree.m2l_class_off[k + 1] - c.tree.m2l_class_off[k];
+                const int64_t K = c.ops.margin >= 0 ? std::min(P16, (c.ops.cls_p[k] * c.ops.cls_p[k] + 15) / 16 * 16)
+                                                    : (int64_t)c.ops.P;
+                macs += n * K * K;
+            }
+            c.stats.m2l_macs = macs;
+        }
     } else {
         c.dir_hi.resize(3 * N);
         c.dir_lo.resize(3 * N);

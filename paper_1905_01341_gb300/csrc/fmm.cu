@@ -580,13 +580,13 @@ void xlat_smem_attr(K kern, size_t bytes) {
 
 // Y[t] += sum of Ypair[k] over the pairs k of target t, in ascending k (fixed order,
 // compensated in FP32). One thread per (target, coefficient).
-// With per-class truncation (pair_cls != nullptr) a pair's row holds only its class's first
-// cls_K coefficients; the rest were never written and count as zeros (skipping a zero leaves a
-// TwoSum accumulation unchanged, so the result is the same as summing the zeros).
+// With per-class truncation (byK != nullptr: byK[k] is the truncated size of the class of pair
+// by[k]) a pair's row holds only its class's first byK coefficients; the rest were never
+// written and count as zeros (skipping a zero leaves a TwoSum accumulation unchanged, so the
+// result is the same as summing the zeros).
 template <class T, int R>
 __global__ void k_reduce_pairs(int t0, const int32_t *__restrict__ off, const int32_t *__restrict__ by,
-                               const T *__restrict__ Ypair, int P, T *__restrict__ Y,
-                               const uint32_t *__restrict__ pair_cls, const int32_t *__restrict__ cls_K) {
+                               const T *__restrict__ Ypair, int P, T *__restrict__ Y, const int32_t *__restrict__ byK) {
     int t = t0 + blockIdx.x;
     int e = blockIdx.y * blockDim.x + threadIdx.x;
     if (e >= R * P) return;
@@ -595,7 +595,7 @@ __global__ void k_reduce_pairs(int t0, const int32_t *__restrict__ off, const in
     const int n = e % P;
     T s = 0, c = 0;
     for (int k = a; k < b; ++k) {
-        if (pair_cls && n >= cls_K[pair_cls[by[k]]]) continue;
+        if (byK && n >= byK[k]) continue;
         T v = Ypair[(size_t)by[k] * R * P + e];
         T tt = s + v;
         T bp = tt - s;
@@ -617,8 +617,7 @@ __device__ __forceinline__ void comp_add(float &s, float &c, float v) {
 template <int R>
 __global__ void __launch_bounds__(64) k_reduce_pairs4(int t0, const int32_t *__restrict__ off,
                                                       const int32_t *__restrict__ by, const float *__restrict__ Ypair,
-                                                      int P, float *__restrict__ Y, const uint32_t *__restrict__ pair_cls,
-                                                      const int32_t *__restrict__ cls_K) {
+                                                      int P, float *__restrict__ Y, const int32_t *__restrict__ byK) {
     const int t = t0 + blockIdx.x;
     const int a = off[t], b = off[t + 1];
     if (a == b) return;
@@ -632,14 +631,21 @@ __global__ void __launch_bounds__(64) k_reduce_pairs4(int t0, const int32_t *__r
             comp_add(s2, c2, v.z);
             comp_add(s3, c3, v.w);
         };
-        if (pair_cls) {
+        if (byK) {
             // truncated classes: the four coefficients (4e .. 4e + 3) % P lie on one side of the
-            // class's cls_K (a multiple of 16) together
+            // pair's class size byK[k] (a multiple of 16) together
             const int n = (4 * e) % P;
-            for (int k = a; k < b; ++k) {
-                const int pk = by[k];
-                if (n < cls_K[pair_cls[pk]]) add(Y4[(size_t)pk * rp4 + e]);
+            int k = a;
+            for (; k + 1 < b; k += 2) {
+                const int p0 = by[k], p1 = by[k + 1];
+                const int K0 = byK[k], K1 = byK[k + 1];
+                const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 v0 = n < K0 ? Y4[(size_t)p0 * rp4 + e] : z;
+                const float4 v1 = n < K1 ? Y4[(size_t)p1 * rp4 + e] : z;
+                if (n < K0) add(v0);
+                if (n < K1) add(v1);
             }
+            if (k < b && n < byK[k]) add(Y4[(size_t)by[k] * rp4 + e]);
         } else {
             int k = a;
             for (; k + 1 < b; k += 2) {
@@ -661,19 +667,26 @@ __global__ void __launch_bounds__(64) k_reduce_pairs4(int t0, const int32_t *__r
 }
 
 // Y[t] += sum over the pairs of t, for the targets t0 .. t0 + ntg - 1
+// byK[k] = cls_K[class of pair by[k]]: the truncated row length, in the target-major order
+__global__ void k_pair_K(int64_t n, const int32_t *__restrict__ by, const uint32_t *__restrict__ pair_cls,
+                         const int32_t *__restrict__ cls_K, int32_t *__restrict__ byK) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < n) byK[k] = cls_K[pair_cls[by[k]]];
+}
+
 template <class T, int R>
 void launch_reduce_pairs(int t0, int ntg, const int32_t *off, const int32_t *by, const T *Ypair, int P, T *Y,
-                         cudaStream_t st, const uint32_t *pair_cls = nullptr, const int32_t *cls_K = nullptr) {
+                         cudaStream_t st, const int32_t *byK = nullptr) {
     if (ntg <= 0) return;
     if constexpr (sizeof(T) == 4) {
         if (P % 4 == 0) {
-            k_reduce_pairs4<R><<<ntg, 64, 0, st>>>(t0, off, by, Ypair, P, Y, pair_cls, cls_K);
+            k_reduce_pairs4<R><<<ntg, 64, 0, st>>>(t0, off, by, Ypair, P, Y, byK);
             BEM_LAUNCH_CHECK();
             return;
         }
     }
     dim3 rg((unsigned)ntg, div_up(R * P, 128));
-    k_reduce_pairs<T, R><<<rg, 128, 0, st>>>(t0, off, by, Ypair, P, Y, pair_cls, cls_K);
+    k_reduce_pairs<T, R><<<rg, 128, 0, st>>>(t0, off, by, Ypair, P, Y, byK);
     BEM_LAUNCH_CHECK();
 }
 
@@ -972,8 +985,14 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
         }
         PhaseScope ps(c, PH_M2L_REDUCE, fs);
         const bool trunc = opr.margin >= 0;
+        if (trunc) {
+            c.m2l_byK.resize(std::max<int64_t>(t.n_m2l, 1));
+            k_pair_K<<<div_up(t.n_m2l, 256), 256, 0, fs>>>(t.n_m2l, t.m2l_by_tgt.p, t.m2l_cls.p, opr.cls_K.p,
+                                                          c.m2l_byK.p);
+            BEM_LAUNCH_CHECK();
+        }
         launch_reduce_pairs<T, R>(t.base[2], t.nbox - t.base[2], t.m2l_tgt_off.p, t.m2l_by_tgt.p, ypair, P, lc, fs,
-                                  trunc ? t.m2l_cls.p : nullptr, trunc ? opr.cls_K.p : nullptr);
+                                  trunc ? c.m2l_byK.p : nullptr);
     }
     // L2L downward, levels 3 -> L: every child has exactly one parent, so it adds in place
     for (int l = 3; l <= L; ++l) {

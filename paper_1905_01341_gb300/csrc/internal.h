@@ -299,6 +299,7 @@ struct Context {
     DevBuf<float> q32, w32;
     DevBuf<double> mp64, lc64;     // expansions [nbox][R][P]
     DevBuf<float> mp32, lc32;
+    DevBuf<int32_t> m2l_byK;       // truncated row length of each M2L pair, target-major order
     DevBuf<double> ypair64;        // per-pair translation results [pair][R][P]
     DevBuf<float> ypair32;
     DevBuf<double> far64;          // far-field potential [R][N] (sorted)
