@@ -89,7 +89,9 @@ def parse():
     ap.add_argument("--m2l-tc", type=int, default=3,
                     help="M2L on the tensor cores: 1 single-RHS products, 2 also the 4-RHS diagonal product, "
                          "3 (default) as 2 for bubbles of at most 2562 vertices, 0 none")
-    ap.add_argument("--overlap", type=int, default=1, help="1 = near field on its own stream, overlapping the far field")
+    ap.add_argument("--overlap", type=int, default=-1,
+                    help="near field on its own stream: 1 from the far field's start, 2 from the M2L's, 0 off, "
+                         "-1 autotuned")
     ap.add_argument("--guess", type=int, default=2,
                     help="AB6 GMRES start: 0 previous q (the paper), 1/2/3 extrapolation in t of that degree")
     ap.add_argument("--pa", type=float, default=0.5, help="acoustic amplitude Pa/p0")

@@ -90,10 +90,14 @@ typedef struct {
                                3.21M-unknown cluster at p_fmm = 14 the off-diagonal part of a
                                product is within 6e-7 of the direct sum, L_ii within 4e-5).
                                Default -1.                                                     */
-    int32_t overlap;        /* 1: within a product, the near field runs on its own stream,
-                               concurrently with the far field; 0: one stream, phase after
-                               phase (the per-kernel timings of a profile then do not
-                               overlap). Same results either way. Default 1.                  */
+    int32_t overlap;        /* within a product, the near field runs on its own stream,
+                               concurrently with the far field: 1 = from the start of the far
+                               field, 2 = from the start of the M2L (the P2M runs alone, then
+                               the near field fills the SMs around the tensor-core M2L);
+                               0 = one stream, phase after phase (the per-kernel timings of a
+                               profile then do not overlap); -1 = automatic (the tile
+                               autotuner's choice between 1 and 2 when leaf_target = 0, else
+                               2). Same results in every mode. Default -1.                     */
     int32_t m2l_tensor_cores; /* Mixed precision only. 1: single-RHS products (every GMRES
                                product) run M2L on the tensor cores (three-piece BF16 split,
                                FP32 accumulation) when p^2 is a multiple of 4 and <= 256;
@@ -159,6 +163,8 @@ typedef struct {
     double last_build_ms;   /* device time of the last fmm_build                               */
     int64_t n_launches;     /* kernels launched by the library in this process (all contexts)   */
     int32_t m2l_stages;     /* tensor-core M2L pipeline stages in use (0 = deepest that fits)   */
+    int32_t overlap;        /* near-field / far-field overlap mode in use (bem_params.overlap)  */
+    int32_t reserved;
     int32_t p2p_blocks_per_sm; /* near-field grid in use (0 = one warp per work unit)           */
     int64_t m2l_macs;       /* multiply-adds of one RHS's M2L, last build: sum over the pairs of
                                (truncated size)^2, the size padded to a multiple of 16 (the

@@ -80,6 +80,8 @@ class bem_stats(ctypes.Structure):
         ("last_build_ms", ctypes.c_double),
         ("n_launches", ctypes.c_int64),
         ("m2l_stages", ctypes.c_int32),
+        ("overlap", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
         ("p2p_blocks_per_sm", ctypes.c_int32),
         ("m2l_macs", ctypes.c_int64),
     ]

@@ -16,6 +16,7 @@ Context::~Context() {
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
     if (ev_far) cudaEventDestroy(ev_far);
+    if (ev_m2l) cudaEventDestroy(ev_m2l);
     if (side) cudaStreamDestroy(side);
     if (hi) cudaStreamDestroy(hi);
     for (auto *p : up_chunks) delete p;
@@ -164,7 +165,7 @@ void check_params(const bem_params &p) {
         fail(BEM_ERR_ARG, "bad diag_precision");
     if (p.diag_p_fmm != -1 && (p.diag_p_fmm < 2 || p.diag_p_fmm > kMaxPfmm))
         fail(BEM_ERR_ARG, "diag_p_fmm must be -1 or in 2..20");
-    if (p.overlap != 0 && p.overlap != 1) fail(BEM_ERR_ARG, "overlap must be 0 or 1");
+    if (p.overlap < -1 || p.overlap > 2) fail(BEM_ERR_ARG, "overlap must be -1, 0, 1 or 2");
     if (p.mvp != BEM_MVP_FMM && p.mvp != BEM_MVP_DIRECT) fail(BEM_ERR_ARG, "bad mvp kind");
     if (p.m2l_tensor_cores < 0 || p.m2l_tensor_cores > 3) fail(BEM_ERR_ARG, "m2l_tensor_cores must be 0..3");
     if (p.gmres_maxit < 1 || p.gmres_restart < 0 || p.gmres_restart > 127) fail(BEM_ERR_ARG, "bad GMRES limits");
@@ -234,6 +235,7 @@ void tune_tiles(Context &c) {
     // 1. depth, with the default tiles
     c.tuned_stages = c.prm.m2l_stages;
     c.tuned_p2p_blocks = c.prm.p2p_blocks_per_sm > 0 ? c.prm.p2p_blocks_per_sm : 0;
+    c.tuned_overlap = c.prm.overlap < 0 ? 1 : c.prm.overlap;
     const int saved_target = c.prm.leaf_target;
     c.prm.leaf_target = 64;
     c.level_override = 0;
@@ -259,27 +261,33 @@ void tune_tiles(Context &c) {
     if (c.prm.m2l_stages == 0 && c.prm.precision == BEM_PREC_MIXED && c.prm.m2l_tensor_cores) stages = {5, 4, 3};
     std::vector<int> blocks = {c.tuned_p2p_blocks};
     if (c.prm.p2p_blocks_per_sm < 0 && c.prm.overlap) blocks = {0, 2, 4};
-    if (stages.size() > 1 || blocks.size() > 1) {
+    std::vector<int> ovls = {c.tuned_overlap};
+    if (c.prm.overlap < 0) ovls = {1, 2};
+    if (stages.size() > 1 || blocks.size() > 1 || ovls.size() > 1) {
         build_tree(c);
         c.m2l_chunks_h.clear();
         c.tc_chunks_ok[0] = c.tc_chunks_ok[1] = false;
         float tbest = 0.f;
-        int bs = stages[0], bb = blocks[0];
+        int bs = stages[0], bb = blocks[0], bo = ovls[0];
         bool first = true;
-        for (int st : stages)
-            for (int bk : blocks) {
-                c.tuned_stages = st;
-                c.tuned_p2p_blocks = bk;
-                const float ms = time_product(2);
-                if (first || ms < tbest) {
-                    tbest = ms;
-                    bs = st;
-                    bb = bk;
-                    first = false;
+        for (int ov : ovls)
+            for (int st : stages)
+                for (int bk : blocks) {
+                    c.tuned_overlap = ov;
+                    c.tuned_stages = st;
+                    c.tuned_p2p_blocks = bk;
+                    const float ms = time_product(3);
+                    if (first || ms < tbest) {
+                        tbest = ms;
+                        bs = st;
+                        bb = bk;
+                        bo = ov;
+                        first = false;
+                    }
                 }
-            }
         c.tuned_stages = bs;
         c.tuned_p2p_blocks = bb;
+        c.tuned_overlap = bo;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -341,6 +349,7 @@ void build_all(Context &c) {
         c.stats.levels = c.tree.L;
         c.stats.leaves = c.tree.nb[c.tree.L];
         c.stats.m2l_stages = c.tuned_stages;
+        c.stats.overlap = c.tuned_overlap;
         c.stats.p2p_blocks_per_sm = c.tuned_p2p_blocks;
         {
             const int P16 = (c.ops.P + 15) / 16 * 16;
@@ -462,7 +471,7 @@ int bem_params_default(bem_params *p) {
     p->mvp = BEM_MVP_FMM;
     p->diag_precision = -1;
     p->diag_p_fmm = -1;
-    p->overlap = 1;
+    p->overlap = -1;
     p->m2l_tensor_cores = 3;
     p->gmres_precond = 0;
     p->gmres_maxit = 100;
@@ -490,6 +499,7 @@ int bem_create(void **ctx_out, const bem_params *p, void *stream) {
         BEM_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
         c->tuned_stages = prm.m2l_stages;
         c->tuned_p2p_blocks = prm.p2p_blocks_per_sm < 0 ? 0 : prm.p2p_blocks_per_sm;
+        c->tuned_overlap = prm.overlap < 0 ? 2 : prm.overlap;
         *ctx_out = c;
         return BEM_OK;
     } catch (const Error &e) {

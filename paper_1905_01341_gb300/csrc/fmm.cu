@@ -857,21 +857,33 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
         BEM_CUDA(cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming));
         BEM_CUDA(cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming));
         BEM_CUDA(cudaEventCreateWithFlags(&c.ev_far, cudaEventDisableTiming));
+        BEM_CUDA(cudaEventCreateWithFlags(&c.ev_m2l, cudaEventDisableTiming));
     }
-    const bool ovl = c.prm.overlap != 0;
+    // overlap mode (c.tuned_overlap): 0 = one stream; 1 = the near field starts with the far
+    // field (right after the strengths); 2 = the near field starts when the M2L does: the
+    // ALU-bound P2M runs alone, and the near field fills the SMs around the tensor-core M2L's
+    // blocks (queued first, on the high-priority stream) and the rest of the far field
+    const int omode = c.tuned_overlap;
+    const bool ovl = omode != 0;
     cudaStream_t ns = ovl ? c.side : st;  // near-field stream
     BEM_CUDA(cudaEventRecord(c.ev_fork, st));
-    if (ovl) BEM_CUDA(cudaStreamWaitEvent(ns, c.ev_fork, 0));
-    {
-        PhaseScope ps(c, PH_P2P, ns);
-        bool hq = false, hw = false;
-        for (int r = 0; r < R; ++r) {
-            hq = hq || a.f[r] != 0.0;
-            hw = hw || a.g[r] != 0.0;
+    bool near_done = false;
+    auto launch_near = [&](cudaEvent_t after) {
+        if (near_done) return;
+        near_done = true;
+        if (ovl) BEM_CUDA(cudaStreamWaitEvent(ns, after, 0));
+        {
+            PhaseScope ps(c, PH_P2P, ns);
+            bool hq = false, hw = false;
+            for (int r = 0; r < R; ++r) {
+                hq = hq || a.f[r] != 0.0;
+                hw = hw || a.g[r] != 0.0;
+            }
+            launch_p2p_list<T, R>(c, q, w, c.near_out.p, hq, hw, ns);
         }
-        launch_p2p_list<T, R>(c, q, w, c.near_out.p, hq, hw, ns);
-    }
-    BEM_CUDA(cudaEventRecord(c.ev_join, ns));
+        BEM_CUDA(cudaEventRecord(c.ev_join, ns));
+    };
+    if (omode != 2) launch_near(c.ev_fork);
     // the far field runs on a high-priority stream, so its blocks (the tensor-core M2L's in
     // particular) are placed as soon as an SM has room and the near field fills the rest
     cudaStream_t fs = ovl ? c.hi : st;
@@ -983,6 +995,10 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
                                                                              opr.margin >= 0 ? opr.cls_K.p : nullptr);
             BEM_LAUNCH_CHECK();
         }
+        if (omode == 2) {  // the M2L is queued: the near field may start (after the multipoles)
+            BEM_CUDA(cudaEventRecord(c.ev_m2l, fs));
+            launch_near(c.ev_m2l);
+        }
         PhaseScope ps(c, PH_M2L_REDUCE, fs);
         const bool trunc = opr.margin >= 0;
         if (trunc) {
@@ -1012,6 +1028,7 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
                                                     lc + (size_t)t.base[L] * R * P, far);
         BEM_LAUNCH_CHECK();
     }
+    launch_near(c.ev_fork);  // (no M2L pairs: the near field has not started yet)
     BEM_CUDA(cudaEventRecord(c.ev_far, fs));
     // join the near field, add the far field, scale by 1/h and return to the caller's order
     if (ovl) {

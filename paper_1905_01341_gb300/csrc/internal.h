@@ -260,7 +260,7 @@ struct Context {
     // streams of the FMM product: after the strengths, the near field and the far field run
     // concurrently on two internal streams and join back into `stream` (created on first use)
     cudaStream_t side = nullptr, hi = nullptr;  // near field (lowest priority), far field (highest)
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_far = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_far = nullptr, ev_m2l = nullptr;
     int device = 0;
     std::string err;
 
@@ -281,7 +281,7 @@ struct Context {
     // tile choices of the products: tensor-core M2L pipeline stages (0 = deepest that fits) and
     // near-field blocks per SM (0 = one warp per unit); set from the parameters, or by the
     // autotuner when those are automatic
-    int tuned_stages = 0, tuned_p2p_blocks = 0;
+    int tuned_stages = 0, tuned_p2p_blocks = 0, tuned_overlap = 1;
     int num_sms = 1;
     DevBuf<int32_t> vcid;          // [N] cluster of every vertex (when C > 1)
 

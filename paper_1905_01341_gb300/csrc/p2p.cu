@@ -384,7 +384,7 @@ static void launch_units(Context &c, const T *q, const T *w, double *out_sorted,
     // memory: the tensor-core M2L needs it, and an SM whose resident near-field blocks had it
     // configured for more L1 would first have to drain them. (A per-device attribute, set on
     // every launch; about a microsecond.)
-    if (c.prm.overlap)
+    if (c.tuned_overlap)
         BEM_CUDA(cudaFuncSetAttribute(k_p2p_units<T, R, HQ, HW>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       (int)cudaSharedmemCarveoutMaxShared));
     k_p2p_units<T, R, HQ, HW><<<(unsigned)blocks, P2P_WARPS * 32, 0, st>>>(

@@ -988,7 +988,7 @@ void step_get_state(Context &c, double *xyz, double *phi, double *q, double *t) 
 // and the step-start solutions of the extrapolated guess [kQh][N].
 struct CkptHeader {
     char magic[8];
-    int32_t version, tuned_level, tuned_stages, tuned_p2p_blocks;
+    int32_t version, tuned_level, tuned_stages, tuned_p2p_blocks, tuned_overlap, reserved;
     int64_t N, T, M;
     bem_step_params sp;
     double t, dt;
@@ -1014,6 +1014,7 @@ void step_save(Context &c, void *buf, int64_t cap) {
     h.tuned_level = c.tuned_level;
     h.tuned_stages = c.tuned_stages;
     h.tuned_p2p_blocks = c.tuned_p2p_blocks;
+    h.tuned_overlap = c.tuned_overlap;
     h.N = N;
     h.T = c.T;
     h.M = c.M;
@@ -1093,6 +1094,7 @@ void step_load(Context &c, const void *buf, int64_t size) {
         c.tuned_level = h.tuned_level;
         c.tuned_stages = h.tuned_stages;
         c.tuned_p2p_blocks = h.tuned_p2p_blocks;
+        if (c.prm.overlap < 0) c.tuned_overlap = h.tuned_overlap;
     }
     BEM_CUDA(cudaStreamSynchronize(c.stream));
 }

@@ -94,7 +94,7 @@ def test_struct_defaults():
     from paper_1905_01341_gb300 import bem
 
     assert bem.bem_params_default().gmres_precond == 0
-    assert bem.bem_params_default().overlap == 1 and bem.bem_params_default().diag_p_fmm == -1
+    assert bem.bem_params_default().overlap == -1 and bem.bem_params_default().diag_p_fmm == -1
     assert bem.bem_params_default().m2l_stages == 0 and bem.bem_params_default().p2p_blocks_per_sm == -1
     sp = bem.bem_step_params_default()
     assert sp.pf == 6 and sp.courant == 0.1 and sp.kappa == 1.4 and sp.guess == 2
