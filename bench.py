@@ -56,10 +56,10 @@ PEAKS = _load_peaks()
 M2L_TC_PRODUCTS = 6
 # DRAM traffic per unit from the ncu captures of the 300-bubble cluster (profiles/), scaled to a
 # full launch by the units it processes: the near field reads each point's data about once
-# (3.65 MB for 192,600 points), the M2L reads gathered multipoles and writes one product row per
-# translation (86.6 MB + 134.2 MB for 241,298 translations).
-P2P_DRAM_BYTES_PER_POINT = 3.648e6 / 192600
-M2L_DRAM_BYTES_PER_TRANSLATION = (86.56e6 + 134.19e6) / 241298
+# (3.69 MB for 192,600 points), the M2L reads gathered multipoles and writes one product row per
+# translation, truncated to its class's order (39.5 MB + 80.4 MB for 241,298 translations).
+P2P_DRAM_BYTES_PER_POINT = 3.687e6 / 192600
+M2L_DRAM_BYTES_PER_TRANSLATION = (39.49e6 + 80.41e6) / 241298
 
 
 def parse():
