@@ -97,7 +97,7 @@ typedef struct {
                                0 = one stream, phase after phase (the per-kernel timings of a
                                profile then do not overlap); -1 = automatic (the tile
                                autotuner's choice between 1 and 2 when leaf_target = 0, else
-                               2). Same results in every mode. Default -1.                     */
+                               1). Same results in every mode. Default -1.                     */
     int32_t m2l_tensor_cores; /* Mixed precision only. 1: single-RHS products (every GMRES
                                product) run M2L on the tensor cores (three-piece BF16 split,
                                FP32 accumulation) when p^2 is a multiple of 4 and <= 256;
@@ -328,6 +328,13 @@ int bem_step(void *ctx, bem_step_stats *st);
 
 /* Current state: xyz[3N] (SoA), phi[N], the last q[N] and t. Any pointer may be NULL. */
 int bem_step_get_state(void *ctx, double *xyz, double *phi, double *q, double *t);
+
+/* Replace the current state: xyz[3N] (SoA), phi[N] and the q[N] the next solve starts from (or
+ * extrapolates with); any pointer may be NULL (that part is kept). The time, the step size and
+ * the history of right-hand sides (Section 3.5) are kept, so the next bem_step continues the
+ * integration from the given state: a caller that holds the state in its own (host) memory
+ * passes it back each step. */
+int bem_step_set_state(void *ctx, const double *xyz, const double *phi, const double *q);
 
 /* Checkpoint and resume of a time integration (the paper has none; Sections 3.5-3.6 define
  * what a step depends on). A checkpoint holds what evolves: r and phi, the last q, t, dt, the

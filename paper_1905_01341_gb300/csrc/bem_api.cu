@@ -499,7 +499,7 @@ int bem_create(void **ctx_out, const bem_params *p, void *stream) {
         BEM_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
         c->tuned_stages = prm.m2l_stages;
         c->tuned_p2p_blocks = prm.p2p_blocks_per_sm < 0 ? 0 : prm.p2p_blocks_per_sm;
-        c->tuned_overlap = prm.overlap < 0 ? 2 : prm.overlap;
+        c->tuned_overlap = prm.overlap < 0 ? 1 : prm.overlap;
         *ctx_out = c;
         return BEM_OK;
     } catch (const Error &e) {
@@ -757,6 +757,10 @@ int bem_step(void *ctx, bem_step_stats *st) {
 
 int bem_step_get_state(void *ctx, double *xyz, double *phi, double *q, double *t) {
     return guarded(ctx, [&](Context &c) { step_get_state(c, xyz, phi, q, t); });
+}
+
+int bem_step_set_state(void *ctx, const double *xyz, const double *phi, const double *q) {
+    return guarded(ctx, [&](Context &c) { step_set_state(c, xyz, phi, q); });
 }
 
 int bem_step_save(void *ctx, void *buf, int64_t cap, int64_t *size) {

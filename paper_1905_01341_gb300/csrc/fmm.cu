@@ -732,51 +732,93 @@ __global__ void __launch_bounds__(L2P_THREADS) k_l2p(int p, const int32_t *__res
     }
     __syncthreads();
     int s0 = bstart[b], cnt = bcount[b];
-    for (int c0 = threadIdx.x; c0 < cnt; c0 += L2P_THREADS) {
-        int64_t i = s0 + c0;
-        T x = loc[i], y = loc[N + i], z = loc[2 * N + i];
-        T r2 = x * x + y * y + z * z;
-        CompSum<T> acc[R];
-        T mr = 1, mi = 0;
+    // each lane evaluates two points at once (c0 and c0 + 32): two independent recurrence chains,
+    // and every coefficient read from shared memory serves both
+    for (int c0 = threadIdx.x; c0 < cnt; c0 += 2 * L2P_THREADS) {
+        const bool two = c0 + L2P_THREADS < cnt;
+        const int64_t i0 = s0 + c0, i1 = s0 + (two ? c0 + L2P_THREADS : c0);
+        T x[2] = {loc[i0], loc[i1]}, y[2] = {loc[N + i0], loc[N + i1]}, z[2] = {loc[2 * N + i0], loc[2 * N + i1]};
+        T r2[2];
+        CompSum<T> acc[2][R];
+        T mr[2], mi[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            r2[u] = x[u] * x[u] + y[u] * y[u] + z[u] * z[u];
+            mr[u] = 1;
+            mi[u] = 0;
+        }
         for (int m = 0; m < p; ++m) {
             if (m > 0) {
                 const T f = tk[m];
-                T nr = f * (x * mr - y * mi), ni = f * (x * mi + y * mr);
-                mr = nr;
-                mi = ni;
-            }
-            T col[R];
 #pragma unroll
-            for (int r = 0; r < R; ++r) col[r] = (T)0;
-            // L_n^m against R_n^m = cr + i ci
-            auto term = [&](int n, T cr, T ci) {
+                for (int u = 0; u < 2; ++u) {
+                    const T nr = f * (x[u] * mr[u] - y[u] * mi[u]), ni = f * (x[u] * mi[u] + y[u] * mr[u]);
+                    mr[u] = nr;
+                    mi[u] = ni;
+                }
+            }
+            T col[2][R];
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int r = 0; r < R; ++r) col[u][r] = (T)0;
+            // L_n^m against R_n^m = cr + i ci, for both points
+            auto term = [&](int n, const T *cr, const T *ci) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const T *Lr = Ls + r * P + n * n;
-                    col[r] += (m == 0) ? Lr[0] * cr : (T)2 * (Lr[2 * m - 1] * cr - Lr[2 * m] * ci);
+                    if (m == 0) {
+                        const T l0 = Lr[0];
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) col[u][r] += l0 * cr[u];
+                    } else {
+                        const T lre = Lr[2 * m - 1], lim = Lr[2 * m];
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) col[u][r] += (T)2 * (lre * cr[u] - lim * ci[u]);
+                    }
                 }
             };
             term(m, mr, mi);
             if (m + 1 < p) {
-                T p2r = mr, p2i = mi, p1r = z * mr, p1i = z * mi;
+                T p2r[2], p2i[2], p1r[2], p1i[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    p2r[u] = mr[u];
+                    p2i[u] = mi[u];
+                    p1r[u] = z[u] * mr[u];
+                    p1i[u] = z[u] * mi[u];
+                }
                 term(m + 1, p1r, p1i);
                 for (int n = m + 2; n < p; ++n) {
                     const T d = tnm[tri_idx(n, m)];
-                    const T c2z = (T)(2 * n - 1) * z;
-                    const T cr = (c2z * p1r - r2 * p2r) * d;
-                    const T ci = (c2z * p1i - r2 * p2i) * d;
+                    const T c2 = (T)(2 * n - 1);
+                    T cr[2], ci[2];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const T c2z = c2 * z[u];
+                        cr[u] = (c2z * p1r[u] - r2[u] * p2r[u]) * d;
+                        ci[u] = (c2z * p1i[u] - r2[u] * p2i[u]) * d;
+                    }
                     term(n, cr, ci);
-                    p2r = p1r;
-                    p2i = p1i;
-                    p1r = cr;
-                    p1i = ci;
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        p2r[u] = p1r[u];
+                        p2i[u] = p1i[u];
+                        p1r[u] = cr[u];
+                        p1i[u] = ci[u];
+                    }
                 }
             }
 #pragma unroll
-            for (int r = 0; r < R; ++r) acc[r].add(col[r]);
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int r = 0; r < R; ++r) acc[u][r].add(col[u][r]);
         }
 #pragma unroll
-        for (int r = 0; r < R; ++r) far[r * N + i] = acc[r].get();
+        for (int r = 0; r < R; ++r) {
+            far[r * N + i0] = acc[0][r].get();
+            if (two) far[r * N + i1] = acc[1][r].get();
+        }
     }
 }
 

@@ -442,6 +442,7 @@ bool is_device_ptr(const Context &c, const void *p);
 void step_init(Context &c, const double *phi0_dev, const double *q0_dev, const bem_step_params &sp);
 void step_advance(Context &c, bem_step_stats &st);
 void step_get_state(Context &c, double *xyz, double *phi, double *q, double *t);
+void step_set_state(Context &c, const double *xyz, const double *phi, const double *q);
 int64_t step_checkpoint_size(const Context &c);
 void step_save(Context &c, void *buf, int64_t cap);
 void step_load(Context &c, const void *buf, int64_t size);

@@ -1099,6 +1099,20 @@ void step_load(Context &c, const void *buf, int64_t size) {
     BEM_CUDA(cudaStreamSynchronize(c.stream));
 }
 
+void step_set_state(Context &c, const double *xyz, const double *phi, const double *q) {
+    StepState &s = state_of(c);
+    if (!s.ready) fail(BEM_ERR_NOT_BUILT, "bem_step_init has not been called");
+    const int64_t N = c.N;
+    auto cp = [&](double *dst, const double *src, int64_t n) {
+        if (!src) return;
+        BEM_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDefault, c.stream));
+    };
+    cp(s.y.p, xyz, 3 * N);
+    cp(s.y.p + 3 * N, phi, N);
+    cp(s.q.p, q, N);
+    BEM_CUDA(cudaStreamSynchronize(c.stream));
+}
+
 void step_free(StepState *s) { delete s; }
 
 const double *step_initial_xyz(Context &c) {

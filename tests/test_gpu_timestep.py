@@ -276,3 +276,26 @@ def test_toroidal_bubble_steps_match_oracle():
         assert np.linalg.norm(disp - disp_ref) < 1e-8 * np.linalg.norm(disp_ref) + 1e-13
         assert np.linalg.norm(ph - st.phi) < 1e-8 * np.linalg.norm(st.phi)
     ctx.close()
+
+
+def test_state_round_trip_through_host_memory_leaves_the_run_unchanged():
+    """bem_step_set_state with the state just read by bem_step_get_state (the state held in host
+    memory between steps) continues the integration exactly as without the round trip."""
+    bem = _bem()
+    mesh, phi = synth.workload_cluster(bubbles=4, level=3, seed=33)
+    prm = dict(mvp=bem.BEM_MVP_FMM, precision=bem.BEM_PREC_FP64, p_fmm=10, fixed_level=3, gmres_tol=1e-9,
+               gmres_precond=1)
+    out = []
+    for roundtrip in (False, True):
+        ctx = bem.BemContext(**prm)
+        ctx.upload_mesh(mesh)
+        bem.bem_step_init(ctx.ctx, phi, bem.bem_step_params_default(pf=6, pa=0.5))
+        for k in range(8):
+            if roundtrip and k >= 5:
+                xyz, ph, q, _ = _state(ctx, mesh.n)
+                bem.bem_step_set_state(ctx.ctx, xyz, ph, q)
+            bem.bem_step(ctx.ctx)
+        out.append(_state(ctx, mesh.n))
+        ctx.close()
+    for a, b in zip(out[0][:3], out[1][:3]):
+        assert np.array_equal(a, b)
