@@ -123,11 +123,10 @@ typedef struct {
     int32_t gmres_maxit;    /* maximum GMRES iterations. Default 100.                          */
     int32_t gmres_restart;  /* restart length; 0 = no restart (= maxit). Default 0.            */
     double gmres_tol;       /* stop when |b - L q| / |b| <= tol (Section 3.8). Default 1e-6.  */
-    int32_t m2l_stages;     /* shared-memory pipeline stages of the tensor-core M2L: 3, 4 or 5
-                               (5 only where it fits, p <= 14); 0 = automatic (the tile
-                               autotuner's choice when leaf_target = 0, else the deepest that
-                               fits). Fewer stages leave shared memory on each SM for the near
-                               field running concurrently. Default 0.                         */
+    int32_t m2l_stages;     /* shared-memory pipeline stages of the tensor-core M2L: 2 or 3;
+                               0 = automatic (the tile autotuner's choice when leaf_target = 0,
+                               else 3). Fewer stages leave shared memory on each SM for the
+                               near field running concurrently. Default 0.                    */
     int32_t p2p_blocks_per_sm; /* near-field grid: 0 = one warp per work unit (all units in one
                                grid); k > 0 = a persistent grid of k blocks per SM looping over
                                the units, which leaves room on every SM for the far-field
@@ -162,7 +161,7 @@ typedef struct {
     double last_relres;     /* true relative residual of the last solve                        */
     double last_build_ms;   /* device time of the last fmm_build                               */
     int64_t n_launches;     /* kernels launched by the library in this process (all contexts)   */
-    int32_t m2l_stages;     /* tensor-core M2L pipeline stages in use (0 = deepest that fits)   */
+    int32_t m2l_stages;     /* tensor-core M2L pipeline stages in use (0 = the default, 3)      */
     int32_t overlap;        /* near-field / far-field overlap mode in use (bem_params.overlap)  */
     int32_t reserved;
     int32_t p2p_blocks_per_sm; /* near-field grid in use (0 = one warp per work unit)           */

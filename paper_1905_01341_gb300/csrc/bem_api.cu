@@ -171,7 +171,7 @@ void check_params(const bem_params &p) {
     if (p.gmres_maxit < 1 || p.gmres_restart < 0 || p.gmres_restart > 127) fail(BEM_ERR_ARG, "bad GMRES limits");
     if (p.gmres_precond < 0 || p.gmres_precond > 2) fail(BEM_ERR_ARG, "gmres_precond must be 0, 1 or 2");
     if (!(p.gmres_tol > 0.0)) fail(BEM_ERR_ARG, "gmres_tol must be > 0");
-    if (p.m2l_stages != 0 && (p.m2l_stages < 3 || p.m2l_stages > 5)) fail(BEM_ERR_ARG, "m2l_stages must be 0 or 3..5");
+    if (p.m2l_stages != 0 && (p.m2l_stages < 2 || p.m2l_stages > 3)) fail(BEM_ERR_ARG, "m2l_stages must be 0, 2 or 3");
     if (p.p2p_blocks_per_sm < -1 || p.p2p_blocks_per_sm > 16) fail(BEM_ERR_ARG, "p2p_blocks_per_sm must be in -1..16");
     if (p.m2l_order_margin < -1 || p.m2l_order_margin > 20) fail(BEM_ERR_ARG, "m2l_order_margin must be in -1..20");
 }
@@ -258,7 +258,7 @@ void tune_tiles(Context &c) {
     c.level_override = best;
     // 2. tiles at that depth
     std::vector<int> stages = {c.prm.m2l_stages};
-    if (c.prm.m2l_stages == 0 && c.prm.precision == BEM_PREC_MIXED && c.prm.m2l_tensor_cores) stages = {5, 4, 3};
+    if (c.prm.m2l_stages == 0 && c.prm.precision == BEM_PREC_MIXED && c.prm.m2l_tensor_cores) stages = {3, 2};
     std::vector<int> blocks = {c.tuned_p2p_blocks};
     if (c.prm.p2p_blocks_per_sm < 0 && c.prm.overlap) blocks = {0, 2, 4};
     std::vector<int> ovls = {c.tuned_overlap};

@@ -1016,8 +1016,17 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
             PhaseScope ps(c, PH_M2L, fs);
             const int ti = R == 1 ? 0 : 1;
             if (!c.tc_chunks_ok[ti]) {
+                // chunk sizes per class: four tiles of rows for small truncated classes, else two
                 std::vector<XChunk> tc;
-                make_chunks(t.m2l_class_off, 0, m2l_tc_pairs_per_chunk(R), tc);
+                const int P16 = (P + 15) / 16 * 16;
+                for (int cc = 0; cc < kNumM2LClasses; ++cc) {
+                    const int Kc = opr.margin >= 0 ? opr.cls_Kh[cc] : P16;
+                    const std::vector<int64_t> one = {t.m2l_class_off[cc], t.m2l_class_off[cc + 1]};
+                    std::vector<XChunk> part;
+                    make_chunks(one, 0, m2l_tc_pairs_per_chunk(R, Kc), part);
+                    for (XChunk &x : part) x.cls = cc;
+                    tc.insert(tc.end(), part.begin(), part.end());
+                }
                 c.tc_chunks[ti].resize(std::max<size_t>(tc.size(), 1));
                 if (!tc.empty())
                     BEM_CUDA(cudaMemcpyAsync(c.tc_chunks[ti].p, tc.data(), tc.size() * sizeof(XChunk),
@@ -1115,6 +1124,7 @@ void build_operators(Context &c, Operators &o, int p) {
         for (int k = 0; k < kNumM2LClasses; ++k)
             K[k] = std::min(Pfull16, (o.cls_p[k] * o.cls_p[k] + 15) / 16 * 16);
         o.cls_K.resize(kNumM2LClasses);
+        o.cls_Kh.assign(K.begin(), K.end());
         BEM_CUDA(cudaMemcpyAsync(o.cls_K.p, K.data(), K.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream));
         BEM_CUDA(cudaStreamSynchronize(c.stream));
         if (o.ready && o.p == p) return;  // only the truncation changed

@@ -161,7 +161,7 @@ struct Operators {
     // the 16-wide steps of the products: cls_K[c] = 16 * ceil(p_c^2 / 16), capped at the full
     // padded size (margin < 0: every class at p)
     int margin = -1;
-    std::vector<int> cls_p;
+    std::vector<int> cls_p, cls_Kh;  // per class: order p_c, truncated size K_c (host copies)
     DevBuf<int32_t> cls_K;
 };
 
@@ -406,7 +406,7 @@ void build_tc_tables(Context &c, Operators &o);
 template <int R>
 void launch_m2l_tc(Context &c, const Operators &o, const XChunk *chunks, int64_t nchunks, const float *X, int64_t xrows, float *Ypair,
                    int *err, cudaStream_t st);
-int m2l_tc_pairs_per_chunk(int R);
+int m2l_tc_pairs_per_chunk(int R, int Kc);
 
 // gmres.cu, gmres_batched.cu (clusters: one GMRES per cluster, in lockstep)
 void gmres_solve(Context &c, const double *b, double *x, int *iters, double *relres);

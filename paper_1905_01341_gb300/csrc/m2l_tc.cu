@@ -1,12 +1,13 @@
 // M2L translations on the 5th-generation tensor cores (tcgen05, TMEM accumulators).
 //
-// For one offset class c and a chunk of up to 256/R (source, target) pairs, the product
+// For one offset class c and a chunk of (source, target) pairs, the product
 //   Y[pair, rhs][n] = sum_k T_c[n][k] X[src, rhs][k]
-// is two MMA tiles D_t = A_t B^T (t = 0, 1) with M = 128 rows (pair, rhs) each, N = P rounded
-// up to 16 output coefficients and K = P input coefficients: A_t = gathered multipole rows,
-// B = T_c (row n of T_c is K-contiguous, i.e. K-major). The two tiles share every staged
-// block of T_c, which halves its traffic; this beat one tile per block at two blocks per SM
-// (3.8 vs 5.0 ms per product at 3.2M unknowns).
+// is up to four MMA tiles D_t = A_t B^T with M = 128 rows (pair, rhs) each, N = K = K_c, the
+// class's truncated size (p_c^2 rounded up to 16; P rounded up without truncation):
+// A_t = gathered multipole rows, B = T_c (row n of T_c is K-contiguous, i.e. K-major). The
+// tiles share every staged block of T_c, which divides its traffic; a chunk of a class with
+// K_c <= 128 has four tiles (TMEM columns 128 apart), the others two (256 apart), so the small
+// truncated classes amortise a block's set-up and pipeline fill over twice the rows.
 //
 // Accuracy: both operands are split into three BF16 pieces, x = x0 + x1 + x2 (x0 = bf16(x),
 // x1 = bf16(x - x0), x2 = bf16(x - x0 - x1)), and D accumulates in FP32 the six products with
@@ -20,8 +21,8 @@
 // pipeline stage holding A (3 pieces x tiles x 128 x 16) and B (3 pieces x N_pad x 16) in
 // the canonical K-major layout without swizzle (8-row x 16-byte core matrices, K-adjacent core
 // matrices 128 B apart, 8-row groups 256 B apart). The block is warp-specialised: warps 1-7
-// fill the stages with cp.async (16-byte copies; rows past the chunk read as zeros), five
-// stages deep where they fit in shared memory, else four, and let each stage's "full"
+// fill the stages with cp.async (16-byte copies; rows past the chunk read as zeros), three
+// stages deep (two on request), and let each stage's "full"
 // mbarrier count their copies' arrival (cp.async.mbarrier.arrive.noinc); one thread of warp 0
 // waits on "full", issues the stage's MMAs and commits them to the stage's "empty" mbarrier,
 // which releases the stage for refilling. No block-wide barrier runs inside the K loop. Every
@@ -37,9 +38,12 @@ namespace bem {
 namespace {
 
 constexpr int TC_M = 128;        // rows per tile
-constexpr int TC_TILES = 2;      // tiles per block (same class, shared B stages)
+constexpr int TC_MAXT = 4;       // tiles per block at most (same class, shared B stages)
+constexpr int TC_SMALL_K = 128;  // classes truncated to at most this size take four tiles per block
+// bytes of one pipeline stage: A (3 pieces x tiles x 128 x 16 BF16) and B (3 pieces x K_c x 16),
+// for four tiles with K_c <= 128 or two tiles with K_c <= 256 (the larger of the two)
+constexpr size_t TC_STAGE_BYTES = 3 * 4 * TC_M * 16 * 2 + 3 * 128 * 16 * 2;
 constexpr int TC_K = 16;         // K per stage (one kind::f16 MMA)
-constexpr int TC_MAX_SMEM = 225 * 1024;  // dynamic shared memory per block (227 KB less the static part)
 constexpr int TC_THREADS = 256;  // 8 warps: two warp groups share the loads and the epilogue
 constexpr uint32_t TC_LBO = 128;  // bytes between K-adjacent core matrices
 constexpr uint32_t TC_SBO = 256;  // bytes between 8-row groups
@@ -164,20 +168,21 @@ __global__ void k_split_x(int64_t rows, int P, int Kp, const float *__restrict__
 }
 
 struct TcLayout {
-    size_t a_bytes, b_bytes, stage_bytes, total;
+    size_t stage_bytes, total;
 };
 
 // ST pipeline stages; the epilogue reuses the stages for one tile of FP32 rows (at most N_pad
 // floats each)
 __host__ __device__ inline TcLayout tc_layout(int Npad, int ST) {
     TcLayout L;
-    L.a_bytes = (size_t)3 * TC_TILES * TC_M * TC_K * 2;
-    L.b_bytes = (size_t)3 * Npad * TC_K * 2;
-    L.stage_bytes = L.a_bytes + L.b_bytes;
+    L.stage_bytes = TC_STAGE_BYTES;
     const size_t epi = (size_t)TC_M * Npad * 4;
     L.total = (ST * L.stage_bytes > epi ? ST * L.stage_bytes : epi) + 2 * ST * 8 + 16 + 1024;
     return L;
 }
+
+// tiles per block and TMEM columns per tile for a class truncated to K_c
+__host__ __device__ inline int tc_tiles_for(int Kc) { return Kc <= TC_SMALL_K ? TC_MAXT : 2; }
 
 template <int R, int TC_STAGES>
 __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __nv_bfloat16 *__restrict__ tcB,
@@ -196,18 +201,21 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(full + TC_STAGES);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     constexpr int NPROD = TC_THREADS - 32;  // warps 1.. fill the stages, warp 0 issues the MMAs
-    __shared__ int s_src[TC_TILES * TC_M];
+    __shared__ int s_src[TC_MAXT * TC_M];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // once a block has reported a wait that ran out, the rest skip their work
     if (*reinterpret_cast<volatile int *>(err) != 0) return;
     const XChunk ch = chunks[blockIdx.x];
     const int nrows = ch.count * R;
-    const int ntiles = (nrows + TC_M - 1) / TC_M;  // <= TC_TILES
-    // the class's truncated size (a multiple of 16, <= Npad): K steps and output columns
+    const int ntiles = (nrows + TC_M - 1) / TC_M;
+    // the class's truncated size (a multiple of 16, <= Npad): K steps and output columns; small
+    // classes take four tiles per block (TMEM columns 128 apart), the others two (256 apart)
     const int Kc = cls_K ? cls_K[ch.cls] : Npad;
     const int nsteps = Kc / TC_K;
-    for (int r = tid; r < TC_TILES * TC_M; r += TC_THREADS) s_src[r] = (r < nrows) ? srcs[ch.start + r / R] : -1;
+    const int tcap = tc_tiles_for(Kc);
+    const uint32_t colstride = Kc <= TC_SMALL_K ? 128u : 256u;
+    for (int r = tid; r < TC_MAXT * TC_M; r += TC_THREADS) s_src[r] = (r < nrows) ? srcs[ch.start + r / R] : -1;
     if (tid == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
@@ -218,7 +226,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "n"(TC_TILES * 256));
+                     "n"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -230,17 +238,20 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
     const int64_t plane = xrows * Kp;
     const __nv_bfloat16 *Bc = tcB + (size_t)ch.cls * (Npad / TC_K) * 3 * Npad * TC_K;  // the class's full table
     const uint32_t sbase = smem_u32(smem);
-    const uint32_t apiece = TC_TILES * TC_M * TC_K * 2, atile = TC_M * TC_K * 2;
-    const uint32_t bpiece = (uint32_t)Npad * TC_K * 2;
+    const uint32_t atile = TC_M * TC_K * 2, apiece = (uint32_t)tcap * atile;
+    const uint32_t a_bytes = 3 * apiece;
+    const uint32_t bpiece = (uint32_t)Kc * TC_K * 2;        // one piece's K_c rows in shared memory
+    const size_t bpiece_g = (size_t)Npad * TC_K * 2;        // one piece's block in the table
 
     // fill stage `st` with K step `ks`
     auto load_stage = [&](int ks, int st, int pt) {
         const uint32_t sa = sbase + st * (uint32_t)Lo.stage_bytes;
-        const uint32_t sb = sa + (uint32_t)Lo.a_bytes;
-        // A: u -> (piece, tile row, j); 16 bytes = 8 consecutive k of one row
-        for (int u = pt; u < 3 * TC_TILES * TC_M * 2; u += NPROD) {
+        const uint32_t sb = sa + a_bytes;
+        // A: u -> (piece, tile row, j) over the chunk's tiles; 16 bytes = 8 consecutive k of one row
+        const int arows = ntiles * TC_M;
+        for (int u = pt; u < 3 * arows * 2; u += NPROD) {
             const int j = u & 1;
-            const int row2 = (u >> 1) % (TC_TILES * TC_M), piece = (u >> 1) / (TC_TILES * TC_M);
+            const int row2 = (u >> 1) % arows, piece = (u >> 1) / arows;
             const int t = row2 / TC_M, row = row2 % TC_M;
             const int s = s_src[row2];
             const int rr = row2 % R;
@@ -255,7 +266,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
         const int per_piece = Kc * TC_K * 2 / 16;  // 16-byte units of one piece's prefix
         for (int u = pt; u < 3 * per_piece; u += NPROD) {
             const int piece = u / per_piece, v = u - piece * per_piece;
-            cp_async16(sb + piece * bpiece + v * 16, bsrc + (size_t)piece * bpiece + (size_t)v * 16, 16u);
+            cp_async16(sb + piece * bpiece + v * 16, bsrc + (size_t)piece * bpiece_g + (size_t)v * 16, 16u);
         }
     };
 
@@ -279,9 +290,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t sa = sbase + st * (uint32_t)Lo.stage_bytes;
-                const uint32_t sb = sa + (uint32_t)Lo.a_bytes;
+                const uint32_t sb = sa + a_bytes;
                 for (int t = 0; t < ntiles; ++t) {
-                    const uint32_t d = tmem + (uint32_t)(t * 256);
+                    const uint32_t d = tmem + (uint32_t)t * colstride;
                     const uint32_t a0 = sa + t * atile;
                     // smallest terms first: (2,0) (1,1) (0,2) (1,0) (0,1) (0,0)
                     mma_bf16(d, make_desc(a0 + 2 * apiece), make_desc(sb), idesc, ks > 0 ? 1u : 0u);
@@ -334,7 +345,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
             for (int c0 = g0 * 16; c0 < g1 * 16; c0 += 16) {
                 if (c0 >= Kc) continue;  // beyond the class's truncation: neither computed nor stored
                 uint32_t v[16];
-                const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(t * 256 + c0);
+                const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)t * colstride + (uint32_t)c0;
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
                     "[%16];"
@@ -368,14 +379,14 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TC_TILES * 256));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(512));
 }
 
 }  // namespace
 
 bool m2l_tc_supported(int P) { return P % 4 == 0 && P <= 256; }
 
-int m2l_tc_pairs_per_chunk(int R) { return TC_TILES * TC_M / R; }
+int m2l_tc_pairs_per_chunk(int R, int Kc) { return tc_tiles_for(Kc) * TC_M / R; }
 
 void build_tc_tables(Context &c, Operators &o) {
     const int P = o.P;
@@ -404,14 +415,13 @@ void launch_m2l_tc(Context &c, const Operators &o, const XChunk *chunks, int64_t
         k_split_x<<<nb, 256, 0, st>>>(xrows, o.P, Npad, X, xs);
         BEM_LAUNCH_CHECK();
     }
-    // pipeline depth: the context's choice (parameter or autotuner), else five stages (the copies
-    // of a step start four steps ahead) where they fit, else four; never more than fit
-    int stages = c.tuned_stages > 0 ? c.tuned_stages : 5;
-    while (stages > 3 && tc_layout(Npad, stages).total > (size_t)TC_MAX_SMEM) --stages;
+    // pipeline depth: the context's choice (parameter or autotuner), else three stages (as many as
+    // fit at the four-tile stage size)
+    const int stages = c.tuned_stages == 2 ? 2 : 3;
     const size_t sm = tc_layout(Npad, stages).total;
-    auto kern = stages == 5 ? k_m2l_tc<R, 5> : stages == 4 ? k_m2l_tc<R, 4> : k_m2l_tc<R, 3>;
+    auto kern = stages == 2 ? k_m2l_tc<R, 2> : k_m2l_tc<R, 3>;
     // set on every launch: the attribute belongs to the current device (~1 us against a ms kernel)
-    BEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_MAX_SMEM));
+    BEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     kern<<<(unsigned)nchunks, TC_THREADS, sm, st>>>(o.P, Npad, reinterpret_cast<const __nv_bfloat16 *>(o.m2l_tc.p),
                                                    chunks, c.tree.m2l_src.p, xrows, xs, Ypair,
                                                    o.margin >= 0 ? o.cls_K.p : nullptr, err);
