@@ -103,6 +103,18 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// Bulk copy (the TMA engine, no tensor map) of `bytes` contiguous bytes global -> shared; it
+// counts its bytes on `mbar`, whose phase the issuing thread opened with expect_tx. Both
+// addresses and the size are multiples of 16 bytes.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
 // element offset of (row, kk) inside one 16-wide K step of a K-major operand block
 __host__ __device__ constexpr int kmajor_off(int row, int kk) {
     return (row >> 3) * 128 + (kk >> 3) * 64 + (row & 7) * 8 + (kk & 7);
@@ -171,13 +183,13 @@ struct TcLayout {
     size_t stage_bytes, total;
 };
 
-// ST pipeline stages; the epilogue reuses the stages for one tile of FP32 rows (at most N_pad
-// floats each)
+// ST pipeline stages and three mbarriers per stage (empty, full, bfull); the epilogue reuses
+// the stages for one tile of FP32 rows (at most N_pad floats each)
 __host__ __device__ inline TcLayout tc_layout(int Npad, int ST) {
     TcLayout L;
     L.stage_bytes = TC_STAGE_BYTES;
     const size_t epi = (size_t)TC_M * Npad * 4;
-    L.total = (ST * L.stage_bytes > epi ? ST * L.stage_bytes : epi) + 2 * ST * 8 + 16 + 1024;
+    L.total = (ST * L.stage_bytes > epi ? ST * L.stage_bytes : epi) + 3 * ST * 8 + 16 + 1024;
     return L;
 }
 
@@ -197,8 +209,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
     const size_t epi_bytes = (size_t)TC_M * Npad * 4;
     uint64_t *empty = reinterpret_cast<uint64_t *>(
         smem + (TC_STAGES * Lo.stage_bytes > epi_bytes ? TC_STAGES * Lo.stage_bytes : epi_bytes));
-    uint64_t *full = empty + TC_STAGES;  // NPROD producer arrivals per use
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(full + TC_STAGES);
+    uint64_t *full = empty + TC_STAGES;  // NPROD producer arrivals per use (the gathered A rows)
+    uint64_t *bfull = full + TC_STAGES;  // one arrival + the bulk copy's bytes (the block of T_c)
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bfull + TC_STAGES);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     constexpr int NPROD = TC_THREADS - 32;  // warps 1.. fill the stages, warp 0 issues the MMAs
     __shared__ int s_src[TC_MAXT * TC_M];
@@ -220,6 +233,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
         for (int s = 0; s < TC_STAGES; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[s])), "r"(NPROD));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bfull[s])));
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
@@ -243,38 +257,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
     const uint32_t bpiece = (uint32_t)Kc * TC_K * 2;        // one piece's K_c rows in shared memory
     const size_t bpiece_g = (size_t)Npad * TC_K * 2;        // one piece's block in the table
 
-    // fill stage `st` with K step `ks`
-    auto load_stage = [&](int ks, int st, int pt) {
-        const uint32_t sa = sbase + st * (uint32_t)Lo.stage_bytes;
-        const uint32_t sb = sa + a_bytes;
-        // A: u -> (piece, tile row, j) over the chunk's tiles; 16 bytes = 8 consecutive k of one row
-        const int arows = ntiles * TC_M;
-        for (int u = pt; u < 3 * arows * 2; u += NPROD) {
-            const int j = u & 1;
-            const int row2 = (u >> 1) % arows, piece = (u >> 1) / arows;
-            const int t = row2 / TC_M, row = row2 % TC_M;
-            const int s = s_src[row2];
-            const int rr = row2 % R;
-            const __nv_bfloat16 *src =
-                Xs + (size_t)piece * plane + ((size_t)(s >= 0 ? s : 0) * R + rr) * Kp + ks * TC_K + j * 8;
-            const uint32_t dst = sa + piece * apiece + t * atile + (uint32_t)kmajor_off(row, j * 8) * 2;
-            cp_async16(dst, src, s >= 0 ? 16u : 0u);
-        }
-        // B: the first Kc rows of each piece's pre-tiled block (8-row core-matrix groups are
-        // contiguous, so that is a prefix of the block)
-        const unsigned char *bsrc = reinterpret_cast<const unsigned char *>(Bc + (size_t)ks * 3 * Npad * TC_K);
-        const int per_piece = Kc * TC_K * 2 / 16;  // 16-byte units of one piece's prefix
-        for (int u = pt; u < 3 * per_piece; u += NPROD) {
-            const int piece = u / per_piece, v = u - piece * per_piece;
-            cp_async16(sb + piece * bpiece + v * 16, bsrc + (size_t)piece * bpiece_g + (size_t)v * 16, 16u);
-        }
-    };
-
     // Warp-specialised pipeline. Producers (warps 1..) wait until the MMAs that last read a stage
-    // are done (its empty barrier), copy their share of the next K step into it and let the
-    // stage's full barrier count their arrival once those copies have landed
-    // (cp.async.mbarrier.arrive.noinc). One thread of warp 0 waits for full, makes the copies
-    // visible to the tensor core (proxy fence), issues the step's MMAs and commits them to empty.
+    // are done (its empty barrier), gather their share of the next K step's A rows into it and let
+    // the stage's full barrier count their arrival once those copies have landed
+    // (cp.async.mbarrier.arrive.noinc); one producer thread also moves the step's block of T_c
+    // (three contiguous pieces) with bulk copies counted on bfull. One thread of warp 0 waits for
+    // full and bfull, makes the gathered copies visible to the tensor core (proxy fence), issues
+    // the step's MMAs and commits them to empty.
     // No block-wide barrier inside the loop; every wait is bounded and a timeout raises the shared
     // abort flag, which stops the other side at its next wait.
     __shared__ int s_last_ks;
@@ -283,7 +272,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
             int ks = 0;
             for (; ks < nsteps; ++ks) {
                 const int st = ks % TC_STAGES;
-                if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((ks / TC_STAGES) & 1)) || *abort_flag) {
+                const uint32_t ph = (uint32_t)((ks / TC_STAGES) & 1);
+                if (!mbar_wait(smem_u32(&full[st]), ph) || !mbar_wait(smem_u32(&bfull[st]), ph) || *abort_flag) {
                     *abort_flag = 1;
                     break;
                 }
@@ -309,6 +299,23 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
         __syncwarp();
     } else {
         const int pt = tid - 32;
+        // this thread's A copies, fixed for the block: unit u = (tile row, 8-element half j) of every
+        // K step; its three pieces are one plane apart in Xs and one piece block apart in a stage
+        constexpr int AU = (TC_MAXT * TC_M * 2 + NPROD - 1) / NPROD;
+        const int arows = ntiles * TC_M;
+        const __nv_bfloat16 *a_src[AU];
+        uint32_t a_dst[AU], a_sz[AU];
+#pragma unroll
+        for (int i = 0; i < AU; ++i) {
+            const int u = pt + i * NPROD;
+            const int j = u & 1, row2 = u >> 1;
+            const int s = u < 2 * arows ? s_src[row2] : -1;
+            a_src[i] = Xs + ((size_t)(s >= 0 ? s : 0) * R + row2 % R) * Kp + j * 8;
+            a_dst[i] = (uint32_t)((row2 / TC_M) * atile + kmajor_off(row2 % TC_M, j * 8) * 2);
+            a_sz[i] = s >= 0 ? 16u : 0u;  // rows past the chunk: zeros, nothing read
+        }
+        const bool bulk = pt == 0;
+        int issued = -1;  // last K step whose block of T_c this thread requested
         for (int ks = 0; ks < nsteps; ++ks) {
             const int st = ks % TC_STAGES;
             // the stage's previous use (step ks - ST) must be consumed: completion ks / ST - 1
@@ -317,10 +324,34 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tc(int P, int Npad, const __
                 *abort_flag = 1;
                 break;
             }
-            load_stage(ks, st, pt);
+            const uint32_t sa = sbase + st * (uint32_t)Lo.stage_bytes;
+            if (bulk) {
+                // B: the first K_c rows of each piece's pre-tiled block (8-row core-matrix groups are
+                // contiguous, so that is a prefix of the block)
+                const uint32_t bb = smem_u32(&bfull[st]);
+                mbar_expect_tx(bb, 3u * bpiece);
+                const unsigned char *bsrc = reinterpret_cast<const unsigned char *>(Bc + (size_t)ks * 3 * Npad * TC_K);
+                for (int piece = 0; piece < 3; ++piece)
+                    bulk_g2s(sa + a_bytes + piece * bpiece, bsrc + (size_t)piece * bpiece_g, bpiece, bb);
+                issued = ks;
+            }
+#pragma unroll
+            for (int i = 0; i < AU; ++i) {
+                if (pt + i * NPROD < 2 * arows) {
+                    const __nv_bfloat16 *src = a_src[i] + ks * TC_K;
+                    const uint32_t dst = sa + a_dst[i];
+                    cp_async16(dst, src, a_sz[i]);
+                    cp_async16(dst + apiece, src + plane, a_sz[i]);
+                    cp_async16(dst + 2 * apiece, src + 2 * plane, a_sz[i]);
+                }
+            }
             asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&full[st])) : "memory");
         }
         cp_async_wait<0>();  // nothing of this thread in flight past this point
+        // the bulk copies of the last steps (those an abort left unconsumed included) land before
+        // the block moves on: each stage's latest bfull phase completes when its copy has landed
+        for (int ks = issued; ks >= 0 && ks > issued - TC_STAGES; --ks)
+            if (!mbar_wait(smem_u32(&bfull[ks % TC_STAGES]), (uint32_t)((ks / TC_STAGES) & 1))) *abort_flag = 1;
     }
     __syncthreads();
     // tcgen05.commit tracks every earlier MMA of the issuing thread: the last commit covers all
