@@ -10,6 +10,7 @@
 #include "internal.h"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace bem {
 namespace {
@@ -227,6 +228,226 @@ __device__ __forceinline__ void p2p_unit(P2PStage<T, R, HQ, HW> &sg, int lane, i
     else p2p_unit_g<T, R, 8, HQ, HW>(sg, lane, b, r0, nr, bstart, bcount, nbr, ncnt, nd, N, loc, nrm, q, w, out);
 }
 
+// FP32 form with packed two-wide arithmetic (add/mul/fma .f32x2: one instruction for two
+// lanes' worth of FP32 work). The near field is issue-bound, so each lane takes its two
+// receivers against two sources at a time: a staged tile holds 16 source pairs, each as
+// (-x, -x', -y, -y'), (-z, -z', q, q') (and (n_x, n_x', n_y, n_y'), (n_z, n_z', w, w') for the
+// double layer); a receiver's coordinate is a broadcast pair, so x_i - x_j is one packed add of
+// the negated source coordinate (exactly the scalar difference) and r^2, the sums and the
+// double layer's n.(r_i - r_j) / r^3 are packed products; the reciprocal square roots stay
+// scalar. Lanes past a tile's end stage a source of zero strength far outside the leaf's
+// neighbourhood (finite r^2), so a partial tile runs whole pairs.
+template <int R, bool HQ, bool HW>
+struct P2PStageX2 {
+    float4 a[16];               // -x, -x', -y, -y'
+    float4 b[16];               // -z, -z', q, q' (first RHS)
+    float4 c[HW ? 16 : 1];      // n_x, n_x', n_y, n_y'
+    float4 d[HW ? 16 : 1];      // n_z, n_z', w, w' (first RHS)
+    float q[(R > 1 && HQ) ? R - 1 : 1][32];
+    float w[(R > 1 && HW) ? R - 1 : 1][32];
+};
+
+template <bool SELF>
+__device__ __forceinline__ float2 rsqrt_x2(float2 r2) {
+    float2 ri;
+    ri.x = SELF ? (r2.x > 0.f ? rsqrt_t<float>(r2.x) : 0.f) : rsqrt_t<float>(r2.x);
+    ri.y = SELF ? (r2.y > 0.f ? rsqrt_t<float>(r2.y) : 0.f) : rsqrt_t<float>(r2.y);
+    return ri;
+}
+
+template <int R, bool HQ, bool HW, bool SELF>
+__device__ __forceinline__ void p2p_source_x2(const P2PStageX2<R, HQ, HW> &sg, int p, const float2 *X,
+                                              const float2 *Y, const float2 *Z, float2 (*part)[R]) {
+    const float4 A = sg.a[p], B = sg.b[p];
+    const float2 mx = make_float2(A.x, A.y), my = make_float2(A.z, A.w), mz = make_float2(B.x, B.y);
+    float4 C, D;
+    if (HW) {
+        C = sg.c[p];
+        D = sg.d[p];
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float2 dx = __fadd2_rn(X[k], mx), dy = __fadd2_rn(Y[k], my), dz = __fadd2_rn(Z[k], mz);
+        float2 r2 = __fmul2_rn(dx, dx);
+        r2 = __ffma2_rn(dy, dy, r2);
+        r2 = __ffma2_rn(dz, dz, r2);
+        const float2 ri = rsqrt_x2<SELF>(r2);
+        if (HQ) {
+            part[k][0] = __ffma2_rn(make_float2(B.z, B.w), ri, part[k][0]);
+#pragma unroll
+            for (int r = 1; r < R; ++r)
+                part[k][r] = __ffma2_rn(*reinterpret_cast<const float2 *>(&sg.q[r - 1][2 * p]), ri, part[k][r]);
+        }
+        if (HW) {
+            float2 nd = __fmul2_rn(make_float2(C.x, C.y), dx);
+            nd = __ffma2_rn(make_float2(C.z, C.w), dy, nd);
+            nd = __ffma2_rn(make_float2(D.x, D.y), dz, nd);
+            const float2 nd3 = __fmul2_rn(nd, __fmul2_rn(__fmul2_rn(ri, ri), ri));
+            part[k][0] = __ffma2_rn(make_float2(D.z, D.w), nd3, part[k][0]);
+#pragma unroll
+            for (int r = 1; r < R; ++r)
+                part[k][r] = __ffma2_rn(*reinterpret_cast<const float2 *>(&sg.w[r - 1][2 * p]), nd3, part[k][r]);
+        }
+    }
+}
+
+// one staged tile (up to 16 source pairs) against a lane's two receivers; group gi of G takes
+// the pairs gi * 16/G .. (gi + 1) * 16/G - 1
+template <int R, int G, bool HQ, bool HW, bool SELF>
+__device__ __forceinline__ void p2p_tile_x2(const P2PStageX2<R, HQ, HW> &sg, int ns, int gi, const float2 *X,
+                                            const float2 *Y, const float2 *Z, Comp<float> (*acc)[R]) {
+    constexpr int SP = 16 / G;  // source pairs per group and tile
+    float2 part[2][R];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int r = 0; r < R; ++r) part[k][r] = make_float2(0.f, 0.f);
+    const int p0 = gi * SP;
+    if (ns == 32) {
+#pragma unroll 4
+        for (int t = 0; t < SP; ++t) p2p_source_x2<R, HQ, HW, SELF>(sg, p0 + t, X, Y, Z, part);
+    } else {
+        const int e = min(SP, (ns + 1) / 2 - p0);
+#pragma unroll 2
+        for (int t = 0; t < e; ++t) p2p_source_x2<R, HQ, HW, SELF>(sg, p0 + t, X, Y, Z, part);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[k][r].add(part[k][r].x + part[k][r].y);
+}
+
+// the packed counterpart of p2p_unit_g (same units, lanes, groups and merge)
+template <int R, int G, bool HQ, bool HW>
+__device__ __forceinline__ void p2p_unit_gx2(P2PStageX2<R, HQ, HW> &sg, int lane, int b, int r0, int nr,
+                                             const int32_t *__restrict__ bstart, const int32_t *__restrict__ bcount,
+                                             const int32_t *__restrict__ nbr, const int32_t *__restrict__ ncnt,
+                                             const int8_t *__restrict__ nd, int64_t N, const float *__restrict__ loc,
+                                             const float *__restrict__ nrm, const float *__restrict__ q,
+                                             const float *__restrict__ w, double *__restrict__ out) {
+    constexpr int LG = 32 / G;
+    const int rs = lane & (LG - 1), gi = lane / LG;
+    const int s0 = bstart[b];
+    float2 X[2], Y[2], Z[2];
+    Comp<float> acc[2][R];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int li = rs + k * LG;
+        const int64_t i = s0 + r0 + (li < nr ? li : 0);
+        const float x = loc[i], y = loc[N + i], z = loc[2 * N + i];
+        X[k] = make_float2(x, x);
+        Y[k] = make_float2(y, y);
+        Z[k] = make_float2(z, z);
+    }
+    const int nn = ncnt[b];
+    int my_f = 0;
+    float my_d[3] = {0.f, 0.f, 0.f};
+    if (lane < nn) {
+        my_f = nbr[b * 27 + lane];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) my_d[d] = (float)nd[(b * 27 + lane) * 4 + d];
+    }
+    const int sp = lane >> 1, h = lane & 1;  // this lane's slot when staging
+    for (int k = 0; k < nn; ++k) {
+        const int f = __shfl_sync(0xffffffffu, my_f, k);
+        const float ox = __shfl_sync(0xffffffffu, my_d[0], k);
+        const float oy = __shfl_sync(0xffffffffu, my_d[1], k);
+        const float oz = __shfl_sync(0xffffffffu, my_d[2], k);
+        const int fs = bstart[f], fc = bcount[f];
+        const bool self = (f == b);
+        for (int t0 = 0; t0 < fc; t0 += 32) {
+            float *a = reinterpret_cast<float *>(&sg.a[sp]);
+            float *bq = reinterpret_cast<float *>(&sg.b[sp]);
+            if (t0 + lane < fc) {
+                const int64_t j = fs + t0 + lane;
+                a[h] = -(loc[j] + ox);
+                a[2 + h] = -(loc[N + j] + oy);
+                bq[h] = -(loc[2 * N + j] + oz);
+                bq[2 + h] = HQ ? q[j] : 0.f;
+                if (HW) {
+                    float *c = reinterpret_cast<float *>(&sg.c[sp]);
+                    float *dd = reinterpret_cast<float *>(&sg.d[sp]);
+                    c[h] = nrm[j];
+                    c[2 + h] = nrm[N + j];
+                    dd[h] = nrm[2 * N + j];
+                    dd[2 + h] = w[j];
+                }
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    if (HQ) sg.q[r - 1][lane] = q[r * N + j];
+                    if (HW) sg.w[r - 1][lane] = w[r * N + j];
+                }
+            } else {  // zero strength, 1e4 leaf widths away
+                a[h] = -1e4f;
+                a[2 + h] = -1e4f;
+                bq[h] = -1e4f;
+                bq[2 + h] = 0.f;
+                if (HW) {
+                    float *c = reinterpret_cast<float *>(&sg.c[sp]);
+                    float *dd = reinterpret_cast<float *>(&sg.d[sp]);
+                    c[h] = 0.f;
+                    c[2 + h] = 0.f;
+                    dd[h] = 0.f;
+                    dd[2 + h] = 0.f;
+                }
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    if (HQ) sg.q[r - 1][lane] = 0.f;
+                    if (HW) sg.w[r - 1][lane] = 0.f;
+                }
+            }
+            __syncwarp();
+            const int ns = min(32, fc - t0);
+            if (self) p2p_tile_x2<R, G, HQ, HW, true>(sg, ns, gi, X, Y, Z, acc);
+            else p2p_tile_x2<R, G, HQ, HW, false>(sg, ns, gi, X, Y, Z, acc);
+            __syncwarp();
+        }
+    }
+#pragma unroll
+    for (int off = LG; off < 32; off <<= 1)
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float os = __shfl_xor_sync(0xffffffffu, acc[k][r].s, off);
+                const float oc = __shfl_xor_sync(0xffffffffu, acc[k][r].c, off);
+                acc[k][r].add(os);
+                acc[k][r].c += oc;
+            }
+    if (gi == 0) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int li = rs + k * LG;
+            if (li < nr) {
+                const int64_t i = s0 + r0 + li;
+#pragma unroll
+                for (int r = 0; r < R; ++r) out[r * N + i] = acc[k][r].get();
+            }
+        }
+    }
+}
+
+template <int R, bool HQ, bool HW>
+__global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_units_x2(
+    const int2 *__restrict__ units, int64_t nunits, const int32_t *__restrict__ bstart,
+    const int32_t *__restrict__ bcount, const int32_t *__restrict__ nbr, const int32_t *__restrict__ ncnt,
+    const int8_t *__restrict__ nd, int64_t N, const float *__restrict__ loc, const float *__restrict__ nrm,
+    const float *__restrict__ q, const float *__restrict__ w, double *__restrict__ out) {
+    __shared__ P2PStageX2<R, HQ, HW> stage[P2P_WARPS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * P2P_WARPS;
+    for (int64_t u = (int64_t)blockIdx.x * P2P_WARPS + warp; u < nunits; u += stride) {
+        const int2 un = units[u];
+        const int b = un.x, r0 = un.y;
+        const int nr = min(P2P_UNIT, bcount[b] - r0);  // uniform in the warp
+        auto &sg = stage[warp];
+        if (nr > 32) p2p_unit_gx2<R, 1, HQ, HW>(sg, lane, b, r0, nr, bstart, bcount, nbr, ncnt, nd, N, loc, nrm, q, w, out);
+        else if (nr > 16) p2p_unit_gx2<R, 2, HQ, HW>(sg, lane, b, r0, nr, bstart, bcount, nbr, ncnt, nd, N, loc, nrm, q, w, out);
+        else if (nr > 8) p2p_unit_gx2<R, 4, HQ, HW>(sg, lane, b, r0, nr, bstart, bcount, nbr, ncnt, nd, N, loc, nrm, q, w, out);
+        else p2p_unit_gx2<R, 8, HQ, HW>(sg, lane, b, r0, nr, bstart, bcount, nbr, ncnt, nd, N, loc, nrm, q, w, out);
+    }
+}
+
 // Each warp takes the units u = blockIdx.x * P2P_WARPS + warp, then every gridDim.x * P2P_WARPS
 // further: one unit per warp when the grid covers all units, or a persistent grid of a fixed
 // number of blocks per SM (leaving room on every SM for the far-field kernels that run
@@ -384,12 +605,16 @@ static void launch_units(Context &c, const T *q, const T *w, double *out_sorted,
     // memory: the tensor-core M2L needs it, and an SM whose resident near-field blocks had it
     // configured for more L1 would first have to drain them. (A per-device attribute, set on
     // every launch; about a microsecond.)
+    // FP32: the packed kernel; FP64: the scalar one
+    auto kern = [] {
+        if constexpr (std::is_same<T, float>::value) return k_p2p_units_x2<R, HQ, HW>;
+        else return k_p2p_units<T, R, HQ, HW>;
+    }();
     if (c.tuned_overlap)
-        BEM_CUDA(cudaFuncSetAttribute(k_p2p_units<T, R, HQ, HW>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        BEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       (int)cudaSharedmemCarveoutMaxShared));
-    k_p2p_units<T, R, HQ, HW><<<(unsigned)blocks, P2P_WARPS * 32, 0, st>>>(
-        t.p2p_units.p, nu, t.bstart.p + t.base[L], t.bcount.p + t.base[L], t.nbr.p, t.nbr_cnt.p, t.nbr_d.p, c.N, loc,
-        nrm, q, w, out_sorted);
+    kern<<<(unsigned)blocks, P2P_WARPS * 32, 0, st>>>(t.p2p_units.p, nu, t.bstart.p + t.base[L], t.bcount.p + t.base[L],
+                                                       t.nbr.p, t.nbr_cnt.p, t.nbr_d.p, c.N, loc, nrm, q, w, out_sorted);
     BEM_LAUNCH_CHECK();
 }
 
