@@ -145,6 +145,15 @@ struct Tree {
     // near-field work units: (leaf, first receiver), up to 64 receivers of one leaf each
     DevBuf<int2> p2p_units;
     int64_t n_p2p_units = 0;
+    DevBuf<int32_t> p2p_ucnt;  // [nleaf] units per leaf
+    // symmetric near field (FP32 single-RHS products): a pair of neighbour leaves A < B is
+    // evaluated once, by A's units; each unit of A writes B's share (one float per point of B)
+    // into its own region of `back`, and a gather adds those shares to B's points in a fixed order
+    DevBuf<int32_t> back_S;     // [nleaf] floats one unit of leaf A writes (its neighbours B > A)
+    DevBuf<int64_t> back_base;  // [nleaf] first float of leaf A's units' region
+    DevBuf<int32_t> back_gofs;  // [nleaf][27] neighbour k = A < B of leaf B: offset of B's share in a unit of A; else -1
+    DevBuf<float> back;         // [n_back]
+    int64_t n_back = 0;
 };
 
 // ------------------------------------------------------------------------------ FMM operators

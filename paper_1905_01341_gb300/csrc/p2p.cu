@@ -7,6 +7,12 @@
 // leaf-box units with coordinates relative to each leaf centre (integer box offsets are
 // exact in FP32), the direct kernel splits coordinates into hi + lo FP32 pairs. Sums are
 // formed per shared-memory tile in FP32 and merged with TwoSum compensation.
+//
+// The kernel of Eq. (ns1) is symmetric in r = |r_i - r_j|, so the FP32 single-RHS products
+// evaluate every pair of neighbour leaves A < B once, by A's units: one reciprocal square root
+// feeds both q_j / r into r_i and q_i / r (and the double layer's exchanged dipole term) into
+// r_j. B's shares are summed over A's receivers inside the warp, stored per (unit of A, B), and
+// added to B's points by a second kernel in a fixed order: no atomics, deterministic results.
 #include "internal.h"
 
 #include <algorithm>
@@ -245,6 +251,7 @@ struct P2PStageX2 {
     float4 d[HW ? 16 : 1];      // n_z, n_z', w, w' (first RHS)
     float q[(R > 1 && HQ) ? R - 1 : 1][32];
     float w[(R > 1 && HW) ? R - 1 : 1][32];
+    float tr[R == 1 ? 32 : 1][20];  // symmetric form: per-lane rows of the sources' shares, transposed
 };
 
 template <bool SELF>
@@ -255,9 +262,18 @@ __device__ __forceinline__ float2 rsqrt_x2(float2 r2) {
     return ri;
 }
 
-template <int R, bool HQ, bool HW, bool SELF>
+// The receivers' own data for the symmetric form (broadcast pairs, zero for lanes past the
+// unit's end): strength q_i, and for the double layer n_i and -w_i.
+struct RecvX2 {
+    float2 q[2], nx[2], ny[2], nz[2], wneg[2];
+};
+
+// BACK: also accumulate the pair's share for the two sources, sum over this lane's receivers of
+// q_i / r - w_i n_i.(r_i - r_j) / r^3 (the kernel with source and receiver exchanged)
+template <int R, bool HQ, bool HW, bool SELF, bool BACK = false>
 __device__ __forceinline__ void p2p_source_x2(const P2PStageX2<R, HQ, HW> &sg, int p, const float2 *X,
-                                              const float2 *Y, const float2 *Z, float2 (*part)[R]) {
+                                              const float2 *Y, const float2 *Z, float2 (*part)[R],
+                                              const RecvX2 *rv = nullptr, float2 *bk = nullptr) {
     const float4 A = sg.a[p], B = sg.b[p];
     const float2 mx = make_float2(A.x, A.y), my = make_float2(A.z, A.w), mz = make_float2(B.x, B.y);
     float4 C, D;
@@ -277,18 +293,84 @@ __device__ __forceinline__ void p2p_source_x2(const P2PStageX2<R, HQ, HW> &sg, i
 #pragma unroll
             for (int r = 1; r < R; ++r)
                 part[k][r] = __ffma2_rn(*reinterpret_cast<const float2 *>(&sg.q[r - 1][2 * p]), ri, part[k][r]);
+            if (BACK) *bk = __ffma2_rn(rv->q[k], ri, *bk);
         }
         if (HW) {
             float2 nd = __fmul2_rn(make_float2(C.x, C.y), dx);
             nd = __ffma2_rn(make_float2(C.z, C.w), dy, nd);
             nd = __ffma2_rn(make_float2(D.x, D.y), dz, nd);
-            const float2 nd3 = __fmul2_rn(nd, __fmul2_rn(__fmul2_rn(ri, ri), ri));
+            const float2 ri3 = __fmul2_rn(__fmul2_rn(ri, ri), ri);
+            const float2 nd3 = __fmul2_rn(nd, ri3);
             part[k][0] = __ffma2_rn(make_float2(D.z, D.w), nd3, part[k][0]);
 #pragma unroll
             for (int r = 1; r < R; ++r)
                 part[k][r] = __ffma2_rn(*reinterpret_cast<const float2 *>(&sg.w[r - 1][2 * p]), nd3, part[k][r]);
+            if (BACK) {
+                float2 ni = __fmul2_rn(rv->nx[k], dx);
+                ni = __ffma2_rn(rv->ny[k], dy, ni);
+                ni = __ffma2_rn(rv->nz[k], dz, ni);
+                *bk = __ffma2_rn(rv->wneg[k], __fmul2_rn(ni, ri3), *bk);
+            }
         }
     }
+}
+
+// A staged tile of an owned neighbour leaf (symmetric form, one RHS): the forward sums as in
+// p2p_tile_x2 and, per batch of up to 16 sources of a group, each source's share summed over the
+// unit's receivers (every group holds all of them), written to back[s] for the tile's source s.
+// The sum over lanes goes through shared memory: every lane stores its row of the batch's
+// values, then lane rs adds up column rs over its group's rows (for one group of 32 lanes, each
+// half of the warp takes half the rows and one shuffle joins them). The groups read their rows
+// in skewed orders so that their columns fall in different banks; the order of every sum is
+// fixed, so the result is deterministic.
+template <int G, bool HQ, bool HW>
+__device__ __forceinline__ void p2p_tile_x2_sym(P2PStageX2<1, HQ, HW> &sg, int ns, int gi, int lane,
+                                                const float2 *X, const float2 *Y, const float2 *Z, const RecvX2 &rv,
+                                                Comp<float> (*acc)[1], float *__restrict__ back) {
+    constexpr int SP = 16 / G, LG = 32 / G;
+    constexpr int HP = SP < 8 ? SP : 8;  // source pairs per batch
+    constexpr int NV = 2 * HP;           // sources per batch: values per lane
+    constexpr int SK = G == 2 ? 4 : (G == 4 ? 2 : 1);  // row skew per group (see above)
+    const int rs = lane & (LG - 1);
+    float2 part[2][1];
+    part[0][0] = part[1][0] = make_float2(0.f, 0.f);
+    const int p0 = gi * SP;
+    const int e = min(SP, (ns + 1) / 2 - p0);  // pairs of this group holding sources
+#pragma unroll
+    for (int h0 = 0; h0 < SP; h0 += HP) {
+        float2 bk[HP];
+#pragma unroll
+        for (int t = 0; t < HP; ++t) bk[t] = make_float2(0.f, 0.f);
+        if (ns == 32) {
+#pragma unroll
+            for (int t = 0; t < HP; ++t) p2p_source_x2<1, HQ, HW, false, true>(sg, p0 + h0 + t, X, Y, Z, part, &rv, &bk[t]);
+        } else {
+#pragma unroll
+            for (int t = 0; t < HP; ++t)
+                if (h0 + t < e) p2p_source_x2<1, HQ, HW, false, true>(sg, p0 + h0 + t, X, Y, Z, part, &rv, &bk[t]);
+        }
+        float4 *row = reinterpret_cast<float4 *>(&sg.tr[lane][0]);
+#pragma unroll
+        for (int c4 = 0; c4 < NV / 4; ++c4)
+            row[c4] = make_float4(bk[2 * c4].x, bk[2 * c4].y, bk[2 * c4 + 1].x, bk[2 * c4 + 1].y);
+        __syncwarp();
+        float tot = 0.f;
+        if constexpr (G == 1) {
+            const int half = lane >> 4, col = lane & 15;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) tot += sg.tr[half * 16 + ((r + 4 * half) & 15)][col];
+            tot += __shfl_xor_sync(0xffffffffu, tot, 16);
+        } else {
+            const int sk = G == 8 ? (gi >> 1) : SK * gi;
+#pragma unroll
+            for (int r = 0; r < LG; ++r) tot += sg.tr[gi * LG + ((r + sk) & (LG - 1))][rs];
+        }
+        __syncwarp();  // the next batch rewrites the rows
+        const int src = 2 * (p0 + h0) + (rs & (NV - 1));
+        if (rs < NV && src < ns) back[src] = tot;
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) acc[k][0].add(part[k][0].x + part[k][0].y);
 }
 
 // one staged tile (up to 16 source pairs) against a lane's two receivers; group gi of G takes
@@ -317,28 +399,56 @@ __device__ __forceinline__ void p2p_tile_x2(const P2PStageX2<R, HQ, HW> &sg, int
         for (int r = 0; r < R; ++r) acc[k][r].add(part[k][r].x + part[k][r].y);
 }
 
+// Symmetric form (SYM, one RHS): a neighbour leaf f > b is owned: its tiles also produce the
+// shares of f's points, written at back + back_unit + (owned points before f) + tile offset; a
+// neighbour f < b is skipped (f's units evaluate the pair and b's points get their shares by
+// the gather); the leaf's own tiles are evaluated one way, all pairs i != j.
+struct BackArgs {
+    float *back;
+    const int32_t *S;
+    const int64_t *base;
+};
+
 // the packed counterpart of p2p_unit_g (same units, lanes, groups and merge)
-template <int R, int G, bool HQ, bool HW>
+template <int R, int G, bool HQ, bool HW, bool SYM = false>
 __device__ __forceinline__ void p2p_unit_gx2(P2PStageX2<R, HQ, HW> &sg, int lane, int b, int r0, int nr,
                                              const int32_t *__restrict__ bstart, const int32_t *__restrict__ bcount,
                                              const int32_t *__restrict__ nbr, const int32_t *__restrict__ ncnt,
                                              const int8_t *__restrict__ nd, int64_t N, const float *__restrict__ loc,
                                              const float *__restrict__ nrm, const float *__restrict__ q,
-                                             const float *__restrict__ w, double *__restrict__ out) {
+                                             const float *__restrict__ w, double *__restrict__ out,
+                                             BackArgs ba = BackArgs{}) {
     constexpr int LG = 32 / G;
     const int rs = lane & (LG - 1), gi = lane / LG;
     const int s0 = bstart[b];
     float2 X[2], Y[2], Z[2];
+    RecvX2 rv;
     Comp<float> acc[2][R];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const int li = rs + k * LG;
-        const int64_t i = s0 + r0 + (li < nr ? li : 0);
+        const bool valid = li < nr;
+        const int64_t i = s0 + r0 + (valid ? li : 0);
         const float x = loc[i], y = loc[N + i], z = loc[2 * N + i];
         X[k] = make_float2(x, x);
         Y[k] = make_float2(y, y);
         Z[k] = make_float2(z, z);
+        if (SYM) {
+            const float qi = (HQ && valid) ? q[i] : 0.f;
+            rv.q[k] = make_float2(qi, qi);
+            if (HW) {
+                const float wi = valid ? -w[i] : 0.f;
+                const float a = nrm[i], bb = nrm[N + i], cc = nrm[2 * N + i];
+                rv.nx[k] = make_float2(a, a);
+                rv.ny[k] = make_float2(bb, bb);
+                rv.nz[k] = make_float2(cc, cc);
+                rv.wneg[k] = make_float2(wi, wi);
+            }
+        }
     }
+    float *back_unit = nullptr;
+    if (SYM) back_unit = ba.back + ba.base[b] + (int64_t)(r0 / P2P_UNIT) * ba.S[b];
+    int boff = 0;  // owned points before the current neighbour
     const int nn = ncnt[b];
     int my_f = 0;
     float my_d[3] = {0.f, 0.f, 0.f};
@@ -353,6 +463,7 @@ __device__ __forceinline__ void p2p_unit_gx2(P2PStageX2<R, HQ, HW> &sg, int lane
         const float ox = __shfl_sync(0xffffffffu, my_d[0], k);
         const float oy = __shfl_sync(0xffffffffu, my_d[1], k);
         const float oz = __shfl_sync(0xffffffffu, my_d[2], k);
+        if (SYM && f < b) continue;  // uniform in the warp
         const int fs = bstart[f], fc = bcount[f];
         const bool self = (f == b);
         for (int t0 = 0; t0 < fc; t0 += 32) {
@@ -399,9 +510,11 @@ __device__ __forceinline__ void p2p_unit_gx2(P2PStageX2<R, HQ, HW> &sg, int lane
             __syncwarp();
             const int ns = min(32, fc - t0);
             if (self) p2p_tile_x2<R, G, HQ, HW, true>(sg, ns, gi, X, Y, Z, acc);
+            else if constexpr (SYM) p2p_tile_x2_sym<G, HQ, HW>(sg, ns, gi, lane, X, Y, Z, rv, acc, back_unit + boff + t0);
             else p2p_tile_x2<R, G, HQ, HW, false>(sg, ns, gi, X, Y, Z, acc);
             __syncwarp();
         }
+        if (SYM && !self) boff += fc;
     }
 #pragma unroll
     for (int off = LG; off < 32; off <<= 1)
@@ -427,12 +540,12 @@ __device__ __forceinline__ void p2p_unit_gx2(P2PStageX2<R, HQ, HW> &sg, int lane
     }
 }
 
-template <int R, bool HQ, bool HW>
-__global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_units_x2(
+template <int R, bool HQ, bool HW, bool SYM>
+__global__ void __launch_bounds__(P2P_WARPS * 32, SYM ? (HW ? 4 : 6) : 1) k_p2p_units_x2(
     const int2 *__restrict__ units, int64_t nunits, const int32_t *__restrict__ bstart,
     const int32_t *__restrict__ bcount, const int32_t *__restrict__ nbr, const int32_t *__restrict__ ncnt,
     const int8_t *__restrict__ nd, int64_t N, const float *__restrict__ loc, const float *__restrict__ nrm,
-    const float *__restrict__ q, const float *__restrict__ w, double *__restrict__ out) {
+    const float *__restrict__ q, const float *__restrict__ w, double *__restrict__ out, BackArgs ba) {
     __shared__ P2PStageX2<R, HQ, HW> stage[P2P_WARPS];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * P2P_WARPS;
@@ -441,11 +554,61 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_units_x2(
         const int b = un.x, r0 = un.y;
         const int nr = min(P2P_UNIT, bcount[b] - r0);  // uniform in the warp
         auto &sg = stage[warp];
-        if (nr > 32) p2p_unit_gx2<R, 1, HQ, HW>(sg, lane, b, r0, nr, bstart, bcount, nbr, ncnt, nd, N, loc, nrm, q, w, out);
-        else if (nr > 16) p2p_unit_gx2<R, 2, HQ, HW>(sg, lane, b, r0, nr, bstart, bcount, nbr, ncnt, nd, N, loc, nrm, q, w, out);
-        else if (nr > 8) p2p_unit_gx2<R, 4, HQ, HW>(sg, lane, b, r0, nr, bstart, bcount, nbr, ncnt, nd, N, loc, nrm, q, w, out);
-        else p2p_unit_gx2<R, 8, HQ, HW>(sg, lane, b, r0, nr, bstart, bcount, nbr, ncnt, nd, N, loc, nrm, q, w, out);
+        if (nr > 32) p2p_unit_gx2<R, 1, HQ, HW, SYM>(sg, lane, b, r0, nr, bstart, bcount, nbr, ncnt, nd, N, loc, nrm, q, w, out, ba);
+        else if (nr > 16) p2p_unit_gx2<R, 2, HQ, HW, SYM>(sg, lane, b, r0, nr, bstart, bcount, nbr, ncnt, nd, N, loc, nrm, q, w, out, ba);
+        else if (nr > 8) p2p_unit_gx2<R, 4, HQ, HW, SYM>(sg, lane, b, r0, nr, bstart, bcount, nbr, ncnt, nd, N, loc, nrm, q, w, out, ba);
+        else p2p_unit_gx2<R, 8, HQ, HW, SYM>(sg, lane, b, r0, nr, bstart, bcount, nbr, ncnt, nd, N, loc, nrm, q, w, out, ba);
     }
+}
+
+// Symmetric near field, second pass: one warp per work unit (up to 64 points of leaf B, two per
+// lane); every point j adds the shares that the units of B's neighbours A < B wrote for it,
+// neighbour by neighbour in B's list, unit by unit, in a compensated FP32 sum (TwoSum; FP64
+// arithmetic is slow on this part). Lane k first looks up neighbour k's region; shuffles
+// broadcast it.
+constexpr int GATHER_WARPS = 8;
+__global__ void __launch_bounds__(GATHER_WARPS * 32) k_p2p_back_gather(
+    const int2 *__restrict__ units, int64_t nunits, const int32_t *__restrict__ bstart,
+    const int32_t *__restrict__ bcount, const int32_t *__restrict__ nbr, const int32_t *__restrict__ ncnt,
+    const int32_t *__restrict__ gofs, const int32_t *__restrict__ ucnt, const int32_t *__restrict__ S,
+    const int64_t *__restrict__ base, const float *__restrict__ back, double *__restrict__ out) {
+    const int64_t uw = (int64_t)blockIdx.x * GATHER_WARPS + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (uw >= nunits) return;  // uniform in the warp
+    const int2 un = units[uw];
+    const int b = un.x, r0 = un.y;
+    const int nn = ncnt[b];
+    int64_t my_off = 0;
+    int my_S = 0, my_n = 0;
+    if (lane < nn) {
+        const int g = gofs[b * 27 + lane];
+        if (g >= 0) {
+            const int a = nbr[b * 27 + lane];
+            my_off = base[a] + g;
+            my_S = S[a];
+            my_n = ucnt[a];
+        }
+    }
+    const int nr = min(P2P_UNIT, bcount[b] - r0);
+    const int j0 = r0 + lane, j1 = r0 + lane + 32;
+    const bool v0 = lane < nr, v1 = lane + 32 < nr;
+    Comp<float> a0, a1;
+    for (int k = 0; k < nn; ++k) {
+        const int nk = __shfl_sync(0xffffffffu, my_n, k);
+        if (nk == 0) continue;
+        const int64_t off = __shfl_sync(0xffffffffu, my_off, k);
+        const int sk = __shfl_sync(0xffffffffu, my_S, k);
+        const float *p = back + off;
+        for (int u = 0; u < nk; ++u) {
+            const float *pu = p + (int64_t)u * sk;
+            const float x0 = v0 ? pu[j0] : 0.f, x1 = v1 ? pu[j1] : 0.f;
+            a0.add(x0);
+            a1.add(x1);
+        }
+    }
+    const int64_t i0 = bstart[b];
+    if (v0) out[i0 + j0] += a0.get();
+    if (v1) out[i0 + j1] += a1.get();
 }
 
 // Each warp takes the units u = blockIdx.x * P2P_WARPS + warp, then every gridDim.x * P2P_WARPS
@@ -605,16 +768,30 @@ static void launch_units(Context &c, const T *q, const T *w, double *out_sorted,
     // memory: the tensor-core M2L needs it, and an SM whose resident near-field blocks had it
     // configured for more L1 would first have to drain them. (A per-device attribute, set on
     // every launch; about a microsecond.)
-    // FP32: the packed kernel; FP64: the scalar one
-    auto kern = [] {
-        if constexpr (std::is_same<T, float>::value) return k_p2p_units_x2<R, HQ, HW>;
-        else return k_p2p_units<T, R, HQ, HW>;
-    }();
-    if (c.tuned_overlap)
-        BEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                      (int)cudaSharedmemCarveoutMaxShared));
-    kern<<<(unsigned)blocks, P2P_WARPS * 32, 0, st>>>(t.p2p_units.p, nu, t.bstart.p + t.base[L], t.bcount.p + t.base[L],
-                                                       t.nbr.p, t.nbr_cnt.p, t.nbr_d.p, c.N, loc, nrm, q, w, out_sorted);
+    const int32_t *bst = t.bstart.p + t.base[L], *bcn = t.bcount.p + t.base[L];
+    if constexpr (std::is_same<T, float>::value) {
+        // FP32: the packed kernel, symmetric for one RHS (then the gather of the shares)
+        constexpr bool SYM = R == 1;
+        auto kern = k_p2p_units_x2<R, HQ, HW, SYM>;
+        if (c.tuned_overlap)
+            BEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          (int)cudaSharedmemCarveoutMaxShared));
+        const BackArgs ba{SYM ? t.back.p : nullptr, t.back_S.p, t.back_base.p};
+        kern<<<(unsigned)blocks, P2P_WARPS * 32, 0, st>>>(t.p2p_units.p, nu, bst, bcn, t.nbr.p, t.nbr_cnt.p, t.nbr_d.p,
+                                                           c.N, loc, nrm, q, w, out_sorted, ba);
+        BEM_LAUNCH_CHECK();
+        if (SYM) {
+            k_p2p_back_gather<<<(unsigned)div_up(nu, GATHER_WARPS), GATHER_WARPS * 32, 0, st>>>(
+                t.p2p_units.p, nu, bst, bcn, t.nbr.p, t.nbr_cnt.p, t.back_gofs.p, t.p2p_ucnt.p, t.back_S.p,
+                t.back_base.p, t.back.p, out_sorted);
+        }
+    } else {
+        if (c.tuned_overlap)
+            BEM_CUDA(cudaFuncSetAttribute(k_p2p_units<T, R, HQ, HW>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          (int)cudaSharedmemCarveoutMaxShared));
+        k_p2p_units<T, R, HQ, HW><<<(unsigned)blocks, P2P_WARPS * 32, 0, st>>>(
+            t.p2p_units.p, nu, bst, bcn, t.nbr.p, t.nbr_cnt.p, t.nbr_d.p, c.N, loc, nrm, q, w, out_sorted);
+    }
     BEM_LAUNCH_CHECK();
 }
 

@@ -562,6 +562,54 @@ __global__ void k_p2p_unit_emit(int nleaf, const int32_t *__restrict__ bcount, c
     for (int u = 0; u < n; ++u) units[off[b] + u] = make_int2(b, 64 * u);
 }
 
+// Symmetric near field: leaf A owns its pairs with the neighbours B > A. S_A = the floats one
+// unit of A writes (the points of its owned neighbours, in neighbour-list order); the leaf's
+// region holds its units' shares one after another, padded to 32 floats.
+__global__ void k_back_sizes(int nleaf, const int32_t *__restrict__ nbr, const int32_t *__restrict__ ncnt,
+                             const int32_t *__restrict__ bcount, const int32_t *__restrict__ ucnt,
+                             int32_t *__restrict__ S, int32_t *__restrict__ blk32) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= nleaf) return;
+    int s = 0;
+    for (int k = 0; k < ncnt[a]; ++k) {
+        const int f = nbr[a * 27 + k];
+        if (f > a) s += bcount[f];
+    }
+    S[a] = s;
+    blk32[a] = (int32_t)(((int64_t)ucnt[a] * s + 31) / 32);
+}
+
+__global__ void k_back_base(int nleaf, const int32_t *__restrict__ blkoff, int64_t *__restrict__ base) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < nleaf) base[a] = 32 * (int64_t)blkoff[a];
+}
+
+// for neighbour k = A of leaf B with A < B: where B's share starts inside each unit of A (the
+// owned neighbours of A before B in A's list, summed)
+__global__ void k_back_gofs(int nleaf, const int32_t *__restrict__ nbr, const int32_t *__restrict__ ncnt,
+                            const int32_t *__restrict__ bcount, int32_t *__restrict__ gofs) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nleaf) return;
+    for (int k = 0; k < 27; ++k) {
+        int g = -1;
+        if (k < ncnt[b]) {
+            const int a = nbr[b * 27 + k];
+            if (a < b) {
+                int off = 0;
+                for (int k2 = 0; k2 < ncnt[a]; ++k2) {
+                    const int f = nbr[a * 27 + k2];
+                    if (f == b) {
+                        g = off;
+                        break;
+                    }
+                    if (f > a) off += bcount[f];
+                }
+            }
+        }
+        gofs[b * 27 + k] = g;
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------------ build
@@ -726,6 +774,29 @@ void build_tree(Context &c) {
         t.p2p_units.resize(std::max<int64_t>(nu, 1));
         k_p2p_unit_emit<<<div_up(nleaf, tb), tb, 0, st>>>(nleaf, t.bcount.p + t.base[L], uoff.p, t.p2p_units.p);
         BEM_LAUNCH_CHECK();
+        t.p2p_ucnt.resize(nleaf);
+        BEM_CUDA(cudaMemcpyAsync(t.p2p_ucnt.p, ucnt.p, nleaf * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        // symmetric near field: per-leaf regions of the shares
+        DevBuf<int32_t> blk, blkoff;
+        blk.resize(nleaf + 1);
+        blkoff.resize(nleaf + 1);
+        t.back_S.resize(nleaf);
+        t.back_base.resize(nleaf);
+        t.back_gofs.resize((size_t)nleaf * 27);
+        k_back_sizes<<<div_up(nleaf, tb), tb, 0, st>>>(nleaf, t.nbr.p, t.nbr_cnt.p, t.bcount.p + t.base[L], ucnt.p,
+                                                        t.back_S.p, blk.p);
+        BEM_LAUNCH_CHECK();
+        exclusive_scan_i32(blk.p, blkoff.p, nleaf, utot.p, st);
+        k_back_base<<<div_up(nleaf, tb), tb, 0, st>>>(nleaf, blkoff.p, t.back_base.p);
+        BEM_LAUNCH_CHECK();
+        k_back_gofs<<<div_up(nleaf, tb), tb, 0, st>>>(nleaf, t.nbr.p, t.nbr_cnt.p, t.bcount.p + t.base[L],
+                                                       t.back_gofs.p);
+        BEM_LAUNCH_CHECK();
+        int32_t nblk = 0;
+        BEM_CUDA(cudaMemcpyAsync(&nblk, utot.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        BEM_CUDA(cudaStreamSynchronize(st));
+        t.n_back = 32 * (int64_t)nblk;
+        t.back.resize(std::max<int64_t>(t.n_back, 1));
     }
 
     // 6. M2L pairs of levels 2..L, then sorted by offset class
