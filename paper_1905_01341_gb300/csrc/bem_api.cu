@@ -249,6 +249,7 @@ void tune_tiles(Context &c) {
         build_tree(c);
         c.m2l_chunks_h.clear();
         c.tc_chunks_ok[0] = c.tc_chunks_ok[1] = false;
+        c.tm_ok = false;
         const float ms = time_product(1);
         if (L == std::max(2, L0 - 1) || ms < best_ms) {
             best = L;
@@ -267,6 +268,7 @@ void tune_tiles(Context &c) {
         build_tree(c);
         c.m2l_chunks_h.clear();
         c.tc_chunks_ok[0] = c.tc_chunks_ok[1] = false;
+        c.tm_ok = false;
         float tbest = 0.f;
         int bs = stages[0], bb = blocks[0], bo = ovls[0];
         bool first = true;
@@ -334,6 +336,7 @@ void build_all(Context &c) {
         build_operators(c, c.ops, c.prm.p_fmm);
         if (c.prm.m2l_tensor_cores && m2l_tc_supported(c.ops.P) && c.ops.tc_Npad == 0) build_tc_tables(c, c.ops);
         c.tc_chunks_ok[0] = c.tc_chunks_ok[1] = false;
+        c.tm_ok = false;
         c.tc_err.resize(1);
         BEM_CUDA(cudaMemsetAsync(c.tc_err.p, 0, sizeof(int), c.stream));
         if (c.prm.leaf_target == 0 && c.prm.fixed_level == 0 && c.tuned_level == 0) tune_tiles(c);
@@ -343,7 +346,8 @@ void build_all(Context &c) {
             build_tree(c);
         }
         c.m2l_chunks_h.clear();
-        c.tc_chunks_ok[0] = c.tc_chunks_ok[1] = false;  // chunk tables follow the tree (the autotuner built others)
+        c.tc_chunks_ok[0] = c.tc_chunks_ok[1] = false;
+        c.tm_ok = false;  // chunk tables follow the tree (the autotuner built others)
         c.stats.p2p_pairs = c.tree.p2p_pairs;
         c.stats.m2l_pairs = c.tree.n_m2l;
         c.stats.levels = c.tree.L;

@@ -1012,7 +1012,11 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
         // are formed by cancellation (Eqs. (s3), (s5)), which magnifies the far field's rounding.
         const bool tc_path = !F64 && (R == 1 ? c.prm.m2l_tensor_cores >= 1 : R == 4 && c.diag_tc) &&
                              m2l_tc_supported(P) && opr.tc_Npad > 0;
-        if (tc_path) {
+        const bool tm_path = tc_path && R == 1;  // target-major: no per-translation rows
+        if (tm_path) {
+            PhaseScope ps(c, PH_M2L, fs);
+            launch_m2l_tm(c, opr, (const float *)mp, (int64_t)t.nbox, c.tc_err.p, fs);
+        } else if (tc_path) {
             PhaseScope ps(c, PH_M2L, fs);
             const int ti = R == 1 ? 0 : 1;
             if (!c.tc_chunks_ok[ti]) {
@@ -1051,15 +1055,19 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
             launch_near(c.ev_m2l);
         }
         PhaseScope ps(c, PH_M2L_REDUCE, fs);
-        const bool trunc = opr.margin >= 0;
-        if (trunc) {
-            c.m2l_byK.resize(std::max<int64_t>(t.n_m2l, 1));
-            k_pair_K<<<div_up(t.n_m2l, 256), 256, 0, fs>>>(t.n_m2l, t.m2l_by_tgt.p, t.m2l_cls.p, opr.cls_K.p,
-                                                          c.m2l_byK.p);
-            BEM_LAUNCH_CHECK();
+        if (tm_path) {
+            launch_m2l_tm_reduce(c, opr, (float *)lc, fs);
+        } else {
+            const bool trunc = opr.margin >= 0;
+            if (trunc) {
+                c.m2l_byK.resize(std::max<int64_t>(t.n_m2l, 1));
+                k_pair_K<<<div_up(t.n_m2l, 256), 256, 0, fs>>>(t.n_m2l, t.m2l_by_tgt.p, t.m2l_cls.p, opr.cls_K.p,
+                                                              c.m2l_byK.p);
+                BEM_LAUNCH_CHECK();
+            }
+            launch_reduce_pairs<T, R>(t.base[2], t.nbox - t.base[2], t.m2l_tgt_off.p, t.m2l_by_tgt.p, ypair, P, lc,
+                                      fs, trunc ? c.m2l_byK.p : nullptr);
         }
-        launch_reduce_pairs<T, R>(t.base[2], t.nbox - t.base[2], t.m2l_tgt_off.p, t.m2l_by_tgt.p, ypair, P, lc, fs,
-                                  trunc ? c.m2l_byK.p : nullptr);
     }
     // L2L downward, levels 3 -> L: every child has exactly one parent, so it adds in place
     for (int l = 3; l <= L; ++l) {

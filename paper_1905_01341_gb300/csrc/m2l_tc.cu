@@ -34,6 +34,9 @@
 
 #include "internal.h"
 
+#include <algorithm>
+#include <vector>
+
 namespace bem {
 namespace {
 
@@ -463,5 +466,459 @@ template void launch_m2l_tc<1>(Context &, const Operators &, const XChunk *, int
                                int *, cudaStream_t);
 template void launch_m2l_tc<4>(Context &, const Operators &, const XChunk *, int64_t, const float *, int64_t, float *,
                                int *, cudaStream_t);
+
+// ------------------------------------------------------------------------------ target-major form
+//
+// Single-RHS products: instead of one output row per translation (summed per target afterwards),
+// a block accumulates, for a tile of 256 target boxes (two M = 128 tensor-memory accumulators),
+// the translations of up to TM_CLS offset classes: for class c its rows are the multipoles of
+// each target's class-c source (zero rows where a target has none), B = T_c, and the MMAs of all
+// the item's classes accumulate into the same columns (N = K_c per class), zeroed first. The
+// pipeline is the pair-major kernel's (gathered A rows by cp.async, T_c blocks by bulk copies, one
+// MMA thread, bounded waits), but it runs across the item's classes without a break. The FP32
+// accumulation runs from small terms to large: classes by truncated size ascending (the far
+// classes, whose translations are the smallest), and within a class the K steps from the highest
+// degrees down. A target's items are summed by k_tm_reduce in a fixed order with TwoSum
+// compensation, so the FP32 accumulation in tensor memory spans at most TM_CLS classes. Target
+// boxes are grouped by octant (their position in the parent), since the 189 classes a box can
+// have depend on it: a tile's classes are then about two thirds full.
+namespace {
+
+constexpr int TM_ROWS = 2 * TC_M;  // target boxes per tile
+constexpr int TM_CLS = 8;          // classes per item at most
+constexpr size_t TM_STAGE_BYTES = 3 * TM_ROWS * 16 * 2 + 3 * 256 * 16 * 2;  // A (two tiles) + B (K_c <= 256)
+
+// target boxes: the boxes of levels 2.. with at least one M2L translation, key = octant
+__global__ void k_tm_flags(int64_t first, int64_t n, const int32_t *__restrict__ tgt_off, int32_t *__restrict__ flag) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = tgt_off[first + i + 1] > tgt_off[first + i] ? 1 : 0;
+}
+__global__ void k_tm_emit(int64_t first, int64_t n, const int32_t *__restrict__ flag, const int32_t *__restrict__ ex,
+                          const uint32_t *__restrict__ bkey, uint32_t *__restrict__ key, int32_t *__restrict__ box) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n && flag[i]) {
+        key[ex[i]] = bkey[first + i] & 7u;
+        box[ex[i]] = (int32_t)(first + i);
+    }
+}
+__global__ void k_tm_rows(int64_t ntgt, int64_t nrows, const int32_t *__restrict__ sorted, int32_t *__restrict__ tm_box,
+                          int32_t *__restrict__ pos) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nrows) return;
+    const int32_t b = i < ntgt ? sorted[i] : -1;
+    tm_box[i] = b;
+    if (b >= 0) pos[b] = (int32_t)i;
+}
+// every translation (s -> t, class c) fills its (tile, class, row) slot
+__global__ void k_tm_fill(int64_t np, const int32_t *__restrict__ src, const int32_t *__restrict__ tgt,
+                          const uint32_t *__restrict__ cls, const int32_t *__restrict__ pos, int32_t *__restrict__ tab) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= np) return;
+    const int32_t r = pos[tgt[k]];
+    const int64_t tile = r / TM_ROWS, row = r % TM_ROWS;
+    tab[(tile * kNumM2LClasses + cls[k]) * TM_ROWS + row] = src[k];
+}
+// per tile, the classes present, in the order `order` (truncated size ascending)
+__global__ void __launch_bounds__(512) k_tm_classes(const int32_t *__restrict__ tab, const int32_t *__restrict__ order,
+                                                    int32_t *__restrict__ tcls, int32_t *__restrict__ ncls) {
+    __shared__ int flag[512];
+    __shared__ int warp_tot[16];
+    const int tile = blockIdx.x, k = threadIdx.x;
+    int f = 0;
+    if (k < kNumM2LClasses) {
+        const int32_t *col = tab + ((int64_t)tile * kNumM2LClasses + order[k]) * TM_ROWS;
+        for (int r = 0; r < TM_ROWS && !f; ++r) f = col[r] >= 0;
+    }
+    flag[k] = f;
+    // block prefix sum of the flags (warp scans, then the warp totals)
+    const int lane = k & 31, w = k >> 5;
+    int v = f;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) warp_tot[w] = v;
+    __syncthreads();
+    int before = 0;
+    for (int i = 0; i < w; ++i) before += warp_tot[i];
+    const int idx = before + v - f;  // exclusive
+    if (f) tcls[(int64_t)tile * kNumM2LClasses + idx] = order[k];
+    if (k == 511) ncls[tile] = before + v;
+}
+__global__ void k_tm_item_count(int64_t ntiles, const int32_t *__restrict__ ncls, int32_t *__restrict__ cnt) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < ntiles) cnt[t] = (ncls[t] + TM_CLS - 1) / TM_CLS;
+}
+__global__ void k_tm_item_emit(int64_t ntiles, const int32_t *__restrict__ ncls, const int32_t *__restrict__ off,
+                               const int32_t *__restrict__ tcls, const int32_t *__restrict__ cls_K, int Npad,
+                               int4 *__restrict__ items) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const int n = ncls[t];
+    for (int c0 = 0, i = 0; c0 < n; c0 += TM_CLS, ++i) {
+        const int nc = min(TM_CLS, n - c0);
+        const int last = tcls[t * kNumM2LClasses + c0 + nc - 1];  // the largest truncated size
+        items[off[t] + i] = make_int4((int)t, c0, nc, cls_K ? cls_K[last] : Npad);
+    }
+}
+
+__device__ __forceinline__ void two_sum_add(float &s, float &c, float v) {
+    const float t = s + v, bp = t - s;
+    c += (s - (t - bp)) + (v - bp);
+    s = t;
+}
+
+// lc[box][col] = sum over the tile's items of the partial row (fixed order, compensated)
+__global__ void k_tm_reduce(int P, int Npad, const int32_t *__restrict__ tm_box, const int32_t *__restrict__ item_off,
+                            const int4 *__restrict__ items, const float *__restrict__ part, float *__restrict__ lc) {
+    const int64_t tile = blockIdx.x;
+    const int row = blockIdx.y;
+    const int32_t box = tm_box[tile * TM_ROWS + row];
+    if (box < 0) return;
+    const int i0 = item_off[tile], i1 = item_off[tile + 1];
+    for (int col = threadIdx.x; col < P; col += blockDim.x) {
+        float s = 0.f, c = 0.f;
+        for (int i = i0; i < i1; ++i)
+            if (col < items[i].w) two_sum_add(s, c, part[((int64_t)i * TM_ROWS + row) * Npad + col]);
+        lc[(int64_t)box * P + col] = s + c;
+    }
+}
+
+template <int TC_STAGES>
+__global__ void __launch_bounds__(TC_THREADS) k_m2l_tm(int P, int Npad, const __nv_bfloat16 *__restrict__ tcB,
+                                                       const int4 *__restrict__ items, const int32_t *__restrict__ tab,
+                                                       const int32_t *__restrict__ tcls, int64_t xrows,
+                                                       const __nv_bfloat16 *__restrict__ Xs, float *__restrict__ part,
+                                                       const int32_t *__restrict__ cls_K, int *__restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    const size_t stage_bytes = TM_STAGE_BYTES;
+    const size_t epi_bytes = (size_t)TC_M * Npad * 4;
+    uint64_t *empty = reinterpret_cast<uint64_t *>(
+        smem + (TC_STAGES * stage_bytes > epi_bytes ? TC_STAGES * stage_bytes : epi_bytes));
+    uint64_t *full = empty + TC_STAGES;
+    uint64_t *bfull = full + TC_STAGES;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bfull + TC_STAGES);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    constexpr int NPROD = TC_THREADS - 32;
+    __shared__ int s_src[TM_CLS * TM_ROWS];
+    __shared__ int s_cls[TM_CLS], s_K[TM_CLS];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (*reinterpret_cast<volatile int *>(err) != 0) return;
+    const int4 it = items[blockIdx.x];
+    const int64_t tile = it.x;
+    const int nc = it.z, kmax = it.w;
+    if (tid < nc) {
+        const int cl = tcls[tile * kNumM2LClasses + it.y + tid];
+        s_cls[tid] = cl;
+        s_K[tid] = cls_K ? cls_K[cl] : Npad;
+    }
+    __syncthreads();
+    for (int e = tid; e < nc * TM_ROWS; e += TC_THREADS) {
+        const int j = e / TM_ROWS, r = e % TM_ROWS;
+        s_src[e] = tab[(tile * kNumM2LClasses + s_cls[j]) * TM_ROWS + r];
+    }
+    int nsteps = 0;
+    for (int j = 0; j < nc; ++j) nsteps += s_K[j] / TC_K;
+    if (tid == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[s])), "r"(NPROD));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bfull[s])));
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "n"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tmem_slot;
+    {
+        // zero the accumulators' first kmax columns: warp w writes its lane quarter (w % 4) of
+        // tile w / 4; every MMA then accumulates
+        const uint32_t zr = 0u;
+        const uint32_t tb = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(warp >> 2) * 256u;
+        for (int c0 = 0; c0 < kmax; c0 += 16)
+            asm volatile(
+                "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(
+                    tb + (uint32_t)c0),
+                "r"(zr)
+                : "memory");
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+    }
+    const int Kp = Npad;
+    const int64_t plane = xrows * Kp;
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t atile = TC_M * TC_K * 2, apiece = 2 * atile;
+    const uint32_t a_bytes = 3 * apiece;
+    const size_t bpiece_g = (size_t)Npad * TC_K * 2;
+    const size_t cls_stride = (size_t)(Npad / TC_K) * 3 * Npad * TC_K;  // elements of one class's table
+
+    __shared__ int s_last_ks;
+    if (warp == 0) {
+        if (lane == 0) {
+            int ks = 0;
+            bool stop = false;
+            for (int j = 0; j < nc && !stop; ++j) {
+                const int Kj = s_K[j];
+                const uint32_t idesc = make_idesc(TC_M, Kj);
+                const uint32_t bpiece = (uint32_t)Kj * TC_K * 2;
+                for (int s = 0; s < Kj / TC_K; ++s, ++ks) {  // K steps from the highest degrees down
+                    const int st = ks % TC_STAGES;
+                    const uint32_t ph = (uint32_t)((ks / TC_STAGES) & 1);
+                    if (!mbar_wait(smem_u32(&full[st]), ph) || !mbar_wait(smem_u32(&bfull[st]), ph) || *abort_flag) {
+                        *abort_flag = 1;
+                        stop = true;
+                        break;
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint32_t sa = sbase + st * (uint32_t)stage_bytes;
+                    const uint32_t sb = sa + a_bytes;
+                    for (int t = 0; t < 2; ++t) {
+                        const uint32_t d = tmem + (uint32_t)t * 256u;
+                        const uint32_t a0 = sa + t * atile;
+                        mma_bf16(d, make_desc(a0 + 2 * apiece), make_desc(sb), idesc, 1u);
+                        mma_bf16(d, make_desc(a0 + apiece), make_desc(sb + bpiece), idesc, 1u);
+                        mma_bf16(d, make_desc(a0), make_desc(sb + 2 * bpiece), idesc, 1u);
+                        mma_bf16(d, make_desc(a0 + apiece), make_desc(sb), idesc, 1u);
+                        mma_bf16(d, make_desc(a0), make_desc(sb + bpiece), idesc, 1u);
+                        mma_bf16(d, make_desc(a0), make_desc(sb), idesc, 1u);
+                    }
+                    mma_commit(smem_u32(&empty[st]));
+                }
+            }
+            s_last_ks = ks - 1;
+        }
+        __syncwarp();
+    } else {
+        const int pt = tid - 32;
+        constexpr int AU = (TM_ROWS * 2 + NPROD - 1) / NPROD;
+        uint32_t a_dst[AU];
+#pragma unroll
+        for (int i = 0; i < AU; ++i) {
+            const int u = pt + i * NPROD;
+            const int row2 = u >> 1, jh = u & 1;
+            a_dst[i] = (uint32_t)((row2 / TC_M) * atile + kmajor_off(row2 % TC_M, jh * 8) * 2);
+        }
+        const bool bulk = pt == 0;
+        int issued = -1, ks = 0;
+        bool stop = false;
+        for (int j = 0; j < nc && !stop; ++j) {
+            const int Kj = s_K[j];
+            const uint32_t bpiece = (uint32_t)Kj * TC_K * 2;
+            const __nv_bfloat16 *Bc = tcB + (size_t)s_cls[j] * cls_stride;
+            const __nv_bfloat16 *a_src[AU];
+            uint32_t a_sz[AU];
+#pragma unroll
+            for (int i = 0; i < AU; ++i) {
+                const int u = pt + i * NPROD;
+                const int sidx = u < 2 * TM_ROWS ? s_src[j * TM_ROWS + (u >> 1)] : -1;
+                a_src[i] = Xs + (size_t)(sidx >= 0 ? sidx : 0) * Kp + (u & 1) * 8;
+                a_sz[i] = sidx >= 0 ? 16u : 0u;  // a target without this class: a zero row
+            }
+            for (int s = 0; s < Kj / TC_K; ++s, ++ks) {
+                const int st = ks % TC_STAGES;
+                if (ks >= TC_STAGES &&
+                    (!mbar_wait(smem_u32(&empty[st]), (uint32_t)((ks / TC_STAGES - 1) & 1)) || *abort_flag)) {
+                    *abort_flag = 1;
+                    stop = true;
+                    break;
+                }
+                const uint32_t sa = sbase + st * (uint32_t)stage_bytes;
+                const int kstep = Kj / TC_K - 1 - s;  // highest degrees first
+                if (bulk) {
+                    const uint32_t bb = smem_u32(&bfull[st]);
+                    mbar_expect_tx(bb, 3u * bpiece);
+                    const unsigned char *bsrc =
+                        reinterpret_cast<const unsigned char *>(Bc + (size_t)kstep * 3 * Npad * TC_K);
+                    for (int piece = 0; piece < 3; ++piece)
+                        bulk_g2s(sa + a_bytes + piece * bpiece, bsrc + (size_t)piece * bpiece_g, bpiece, bb);
+                    issued = ks;
+                }
+#pragma unroll
+                for (int i = 0; i < AU; ++i) {
+                    if (pt + i * NPROD < 2 * TM_ROWS) {
+                        const __nv_bfloat16 *src = a_src[i] + kstep * TC_K;
+                        const uint32_t dst = sa + a_dst[i];
+                        cp_async16(dst, src, a_sz[i]);
+                        cp_async16(dst + apiece, src + plane, a_sz[i]);
+                        cp_async16(dst + 2 * apiece, src + 2 * plane, a_sz[i]);
+                    }
+                }
+                asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&full[st])) : "memory");
+            }
+        }
+        cp_async_wait<0>();
+        for (int k2 = issued; k2 >= 0 && k2 > issued - TC_STAGES; --k2)
+            if (!mbar_wait(smem_u32(&bfull[k2 % TC_STAGES]), (uint32_t)((k2 / TC_STAGES) & 1))) *abort_flag = 1;
+    }
+    __syncthreads();
+    const int lk = s_last_ks;
+    const bool done = lk >= 0 && mbar_wait(smem_u32(&empty[lk % TC_STAGES]), (uint32_t)((lk / TC_STAGES) & 1));
+    bool ok = !*abort_flag && lk == nsteps - 1 && done;
+    if (!ok && tid == 0) atomicOr(err, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok) {
+        // epilogue, one tile at a time, as in k_m2l_tc: TMEM -> shared memory -> coalesced rows of
+        // the item's partial (the first kmax coefficients; the rest of the row is never read)
+        float *stage = reinterpret_cast<float *>(smem);
+        float *dst_item = part + (size_t)blockIdx.x * TM_ROWS * Npad;
+        for (int t = 0; t < 2; ++t) {
+            const int q4 = warp & 3, half = warp >> 2;
+            const int ngroups = kmax / 16, g0 = half ? (ngroups + 1) / 2 : 0, g1 = half ? ngroups : (ngroups + 1) / 2;
+            float *srow = stage + (size_t)(q4 * 32 + lane) * Npad;
+            for (int c0 = g0 * 16; c0 < g1 * 16; c0 += 16) {
+                uint32_t v[16];
+                const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)t * 256u + (uint32_t)c0;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int i = 0; i < 16; i += 4)
+                    *reinterpret_cast<float4 *>(srow + c0 + i) =
+                        make_float4(__uint_as_float(v[i]), __uint_as_float(v[i + 1]), __uint_as_float(v[i + 2]),
+                                    __uint_as_float(v[i + 3]));
+            }
+            __syncthreads();
+            const int k4 = kmax / 4, n4 = Npad / 4;
+            float4 *dst = reinterpret_cast<float4 *>(dst_item + (size_t)t * TC_M * Npad);
+            const float4 *src = reinterpret_cast<const float4 *>(stage);
+            for (int e = tid; e < TC_M * k4; e += TC_THREADS) {
+                const int row = e / k4, col = e - row * k4;
+                dst[row * n4 + col] = src[row * n4 + col];
+            }
+            __syncthreads();
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(512));
+}
+
+}  // namespace
+
+static void build_tm_tables(Context &c, const Operators &o, cudaStream_t st) {
+    Tree &t = c.tree;
+    const int tb = 256;
+    const int64_t first = t.base[2], n = (int64_t)t.nbox - first;
+    if (n <= 0 || t.n_m2l == 0) {  // no translations: nothing to launch
+        c.tm_ntiles = c.tm_nitems = 0;
+        c.tm_ok = true;
+        return;
+    }
+    DevBuf<int32_t> flag, ex, tot;
+    flag.resize(std::max<int64_t>(n, 1));
+    ex.resize(std::max<int64_t>(n, 1));
+    tot.resize(1);
+    k_tm_flags<<<div_up(n, tb), tb, 0, st>>>(first, n, t.m2l_tgt_off.p, flag.p);
+    BEM_LAUNCH_CHECK();
+    exclusive_scan_i32(flag.p, ex.p, n, tot.p, st);
+    int32_t ntgt = 0;
+    BEM_CUDA(cudaMemcpyAsync(&ntgt, tot.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    BEM_CUDA(cudaStreamSynchronize(st));
+    DevBuf<uint32_t> key, ktmp;
+    DevBuf<int32_t> box, btmp, pos;
+    key.resize(std::max(ntgt, 1));
+    ktmp.resize(std::max(ntgt, 1));
+    box.resize(std::max(ntgt, 1));
+    btmp.resize(std::max(ntgt, 1));
+    pos.resize(t.nbox);
+    k_tm_emit<<<div_up(n, tb), tb, 0, st>>>(first, n, flag.p, ex.p, t.bkey.p, key.p, box.p);
+    BEM_LAUNCH_CHECK();
+    if (ntgt > 0) radix_sort_u32(key.p, box.p, ntgt, 3, ktmp.p, btmp.p, st);  // stable: box order within an octant
+    const int64_t ntiles = div_up((int64_t)ntgt, TM_ROWS);
+    c.tm_ntiles = ntiles;
+    c.tm_box.resize(std::max<int64_t>(ntiles * TM_ROWS, 1));
+    k_tm_rows<<<div_up(ntiles * TM_ROWS, tb), tb, 0, st>>>(ntgt, ntiles * TM_ROWS, box.p, c.tm_box.p, pos.p);
+    BEM_LAUNCH_CHECK();
+    const size_t ntab = (size_t)ntiles * kNumM2LClasses * TM_ROWS;
+    c.tm_src.resize(std::max<size_t>(ntab, 1));
+    BEM_CUDA(cudaMemsetAsync(c.tm_src.p, 0xff, std::max<size_t>(ntab, 1) * sizeof(int32_t), st));
+    if (t.n_m2l > 0) {
+        k_tm_fill<<<div_up(t.n_m2l, tb), tb, 0, st>>>(t.n_m2l, t.m2l_src.p, t.m2l_tgt.p, t.m2l_cls.p, pos.p, c.tm_src.p);
+        BEM_LAUNCH_CHECK();
+    }
+    // class order: truncated size ascending, ties by class index
+    const int P16 = o.tc_Npad;
+    std::vector<int32_t> order(kNumM2LClasses);
+    for (int k = 0; k < kNumM2LClasses; ++k) order[k] = k;
+    auto Kof = [&](int k) { return o.margin >= 0 ? o.cls_Kh[k] : P16; };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return Kof(a) < Kof(b); });
+    DevBuf<int32_t> dorder, ncls, icnt;
+    dorder.resize(kNumM2LClasses);
+    ncls.resize(std::max<int64_t>(ntiles, 1));
+    icnt.resize(ntiles + 1);
+    BEM_CUDA(cudaMemcpyAsync(dorder.p, order.data(), kNumM2LClasses * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    c.tm_cls.resize(std::max<int64_t>(ntiles * kNumM2LClasses, 1));
+    c.tm_item_off.resize(ntiles + 1);
+    if (ntiles > 0) {
+        k_tm_classes<<<(unsigned)ntiles, 512, 0, st>>>(c.tm_src.p, dorder.p, c.tm_cls.p, ncls.p);
+        BEM_LAUNCH_CHECK();
+        k_tm_item_count<<<div_up(ntiles, tb), tb, 0, st>>>(ntiles, ncls.p, icnt.p);
+        BEM_LAUNCH_CHECK();
+    }
+    exclusive_scan_i32(icnt.p, c.tm_item_off.p, ntiles, tot.p, st);
+    // the last entry: the total
+    BEM_CUDA(cudaMemcpyAsync(c.tm_item_off.p + ntiles, tot.p, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    int32_t nitems = 0;
+    BEM_CUDA(cudaMemcpyAsync(&nitems, tot.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    BEM_CUDA(cudaStreamSynchronize(st));
+    c.tm_nitems = nitems;
+    c.tm_items.resize(std::max(nitems, 1));
+    if (ntiles > 0) {
+        k_tm_item_emit<<<div_up(ntiles, tb), tb, 0, st>>>(ntiles, ncls.p, c.tm_item_off.p, c.tm_cls.p,
+                                                           o.margin >= 0 ? o.cls_K.p : nullptr, P16, c.tm_items.p);
+        BEM_LAUNCH_CHECK();
+    }
+    c.tm_part.resize(std::max<size_t>((size_t)nitems * TM_ROWS * P16, 1));
+    BEM_CUDA(cudaStreamSynchronize(st));  // the temporaries are freed on return
+    c.tm_ok = true;
+}
+
+void launch_m2l_tm(Context &c, const Operators &o, const float *X, int64_t xrows, int *err, cudaStream_t st) {
+    if (!c.tm_ok) build_tm_tables(c, o, st);
+    const int Npad = o.tc_Npad;
+    const size_t nxs = (size_t)3 * xrows * Npad;
+    c.xsplit.resize(nxs);
+    __nv_bfloat16 *xs = reinterpret_cast<__nv_bfloat16 *>(c.xsplit.p);
+    {
+        const int64_t plane = xrows * Npad;
+        const int nb = (int)std::min<int64_t>(div_up(plane, 256), 152 * 16);
+        k_split_x<<<nb, 256, 0, st>>>(xrows, o.P, Npad, X, xs);
+        BEM_LAUNCH_CHECK();
+    }
+    if (c.tm_nitems == 0) return;
+    const int stages = 3;
+    const size_t epi = (size_t)TC_M * Npad * 4;
+    const size_t sm = (stages * TM_STAGE_BYTES > epi ? stages * TM_STAGE_BYTES : epi) + 3 * stages * 8 + 16 + 1024;
+    BEM_CUDA(cudaFuncSetAttribute(k_m2l_tm<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_m2l_tm<3><<<(unsigned)c.tm_nitems, TC_THREADS, sm, st>>>(
+        o.P, Npad, reinterpret_cast<const __nv_bfloat16 *>(o.m2l_tc.p), c.tm_items.p, c.tm_src.p, c.tm_cls.p, xrows, xs,
+        c.tm_part.p, o.margin >= 0 ? o.cls_K.p : nullptr, err);
+    BEM_LAUNCH_CHECK();
+}
+
+void launch_m2l_tm_reduce(Context &c, const Operators &o, float *lc, cudaStream_t st) {
+    if (c.tm_nitems == 0) return;
+    dim3 grid((unsigned)c.tm_ntiles, TM_ROWS);
+    k_tm_reduce<<<grid, 128, 0, st>>>(o.P, o.tc_Npad, c.tm_box.p, c.tm_item_off.p, c.tm_items.p, c.tm_part.p, lc);
+    BEM_LAUNCH_CHECK();
+}
 
 }  // namespace bem
