@@ -311,7 +311,7 @@ void build_all(Context &c) {
     {
         // a non-finite coordinate (an uploaded NaN, or a time step that blew up) is reported as
         // such before any geometry or key is formed from it
-        DevBuf<int> badx;
+        DevBuf<int> &badx = c.chk[0];
         badx.resize(1);
         BEM_CUDA(cudaMemsetAsync(badx.p, 0, sizeof(int), c.stream));
         k_check_finite<<<div_up(3 * N, 256), 256, 0, c.stream>>>(3 * N, c.xyz.p, badx.p);
@@ -394,7 +394,7 @@ void build_all(Context &c) {
     c.ones.resize(N);
     k_fill<<<div_up(N, 256), 256, 0, c.stream>>>(N, 1.0, c.ones.p);
     BEM_LAUNCH_CHECK();
-    DevBuf<double> tmp;
+    DevBuf<double> &tmp = c.diag_tmp;
     tmp.resize(4 * N);
     double fa[4] = {0.0, -1.0, -1.0, -1.0}, ga[4] = {1.0, 1.0, 1.0, 1.0};
     const double *xl[4] = {nullptr, c.nrm.p, c.nrm.p + N, c.nrm.p + 2 * N};
@@ -425,7 +425,7 @@ void build_all(Context &c) {
     k_diag_identities<<<div_up(N, 256), 256, 0, c.stream>>>(N, o[0], o[1], o[2], o[3], c.xyz.p, c.nrm.p, c.ldiag.p,
                                                             c.mdiag.p);
     BEM_LAUNCH_CHECK();
-    DevBuf<int> bad;
+    DevBuf<int> &bad = c.chk[1];
     bad.resize(1);
     BEM_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), c.stream));
     k_check_finite<<<div_up(N, 256), 256, 0, c.stream>>>(N, c.ldiag.p, bad.p);

@@ -116,7 +116,7 @@ void build_vertex_triangle_csr(Context &c) {
 
 void compute_vertex_geometry(Context &c) {
     cudaStream_t st = c.stream;
-    DevBuf<int> bad;
+    DevBuf<int> &bad = c.chk[2];
     bad.resize(1);
     BEM_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
     c.s.resize(c.N);

@@ -154,6 +154,13 @@ struct Tree {
     DevBuf<int32_t> back_gofs;  // [nleaf][27] neighbour k = A < B of leaf B: offset of B's share in a unit of A; else -1
     DevBuf<float> back;         // [n_back]
     int64_t n_back = 0;
+    // scratch of the build, kept between builds so that a rebuild allocates (and synchronises)
+    // nothing once the sizes have settled; each slot has one use
+    DevBuf<int32_t> s_i32[22];
+    DevBuf<uint32_t> s_u32[6];
+    DevBuf<int64_t> s_i64[1];
+    DevBuf<double> s_f64[3];
+    DevBuf<unsigned long long> s_u64[1];
 };
 
 // ------------------------------------------------------------------------------ FMM operators
@@ -333,7 +340,13 @@ struct Context {
     DevBuf<int32_t> tm_item_off;     // [tiles + 1] first item of each tile
     DevBuf<int4> tm_items;           // [items] (tile, first class slot, classes, largest truncated size)
     DevBuf<float> tm_part;           // [items][256][N_pad] partial local expansions
+    DevBuf<int32_t> tm_s_i32[8];     // scratch of the table build (kept between builds)
+    DevBuf<uint32_t> tm_s_u32[2];
     DevBuf<int> tc_err;              // set by a tensor-core block whose wait ran out
+    // per-build and per-step scratch kept in the context (a cudaFree synchronises the device):
+    // flags of the finiteness and mesh checks, one per check site, and the diagonal product's output
+    DevBuf<int> chk[4];
+    DevBuf<double> diag_tmp;
     std::vector<DevBuf<XChunk> *> up_chunks;  // per level
     std::vector<std::vector<XChunk>> up_chunks_h;
     DevBuf<double> ones;

@@ -822,7 +822,7 @@ static void build_tm_tables(Context &c, const Operators &o, cudaStream_t st) {
         c.tm_ok = true;
         return;
     }
-    DevBuf<int32_t> flag, ex, tot;
+    DevBuf<int32_t> &flag = c.tm_s_i32[0], &ex = c.tm_s_i32[1], &tot = c.tm_s_i32[2];
     flag.resize(std::max<int64_t>(n, 1));
     ex.resize(std::max<int64_t>(n, 1));
     tot.resize(1);
@@ -832,8 +832,8 @@ static void build_tm_tables(Context &c, const Operators &o, cudaStream_t st) {
     int32_t ntgt = 0;
     BEM_CUDA(cudaMemcpyAsync(&ntgt, tot.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     BEM_CUDA(cudaStreamSynchronize(st));
-    DevBuf<uint32_t> key, ktmp;
-    DevBuf<int32_t> box, btmp, pos;
+    DevBuf<uint32_t> &key = c.tm_s_u32[0], &ktmp = c.tm_s_u32[1];
+    DevBuf<int32_t> &box = c.tm_s_i32[3], &btmp = c.tm_s_i32[4], &pos = c.tm_s_i32[5];
     key.resize(std::max(ntgt, 1));
     ktmp.resize(std::max(ntgt, 1));
     box.resize(std::max(ntgt, 1));
@@ -860,7 +860,8 @@ static void build_tm_tables(Context &c, const Operators &o, cudaStream_t st) {
     for (int k = 0; k < kNumM2LClasses; ++k) order[k] = k;
     auto Kof = [&](int k) { return o.margin >= 0 ? o.cls_Kh[k] : P16; };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return Kof(a) < Kof(b); });
-    DevBuf<int32_t> dorder, ncls, icnt;
+    DevBuf<int32_t> &ncls = c.tm_s_i32[6], &icnt = c.tm_s_i32[7];
+    DevBuf<int32_t> dorder;
     dorder.resize(kNumM2LClasses);
     ncls.resize(std::max<int64_t>(ntiles, 1));
     icnt.resize(ntiles + 1);
@@ -887,7 +888,7 @@ static void build_tm_tables(Context &c, const Operators &o, cudaStream_t st) {
         BEM_LAUNCH_CHECK();
     }
     c.tm_part.resize(std::max<size_t>((size_t)nitems * TM_ROWS * P16, 1));
-    BEM_CUDA(cudaStreamSynchronize(st));  // the temporaries are freed on return
+    BEM_CUDA(cudaStreamSynchronize(st));  // dorder is freed on return
     c.tm_ok = true;
 }
 

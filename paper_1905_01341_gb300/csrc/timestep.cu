@@ -560,7 +560,7 @@ void rhs(Context &c, StepState &s, const double *y, double t, double *f, bem_ste
     k_tangential<<<div_up(N, tb), tb, 0, c.stream>>>(N, c.T, s.yf.p, s.yf.p + 3 * N, c.tri.p, c.v2t_off.p, c.v2t.p,
                                                       c.s.p, c.nrm.p, s.vt.p);
     BEM_LAUNCH_CHECK();
-    DevBuf<int> bad;
+    DevBuf<int> &bad = c.chk[3];
     bad.resize(1);
     BEM_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), c.stream));
     k_curvature<<<div_up(N, tb), tb, 0, c.stream>>>(N, s.yf.p, c.nrm.p, s.nbr5.p, s.H.p, bad.p);

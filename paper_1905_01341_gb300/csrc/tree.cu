@@ -425,18 +425,14 @@ __global__ void k_neighbours(int nleaf, int L, const uint32_t *__restrict__ lkey
 }
 
 // Compact index of an M2L offset (dx,dy,dz) in [-3,3]^3 with max |d| >= 2, in lexicographic
-// order; must match the order in which the operator builder enumerates the offsets.
+// order; must match the order in which the operator builder enumerates the offsets. It is the
+// offset's position among all 343 offsets minus the near offsets (all |d| <= 1) before it.
 __device__ __forceinline__ int m2l_class(int dx, int dy, int dz) {
-    int c = 0;
-    for (int x = -3; x <= 3; ++x)
-        for (int y = -3; y <= 3; ++y)
-            for (int z = -3; z <= 3; ++z) {
-                bool near = (x >= -1 && x <= 1 && y >= -1 && y <= 1 && z >= -1 && z <= 1);
-                if (near) continue;
-                if (x == dx && y == dy && z == dz) return c;
-                ++c;
-            }
-    return -1;
+    const int full = (dx + 3) * 49 + (dy + 3) * 7 + (dz + 3);
+    auto below = [](int d) { return min(max(d + 1, 0), 3); };  // near values (-1, 0, 1) below d
+    const bool nx = dx >= -1 && dx <= 1, ny = dy >= -1 && dy <= 1;
+    const int near_before = below(dx) * 9 + (nx ? below(dy) * 3 + (ny ? below(dz) : 0) : 0);
+    return full - near_before;
 }
 
 // M2L list of a box: children of the parent's neighbours that are not its own neighbours.
@@ -461,13 +457,14 @@ __global__ void k_m2l_lists(int n, int l, const uint32_t *__restrict__ key, cons
             for (int dz = -1; dz <= 1; ++dz) {
                 int x = px + dx, y = py + dy, z = pz + dz;
                 if (x < 0 || y < 0 || z < 0 || x >= plim || y >= plim || z >= plim) continue;
-                if (find_box(pkey, np, ppre | morton(x, y, z)) < 0) continue;
-                for (int oc = 0; oc < 8; ++oc) {
+                const uint32_t pk = ppre | morton(x, y, z);
+                if (find_box(pkey, np, pk) < 0) continue;
+                // the parent's children are consecutive in key order: key = parent key * 8 + octant
+                for (int f = lower_bound_u32(key, n, pk << 3); f < n && (key[f] >> 3) == pk; ++f) {
+                    const int oc = (int)(key[f] & 7u);
                     int cx = 2 * x + ((oc >> 2) & 1), cy = 2 * y + ((oc >> 1) & 1), cz = 2 * z + (oc & 1);
                     int ddx = cx - gx, ddy = cy - gy, ddz = cz - gz;
                     if (ddx >= -1 && ddx <= 1 && ddy >= -1 && ddy <= 1 && ddz >= -1 && ddz <= 1) continue;
-                    int f = find_box(key, n, pre | morton(cx, cy, cz));
-                    if (f < 0) continue;
                     if (pass) {
                         tgt[o + c] = gbase + b;
                         src[o + c] = gbase + f;
@@ -622,12 +619,12 @@ void build_tree(Context &c) {
 
     const bool clusters = c.C > 1;
     t.deep = clusters ? kClusterDeep : kDeepLevel;
-    DevBuf<double> cube;  // per cluster: origin x, y, z, 1 / size
+    DevBuf<double> &cube = t.s_f64[0];  // per cluster: origin x, y, z, 1 / size
     cube.resize(4 * std::max<int64_t>(c.C, 1));
     std::vector<double> hcube(4 * std::max<int64_t>(c.C, 1));
     // 1. bounding cube (one per cluster)
     int nbb = std::min<int64_t>(div_up(N, tb), 1024);
-    DevBuf<double> part;
+    DevBuf<double> &part = t.s_f64[1];
     part.resize((size_t)nbb * 6);
     k_bbox<<<nbb, tb, 0, st>>>(N, c.xyz.p, part.p);
     BEM_LAUNCH_CHECK();
@@ -653,8 +650,8 @@ void build_tree(Context &c) {
     if (clusters) {
         std::vector<int64_t> cvoff(c.C + 1);
         for (int64_t k = 0; k <= c.C; ++k) cvoff[k] = c.vert_off[c.cluster_boff[k]];
-        DevBuf<int64_t> dcv;
-        DevBuf<double> cb;
+        DevBuf<int64_t> &dcv = t.s_i64[0];
+        DevBuf<double> &cb = t.s_f64[2];
         dcv.resize(c.C + 1);
         cb.resize(6 * c.C);
         BEM_CUDA(cudaMemcpyAsync(dcv.p, cvoff.data(), (c.C + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
@@ -677,8 +674,8 @@ void build_tree(Context &c) {
     // 2. Morton keys at the key depth and sort
     t.key.resize(N);
     t.perm.resize(N);
-    DevBuf<uint32_t> ktmp;
-    DevBuf<int32_t> vtmp;
+    DevBuf<uint32_t> &ktmp = t.s_u32[0];
+    DevBuf<int32_t> &vtmp = t.s_i32[0];
     ktmp.resize(N);
     vtmp.resize(N);
     if (clusters)
@@ -690,7 +687,7 @@ void build_tree(Context &c) {
     radix_sort_u32(t.key.p, t.perm.p, N, clusters ? 32 : 3 * kDeepLevel, ktmp.p, vtmp.p, st);
 
     // 3. unique boxes per level; choose l_max
-    DevBuf<int32_t> lc;
+    DevBuf<int32_t> &lc = t.s_i32[1];
     lc.resize(kDeepLevel + 1);
     BEM_CUDA(cudaMemsetAsync(lc.p, 0, (kDeepLevel + 1) * sizeof(int32_t), st));
     k_level_counts<<<div_up(N, tb), tb, 0, st>>>(N, t.deep, t.key.p, lc.p);
@@ -721,7 +718,7 @@ void build_tree(Context &c) {
     t.bcount.resize(t.nbox);
     t.parent.resize(t.nbox);
     t.leaf_of.resize(N);
-    DevBuf<int32_t> flag, ex;
+    DevBuf<int32_t> &flag = t.s_i32[2], &ex = t.s_i32[3];
     flag.resize(N);
     ex.resize(N);
     int shiftL = 3 * (t.deep - L);
@@ -753,14 +750,14 @@ void build_tree(Context &c) {
     t.nbr.resize((size_t)nleaf * 27);
     t.nbr_cnt.resize(nleaf);
     t.nbr_d.resize((size_t)nleaf * 27 * 4);
-    DevBuf<unsigned long long> pairs;
+    DevBuf<unsigned long long> &pairs = t.s_u64[0];
     pairs.resize(1);
     BEM_CUDA(cudaMemsetAsync(pairs.p, 0, sizeof(unsigned long long), st));
     k_neighbours<<<div_up(nleaf, tb), tb, 0, st>>>(nleaf, L, t.bkey.p + t.base[L], t.bcount.p + t.base[L],
                                                     t.nbr.p, t.nbr_cnt.p, t.nbr_d.p, pairs.p);
     BEM_LAUNCH_CHECK();
     {
-        DevBuf<int32_t> ucnt, uoff, utot;
+        DevBuf<int32_t> &ucnt = t.s_i32[4], &uoff = t.s_i32[5], &utot = t.s_i32[6];
         ucnt.resize(nleaf + 1);
         uoff.resize(nleaf + 1);
         utot.resize(1);
@@ -777,7 +774,7 @@ void build_tree(Context &c) {
         t.p2p_ucnt.resize(nleaf);
         BEM_CUDA(cudaMemcpyAsync(t.p2p_ucnt.p, ucnt.p, nleaf * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
         // symmetric near field: per-leaf regions of the shares
-        DevBuf<int32_t> blk, blkoff;
+        DevBuf<int32_t> &blk = t.s_i32[7], &blkoff = t.s_i32[8];
         blk.resize(nleaf + 1);
         blkoff.resize(nleaf + 1);
         t.back_S.resize(nleaf);
@@ -801,7 +798,7 @@ void build_tree(Context &c) {
 
     // 6. M2L pairs of levels 2..L, then sorted by offset class
     std::vector<int64_t> lvl_off(L + 2, 0);
-    DevBuf<int32_t> cnt, off;
+    DevBuf<int32_t> &cnt = t.s_i32[9], &off = t.s_i32[10];
     std::vector<int32_t> level_tot(L + 1, 0);
     {
         size_t maxn = 0;
@@ -809,7 +806,7 @@ void build_tree(Context &c) {
         cnt.resize(maxn + 1);
         off.resize(maxn + 1);
     }
-    DevBuf<int32_t> tot;
+    DevBuf<int32_t> &tot = t.s_i32[11];
     tot.resize(1);
     for (int l = 2; l <= L; ++l) {
         int n = t.nb[l];
@@ -828,7 +825,7 @@ void build_tree(Context &c) {
         nm2l += level_tot[l];
     }
     t.n_m2l = nm2l;
-    DevBuf<int32_t> ptgt, psrc;
+    DevBuf<int32_t> &ptgt = t.s_i32[12], &psrc = t.s_i32[13];
     DevBuf<uint32_t> &pcls = t.m2l_cls;  // sorted in place below: the class of every sorted pair
     ptgt.resize(nm2l);
     psrc.resize(nm2l);
@@ -849,12 +846,12 @@ void build_tree(Context &c) {
     t.m2l_tgt.resize(nm2l);
     t.m2l_class_off.assign(kNumM2LClasses + 1, 0);
     if (nm2l > 0) {
-        DevBuf<int32_t> order, otmp;
-        DevBuf<uint32_t> ctmp;
+        DevBuf<int32_t> &order = t.s_i32[14], &otmp = t.s_i32[15];
+        DevBuf<uint32_t> &ctmp = t.s_u32[1];
         order.resize(nm2l);
         otmp.resize(nm2l);
         ctmp.resize(nm2l);
-        DevBuf<int32_t> hist;
+        DevBuf<int32_t> &hist = t.s_i32[16];
         hist.resize(kNumM2LClasses);
         BEM_CUDA(cudaMemsetAsync(hist.p, 0, kNumM2LClasses * sizeof(int32_t), st));
         k_hist_small<<<div_up(nm2l, tb), tb, 0, st>>>(nm2l, pcls.p, kNumM2LClasses, hist.p);
@@ -884,8 +881,8 @@ void build_tree(Context &c) {
     t.up_parent.resize(nup);
     for (int l = 3; l <= L; ++l) {
         int n = t.nb[l];
-        DevBuf<uint32_t> ok, oktmp;
-        DevBuf<int32_t> id, idtmp, h8;
+        DevBuf<uint32_t> &ok = t.s_u32[2], &oktmp = t.s_u32[3];
+        DevBuf<int32_t> &id = t.s_i32[17], &idtmp = t.s_i32[18], &h8 = t.s_i32[19];
         ok.resize(n);
         oktmp.resize(n);
         id.resize(n);
@@ -910,12 +907,12 @@ void build_tree(Context &c) {
     auto target_csr = [&](const int32_t *tgt, int64_t np, DevBuf<int32_t> &off, DevBuf<int32_t> &by) {
         off.resize((size_t)t.nbox + 1);
         by.resize(np > 0 ? np : 1);
-        DevBuf<int32_t> cnt2;
+        DevBuf<int32_t> &cnt2 = t.s_i32[20];
         cnt2.resize((size_t)t.nbox + 1);
         BEM_CUDA(cudaMemsetAsync(cnt2.p, 0, ((size_t)t.nbox + 1) * sizeof(int32_t), st));
         if (np > 0) {
-            DevBuf<uint32_t> k, ktmp2;
-            DevBuf<int32_t> vtmp2;
+            DevBuf<uint32_t> &k = t.s_u32[4], &ktmp2 = t.s_u32[5];
+            DevBuf<int32_t> &vtmp2 = t.s_i32[21];
             k.resize(np);
             ktmp2.resize(np);
             vtmp2.resize(np);
