@@ -54,12 +54,13 @@ def _load_peaks() -> dict:
 PEAKS = _load_peaks()
 # Tensor-core M2L: six BF16 products per translation (three-piece split of both operands).
 M2L_TC_PRODUCTS = 6
-# DRAM traffic per unit from the ncu captures of the 300-bubble cluster (profiles/), scaled to a
-# full launch by the units it processes: the near field reads each point's data about once
-# (3.69 MB for 192,600 points), the M2L reads gathered multipoles and writes one product row per
-# translation, truncated to its class's order (39.5 MB + 80.4 MB for 241,298 translations).
-P2P_DRAM_BYTES_PER_POINT = 3.687e6 / 192600
-M2L_DRAM_BYTES_PER_TRANSLATION = (39.49e6 + 80.41e6) / 241298
+# DRAM traffic per unit from the ncu capture of the 2000-bubble cluster at depth 5 (profiles/;
+# 1,284,000 points, 2,231,186 translations: large enough that the near field's shares and the
+# M2L's partial expansions leave L2), scaled to a full launch by the units it processes. Near
+# field (symmetric kernel + gather of the shares): 25.2 + 22.5 MB and 89.5 + 0.3 MB; target-major
+# M2L: 228.7 MB read (gathered multipoles, operator blocks) + 269.4 MB written (partials).
+P2P_DRAM_BYTES_PER_POINT = (25.21e6 + 22.49e6 + 89.54e6 + 0.34e6) / 1284000
+M2L_DRAM_BYTES_PER_TRANSLATION = (228.67e6 + 269.36e6) / 2231186
 
 
 def parse():
@@ -453,14 +454,17 @@ def run_ours(args):
         t_launch = ms_i / 1e3 / n_i
         achieved = P2P_FLOPS_SL * st_iso["p2p_pairs"] / t_launch / 1e12
         peak = FP32_ALU_PEAK_TFLOPS if prec == bem.BEM_PREC_MIXED else None
-        return {"kernel": "k_p2p_units (near field, single layer)", "bound": "alu", "achieved": achieved,
+        kname = ("k_p2p_units_x2 + k_p2p_back_gather (near field, single layer, symmetric)"
+                 if prec == bem.BEM_PREC_MIXED else "k_p2p_units (near field, single layer)")
+        return {"kernel": kname, "bound": "alu", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if peak else None,
                 "traffic": P2P_DRAM_BYTES_PER_POINT * N if prec == bem.BEM_PREC_MIXED else None,
-                "traffic_source": "ncu capture of the 300-bubble cluster, bytes per point x N",
+                "traffic_source": "ncu capture of the 2000-bubble cluster, bytes per point x N (both kernels)",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (max SM clock)",
                 "launch_ms": t_launch * 1e3, "launches_timed": n_i,
                 "launch_ms_in_step": per_step.get("p2p", 0) / max(1.0, launches["p2p"]),
-                "work_per_launch": "11 flops x %d near-field pairs" % st_iso["p2p_pairs"],
+                "work_per_launch": "11 flops x %d near-field pairs (algorithmic; the symmetric kernel evaluates "
+                                   "each pair of distinct leaves once for both directions)" % st_iso["p2p_pairs"],
                 "timing": "single-layer products on the step's geometry, phases run one after another"}
 
     def m2l_roofline():
@@ -472,16 +476,16 @@ def run_ours(args):
         t_launch = ms_i / 1e3 / n_i
         achieved = M2L_TC_PRODUCTS * 2.0 * st_iso["m2l_macs"] / t_launch / 1e12
         pk = PEAKS.get("bf16_tflops_sustained")
-        return {"kernel": "k_m2l_tc (M2L)", "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
-                "frac": achieved / pk if pk else None,
+        return {"kernel": "k_m2l_tm (M2L, target-major)", "bound": "tensor", "achieved": achieved, "peak": pk,
+                "unit": "TFLOP/s", "frac": achieved / pk if pk else None,
                 "traffic": M2L_DRAM_BYTES_PER_TRANSLATION * st_iso["m2l_pairs"],
-                "traffic_source": "ncu capture of the 300-bubble cluster, bytes per translation x translations",
+                "traffic_source": "ncu capture of the 2000-bubble cluster, bytes per translation x translations",
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS, long loop)",
                 "launch_ms": t_launch * 1e3, "launches_timed": n_i,
                 "launch_ms_in_step": per_step.get("m2l", 0) / max(1.0, launches["m2l"]),
                 "work_per_launch": "6 BF16 products x 2 flops x %d multiply-adds (%d M2L translations, each "
-                                   "truncated to its class's order, sizes padded to 16)" % (st_iso["m2l_macs"],
-                                                                                            st_iso["m2l_pairs"]),
+                                   "truncated to its class's order, sizes padded to 16; the target-major tiles "
+                                   "also multiply zero rows, not counted)" % (st_iso["m2l_macs"], st_iso["m2l_pairs"]),
                 "timing": "single-layer products on the step's geometry, phases run one after another"}
 
     roof_p2p, roof_m2l = p2p_roofline(), m2l_roofline()
