@@ -123,7 +123,8 @@ typedef struct {
     int32_t gmres_maxit;    /* maximum GMRES iterations. Default 100.                          */
     int32_t gmres_restart;  /* restart length; 0 = no restart (= maxit). Default 0.            */
     double gmres_tol;       /* stop when |b - L q| / |b| <= tol (Section 3.8). Default 1e-6.  */
-    int32_t m2l_stages;     /* shared-memory pipeline stages of the tensor-core M2L: 2 or 3;
+    int32_t m2l_stages;     /* shared-memory pipeline stages of the pair-major tensor-core M2L
+                               (m2l_target_major = 0; the target-major kernel uses 3): 2 or 3;
                                0 = automatic (the tile autotuner's choice when leaf_target = 0,
                                else 3). Fewer stages leave shared memory on each SM for the
                                near field running concurrently. Default 0.                    */
@@ -146,6 +147,11 @@ typedef struct {
                                the product error within ~5 % of the untruncated one at p_fmm 14
                                (mixed) and within 2x at 16 (FP64), for about 38 % of the M2L
                                multiply work. Default 6.                                      */
+    int32_t m2l_target_major; /* layout of the tensor-core M2L (mixed precision): 1 = target-major
+                               (per tile of target boxes, the MMAs of a few offset classes
+                               accumulate in tensor memory; no row per translation); 0 =
+                               pair-major (one product row per translation, summed per target
+                               afterwards). Both sum in a fixed order. Default 1.             */
 } bem_params;
 
 /* Run-time counters of a context (cumulative since bem_create or bem_reset_stats). */

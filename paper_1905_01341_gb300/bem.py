@@ -63,6 +63,7 @@ class bem_params(ctypes.Structure):
         ("m2l_stages", ctypes.c_int32),
         ("p2p_blocks_per_sm", ctypes.c_int32),
         ("m2l_order_margin", ctypes.c_int32),
+        ("m2l_target_major", ctypes.c_int32),
     ]
 
 

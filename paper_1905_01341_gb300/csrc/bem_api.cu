@@ -174,6 +174,7 @@ void check_params(const bem_params &p) {
     if (p.m2l_stages != 0 && (p.m2l_stages < 2 || p.m2l_stages > 3)) fail(BEM_ERR_ARG, "m2l_stages must be 0, 2 or 3");
     if (p.p2p_blocks_per_sm < -1 || p.p2p_blocks_per_sm > 16) fail(BEM_ERR_ARG, "p2p_blocks_per_sm must be in -1..16");
     if (p.m2l_order_margin < -1 || p.m2l_order_margin > 20) fail(BEM_ERR_ARG, "m2l_order_margin must be in -1..20");
+    if (p.m2l_target_major != 0 && p.m2l_target_major != 1) fail(BEM_ERR_ARG, "m2l_target_major must be 0 or 1");
 }
 
 }  // namespace
@@ -249,7 +250,7 @@ void tune_tiles(Context &c) {
         build_tree(c);
         c.m2l_chunks_h.clear();
         c.tc_chunks_ok[0] = c.tc_chunks_ok[1] = false;
-        c.tm_ok = false;
+        c.tm[0].ok = c.tm[1].ok = false;
         const float ms = time_product(1);
         if (L == std::max(2, L0 - 1) || ms < best_ms) {
             best = L;
@@ -259,7 +260,9 @@ void tune_tiles(Context &c) {
     c.level_override = best;
     // 2. tiles at that depth
     std::vector<int> stages = {c.prm.m2l_stages};
-    if (c.prm.m2l_stages == 0 && c.prm.precision == BEM_PREC_MIXED && c.prm.m2l_tensor_cores) stages = {3, 2};
+    if (c.prm.m2l_stages == 0 && c.prm.precision == BEM_PREC_MIXED && c.prm.m2l_tensor_cores &&
+        !c.prm.m2l_target_major)
+        stages = {3, 2};
     std::vector<int> blocks = {c.tuned_p2p_blocks};
     if (c.prm.p2p_blocks_per_sm < 0 && c.prm.overlap) blocks = {0, 2, 4};
     std::vector<int> ovls = {c.tuned_overlap};
@@ -268,7 +271,7 @@ void tune_tiles(Context &c) {
         build_tree(c);
         c.m2l_chunks_h.clear();
         c.tc_chunks_ok[0] = c.tc_chunks_ok[1] = false;
-        c.tm_ok = false;
+        c.tm[0].ok = c.tm[1].ok = false;
         float tbest = 0.f;
         int bs = stages[0], bb = blocks[0], bo = ovls[0];
         bool first = true;
@@ -336,7 +339,7 @@ void build_all(Context &c) {
         build_operators(c, c.ops, c.prm.p_fmm);
         if (c.prm.m2l_tensor_cores && m2l_tc_supported(c.ops.P) && c.ops.tc_Npad == 0) build_tc_tables(c, c.ops);
         c.tc_chunks_ok[0] = c.tc_chunks_ok[1] = false;
-        c.tm_ok = false;
+        c.tm[0].ok = c.tm[1].ok = false;
         c.tc_err.resize(1);
         BEM_CUDA(cudaMemsetAsync(c.tc_err.p, 0, sizeof(int), c.stream));
         if (c.prm.leaf_target == 0 && c.prm.fixed_level == 0 && c.tuned_level == 0) tune_tiles(c);
@@ -347,7 +350,7 @@ void build_all(Context &c) {
         }
         c.m2l_chunks_h.clear();
         c.tc_chunks_ok[0] = c.tc_chunks_ok[1] = false;
-        c.tm_ok = false;  // chunk tables follow the tree (the autotuner built others)
+        c.tm[0].ok = c.tm[1].ok = false;  // chunk tables follow the tree (the autotuner built others)
         c.stats.p2p_pairs = c.tree.p2p_pairs;
         c.stats.m2l_pairs = c.tree.n_m2l;
         c.stats.levels = c.tree.L;
@@ -484,6 +487,7 @@ int bem_params_default(bem_params *p) {
     p->m2l_stages = 0;
     p->p2p_blocks_per_sm = -1;
     p->m2l_order_margin = 6;
+    p->m2l_target_major = 1;
     return BEM_OK;
 }
 

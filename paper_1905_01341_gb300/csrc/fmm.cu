@@ -1012,10 +1012,13 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
         // are formed by cancellation (Eqs. (s3), (s5)), which magnifies the far field's rounding.
         const bool tc_path = !F64 && (R == 1 ? c.prm.m2l_tensor_cores >= 1 : R == 4 && c.diag_tc) &&
                              m2l_tc_supported(P) && opr.tc_Npad > 0;
-        const bool tm_path = tc_path && R == 1;  // target-major: no per-translation rows
+        // target-major (no per-translation rows) for the single-RHS products; the 4-RHS diagonal
+        // product stays pair-major (its target-major form, at 64 targets per tile, was slower and
+        // less accurate)
+        const bool tm_path = tc_path && R == 1 && c.prm.m2l_target_major;
         if (tm_path) {
             PhaseScope ps(c, PH_M2L, fs);
-            launch_m2l_tm(c, opr, (const float *)mp, (int64_t)t.nbox, c.tc_err.p, fs);
+            launch_m2l_tm<1>(c, opr, (const float *)mp, (int64_t)t.nbox, c.tc_err.p, fs);
         } else if (tc_path) {
             PhaseScope ps(c, PH_M2L, fs);
             const int ti = R == 1 ? 0 : 1;
@@ -1056,7 +1059,7 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
         }
         PhaseScope ps(c, PH_M2L_REDUCE, fs);
         if (tm_path) {
-            launch_m2l_tm_reduce(c, opr, (float *)lc, fs);
+            launch_m2l_tm_reduce<1>(c, opr, (float *)lc, fs);
         } else {
             const bool trunc = opr.margin >= 0;
             if (trunc) {

@@ -329,19 +329,24 @@ struct Context {
     bool diag_tc = false;                     // the 4-RHS diagonal product uses the tensor-core M2L
     int64_t n_tc_chunks[2] = {0, 0};
     DevBuf<uint16_t> xsplit;         // multipoles split into three BF16 planes (tensor-core M2L)
-    // target-major tensor-core M2L (single-RHS products): target boxes grouped by octant into
-    // tiles of 256 rows; per tile the offset classes present, by truncated size (descending), cut
-    // into items of at most 16 classes; each item's partial local expansions, summed per target
-    bool tm_ok = false;              // built for the current tree and operators
-    int64_t tm_ntiles = 0, tm_nitems = 0;
-    DevBuf<int32_t> tm_box;          // [tiles * 256] global box index of each tile row, -1 past the end
-    DevBuf<int32_t> tm_src;          // [tiles][316][256] source box of each (tile, class, row), -1 if none
-    DevBuf<int32_t> tm_cls;          // [tiles][316] the tile's classes, truncated size descending
-    DevBuf<int32_t> tm_item_off;     // [tiles + 1] first item of each tile
-    DevBuf<int4> tm_items;           // [items] (tile, first class slot, classes, largest truncated size)
-    DevBuf<float> tm_part;           // [items][256][N_pad] partial local expansions
-    DevBuf<int32_t> tm_s_i32[8];     // scratch of the table build (kept between builds)
-    DevBuf<uint32_t> tm_s_u32[2];
+    // target-major tensor-core M2L, one state per RHS count (1: GMRES products, 4: the diagonal
+    // product): target boxes grouped by octant into tiles of 256 / R targets (256 rows of
+    // (target, rhs)); per tile the offset classes present, by truncated size (ascending), cut into
+    // items of a few classes; each item's partial local expansions, summed per target
+    struct TmState {
+        bool ok = false;                 // built for the current tree and the operators `ops`
+        const Operators *ops = nullptr;
+        int64_t ntiles = 0, nitems = 0;
+        DevBuf<int32_t> box;             // [tiles * 256 / R] global box index of each tile slot, -1 past the end
+        DevBuf<int32_t> src;             // [tiles][316][256 / R] source box of each (tile, class, slot), -1 if none
+        DevBuf<int32_t> cls;             // [tiles][316] the tile's classes, truncated size ascending
+        DevBuf<int32_t> item_off;        // [tiles + 1] first item of each tile
+        DevBuf<int4> items;              // [items] (tile, first class slot, classes, largest truncated size)
+        DevBuf<float> part;              // [items][256][N_pad] partial local expansions
+        DevBuf<int32_t> s_i32[8];        // scratch of the table build (kept between builds)
+        DevBuf<uint32_t> s_u32[2];
+    };
+    TmState tm[2];
     DevBuf<int> tc_err;              // set by a tensor-core block whose wait ran out
     // per-build and per-step scratch kept in the context (a cudaFree synchronises the device):
     // flags of the finiteness and mesh checks, one per check site, and the diagonal product's output
@@ -440,9 +445,11 @@ template <int R>
 void launch_m2l_tc(Context &c, const Operators &o, const XChunk *chunks, int64_t nchunks, const float *X, int64_t xrows, float *Ypair,
                    int *err, cudaStream_t st);
 int m2l_tc_pairs_per_chunk(int R, int Kc);
-// target-major form (one RHS): the items' partial local expansions, then (reduce) the locals
-// lc[box][P] of every M2L target = its partials summed
+// target-major form (R = 1 or 4 right-hand sides): the items' partial local expansions, then
+// (reduce) the locals lc[box][R][P] of every M2L target = its partials summed
+template <int R>
 void launch_m2l_tm(Context &c, const Operators &o, const float *X, int64_t xrows, int *err, cudaStream_t st);
+template <int R>
 void launch_m2l_tm_reduce(Context &c, const Operators &o, float *lc, cudaStream_t st);
 
 // gmres.cu, gmres_batched.cu (clusters: one GMRES per cluster, in lockstep)

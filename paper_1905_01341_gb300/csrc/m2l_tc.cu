@@ -469,23 +469,25 @@ template void launch_m2l_tc<4>(Context &, const Operators &, const XChunk *, int
 
 // ------------------------------------------------------------------------------ target-major form
 //
-// Single-RHS products: instead of one output row per translation (summed per target afterwards),
-// a block accumulates, for a tile of 256 target boxes (two M = 128 tensor-memory accumulators),
-// the translations of up to TM_CLS offset classes: for class c its rows are the multipoles of
-// each target's class-c source (zero rows where a target has none), B = T_c, and the MMAs of all
-// the item's classes accumulate into the same columns (N = K_c per class), zeroed first. The
-// pipeline is the pair-major kernel's (gathered A rows by cp.async, T_c blocks by bulk copies, one
-// MMA thread, bounded waits), but it runs across the item's classes without a break. The FP32
-// accumulation runs from small terms to large: classes by truncated size ascending (the far
-// classes, whose translations are the smallest), and within a class the K steps from the highest
-// degrees down. A target's items are summed by k_tm_reduce in a fixed order with TwoSum
-// compensation, so the FP32 accumulation in tensor memory spans at most TM_CLS classes. Target
-// boxes are grouped by octant (their position in the parent), since the 189 classes a box can
-// have depend on it: a tile's classes are then about two thirds full.
+// Instead of one output row per translation (summed per target afterwards), a block
+// accumulates, for a tile of 256 rows = 256 / R target boxes x R right-hand sides (two M = 128
+// tensor-memory accumulators), the translations of a few offset classes: for class c a row's A is
+// the multipole of its target's class-c source for its right-hand side (zero rows where a target
+// has none), B = T_c, and the MMAs of all the item's classes accumulate into the same columns
+// (N = K_c per class), zeroed first. The pipeline is the pair-major kernel's (gathered A rows by
+// cp.async, T_c blocks by bulk copies, one MMA thread, bounded waits), but it runs across the
+// item's classes without a break. The FP32 accumulation runs from small terms to large: classes
+// by truncated size ascending (the far classes, whose translations are the smallest), and within
+// a class the K steps from the highest degrees down. A target's items are summed by k_tm_reduce
+// in a fixed order with TwoSum compensation, so the FP32 accumulation in tensor memory spans at
+// most a few classes (8 for one RHS, 4 for four). Target boxes are grouped by octant (their
+// position in the parent), since the 189 classes a box can have depend on it: a tile's classes
+// are then about two thirds full. The products use it with one RHS; with four (the diagonal
+// product, 64 targets per tile) it was slower than the pair-major kernel.
 namespace {
 
-constexpr int TM_ROWS = 2 * TC_M;  // target boxes per tile
-constexpr int TM_CLS = 8;          // classes per item at most
+constexpr int TM_ROWS = 2 * TC_M;  // rows per tile: (target, rhs)
+constexpr int TM_MAXCLS = 8;       // classes per item at most
 constexpr size_t TM_STAGE_BYTES = 3 * TM_ROWS * 16 * 2 + 3 * 256 * 16 * 2;  // A (two tiles) + B (K_c <= 256)
 
 // target boxes: the boxes of levels 2.. with at least one M2L translation, key = octant
@@ -501,35 +503,34 @@ __global__ void k_tm_emit(int64_t first, int64_t n, const int32_t *__restrict__ 
         box[ex[i]] = (int32_t)(first + i);
     }
 }
-__global__ void k_tm_rows(int64_t ntgt, int64_t nrows, const int32_t *__restrict__ sorted, int32_t *__restrict__ tm_box,
-                          int32_t *__restrict__ pos) {
+__global__ void k_tm_slots(int64_t ntgt, int64_t nslots, const int32_t *__restrict__ sorted,
+                           int32_t *__restrict__ tm_box, int32_t *__restrict__ pos) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= nrows) return;
+    if (i >= nslots) return;
     const int32_t b = i < ntgt ? sorted[i] : -1;
     tm_box[i] = b;
     if (b >= 0) pos[b] = (int32_t)i;
 }
-// every translation (s -> t, class c) fills its (tile, class, row) slot
-__global__ void k_tm_fill(int64_t np, const int32_t *__restrict__ src, const int32_t *__restrict__ tgt,
+// every translation (s -> t, class c) fills its (tile, class, slot) entry; TT targets per tile
+__global__ void k_tm_fill(int64_t np, int TT, const int32_t *__restrict__ src, const int32_t *__restrict__ tgt,
                           const uint32_t *__restrict__ cls, const int32_t *__restrict__ pos, int32_t *__restrict__ tab) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= np) return;
     const int32_t r = pos[tgt[k]];
-    const int64_t tile = r / TM_ROWS, row = r % TM_ROWS;
-    tab[(tile * kNumM2LClasses + cls[k]) * TM_ROWS + row] = src[k];
+    const int64_t tile = r / TT, slot = r % TT;
+    tab[(tile * kNumM2LClasses + cls[k]) * TT + slot] = src[k];
 }
 // per tile, the classes present, in the order `order` (truncated size ascending)
-__global__ void __launch_bounds__(512) k_tm_classes(const int32_t *__restrict__ tab, const int32_t *__restrict__ order,
-                                                    int32_t *__restrict__ tcls, int32_t *__restrict__ ncls) {
-    __shared__ int flag[512];
+__global__ void __launch_bounds__(512) k_tm_classes(int TT, const int32_t *__restrict__ tab,
+                                                    const int32_t *__restrict__ order, int32_t *__restrict__ tcls,
+                                                    int32_t *__restrict__ ncls) {
     __shared__ int warp_tot[16];
     const int tile = blockIdx.x, k = threadIdx.x;
     int f = 0;
     if (k < kNumM2LClasses) {
-        const int32_t *col = tab + ((int64_t)tile * kNumM2LClasses + order[k]) * TM_ROWS;
-        for (int r = 0; r < TM_ROWS && !f; ++r) f = col[r] >= 0;
+        const int32_t *col = tab + ((int64_t)tile * kNumM2LClasses + order[k]) * TT;
+        for (int r = 0; r < TT && !f; ++r) f = col[r] >= 0;
     }
-    flag[k] = f;
     // block prefix sum of the flags (warp scans, then the warp totals)
     const int lane = k & 31, w = k >> 5;
     int v = f;
@@ -546,18 +547,18 @@ __global__ void __launch_bounds__(512) k_tm_classes(const int32_t *__restrict__ 
     if (f) tcls[(int64_t)tile * kNumM2LClasses + idx] = order[k];
     if (k == 511) ncls[tile] = before + v;
 }
-__global__ void k_tm_item_count(int64_t ntiles, const int32_t *__restrict__ ncls, int32_t *__restrict__ cnt) {
+__global__ void k_tm_item_count(int64_t ntiles, int per, const int32_t *__restrict__ ncls, int32_t *__restrict__ cnt) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t < ntiles) cnt[t] = (ncls[t] + TM_CLS - 1) / TM_CLS;
+    if (t < ntiles) cnt[t] = (ncls[t] + per - 1) / per;
 }
-__global__ void k_tm_item_emit(int64_t ntiles, const int32_t *__restrict__ ncls, const int32_t *__restrict__ off,
-                               const int32_t *__restrict__ tcls, const int32_t *__restrict__ cls_K, int Npad,
-                               int4 *__restrict__ items) {
+__global__ void k_tm_item_emit(int64_t ntiles, int per, const int32_t *__restrict__ ncls,
+                               const int32_t *__restrict__ off, const int32_t *__restrict__ tcls,
+                               const int32_t *__restrict__ cls_K, int Npad, int4 *__restrict__ items) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= ntiles) return;
     const int n = ncls[t];
-    for (int c0 = 0, i = 0; c0 < n; c0 += TM_CLS, ++i) {
-        const int nc = min(TM_CLS, n - c0);
+    for (int c0 = 0, i = 0; c0 < n; c0 += per, ++i) {
+        const int nc = min(per, n - c0);
         const int last = tcls[t * kNumM2LClasses + c0 + nc - 1];  // the largest truncated size
         items[off[t] + i] = make_int4((int)t, c0, nc, cls_K ? cls_K[last] : Npad);
     }
@@ -569,28 +570,32 @@ __device__ __forceinline__ void two_sum_add(float &s, float &c, float v) {
     s = t;
 }
 
-// lc[box][col] = sum over the tile's items of the partial row (fixed order, compensated)
+// lc[box][rhs][col] = sum over the tile's items of the partial row (fixed order, compensated)
+template <int R>
 __global__ void k_tm_reduce(int P, int Npad, const int32_t *__restrict__ tm_box, const int32_t *__restrict__ item_off,
                             const int4 *__restrict__ items, const float *__restrict__ part, float *__restrict__ lc) {
+    constexpr int TT = TM_ROWS / R;
     const int64_t tile = blockIdx.x;
     const int row = blockIdx.y;
-    const int32_t box = tm_box[tile * TM_ROWS + row];
+    const int32_t box = tm_box[tile * TT + row / R];
     if (box < 0) return;
     const int i0 = item_off[tile], i1 = item_off[tile + 1];
+    float *dst = lc + ((int64_t)box * R + row % R) * P;
     for (int col = threadIdx.x; col < P; col += blockDim.x) {
         float s = 0.f, c = 0.f;
         for (int i = i0; i < i1; ++i)
             if (col < items[i].w) two_sum_add(s, c, part[((int64_t)i * TM_ROWS + row) * Npad + col]);
-        lc[(int64_t)box * P + col] = s + c;
+        dst[col] = s + c;
     }
 }
 
-template <int TC_STAGES>
+template <int R, int TC_STAGES>
 __global__ void __launch_bounds__(TC_THREADS) k_m2l_tm(int P, int Npad, const __nv_bfloat16 *__restrict__ tcB,
                                                        const int4 *__restrict__ items, const int32_t *__restrict__ tab,
                                                        const int32_t *__restrict__ tcls, int64_t xrows,
                                                        const __nv_bfloat16 *__restrict__ Xs, float *__restrict__ part,
                                                        const int32_t *__restrict__ cls_K, int *__restrict__ err) {
+    constexpr int TT = TM_ROWS / R;  // target slots per tile
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const size_t stage_bytes = TM_STAGE_BYTES;
@@ -602,8 +607,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tm(int P, int Npad, const __
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bfull + TC_STAGES);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     constexpr int NPROD = TC_THREADS - 32;
-    __shared__ int s_src[TM_CLS * TM_ROWS];
-    __shared__ int s_cls[TM_CLS], s_K[TM_CLS];
+    __shared__ int s_src[TM_MAXCLS * TT];
+    __shared__ int s_cls[TM_MAXCLS], s_K[TM_MAXCLS];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (*reinterpret_cast<volatile int *>(err) != 0) return;
@@ -616,9 +621,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tm(int P, int Npad, const __
         s_K[tid] = cls_K ? cls_K[cl] : Npad;
     }
     __syncthreads();
-    for (int e = tid; e < nc * TM_ROWS; e += TC_THREADS) {
-        const int j = e / TM_ROWS, r = e % TM_ROWS;
-        s_src[e] = tab[(tile * kNumM2LClasses + s_cls[j]) * TM_ROWS + r];
+    for (int e = tid; e < nc * TT; e += TC_THREADS) {
+        const int j = e / TT, r = e % TT;
+        s_src[e] = tab[(tile * kNumM2LClasses + s_cls[j]) * TT + r];
     }
     int nsteps = 0;
     for (int j = 0; j < nc; ++j) nsteps += s_K[j] / TC_K;
@@ -723,8 +728,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tm(int P, int Npad, const __
 #pragma unroll
             for (int i = 0; i < AU; ++i) {
                 const int u = pt + i * NPROD;
-                const int sidx = u < 2 * TM_ROWS ? s_src[j * TM_ROWS + (u >> 1)] : -1;
-                a_src[i] = Xs + (size_t)(sidx >= 0 ? sidx : 0) * Kp + (u & 1) * 8;
+                const int row2 = u >> 1;  // (target slot, rhs) = (row2 / R, row2 % R)
+                const int sidx = u < 2 * TM_ROWS ? s_src[j * TT + row2 / R] : -1;
+                a_src[i] = Xs + ((size_t)(sidx >= 0 ? sidx : 0) * R + row2 % R) * Kp + (u & 1) * 8;
                 a_sz[i] = sidx >= 0 ? 16u : 0u;  // a target without this class: a zero row
             }
             for (int s = 0; s < Kj / TC_K; ++s, ++ks) {
@@ -813,16 +819,23 @@ __global__ void __launch_bounds__(TC_THREADS) k_m2l_tm(int P, int Npad, const __
 
 }  // namespace
 
+// classes per item: 8 for one RHS; 4 for four (the diagonal product's identities cancel O(1)
+// sums down to O(h), which magnifies the rounding of the FP32 accumulation)
+template <int R>
 static void build_tm_tables(Context &c, const Operators &o, cudaStream_t st) {
+    Context::TmState &S = c.tm[R == 1 ? 0 : 1];
+    constexpr int TT = TM_ROWS / R;
+    const int per = R == 1 ? 8 : 4;
     Tree &t = c.tree;
     const int tb = 256;
     const int64_t first = t.base[2], n = (int64_t)t.nbox - first;
     if (n <= 0 || t.n_m2l == 0) {  // no translations: nothing to launch
-        c.tm_ntiles = c.tm_nitems = 0;
-        c.tm_ok = true;
+        S.ntiles = S.nitems = 0;
+        S.ok = true;
+        S.ops = &o;
         return;
     }
-    DevBuf<int32_t> &flag = c.tm_s_i32[0], &ex = c.tm_s_i32[1], &tot = c.tm_s_i32[2];
+    DevBuf<int32_t> &flag = S.s_i32[0], &ex = S.s_i32[1], &tot = S.s_i32[2];
     flag.resize(std::max<int64_t>(n, 1));
     ex.resize(std::max<int64_t>(n, 1));
     tot.resize(1);
@@ -832,8 +845,8 @@ static void build_tm_tables(Context &c, const Operators &o, cudaStream_t st) {
     int32_t ntgt = 0;
     BEM_CUDA(cudaMemcpyAsync(&ntgt, tot.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     BEM_CUDA(cudaStreamSynchronize(st));
-    DevBuf<uint32_t> &key = c.tm_s_u32[0], &ktmp = c.tm_s_u32[1];
-    DevBuf<int32_t> &box = c.tm_s_i32[3], &btmp = c.tm_s_i32[4], &pos = c.tm_s_i32[5];
+    DevBuf<uint32_t> &key = S.s_u32[0], &ktmp = S.s_u32[1];
+    DevBuf<int32_t> &box = S.s_i32[3], &btmp = S.s_i32[4], &pos = S.s_i32[5];
     key.resize(std::max(ntgt, 1));
     ktmp.resize(std::max(ntgt, 1));
     box.resize(std::max(ntgt, 1));
@@ -842,58 +855,54 @@ static void build_tm_tables(Context &c, const Operators &o, cudaStream_t st) {
     k_tm_emit<<<div_up(n, tb), tb, 0, st>>>(first, n, flag.p, ex.p, t.bkey.p, key.p, box.p);
     BEM_LAUNCH_CHECK();
     if (ntgt > 0) radix_sort_u32(key.p, box.p, ntgt, 3, ktmp.p, btmp.p, st);  // stable: box order within an octant
-    const int64_t ntiles = div_up((int64_t)ntgt, TM_ROWS);
-    c.tm_ntiles = ntiles;
-    c.tm_box.resize(std::max<int64_t>(ntiles * TM_ROWS, 1));
-    k_tm_rows<<<div_up(ntiles * TM_ROWS, tb), tb, 0, st>>>(ntgt, ntiles * TM_ROWS, box.p, c.tm_box.p, pos.p);
+    const int64_t ntiles = div_up((int64_t)ntgt, TT);
+    S.ntiles = ntiles;
+    S.box.resize(std::max<int64_t>(ntiles * TT, 1));
+    k_tm_slots<<<div_up(ntiles * TT, tb), tb, 0, st>>>(ntgt, ntiles * TT, box.p, S.box.p, pos.p);
     BEM_LAUNCH_CHECK();
-    const size_t ntab = (size_t)ntiles * kNumM2LClasses * TM_ROWS;
-    c.tm_src.resize(std::max<size_t>(ntab, 1));
-    BEM_CUDA(cudaMemsetAsync(c.tm_src.p, 0xff, std::max<size_t>(ntab, 1) * sizeof(int32_t), st));
-    if (t.n_m2l > 0) {
-        k_tm_fill<<<div_up(t.n_m2l, tb), tb, 0, st>>>(t.n_m2l, t.m2l_src.p, t.m2l_tgt.p, t.m2l_cls.p, pos.p, c.tm_src.p);
-        BEM_LAUNCH_CHECK();
-    }
+    const size_t ntab = (size_t)ntiles * kNumM2LClasses * TT;
+    S.src.resize(std::max<size_t>(ntab, 1));
+    BEM_CUDA(cudaMemsetAsync(S.src.p, 0xff, std::max<size_t>(ntab, 1) * sizeof(int32_t), st));
+    k_tm_fill<<<div_up(t.n_m2l, tb), tb, 0, st>>>(t.n_m2l, TT, t.m2l_src.p, t.m2l_tgt.p, t.m2l_cls.p, pos.p, S.src.p);
+    BEM_LAUNCH_CHECK();
     // class order: truncated size ascending, ties by class index
     const int P16 = o.tc_Npad;
     std::vector<int32_t> order(kNumM2LClasses);
     for (int k = 0; k < kNumM2LClasses; ++k) order[k] = k;
     auto Kof = [&](int k) { return o.margin >= 0 ? o.cls_Kh[k] : P16; };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return Kof(a) < Kof(b); });
-    DevBuf<int32_t> &ncls = c.tm_s_i32[6], &icnt = c.tm_s_i32[7];
+    DevBuf<int32_t> &ncls = S.s_i32[6], &icnt = S.s_i32[7];
     DevBuf<int32_t> dorder;
     dorder.resize(kNumM2LClasses);
     ncls.resize(std::max<int64_t>(ntiles, 1));
     icnt.resize(ntiles + 1);
     BEM_CUDA(cudaMemcpyAsync(dorder.p, order.data(), kNumM2LClasses * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    c.tm_cls.resize(std::max<int64_t>(ntiles * kNumM2LClasses, 1));
-    c.tm_item_off.resize(ntiles + 1);
-    if (ntiles > 0) {
-        k_tm_classes<<<(unsigned)ntiles, 512, 0, st>>>(c.tm_src.p, dorder.p, c.tm_cls.p, ncls.p);
-        BEM_LAUNCH_CHECK();
-        k_tm_item_count<<<div_up(ntiles, tb), tb, 0, st>>>(ntiles, ncls.p, icnt.p);
-        BEM_LAUNCH_CHECK();
-    }
-    exclusive_scan_i32(icnt.p, c.tm_item_off.p, ntiles, tot.p, st);
-    // the last entry: the total
-    BEM_CUDA(cudaMemcpyAsync(c.tm_item_off.p + ntiles, tot.p, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    S.cls.resize(std::max<int64_t>(ntiles * kNumM2LClasses, 1));
+    S.item_off.resize(ntiles + 1);
+    k_tm_classes<<<(unsigned)ntiles, 512, 0, st>>>(TT, S.src.p, dorder.p, S.cls.p, ncls.p);
+    BEM_LAUNCH_CHECK();
+    k_tm_item_count<<<div_up(ntiles, tb), tb, 0, st>>>(ntiles, per, ncls.p, icnt.p);
+    BEM_LAUNCH_CHECK();
+    exclusive_scan_i32(icnt.p, S.item_off.p, ntiles, tot.p, st);
+    BEM_CUDA(cudaMemcpyAsync(S.item_off.p + ntiles, tot.p, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
     int32_t nitems = 0;
     BEM_CUDA(cudaMemcpyAsync(&nitems, tot.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     BEM_CUDA(cudaStreamSynchronize(st));
-    c.tm_nitems = nitems;
-    c.tm_items.resize(std::max(nitems, 1));
-    if (ntiles > 0) {
-        k_tm_item_emit<<<div_up(ntiles, tb), tb, 0, st>>>(ntiles, ncls.p, c.tm_item_off.p, c.tm_cls.p,
-                                                           o.margin >= 0 ? o.cls_K.p : nullptr, P16, c.tm_items.p);
-        BEM_LAUNCH_CHECK();
-    }
-    c.tm_part.resize(std::max<size_t>((size_t)nitems * TM_ROWS * P16, 1));
+    S.nitems = nitems;
+    S.items.resize(std::max(nitems, 1));
+    k_tm_item_emit<<<div_up(ntiles, tb), tb, 0, st>>>(ntiles, per, ncls.p, S.item_off.p, S.cls.p,
+                                                       o.margin >= 0 ? o.cls_K.p : nullptr, P16, S.items.p);
+    BEM_LAUNCH_CHECK();
+    S.part.resize(std::max<size_t>((size_t)nitems * TM_ROWS * P16, 1));
     BEM_CUDA(cudaStreamSynchronize(st));  // dorder is freed on return
-    c.tm_ok = true;
+    S.ok = true;
+    S.ops = &o;
 }
 
+template <int R>
 void launch_m2l_tm(Context &c, const Operators &o, const float *X, int64_t xrows, int *err, cudaStream_t st) {
-    if (!c.tm_ok) build_tm_tables(c, o, st);
+    Context::TmState &S = c.tm[R == 1 ? 0 : 1];
+    if (!S.ok || S.ops != &o) build_tm_tables<R>(c, o, st);
     const int Npad = o.tc_Npad;
     const size_t nxs = (size_t)3 * xrows * Npad;
     c.xsplit.resize(nxs);
@@ -904,22 +913,27 @@ void launch_m2l_tm(Context &c, const Operators &o, const float *X, int64_t xrows
         k_split_x<<<nb, 256, 0, st>>>(xrows, o.P, Npad, X, xs);
         BEM_LAUNCH_CHECK();
     }
-    if (c.tm_nitems == 0) return;
+    if (S.nitems == 0) return;
     const int stages = 3;
     const size_t epi = (size_t)TC_M * Npad * 4;
     const size_t sm = (stages * TM_STAGE_BYTES > epi ? stages * TM_STAGE_BYTES : epi) + 3 * stages * 8 + 16 + 1024;
-    BEM_CUDA(cudaFuncSetAttribute(k_m2l_tm<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_m2l_tm<3><<<(unsigned)c.tm_nitems, TC_THREADS, sm, st>>>(
-        o.P, Npad, reinterpret_cast<const __nv_bfloat16 *>(o.m2l_tc.p), c.tm_items.p, c.tm_src.p, c.tm_cls.p, xrows, xs,
-        c.tm_part.p, o.margin >= 0 ? o.cls_K.p : nullptr, err);
+    BEM_CUDA(cudaFuncSetAttribute(k_m2l_tm<R, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_m2l_tm<R, 3><<<(unsigned)S.nitems, TC_THREADS, sm, st>>>(
+        o.P, Npad, reinterpret_cast<const __nv_bfloat16 *>(o.m2l_tc.p), S.items.p, S.src.p, S.cls.p, xrows, xs, S.part.p,
+        o.margin >= 0 ? o.cls_K.p : nullptr, err);
     BEM_LAUNCH_CHECK();
 }
 
+template <int R>
 void launch_m2l_tm_reduce(Context &c, const Operators &o, float *lc, cudaStream_t st) {
-    if (c.tm_nitems == 0) return;
-    dim3 grid((unsigned)c.tm_ntiles, TM_ROWS);
-    k_tm_reduce<<<grid, 128, 0, st>>>(o.P, o.tc_Npad, c.tm_box.p, c.tm_item_off.p, c.tm_items.p, c.tm_part.p, lc);
+    Context::TmState &S = c.tm[R == 1 ? 0 : 1];
+    if (S.nitems == 0) return;
+    dim3 grid((unsigned)S.ntiles, TM_ROWS);
+    k_tm_reduce<R><<<grid, 128, 0, st>>>(o.P, o.tc_Npad, S.box.p, S.item_off.p, S.items.p, S.part.p, lc);
     BEM_LAUNCH_CHECK();
 }
+
+template void launch_m2l_tm<1>(Context &, const Operators &, const float *, int64_t, int *, cudaStream_t);
+template void launch_m2l_tm_reduce<1>(Context &, const Operators &, float *, cudaStream_t);
 
 }  // namespace bem

@@ -96,6 +96,7 @@ def test_struct_defaults():
     assert bem.bem_params_default().gmres_precond == 0
     assert bem.bem_params_default().overlap == -1 and bem.bem_params_default().diag_p_fmm == -1
     assert bem.bem_params_default().m2l_stages == 0 and bem.bem_params_default().p2p_blocks_per_sm == -1
+    assert bem.bem_params_default().m2l_target_major == 1
     sp = bem.bem_step_params_default()
     assert sp.pf == 6 and sp.courant == 0.1 and sp.kappa == 1.4 and sp.guess == 2
     assert [bem.bem_phase_name(i) for i in range(bem.BEM_NUM_PHASES)][6] == "m2l"

@@ -257,28 +257,51 @@ def test_residual_history_and_mvp_count():
 
 @pytest.mark.parametrize("p", [8, 14, 16])
 def test_tensor_core_m2l_matches_cuda_core_m2l(p):
-    """The tcgen05 M2L (three-piece BF16 split of both operands, FP32 accumulation) against the FP32 CUDA-core
-    M2L: measured against the FP64 FMM at the same p (same truncation, so only arithmetic
-    error is left), the tensor-core product is as accurate as the CUDA-core one, and both stay
-    within the mixed-precision bound of the oracle."""
+    """The tcgen05 M2L (three-piece BF16 split of both operands, FP32 accumulation), in both
+    layouts (target-major: several classes accumulated per tile in tensor memory; pair-major:
+    one row per translation), against the FP32 CUDA-core M2L: measured against the FP64 FMM at
+    the same p (same truncation, so only arithmetic error is left), the tensor-core products are
+    as accurate as the CUDA-core one, and stay within the mixed-precision bound of the oracle."""
     bem = _bem()
     mesh = small_cluster(20, 3, seed=11)
     rng = np.random.Generator(np.random.PCG64(12))
     xL, xM = rng.standard_normal(mesh.n), rng.standard_normal(mesh.n)
     outs = {}
-    for key, prec, tc in (("tc", 1, 1), ("cc", 1, 0), ("f64", 0, 0)):
+    for key, prec, tc, tm in (("tc", 1, 1, 1), ("tc_pm", 1, 1, 0), ("cc", 1, 0, 1), ("f64", 0, 0, 1)):
         ctx = make_ctx(mesh, mvp=bem.BEM_MVP_FMM, precision=prec, p_fmm=p, leaf_target=32, m2l_tensor_cores=tc,
-                       diag_precision=0)
+                       diag_precision=0, m2l_target_major=tm)
         o = torch.zeros(mesh.n, dtype=torch.float64, device="cuda")
         ctx.apply(0.7, dev(xL), -1.3, dev(xM), o)
         outs[key] = o.cpu().numpy()
         ctx.close()
-    e_tc, e_cc = rel(outs["tc"], outs["f64"]), rel(outs["cc"], outs["f64"])
-    print("p=%d arithmetic error vs FP64 FMM: tensor cores %.2e, CUDA cores %.2e" % (p, e_tc, e_cc))
-    assert e_tc < 2.0 * e_cc + 1e-7
+    e_tc, e_pm, e_cc = (rel(outs[k], outs["f64"]) for k in ("tc", "tc_pm", "cc"))
+    print("p=%d arithmetic error vs FP64 FMM: tensor cores %.2e (pair-major %.2e), CUDA cores %.2e"
+          % (p, e_tc, e_pm, e_cc))
+    assert e_tc < 2.0 * e_cc + 1e-7 and e_pm < 2.0 * e_cc + 1e-7
     if p >= 14:
         ref = oracle.BemOperator(mesh.xyz, mesh.tri).apply(0.7, xL, -1.3, xM)
-        assert rel(outs["tc"], ref) < 1e-5
+        assert rel(outs["tc"], ref) < 1e-5 and rel(outs["tc_pm"], ref) < 1e-5
+
+
+def test_tensor_core_diagonals_match_oracle():
+    """The singular diagonals (Eqs. s3, s5) from the 4-RHS product with its M2L on the tensor
+    cores (m2l_tensor_cores = 2) against the oracle's and against the same product on the CUDA
+    cores: the identities cancel O(1) sums down to O(h), so they show the M2L's rounding
+    magnified."""
+    bem = _bem()
+    mesh = small_cluster(20, 3, seed=11)
+    ref = oracle.BemOperator(mesh.xyz, mesh.tri)
+    errs = {}
+    for tc in (2, 0):
+        ctx = make_ctx(mesh, mvp=bem.BEM_MVP_FMM, precision=1, p_fmm=14, leaf_target=32, m2l_tensor_cores=tc)
+        s, n, ld, md = np.zeros(mesh.n), np.zeros(3 * mesh.n), np.zeros(mesh.n), np.zeros(mesh.n)
+        bem.bem_get_geometry(ctx.ctx, s, n, ld, md)
+        errs[tc] = (rel(ld, ref.ldiag), rel(md, ref.mdiag))
+        ctx.close()
+    print("diagonals vs oracle (L, M): tensor cores %.2e %.2e, CUDA cores %.2e %.2e" % (errs[2] + errs[0]))
+    for tc in (2, 0):
+        assert errs[tc][0] < 1e-4 and errs[tc][1] < 1e-4
+    assert errs[2][0] < 2.0 * errs[0][0] + 1e-6 and errs[2][1] < 2.0 * errs[0][1] + 1e-6
 
 
 def test_mixed_tensor_core_solve_converges_below_1e6():
