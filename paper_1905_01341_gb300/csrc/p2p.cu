@@ -8,11 +8,14 @@
 // exact in FP32), the direct kernel splits coordinates into hi + lo FP32 pairs. Sums are
 // formed per shared-memory tile in FP32 and merged with TwoSum compensation.
 //
-// The kernel of Eq. (ns1) is symmetric in r = |r_i - r_j|, so the FP32 single-RHS products
-// evaluate every pair of neighbour leaves A < B once, by A's units: one reciprocal square root
-// feeds both q_j / r into r_i and q_i / r (and the double layer's exchanged dipole term) into
+// The single-layer kernel of Eq. (ns1) is symmetric in r = |r_i - r_j|, so the FP32 single-RHS,
+// single-layer products (every GMRES product) evaluate every pair of neighbour leaves A < B
+// once, by A's units: one reciprocal square root feeds both q_j / r into r_i and q_i / r into
 // r_j. B's shares are summed over A's receivers inside the warp, stored per (unit of A, B), and
 // added to B's points by a second kernel in a fixed order: no atomics, deterministic results.
+// Products with the double layer run one way: its exchanged dipole term (n_i instead of n_j)
+// costs more arithmetic and registers than the shared square root saves (measured: 5.96 ms
+// symmetric against 5.37 ms one way at the benchmark's size).
 #include "internal.h"
 
 #include <algorithm>
@@ -262,14 +265,14 @@ __device__ __forceinline__ float2 rsqrt_x2(float2 r2) {
     return ri;
 }
 
-// The receivers' own data for the symmetric form (broadcast pairs, zero for lanes past the
-// unit's end): strength q_i, and for the double layer n_i and -w_i.
+// The receivers' own strengths for the symmetric form (broadcast pairs, zero for lanes past the
+// unit's end).
 struct RecvX2 {
-    float2 q[2], nx[2], ny[2], nz[2], wneg[2];
+    float2 q[2];
 };
 
-// BACK: also accumulate the pair's share for the two sources, sum over this lane's receivers of
-// q_i / r - w_i n_i.(r_i - r_j) / r^3 (the kernel with source and receiver exchanged)
+// BACK (single layer): also accumulate the pair's share for the two sources, the sum over this
+// lane's receivers of q_i / r
 template <int R, bool HQ, bool HW, bool SELF, bool BACK = false>
 __device__ __forceinline__ void p2p_source_x2(const P2PStageX2<R, HQ, HW> &sg, int p, const float2 *X,
                                               const float2 *Y, const float2 *Z, float2 (*part)[R],
@@ -299,18 +302,11 @@ __device__ __forceinline__ void p2p_source_x2(const P2PStageX2<R, HQ, HW> &sg, i
             float2 nd = __fmul2_rn(make_float2(C.x, C.y), dx);
             nd = __ffma2_rn(make_float2(C.z, C.w), dy, nd);
             nd = __ffma2_rn(make_float2(D.x, D.y), dz, nd);
-            const float2 ri3 = __fmul2_rn(__fmul2_rn(ri, ri), ri);
-            const float2 nd3 = __fmul2_rn(nd, ri3);
+            const float2 nd3 = __fmul2_rn(nd, __fmul2_rn(__fmul2_rn(ri, ri), ri));
             part[k][0] = __ffma2_rn(make_float2(D.z, D.w), nd3, part[k][0]);
 #pragma unroll
             for (int r = 1; r < R; ++r)
                 part[k][r] = __ffma2_rn(*reinterpret_cast<const float2 *>(&sg.w[r - 1][2 * p]), nd3, part[k][r]);
-            if (BACK) {
-                float2 ni = __fmul2_rn(rv->nx[k], dx);
-                ni = __ffma2_rn(rv->ny[k], dy, ni);
-                ni = __ffma2_rn(rv->nz[k], dz, ni);
-                *bk = __ffma2_rn(rv->wneg[k], __fmul2_rn(ni, ri3), *bk);
-            }
         }
     }
 }
@@ -434,16 +430,8 @@ __device__ __forceinline__ void p2p_unit_gx2(P2PStageX2<R, HQ, HW> &sg, int lane
         Y[k] = make_float2(y, y);
         Z[k] = make_float2(z, z);
         if (SYM) {
-            const float qi = (HQ && valid) ? q[i] : 0.f;
+            const float qi = valid ? q[i] : 0.f;
             rv.q[k] = make_float2(qi, qi);
-            if (HW) {
-                const float wi = valid ? -w[i] : 0.f;
-                const float a = nrm[i], bb = nrm[N + i], cc = nrm[2 * N + i];
-                rv.nx[k] = make_float2(a, a);
-                rv.ny[k] = make_float2(bb, bb);
-                rv.nz[k] = make_float2(cc, cc);
-                rv.wneg[k] = make_float2(wi, wi);
-            }
         }
     }
     float *back_unit = nullptr;
@@ -541,11 +529,12 @@ __device__ __forceinline__ void p2p_unit_gx2(P2PStageX2<R, HQ, HW> &sg, int lane
 }
 
 template <int R, bool HQ, bool HW, bool SYM>
-__global__ void __launch_bounds__(P2P_WARPS * 32, SYM ? (HW ? 4 : 6) : 1) k_p2p_units_x2(
+__global__ void __launch_bounds__(P2P_WARPS * 32, SYM ? 6 : (R == 1 ? 5 : 1)) k_p2p_units_x2(
     const int2 *__restrict__ units, int64_t nunits, const int32_t *__restrict__ bstart,
     const int32_t *__restrict__ bcount, const int32_t *__restrict__ nbr, const int32_t *__restrict__ ncnt,
     const int8_t *__restrict__ nd, int64_t N, const float *__restrict__ loc, const float *__restrict__ nrm,
     const float *__restrict__ q, const float *__restrict__ w, double *__restrict__ out, BackArgs ba) {
+    static_assert(!SYM || (R == 1 && !HW), "the symmetric form is single-RHS, single-layer");
     __shared__ P2PStageX2<R, HQ, HW> stage[P2P_WARPS];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * P2P_WARPS;
@@ -771,7 +760,7 @@ static void launch_units(Context &c, const T *q, const T *w, double *out_sorted,
     const int32_t *bst = t.bstart.p + t.base[L], *bcn = t.bcount.p + t.base[L];
     if constexpr (std::is_same<T, float>::value) {
         // FP32: the packed kernel, symmetric for one RHS (then the gather of the shares)
-        constexpr bool SYM = R == 1;
+        constexpr bool SYM = R == 1 && !HW;
         auto kern = k_p2p_units_x2<R, HQ, HW, SYM>;
         if (c.tuned_overlap)
             BEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
