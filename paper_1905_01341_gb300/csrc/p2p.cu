@@ -529,7 +529,7 @@ __device__ __forceinline__ void p2p_unit_gx2(P2PStageX2<R, HQ, HW> &sg, int lane
 }
 
 template <int R, bool HQ, bool HW, bool SYM>
-__global__ void __launch_bounds__(P2P_WARPS * 32, SYM ? 6 : (R == 1 ? 5 : 1)) k_p2p_units_x2(
+__global__ void __launch_bounds__(P2P_WARPS * 32, SYM ? 6 : (R == 1 ? 5 : 4)) k_p2p_units_x2(
     const int2 *__restrict__ units, int64_t nunits, const int32_t *__restrict__ bstart,
     const int32_t *__restrict__ bcount, const int32_t *__restrict__ nbr, const int32_t *__restrict__ ncnt,
     const int8_t *__restrict__ nd, int64_t N, const float *__restrict__ loc, const float *__restrict__ nrm,
