@@ -334,21 +334,24 @@ __device__ __forceinline__ void p2p_tile_x2_sym(P2PStageX2<1, HQ, HW> &sg, int n
     const int e = min(SP, (ns + 1) / 2 - p0);  // pairs of this group holding sources
 #pragma unroll
     for (int h0 = 0; h0 < SP; h0 += HP) {
-        float2 bk[HP];
-#pragma unroll
-        for (int t = 0; t < HP; ++t) bk[t] = make_float2(0.f, 0.f);
         if (ns == 32) {
+            float2 bk[HP];
+#pragma unroll
+            for (int t = 0; t < HP; ++t) bk[t] = make_float2(0.f, 0.f);
 #pragma unroll
             for (int t = 0; t < HP; ++t) p2p_source_x2<1, HQ, HW, false, true>(sg, p0 + h0 + t, X, Y, Z, part, &rv, &bk[t]);
-        } else {
+            float4 *row = reinterpret_cast<float4 *>(&sg.tr[lane][0]);
 #pragma unroll
-            for (int t = 0; t < HP; ++t)
-                if (h0 + t < e) p2p_source_x2<1, HQ, HW, false, true>(sg, p0 + h0 + t, X, Y, Z, part, &rv, &bk[t]);
+            for (int c4 = 0; c4 < NV / 4; ++c4)
+                row[c4] = make_float4(bk[2 * c4].x, bk[2 * c4].y, bk[2 * c4 + 1].x, bk[2 * c4 + 1].y);
+        } else {  // a partial tile: a rolled loop (small code), each pair's shares stored as it goes
+#pragma unroll 1
+            for (int t = 0; t < HP; ++t) {
+                float2 b = make_float2(0.f, 0.f);
+                if (h0 + t < e) p2p_source_x2<1, HQ, HW, false, true>(sg, p0 + h0 + t, X, Y, Z, part, &rv, &b);
+                *reinterpret_cast<float2 *>(&sg.tr[lane][2 * t]) = b;
+            }
         }
-        float4 *row = reinterpret_cast<float4 *>(&sg.tr[lane][0]);
-#pragma unroll
-        for (int c4 = 0; c4 < NV / 4; ++c4)
-            row[c4] = make_float4(bk[2 * c4].x, bk[2 * c4].y, bk[2 * c4 + 1].x, bk[2 * c4 + 1].y);
         __syncwarp();
         float tot = 0.f;
         if constexpr (G == 1) {
@@ -386,7 +389,7 @@ __device__ __forceinline__ void p2p_tile_x2(const P2PStageX2<R, HQ, HW> &sg, int
         for (int t = 0; t < SP; ++t) p2p_source_x2<R, HQ, HW, SELF>(sg, p0 + t, X, Y, Z, part);
     } else {
         const int e = min(SP, (ns + 1) / 2 - p0);
-#pragma unroll 2
+#pragma unroll 1
         for (int t = 0; t < e; ++t) p2p_source_x2<R, HQ, HW, SELF>(sg, p0 + t, X, Y, Z, part);
     }
 #pragma unroll
