@@ -822,6 +822,110 @@ __global__ void __launch_bounds__(L2P_THREADS) k_l2p(int p, const int32_t *__res
     }
 }
 
+// FP32 form of k_l2p with packed two-wide arithmetic (add/mul/fma .f32x2): each lane's two
+// points are the two halves of every recurrence and sum, so one instruction advances both. The
+// tables are stored as broadcast pairs: the local expansion with the real form's factors folded
+// in (m = 0: 1; m > 0: 2 Re, -2 Im), -1/(2k), 1/((n+m)(n-m)) and 2n - 1. Same recurrences, same
+// column order and the same TwoSum over the columns as k_l2p.
+template <int R>
+__global__ void __launch_bounds__(L2P_THREADS) k_l2p_x2(int p, const int32_t *__restrict__ bstart,
+                                                        const int32_t *__restrict__ bcount, int64_t N,
+                                                        const float *__restrict__ loc, const float *__restrict__ lc,
+                                                        float *__restrict__ far) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int P = p * p, ntri = p * (p + 1) / 2;
+    float2 *Ls = reinterpret_cast<float2 *>(smraw);  // [R][P]
+    float2 *tk = Ls + R * P;                          // [p]
+    float2 *tnm = tk + p;                             // [ntri]
+    float2 *c2t = tnm + ntri;                         // [p]: 2n - 1
+    const int b = blockIdx.x;
+    for (int e = threadIdx.x; e < R * P; e += L2P_THREADS) {
+        const int k = e % P;
+        int n = 0;
+        while ((n + 1) * (n + 1) <= k) ++n;
+        const int j = k - n * n;
+        const float f = j == 0 ? 1.f : ((j & 1) ? 2.f : -2.f);
+        const float v = f * lc[(size_t)b * R * P + e];
+        Ls[e] = make_float2(v, v);
+    }
+    for (int e = threadIdx.x; e < p; e += L2P_THREADS) {
+        const float v = e > 0 ? -0.5f / (float)e : 0.f;
+        tk[e] = make_float2(v, v);
+        const float c = (float)(2 * e - 1);
+        c2t[e] = make_float2(c, c);
+    }
+    for (int e = threadIdx.x; e < ntri; e += L2P_THREADS) {
+        int n = 0;
+        while ((n + 1) * (n + 2) / 2 <= e) ++n;
+        const int m = e - n * (n + 1) / 2;
+        const float v = n >= m + 2 ? 1.f / ((float)(n + m) * (float)(n - m)) : 0.f;
+        tnm[e] = make_float2(v, v);
+    }
+    __syncthreads();
+    const int s0 = bstart[b], cnt = bcount[b];
+    for (int c0 = threadIdx.x; c0 < cnt; c0 += 2 * L2P_THREADS) {
+        const bool two = c0 + L2P_THREADS < cnt;
+        const int64_t i0 = s0 + c0, i1 = s0 + (two ? c0 + L2P_THREADS : c0);
+        const float2 X = make_float2(loc[i0], loc[i1]), Y = make_float2(loc[N + i0], loc[N + i1]),
+                     Z = make_float2(loc[2 * N + i0], loc[2 * N + i1]);
+        const float2 NY = make_float2(-Y.x, -Y.y);
+        const float2 R2 = __ffma2_rn(Z, Z, __ffma2_rn(Y, Y, __fmul2_rn(X, X)));
+        const float2 NR2 = make_float2(-R2.x, -R2.y);
+        CompSum<float> acc[2][R];
+        float2 MR = make_float2(1.f, 1.f), MI = make_float2(0.f, 0.f);
+        for (int m = 0; m < p; ++m) {
+            if (m > 0) {
+                const float2 F = tk[m];
+                const float2 a = __ffma2_rn(X, MR, __fmul2_rn(NY, MI));  // x mr - y mi
+                const float2 bb = __ffma2_rn(X, MI, __fmul2_rn(Y, MR));  // x mi + y mr
+                MR = __fmul2_rn(F, a);
+                MI = __fmul2_rn(F, bb);
+            }
+            float2 col[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) col[r] = make_float2(0.f, 0.f);
+            auto term = [&](int n, float2 cr, float2 ci) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float2 *Lr = Ls + r * P + n * n;
+                    if (m == 0) {
+                        col[r] = __ffma2_rn(Lr[0], cr, col[r]);
+                    } else {
+                        col[r] = __ffma2_rn(Lr[2 * m - 1], cr, col[r]);
+                        col[r] = __ffma2_rn(Lr[2 * m], ci, col[r]);
+                    }
+                }
+            };
+            term(m, MR, MI);
+            if (m + 1 < p) {
+                float2 P2R = MR, P2I = MI, P1R = __fmul2_rn(Z, MR), P1I = __fmul2_rn(Z, MI);
+                term(m + 1, P1R, P1I);
+                for (int n = m + 2; n < p; ++n) {
+                    const float2 D = tnm[tri_idx(n, m)];
+                    const float2 C2Z = __fmul2_rn(c2t[n], Z);
+                    const float2 CR = __fmul2_rn(__ffma2_rn(C2Z, P1R, __fmul2_rn(NR2, P2R)), D);
+                    const float2 CI = __fmul2_rn(__ffma2_rn(C2Z, P1I, __fmul2_rn(NR2, P2I)), D);
+                    term(n, CR, CI);
+                    P2R = P1R;
+                    P2I = P1I;
+                    P1R = CR;
+                    P1I = CI;
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                acc[0][r].add(col[r].x);
+                acc[1][r].add(col[r].y);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            far[r * N + i0] = acc[0][r].get();
+            if (two) far[r * N + i1] = acc[1][r].get();
+        }
+    }
+}
+
 template <class T>
 __global__ void k_zero(size_t n, T *a) {
     size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -1085,9 +1189,16 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
     // L2P
     {
         PhaseScope ps(c, PH_L2P, fs);
-        size_t sm = ((size_t)R * P + p + (size_t)p * (p + 1) / 2) * sizeof(T);  // expansion + divisor tables
-        k_l2p<T, R><<<nleaf, L2P_THREADS, sm, fs>>>(p, t.bstart.p + t.base[L], t.bcount.p + t.base[L], N, loc,
-                                                    lc + (size_t)t.base[L] * R * P, far);
+        if constexpr (F64) {
+            size_t sm = ((size_t)R * P + p + (size_t)p * (p + 1) / 2) * sizeof(T);  // expansion + divisor tables
+            k_l2p<T, R><<<nleaf, L2P_THREADS, sm, fs>>>(p, t.bstart.p + t.base[L], t.bcount.p + t.base[L], N, loc,
+                                                        lc + (size_t)t.base[L] * R * P, far);
+        } else {  // packed FP32x2: the expansion and the tables as broadcast pairs
+            size_t sm = ((size_t)R * P + 2 * p + (size_t)p * (p + 1) / 2) * sizeof(float2);
+            k_l2p_x2<R><<<nleaf, L2P_THREADS, sm, fs>>>(p, t.bstart.p + t.base[L], t.bcount.p + t.base[L], N,
+                                                        (const float *)loc, (const float *)lc + (size_t)t.base[L] * R * P,
+                                                        (float *)far);
+        }
         BEM_LAUNCH_CHECK();
     }
     launch_near(c.ev_fork);  // (no M2L pairs: the near field has not started yet)
