@@ -394,6 +394,141 @@ __global__ void __launch_bounds__(256) k_p2m(int p, int nleaf, const int32_t *__
     }
 }
 
+// FP32 single-RHS, single-layer P2M (every GMRES product) in packed two-wide arithmetic
+// (add/mul/fma .f32x2). The same two phases as k_p2m, with the harmonics of a chunk stored as
+// planes re[ntri][P2MX_RS], im[ntri][P2MX_RS] (point index fastest, rows padded against bank
+// conflicts): a recurrence task (order m, four points) runs as two packed pairs of points and
+// stores each pair with one 8-byte store; a coefficient's thread sums q x R over the chunk's
+// points two at a time (q of the points past the chunk's end is zero, their harmonics finite).
+constexpr int P2MX_RS = P2M_PC + 2;
+__global__ void __launch_bounds__(128) k_p2m_x2(int p, int nleaf, const int32_t *__restrict__ bstart,
+                                                const int32_t *__restrict__ bcount, int64_t N,
+                                                const float *__restrict__ loc, const float *__restrict__ q,
+                                                float *__restrict__ mp) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int P = p * p;
+    const int ntri = p * (p + 1) / 2;
+    float *re = reinterpret_cast<float *>(smraw);  // [ntri][P2MX_RS]
+    float *im = re + ntri * P2MX_RS;               // [ntri][P2MX_RS]
+    float *pq = im + ntri * P2MX_RS;               // [P2M_PC]
+    float2 *tk = reinterpret_cast<float2 *>(pq + P2M_PC);  // [p]: -1 / (2k)
+    float2 *c2t = tk + p;                                  // [p]: 2n - 1
+    float2 *tnm = c2t + p;                                 // [ntri]: 1 / ((n + m)(n - m)), n >= m + 2
+    for (int e = threadIdx.x; e < p; e += blockDim.x) {
+        const float v = e > 0 ? -0.5f / (float)e : 0.f, c = (float)(2 * e - 1);
+        tk[e] = make_float2(v, v);
+        c2t[e] = make_float2(c, c);
+    }
+    for (int e = threadIdx.x; e < ntri; e += blockDim.x) {
+        int n = 0;
+        while ((n + 1) * (n + 2) / 2 <= e) ++n;
+        const int m = e - n * (n + 1) / 2;
+        const float v = n >= m + 2 ? 1.f / ((float)(n + m) * (float)(n - m)) : 0.f;
+        tnm[e] = make_float2(v, v);
+    }
+    const int b = blockIdx.x;
+    const int s0 = bstart[b], cnt = bcount[b];
+    constexpr int MAXC = 2;  // complex coefficients per thread (ntri <= 2 * blockDim)
+    int cn[MAXC], cm[MAXC];
+    float2 accr[MAXC], acci[MAXC];
+#pragma unroll
+    for (int o = 0; o < MAXC; ++o) {
+        const int c = threadIdx.x + o * blockDim.x;
+        int n = 0;
+        while ((n + 1) * (n + 2) / 2 <= c) ++n;
+        cn[o] = (c < ntri) ? n : -1;
+        cm[o] = c - n * (n + 1) / 2;
+        accr[o] = acci[o] = make_float2(0.f, 0.f);
+    }
+    for (int c0 = 0; c0 < cnt; c0 += P2M_PC) {
+        const int pc = min(P2M_PC, cnt - c0);
+        __syncthreads();
+        for (int jj = threadIdx.x; jj < P2M_PC; jj += blockDim.x) pq[jj] = jj < pc ? q[s0 + c0 + jj] : 0.f;
+        // recurrence tasks: (order m, four points), the point groups fastest
+        constexpr int NG = P2M_PC / 4;
+        for (int task = threadIdx.x; task < NG * p; task += blockDim.x) {
+            const int g = task % NG, m = task / NG;
+            float2 X[2], Y[2], Z[2], NR2[2], MR[2], MI[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t ia = s0 + c0 + min(g * 4 + 2 * h, pc - 1), ib = s0 + c0 + min(g * 4 + 2 * h + 1, pc - 1);
+                X[h] = make_float2(loc[ia], loc[ib]);
+                Y[h] = make_float2(loc[N + ia], loc[N + ib]);
+                Z[h] = make_float2(loc[2 * N + ia], loc[2 * N + ib]);
+                const float2 r2 = __ffma2_rn(Z[h], Z[h], __ffma2_rn(Y[h], Y[h], __fmul2_rn(X[h], X[h])));
+                NR2[h] = make_float2(-r2.x, -r2.y);
+                MR[h] = make_float2(1.f, 1.f);
+                MI[h] = make_float2(0.f, 0.f);
+            }
+            for (int k = 1; k <= m; ++k) {
+                const float2 F = tk[k];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float2 a = __ffma2_rn(X[h], MR[h], __fmul2_rn(make_float2(-Y[h].x, -Y[h].y), MI[h]));
+                    const float2 bb = __ffma2_rn(X[h], MI[h], __fmul2_rn(Y[h], MR[h]));
+                    MR[h] = __fmul2_rn(F, a);
+                    MI[h] = __fmul2_rn(F, bb);
+                }
+            }
+            float2 P2R[2], P2I[2], P1R[2], P1I[2];
+            const int rmm = tri_idx(m, m) * P2MX_RS + g * 4, rm1 = tri_idx(m + 1, m) * P2MX_RS + g * 4;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                *reinterpret_cast<float2 *>(re + rmm + 2 * h) = MR[h];
+                *reinterpret_cast<float2 *>(im + rmm + 2 * h) = MI[h];
+                P2R[h] = MR[h];
+                P2I[h] = MI[h];
+                P1R[h] = __fmul2_rn(Z[h], MR[h]);
+                P1I[h] = __fmul2_rn(Z[h], MI[h]);
+                if (m + 1 < p) {
+                    *reinterpret_cast<float2 *>(re + rm1 + 2 * h) = P1R[h];
+                    *reinterpret_cast<float2 *>(im + rm1 + 2 * h) = P1I[h];
+                }
+            }
+            for (int n = m + 2; n < p; ++n) {
+                const int idx = tri_idx(n, m);
+                const float2 D = tnm[idx], C2 = c2t[n];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float2 C2Z = __fmul2_rn(C2, Z[h]);
+                    const float2 CR = __fmul2_rn(__ffma2_rn(C2Z, P1R[h], __fmul2_rn(NR2[h], P2R[h])), D);
+                    const float2 CI = __fmul2_rn(__ffma2_rn(C2Z, P1I[h], __fmul2_rn(NR2[h], P2I[h])), D);
+                    *reinterpret_cast<float2 *>(re + idx * P2MX_RS + g * 4 + 2 * h) = CR;
+                    *reinterpret_cast<float2 *>(im + idx * P2MX_RS + g * 4 + 2 * h) = CI;
+                    P2R[h] = P1R[h];
+                    P2I[h] = P1I[h];
+                    P1R[h] = CR;
+                    P1I[h] = CI;
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int o = 0; o < MAXC; ++o) {
+            if (cn[o] < 0) continue;
+            const int row = tri_idx(cn[o], cm[o]) * P2MX_RS;
+#pragma unroll 4
+            for (int jj = 0; jj < P2M_PC; jj += 2) {
+                const float2 Q = *reinterpret_cast<const float2 *>(pq + jj);
+                accr[o] = __ffma2_rn(Q, *reinterpret_cast<const float2 *>(re + row + jj), accr[o]);
+                acci[o] = __ffma2_rn(Q, *reinterpret_cast<const float2 *>(im + row + jj), acci[o]);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < MAXC; ++o) {
+        const int n = cn[o], m = cm[o];
+        if (n < 0) continue;
+        float *dst = mp + (size_t)b * P;
+        if (m == 0) {
+            dst[n * n] = accr[o].x + accr[o].y;
+        } else {
+            dst[n * n + 2 * m - 1] = accr[o].x + accr[o].y;
+            dst[n * n + 2 * m] = -(acci[o].x + acci[o].y);
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------ translations
 // Class-grouped product: for every pair (src, tgt) of a chunk, Y[tgt] += T_cls X[src], as a
 // tiled GEMM (128 output rows x 128 columns per block in FP32, 64 x 64 in FP64; a column is one
@@ -1072,10 +1207,21 @@ void run_fmm(Context &c, const RhsArgs<R> &a, const Operators &opr) {
         const int threads = ntri <= 256 ? 128 : 256;  // ntri <= 2 * threads
         bool hw = false;
         for (int r = 0; r < R; ++r) hw = hw || a.g[r] != 0.0;
-        auto kern = hw ? k_p2m<T, R, true> : k_p2m<T, R, false>;
-        if (sm > 48 * 1024) BEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        kern<<<nleaf, threads, sm, fs>>>(p, nleaf, t.bstart.p + t.base[L], t.bcount.p + t.base[L], N, loc, nrm, q, w,
-                                         mp + (size_t)t.base[L] * R * P);
+        if (!F64 && R == 1 && !hw && ntri <= 256) {  // packed FP32x2 form (every GMRES product)
+            const size_t smx = (size_t)2 * ntri * P2MX_RS * sizeof(float) + P2M_PC * sizeof(float) +
+                               (size_t)(2 * p + ntri) * sizeof(float2);
+            if (smx > 48 * 1024)
+                BEM_CUDA(cudaFuncSetAttribute(k_p2m_x2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx));
+            k_p2m_x2<<<nleaf, 128, smx, fs>>>(p, nleaf, t.bstart.p + t.base[L], t.bcount.p + t.base[L], N,
+                                              (const float *)loc, (const float *)q,
+                                              (float *)mp + (size_t)t.base[L] * P);
+        } else {
+            auto kern = hw ? k_p2m<T, R, true> : k_p2m<T, R, false>;
+            if (sm > 48 * 1024)
+                BEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            kern<<<nleaf, threads, sm, fs>>>(p, nleaf, t.bstart.p + t.base[L], t.bcount.p + t.base[L], N, loc, nrm, q,
+                                             w, mp + (size_t)t.base[L] * R * P);
+        }
         BEM_LAUNCH_CHECK();
     }
     // zero the multipoles above the leaves and all locals
