@@ -329,10 +329,11 @@ struct Context {
     bool diag_tc = false;                     // the 4-RHS diagonal product uses the tensor-core M2L
     int64_t n_tc_chunks[2] = {0, 0};
     DevBuf<uint16_t> xsplit;         // multipoles split into three BF16 planes (tensor-core M2L)
-    // target-major tensor-core M2L, one state per RHS count (1: GMRES products, 4: the diagonal
-    // product): target boxes grouped by octant into tiles of 256 / R targets (256 rows of
-    // (target, rhs)); per tile the offset classes present, by truncated size (ascending), cut into
-    // items of a few classes; each item's partial local expansions, summed per target
+    // target-major tensor-core M2L, one state per RHS count R (index 0: R = 1, index 1: R = 4;
+    // the products use R = 1, the 4-RHS diagonal product the pair-major kernel): target boxes
+    // grouped by octant into tiles of 256 / R targets (256 rows of (target, rhs)); per tile the
+    // offset classes present, by truncated size (ascending), cut into items of a few classes;
+    // each item's partial local expansions, summed per target
     struct TmState {
         bool ok = false;                 // built for the current tree and the operators `ops`
         const Operators *ops = nullptr;

@@ -240,6 +240,30 @@ def test_fmm_apply_is_deterministic(prec):
     ctx.close()
 
 
+@pytest.mark.parametrize("leaf_target", [32, 128])
+def test_symmetric_near_field_single_layer(leaf_target):
+    """Single-layer mixed products (the GMRES products) take the symmetric near field (each pair of
+    neighbour leaves evaluated once, the far leaf's shares added by a second kernel) and the
+    target-major M2L: against the oracle they stay within the mixed bound, and repeated products
+    are bit-identical (every share and partial is summed in a fixed order). With leaves of about
+    128 points every leaf has several work units, each writing its own shares."""
+    bem = _bem()
+    mesh = small_cluster(20, 3, seed=11)
+    ctx = make_ctx(mesh, mvp=bem.BEM_MVP_FMM, precision=bem.BEM_PREC_MIXED, p_fmm=14, leaf_target=leaf_target)
+    x = np.random.Generator(np.random.PCG64(19)).standard_normal(mesh.n)
+    outs = []
+    for _ in range(3):
+        o = torch.zeros(mesh.n, dtype=torch.float64, device="cuda")
+        ctx.apply(1.0, dev(x), 0.0, None, o)
+        outs.append(o.cpu().numpy())
+    ctx.close()
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    ref = oracle.BemOperator(mesh.xyz, mesh.tri).apply(1.0, x, 0.0, np.zeros(mesh.n))
+    err = rel(outs[0], ref)
+    print("leaf target %d: single-layer product vs oracle %.2e" % (leaf_target, err))
+    assert err < 1e-5
+
+
 def test_residual_history_and_mvp_count():
     bem = _bem()
     mesh, phi = synth.workload_single_sphere()
