@@ -379,6 +379,7 @@ struct Context {
         DevBuf<float> inv32;
         DevBuf<int64_t> bub_voff;         // [M] first vertex of each bubble, grouped by shape
         DevBuf<double> bub_scale;         // [M] 1 / (mean centroid distance) at the current geometry
+        DevBuf<float> yf;                 // [N] the right-hand side in FP32 (mixed precision)
     } bp;
     HostPinned<double> hscal;
     // GMRES of independent clusters (gmres_batched.cu): reduction segments and per-cluster state

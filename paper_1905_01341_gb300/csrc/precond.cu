@@ -201,6 +201,72 @@ __global__ void __launch_bounds__(BP_THREADS) k_bp_apply(int n, const T *__restr
     }
 }
 
+// FP32 form of the block product: the right-hand side is converted to FP32 once per
+// application (k_to_f32), then z_b = s_b Inv y_b for all bubbles of one shape as a tiled GEMM:
+// 128 rows x 64 bubbles per block, K in steps of 16 through shared memory, 8 rows x 4 bubbles
+// per thread (rows tx*4 + {0..3} and 64 + tx*4 + {0..3}, bubbles ty*4 + {0..3}) read as 16-byte
+// vectors, FP32 accumulation in a fixed order.
+constexpr int BPF_TM = 128, BPF_TN = 64, BPF_TK = 16, BPF_THREADS = 256;
+__global__ void k_to_f32(int64_t n, const double *__restrict__ y, float *__restrict__ yf) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        yf[i] = (float)y[i];
+}
+__global__ void __launch_bounds__(BPF_THREADS) k_bp_apply_f32(int n, const float *__restrict__ inv, int nb,
+                                                              const int64_t *__restrict__ voff,
+                                                              const double *__restrict__ scale,
+                                                              const float *__restrict__ yf, double *__restrict__ z) {
+    // rows padded by 4 floats: the tile loads (consecutive threads along k) hit two banks at most,
+    // and rows stay 16-byte aligned for the vector reads
+    __shared__ __align__(16) float As[BPF_TK][BPF_TM + 4];
+    __shared__ __align__(16) float Bs[BPF_TK][BPF_TN + 4];
+    __shared__ int64_t sv[BPF_TN];
+    const int row0 = blockIdx.x * BPF_TM, b0 = blockIdx.y * BPF_TN;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    if (tid < BPF_TN) sv[tid] = (b0 + tid < nb) ? voff[b0 + tid] : -1;
+    float acc[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int k0 = 0; k0 < n; k0 += BPF_TK) {
+        __syncthreads();
+        for (int e = tid; e < BPF_TM * BPF_TK; e += BPF_THREADS) {  // As[kk][r] = Inv[row0 + r][k0 + kk]
+            const int r = e / BPF_TK, kk = e % BPF_TK;
+            As[kk][r] = (row0 + r < n && k0 + kk < n) ? inv[(size_t)(row0 + r) * n + k0 + kk] : 0.f;
+        }
+        for (int e = tid; e < BPF_TN * BPF_TK; e += BPF_THREADS) {  // Bs[kk][b] = y_b[k0 + kk]
+            const int bb = e / BPF_TK, kk = e % BPF_TK;
+            const int64_t v = sv[bb];
+            Bs[kk][bb] = (v >= 0 && k0 + kk < n) ? yf[v + k0 + kk] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BPF_TK; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[kk][tx * 4]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[kk][64 + tx * 4]);
+            const float4 bv = *reinterpret_cast<const float4 *>(&Bs[kk][ty * 4]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int bb = ty * 4 + j;
+        const int64_t v = sv[bb];
+        if (v < 0) continue;
+        const double sc = scale[b0 + bb];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int r = row0 + (i < 4 ? tx * 4 + i : 64 + tx * 4 + (i - 4));
+            if (r < n) z[v + r] = sc * (double)acc[i][j];
+        }
+    }
+}
+
 // Bubbles whose meshes have the same connectivity (vertex count and triangle list relative to
 // their first vertex) share one block inverse: the representative's, scaled by size. A mesh
 // copied from one template (every icosphere of one level) is one group however it deforms.
@@ -326,6 +392,11 @@ void block_precond_prepare(Context &c) {
 void block_precond_apply(Context &c, const double *y, double *z) {
     auto &bp = c.bp;
     const bool f64 = c.prm.precision == BEM_PREC_FP64;
+    if (!f64) {  // the right-hand side in FP32 once, for every shape's product
+        bp.yf.resize(c.N);
+        k_to_f32<<<(unsigned)std::min<int64_t>(div_up(c.N, 256), 152 * 8), 256, 0, c.stream>>>(c.N, y, bp.yf.p);
+        BEM_LAUNCH_CHECK();
+    }
     for (size_t k = 0; k + 1 < bp.first.size(); ++k) {
         const int64_t nb = bp.first[k + 1] - bp.first[k];
         if (nb == 0) continue;
@@ -333,10 +404,12 @@ void block_precond_apply(Context &c, const double *y, double *z) {
         const dim3 grid((unsigned)div_up(n, BP_TM), (unsigned)div_up(nb, BP_TN));
         const int64_t *vo = bp.bub_voff.p + bp.first[k];
         const double *sc = bp.bub_scale.p + bp.first[k];
-        if (f64)
+        if (f64) {
             k_bp_apply<double><<<grid, BP_THREADS, 0, c.stream>>>(n, bp.inv64.p + bp.inv_off[k], (int)nb, vo, sc, y, z);
-        else
-            k_bp_apply<float><<<grid, BP_THREADS, 0, c.stream>>>(n, bp.inv32.p + bp.inv_off[k], (int)nb, vo, sc, y, z);
+        } else {
+            const dim3 gf((unsigned)div_up(n, BPF_TM), (unsigned)div_up(nb, BPF_TN));
+            k_bp_apply_f32<<<gf, BPF_THREADS, 0, c.stream>>>(n, bp.inv32.p + bp.inv_off[k], (int)nb, vo, sc, bp.yf.p, z);
+        }
         BEM_LAUNCH_CHECK();
     }
 }
