@@ -571,20 +571,36 @@ __device__ __forceinline__ void two_sum_add(float &s, float &c, float v) {
 }
 
 // lc[box][rhs][col] = sum over the tile's items of the partial row (fixed order, compensated)
+// (the loads of four items are issued before their sums, which stay in item order; a row's
+// coefficients past an item's size read as zero and leave the TwoSum unchanged)
+constexpr int TM_MAXITEMS = (kNumM2LClasses + 3) / 4;  // items of one tile at most (4 classes per item)
 template <int R>
 __global__ void k_tm_reduce(int P, int Npad, const int32_t *__restrict__ tm_box, const int32_t *__restrict__ item_off,
                             const int4 *__restrict__ items, const float *__restrict__ part, float *__restrict__ lc) {
     constexpr int TT = TM_ROWS / R;
+    __shared__ int s_kmax[TM_MAXITEMS];
     const int64_t tile = blockIdx.x;
     const int row = blockIdx.y;
     const int32_t box = tm_box[tile * TT + row / R];
-    if (box < 0) return;
-    const int i0 = item_off[tile], i1 = item_off[tile + 1];
+    if (box < 0) return;  // uniform in the block
+    const int i0 = item_off[tile], i1 = item_off[tile + 1], ni = i1 - i0;
+    for (int i = threadIdx.x; i < ni; i += blockDim.x) s_kmax[i] = items[i0 + i].w;
+    __syncthreads();
     float *dst = lc + ((int64_t)box * R + row % R) * P;
+    const float *src = part + ((int64_t)i0 * TM_ROWS + row) * Npad;
+    const int64_t istride = (int64_t)TM_ROWS * Npad;
     for (int col = threadIdx.x; col < P; col += blockDim.x) {
         float s = 0.f, c = 0.f;
-        for (int i = i0; i < i1; ++i)
-            if (col < items[i].w) two_sum_add(s, c, part[((int64_t)i * TM_ROWS + row) * Npad + col]);
+        int i = 0;
+        for (; i + 4 <= ni; i += 4) {
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = col < s_kmax[i + u] ? src[(i + u) * istride + col] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) two_sum_add(s, c, v[u]);
+        }
+        for (; i < ni; ++i)
+            if (col < s_kmax[i]) two_sum_add(s, c, src[i * istride + col]);
         dst[col] = s + c;
     }
 }
