@@ -770,26 +770,32 @@ __global__ void __launch_bounds__(64) k_reduce_pairs4(int t0, const int32_t *__r
             // truncated classes: the four coefficients (4e .. 4e + 3) % P lie on one side of the
             // pair's class size byK[k] (a multiple of 16) together
             const int n = (4 * e) % P;
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
             int k = a;
-            for (; k + 1 < b; k += 2) {
-                const int p0 = by[k], p1 = by[k + 1];
-                const int K0 = byK[k], K1 = byK[k + 1];
-                const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-                const float4 v0 = n < K0 ? Y4[(size_t)p0 * rp4 + e] : z;
-                const float4 v1 = n < K1 ? Y4[(size_t)p1 * rp4 + e] : z;
-                if (n < K0) add(v0);
-                if (n < K1) add(v1);
+            for (; k + 3 < b; k += 4) {  // four rows in flight, added in pair order
+                float4 v[4];
+                bool in[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    in[u] = n < byK[k + u];
+                    v[u] = in[u] ? Y4[(size_t)by[k + u] * rp4 + e] : z;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (in[u]) add(v[u]);
             }
-            if (k < b && n < byK[k]) add(Y4[(size_t)by[k] * rp4 + e]);
+            for (; k < b; ++k)
+                if (n < byK[k]) add(Y4[(size_t)by[k] * rp4 + e]);
         } else {
             int k = a;
-            for (; k + 1 < b; k += 2) {
-                const float4 v0 = Y4[(size_t)by[k] * rp4 + e];
-                const float4 v1 = Y4[(size_t)by[k + 1] * rp4 + e];
-                add(v0);
-                add(v1);
+            for (; k + 3 < b; k += 4) {
+                float4 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = Y4[(size_t)by[k + u] * rp4 + e];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) add(v[u]);
             }
-            if (k < b) add(Y4[(size_t)by[k] * rp4 + e]);
+            for (; k < b; ++k) add(Y4[(size_t)by[k] * rp4 + e]);
         }
         float4 *dst = reinterpret_cast<float4 *>(Y) + (size_t)t * rp4 + e;
         float4 y = *dst;
