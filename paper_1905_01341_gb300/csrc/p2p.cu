@@ -591,11 +591,20 @@ __global__ void __launch_bounds__(GATHER_WARPS * 32) k_p2p_back_gather(
         const int64_t off = __shfl_sync(0xffffffffu, my_off, k);
         const int sk = __shfl_sync(0xffffffffu, my_S, k);
         const float *p = back + off;
-        for (int u = 0; u < nk; ++u) {
-            const float *pu = p + (int64_t)u * sk;
+        int u = 0;
+        for (; u + 2 <= nk; u += 2) {  // the loads of two units issued before their (ordered) sums
+            const float *pu = p + (int64_t)u * sk, *pv = pu + sk;
             const float x0 = v0 ? pu[j0] : 0.f, x1 = v1 ? pu[j1] : 0.f;
+            const float y0 = v0 ? pv[j0] : 0.f, y1 = v1 ? pv[j1] : 0.f;
             a0.add(x0);
             a1.add(x1);
+            a0.add(y0);
+            a1.add(y1);
+        }
+        for (; u < nk; ++u) {
+            const float *pu = p + (int64_t)u * sk;
+            a0.add(v0 ? pu[j0] : 0.f);
+            a1.add(v1 ? pu[j1] : 0.f);
         }
     }
     const int64_t i0 = bstart[b];
