@@ -260,6 +260,19 @@ int bem_rhs(void *ctx, const double *phi, double *b);
  * |b - L q| / |b|) may be NULL. Returns BEM_ERR_NOCONV when maxit is reached. */
 int bem_solve(void *ctx, const double *phi, double *q_inout, int32_t *iters, double *relres);
 
+/* The bubble-block preconditioner of the solve with gmres_precond = 2, applied once:
+ * z = P y with P = blockdiag_m (1 / R_m) Inv_k(m), Inv_k the inverse of the isolated
+ * single-layer block (Eq. (d1), its diagonal from the identity of Eq. (s5) summed over that
+ * bubble alone) of the first bubble with mesh connectivity k, scaled to unit size, and R_m the
+ * current mean centroid distance of bubble m. Built on the first use after a mesh upload from
+ * the geometry of that moment; the scales follow the current geometry. y and z have length N
+ * (caller's vertex order, host or device memory, not overlapping). Mixed precision: one
+ * tensor-core product per connectivity class, operands split into three BF16 pieces and
+ * accumulated in FP32 (FP32 accuracy); FP64: an FP64 product. Returns BEM_ERR_ARG without
+ * bubble offsets, BEM_ERR_MESH for a non-positive pivot in the setup, BEM_ERR_TIMEOUT when a
+ * tensor-core wait ran out (the output is then undefined). */
+int bem_precond_apply(void *ctx, const double *y, double *z);
+
 /* Copies of the geometry of the last build, in the caller's vertex order: s[N], n[3N]
  * (SoA), Ldiag[N], Mdiag[N]. Any pointer may be NULL. */
 int bem_get_geometry(void *ctx, double *s, double *n, double *ldiag, double *mdiag);

@@ -34,7 +34,7 @@ BEM_MVP_DIRECT = 1
 EXPORTED = [
     "bem_params_default", "bem_create", "bem_destroy", "bem_set_stream", "bem_last_error",
     "bem_mesh_upload", "bem_points_upload", "bem_mesh_set_clusters", "bem_mesh_update_xyz", "fmm_build", "bem_apply", "bem_apply_sl",
-    "bem_apply_dl", "bem_rhs", "bem_solve", "bem_get_geometry", "bem_get_stats",
+    "bem_apply_dl", "bem_rhs", "bem_solve", "bem_precond_apply", "bem_get_geometry", "bem_get_stats",
     "bem_reset_stats", "bem_profile_enable", "bem_profile_read", "bem_phase_name",
     "bem_get_residual_history", "bem_step_params_default", "bem_step_init", "bem_step",
     "bem_step_get_state", "bem_step_set_state", "bem_step_save", "bem_step_load", "bem_apply_direct_noalloc", "bem_mlp_init", "bem_mlp_set_mode", "bem_mlp_train",
@@ -174,6 +174,7 @@ def lib() -> ctypes.CDLL:
             "bem_apply_sl": ([vp, vp, vp], ctypes.c_int),
             "bem_apply_dl": ([vp, vp, vp], ctypes.c_int),
             "bem_rhs": ([vp, vp, vp], ctypes.c_int),
+            "bem_precond_apply": ([vp, vp, vp], ctypes.c_int),
             "bem_solve": ([vp, vp, vp, ctypes.POINTER(i32), ctypes.POINTER(dbl)], ctypes.c_int),
             "bem_get_geometry": ([vp, vp, vp, vp, vp], ctypes.c_int),
             "bem_get_stats": ([vp, ctypes.POINTER(bem_stats)], ctypes.c_int),
@@ -315,6 +316,10 @@ def bem_apply_dl(ctx, phi, out) -> None:
 
 def bem_rhs(ctx, phi, b) -> None:
     _check(ctx, lib().bem_rhs(ctx, _ptr(phi, np.float64), _ptr(b, np.float64)))
+
+
+def bem_precond_apply(ctx, y, z) -> None:
+    _check(ctx, lib().bem_precond_apply(ctx, _ptr(y, np.float64), _ptr(z, np.float64)))
 
 
 def bem_solve(ctx, phi, q_inout, raise_on_noconv: bool = True):
@@ -553,6 +558,9 @@ class BemContext:
 
     def solve(self, phi, q, raise_on_noconv=True):
         return bem_solve(self.ctx, phi, q, raise_on_noconv)
+
+    def precond_apply(self, y, z):
+        bem_precond_apply(self.ctx, y, z)
 
     def stats(self) -> dict:
         return bem_get_stats(self.ctx)

@@ -672,6 +672,19 @@ int bem_rhs(void *ctx, const double *phi, double *b) {
     });
 }
 
+int bem_precond_apply(void *ctx, const double *y, double *z) {
+    return guarded(ctx, [&](Context &c) {
+        require_built(c);
+        if (!y || !z) fail(BEM_ERR_ARG, "null y or z");
+        const double *dy = dev_in(c, y, c.N, 0);
+        OutView ov(c, z, c.N);
+        block_precond_prepare(c);
+        block_precond_apply(c, dy, ov.dev);
+        ov.finish();
+        block_precond_check(c);
+    });
+}
+
 int bem_solve(void *ctx, const double *phi, double *q_inout, int32_t *iters, double *relres) {
     int it = 0;
     double rr = 0.0;

@@ -310,6 +310,7 @@ void gmres_solve(Context &c, const double *b, double *x, int *iters_out, double 
             vec.multiaxpy(kk, c.V.p, N, c.yvec.p, 1.0, x);
         }
     }
+    if (pmode == 2) block_precond_check(c);
     c.stats.last_iters = iters;
     c.stats.last_mvps = mvps;
     c.stats.last_relres = relres;

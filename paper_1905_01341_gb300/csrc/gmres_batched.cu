@@ -430,6 +430,7 @@ void gmres_solve_batched(Context &c, const double *b, double *x, int *iters_out,
         worst = std::max(worst, rel[q]);
         conv_all = conv_all && (bn[q] == 0.0 || rel[q] <= tol);
     }
+    if (pmode == 2) block_precond_check(c);
     c.stats.last_iters = iters;
     c.stats.last_mvps = mvps;
     c.stats.last_relres = worst;

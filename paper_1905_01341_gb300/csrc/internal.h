@@ -249,6 +249,7 @@ struct BubbleShape {
 struct ShBasis {
     int pf = 0, Pf = 0;
     DevBuf<double> G, Gp;
+    DevBuf<float2> Gs, Gps;    // G transposed ([Pf][nd] per shape) and G+ as FP32 (hi, lo) pairs
     DevBuf<int64_t> g_off;     // per shape offset (elements) into G / Gp
     DevBuf<int32_t> shape_of;  // [M] shape index of each bubble
 };
@@ -373,13 +374,15 @@ struct Context {
     struct BlockPrecond {
         bool ready = false;
         std::vector<int> nd;              // vertices per shape
-        std::vector<int64_t> inv_off;     // [shapes + 1] offsets (elements) into inv64 / inv32
+        std::vector<int64_t> inv_off;     // [shapes + 1] offsets (elements) into inv64
         std::vector<int64_t> first;       // [shapes + 1] offsets into the grouped bubble lists
         DevBuf<double> inv64;             // row-major nd x nd per shape, unit size
-        DevBuf<float> inv32;
+        std::vector<int64_t> tc_off;      // [shapes + 1] offsets (elements) into tcA
+        DevBuf<uint16_t> tcA;             // per shape the inverse as three BF16 pieces, K-major blocks
+        bool tc_attr = false;             // the tensor-core apply's shared-memory size is set
         DevBuf<int64_t> bub_voff;         // [M] first vertex of each bubble, grouped by shape
         DevBuf<double> bub_scale;         // [M] 1 / (mean centroid distance) at the current geometry
-        DevBuf<float> yf;                 // [N] the right-hand side in FP32 (mixed precision)
+        DevBuf<uint16_t> ys;              // the right-hand side as three BF16 pieces (mixed precision)
     } bp;
     HostPinned<double> hscal;
     // GMRES of independent clusters (gmres_batched.cu): reduction segments and per-cluster state
@@ -499,6 +502,7 @@ void find_shapes(const Context &c, const std::vector<double> &hx, std::vector<Bu
 // precond.cu: bubble-block preconditioner of GMRES
 void block_precond_prepare(Context &c);                     // build once, refresh the per-bubble scales
 void block_precond_apply(Context &c, const double *y, double *z);  // z = P y
+void block_precond_check(Context &c);  // fails with BEM_ERR_TIMEOUT if a tensor-core wait ran out
 const double *step_initial_xyz(Context &c);
 
 // mlp.cu

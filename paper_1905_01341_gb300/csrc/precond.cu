@@ -18,9 +18,13 @@
 // Gauss-Jordan elimination without pivoting (two launches per pivot). The block is K S with K
 // the symmetric single-layer kernel matrix and S the diagonal of vertex areas, so every
 // leading principal minor is positive when K is positive definite; a pivot that is not
-// positive stops the setup with an error. Apply: one tiled GEMM per shape, FP32 on the mixed
-// path and FP64 on the FP64 path, with the bubbles' vertex ranges as the right-hand columns.
+// positive stops the setup with an error. Apply: one GEMM per shape with the bubbles' vertex
+// ranges as the right-hand columns: on the tensor cores on the mixed path (both operands split
+// into three BF16 pieces, six products accumulated in FP32: as accurate as an FP32 product, so
+// the preconditioner stays one fixed linear map, which right-preconditioned GMRES needs), and a
+// tiled FP64 GEMM on the FP64 path.
 #include "internal.h"
+#include "tcgen05.cuh"
 
 #include <cmath>
 
@@ -88,14 +92,10 @@ __global__ void k_gj_pivot(int n, int k, double *__restrict__ A, const double *_
     }
 }
 
-// inverse at size R -> unit size (times R), FP64 and FP32 copies
-__global__ void k_bp_store(size_t cnt, double R, const double *__restrict__ A, double *__restrict__ o64,
-                           float *__restrict__ o32) {
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < cnt; e += (size_t)gridDim.x * blockDim.x) {
-        const double v = A[e] * R;
-        o64[e] = v;
-        o32[e] = (float)v;
-    }
+// inverse at size R -> unit size (times R)
+__global__ void k_bp_store(size_t cnt, double R, const double *__restrict__ A, double *__restrict__ o64) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < cnt; e += (size_t)gridDim.x * blockDim.x)
+        o64[e] = A[e] * R;
 }
 
 // per bubble of a shape (one block each): 1 / mean distance of its vertices from their centroid
@@ -201,70 +201,187 @@ __global__ void __launch_bounds__(BP_THREADS) k_bp_apply(int n, const T *__restr
     }
 }
 
-// FP32 form of the block product: the right-hand side is converted to FP32 once per
-// application (k_to_f32), then z_b = s_b Inv y_b for all bubbles of one shape as a tiled GEMM:
-// 128 rows x 64 bubbles per block, K in steps of 16 through shared memory, 8 rows x 4 bubbles
-// per thread (rows tx*4 + {0..3} and 64 + tx*4 + {0..3}, bubbles ty*4 + {0..3}) read as 16-byte
-// vectors, FP32 accumulation in a fixed order.
-constexpr int BPF_TM = 128, BPF_TN = 64, BPF_TK = 16, BPF_THREADS = 256;
-__global__ void k_to_f32(int64_t n, const double *__restrict__ y, float *__restrict__ yf) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        yf[i] = (float)y[i];
-}
-__global__ void __launch_bounds__(BPF_THREADS) k_bp_apply_f32(int n, const float *__restrict__ inv, int nb,
-                                                              const int64_t *__restrict__ voff,
-                                                              const double *__restrict__ scale,
-                                                              const float *__restrict__ yf, double *__restrict__ z) {
-    // rows padded by 4 floats: the tile loads (consecutive threads along k) hit two banks at most,
-    // and rows stay 16-byte aligned for the vector reads
-    __shared__ __align__(16) float As[BPF_TK][BPF_TM + 4];
-    __shared__ __align__(16) float Bs[BPF_TK][BPF_TN + 4];
-    __shared__ int64_t sv[BPF_TN];
-    const int row0 = blockIdx.x * BPF_TM, b0 = blockIdx.y * BPF_TN;
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    if (tid < BPF_TN) sv[tid] = (b0 + tid < nb) ? voff[b0 + tid] : -1;
-    float acc[8][4];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-    for (int k0 = 0; k0 < n; k0 += BPF_TK) {
-        __syncthreads();
-        for (int e = tid; e < BPF_TM * BPF_TK; e += BPF_THREADS) {  // As[kk][r] = Inv[row0 + r][k0 + kk]
-            const int r = e / BPF_TK, kk = e % BPF_TK;
-            As[kk][r] = (row0 + r < n && k0 + kk < n) ? inv[(size_t)(row0 + r) * n + k0 + kk] : 0.f;
-        }
-        for (int e = tid; e < BPF_TN * BPF_TK; e += BPF_THREADS) {  // Bs[kk][b] = y_b[k0 + kk]
-            const int bb = e / BPF_TK, kk = e % BPF_TK;
-            const int64_t v = sv[bb];
-            Bs[kk][bb] = (v >= 0 && k0 + kk < n) ? yf[v + k0 + kk] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BPF_TK; ++kk) {
-            const float4 a0 = *reinterpret_cast<const float4 *>(&As[kk][tx * 4]);
-            const float4 a1 = *reinterpret_cast<const float4 *>(&As[kk][64 + tx * 4]);
-            const float4 bv = *reinterpret_cast<const float4 *>(&Bs[kk][ty * 4]);
-            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float b[4] = {bv.x, bv.y, bv.z, bv.w};
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int bb = ty * 4 + j;
-        const int64_t v = sv[bb];
-        if (v < 0) continue;
-        const double sc = scale[b0 + bb];
+// Tensor-core form of the block product (mixed precision). For one shape with n vertices and
+// nb bubbles, Z (n x nb) = Inv (n x n) Y (n x nb) with D = A B^T on tcgen05: A = Inv (row r is
+// K-contiguous), B = Y^T (bubble b's segment is K-contiguous), M = 128 rows, N = 256 bubbles
+// per tile, K in steps of 16. Both operands are stored in global memory already in the
+// canonical K-major blocks of one K step, [piece][K step][rows][16], so that every stage is
+// six contiguous bulk copies (the TMA engine): A from the table split once per build, B from
+// the right-hand side split once per application (k_bp_split_y). Thread 0 fills the stages,
+// thread 32 issues six MMAs per stage (the small cross terms first) and commits each stage to
+// its "empty" barrier; every wait is bounded and raises the error flag when it runs out. The
+// epilogue reads the accumulator tile from TMEM (warp w: lanes 32 (w % 4) .. + 31 = rows,
+// columns 128 (w / 4) .. + 127 = bubbles) and writes z_b[r] = s_b D[r][b] in FP64, 32
+// consecutive rows of one bubble per store instruction.
+constexpr int BPC_M = 128, BPC_N = 256, BPC_STAGES = 4, BPC_THREADS = 256;
+constexpr uint32_t BPC_A_PIECE = BPC_M * TC_K * 2, BPC_B_PIECE = BPC_N * TC_K * 2;
+constexpr uint32_t BPC_STAGE = 3 * (BPC_A_PIECE + BPC_B_PIECE);
+constexpr size_t BPC_SMEM = (size_t)BPC_STAGES * BPC_STAGE + 2 * BPC_STAGES * 8 + 16 + 1024;
+
+// Inv (row-major n x n, FP64) -> [3][nks][Mpad x 16] K-major blocks; zero past n.
+__global__ void k_bp_split_inv(int n, int nks, int Mpad, const double *__restrict__ inv,
+                               __nv_bfloat16 *__restrict__ out) {
+    const int64_t units = (int64_t)Mpad * nks * 2;  // (row, 8-wide K chunk)
+    const size_t plane = (size_t)nks * Mpad * TC_K;
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < units; u += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(u / (nks * 2)), k8 = (int)(u % (nks * 2));
+        const int ks = k8 >> 1, kk0 = (k8 & 1) * 8;
+        __nv_bfloat16 p0[8], p1[8], p2[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const int r = row0 + (i < 4 ? tx * 4 + i : 64 + tx * 4 + (i - 4));
-            if (r < n) z[v + r] = sc * (double)acc[i][j];
+            const int k = ks * TC_K + kk0 + i;
+            split3_d(r < n && k < n ? inv[(size_t)r * n + k] : 0.0, p0[i], p1[i], p2[i]);
+        }
+        const size_t o = (size_t)ks * Mpad * TC_K + kmajor_off(r, kk0);
+        *reinterpret_cast<uint4 *>(out + o) = *reinterpret_cast<const uint4 *>(p0);
+        *reinterpret_cast<uint4 *>(out + plane + o) = *reinterpret_cast<const uint4 *>(p1);
+        *reinterpret_cast<uint4 *>(out + 2 * plane + o) = *reinterpret_cast<const uint4 *>(p2);
+    }
+}
+
+// y_b (FP64, vertices voff_b .. + n - 1) -> [3][nks][NBpad x 16] K-major blocks; zero past n
+// and for the padding bubbles b >= nb.
+__global__ void k_bp_split_y(int n, int nks, int nb, int NBpad, const int64_t *__restrict__ voff,
+                             const double *__restrict__ y, __nv_bfloat16 *__restrict__ out) {
+    const int64_t units = (int64_t)NBpad * nks * 2;  // (bubble, 8-wide K chunk)
+    const size_t plane = (size_t)nks * NBpad * TC_K;
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < units; u += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(u / (nks * 2)), k8 = (int)(u % (nks * 2));
+        const int ks = k8 >> 1, kk0 = (k8 & 1) * 8;
+        const double *yb = b < nb ? y + voff[b] : nullptr;
+        __nv_bfloat16 p0[8], p1[8], p2[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int k = ks * TC_K + kk0 + i;
+            split3_d(yb && k < n ? yb[k] : 0.0, p0[i], p1[i], p2[i]);
+        }
+        const size_t o = (size_t)ks * NBpad * TC_K + kmajor_off(b, kk0);
+        *reinterpret_cast<uint4 *>(out + o) = *reinterpret_cast<const uint4 *>(p0);
+        *reinterpret_cast<uint4 *>(out + plane + o) = *reinterpret_cast<const uint4 *>(p1);
+        *reinterpret_cast<uint4 *>(out + 2 * plane + o) = *reinterpret_cast<const uint4 *>(p2);
+    }
+}
+
+__global__ void __launch_bounds__(BPC_THREADS, 1)
+    k_bp_apply_tc(int n, int nks, int Mpad, int NBpad, int nb, const __nv_bfloat16 *__restrict__ A,
+                  const __nv_bfloat16 *__restrict__ Ys, const int64_t *__restrict__ voff,
+                  const double *__restrict__ scale, double *__restrict__ z, int *__restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)BPC_STAGES * BPC_STAGE);
+    uint64_t *empty = full + BPC_STAGES;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(empty + BPC_STAGES);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    __shared__ int64_t s_v[BPC_N];
+    __shared__ double s_sc[BPC_N];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    __shared__ int s_skip;  // one read of the flag, so that the whole block leaves or stays
+    if (tid == 0) s_skip = *reinterpret_cast<volatile int *>(err);
+    __syncthreads();
+    if (s_skip) return;
+    const int r0 = blockIdx.x * BPC_M, b0 = blockIdx.y * BPC_N;
+    {
+        const int b = b0 + tid;  // BPC_THREADS == BPC_N
+        s_v[tid] = b < nb ? voff[b] : -1;
+        s_sc[tid] = b < nb ? scale[b] : 0.0;
+    }
+    if (tid == 0) {
+        for (int s = 0; s < BPC_STAGES; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "n"(BPC_N));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t sbase = smem_u32(smem);
+    __shared__ int s_last;
+    if (tid == 0) {  // producer: six bulk copies per stage
+        int issued = -1;
+        for (int ks = 0; ks < nks; ++ks) {
+            const int st = ks % BPC_STAGES;
+            if (ks >= BPC_STAGES &&
+                (!mbar_wait(smem_u32(&empty[st]), (uint32_t)((ks / BPC_STAGES - 1) & 1)) || *abort_flag)) {
+                *abort_flag = 1;
+                break;
+            }
+            const uint32_t sa = sbase + st * BPC_STAGE, sb = sa + 3 * BPC_A_PIECE, fb = smem_u32(&full[st]);
+            mbar_expect_tx(fb, BPC_STAGE);
+            for (int piece = 0; piece < 3; ++piece) {
+                bulk_g2s(sa + piece * BPC_A_PIECE, A + ((size_t)(piece * nks + ks) * Mpad + r0) * TC_K, BPC_A_PIECE,
+                         fb);
+                bulk_g2s(sb + piece * BPC_B_PIECE, Ys + ((size_t)(piece * nks + ks) * NBpad + b0) * TC_K,
+                         BPC_B_PIECE, fb);
+            }
+            issued = ks;
+        }
+        // no copy may still be in flight when the block leaves
+        for (int k2 = issued; k2 >= 0 && k2 > issued - BPC_STAGES; --k2)
+            if (!mbar_wait(smem_u32(&full[k2 % BPC_STAGES]), (uint32_t)((k2 / BPC_STAGES) & 1))) *abort_flag = 1;
+    } else if (tid == 32) {  // MMA issuer
+        const uint32_t idesc = make_idesc(BPC_M, BPC_N);
+        int ks = 0;
+        for (; ks < nks; ++ks) {
+            const int st = ks % BPC_STAGES;
+            if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((ks / BPC_STAGES) & 1)) || *abort_flag) {
+                *abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t sa = sbase + st * BPC_STAGE, sb = sa + 3 * BPC_A_PIECE;
+            const uint32_t a0 = sa, a1 = sa + BPC_A_PIECE, a2 = sa + 2 * BPC_A_PIECE;
+            const uint32_t y0 = sb, y1 = sb + BPC_B_PIECE, y2 = sb + 2 * BPC_B_PIECE;
+            mma_bf16(tmem, make_desc(a2), make_desc(y0), idesc, ks > 0 ? 1u : 0u);
+            mma_bf16(tmem, make_desc(a1), make_desc(y1), idesc, 1u);
+            mma_bf16(tmem, make_desc(a0), make_desc(y2), idesc, 1u);
+            mma_bf16(tmem, make_desc(a1), make_desc(y0), idesc, 1u);
+            mma_bf16(tmem, make_desc(a0), make_desc(y1), idesc, 1u);
+            mma_bf16(tmem, make_desc(a0), make_desc(y0), idesc, 1u);
+            mma_commit(smem_u32(&empty[st]));
+        }
+        s_last = ks - 1;
+    }
+    __syncthreads();
+    const int lk = s_last;
+    const bool done =
+        lk >= 0 && mbar_wait(smem_u32(&empty[lk % BPC_STAGES]), (uint32_t)((lk / BPC_STAGES) & 1));
+    const bool ok = !*abort_flag && lk == nks - 1 && done;
+    if (!ok && tid == 0) atomicOr(err, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok) {
+        const int q4 = warp & 3, half = warp >> 2;
+        const int row = r0 + q4 * 32 + lane;
+        for (int c0 = half * 128; c0 < half * 128 + 128 && b0 + c0 < nb; c0 += 16) {
+            uint32_t v[16];
+            const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < n) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int64_t vb = s_v[c0 + i];
+                    if (vb >= 0) z[vb + row] = s_sc[c0 + i] * (double)__uint_as_float(v[i]);
+                }
+            }
         }
     }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(BPC_N));
 }
 
 // Bubbles whose meshes have the same connectivity (vertex count and triangle list relative to
@@ -334,7 +451,13 @@ void build(Context &c) {
     BEM_CUDA(cudaMemcpyAsync(bp.bub_voff.p, grouped.data(), M * sizeof(int64_t), cudaMemcpyHostToDevice, st));
 
     bp.inv64.resize(bp.inv_off.back());
-    bp.inv32.resize(bp.inv_off.back());
+    // the tensor-core tables: per shape [3][n_ks][M_pad x 16]
+    bp.tc_off.assign(ns + 1, 0);
+    for (size_t k = 0; k < ns; ++k) {
+        const int64_t nks = div_up(shapes[k].nd, TC_K), Mpad = (int64_t)div_up(shapes[k].nd, BPC_M) * BPC_M;
+        bp.tc_off[k + 1] = bp.tc_off[k] + 3 * nks * Mpad * TC_K;
+    }
+    bp.tcA.resize(bp.tc_off.back());
     int ndmax = 0;
     for (auto &sh : shapes) ndmax = std::max(ndmax, sh.nd);
     DevBuf<double> A, piv;
@@ -364,7 +487,11 @@ void build(Context &c) {
         }
         const size_t cnt = (size_t)n * n;
         k_bp_store<<<(unsigned)std::min<size_t>(div_up((int64_t)cnt, 256), 4096), 256, 0, st>>>(
-            cnt, R, A.p, bp.inv64.p + bp.inv_off[k], bp.inv32.p + bp.inv_off[k]);
+            cnt, R, A.p, bp.inv64.p + bp.inv_off[k]);
+        const int nks = div_up(n, TC_K), Mpad = div_up(n, BPC_M) * BPC_M;
+        k_bp_split_inv<<<(unsigned)std::min(div_up((int64_t)Mpad * nks * 2, 256), 4096), 256, 0, st>>>(
+            n, nks, Mpad, bp.inv64.p + bp.inv_off[k],
+            reinterpret_cast<__nv_bfloat16 *>(bp.tcA.p) + bp.tc_off[k]);
         BEM_LAUNCH_CHECK();
     }
     int hb = 0;
@@ -380,6 +507,16 @@ void block_precond_prepare(Context &c) {
     if (c.M < 1) fail(BEM_ERR_ARG, "the bubble-block preconditioner needs bubbles (vertex offsets)");
     if (!c.bp.ready) build(c);
     auto &bp = c.bp;
+    if (c.prm.precision != BEM_PREC_FP64) {
+        if (!bp.tc_attr) {
+            BEM_CUDA(cudaFuncSetAttribute(k_bp_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BPC_SMEM));
+            bp.tc_attr = true;
+        }
+        if (c.tc_err.n == 0) {
+            c.tc_err.resize(1);
+            BEM_CUDA(cudaMemsetAsync(c.tc_err.p, 0, sizeof(int), c.stream));
+        }
+    }
     for (size_t k = 0; k + 1 < bp.first.size(); ++k) {
         const int64_t nb = bp.first[k + 1] - bp.first[k];
         if (nb == 0) continue;
@@ -389,26 +526,38 @@ void block_precond_prepare(Context &c) {
     }
 }
 
+void block_precond_check(Context &c) {
+    if (c.prm.precision == BEM_PREC_FP64 || c.tc_err.n == 0) return;
+    int he = 0;
+    BEM_CUDA(cudaMemcpyAsync(&he, c.tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    BEM_CUDA(cudaStreamSynchronize(c.stream));
+    if (he) fail(BEM_ERR_TIMEOUT, "tensor-core wait ran out (preconditioner or M2L)");
+}
+
 void block_precond_apply(Context &c, const double *y, double *z) {
     auto &bp = c.bp;
     const bool f64 = c.prm.precision == BEM_PREC_FP64;
-    if (!f64) {  // the right-hand side in FP32 once, for every shape's product
-        bp.yf.resize(c.N);
-        k_to_f32<<<(unsigned)std::min<int64_t>(div_up(c.N, 256), 152 * 8), 256, 0, c.stream>>>(c.N, y, bp.yf.p);
-        BEM_LAUNCH_CHECK();
-    }
     for (size_t k = 0; k + 1 < bp.first.size(); ++k) {
         const int64_t nb = bp.first[k + 1] - bp.first[k];
         if (nb == 0) continue;
         const int n = bp.nd[k];
-        const dim3 grid((unsigned)div_up(n, BP_TM), (unsigned)div_up(nb, BP_TN));
         const int64_t *vo = bp.bub_voff.p + bp.first[k];
         const double *sc = bp.bub_scale.p + bp.first[k];
         if (f64) {
+            const dim3 grid((unsigned)div_up(n, BP_TM), (unsigned)div_up(nb, BP_TN));
             k_bp_apply<double><<<grid, BP_THREADS, 0, c.stream>>>(n, bp.inv64.p + bp.inv_off[k], (int)nb, vo, sc, y, z);
         } else {
-            const dim3 gf((unsigned)div_up(n, BPF_TM), (unsigned)div_up(nb, BPF_TN));
-            k_bp_apply_f32<<<gf, BPF_THREADS, 0, c.stream>>>(n, bp.inv32.p + bp.inv_off[k], (int)nb, vo, sc, bp.yf.p, z);
+            const int nks = div_up(n, TC_K), Mpad = div_up(n, BPC_M) * BPC_M;
+            const int NBpad = div_up(nb, BPC_N) * BPC_N;
+            bp.ys.resize((size_t)3 * nks * NBpad * TC_K);
+            __nv_bfloat16 *ys = reinterpret_cast<__nv_bfloat16 *>(bp.ys.p);
+            k_bp_split_y<<<(unsigned)std::min(div_up((int64_t)NBpad * nks * 2, 256), 152 * 16), 256, 0, c.stream>>>(
+                n, nks, (int)nb, NBpad, vo, y, ys);
+            BEM_LAUNCH_CHECK();
+            const dim3 grid((unsigned)(Mpad / BPC_M), (unsigned)(NBpad / BPC_N));
+            k_bp_apply_tc<<<grid, BPC_THREADS, BPC_SMEM, c.stream>>>(
+                n, nks, Mpad, NBpad, (int)nb, reinterpret_cast<const __nv_bfloat16 *>(bp.tcA.p) + bp.tc_off[k], ys, vo,
+                sc, z, c.tc_err.p);
         }
         BEM_LAUNCH_CHECK();
     }

@@ -244,6 +244,119 @@ __global__ void k_filter_apply(int64_t N, const int64_t *__restrict__ voff, cons
     }
 }
 
+// The same filter in compensated FP32 arithmetic (mixed precision; FP64 runs at a small fraction
+// of the FP32 rate on this part): G and G+ stored as (hi, lo) FP32 pairs, G transposed to
+// [P][nd] so that both phases read rows of consecutive vertices; the bubble's fields are split
+// the same way as they are staged (FD_CHUNK vertices at a time); every dot product is a TwoProd
+// (with the two cross terms) into a TwoSum-compensated sum: about 48 bits, far below any
+// tolerance of the time step. Phase 1 (c = G+ x): warp w owns the rows p = w, w + FD_WARPS, ...
+// (FD_ROWS per pass) with all four fields, its lanes striding over the vertices, joined by a
+// fixed butterfly; phase 2 (x^ = G c): one thread per vertex, four compensated sums.
+constexpr int FD_THREADS = 256, FD_WARPS = FD_THREADS / 32, FD_ROWS = 5, FD_CHUNK = 256;
+
+__device__ __forceinline__ void cdot_add(float &s, float &c, float2 g, float2 x) {
+    const float p = g.x * x.x;
+    float e = fmaf(g.x, x.x, -p);  // exact error of the leading product
+    e = fmaf(g.x, x.y, e);
+    e = fmaf(g.y, x.x, e);
+    const float t = s + p, bp = t - s;
+    c += ((s - (t - bp)) + (p - bp)) + e;
+    s = t;
+}
+
+__device__ __forceinline__ float2 split_df(double v) {
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+}
+
+// b[p * nd + i] = a[i * P + p] (transpose = true) or b[e] = a[e], as (hi, lo) pairs.
+__global__ void k_split_df(int64_t nd, int P, bool transpose, const double *__restrict__ a,
+                           float2 *__restrict__ b) {
+    const int64_t n = nd * P;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        b[e] = split_df(transpose ? a[(e % nd) * P + e / nd] : a[e]);
+}
+
+__global__ void __launch_bounds__(FD_THREADS) k_filter_apply_df(int64_t N, const int64_t *__restrict__ voff,
+                                                                const int32_t *__restrict__ shape_of,
+                                                                const int64_t *__restrict__ g_off, int P,
+                                                                const float2 *__restrict__ GT,
+                                                                const float2 *__restrict__ Gp, const double *X,
+                                                                double *Y) {
+    extern __shared__ float2 fsm[];
+    float2 *xs = fsm;                 // [4][FD_CHUNK] the fields, split
+    float2 *C = fsm + 4 * FD_CHUNK;   // [P][4] the coefficients, (sum, compensation)
+    const int m = blockIdx.x;
+    const int64_t a = voff[m];
+    const int nd = (int)(voff[m + 1] - a);
+    const float2 *GTm = GT + g_off[shape_of[m]];
+    const float2 *Gpm = Gp + g_off[shape_of[m]];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int r0 = 0; r0 < P; r0 += FD_WARPS * FD_ROWS) {
+        float s[FD_ROWS][4], cc[FD_ROWS][4];
+#pragma unroll
+        for (int r = 0; r < FD_ROWS; ++r)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s[r][k] = cc[r][k] = 0.f;
+        for (int c0 = 0; c0 < nd; c0 += FD_CHUNK) {
+            const int len = min(FD_CHUNK, nd - c0);
+            __syncthreads();
+            for (int e = tid; e < 4 * FD_CHUNK; e += FD_THREADS) {
+                const int comp = e / FD_CHUNK, t = e % FD_CHUNK;
+                if (t < len) xs[e] = split_df(X[comp * N + a + c0 + t]);
+            }
+            __syncthreads();
+#pragma unroll 2
+            for (int t = lane; t < len; t += 32) {
+                float2 g[FD_ROWS];
+#pragma unroll
+                for (int r = 0; r < FD_ROWS; ++r) {
+                    const int p = r0 + warp + r * FD_WARPS;
+                    g[r] = p < P ? Gpm[(size_t)p * nd + c0 + t] : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float2 x = xs[k * FD_CHUNK + t];
+#pragma unroll
+                    for (int r = 0; r < FD_ROWS; ++r) cdot_add(s[r][k], cc[r][k], g[r], x);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < FD_ROWS; ++r) {
+            const int p = r0 + warp + r * FD_WARPS;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float sj = s[r][k], cj = cc[r][k];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float os = __shfl_xor_sync(0xffffffffu, sj, o), oc = __shfl_xor_sync(0xffffffffu, cj, o);
+                    const float t = sj + os, bp = t - sj;
+                    cj += ((sj - (t - bp)) + (os - bp)) + oc;
+                    sj = t;
+                }
+                if (lane == 0 && p < P) C[p * 4 + k] = make_float2(sj, cj);
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < nd; i += FD_THREADS) {
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+#pragma unroll 4
+        for (int p = 0; p < P; ++p) {
+            const float2 gv = GTm[(size_t)p * nd + i];
+            cdot_add(s0, c0, gv, C[p * 4 + 0]);
+            cdot_add(s1, c1, gv, C[p * 4 + 1]);
+            cdot_add(s2, c2, gv, C[p * 4 + 2]);
+            cdot_add(s3, c3, gv, C[p * 4 + 3]);
+        }
+        Y[a + i] = (double)s0 + (double)c0;
+        Y[N + a + i] = (double)s1 + (double)c1;
+        Y[2 * N + a + i] = (double)s2 + (double)c2;
+        Y[3 * N + a + i] = (double)s3 + (double)c3;
+    }
+}
+
 // Eqs. (3.10)-(3.11): v_t,j = (n x v)_j x n_j with (n x v)_j = (1/(3 s_j)) sum_k (n x v)_k A_k
 // and (n x v)_k A_k = [(r2 - r3) phi1 + (r3 - r1) phi2 + (r1 - r2) phi3] / 2.
 __global__ void k_tangential(int64_t N, int64_t T, const double *__restrict__ xyz, const double *__restrict__ phi,
@@ -437,8 +550,15 @@ void apply_filter(Context &c, StepState &s, const double *X, double *Y) {
         if (X != Y) BEM_CUDA(cudaMemcpyAsync(Y, X, 4 * c.N * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
         return;
     }
-    k_filter_apply<<<(unsigned)c.M, 256, (size_t)s.Pf * 4 * sizeof(double), c.stream>>>(
-        c.N, s.voff.p, s.filt.shape_of.p, s.filt.g_off.p, s.Pf, s.filt.G.p, s.filt.Gp.p, X, Y);
+    if (c.prm.precision == BEM_PREC_FP64) {
+        k_filter_apply<<<(unsigned)c.M, 256, (size_t)s.Pf * 4 * sizeof(double), c.stream>>>(
+            c.N, s.voff.p, s.filt.shape_of.p, s.filt.g_off.p, s.Pf, s.filt.G.p, s.filt.Gp.p, X, Y);
+    } else {  // compensated FP32 on the (hi, lo) copies of G and G+
+        const size_t sm = ((size_t)4 * FD_CHUNK + (size_t)s.Pf * 4) * sizeof(float2);
+        k_filter_apply_df<<<(unsigned)c.M, FD_THREADS, sm, c.stream>>>(c.N, s.voff.p, s.filt.shape_of.p,
+                                                                        s.filt.g_off.p, s.Pf, s.filt.Gs.p,
+                                                                        s.filt.Gps.p, X, Y);
+    }
     BEM_LAUNCH_CHECK();
 }
 
@@ -787,6 +907,14 @@ void build_sh_basis(Context &c, int pf, ShBasis &B, int *bad, const double *xyz,
                 BEM_CUDA(cudaStreamSynchronize(st));  // Gt is reused
             }
             k_filter_pinv<<<1, 256, 0, st>>>(sh.nd, Pk[k], B.Pf, B.G.p + goff[k], A.p, B.Gp.p + goff[k], bad);
+            BEM_LAUNCH_CHECK();
+        }
+        B.Gs.resize(goff.back());
+        B.Gps.resize(goff.back());
+        for (size_t k = 0; k < shapes.size(); ++k) {
+            const int64_t n = goff[k + 1] - goff[k];
+            k_split_df<<<grid_for(n), 256, 0, st>>>(shapes[k].nd, B.Pf, true, B.G.p + goff[k], B.Gs.p + goff[k]);
+            k_split_df<<<grid_for(n), 256, 0, st>>>(shapes[k].nd, B.Pf, false, B.Gp.p + goff[k], B.Gps.p + goff[k]);
             BEM_LAUNCH_CHECK();
         }
         B.shape_of.resize(M);

@@ -401,6 +401,45 @@ def test_bubble_block_preconditioner_same_solution_far_fewer_iterations(prec):
     assert its[2] * 2 < its[0]
 
 
+def test_bubble_block_preconditioner_inverts_each_isolated_block():
+    """bem_precond_apply (z = P y) against the oracle. The bubbles are exact scaled and
+    translated copies of two icospheres (levels 2 and 3: two connectivity classes, interleaved
+    in the vertex order), so bubble m's block of P is the inverse of its own isolated
+    single-layer block, and the oracle's single layer of that bubble alone maps z_m back to y_m.
+    The 260 level-2 bubbles span two bubble tiles of the tensor-core product (the second
+    ragged), their 162 rows two ragged row tiles, the level-3 blocks six (ragged), K ragged in
+    both. Mixed precision (split BF16 operands, FP32 accumulation) agrees with the FP64 product
+    to FP32 accuracy and repeats bit for bit."""
+    bem = _bem()
+    rng = np.random.Generator(np.random.PCG64(43))
+    nb = 263
+    levels = np.full(nb, 2)
+    levels[[0, 131, 262]] = 3
+    radii = np.exp(0.3 * rng.standard_normal(nb))
+    centres = synth._place_centres(radii, 4.0 * nb ** (1 / 3), 0.5, rng)
+    mesh = synth.cluster(levels, radii, centres)
+    y = rng.standard_normal(mesh.n)
+    z = {}
+    for prec in (0, 1):
+        ctx = make_ctx(mesh, mvp=bem.BEM_MVP_DIRECT, precision=prec, gmres_precond=2)
+        out = torch.zeros(mesh.n, dtype=torch.float64, device="cuda")
+        ctx.precond_apply(dev(y), out)
+        z[prec] = out.cpu().numpy()
+        if prec == 1:
+            again = torch.zeros_like(out)
+            ctx.precond_apply(dev(y), again)
+            assert torch.equal(out, again)
+        ctx.close()
+    print("mixed vs FP64 product: %.2e" % rel(z[1], z[0]))
+    assert rel(z[1], z[0]) < 5e-6  # FP32 accumulation; a dropped cross term of the split is ~1.5e-5
+    for m in (0, 1, 130, 131, 132, 257, 258, 261, 262):
+        a, b = mesh.vert_off[m], mesh.vert_off[m + 1]
+        op = oracle.BemOperator(mesh.xyz[a:b], mesh.tri[mesh.tri_off[m]:mesh.tri_off[m + 1]] - a)
+        for prec, tol in ((0, 1e-9), (1, 3e-5)):
+            back = op.apply(1.0, z[prec][a:b], 0.0, None)
+            assert rel(back, y[a:b]) < tol, (m, prec, rel(back, y[a:b]))
+
+
 def test_depth_autotuner_keeps_the_operator():
     """leaf_target = 0 times one product at three depths on the first build and keeps the
     fastest; the product at the chosen depth still matches the oracle, and a solve straight
