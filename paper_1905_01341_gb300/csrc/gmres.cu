@@ -7,6 +7,17 @@
 // multi-axpy per pass): the same basis as modified Gram-Schmidt up to rounding, with two
 // reads of V per pass instead of one dependent pass per basis vector. All reductions are
 // two-stage with a fixed summation order, so a solve is reproducible run to run.
+//
+// Mixed precision stores the basis in FP32 (a compressed-basis GMRES, after Aliaga, Anzt et
+// al.): the work vector, the Hessenberg matrix, the rotations and the iterate stay FP64, each
+// v_{k+1} is rounded to FP32 once when it is normalised, and every later use (the product
+// A P v_k, the projections, the solution update) reads that same stored vector, so the Arnoldi
+// relation holds with the stored basis up to the one rounding of each new vector (~6e-8 of its
+// norm, far below the 1e-6 tolerance). The projections V^T w and updates w - V h run in
+// compensated FP32 (an exact product of the FP32 basis value with the (hi, lo) split of the
+// FP64 operand plus the cross term, summed with TwoSum; about 1e-14 relative), half the bytes
+// and none of the FP64 arithmetic of the FP64 basis. Every solve still stops on the FP64 true
+// residual |b - L q| / |b|.
 #include "internal.h"
 
 #include <algorithm>
@@ -34,7 +45,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_multidot(int nv, int64_t N, con
         double s[RED_JB];
 #pragma unroll
         for (int jj = 0; jj < RED_JB; ++jj) s[jj] = 0.0;
-#pragma unroll 2
+#pragma unroll 4
         for (int64_t i = i0 + threadIdx.x; i < i1; i += RED_THREADS) {
             const double wi = w[i];
 #pragma unroll
@@ -83,6 +94,98 @@ __global__ void k_multiaxpy(int nv, int64_t N, const double *__restrict__ V, siz
         for (int j = 0; j < nv; ++j) acc = fma(hs[j], V[j * ldv + i], acc);
         w[i] += sign * acc;
     }
+}
+
+// s + c += p + e with TwoSum (e: the product's rounding error, added to the compensation)
+__device__ __forceinline__ void two_sum_acc(float &s, float &c, float p, float e) {
+    const float t = s + p, bp = t - s;
+    c += ((s - (t - bp)) + (p - bp)) + e;
+    s = t;
+}
+
+// k_multidot with an FP32 basis: partial[j * RED_BLOCKS + block] = the block's share of V_j . w,
+// compensated FP32 per thread, the (sum, compensation) pairs joined in a fixed order
+__global__ void __launch_bounds__(RED_THREADS) k_multidot32(int nv, int64_t N, const float *__restrict__ V,
+                                                            size_t ldv, const double *__restrict__ w,
+                                                            double *__restrict__ partial) {
+    __shared__ float red[2][RED_THREADS / 32][RED_JB];
+    const int64_t chunk = (N + RED_BLOCKS - 1) / RED_BLOCKS;
+    const int64_t i0 = blockIdx.x * chunk, i1 = (N < i0 + chunk) ? N : i0 + chunk;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j0 = 0; j0 < nv; j0 += RED_JB) {
+        const int nj = min(RED_JB, nv - j0);
+        float s[RED_JB], c[RED_JB];
+#pragma unroll
+        for (int jj = 0; jj < RED_JB; ++jj) s[jj] = c[jj] = 0.f;
+#pragma unroll 4
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += RED_THREADS) {
+            const double wi = w[i];
+            const float wh = (float)wi, wl = (float)(wi - (double)wh);
+#pragma unroll
+            for (int jj = 0; jj < RED_JB; ++jj)
+                if (jj < nj) {
+                    const float v = V[(size_t)(j0 + jj) * ldv + i];
+                    const float p = v * wh;
+                    two_sum_acc(s[jj], c[jj], p, fmaf(v, wl, fmaf(v, wh, -p)));
+                }
+        }
+#pragma unroll
+        for (int jj = 0; jj < RED_JB; ++jj) {
+            float t = s[jj], u = c[jj];
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ot = __shfl_down_sync(0xffffffffu, t, o), ou = __shfl_down_sync(0xffffffffu, u, o);
+                two_sum_acc(t, u, ot, ou);
+            }
+            if (lane == 0) {
+                red[0][warp][jj] = t;
+                red[1][warp][jj] = u;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < nj) {
+            double t = 0.0;
+            for (int k = 0; k < RED_THREADS / 32; ++k) t += (double)red[0][k][threadIdx.x] + (double)red[1][k][threadIdx.x];
+            partial[(size_t)(j0 + threadIdx.x) * RED_BLOCKS + blockIdx.x] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// k_multiaxpy with an FP32 basis: w += sign * sum_j h[j] V_j, the sum in compensated FP32 with
+// h split into (hi, lo) pairs, added to the FP64 w once per element
+__global__ void k_multiaxpy32(int nv, int64_t N, const float *__restrict__ V, size_t ldv,
+                              const double *__restrict__ h, double sign, double *__restrict__ w) {
+    __shared__ float2 hs[128];
+    if (threadIdx.x < nv) {
+        const double hv = h[threadIdx.x];
+        const float hh = (float)hv;
+        hs[threadIdx.x] = make_float2(hh, (float)(hv - (double)hh));
+    }
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        float s = 0.f, c = 0.f;
+#pragma unroll 8
+        for (int j = 0; j < nv; ++j) {
+            const float v = V[(size_t)j * ldv + i];
+            const float2 g = hs[j];
+            const float p = g.x * v;
+            two_sum_acc(s, c, p, fmaf(g.y, v, fmaf(g.x, v, -p)));
+        }
+        w[i] += sign * ((double)s + (double)c);
+    }
+}
+
+// v = (float)(w / sqrt(nrm2[0])) into the FP32 basis, and its exact FP64 copy for the product
+__global__ void k_normalise32(int64_t N, const double *__restrict__ w, const double *__restrict__ nrm2,
+                              float *__restrict__ v, double *__restrict__ v64, double *__restrict__ out_norm) {
+    double nn = sqrt(fmax(nrm2[0], 0.0));
+    double inv = nn > 0.0 ? 1.0 / nn : 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const float f = (float)(w[i] * inv);
+        v[i] = f;
+        v64[i] = (double)f;
+    }
+    if (out_norm && blockIdx.x == 0 && threadIdx.x == 0) *out_norm = nn;
 }
 
 // y = alpha * x + beta * y
@@ -177,14 +280,32 @@ struct Vec {
         k_multiaxpy<<<grid, 256, 0, c.stream>>>(nv, N, V, ldv, h, sign, w);
         BEM_LAUNCH_CHECK();
     }
+    // the same with the FP32 basis
+    void dots(int nv, const float *V, size_t ldv, const double *w, double *out, int accumulate) {
+        PhaseScope ps(c, PH_GMRES);
+        k_multidot32<<<RED_BLOCKS, RED_THREADS, 0, c.stream>>>(nv, N, V, ldv, w, c.partial.p);
+        BEM_LAUNCH_CHECK();
+        k_dot_final<<<nv, RED_THREADS, 0, c.stream>>>(c.partial.p, out, accumulate);
+        BEM_LAUNCH_CHECK();
+    }
+    void multiaxpy(int nv, const float *V, size_t ldv, const double *h, double sign, double *w) {
+        PhaseScope ps(c, PH_GMRES);
+        k_multiaxpy32<<<grid, 256, 0, c.stream>>>(nv, N, V, ldv, h, sign, w);
+        BEM_LAUNCH_CHECK();
+    }
+    // v_k = w / |w| into the basis (FP64, or FP32 with the FP64 copy v64); |w| to out_norm
+    void normalise(const double *w, const double *nrm2, double *V, float *V32, int k, double *v64,
+                   double *out_norm) {
+        PhaseScope ps(c, PH_GMRES);
+        if (V32)
+            k_normalise32<<<grid, 256, 0, c.stream>>>(N, w, nrm2, V32 + (size_t)k * N, v64, out_norm);
+        else
+            k_normalise<<<grid, 256, 0, c.stream>>>(N, w, nrm2, V + (size_t)k * N, out_norm);
+        BEM_LAUNCH_CHECK();
+    }
     void axpby(double a, const double *x, double b, double *y) {
         PhaseScope ps(c, PH_GMRES);
         k_axpby<<<grid, 256, 0, c.stream>>>(N, a, x, b, y);
-        BEM_LAUNCH_CHECK();
-    }
-    void normalise(const double *w, const double *nrm2, double *v, double *out_norm) {
-        PhaseScope ps(c, PH_GMRES);
-        k_normalise<<<grid, 256, 0, c.stream>>>(N, w, nrm2, v, out_norm);
         BEM_LAUNCH_CHECK();
     }
 };
@@ -210,7 +331,21 @@ void gmres_solve(Context &c, const double *b, double *x, int *iters_out, double 
     const bool precond = pmode != 0;
     if (precond) c.zv.resize(N);
     if (pmode == 2) block_precond_prepare(c);
-    c.V.resize((size_t)(m + 1) * N);
+    const bool b32 = c.prm.precision != BEM_PREC_FP64;  // the basis in FP32 (mixed precision)
+    if (b32) {
+        c.V32.resize((size_t)(m + 1) * N);
+        c.vk64.resize(N);
+    } else {
+        c.V.resize((size_t)(m + 1) * N);
+    }
+    auto project = [&](int nv, const double *w, double *out) {
+        if (b32) vec.dots(nv, (const float *)c.V32.p, N, w, out, 0);
+        else vec.dots(nv, (const double *)c.V.p, N, w, out, 0);
+    };
+    auto update = [&](int nv, const double *h, double sign, double *w) {
+        if (b32) vec.multiaxpy(nv, (const float *)c.V32.p, N, h, sign, w);
+        else vec.multiaxpy(nv, (const double *)c.V.p, N, h, sign, w);
+    };
     c.wv.resize(N);
     c.rv.resize(N);
     c.partial.resize((size_t)(m + 2) * RED_BLOCKS);
@@ -253,12 +388,12 @@ void gmres_solve(Context &c, const double *b, double *x, int *iters_out, double 
             break;
         }
         if (iters >= maxit) break;
-        vec.normalise(c.rv.p, d_beta2, c.V.p, d_beta);
+        vec.normalise(c.rv.p, d_beta2, c.V.p, b32 ? c.V32.p : nullptr, 0, c.vk64.p, d_beta);
         k_cycle_start<<<1, 128, 0, c.stream>>>(m, d_beta, c.gvec.p);
         BEM_LAUNCH_CHECK();
         int kk = 0;
         for (int k = 0; k < m; ++k) {
-            double *vk = c.V.p + (size_t)k * N;
+            const double *vk = b32 ? c.vk64.p : c.V.p + (size_t)k * N;  // the stored v_k
             if (pmode == 1) {  // w = A D^-1 v_k
                 k_scale_by<<<vec.grid, 256, 0, c.stream>>>(N, c.ldiag.p, vk, c.zv.p);
                 BEM_LAUNCH_CHECK();
@@ -274,15 +409,15 @@ void gmres_solve(Context &c, const double *b, double *x, int *iters_out, double 
             }
             ++mvps;
             // classical Gram-Schmidt, twice
-            vec.dots(k + 1, c.V.p, N, c.wv.p, c.hcol.p, 0);
-            vec.multiaxpy(k + 1, c.V.p, N, c.hcol.p, -1.0, c.wv.p);
-            vec.dots(k + 1, c.V.p, N, c.wv.p, c.yvec.p, 0);  // second pass into y (free here)
-            vec.multiaxpy(k + 1, c.V.p, N, c.yvec.p, -1.0, c.wv.p);
+            project(k + 1, c.wv.p, c.hcol.p);
+            update(k + 1, c.hcol.p, -1.0, c.wv.p);
+            project(k + 1, c.wv.p, c.yvec.p);  // second pass into y (free here)
+            update(k + 1, c.yvec.p, -1.0, c.wv.p);
             k_axpby<<<1, 128, 0, c.stream>>>(k + 1, 1.0, c.yvec.p, 1.0, c.hcol.p);
             BEM_LAUNCH_CHECK();
             vec.dots(1, c.wv.p, N, c.wv.p, d_tmp, 0);
             // h[k+1] = |w|, v_{k+1} = w / |w|
-            vec.normalise(c.wv.p, d_tmp, c.V.p + (size_t)(k + 1) * N, c.hcol.p + k + 1);
+            vec.normalise(c.wv.p, d_tmp, c.V.p, b32 ? c.V32.p : nullptr, k + 1, c.vk64.p, c.hcol.p + k + 1);
             k_givens<<<1, 1, 0, c.stream>>>(k, m, c.hcol.p, c.hmat.p, cs, sn, c.gvec.p, d_res);
             BEM_LAUNCH_CHECK();
             ++iters;
@@ -295,19 +430,19 @@ void gmres_solve(Context &c, const double *b, double *x, int *iters_out, double 
         BEM_LAUNCH_CHECK();
         if (pmode == 1) {  // x += D^-1 V y
             BEM_CUDA(cudaMemsetAsync(c.zv.p, 0, N * sizeof(double), c.stream));
-            vec.multiaxpy(kk, c.V.p, N, c.yvec.p, 1.0, c.zv.p);
+            update(kk, c.yvec.p, 1.0, c.zv.p);
             k_add_scaled<<<vec.grid, 256, 0, c.stream>>>(N, c.ldiag.p, c.zv.p, x);
             BEM_LAUNCH_CHECK();
         } else if (pmode == 2) {  // x += P V y
             BEM_CUDA(cudaMemsetAsync(c.zv.p, 0, N * sizeof(double), c.stream));
-            vec.multiaxpy(kk, c.V.p, N, c.yvec.p, 1.0, c.zv.p);
+            update(kk, c.yvec.p, 1.0, c.zv.p);
             {
                 PhaseScope ps(c, PH_GMRES);
                 block_precond_apply(c, c.zv.p, c.rv.p);
             }
             vec.axpby(1.0, c.rv.p, 1.0, x);
         } else {
-            vec.multiaxpy(kk, c.V.p, N, c.yvec.p, 1.0, x);
+            update(kk, c.yvec.p, 1.0, x);
         }
     }
     if (pmode == 2) block_precond_check(c);

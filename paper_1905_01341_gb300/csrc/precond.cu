@@ -240,13 +240,14 @@ __global__ void k_bp_split_inv(int n, int nks, int Mpad, const double *__restric
 }
 
 // y_b (FP64, vertices voff_b .. + n - 1) -> [3][nks][NBpad x 16] K-major blocks; zero past n
-// and for the padding bubbles b >= nb.
+// and for the padding bubbles b >= nb. Consecutive threads take consecutive bubbles of one
+// 8-wide K chunk, so that a warp's 16-byte pieces form four contiguous 128-byte runs.
 __global__ void k_bp_split_y(int n, int nks, int nb, int NBpad, const int64_t *__restrict__ voff,
                              const double *__restrict__ y, __nv_bfloat16 *__restrict__ out) {
-    const int64_t units = (int64_t)NBpad * nks * 2;  // (bubble, 8-wide K chunk)
+    const int64_t units = (int64_t)NBpad * nks * 2;  // (8-wide K chunk, bubble)
     const size_t plane = (size_t)nks * NBpad * TC_K;
     for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < units; u += (int64_t)gridDim.x * blockDim.x) {
-        const int b = (int)(u / (nks * 2)), k8 = (int)(u % (nks * 2));
+        const int b = (int)(u % NBpad), k8 = (int)(u / NBpad);
         const int ks = k8 >> 1, kk0 = (k8 & 1) * 8;
         const double *yb = b < nb ? y + voff[b] : nullptr;
         __nv_bfloat16 p0[8], p1[8], p2[8];

@@ -385,6 +385,38 @@ __global__ void k_tangential(int64_t N, int64_t T, const double *__restrict__ xy
     vt[2 * N + j] = ax * ny - ay * nx;
 }
 
+// Column c of the elimination of the 5 x 6 system [A | z] of k_curvature: partial pivoting
+// (the row swap as selects), one reciprocal of the pivot, the rows below updated.
+template <int c>
+__device__ __forceinline__ void curv_elim_step(double (&A)[5][6], double (&rp)[5], bool &singular) {
+    int piv = c;
+    double best = fabs(A[c][c]);
+#pragma unroll
+    for (int r = c + 1; r < 5; ++r)
+        if (fabs(A[r][c]) > best) {
+            best = fabs(A[r][c]);
+            piv = r;
+        }
+#pragma unroll
+    for (int r = c + 1; r < 5; ++r) {
+        const bool sw = piv == r;
+#pragma unroll
+        for (int k = c; k < 6; ++k) {
+            const double a = A[c][k], b = A[r][k];
+            A[c][k] = sw ? b : a;
+            A[r][k] = sw ? a : b;
+        }
+    }
+    singular = singular || A[c][c] == 0.0;
+    rp[c] = 1.0 / A[c][c];
+#pragma unroll
+    for (int r = c + 1; r < 5; ++r) {
+        const double f = A[r][c] * rp[c];
+#pragma unroll
+        for (int k = c + 1; k < 6; ++k) A[r][k] -= f * A[c][k];
+    }
+}
+
 // Eqs. (parab1)-(parab2): 5x5 interpolation in the frame (e1, e2, n_j); H = -B3 - B5.
 // Gaussian elimination with partial pivoting (same solution as Cramer's rule).
 __global__ void k_curvature(int64_t N, const double *__restrict__ xyz, const double *__restrict__ nrm,
@@ -392,17 +424,24 @@ __global__ void k_curvature(int64_t N, const double *__restrict__ xyz, const dou
     int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= N) return;
     double n[3] = {nrm[j], nrm[N + j], nrm[2 * N + j]};
+    // e1: the coordinate axis least aligned with n, made orthogonal to n
     int ax = 0;
-    for (int d = 1; d < 3; ++d)
-        if (fabs(n[d]) < fabs(n[ax])) ax = d;
-    double e1[3] = {0, 0, 0};
-    e1[ax] = 1.0;
+    double amin = fabs(n[0]);
+    if (fabs(n[1]) < amin) {
+        ax = 1;
+        amin = fabs(n[1]);
+    }
+    if (fabs(n[2]) < amin) ax = 2;
+    double e1[3] = {ax == 0 ? 1.0 : 0.0, ax == 1 ? 1.0 : 0.0, ax == 2 ? 1.0 : 0.0};
     double dn = e1[0] * n[0] + e1[1] * n[1] + e1[2] * n[2];
+#pragma unroll
     for (int d = 0; d < 3; ++d) e1[d] -= dn * n[d];
     double l1 = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+#pragma unroll
     for (int d = 0; d < 3; ++d) e1[d] /= l1;
     double e2[3] = {n[1] * e1[2] - n[2] * e1[1], n[2] * e1[0] - n[0] * e1[2], n[0] * e1[1] - n[1] * e1[0]};
     double A[5][6];
+#pragma unroll
     for (int l = 0; l < 5; ++l) {
         int k = nbr5[j * 5 + l];
         double d[3] = {xyz[k] - xyz[j], xyz[N + k] - xyz[N + j], xyz[2 * N + k] - xyz[2 * N + j]};
@@ -416,31 +455,27 @@ __global__ void k_curvature(int64_t N, const double *__restrict__ xyz, const dou
         A[l][4] = y * y;
         A[l][5] = z;
     }
-    for (int c = 0; c < 5; ++c) {
-        int piv = c;
-        for (int r = c + 1; r < 5; ++r)
-            if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
-        if (A[piv][c] == 0.0) {
-            atomicOr(bad, 8);
-            H[j] = 0.0;
-            return;
-        }
-        if (piv != c)
-            for (int k = 0; k < 6; ++k) {
-                double t = A[c][k];
-                A[c][k] = A[piv][k];
-                A[piv][k] = t;
-            }
-        for (int r = c + 1; r < 5; ++r) {
-            double f = A[r][c] / A[c][c];
-            for (int k = c; k < 6; ++k) A[r][k] -= f * A[c][k];
-        }
+    // Gaussian elimination with partial pivoting, one step per column instantiated at compile
+    // time so that the system stays in registers
+    double rp[5];
+    bool singular = false;
+    curv_elim_step<0>(A, rp, singular);
+    curv_elim_step<1>(A, rp, singular);
+    curv_elim_step<2>(A, rp, singular);
+    curv_elim_step<3>(A, rp, singular);
+    curv_elim_step<4>(A, rp, singular);
+    if (singular) {
+        atomicOr(bad, 8);
+        H[j] = 0.0;
+        return;
     }
     double B[5];
+#pragma unroll
     for (int r = 4; r >= 0; --r) {
         double s = A[r][5];
+#pragma unroll
         for (int k = r + 1; k < 5; ++k) s -= A[r][k] * B[k];
-        B[r] = s / A[r][r];
+        B[r] = s * rp[r];
     }
     H[j] = -B[2] - B[4];
 }
