@@ -347,6 +347,14 @@ int bem_step(void *ctx, bem_step_stats *st);
 /* Current state: xyz[3N] (SoA), phi[N], the last q[N] and t. Any pointer may be NULL. */
 int bem_step_get_state(void *ctx, double *xyz, double *phi, double *q, double *t);
 
+/* Eqs. (3.22)-(3.25): the shape filter of the time integration applied once, y = x^ with
+ * x^ = G (G+ x) per bubble for each of the four fields of x = (xyz [3N] SoA, phi [N]), using the
+ * bases that bem_step_init built (spherical harmonics of degree < pf, or the torus basis for a
+ * ring-shaped bubble; the identity when pf = 0). Mixed precision evaluates it in compensated
+ * FP32 (G and G+ as (hi, lo) pairs, about 48 bits), FP64 in FP64. x and y have length 4N, host
+ * or device memory, and may be the same array. Returns BEM_ERR_NOT_BUILT before bem_step_init. */
+int bem_step_filter(void *ctx, const double *x, double *y);
+
 /* Replace the current state: xyz[3N] (SoA), phi[N] and the q[N] the next solve starts from (or
  * extrapolates with); any pointer may be NULL (that part is kept). The time, the step size and
  * the history of right-hand sides (Section 3.5) are kept, so the next bem_step continues the

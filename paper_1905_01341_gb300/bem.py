@@ -37,7 +37,7 @@ EXPORTED = [
     "bem_apply_dl", "bem_rhs", "bem_solve", "bem_precond_apply", "bem_get_geometry", "bem_get_stats",
     "bem_reset_stats", "bem_profile_enable", "bem_profile_read", "bem_phase_name",
     "bem_get_residual_history", "bem_step_params_default", "bem_step_init", "bem_step",
-    "bem_step_get_state", "bem_step_set_state", "bem_step_save", "bem_step_load", "bem_apply_direct_noalloc", "bem_mlp_init", "bem_mlp_set_mode", "bem_mlp_train",
+    "bem_step_get_state", "bem_step_set_state", "bem_step_filter", "bem_step_save", "bem_step_load", "bem_apply_direct_noalloc", "bem_mlp_init", "bem_mlp_set_mode", "bem_mlp_train",
     "bem_mlp_loss_grad", "bem_mlp_forward", "bem_mlp_get_params", "bem_mlp_set_params", "bem_mlp_info",
     "bem_m2l_orders", "bem_get_cluster_stats",
 ]
@@ -188,6 +188,7 @@ def lib() -> ctypes.CDLL:
             "bem_step": ([vp, ctypes.POINTER(bem_step_stats)], ctypes.c_int),
             "bem_step_get_state": ([vp, vp, vp, vp, ctypes.POINTER(dbl)], ctypes.c_int),
             "bem_step_set_state": ([vp, vp, vp, vp], ctypes.c_int),
+            "bem_step_filter": ([vp, vp, vp], ctypes.c_int),
             "bem_step_save": ([vp, vp, i64, ctypes.POINTER(i64)], ctypes.c_int),
             "bem_step_load": ([vp, vp, i64], ctypes.c_int),
             "bem_apply_direct_noalloc": ([i64, vp, vp, vp, vp, vp, dbl, vp, dbl, vp, vp, vp], ctypes.c_int),
@@ -374,6 +375,10 @@ def bem_step_get_state(ctx, xyz=None, phi=None, q=None) -> float:
 
 def bem_step_set_state(ctx, xyz=None, phi=None, q=None) -> None:
     _check(ctx, lib().bem_step_set_state(ctx, _ptr(xyz, np.float64), _ptr(phi, np.float64), _ptr(q, np.float64)))
+
+
+def bem_step_filter(ctx, x, y) -> None:
+    _check(ctx, lib().bem_step_filter(ctx, _ptr(x, np.float64), _ptr(y, np.float64)))
 
 
 def bem_step_save(ctx, buf=None) -> int:

@@ -784,6 +784,10 @@ int bem_step_set_state(void *ctx, const double *xyz, const double *phi, const do
     return guarded(ctx, [&](Context &c) { step_set_state(c, xyz, phi, q); });
 }
 
+int bem_step_filter(void *ctx, const double *x, double *y) {
+    return guarded(ctx, [&](Context &c) { step_filter(c, x, y); });
+}
+
 int bem_step_save(void *ctx, void *buf, int64_t cap, int64_t *size) {
     return guarded(ctx, [&](Context &c) {
         if (!c.mesh_ok) fail(BEM_ERR_NOT_BUILT, "no mesh uploaded");

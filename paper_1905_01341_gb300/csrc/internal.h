@@ -494,6 +494,7 @@ void step_init(Context &c, const double *phi0_dev, const double *q0_dev, const b
 void step_advance(Context &c, bem_step_stats &st);
 void step_get_state(Context &c, double *xyz, double *phi, double *q, double *t);
 void step_set_state(Context &c, const double *xyz, const double *phi, const double *q);
+void step_filter(Context &c, const double *x, double *y);
 int64_t step_checkpoint_size(const Context &c);
 void step_save(Context &c, void *buf, int64_t cap);
 void step_load(Context &c, const void *buf, int64_t size);

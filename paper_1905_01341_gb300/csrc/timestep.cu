@@ -65,6 +65,7 @@ struct StepState {
     int order[5] = {0, 1, 2, 3, 4};
     int Pf = 0;
     DevBuf<double> y, q, hist, ks[7], ytmp, yf, f, fp;
+    DevBuf<double> fio;  // host-side arguments of bem_step_filter, staged
     DevBuf<double> V0, a0, V, pg;
     DevBuf<int32_t> bub_of, nbr5;
     DevBuf<int64_t> voff, toff;
@@ -1143,6 +1144,24 @@ void step_get_state(Context &c, double *xyz, double *phi, double *q, double *t) 
     cp(q, s.q.p, N);
     BEM_CUDA(cudaStreamSynchronize(c.stream));
     if (t) *t = s.t;
+}
+
+void step_filter(Context &c, const double *x, double *y) {
+    StepState &s = state_of(c);
+    if (!s.ready) fail(BEM_ERR_NOT_BUILT, "bem_step_init has not been called");
+    if (!x || !y) fail(BEM_ERR_ARG, "null x or y");
+    const int64_t n4 = 4 * c.N;
+    const bool hx = !is_device_ptr(c, x), hy = !is_device_ptr(c, y);
+    if (hx || hy) s.fio.resize(n4);
+    const double *src = x;
+    if (hx) {
+        BEM_CUDA(cudaMemcpyAsync(s.fio.p, x, n4 * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+        src = s.fio.p;
+    }
+    double *dst = hy ? s.fio.p : y;
+    apply_filter(c, s, src, dst);  // in place when both are the staging buffer
+    if (hy) BEM_CUDA(cudaMemcpyAsync(y, dst, n4 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    BEM_CUDA(cudaStreamSynchronize(c.stream));
 }
 
 // ------------------------------------------------------------------------------ checkpoint
