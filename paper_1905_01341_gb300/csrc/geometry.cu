@@ -51,29 +51,39 @@ __global__ void k_sort_lists(int64_t N, const int32_t *__restrict__ off, int32_t
     }
 }
 
-// Eq. (ns1) per vertex.
-__global__ void k_vertex_geometry(int64_t N, int64_t T, const double *__restrict__ xyz,
-                                  const int32_t *__restrict__ tri, const int32_t *__restrict__ off,
+// Eq. (ns1), per triangle: N_k A_k (half the cross product of the edges) and A_k / 3, stored
+// as the pairs (x, y), (z, A_k / 3); computed once per triangle instead of once per corner.
+__global__ void k_tri_area_vectors(int64_t T, int64_t N, const double *__restrict__ xyz,
+                                   const int32_t *__restrict__ tri, double2 *__restrict__ av) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= T) return;
+    const double *X = xyz, *Y = xyz + N, *Z = xyz + 2 * N;
+    const int32_t a = tri[k], b = tri[T + k], c = tri[2 * T + k];
+    const double e1x = X[b] - X[a], e1y = Y[b] - Y[a], e1z = Z[b] - Z[a];
+    const double e2x = X[c] - X[a], e2y = Y[c] - Y[a], e2z = Z[c] - Z[a];
+    const double nax = 0.5 * (e1y * e2z - e1z * e2y);
+    const double nay = 0.5 * (e1z * e2x - e1x * e2z);
+    const double naz = 0.5 * (e1x * e2y - e1y * e2x);
+    const double A = sqrt(nax * nax + nay * nay + naz * naz);
+    av[2 * k] = make_double2(nax, nay);
+    av[2 * k + 1] = make_double2(naz, A / 3.0);
+}
+
+// Eq. (ns1) per vertex: s_j = sum of A_k / 3 and n_j = m_j / |m_j|, m_j = sum of N_k A_k over the
+// vertex's triangles in vertex-to-triangle list order.
+__global__ void k_vertex_geometry(int64_t N, const double2 *__restrict__ av, const int32_t *__restrict__ off,
                                   const int32_t *__restrict__ v2t, double *__restrict__ s,
                                   double *__restrict__ nrm, int *__restrict__ bad) {
     int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= N) return;
-    const double *X = xyz, *Y = xyz + N, *Z = xyz + 2 * N;
     double sj = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
     for (int t = off[j]; t < off[j + 1]; ++t) {
-        int64_t k = v2t[t];
-        int32_t a = tri[k], b = tri[T + k], c = tri[2 * T + k];
-        double e1x = X[b] - X[a], e1y = Y[b] - Y[a], e1z = Z[b] - Z[a];
-        double e2x = X[c] - X[a], e2y = Y[c] - Y[a], e2z = Z[c] - Z[a];
-        // N_k A_k is half the cross product of the edges; A_k its length.
-        double nax = 0.5 * (e1y * e2z - e1z * e2y);
-        double nay = 0.5 * (e1z * e2x - e1x * e2z);
-        double naz = 0.5 * (e1x * e2y - e1y * e2x);
-        double A = sqrt(nax * nax + nay * nay + naz * naz);
-        sj += A / 3.0;
-        mx += nax;
-        my += nay;
-        mz += naz;
+        const int64_t k = v2t[t];
+        const double2 u = av[2 * k], w = av[2 * k + 1];
+        sj += w.y;
+        mx += u.x;
+        my += u.y;
+        mz += w.x;
     }
     double len = sqrt(mx * mx + my * my + mz * mz);
     if (!(sj > 0.0) || !(len > 0.0)) {
@@ -122,8 +132,13 @@ void compute_vertex_geometry(Context &c) {
     c.s.resize(c.N);
     c.nrm.resize(3 * c.N);
     int tb = 256;
-    k_vertex_geometry<<<div_up(c.N, tb), tb, 0, st>>>(c.N, c.T, c.xyz.p, c.tri.p, c.v2t_off.p, c.v2t.p,
-                                                      c.s.p, c.nrm.p, bad.p);
+    c.tri_tmp.resize(2 * (size_t)c.T);
+    if (c.T > 0) {
+        k_tri_area_vectors<<<div_up(c.T, tb), tb, 0, st>>>(c.T, c.N, c.xyz.p, c.tri.p, c.tri_tmp.p);
+        BEM_LAUNCH_CHECK();
+    }
+    k_vertex_geometry<<<div_up(c.N, tb), tb, 0, st>>>(c.N, c.tri_tmp.p, c.v2t_off.p, c.v2t.p, c.s.p, c.nrm.p,
+                                                      bad.p);
     BEM_LAUNCH_CHECK();
     int hbad = 0;
     BEM_CUDA(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -350,6 +350,7 @@ struct Context {
     };
     TmState tm[2];
     DevBuf<int> tc_err;              // set by a tensor-core block whose wait ran out
+    DevBuf<double2> tri_tmp;         // [2T] per-triangle pairs: area vectors, then (n x v)_k A_k
     // per-build and per-step scratch kept in the context (a cudaFree synchronises the device):
     // flags of the finiteness and mesh checks, one per check site, and the diagonal product's output
     DevBuf<int> chk[4];

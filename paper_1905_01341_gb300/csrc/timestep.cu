@@ -358,23 +358,36 @@ __global__ void __launch_bounds__(FD_THREADS) k_filter_apply_df(int64_t N, const
     }
 }
 
-// Eqs. (3.10)-(3.11): v_t,j = (n x v)_j x n_j with (n x v)_j = (1/(3 s_j)) sum_k (n x v)_k A_k
-// and (n x v)_k A_k = [(r2 - r3) phi1 + (r3 - r1) phi2 + (r1 - r2) phi3] / 2.
-__global__ void k_tangential(int64_t N, int64_t T, const double *__restrict__ xyz, const double *__restrict__ phi,
-                             const int32_t *__restrict__ tri, const int32_t *__restrict__ off,
+// Eq. (3.11) per triangle: (n x v)_k A_k = [(r2 - r3) phi1 + (r3 - r1) phi2 + (r1 - r2) phi3] / 2,
+// stored as the pairs (x, y), (z, 0); computed once per triangle instead of once per corner.
+__global__ void k_tri_nxv(int64_t T, int64_t N, const double *__restrict__ xyz, const double *__restrict__ phi,
+                          const int32_t *__restrict__ tri, double2 *__restrict__ w) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= T) return;
+    const double *X = xyz, *Y = xyz + N, *Z = xyz + 2 * N;
+    const int a = tri[k], b = tri[T + k], c = tri[2 * T + k];
+    const double pa = phi[a], pb = phi[b], pc = phi[c];
+    const double wx = 0.5 * ((X[b] - X[c]) * pa + (X[c] - X[a]) * pb + (X[a] - X[b]) * pc);
+    const double wy = 0.5 * ((Y[b] - Y[c]) * pa + (Y[c] - Y[a]) * pb + (Y[a] - Y[b]) * pc);
+    const double wz = 0.5 * ((Z[b] - Z[c]) * pa + (Z[c] - Z[a]) * pb + (Z[a] - Z[b]) * pc);
+    w[2 * k] = make_double2(wx, wy);
+    w[2 * k + 1] = make_double2(wz, 0.0);
+}
+
+// Eqs. (3.10)-(3.11): v_t,j = (n x v)_j x n_j with (n x v)_j = (1/(3 s_j)) sum_k (n x v)_k A_k over
+// the vertex's triangles in vertex-to-triangle list order.
+__global__ void k_tangential(int64_t N, const double2 *__restrict__ w, const int32_t *__restrict__ off,
                              const int32_t *__restrict__ v2t, const double *__restrict__ s,
                              const double *__restrict__ nrm, double *__restrict__ vt) {
     int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= N) return;
-    const double *X = xyz, *Y = xyz + N, *Z = xyz + 2 * N;
     double ax = 0, ay = 0, az = 0;
     for (int t = off[j]; t < off[j + 1]; ++t) {
-        int64_t k = v2t[t];
-        int a = tri[k], b = tri[T + k], c = tri[2 * T + k];
-        double pa = phi[a], pb = phi[b], pc = phi[c];
-        ax += 0.5 * ((X[b] - X[c]) * pa + (X[c] - X[a]) * pb + (X[a] - X[b]) * pc);
-        ay += 0.5 * ((Y[b] - Y[c]) * pa + (Y[c] - Y[a]) * pb + (Y[a] - Y[b]) * pc);
-        az += 0.5 * ((Z[b] - Z[c]) * pa + (Z[c] - Z[a]) * pb + (Z[a] - Z[b]) * pc);
+        const int64_t k = v2t[t];
+        const double2 u = w[2 * k], v = w[2 * k + 1];
+        ax += u.x;
+        ay += u.y;
+        az += v.x;
     }
     double inv = 1.0 / (3.0 * s[j]);
     ax *= inv;
@@ -492,9 +505,9 @@ __global__ void k_volumes(int64_t N, int64_t T, const int64_t *__restrict__ toff
         int a = tri[k], b = tri[T + k], c = tri[2 * T + k];
         double e1x = X[b] - X[a], e1y = Y[b] - Y[a], e1z = Z[b] - Z[a];
         double e2x = X[c] - X[a], e2y = Y[c] - Y[a], e2z = Z[c] - Z[a];
-        double nax = 0.5 * (e1y * e2z - e1z * e2y), nay = 0.5 * (e1z * e2x - e1x * e2z), naz = 0.5 * (e1x * e2y - e1y * e2x);
-        double cx = (X[a] + X[b] + X[c]) / 3.0, cy = (Y[a] + Y[b] + Y[c]) / 3.0, cz = (Z[a] + Z[b] + Z[c]) / 3.0;
-        acc += (nax * cx + nay * cy + naz * cz) / 3.0;
+        // 2 N_k A_k . 3 c_k; the constant factor 1/18 is applied once to the bubble's sum
+        double nx2 = e1y * e2z - e1z * e2y, ny2 = e1z * e2x - e1x * e2z, nz2 = e1x * e2y - e1y * e2x;
+        acc += nx2 * (X[a] + X[b] + X[c]) + ny2 * (Y[a] + Y[b] + Y[c]) + nz2 * (Z[a] + Z[b] + Z[c]);
     }
     red[threadIdx.x] = acc;
     __syncthreads();
@@ -502,7 +515,7 @@ __global__ void k_volumes(int64_t N, int64_t T, const int64_t *__restrict__ toff
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0) V[m] = red[0];
+    if (threadIdx.x == 0) V[m] = red[0] / 18.0;
 }
 
 __global__ void k_init_bubbles(int M, const double *__restrict__ V, double *__restrict__ V0, double *__restrict__ a0) {
@@ -713,8 +726,12 @@ void rhs(Context &c, StepState &s, const double *y, double t, double *f, bem_ste
     const int tb = 256;
     s.vt.resize(3 * N);
     s.H.resize(N);
-    k_tangential<<<div_up(N, tb), tb, 0, c.stream>>>(N, c.T, s.yf.p, s.yf.p + 3 * N, c.tri.p, c.v2t_off.p, c.v2t.p,
-                                                      c.s.p, c.nrm.p, s.vt.p);
+    c.tri_tmp.resize(2 * (size_t)c.T);
+    if (c.T > 0) {
+        k_tri_nxv<<<div_up(c.T, tb), tb, 0, c.stream>>>(c.T, N, s.yf.p, s.yf.p + 3 * N, c.tri.p, c.tri_tmp.p);
+        BEM_LAUNCH_CHECK();
+    }
+    k_tangential<<<div_up(N, tb), tb, 0, c.stream>>>(N, c.tri_tmp.p, c.v2t_off.p, c.v2t.p, c.s.p, c.nrm.p, s.vt.p);
     BEM_LAUNCH_CHECK();
     DevBuf<int> &bad = c.chk[3];
     bad.resize(1);
