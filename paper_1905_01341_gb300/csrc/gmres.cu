@@ -16,8 +16,16 @@
 // norm, far below the 1e-6 tolerance). The projections V^T w and updates w - V h run in
 // compensated FP32 (an exact product of the FP32 basis value with the (hi, lo) split of the
 // FP64 operand plus the cross term, summed with TwoSum; about 1e-14 relative), half the bytes
-// and none of the FP64 arithmetic of the FP64 basis. Every solve still stops on the FP64 true
-// residual |b - L q| / |b|.
+// and none of the FP64 arithmetic of the FP64 basis.
+//
+// A solve stops on the residual r = b - L q evaluated with operator products, not on GMRES's
+// own estimate: the first cycle starts from r_0 = b - A x_0 (a product of the initial iterate),
+// and every cycle ends with r = r_0 - A d, d = P V y its update, one product of d. Evaluating
+// A on the whole new iterate instead would round x_0 + d to the mixed product's FP32 inputs a
+// second time, which moves A x by about 1e-7 of |b| (a tenth of a 1e-6 tolerance) in a direction
+// unrelated to the Krylov space, so that a cycle whose estimate met the tolerance could fail the
+// check and restart for no gain; r_0 - A d agrees with the estimate to the rounding of A d, and
+// the next cycle starts from it.
 #include "internal.h"
 
 #include <algorithm>
@@ -244,11 +252,6 @@ __global__ void k_scale_by(int64_t N, const double *__restrict__ d, const double
         z[i] = v[i] / d[i];
 }
 
-// x += t ./ d
-__global__ void k_add_scaled(int64_t N, const double *__restrict__ d, const double *__restrict__ t, double *__restrict__ x) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-        x[i] += t[i] / d[i];
-}
 
 // Back substitution: H(0:kk,0:kk) y = g(0:kk).
 __global__ void k_backsolve(int kk, int m, const double *__restrict__ H, const double *__restrict__ g,
@@ -373,12 +376,14 @@ void gmres_solve(Context &c, const double *b, double *x, int *iters_out, double 
         if (relres_out) *relres_out = 0.0;
         return;
     }
-    bool converged = false;
+    bool converged = false, have_r = false;
+    c.dv.resize(N);
     while (true) {
-        // r = b - A x
-        apply_full(c, 1.0, x, 0.0, nullptr, c.rv.p);
-        ++mvps;
-        vec.axpby(1.0, b, -1.0, c.rv.p);
+        if (!have_r) {  // r = b - A x, the product of the full iterate (the first cycle's start)
+            apply_full(c, 1.0, x, 0.0, nullptr, c.rv.p);
+            ++mvps;
+            vec.axpby(1.0, b, -1.0, c.rv.p);
+        }
         vec.dots(1, c.rv.p, N, c.rv.p, d_beta2, 0);
         double beta = std::sqrt(read_scalar(c, d_beta2));
         relres = beta / bnorm;
@@ -428,22 +433,27 @@ void gmres_solve(Context &c, const double *b, double *x, int *iters_out, double 
         }
         k_backsolve<<<1, 1, 0, c.stream>>>(kk, m, c.hmat.p, c.gvec.p, c.yvec.p);
         BEM_LAUNCH_CHECK();
-        if (pmode == 1) {  // x += D^-1 V y
+        // the cycle's update d = P V y (P = D^-1, the bubble blocks or the identity), x += d
+        if (pmode == 1) {
             BEM_CUDA(cudaMemsetAsync(c.zv.p, 0, N * sizeof(double), c.stream));
             update(kk, c.yvec.p, 1.0, c.zv.p);
-            k_add_scaled<<<vec.grid, 256, 0, c.stream>>>(N, c.ldiag.p, c.zv.p, x);
+            k_scale_by<<<vec.grid, 256, 0, c.stream>>>(N, c.ldiag.p, c.zv.p, c.dv.p);
             BEM_LAUNCH_CHECK();
-        } else if (pmode == 2) {  // x += P V y
+        } else if (pmode == 2) {
             BEM_CUDA(cudaMemsetAsync(c.zv.p, 0, N * sizeof(double), c.stream));
             update(kk, c.yvec.p, 1.0, c.zv.p);
-            {
-                PhaseScope ps(c, PH_GMRES);
-                block_precond_apply(c, c.zv.p, c.rv.p);
-            }
-            vec.axpby(1.0, c.rv.p, 1.0, x);
+            PhaseScope ps(c, PH_GMRES);
+            block_precond_apply(c, c.zv.p, c.dv.p);
         } else {
-            update(kk, c.yvec.p, 1.0, x);
+            BEM_CUDA(cudaMemsetAsync(c.dv.p, 0, N * sizeof(double), c.stream));
+            update(kk, c.yvec.p, 1.0, c.dv.p);
         }
+        vec.axpby(1.0, c.dv.p, 1.0, x);
+        // r = r_0 - A d: the product of the update, not of the whole iterate (see the header)
+        apply_full(c, 1.0, c.dv.p, 0.0, nullptr, c.wv.p);
+        ++mvps;
+        vec.axpby(-1.0, c.wv.p, 1.0, c.rv.p);
+        have_r = true;
     }
     if (pmode == 2) block_precond_check(c);
     c.stats.last_iters = iters;

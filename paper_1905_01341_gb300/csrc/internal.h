@@ -369,6 +369,7 @@ struct Context {
 
     // GMRES
     DevBuf<double> V, wv, rv, bv, zv, hcol, hmat, givens, gvec, yvec, partial, scal;
+    DevBuf<double> dv;   // a GMRES cycle's update d = P V y
     DevBuf<float> V32;   // the Krylov basis in FP32 (mixed precision)
     DevBuf<double> vk64; // the current basis vector of V32 in FP64, the product's input
     // bubble-block preconditioner (gmres_precond = 2, precond.cu): per distinct bubble mesh
