@@ -257,7 +257,8 @@ void gmres_solve_batched(Context &c, const double *b, double *x, int *iters_out,
         BEM_CUDA(cudaMemcpyAsync(dst.p, v.data(), C * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream));
         BEM_CUDA(cudaStreamSynchronize(c.stream));  // the host vector may change right after
     };
-    // x += P V y for the clusters in `sel` (y is zero for the others)
+    // x += t and d += t, t = P V y for the clusters in `sel` (y is zero for the others); the work
+    // vector w is free whenever this runs (after a Givens step, or at the end of a cycle)
     auto update = [&](const std::vector<int32_t> &kk, const std::vector<int32_t> &sel) {
         upload(G.kk, kk);
         upload(G.sel, sel);
@@ -269,16 +270,18 @@ void gmres_solve_batched(Context &c, const double *b, double *x, int *iters_out,
         k_backsolve_b<<<gc, 128, 0, c.stream>>>(m, C, G.kk.p, G.sel.p, G.H.p, G.g.p, G.y.p);
         BEM_LAUNCH_CHECK();
         if (pmode == 0) {
-            k_segaxpy<<<g1, 256, 0, c.stream>>>(kmax, N, C, c.V.p, N, G.y.p, c.vcid.p, 1.0, x);
+            BEM_CUDA(cudaMemsetAsync(c.wv.p, 0, N * sizeof(double), c.stream));
+            k_segaxpy<<<g1, 256, 0, c.stream>>>(kmax, N, C, c.V.p, N, G.y.p, c.vcid.p, 1.0, c.wv.p);
             BEM_LAUNCH_CHECK();
         } else {
             BEM_CUDA(cudaMemsetAsync(c.zv.p, 0, N * sizeof(double), c.stream));
             k_segaxpy<<<g1, 256, 0, c.stream>>>(kmax, N, C, c.V.p, N, G.y.p, c.vcid.p, 1.0, c.zv.p);
             BEM_LAUNCH_CHECK();
-            precond_apply(c.zv.p, c.rv.p);
-            k_axpby_b<<<g1, 256, 0, c.stream>>>(N, 1.0, c.rv.p, 1.0, x);
-            BEM_LAUNCH_CHECK();
+            precond_apply(c.zv.p, c.wv.p);
         }
+        k_axpby_b<<<g1, 256, 0, c.stream>>>(N, 1.0, c.wv.p, 1.0, x);
+        k_axpby_b<<<g1, 256, 0, c.stream>>>(N, 1.0, c.wv.p, 1.0, c.dv.p);
+        BEM_LAUNCH_CHECK();
     };
 
     // per-cluster right-hand-side norms
@@ -315,12 +318,22 @@ void gmres_solve_batched(Context &c, const double *b, double *x, int *iters_out,
         k_zero_clusters<<<g1, 256, 0, c.stream>>>(N, c.vcid.p, G.sel.p, x);
         BEM_LAUNCH_CHECK();
     }
+    bool have_r = false;
+    c.dv.resize(N);
     while (true) {
-        // true residuals r = b - A x, per cluster
-        apply_full(c, 1.0, x, 0.0, nullptr, c.rv.p);
+        // residuals per cluster: r = b - A x on entry, then r = r_0 - A d after each cycle (d the
+        // cycle's updates; zero, with a zero product, on clusters it did not update), for the
+        // reason given in gmres.cu
+        if (!have_r) {
+            apply_full(c, 1.0, x, 0.0, nullptr, c.rv.p);
+            k_axpby_b<<<g1, 256, 0, c.stream>>>(N, 1.0, b, -1.0, c.rv.p);
+        } else {
+            apply_full(c, 1.0, c.dv.p, 0.0, nullptr, c.wv.p);
+            k_axpby_b<<<g1, 256, 0, c.stream>>>(N, -1.0, c.wv.p, 1.0, c.rv.p);
+        }
         ++mvps;
-        k_axpby_b<<<g1, 256, 0, c.stream>>>(N, 1.0, b, -1.0, c.rv.p);
         BEM_LAUNCH_CHECK();
+        have_r = true;
         segdots(1, c.rv.p, N, c.rv.p, G.nrm2.p, 0);
         const std::vector<double> beta2 = read_C(G.nrm2.p);
         double worst = 0.0;
@@ -341,6 +354,7 @@ void gmres_solve_batched(Context &c, const double *b, double *x, int *iters_out,
         k_segnormalise<<<g1, 256, 0, c.stream>>>(N, c.rv.p, G.nrm2.p, c.vcid.p, G.active.p, c.V.p);
         k_cycle_start_b<<<gc, 128, 0, c.stream>>>(m, C, G.nrm2.p, G.g.p);
         BEM_LAUNCH_CHECK();
+        BEM_CUDA(cudaMemsetAsync(c.dv.p, 0, N * sizeof(double), c.stream));
         std::fill(kk.begin(), kk.end(), 0);
         std::vector<int32_t> conv(C, 0);  // converged within this cycle (solution already updated)
         for (int k = 0; k < m; ++k) {
