@@ -256,8 +256,10 @@ int bem_apply_dl(void *ctx, const double *phi, double *out);
 int bem_rhs(void *ctx, const double *phi, double *b);
 
 /* Eqs. (3.1)-(3.2), Section 3.8: given phi on S solve L q = b by GMRES with initial guess
- * q_inout (in), returning q in q_inout. iters and relres (true relative residual
- * |b - L q| / |b|) may be NULL. Returns BEM_ERR_NOCONV when maxit is reached. */
+ * q_inout (in), returning q in q_inout. iters and relres may be NULL. relres is the relative
+ * residual |b - L q| / |b| evaluated with operator products, not GMRES's estimate: b - L q_0 for
+ * the initial guess, then r_0 - L d at the end of every restart cycle (d the cycle's update of q),
+ * and the solve stops when it meets gmres_tol. Returns BEM_ERR_NOCONV when maxit is reached. */
 int bem_solve(void *ctx, const double *phi, double *q_inout, int32_t *iters, double *relres);
 
 /* The bubble-block preconditioner of the solve with gmres_precond = 2, applied once:
