@@ -113,6 +113,38 @@ def test_create_reports_errors_without_gpu(lib):
         bem.bem_create(bem.bem_params_default(), 0)
 
 
+def test_entry_points_reject_a_null_context():
+    """Every entry point that takes a context returns BEM_ERR_ARG for a NULL one, with the reason
+    in bem_last_error(NULL), before any CUDA call (host only): the context check comes first in
+    each of them, the ones added for the preconditioner and the filter included."""
+    import ctypes
+
+    from paper_1905_01341_gb300 import bem
+
+    L = bem.lib()
+    checked = []
+    for name in bem.EXPORTED:
+        fn = getattr(L, name)
+        args = fn.argtypes or []
+        if not args or args[0] is not ctypes.c_void_p or fn.restype is not ctypes.c_int:
+            continue
+        vals = []
+        for a in args:
+            if a is ctypes.c_double:
+                vals.append(0.0)
+            elif a in (ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64):
+                vals.append(0)
+            else:
+                vals.append(None)
+        assert fn(*vals) == bem.BEM_ERR_ARG, name
+        assert b"null context" in L.bem_last_error(None), name
+        checked.append(name)
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "bem.h")).read(), flags=re.S)
+    with_ctx = set(re.findall(r"^int\s+([a-z_0-9]+)\s*\(\s*void\s*\*\s*ctx\b", text, re.M))
+    assert set(checked) == with_ctx
+    assert {"bem_precond_apply", "bem_step_filter", "bem_solve"} <= with_ctx
+
+
 def test_m2l_class_orders_follow_the_separation():
     """Per-class M2L truncation (host logic, no GPU): margin -1 keeps every class at p; otherwise
     the six nearest classes (face offsets 2 boxes apart) keep p, orders never grow with the
